@@ -1,0 +1,104 @@
+"""Locality reordering and the device connectivity tables (oracle; test infrastructure only).
+
+The paper's "Divide and conqueror" section motivates keeping neighbouring triangles together in
+memory (KD parts, shared-boundary length).  Within one mesh the library orders triangles by
+reverse Cuthill-McKee on the dual graph (triangles joined by interior edges).  The paper gives
+no tie-break rules; the ones used here (and, independently, by the library) are:
+
+* components in increasing order of their smallest caller triangle id;
+* the start of a component is its triangle of minimum (degree, caller id), degree = number of
+  interior edges;
+* breadth-first: each dequeued triangle appends its unvisited neighbours sorted by
+  (degree, caller id);
+* the concatenated order is reversed at the end.
+
+From an order the tables follow (same definitions in the library, separate code):
+
+* ``perm_tri[new] = caller triangle id``;
+* each triangle's CCW vertex triple is rotated so that its smallest caller node id comes first;
+  its edges A(j, q) are then (v_q, v_q+1);
+* interior edges are numbered by (min, max) of their two new triangle ids;
+  ``edge_caller[k]`` = caller edge id, ``edge_tri[k] = (R, L)`` in new triangle ids;
+* ``tri_code[j, q] = 2 k + (s(j,q) < 0)`` for an interior edge k, ``2 n_ei`` for a boundary edge
+  (a slot whose value stays 0).
+
+Parity: pinned by tests/test_oracle_mesh.py (valid permutation, contiguous components, a strip
+whose RCM order is known in closed form, bandwidth not above the caller order's on lattices).
+"""
+from __future__ import annotations
+
+from collections import deque
+
+import numpy as np
+
+from .mesh import Mesh
+
+
+def dual_adjacency(mesh: Mesh):
+    nbr = [[] for _ in range(mesh.n_tris)]
+    for i in mesh.interior_ids:
+        r, l = int(mesh.R[i]), int(mesh.L[i])
+        nbr[r].append(l)
+        nbr[l].append(r)
+    return nbr
+
+
+def rcm_order(mesh: Mesh) -> np.ndarray:
+    nbr = dual_adjacency(mesh)
+    deg = [len(a) for a in nbr]
+    n = mesh.n_tris
+    seen = [False] * n
+    order = []
+    for root in range(n):
+        if seen[root]:
+            continue
+        # collect the component to find its start vertex
+        comp = [root]
+        seen[root] = True
+        k = 0
+        while k < len(comp):
+            for w in nbr[comp[k]]:
+                if not seen[w]:
+                    seen[w] = True
+                    comp.append(w)
+            k += 1
+        for v in comp:
+            seen[v] = False
+        start = min(comp, key=lambda v: (deg[v], v))
+        q = deque([start])
+        seen[start] = True
+        while q:
+            v = q.popleft()
+            order.append(v)
+            for w in sorted((w for w in nbr[v] if not seen[w]), key=lambda w: (deg[w], w)):
+                seen[w] = True
+                q.append(w)
+    return np.asarray(order[::-1], np.int64)
+
+
+def device_tables(mesh: Mesh, perm_tri: np.ndarray):
+    """Connectivity tables for a given triangle order (see module docstring)."""
+    n_t = mesh.n_tris
+    new_of = np.empty(n_t, np.int64)
+    new_of[perm_tri] = np.arange(n_t)
+    tv = mesh.tris[perm_tri]
+    rot = np.argmin(tv, axis=1)
+    idx = (rot[:, None] + np.arange(3)[None, :]) % 3
+    tv = np.take_along_axis(tv, idx, axis=1)
+    te = np.take_along_axis(mesh.tri_edge[perm_tri], idx, axis=1)
+    ts = np.take_along_axis(mesh.tri_sign[perm_tri], idx, axis=1)
+    ie = mesh.interior_ids
+    r = new_of[mesh.R[ie]]
+    l = new_of[mesh.L[ie]]
+    lo = np.minimum(r, l)
+    hi = np.maximum(r, l)
+    o = np.lexsort((hi, lo))
+    edge_caller = ie[o]
+    edge_tri = np.stack([r[o], l[o]], axis=1)
+    n_ei = ie.size
+    k_of_edge = np.full(mesh.n_edges, n_ei, np.int64)
+    k_of_edge[edge_caller] = np.arange(n_ei)
+    k = k_of_edge[te]
+    code = 2 * k + ((ts < 0) & (k < n_ei))
+    return dict(perm_tri=perm_tri.astype(np.int64), tri_nodes=tv, edge_caller=edge_caller,
+                edge_tri=edge_tri, tri_code=code, n_ei=n_ei)

@@ -1,0 +1,132 @@
+"""Spectrum, stability bound (eq. 20), dispersion (eqs. 18-19) and cavity convergence pins."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize_scalar
+
+import meshgen
+from oracle import leapfrog as lf, mesh as om, operators, spectral
+
+
+def _ops(ms):
+    return operators.Operators(om.canonicalize(ms.xy, ms.tris))
+
+
+@pytest.fixture(scope="module")
+def small():
+    return _ops(meshgen.cavity_lattice(17, 9, 1.0, 0.5, seed=7))   # 256 triangles
+
+
+def test_power_iteration_and_bracket_against_dense_eigenvalues(small):
+    rho_dense = spectral.dense_rho(small)
+    rho_pi, hist = spectral.power_iteration(small, 200, seed=3)
+    lo, hi = spectral.certified_bracket(small)
+    assert lo <= rho_dense <= hi
+    assert rho_pi <= rho_dense * (1 + 1e-12)           # Rayleigh quotient: a lower bound
+    assert rho_pi >= rho_dense * (1 - 2e-3)
+    assert np.all(np.diff(hist) >= -1e-9 * hist[-1])    # monotone for a PSD operator
+
+
+def test_omegas_are_real_and_zero_modes_exist(small):
+    """Section 2: w real (K PSD), and a static subspace (uniform B) of zero eigenvalues."""
+    lam = np.linalg.eigvalsh(spectral.symmetric_K(small))
+    assert lam.min() > -1e-9 * lam.max()
+    assert np.sum(np.abs(lam) < 1e-9 * lam.max()) >= 1
+
+
+def test_stability_bound_brute_force(small):
+    """Eq. 20: leap-frog is bounded at dt = 0.99 * 2/rho and grows at 1.01 * 2/rho."""
+    rho = spectral.dense_rho(small)
+    rng = np.random.default_rng(0)
+    res = {}
+    for f in (0.99, 1.01):
+        st = lf.State(rng.standard_normal(small.n_ei), rng.standard_normal(small.n_t),
+                      np.zeros(small.n_ei), 0)
+        w0 = lf.energy_W(small, st.E, st.B)
+        with np.errstate(all="ignore"):
+            st = lf.run(small, st, f * 2.0 / rho, 3000)
+            res[f] = lf.energy_W(small, st.E, st.B) / w0
+    assert res[0.99] < 1e3
+    assert not np.isfinite(res[1.01]) or res[1.01] > 1e6
+
+
+def test_yee_limit_on_merged_right_split_lattice():
+    """Cocircular pairs merged: the right-split lattice is Yee's mesh; all modes match
+    w^2 = (4/hx^2) sin^2(m pi hx / 2a) + (4/hy^2) sin^2(n pi hy / 2b)."""
+    nx, ny, a, b = 13, 8, 1.2, 0.7
+    ms = meshgen.right_split_lattice(nx, ny, a, b)
+    m = om.canonicalize(ms.xy, ms.tris)
+    mo = operators.MergedOperators(m)
+    assert mo.n_c == (nx - 1) * (ny - 1)
+    LB = mo.L_B.toarray()
+    G = LB.T @ (mo.w_E[:, None] * LB)
+    s = 1 / np.sqrt(mo.w_B)
+    lam = np.sort(np.linalg.eigvalsh(s[:, None] * G * s[None, :]))
+    hx, hy = a / (nx - 1), b / (ny - 1)
+    M, N = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1))
+    yee = np.sort(((4 / hx ** 2) * np.sin(M * np.pi * hx / (2 * a)) ** 2
+                   + (4 / hy ** 2) * np.sin(N * np.pi * hy / (2 * b)) ** 2).ravel())
+    np.testing.assert_allclose(lam, yee, rtol=1e-10, atol=1e-9 * yee.max())
+
+
+def _mode_series(ops, v, w, dt, nsteps):
+    st = lf.State(np.zeros(ops.n_ei), v.copy(), np.zeros(ops.n_ei), 0)
+    amp = []
+    lf.run(ops, st, dt, nsteps, record=lambda s: amp.append(np.dot(ops.w_B * s.B, v)))
+    return np.array(amp)
+
+
+def test_leapfrog_dispersion_relation(small):
+    """Eqs. 18-19: a mode of frequency w steps with sin(W dt/2) = w dt/2; the mode amplitude
+    obeys b_{n+1} + b_{n-1} = 2 cos(W dt) b_n exactly."""
+    lam, V = np.linalg.eigh(spectral.symmetric_K(small))
+    rho = math.sqrt(lam[-1])
+    for k in (len(lam) // 3, len(lam) - 1):
+        w = math.sqrt(lam[k])
+        v = V[:, k] / np.sqrt(small.w_B)        # back from the symmetric form
+        v /= math.sqrt(np.dot(small.w_B * v, v))
+        dt = 0.9 * 2 / rho
+        b = _mode_series(small, v, w, dt, 60)
+        Wdt = 2 * math.asin(w * dt / 2)
+        np.testing.assert_allclose(b[2:] + b[:-2], 2 * math.cos(Wdt) * b[1:-1], atol=1e-9)
+
+
+def _fit_frequency(t, a):
+    a = a - a.mean()
+    spec = np.abs(np.fft.rfft(a * np.hanning(a.size)))
+    f0 = np.argmax(spec[1:]) + 1
+    w0 = 2 * np.pi * f0 / (t[-1] - t[0]) * (a.size - 1) / a.size
+
+    def resid(w):
+        X = np.stack([np.cos(w * t), np.sin(w * t), np.ones_like(t)], 1)
+        c, *_ = np.linalg.lstsq(X, a, rcond=None)
+        return np.sum((X @ c - a) ** 2)
+
+    r = minimize_scalar(resid, bracket=(0.9 * w0, w0, 1.1 * w0), tol=1e-12)
+    return r.x
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 1)])
+def test_cavity_TE_frequency_converges(m, n):
+    """North-star check (c): measured TE(m,n) frequency -> pi sqrt((m/a)^2 + (n/b)^2)."""
+    a, b = 1.0, 0.5
+    exact = math.pi * math.sqrt((m / a) ** 2 + (n / b) ** 2)
+    errs = []
+    for k in (16, 32, 64):
+        ms = meshgen.cavity_lattice(k + 1, k // 2 + 1, a, b, seed=1001 + k)
+        ops = _ops(ms)
+        rho, _ = spectral.power_iteration(ops, 200)
+        dt = 1.0 / rho
+        B0 = meshgen.te_mode_b(ops.geom.O, m, n, a, b)
+        T = 6 * 2 * math.pi / exact
+        nsteps = int(T / dt)
+        amp = []
+        st = lf.State(np.zeros(ops.n_ei), B0.copy(), np.zeros(ops.n_ei), 0)
+        lf.run(ops, st, dt, nsteps, record=lambda s: amp.append(np.dot(ops.w_B * s.B, B0)))
+        t = (np.arange(nsteps) + 1.5) * dt
+        W = _fit_frequency(t, np.array(amp))
+        w = 2 / dt * math.sin(W * dt / 2)          # undo the leap-frog dispersion (eq. 19)
+        errs.append(abs(w - exact) / exact)
+    assert errs[0] < 0.02
+    assert errs[2] < errs[0] / 3
