@@ -1,0 +1,295 @@
+"""Benchmark: leap-frog triangle-steps per second on the ~4M-triangle scatterer workload.
+
+One bench "step" is one full leap-frog step (E half-step over every interior edge, the line
+source, B half-step over every triangle) of the graded unit-square mesh with an equilateral
+PEC hole (h 2e-4 .. 8e-4, ~4M triangles, RCM order, FP32 fields, FP64-built coefficients).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line.  ``value`` = triangles * K / device time of the K timed steps (inputs
+resident in HBM); ``e2e`` = the same work through the public API with host buffers: fields
+written from pinned host memory, K steps, fields read back, all inside the timed region.
+``roofline`` refers to the dominant kernel, timed per launch with CUDA events on the launch
+stream in a window right after the timed region; ``cpu_baseline`` is the FP64 oracle on a
+bounded window of the same workload.  ``--impl reference`` times that oracle alone.
+N > 1 (torchrun): independent replicas, one per GPU, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("scatterer-4M: unit square, PEC walls and PEC equilateral hole (side 0.2, centre "
+            "(0.5,0.5)), spacing graded 2e-4..8e-4, jitter 0.2h, RCM order, FP32 fields, line "
+            "source x=0.35, w0=2*pi*20")
+METRIC = "cell-updates/s"
+UNIT = "triangle-steps/s"
+L2_BYTES = 129e6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload():
+    import meshgen
+    ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, 2e-4)
+    return ms, ids, amp, 2 * math.pi * 20, 0.1, 0.05
+
+
+def cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, max_steps, budget_s):
+    """Time the FP64 oracle on this workload for up to max_steps steps / budget_s seconds."""
+    from oracle import leapfrog as lf, mesh as om, operators
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    src = lf.Source(ids, amp, w0, t0, tau)
+    st = lf.initial_state(ops)
+    cols = ops.col_of_edge[src.edge_ids]
+    st = lf.step(ops, st, dt, source=src, src_cols=cols)      # first touch
+    n = 0
+    t = time.perf_counter()
+    while n < max_steps and (n < 3 or time.perf_counter() - t < budget_s):
+        st = lf.step(ops, st, dt, source=src, src_cols=cols)
+        n += 1
+    el = time.perf_counter() - t
+    return ms.n_tris * n / el, n, el
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    ms, ids, amp, w0, t0, tau = load_workload()
+    from oracle import mesh as om, operators, spectral
+    # the oracle takes the same dt the library would (dt = 0.5 * 2 / rho, rho by power iteration)
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    rho, _ = spectral.power_iteration(ops, 200)
+    dt = 1.0 / rho
+    del ops
+    rate, n, el = cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, args.steps, 60.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tris": ms.n_tris},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} of {args.steps} leap-frog steps on the full mesh "
+                                   f"(numpy/scipy.sparse FP64, {el:.1f} s)"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+
+    ms, ids, amp, w0, t0, tau = load_workload()
+    stream = torch.cuda.current_stream()
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(stream=stream)
+    dt, rho, _ = m.get_dt()
+    m.set_source(ids, amp, w0, t0, tau)
+    st = m.stats()
+    n_t, n_ei = st["n_tris"], st["n_interior_edges"]
+
+    # warm-up (also captures the step graph)
+    m.step_n(args.warmup, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    launches0 = m.stats()["kernel_launches"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        m.step_n(args.steps, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = m.stats()["kernel_launches"] - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * n_t * args.steps / (ms_total * 1e-3)
+
+    # per-kernel device times, CUDA events on the launch stream, right after the timed region
+    prof_ms, prof_bytes = m.profile_steps(min(200, max(20, args.steps // 10)), stream)
+    names = ["E half-step (eq. 3)", "source", "B half-step (eq. 4)"]
+    k = int(np.argmax(prof_ms))
+    peak, peak_kind = _peaks()
+    achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
+    step_bytes = st["bytes_per_step"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": names[k],
+            "bytes_per_launch": prof_bytes[k], "ms_per_launch": prof_ms[k],
+            "peak_kind": f"{peak_kind} (STREAM-style copy)",
+            "step": {"bytes": step_bytes, "achieved_gbs": step_bytes * args.steps / (ms_total * 1e-3) / 1e9,
+                     "frac": step_bytes * args.steps / (ms_total * 1e-3) / 1e9 / peak,
+                     "kernel_ms": [float(x) for x in prof_ms]}}
+
+    # end to end through the public API with host buffers
+    E0 = torch.zeros(m.n_edges, dtype=torch.float64, pin_memory=True).numpy()
+    B0 = torch.zeros(m.n_tris, dtype=torch.float64, pin_memory=True).numpy()
+    Eo = torch.empty(m.n_edges, dtype=torch.float64, pin_memory=True).numpy()
+    Bo = torch.empty(m.n_tris, dtype=torch.float64, pin_memory=True).numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    m.write_fields(E0, B0, stream=stream)
+    m.set_step(0)
+    m.step_n(args.steps, stream)
+    m.read_fields(out={"E": Eo, "B": Bo}, stream=stream)
+    t_e2e = time.perf_counter() - t_e2e
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    io = 8.0 * (m.n_edges + m.n_tris)
+    e2e = {"value": world * n_t * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
+           "what": "ue_write_fields (pinned host) + ue_step_n(K) + ue_read_fields (pinned host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el = cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, 10 ** 9, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} leap-frog steps of the full mesh in {el:.1f} s (numpy/scipy.sparse FP64, one thread)"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_tris": n_t, "n_interior_edges": n_ei,
+                       "n_edges": m.n_edges, "dt": dt, "rho": rho, "variant": "plain, CUDA graph of 32 steps",
+                       "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * ue.h - C ABI of the leap-frog Maxwell solver on unstructured triangle meshes.
+ *
+ * Method: D.A. Fadeev, "Numerical simulation of 2D electrodynamic problems with unstructured
+ * triangular meshes".  E (and the plasma current j) live on edges, B (out of plane) at the
+ * triangles' circumcentres, the plasma density n on nodes (Section 1, Fig. 1).  One time step
+ * is the leap-frog pair of eq. 14 (E from t to t+dt, with eq. 3 or, in plasma, eqs. 5-6) and
+ * eq. 15 (B from t+dt/2 to t+3dt/2 with eq. 4).
+ *
+ * Conventions shared by every call:
+ *  - All arrays passed in or out are HOST arrays in the CALLER's numbering, owned by the caller;
+ *    the library copies what it needs before returning.  Device memory is the library's.
+ *  - Nodes: xy[2*v + 0/1].  Triangles: tris[3*j + 0..2] (any orientation; the library makes
+ *    them counter-clockwise using the sign of the FP64 orientation determinant).
+ *  - Edges are the unique unordered node pairs, numbered by sorting (low id, high id)
+ *    lexicographically.  E_i is the projection of E on the edge directed low -> high node id
+ *    (the paper leaves the direction free, Fig. 2).  Boundary edges (one triangle) are perfect
+ *    conductors: E = 0 there (ideal resonator, eq. 10); they are not unknowns.
+ *  - R(i) is the triangle around which edge i runs counter-clockwise, L(i) the other (the
+ *    choice that makes eq. 10 vanish).  B is the +z component for right-handed (x, y).
+ *  - Time levels: after k steps E is at k*dt, B and j at (k + 1/2)*dt.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = legacy default stream).
+ *  - Return codes: UE_OK or a negative UE_ERR_*; ue_last_error() gives the text (per thread).
+ *    No C++ exception crosses this boundary.
+ */
+#ifndef UE_H
+#define UE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UE_OK 0
+#define UE_ERR_ARG (-1)          /* bad argument, size or state                               */
+#define UE_ERR_NONMANIFOLD (-2)  /* an edge with >2 triangles, or two on the same side        */
+#define UE_ERR_DEGENERATE (-3)   /* zero orientation determinant or repeated vertex           */
+#define UE_ERR_DUAL (-4)         /* |O_R O_L| <= 0 on an interior edge (mesh not Delaunay)    */
+#define UE_ERR_CUDA (-5)         /* a CUDA runtime call failed                                */
+#define UE_ERR_ALLOC (-6)        /* device allocation failed (callback returned NULL)         */
+#define UE_ERR_UNSTABLE (-7)     /* energy watchdog: growth or non-finite field               */
+#define UE_ERR_TIMEOUT (-8)      /* a bounded device wait ran out (persistent kernels)        */
+
+#define UE_REORDER_NONE 0        /* triangles in caller order                                 */
+#define UE_REORDER_RCM 1         /* reverse Cuthill-McKee on the dual graph (default)         */
+
+#define UE_PREC_FP32 0           /* FP32 fields and coefficients (product)                    */
+#define UE_PREC_FP64 1           /* FP64 fields and coefficients (check build)                */
+
+#define UE_DT_GIVEN 0            /* use ue_options.dt                                         */
+#define UE_DT_POWER 1            /* dt = safety * 2 / rho(M), rho by FP64 power iteration     */
+
+#define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
+
+#define UE_RHO_GIVEN 0
+#define UE_RHO_POWER 1
+
+typedef struct ue_mesh ue_mesh;  /* opaque, owned by the library until ue_mesh_free        */
+
+/* Device allocator hooks: alloc(bytes, stream, ctx) returns a device pointer or NULL;
+ * free(ptr, stream, ctx) releases it.  Both NULL = cudaMalloc / cudaFree. */
+typedef void* (*ue_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ue_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct ue_options {
+    int32_t reorder;       /* UE_REORDER_*, used by ue_mesh_load                              */
+    int32_t precision;     /* UE_PREC_*                                                      */
+    int32_t dt_mode;       /* UE_DT_*                                                        */
+    int32_t power_iters;   /* power-iteration steps (default 200)                            */
+    uint32_t power_seed;   /* start vector: SplitMix64(seed * 2^32 + caller triangle id)     */
+    int32_t variant;       /* UE_VARIANT_* (0 = default)                                     */
+    int32_t graph_chunk;   /* steps per captured CUDA graph launch; 0 = default, <0 = none   */
+    int32_t reserved0;
+    double dt;             /* UE_DT_GIVEN: the time step                                     */
+    double safety;         /* UE_DT_POWER: dt = safety * 2 / rho (default 0.5)               */
+} ue_options;
+
+typedef struct ue_stats_t {
+    int64_t n_nodes, n_tris, n_edges, n_interior_edges;
+    int64_t steps_done;          /* leap-frog steps taken since the last ue_set_step          */
+    double dt, rho;
+    int32_t rho_source;          /* UE_RHO_*                                                  */
+    int32_t precision;
+    double bytes_per_step;       /* algorithmic HBM bytes of one plain step                   */
+    int64_t kernel_launches;     /* kernels the library launched so far                       */
+} ue_stats_t;
+
+/* Fill *opt with defaults (RCM, FP32, power-iteration dt, safety 0.5, 200 iterations). */
+void ue_options_default(ue_options* opt);
+
+/* Mesh ingest (host only; Fig. 2 symbols).  xy: n_nodes*2 doubles, tris: n_tris*3 int32.
+ * Orients triangles, builds edges, R/L and the sign table, drops boundary edges from the
+ * unknowns and reorders triangles (opt->reorder; opt may be NULL).  alloc/free may be NULL.
+ * Errors: UE_ERR_ARG (sizes, indices), UE_ERR_NONMANIFOLD, UE_ERR_DEGENERATE. */
+int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                 const ue_options* opt, ue_alloc_fn alloc, ue_free_fn free_fn, void* alloc_ctx,
+                 ue_mesh** out);
+
+/* Device setup: FP64 geometry on the GPU (circumcentres O_j, |e_i|, S_j, and the dual length
+ * |O_R O_L| of eq. 3 in the cotangent form), the time step (eq. 20 with rho(M) from FP64 power
+ * iteration, Section 2, or the given dt), the update coefficients dt*|e|/d (eq. 3) and dt/S
+ * (eq. 4) rounded to the field precision, and zeroed fields.  Synchronous.
+ * Errors: UE_ERR_DUAL if some interior edge has d <= 1e-12*|e|; UE_ERR_CUDA; UE_ERR_ALLOC. */
+int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream);
+
+/* dt, rho(M) and how rho was obtained (UE_RHO_*). */
+int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* rho_source);
+
+/* Plasma-like medium (eqs. 5-6): n_nodes_density[v] is n at caller node v (n = omega_p^2 in
+ * the paper's dimensionless units), nu the collision rate.  The edge density is the mean of
+ * its two end nodes.  Requires ue_geometry_build; switches the step to the plasma update.
+ * Passing NULL removes the medium. */
+int ue_set_plasma(ue_mesh* m, const double* n_nodes_density, double nu);
+
+/* Soft source: at the E update that ends at step n+1, E_i += dt * amp[k] * g(t) with
+ * t = (n + 1/2) dt and g(t) = sin(omega0 t) exp(-((t - t0)/tau)^2), for edge_ids[k] (caller
+ * numbering, interior edges only, no repeats).  n = 0 removes the source. */
+int ue_set_source(ue_mesh* m, const int32_t* edge_ids, const double* amp, int64_t n,
+                  double omega0, double t0, double tau);
+
+/* Set E^0 (n_edges values; boundary entries ignored), B^{1/2} (n_tris values) and, in plasma,
+ * j^{-1/2} (n_edges values, may be NULL = 0).  Any pointer may be NULL to leave that field. */
+int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream);
+
+/* Advance n_steps leap-frog steps, asynchronously on `stream`.  Errors of the launches are
+ * reported here; device-side conditions surface at the next synchronous call. */
+int ue_step_n(ue_mesh* m, int64_t n_steps, void* stream);
+
+/* Copy the fields back in the caller's numbering (synchronous).  E, j: n_edges values (0 on
+ * boundary edges); B: n_tris values.  Any pointer may be NULL. */
+int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream);
+
+/* Step counter used by the source time t = (n + 1/2) dt (checkpoint / resume). */
+int ue_get_step(const ue_mesh* m, int64_t* step);
+int ue_set_step(ue_mesh* m, int64_t step);
+
+/* Sizes: nodes, triangles, edges, interior edges (unknowns). */
+int ue_get_sizes(const ue_mesh* m, int64_t* n_nodes, int64_t* n_tris, int64_t* n_edges,
+                 int64_t* n_interior_edges);
+
+/* Connectivity tables as stored on the device (bit-exact checks):
+ * perm_tri[n_tris]: caller id of stored triangle j; edge_caller[n_ei]: caller id of stored
+ * interior edge k; edge_tri[2*n_ei]: (R, L) in stored triangle ids; tri_code[3*n_tris]:
+ * 2*k + (s(j,q) < 0) for the stored edge k = A(j,q), 2*n_ei for a boundary edge, q taken from
+ * the vertex triple rotated to start at its smallest caller node id. Any pointer may be NULL. */
+int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int32_t* edge_tri,
+                  int32_t* tri_code);
+
+/* FP64 geometry computed on the device, caller numbering (after ue_geometry_build):
+ * O[2*n_tris] circumcentres, S[n_tris] areas, elen[n_edges] lengths, d[n_edges] signed dual
+ * lengths (NaN on boundary edges).  Any pointer may be NULL. */
+int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
+
+/* Time the kernels of the plain step with CUDA events: n_steps steps (1..4096) launched one by
+ * one on `stream` (no graph), then synchronised.  ms[0], ms[1], ms[2] receive the mean device
+ * duration in milliseconds of the E half-step (eq. 3 / eqs. 5-6), the source and the B half-step
+ * (eq. 4) kernels; bytes[0..2] their algorithmic HBM bytes per launch.  The fields advance. */
+int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
+
+int ue_stats(const ue_mesh* m, ue_stats_t* out);
+const char* ue_last_error(void);
+void ue_mesh_free(ue_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UE_H */

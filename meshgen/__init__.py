@@ -27,4 +27,5 @@ from .configs import (  # noqa: F401
     source_line_amplitudes,
     plasma_density_nodes,
     te_mode_b,
+    cached,
 )

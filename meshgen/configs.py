@@ -109,3 +109,24 @@ def batch_meshes(n_meshes: int = 512, seed: int = 1004, n_min: int = 5_000, n_ma
                              seed=int(rng.integers(1 << 31)))
         yield dict(mesh=mesh, omega0=omega0, kind=("triangle", "ellipse", "rectangle")[kind],
                    size=size, jitter=jit)
+
+
+def cached(name: str, make, cache_dir: str | None = None) -> MeshArrays:
+    """Return make() memoised in an .npz under $UE_MESH_CACHE (default: the system temp dir).
+
+    Large graded meshes take tens of seconds to generate; tests and the benchmark that run in
+    one session share them through this cache.  ``name`` must encode every generator argument.
+    """
+    import os
+    import tempfile
+    d = cache_dir or os.environ.get("UE_MESH_CACHE") or os.path.join(tempfile.gettempdir(), "ue_meshcache")
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, name + ".npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return MeshArrays(z["xy"], z["tris"], float(z["h"]), z["boundary_node"], dict(cached=path))
+    m = make()
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, xy=m.xy, tris=m.tris, h=m.h, boundary_node=m.boundary_node)
+    os.replace(tmp, path)
+    return m

@@ -1,0 +1,185 @@
+"""Python binding of the C ABI: the same calls, numpy host arrays in and out.
+
+Argument marshalling only: every step of the method runs in libue.so.  Streams are
+cudaStream_t handles passed as integers (``torch.cuda.current_stream().cuda_stream``); device
+memory comes from PyTorch's caching allocator when ``torch_alloc=True``, else from cudaMalloc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(N.PD)
+
+
+def options(**kw) -> N.Options:
+    o = N.Options()
+    N.lib().ue_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations to torch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.dev, stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = N.ALLOC_FN(_alloc)
+        self.free = N.FREE_FN(_free)
+
+
+class Mesh:
+    """A loaded mesh (``ue_mesh``).  Methods mirror the C calls of include/ue.h."""
+
+    def __init__(self, xy, tris, reorder: int = N.UE_REORDER_RCM, torch_alloc: bool = False):
+        L = N.lib()
+        self._xy = np.ascontiguousarray(xy, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        if self._xy.ndim != 2 or self._xy.shape[1] != 2 or t.ndim != 2 or t.shape[1] != 3:
+            raise ValueError("xy must be [n,2], tris [m,3]")
+        self._allocator = _TorchAllocator() if torch_alloc else None
+        h = C.c_void_p()
+        o = options(reorder=reorder)
+        a = self._allocator.alloc if self._allocator else N.ALLOC_FN()
+        f = self._allocator.free if self._allocator else N.FREE_FN()
+        N.check(L.ue_mesh_load(_dptr(self._xy), self._xy.shape[0], t.ctypes.data_as(N.PI32),
+                               t.shape[0], C.byref(o), a, f, None, C.byref(h)), "ue_mesh_load")
+        self._h = h
+        nn, nt, ne, nei = (C.c_int64() for _ in range(4))
+        N.check(L.ue_get_sizes(h, C.byref(nn), C.byref(nt), C.byref(ne), C.byref(nei)), "ue_get_sizes")
+        self.n_nodes, self.n_tris, self.n_edges, self.n_ei = nn.value, nt.value, ne.value, nei.value
+        self.precision = N.UE_PREC_FP32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().ue_mesh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def geometry_build(self, stream=None, **opts):
+        o = options(**opts)
+        self.precision = o.precision
+        N.check(N.lib().ue_geometry_build(self._h, C.byref(o), _stream(stream)), "ue_geometry_build")
+
+    def get_dt(self):
+        dt, rho, src = C.c_double(), C.c_double(), C.c_int32()
+        N.check(N.lib().ue_get_dt(self._h, C.byref(dt), C.byref(rho), C.byref(src)), "ue_get_dt")
+        return dt.value, rho.value, src.value
+
+    def set_plasma(self, n_nodes_density, nu: float):
+        n = None if n_nodes_density is None else np.ascontiguousarray(n_nodes_density, np.float64)
+        if n is not None and n.shape != (self.n_nodes,):
+            raise ValueError("density must have one value per node")
+        N.check(N.lib().ue_set_plasma(self._h, _dptr(n), float(nu)), "ue_set_plasma")
+
+    def set_source(self, edge_ids, amp, omega0: float, t0: float, tau: float):
+        ids = np.ascontiguousarray(edge_ids, np.int32)
+        a = np.ascontiguousarray(amp, np.float64)
+        if ids.shape != a.shape:
+            raise ValueError("edge_ids and amp must have the same length")
+        N.check(N.lib().ue_set_source(self._h, ids.ctypes.data_as(N.PI32), _dptr(a), ids.size,
+                                      float(omega0), float(t0), float(tau)), "ue_set_source")
+
+    def write_fields(self, E=None, B=None, j=None, stream=None):
+        def chk(x, n):
+            if x is None:
+                return None
+            x = np.ascontiguousarray(x, np.float64)
+            if x.shape != (n,):
+                raise ValueError(f"expected {n} values")
+            return x
+        E, B, j = chk(E, self.n_edges), chk(B, self.n_tris), chk(j, self.n_edges)
+        N.check(N.lib().ue_write_fields(self._h, _dptr(E), _dptr(B), _dptr(j), _stream(stream)),
+                "ue_write_fields")
+
+    def step_n(self, n: int, stream=None):
+        N.check(N.lib().ue_step_n(self._h, int(n), _stream(stream)), "ue_step_n")
+
+    def read_fields(self, E=True, B=True, j=False, stream=None, out=None):
+        """Return (E, B, j) as float64 arrays in caller numbering (None where not asked)."""
+        o = out or {}
+        Ea = o.get("E", np.empty(self.n_edges)) if E else None
+        Ba = o.get("B", np.empty(self.n_tris)) if B else None
+        ja = o.get("j", np.empty(self.n_edges)) if j else None
+        N.check(N.lib().ue_read_fields(self._h, _dptr(Ea), _dptr(Ba), _dptr(ja), _stream(stream)),
+                "ue_read_fields")
+        return Ea, Ba, ja
+
+    def get_step(self) -> int:
+        v = C.c_int64()
+        N.check(N.lib().ue_get_step(self._h, C.byref(v)), "ue_get_step")
+        return v.value
+
+    def set_step(self, step: int):
+        N.check(N.lib().ue_set_step(self._h, int(step)), "ue_set_step")
+
+    def tables(self):
+        perm = np.empty(self.n_tris, np.int64)
+        ec = np.empty(self.n_ei, np.int64)
+        et = np.empty((self.n_ei, 2), np.int32)
+        tc = np.empty((self.n_tris, 3), np.int32)
+        N.check(N.lib().ue_get_tables(self._h, perm.ctypes.data_as(N.PI64), ec.ctypes.data_as(N.PI64),
+                                      et.ctypes.data_as(N.PI32), tc.ctypes.data_as(N.PI32)),
+                "ue_get_tables")
+        return dict(perm_tri=perm, edge_caller=ec, edge_tri=et, tri_code=tc, n_ei=self.n_ei)
+
+    def geometry(self):
+        O = np.empty((self.n_tris, 2))
+        S = np.empty(self.n_tris)
+        le = np.empty(self.n_edges)
+        d = np.empty(self.n_edges)
+        N.check(N.lib().ue_get_geometry(self._h, _dptr(O), _dptr(S), _dptr(le), _dptr(d)),
+                "ue_get_geometry")
+        return dict(O=O, S=S, elen=le, d=d)
+
+    def profile_steps(self, n: int, stream=None):
+        """Mean per-kernel device time (ms) and algorithmic bytes per launch, n plain steps."""
+        ms = np.zeros(3)
+        by = np.zeros(3)
+        N.check(N.lib().ue_profile_steps(self._h, int(n), _stream(stream), _dptr(ms), _dptr(by)),
+                "ue_profile_steps")
+        return ms, by
+
+    def stats(self) -> dict:
+        s = N.Stats()
+        N.check(N.lib().ue_stats(self._h, C.byref(s)), "ue_stats")
+        return {k: getattr(s, k) for k, _ in N.Stats._fields_}

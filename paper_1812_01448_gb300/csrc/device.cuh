@@ -1,0 +1,78 @@
+// Device-side definitions shared by the kernels (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/ue.h"
+
+namespace ue {
+
+// Arithmetic with explicit rounding: every variant of the step evaluates the same sequence of
+// correctly rounded operations, so their results are bit-identical (no contraction choices).
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+// Everything the step kernels need, in the stored numbering.
+struct DevMesh {
+    int precision = 0;            // UE_PREC_*
+    int64_t n_t = 0, n_ei = 0, n_nodes = 0;
+    const int2* rl = nullptr;     // [n_ei] (R, L)
+    int4* tri = nullptr;          // [n_t] {code0, code1, code2, bits of dt/S (fp32) | 0}
+    void* cU = nullptr;           // [n_ei] dt*|e|/d, field precision
+    void* cB = nullptr;           // [n_t] dt/S (fp64 check build only)
+    void* U = nullptr;            // [n_ei + 1] circulation |e| E; slot n_ei stays 0
+    void* B = nullptr;            // [n_t]
+    bool plasma = false;
+    void* J = nullptr;            // [n_ei + 1] circulation |e| j
+    void* pb = nullptr;           // [n_ei] dt*nbar/(1 + nu dt/2)
+    double pa = 1.0;              // (1 - nu dt/2)/(1 + nu dt/2)
+    int64_t n_src = 0;
+    int32_t* src_k = nullptr;     // [n_src] stored edge ids
+    void* src_c = nullptr;        // [n_src] dt*|e|*amp
+    double w0 = 0, t0 = 0, tau = 1;
+    long long* step = nullptr;    // device step counter (source time)
+    double dt = 0;
+};
+
+// Launchers (kernels_step.cu).
+cudaError_t launch_step_plain(const DevMesh& m, cudaStream_t s);
+// One kernel of the plain step: 0 = E half-step, 1 = source, 2 = B half-step.
+cudaError_t launch_step_part(const DevMesh& m, int part, cudaStream_t s);
+
+// Geometry, coefficients, power iteration and field transfer (kernels_geom.cu).
+cudaError_t launch_geom_tri(const double* xy, const int32_t* tri_nodes, double* O, double* S,
+                            int64_t n_t, cudaStream_t s);
+cudaError_t launch_geom_edge(const double* xy, const int32_t* edge_nodes, const int32_t* edge_opp,
+                             double* elen, double* d, int64_t n_ei, cudaStream_t s);
+cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, const double* S,
+                         const int32_t* tri_code, double dt, cudaStream_t s);
+// FP64 power iteration on K = -L_E L_B in the S metric; returns rho in *rho (synchronous).
+cudaError_t power_iteration(const int2* rl, const int4* tri, const double* elen, const double* d,
+                            const double* S, const int64_t* perm_tri, int64_t n_t, int64_t n_ei,
+                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s);
+size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei);
+cudaError_t launch_fields_in(const DevMesh& m, const double* E_caller, const double* B_caller,
+                             const double* J_caller, const int64_t* edge_caller,
+                             const int64_t* perm_tri, const double* elen, cudaStream_t s);
+cudaError_t launch_fields_out(const DevMesh& m, double* E_caller, double* B_caller,
+                              double* J_caller, const int64_t* edge_caller,
+                              const int64_t* perm_tri, const double* elen, cudaStream_t s);
+cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const int32_t* edge_nodes,
+                                double nu, double dt, cudaStream_t s);
+cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen,
+                                double dt, cudaStream_t s);
+cudaError_t launch_scatter_geometry(const double* O, const double* S, const double* elen,
+                                    const double* d, const int64_t* perm_tri,
+                                    const int64_t* edge_caller, int64_t n_t, int64_t n_ei,
+                                    int64_t n_e, double* O_c, double* S_c, double* elen_c,
+                                    double* d_c, cudaStream_t s);
+
+}  // namespace ue

@@ -1,0 +1,407 @@
+// FP64 setup kernels: geometry of eqs. 3-4 and 7, update coefficients, the power iteration of
+// Section 2 ("complex time" method) for rho(M), and field transfer between the caller's
+// numbering and the stored one.  One thread per triangle or edge; these run once per mesh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "device.cuh"
+
+namespace ue {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// Circumcentre O_j (where B_j lives, Fig. 2) and area S_j of each stored triangle.
+__global__ void k_geom_tri(const double* __restrict__ xy, const int32_t* __restrict__ tn,
+                           double* __restrict__ O, double* __restrict__ S, int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    const int a = tn[3 * j], b = tn[3 * j + 1], c = tn[3 * j + 2];
+    const double ax = xy[2 * a], ay = xy[2 * a + 1];
+    const double bx = xy[2 * b] - ax, by = xy[2 * b + 1] - ay;
+    const double cx = xy[2 * c] - ax, cy = xy[2 * c + 1] - ay;
+    const double det = bx * cy - by * cx;
+    const double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    O[2 * j] = ax + (cy * b2 - by * c2) / (2.0 * det);
+    O[2 * j + 1] = ay + (bx * c2 - cx * b2) / (2.0 * det);
+    S[j] = 0.5 * det;
+}
+
+// cot of the angle at o in triangle (a, b, o).
+__device__ __forceinline__ double cot_at(double ax, double ay, double bx, double by, double ox,
+                                         double oy) {
+    const double ux = ax - ox, uy = ay - oy, vx = bx - ox, vy = by - oy;
+    return (ux * vx + uy * vy) / fabs(ux * vy - uy * vx);
+}
+
+// |e_i| and the dual length |O_R O_L| of eq. 3 in the cotangent form
+// d_i = |e_i|/2 (cot alpha_R + cot alpha_L), alpha = angle opposite e_i (stable for
+// near-degenerate triangles, where subtracting two circumcentres would cancel).
+__global__ void k_geom_edge(const double* __restrict__ xy, const int32_t* __restrict__ en,
+                            const int32_t* __restrict__ eo, double* __restrict__ elen,
+                            double* __restrict__ d, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    const int a = en[2 * k], b = en[2 * k + 1], r = eo[2 * k], l = eo[2 * k + 1];
+    const double ax = xy[2 * a], ay = xy[2 * a + 1], bx = xy[2 * b], by = xy[2 * b + 1];
+    const double len = hypot(bx - ax, by - ay);
+    const double cr = cot_at(ax, ay, bx, by, xy[2 * r], xy[2 * r + 1]);
+    const double cl = cot_at(ax, ay, bx, by, xy[2 * l], xy[2 * l + 1]);
+    elen[k] = len;
+    d[k] = 0.5 * len * (cr + cl);
+}
+
+template <typename T>
+__global__ void k_coeff_edge(const double* __restrict__ elen, const double* __restrict__ d,
+                             T* __restrict__ cU, double dt, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    cU[k] = (T)(dt * elen[k] / d[k]);
+}
+
+// Triangle record {code0, code1, code2, bits of (float)(dt/S)}; FP64 build: separate dt/S.
+__global__ void k_coeff_tri(const int32_t* __restrict__ code, const double* __restrict__ S,
+                            int4* __restrict__ tri, double* __restrict__ cB64, double dt,
+                            int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    const double c = dt / S[j];
+    int4 r;
+    r.x = code[3 * j];
+    r.y = code[3 * j + 1];
+    r.z = code[3 * j + 2];
+    r.w = cB64 ? 0 : __float_as_int((float)c);
+    tri[j] = r;
+    if (cB64) cB64[j] = c;
+}
+
+// ---------------------------------------------------------------------------------------
+// power iteration, FP64.  (K v)_j = (1/S_j) sum_q s(j,q) |e_q| (v_R - v_L)/d_q.
+// ---------------------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea, Flood 2014), published constants.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_pi_init(double* __restrict__ v, const int64_t* __restrict__ perm, uint32_t seed,
+                          int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    const uint64_t z = splitmix64(((uint64_t)seed << 32) + (uint64_t)perm[j]);
+    v[j] = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+}
+
+__global__ void k_pi_edge(const int2* __restrict__ rl, const double* __restrict__ elen,
+                          const double* __restrict__ d, const double* __restrict__ v,
+                          double* __restrict__ g, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    const int2 e = rl[k];
+    g[k] = elen[k] * (v[e.x] - v[e.y]) / d[k];
+}
+
+// w = K v and block partial sums of S v w and S w w (fixed-order tree: deterministic).
+__global__ void k_pi_tri(const int4* __restrict__ tri, const double* __restrict__ S,
+                         const double* __restrict__ g, const double* __restrict__ v,
+                         double* __restrict__ w, double* __restrict__ part, int64_t n_t) {
+    __shared__ double s_vw[kThreads], s_ww[kThreads];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double vw = 0.0, ww = 0.0;
+    if (j < n_t) {
+        const int4 t = tri[j];
+        double a = g[t.x >> 1], b = g[t.y >> 1], c = g[t.z >> 1];
+        if (t.x & 1) a = -a;
+        if (t.y & 1) b = -b;
+        if (t.z & 1) c = -c;
+        const double x = (a + b + c) / S[j];
+        w[j] = x;
+        vw = S[j] * v[j] * x;
+        ww = S[j] * x * x;
+    }
+    s_vw[threadIdx.x] = vw;
+    s_ww[threadIdx.x] = ww;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_vw[threadIdx.x] += s_vw[threadIdx.x + o];
+            s_ww[threadIdx.x] += s_ww[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s_vw[0];
+        part[2 * blockIdx.x + 1] = s_ww[0];
+    }
+}
+
+// Sum the block partials in a fixed order (one block), then scal[0] = sum vw, scal[1] = sum ww.
+__global__ void k_pi_reduce(const double* __restrict__ part, int64_t nb, double* __restrict__ scal) {
+    __shared__ double a[kThreads], b[kThreads];
+    double x = 0.0, y = 0.0;
+    for (int64_t i = threadIdx.x; i < nb; i += kThreads) {
+        x += part[2 * i];
+        y += part[2 * i + 1];
+    }
+    a[threadIdx.x] = x;
+    b[threadIdx.x] = y;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            a[threadIdx.x] += a[threadIdx.x + o];
+            b[threadIdx.x] += b[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        scal[0] = a[0];
+        scal[1] = b[0];
+    }
+}
+
+// v = w / sqrt(scal[1]) (S-normalisation).  Also the initial normalisation (w = v0).
+__global__ void k_pi_scale(const double* __restrict__ w, const double* __restrict__ scal,
+                           double* __restrict__ v, int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    v[j] = w[j] / sqrt(scal[1]);
+}
+
+__global__ void k_pi_norm_parts(const double* __restrict__ S, const double* __restrict__ v,
+                                double* __restrict__ part, int64_t n_t) {
+    __shared__ double s_ww[kThreads];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    s_ww[threadIdx.x] = j < n_t ? S[j] * v[j] * v[j] : 0.0;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_ww[threadIdx.x] += s_ww[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = 0.0;
+        part[2 * blockIdx.x + 1] = s_ww[0];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// fields: caller numbering (E per edge, B per triangle, FP64) <-> stored circulation form
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fields_in_edges(const double* __restrict__ Ec, const int64_t* __restrict__ ec,
+                                  const double* __restrict__ elen, T* __restrict__ U, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_ei) return;
+    U[k] = (k == n_ei) ? (T)0 : (T)(elen[k] * Ec[ec[k]]);
+}
+
+template <typename T>
+__global__ void k_fields_in_tris(const double* __restrict__ Bc, const int64_t* __restrict__ perm,
+                                 T* __restrict__ B, int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    B[j] = (T)Bc[perm[j]];
+}
+
+template <typename T>
+__global__ void k_fields_out_edges(const T* __restrict__ U, const int64_t* __restrict__ ec,
+                                   const double* __restrict__ elen, double* __restrict__ Ec,
+                                   int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    Ec[ec[k]] = (double)U[k] / elen[k];
+}
+
+template <typename T>
+__global__ void k_fields_out_tris(const T* __restrict__ B, const int64_t* __restrict__ perm,
+                                  double* __restrict__ Bc, int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    Bc[perm[j]] = (double)B[j];
+}
+
+template <typename T>
+__global__ void k_plasma_coeff(const double* __restrict__ nn, const int32_t* __restrict__ en,
+                               T* __restrict__ pb, double c, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    pb[k] = (T)(c * 0.5 * (nn[en[2 * k]] + nn[en[2 * k + 1]]));
+}
+
+template <typename T>
+__global__ void k_source_coeff(const int32_t* __restrict__ sk, const double* __restrict__ amp,
+                               const double* __restrict__ elen, T* __restrict__ sc, double dt,
+                               int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sc[i] = (T)(dt * elen[sk[i]] * amp[i]);
+}
+
+__global__ void k_scatter_geom_tri(const double* __restrict__ O, const double* __restrict__ S,
+                                   const int64_t* __restrict__ perm, double* __restrict__ Oc,
+                                   double* __restrict__ Sc, int64_t n_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    const int64_t c = perm[j];
+    if (Oc) {
+        Oc[2 * c] = O[2 * j];
+        Oc[2 * c + 1] = O[2 * j + 1];
+    }
+    if (Sc) Sc[c] = S[j];
+}
+
+__global__ void k_fill_nan(double* __restrict__ a, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+__global__ void k_scatter_geom_edge(const double* __restrict__ elen, const double* __restrict__ d,
+                                    const int64_t* __restrict__ ec, double* __restrict__ lc,
+                                    double* __restrict__ dc, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ei) return;
+    if (lc) lc[ec[k]] = elen[k];
+    if (dc) dc[ec[k]] = d[k];
+}
+
+}  // namespace
+
+cudaError_t launch_geom_tri(const double* xy, const int32_t* tri_nodes, double* O, double* S,
+                            int64_t n_t, cudaStream_t s) {
+    k_geom_tri<<<blocks_for(n_t), kThreads, 0, s>>>(xy, tri_nodes, O, S, n_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom_edge(const double* xy, const int32_t* edge_nodes, const int32_t* edge_opp,
+                             double* elen, double* d, int64_t n_ei, cudaStream_t s) {
+    if (n_ei == 0) return cudaSuccess;
+    k_geom_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(xy, edge_nodes, edge_opp, elen, d, n_ei);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, const double* S,
+                         const int32_t* tri_code, double dt, cudaStream_t s) {
+    if (m.n_ei > 0) {
+        if (m.precision == UE_PREC_FP64)
+            k_coeff_edge<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>(elen, d, (double*)m.cU, dt, m.n_ei);
+        else
+            k_coeff_edge<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>(elen, d, (float*)m.cU, dt, m.n_ei);
+    }
+    k_coeff_tri<<<blocks_for(m.n_t), kThreads, 0, s>>>(
+        tri_code, S, m.tri, m.precision == UE_PREC_FP64 ? (double*)m.cB : nullptr, dt, m.n_t);
+    return cudaGetLastError();
+}
+
+size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei) {
+    const int64_t nb = (n_t + kThreads - 1) / kThreads;
+    return (size_t)(2 * n_t + (n_ei + 1) + 2 * nb + 2);
+}
+
+cudaError_t power_iteration(const int2* rl, const int4* tri, const double* elen, const double* d,
+                            const double* S, const int64_t* perm_tri, int64_t n_t, int64_t n_ei,
+                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s) {
+    const int64_t nb = (n_t + kThreads - 1) / kThreads;
+    double* v = work;
+    double* w = v + n_t;
+    double* g = w + n_t;
+    double* part = g + (n_ei + 1);
+    double* scal = part + 2 * nb;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g, 0, sizeof(double) * (n_ei + 1), s)) != cudaSuccess) return e;
+    k_pi_init<<<blocks_for(n_t), kThreads, 0, s>>>(w, perm_tri, seed, n_t);
+    k_pi_norm_parts<<<(unsigned)nb, kThreads, 0, s>>>(S, w, part, n_t);
+    k_pi_reduce<<<1, kThreads, 0, s>>>(part, nb, scal);
+    k_pi_scale<<<blocks_for(n_t), kThreads, 0, s>>>(w, scal, v, n_t);
+    for (int it = 0; it < iters; ++it) {
+        if (n_ei > 0) k_pi_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(rl, elen, d, v, g, n_ei);
+        k_pi_tri<<<(unsigned)nb, kThreads, 0, s>>>(tri, S, g, v, w, part, n_t);
+        k_pi_reduce<<<1, kThreads, 0, s>>>(part, nb, scal);
+        if (it + 1 < iters) k_pi_scale<<<blocks_for(n_t), kThreads, 0, s>>>(w, scal, v, n_t);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    double h[2];
+    if ((e = cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *rho = sqrt(h[0] > 0 ? h[0] : 0.0);
+    return cudaSuccess;
+}
+
+cudaError_t launch_fields_in(const DevMesh& m, const double* Ec, const double* Bc, const double* Jc,
+                             const int64_t* edge_caller, const int64_t* perm_tri,
+                             const double* elen, cudaStream_t s) {
+    const bool f64 = m.precision == UE_PREC_FP64;
+    if (Ec) {
+        if (f64) k_fields_in_edges<double><<<blocks_for(m.n_ei + 1), kThreads, 0, s>>>(Ec, edge_caller, elen, (double*)m.U, m.n_ei);
+        else k_fields_in_edges<float><<<blocks_for(m.n_ei + 1), kThreads, 0, s>>>(Ec, edge_caller, elen, (float*)m.U, m.n_ei);
+    }
+    if (Jc && m.J) {
+        if (f64) k_fields_in_edges<double><<<blocks_for(m.n_ei + 1), kThreads, 0, s>>>(Jc, edge_caller, elen, (double*)m.J, m.n_ei);
+        else k_fields_in_edges<float><<<blocks_for(m.n_ei + 1), kThreads, 0, s>>>(Jc, edge_caller, elen, (float*)m.J, m.n_ei);
+    }
+    if (Bc) {
+        if (f64) k_fields_in_tris<double><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, perm_tri, (double*)m.B, m.n_t);
+        else k_fields_in_tris<float><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, perm_tri, (float*)m.B, m.n_t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_out(const DevMesh& m, double* Ec, double* Bc, double* Jc,
+                              const int64_t* edge_caller, const int64_t* perm_tri,
+                              const double* elen, cudaStream_t s) {
+    const bool f64 = m.precision == UE_PREC_FP64;
+    if (Ec && m.n_ei > 0) {
+        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.U, edge_caller, elen, Ec, m.n_ei);
+        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.U, edge_caller, elen, Ec, m.n_ei);
+    }
+    if (Jc && m.J && m.n_ei > 0) {
+        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.J, edge_caller, elen, Jc, m.n_ei);
+        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.J, edge_caller, elen, Jc, m.n_ei);
+    }
+    if (Bc) {
+        if (f64) k_fields_out_tris<double><<<blocks_for(m.n_t), kThreads, 0, s>>>((const double*)m.B, perm_tri, Bc, m.n_t);
+        else k_fields_out_tris<float><<<blocks_for(m.n_t), kThreads, 0, s>>>((const float*)m.B, perm_tri, Bc, m.n_t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const int32_t* edge_nodes,
+                                double nu, double dt, cudaStream_t s) {
+    if (m.n_ei == 0) return cudaSuccess;
+    const double c = dt / (1.0 + 0.5 * nu * dt);
+    if (m.precision == UE_PREC_FP64)
+        k_plasma_coeff<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>(n_nodes, edge_nodes, (double*)m.pb, c, m.n_ei);
+    else
+        k_plasma_coeff<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>(n_nodes, edge_nodes, (float*)m.pb, c, m.n_ei);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen, double dt,
+                                cudaStream_t s) {
+    if (m.n_src == 0) return cudaSuccess;
+    if (m.precision == UE_PREC_FP64)
+        k_source_coeff<double><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, amp, elen, (double*)m.src_c, dt, m.n_src);
+    else
+        k_source_coeff<float><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, amp, elen, (float*)m.src_c, dt, m.n_src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_geometry(const double* O, const double* S, const double* elen,
+                                    const double* d, const int64_t* perm_tri,
+                                    const int64_t* edge_caller, int64_t n_t, int64_t n_ei,
+                                    int64_t n_e, double* O_c, double* S_c, double* elen_c,
+                                    double* d_c, cudaStream_t s) {
+    if (O_c || S_c) k_scatter_geom_tri<<<blocks_for(n_t), kThreads, 0, s>>>(O, S, perm_tri, O_c, S_c, n_t);
+    if (elen_c) k_fill_nan<<<blocks_for(n_e), kThreads, 0, s>>>(elen_c, n_e);
+    if (d_c) k_fill_nan<<<blocks_for(n_e), kThreads, 0, s>>>(d_c, n_e);
+    if ((elen_c || d_c) && n_ei > 0)
+        k_scatter_geom_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(elen, d, edge_caller, elen_c, d_c, n_ei);
+    return cudaGetLastError();
+}
+
+}  // namespace ue

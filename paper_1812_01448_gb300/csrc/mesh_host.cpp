@@ -1,0 +1,253 @@
+// Host mesh ingest: the Fig. 2 symbols (edges e_i, R(i), L(i), A(j,q) and the sign factor of
+// eq. 4), PEC boundary edges removed from the unknowns (eq. 10), and the locality reordering
+// of the triangles (reverse Cuthill-McKee on the dual graph; the "Divide and conqueror"
+// section motivates keeping neighbours together).  Compiled with -ffp-contract=off so that
+// the FP64 orientation determinant rounds the same way on every host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <utility>
+
+#include "ue_internal.h"
+
+namespace ue {
+
+namespace {
+
+// (p1 - p0) x (p2 - p0), twice the signed area.
+inline double orient2d(const double* a, const double* b, const double* c) {
+    const double bx = b[0] - a[0], by = b[1] - a[1];
+    const double cx = c[0] - a[0], cy = c[1] - a[1];
+    return bx * cy - by * cx;
+}
+
+struct Canon {
+    std::vector<int64_t> tri;       // 3*n_t CCW caller node ids
+    std::vector<int64_t> tri_edge;  // 3*n_t caller edge ids, A(j,q) = (v_q, v_{q+1})
+    std::vector<int8_t> tri_neg;    // 3*n_t: 1 where s(j,q) = -1
+    std::vector<int64_t> edges;     // 2*n_e
+    std::vector<int64_t> R, L;      // n_e
+};
+
+int canonicalize(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, Canon& c,
+                 std::string& err) {
+    c.tri.resize(3 * nt);
+    for (int64_t j = 0; j < nt; ++j) {
+        int64_t v0 = tris[3 * j], v1 = tris[3 * j + 1], v2 = tris[3 * j + 2];
+        if (v0 < 0 || v1 < 0 || v2 < 0 || v0 >= nn || v1 >= nn || v2 >= nn) {
+            err = "triangle " + std::to_string(j) + " has a vertex index out of range";
+            return UE_ERR_ARG;
+        }
+        if (v0 == v1 || v1 == v2 || v0 == v2) {
+            err = "triangle " + std::to_string(j) + " repeats a vertex";
+            return UE_ERR_DEGENERATE;
+        }
+        const double det = orient2d(xy + 2 * v0, xy + 2 * v1, xy + 2 * v2);
+        if (det == 0.0 || !std::isfinite(det)) {
+            err = "triangle " + std::to_string(j) + " is degenerate (zero orientation determinant)";
+            return UE_ERR_DEGENERATE;
+        }
+        if (det < 0) std::swap(v1, v2);
+        c.tri[3 * j] = v0;
+        c.tri[3 * j + 1] = v1;
+        c.tri[3 * j + 2] = v2;
+    }
+    // half-edges sorted by (low, high) key
+    const int64_t nh = 3 * nt;
+    std::vector<std::pair<int64_t, int64_t>> he(nh);
+    for (int64_t h = 0; h < nh; ++h) {
+        const int64_t j = h / 3, q = h % 3;
+        const int64_t a = c.tri[3 * j + q], b = c.tri[3 * j + (q + 1) % 3];
+        he[h] = {std::min(a, b) * nn + std::max(a, b), h};
+    }
+    std::sort(he.begin(), he.end());
+    c.tri_edge.assign(nh, -1);
+    c.tri_neg.assign(nh, 0);
+    c.edges.clear();
+    c.edges.reserve(nh);
+    int64_t ne = 0;
+    for (int64_t s = 0; s < nh;) {
+        int64_t e = s;
+        while (e < nh && he[e].first == he[s].first) ++e;
+        if (e - s > 2) {
+            err = "edge shared by more than two triangles";
+            return UE_ERR_NONMANIFOLD;
+        }
+        const int64_t key = he[s].first;
+        c.edges.push_back(key / nn);
+        c.edges.push_back(key % nn);
+        for (int64_t t = s; t < e; ++t) c.tri_edge[he[t].second] = ne;
+        ++ne;
+        s = e;
+    }
+    c.R.assign(ne, -1);
+    c.L.assign(ne, -1);
+    for (int64_t h = 0; h < nh; ++h) {
+        const int64_t j = h / 3, q = h % 3;
+        const int64_t a = c.tri[3 * j + q], b = c.tri[3 * j + (q + 1) % 3];
+        const int64_t e = c.tri_edge[h];
+        if (a < b) {
+            if (c.R[e] >= 0) {
+                err = "edge walked twice in the same direction (folded or overlapping triangles)";
+                return UE_ERR_NONMANIFOLD;
+            }
+            c.R[e] = j;
+        } else {
+            c.tri_neg[h] = 1;
+            if (c.L[e] >= 0) {
+                err = "edge walked twice in the same direction (folded or overlapping triangles)";
+                return UE_ERR_NONMANIFOLD;
+            }
+            c.L[e] = j;
+        }
+    }
+    return UE_OK;
+}
+
+// Reverse Cuthill-McKee on the dual graph with the tie-breaks: components by smallest caller
+// id, start = min (degree, id), neighbours appended in (degree, id) order, reversed at the end.
+std::vector<int64_t> rcm(const Canon& c, int64_t nt) {
+    std::vector<int64_t> ptr(nt + 1, 0);
+    const int64_t ne = (int64_t)c.R.size();
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            ++ptr[c.R[e] + 1];
+            ++ptr[c.L[e] + 1];
+        }
+    for (int64_t j = 0; j < nt; ++j) ptr[j + 1] += ptr[j];
+    std::vector<int64_t> adj(ptr[nt]);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            adj[fill[c.R[e]]++] = c.L[e];
+            adj[fill[c.L[e]]++] = c.R[e];
+        }
+    auto deg = [&](int64_t v) { return ptr[v + 1] - ptr[v]; };
+    auto less = [&](int64_t a, int64_t b) {
+        const int64_t da = deg(a), db = deg(b);
+        return da != db ? da < db : a < b;
+    };
+    std::vector<char> seen(nt, 0);
+    std::vector<int64_t> order;
+    order.reserve(nt);
+    std::vector<int64_t> comp;
+    std::vector<int64_t> nb;
+    for (int64_t root = 0; root < nt; ++root) {
+        if (seen[root]) continue;
+        comp.clear();
+        comp.push_back(root);
+        seen[root] = 1;
+        for (size_t k = 0; k < comp.size(); ++k)
+            for (int64_t p = ptr[comp[k]]; p < ptr[comp[k] + 1]; ++p)
+                if (!seen[adj[p]]) {
+                    seen[adj[p]] = 1;
+                    comp.push_back(adj[p]);
+                }
+        int64_t start = comp[0];
+        for (int64_t v : comp) {
+            seen[v] = 0;
+            if (less(v, start)) start = v;
+        }
+        size_t head = order.size();
+        order.push_back(start);
+        seen[start] = 1;
+        while (head < order.size()) {
+            const int64_t v = order[head++];
+            nb.clear();
+            for (int64_t p = ptr[v]; p < ptr[v + 1]; ++p)
+                if (!seen[adj[p]]) nb.push_back(adj[p]);
+            std::sort(nb.begin(), nb.end(), less);
+            for (int64_t w : nb) {
+                seen[w] = 1;
+                order.push_back(w);
+            }
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    return order;
+}
+
+}  // namespace
+
+int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                    int reorder, HostMesh& hm, std::string& err) {
+    if (!xy || !tris || n_nodes < 3 || n_tris < 1 || n_nodes > INT32_MAX || n_tris > (INT32_MAX / 4)) {
+        err = "bad mesh arguments (null pointer or size out of range)";
+        return UE_ERR_ARG;
+    }
+    for (int64_t i = 0; i < 2 * n_nodes; ++i)
+        if (!std::isfinite(xy[i])) {
+            err = "non-finite node coordinate";
+            return UE_ERR_ARG;
+        }
+    Canon c;
+    int rc = canonicalize(xy, n_nodes, tris, n_tris, c, err);
+    if (rc != UE_OK) return rc;
+    const int64_t ne = (int64_t)c.R.size();
+    hm.n_nodes = n_nodes;
+    hm.n_tris = n_tris;
+    hm.n_edges = ne;
+    hm.xy.assign(xy, xy + 2 * n_nodes);
+    hm.edges = c.edges;
+    // triangle order
+    if (reorder == UE_REORDER_RCM) {
+        hm.perm_tri = rcm(c, n_tris);
+    } else {
+        hm.perm_tri.resize(n_tris);
+        std::iota(hm.perm_tri.begin(), hm.perm_tri.end(), 0);
+    }
+    std::vector<int64_t> new_of(n_tris);
+    for (int64_t j = 0; j < n_tris; ++j) new_of[hm.perm_tri[j]] = j;
+    // interior edges numbered by (min, max) stored triangle id
+    std::vector<std::pair<std::pair<int64_t, int64_t>, int64_t>> ie;
+    ie.reserve(ne);
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            const int64_t r = new_of[c.R[e]], l = new_of[c.L[e]];
+            ie.push_back({{std::min(r, l), std::max(r, l)}, e});
+        }
+    std::sort(ie.begin(), ie.end());
+    const int64_t n_ei = (int64_t)ie.size();
+    hm.n_ei = n_ei;
+    hm.edge_caller.resize(n_ei);
+    hm.k_of_edge.assign(ne, -1);
+    hm.edge_tri.resize(2 * n_ei);
+    hm.edge_nodes.resize(2 * n_ei);
+    for (int64_t k = 0; k < n_ei; ++k) {
+        const int64_t e = ie[k].second;
+        hm.edge_caller[k] = e;
+        hm.k_of_edge[e] = k;
+        hm.edge_tri[2 * k] = (int32_t)new_of[c.R[e]];
+        hm.edge_tri[2 * k + 1] = (int32_t)new_of[c.L[e]];
+        hm.edge_nodes[2 * k] = (int32_t)c.edges[2 * e];
+        hm.edge_nodes[2 * k + 1] = (int32_t)c.edges[2 * e + 1];
+    }
+    // per stored triangle: vertices rotated to start at the smallest caller node id
+    hm.tri_nodes.resize(3 * n_tris);
+    hm.tri_code.resize(3 * n_tris);
+    hm.edge_opp.assign(2 * n_ei, -1);
+    for (int64_t j = 0; j < n_tris; ++j) {
+        const int64_t cj = hm.perm_tri[j];
+        const int64_t* v = &c.tri[3 * cj];
+        int rot = 0;
+        if (v[1] < v[rot]) rot = 1;
+        if (v[2] < v[rot]) rot = 2;
+        for (int q = 0; q < 3; ++q) {
+            const int src = (rot + q) % 3;
+            hm.tri_nodes[3 * j + q] = (int32_t)v[src];
+            const int64_t e = c.tri_edge[3 * cj + src];
+            const int64_t k = hm.k_of_edge[e];
+            if (k < 0) {
+                hm.tri_code[3 * j + q] = (int32_t)(2 * n_ei);
+            } else {
+                const int neg = c.tri_neg[3 * cj + src];
+                hm.tri_code[3 * j + q] = (int32_t)(2 * k + neg);
+                hm.edge_opp[2 * k + neg] = (int32_t)v[(src + 2) % 3];
+            }
+        }
+    }
+    return UE_OK;
+}
+
+}  // namespace ue

@@ -1,0 +1,572 @@
+// C ABI of the library (include/ue.h): mesh ingest, device setup, fields, time stepping.
+// Host logic only; every arithmetic step of the method runs in the kernels of
+// kernels_geom.cu and kernels_step.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "ue_internal.h"
+
+using ue::DevMesh;
+using ue::HostMesh;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+}  // namespace
+
+struct ue_mesh {
+    HostMesh hm;
+    ue_alloc_fn alloc = nullptr;
+    ue_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<void*> allocs;
+
+    bool built = false;
+    int precision = UE_PREC_FP32;
+    int variant = UE_VARIANT_PLAIN;
+    int graph_chunk = 32;
+    double dt = 0, rho = 0;
+    int rho_source = UE_RHO_GIVEN;
+    int64_t steps_done = 0;
+    int64_t launches = 0;
+
+    // device tables and geometry (stored numbering)
+    double* d_xy = nullptr;
+    int32_t* d_tri_nodes = nullptr;
+    int32_t* d_edge_nodes = nullptr;
+    int32_t* d_edge_opp = nullptr;
+    int32_t* d_tri_code = nullptr;
+    int2* d_rl = nullptr;
+    int64_t* d_perm = nullptr;
+    int64_t* d_ecaller = nullptr;
+    double *d_O = nullptr, *d_S = nullptr, *d_elen = nullptr, *d_d = nullptr;
+    // transfer buffers in caller numbering
+    double *d_Ec = nullptr, *d_Bc = nullptr, *d_Jc = nullptr;
+    DevMesh dm;
+
+    // plasma and source, kept on the host so that a rebuild can re-bake them
+    std::vector<double> plasma_n;
+    double plasma_nu = 0;
+    std::vector<int32_t> src_k;
+    std::vector<double> src_amp;
+
+    // captured step graph
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_version = -1;
+    int64_t version = 0;
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+void* dev_alloc(ue_mesh* m, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (m->alloc) {
+        p = m->alloc(bytes, (void*)s, m->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) m->allocs.push_back(p);
+    return p;
+}
+
+void dev_free_all(ue_mesh* m, cudaStream_t s) {
+    for (void* p : m->allocs) {
+        if (m->free_fn) m->free_fn(p, (void*)s, m->alloc_ctx);
+        else cudaFree(p);
+    }
+    m->allocs.clear();
+}
+
+template <typename P>
+bool alloc_into(ue_mesh* m, P*& out, size_t count, size_t elem, cudaStream_t s) {
+    out = (P*)dev_alloc(m, count * elem, s);
+    return out != nullptr;
+}
+
+#define UE_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(UE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_graph(ue_mesh* m) {
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+    m->graph_version = -1;
+}
+
+int ensure_graph(ue_mesh* m) {
+    if (m->gexec && m->graph_version == m->version) return UE_OK;
+    drop_graph(m);
+    if (!m->capture_stream)
+        UE_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    UE_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < m->graph_chunk && le == cudaSuccess; ++i)
+        le = ue::launch_step_plain(m->dm, m->capture_stream);
+    cudaError_t ce = cudaStreamEndCapture(m->capture_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(UE_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(le));
+    }
+    if (ce != cudaSuccess) return fail(UE_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&m->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        m->gexec = nullptr;
+        return fail(UE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    m->graph_version = m->version;
+    return UE_OK;
+}
+
+int kernels_per_step(const ue_mesh* m) { return 2 + (m->dm.n_src > 0 ? 1 : 0); }
+
+int bake_plasma(ue_mesh* m, cudaStream_t s) {
+    DevMesh& dm = m->dm;
+    if (m->plasma_n.empty()) {
+        dm.plasma = false;
+        return UE_OK;
+    }
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    if (!dm.J && !alloc_into(m, dm.J, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
+    if (!dm.pb && !alloc_into(m, dm.pb, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma coefficient");
+    double* d_n = nullptr;
+    if (!alloc_into(m, d_n, m->hm.n_nodes, 8, s)) return fail(UE_ERR_ALLOC, "plasma density");
+    UE_CUDA(cudaMemcpyAsync(d_n, m->plasma_n.data(), 8 * m->hm.n_nodes, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemsetAsync(dm.J, 0, esz * (m->hm.n_ei + 1), s));
+    UE_CUDA(ue::launch_plasma_coeff(dm, d_n, m->d_edge_nodes, m->plasma_nu, m->dt, s));
+    dm.pa = (1.0 - 0.5 * m->plasma_nu * m->dt) / (1.0 + 0.5 * m->plasma_nu * m->dt);
+    dm.plasma = true;
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int bake_source(ue_mesh* m, cudaStream_t s) {
+    DevMesh& dm = m->dm;
+    dm.n_src = (int64_t)m->src_k.size();
+    if (dm.n_src == 0) return UE_OK;
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    int32_t* k = nullptr;
+    double* amp = nullptr;
+    void* c = nullptr;
+    if (!alloc_into(m, k, dm.n_src, 4, s) || !alloc_into(m, amp, dm.n_src, 8, s) ||
+        !alloc_into(m, c, dm.n_src, esz, s))
+        return fail(UE_ERR_ALLOC, "source arrays");
+    UE_CUDA(cudaMemcpyAsync(k, m->src_k.data(), 4 * dm.n_src, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(amp, m->src_amp.data(), 8 * dm.n_src, cudaMemcpyHostToDevice, s));
+    dm.src_k = k;
+    dm.src_c = c;
+    UE_CUDA(ue::launch_source_coeff(dm, amp, m->d_elen, m->dt, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ue_options_default(ue_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->reorder = UE_REORDER_RCM;
+    o->precision = UE_PREC_FP32;
+    o->dt_mode = UE_DT_POWER;
+    o->power_iters = 200;
+    o->power_seed = 0;
+    o->variant = UE_VARIANT_PLAIN;
+    o->graph_chunk = 32;
+    o->dt = 0.0;
+    o->safety = 0.5;
+}
+
+const char* ue_last_error(void) { return g_err.c_str(); }
+
+int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                 const ue_options* opt, ue_alloc_fn alloc, ue_free_fn free_fn, void* alloc_ctx,
+                 ue_mesh** out) {
+    if (!out) return fail(UE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(UE_ERR_ARG, "alloc and free callbacks must both be set or both be NULL");
+    ue_options d;
+    ue_options_default(&d);
+    const ue_options& o = opt ? *opt : d;
+    if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM)
+        return fail(UE_ERR_ARG, "unknown reorder option");
+    ue_mesh* m = new (std::nothrow) ue_mesh();
+    if (!m) return fail(UE_ERR_ARG, "out of host memory");
+    std::string err;
+    int rc;
+    try {
+        rc = ue::build_host_mesh(xy, n_nodes, tris, n_tris, o.reorder, m->hm, err);
+    } catch (const std::bad_alloc&) {
+        rc = UE_ERR_ARG;
+        err = "out of host memory";
+    }
+    if (rc != UE_OK) {
+        delete m;
+        return fail(rc, err);
+    }
+    m->alloc = alloc;
+    m->free_fn = free_fn;
+    m->alloc_ctx = alloc_ctx;
+    *out = m;
+    return UE_OK;
+}
+
+int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
+    if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
+    ue_options d;
+    ue_options_default(&d);
+    const ue_options& o = opt ? *opt : d;
+    if (o.precision != UE_PREC_FP32 && o.precision != UE_PREC_FP64)
+        return fail(UE_ERR_ARG, "unknown precision");
+    if (o.dt_mode == UE_DT_GIVEN && !(o.dt > 0)) return fail(UE_ERR_ARG, "dt must be > 0");
+    if (o.dt_mode != UE_DT_GIVEN && o.dt_mode != UE_DT_POWER) return fail(UE_ERR_ARG, "unknown dt mode");
+    if (o.dt_mode == UE_DT_POWER && (o.power_iters < 1 || !(o.safety > 0)))
+        return fail(UE_ERR_ARG, "power iteration needs iters >= 1 and safety > 0");
+    if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN) return fail(UE_ERR_ARG, "unknown variant");
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostMesh& h = m->hm;
+    // a rebuild starts from scratch
+    drop_graph(m);
+    UE_CUDA(cudaStreamSynchronize(s));
+    dev_free_all(m, s);
+    m->built = false;
+    m->dm = DevMesh();
+    m->precision = o.precision;
+    m->graph_chunk = o.graph_chunk == 0 ? 32 : o.graph_chunk;
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    const int64_t nt = h.n_tris, nei = h.n_ei, nn = h.n_nodes, ne = h.n_edges;
+    bool ok = alloc_into(m, m->d_xy, 2 * nn, 8, s) && alloc_into(m, m->d_tri_nodes, 3 * nt, 4, s) &&
+              alloc_into(m, m->d_edge_nodes, 2 * nei + 2, 4, s) &&
+              alloc_into(m, m->d_edge_opp, 2 * nei + 2, 4, s) &&
+              alloc_into(m, m->d_tri_code, 3 * nt, 4, s) && alloc_into(m, m->d_rl, nei + 1, 8, s) &&
+              alloc_into(m, m->d_perm, nt, 8, s) && alloc_into(m, m->d_ecaller, nei + 1, 8, s) &&
+              alloc_into(m, m->d_O, 2 * nt, 8, s) && alloc_into(m, m->d_S, nt, 8, s) &&
+              alloc_into(m, m->d_elen, nei + 1, 8, s) && alloc_into(m, m->d_d, nei + 1, 8, s) &&
+              alloc_into(m, m->d_Ec, ne, 8, s) && alloc_into(m, m->d_Bc, nt, 8, s) &&
+              alloc_into(m, m->d_Jc, ne, 8, s);
+    DevMesh& dm = m->dm;
+    dm.precision = m->precision;
+    dm.n_t = nt;
+    dm.n_ei = nei;
+    dm.n_nodes = nn;
+    ok = ok && alloc_into(m, dm.tri, nt, 16, s) && alloc_into(m, dm.cU, nei + 1, esz, s) &&
+         alloc_into(m, dm.U, nei + 1, esz, s) && alloc_into(m, dm.B, nt, esz, s) &&
+         alloc_into(m, dm.step, 1, 8, s);
+    if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, nt, 8, s);
+    if (!ok) {
+        dev_free_all(m, s);
+        return fail(UE_ERR_ALLOC, "device allocation failed");
+    }
+    dm.rl = m->d_rl;
+    UE_CUDA(cudaMemcpyAsync(m->d_xy, h.xy.data(), 16 * nn, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_tri_nodes, h.tri_nodes.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_perm, h.perm_tri.data(), 8 * nt, cudaMemcpyHostToDevice, s));
+    if (nei > 0) {
+        UE_CUDA(cudaMemcpyAsync(m->d_edge_nodes, h.edge_nodes.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_edge_opp, h.edge_opp.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_rl, h.edge_tri.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_ecaller, h.edge_caller.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+    }
+    UE_CUDA(ue::launch_geom_tri(m->d_xy, m->d_tri_nodes, m->d_O, m->d_S, nt, s));
+    UE_CUDA(ue::launch_geom_edge(m->d_xy, m->d_edge_nodes, m->d_edge_opp, m->d_elen, m->d_d, nei, s));
+    // dual lengths must be positive (eq. 3 divides by |O_R O_L|)
+    {
+        std::vector<double> dd(nei), ll(nei);
+        if (nei > 0) {
+            UE_CUDA(cudaMemcpyAsync(dd.data(), m->d_d, 8 * nei, cudaMemcpyDeviceToHost, s));
+            UE_CUDA(cudaMemcpyAsync(ll.data(), m->d_elen, 8 * nei, cudaMemcpyDeviceToHost, s));
+        }
+        UE_CUDA(cudaStreamSynchronize(s));
+        for (int64_t k = 0; k < nei; ++k)
+            if (!(dd[k] > 1e-12 * ll[k])) {
+                const int64_t e = h.edge_caller[k];
+                return fail(UE_ERR_DUAL, "interior edge " + std::to_string(e) + " (nodes " +
+                                             std::to_string(h.edges[2 * e]) + "," +
+                                             std::to_string(h.edges[2 * e + 1]) +
+                                             ") has dual length |O_R O_L| <= 0: mesh is not Delaunay");
+            }
+    }
+    // triangle records first with dt = 0: the power iteration reads only their edge codes
+    UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, 0.0, s));
+    if (o.dt_mode == UE_DT_POWER) {
+        double* work = nullptr;
+        if (!alloc_into(m, work, ue::power_iteration_work_doubles(nt, nei), 8, s))
+            return fail(UE_ERR_ALLOC, "power iteration work space");
+        double rho = 0;
+        UE_CUDA(ue::power_iteration(m->d_rl, dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei,
+                                    o.power_iters, o.power_seed, work, &rho, s));
+        if (!(rho > 0) || !std::isfinite(rho)) return fail(UE_ERR_DUAL, "power iteration gave rho <= 0");
+        m->rho = rho;
+        m->rho_source = UE_RHO_POWER;
+        m->dt = o.safety * 2.0 / rho;
+    } else {
+        m->rho = 0;
+        m->rho_source = UE_RHO_GIVEN;
+        m->dt = o.dt;
+    }
+    dm.dt = m->dt;
+    UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, m->dt, s));
+    UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * (nei + 1), s));
+    UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * nt, s));
+    UE_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    m->steps_done = 0;
+    m->built = true;
+    m->version++;
+    int rc = bake_plasma(m, s);
+    if (rc != UE_OK) return rc;
+    return bake_source(m, s);
+}
+
+int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (dt) *dt = m->dt;
+    if (rho) *rho = m->rho;
+    if (src) *src = m->rho_source;
+    return UE_OK;
+}
+
+int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (n && !(nu >= 0)) return fail(UE_ERR_ARG, "collision rate must be >= 0");
+    if (n) {
+        for (int64_t v = 0; v < m->hm.n_nodes; ++v)
+            if (!std::isfinite(n[v]) || n[v] < 0) return fail(UE_ERR_ARG, "density must be finite and >= 0");
+        m->plasma_n.assign(n, n + m->hm.n_nodes);
+        m->plasma_nu = nu;
+    } else {
+        m->plasma_n.clear();
+    }
+    m->version++;
+    return bake_plasma(m, nullptr);
+}
+
+int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, double w0,
+                  double t0, double tau) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (n < 0 || (n > 0 && (!ids || !amp))) return fail(UE_ERR_ARG, "bad source arrays");
+    if (n > 0 && !(tau > 0)) return fail(UE_ERR_ARG, "tau must be > 0");
+    std::vector<int32_t> ks(n);
+    std::vector<char> used(m->hm.n_ei, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (ids[i] < 0 || ids[i] >= m->hm.n_edges) return fail(UE_ERR_ARG, "source edge id out of range");
+        const int64_t k = m->hm.k_of_edge[ids[i]];
+        if (k < 0) return fail(UE_ERR_ARG, "source on a boundary edge (E = 0 there)");
+        if (used[k]) return fail(UE_ERR_ARG, "repeated source edge");
+        if (!std::isfinite(amp[i])) return fail(UE_ERR_ARG, "non-finite source amplitude");
+        used[k] = 1;
+        ks[i] = (int32_t)k;
+    }
+    m->src_k = ks;
+    m->src_amp.assign(amp, amp + n);
+    m->dm.w0 = w0;
+    m->dm.t0 = t0;
+    m->dm.tau = tau;
+    m->dm.n_src = 0;
+    m->version++;
+    return bake_source(m, nullptr);
+}
+
+int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostMesh& h = m->hm;
+    if (E) UE_CUDA(cudaMemcpyAsync(m->d_Ec, E, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
+    if (B) UE_CUDA(cudaMemcpyAsync(m->d_Bc, B, 8 * h.n_tris, cudaMemcpyHostToDevice, s));
+    if (j && m->dm.J) UE_CUDA(cudaMemcpyAsync(m->d_Jc, j, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
+    UE_CUDA(ue::launch_fields_in(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
+                                 (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
+                                 m->d_elen, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (n < 0) return fail(UE_ERR_ARG, "n_steps < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t left = n;
+    if (m->graph_chunk > 0 && n >= m->graph_chunk) {
+        int rc = ensure_graph(m);
+        if (rc != UE_OK) return rc;
+        while (left >= m->graph_chunk) {
+            UE_CUDA(cudaGraphLaunch(m->gexec, s));
+            left -= m->graph_chunk;
+        }
+    }
+    for (; left > 0; --left) UE_CUDA(ue::launch_step_plain(m->dm, s));
+    m->steps_done += n;
+    m->launches += n * kernels_per_step(m);
+    return UE_OK;
+}
+
+int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostMesh& h = m->hm;
+    if (E) UE_CUDA(cudaMemsetAsync(m->d_Ec, 0, 8 * h.n_edges, s));
+    if (j) UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
+    UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
+                                  (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
+                                  m->d_elen, s));
+    if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+    if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
+    if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int ue_get_step(const ue_mesh* m, int64_t* step) {
+    if (!m || !m->built || !step) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+    long long v = 0;
+    UE_CUDA(cudaMemcpy(&v, m->dm.step, 8, cudaMemcpyDeviceToHost));
+    *step = v;
+    return UE_OK;
+}
+
+int ue_set_step(ue_mesh* m, int64_t step) {
+    if (!m || !m->built || step < 0) return fail(UE_ERR_ARG, "geometry not built or step < 0");
+    long long v = step;
+    UE_CUDA(cudaMemcpy(m->dm.step, &v, 8, cudaMemcpyHostToDevice));
+    m->steps_done = 0;
+    return UE_OK;
+}
+
+int ue_get_sizes(const ue_mesh* m, int64_t* nn, int64_t* nt, int64_t* ne, int64_t* nei) {
+    if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
+    if (nn) *nn = m->hm.n_nodes;
+    if (nt) *nt = m->hm.n_tris;
+    if (ne) *ne = m->hm.n_edges;
+    if (nei) *nei = m->hm.n_ei;
+    return UE_OK;
+}
+
+int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int32_t* edge_tri,
+                  int32_t* tri_code) {
+    if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
+    const HostMesh& h = m->hm;
+    if (perm_tri) std::memcpy(perm_tri, h.perm_tri.data(), 8 * h.n_tris);
+    if (edge_caller) std::memcpy(edge_caller, h.edge_caller.data(), 8 * h.n_ei);
+    if (edge_tri) std::memcpy(edge_tri, h.edge_tri.data(), 8 * h.n_ei);
+    if (tri_code) std::memcpy(tri_code, h.tri_code.data(), 12 * h.n_tris);
+    return UE_OK;
+}
+
+int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    const HostMesh& h = m->hm;
+    cudaStream_t s = nullptr;
+    double *tO = nullptr, *tS = nullptr, *tl = nullptr, *td = nullptr;
+    if ((O && !alloc_into(m, tO, 2 * h.n_tris, 8, s)) || (S && !alloc_into(m, tS, h.n_tris, 8, s)) ||
+        (elen && !alloc_into(m, tl, h.n_edges, 8, s)) || (d && !alloc_into(m, td, h.n_edges, 8, s)))
+        return fail(UE_ERR_ALLOC, "geometry export buffers");
+    UE_CUDA(ue::launch_scatter_geometry(m->d_O, m->d_S, m->d_elen, m->d_d, m->d_perm, m->d_ecaller,
+                                        h.n_tris, h.n_ei, h.n_edges, tO, tS, tl, td, s));
+    if (O) UE_CUDA(cudaMemcpy(O, tO, 16 * h.n_tris, cudaMemcpyDeviceToHost));
+    if (S) UE_CUDA(cudaMemcpy(S, tS, 8 * h.n_tris, cudaMemcpyDeviceToHost));
+    if (elen) UE_CUDA(cudaMemcpy(elen, tl, 8 * h.n_edges, cudaMemcpyDeviceToHost));
+    if (d) UE_CUDA(cudaMemcpy(d, td, 8 * h.n_edges, cudaMemcpyDeviceToHost));
+    return UE_OK;
+}
+
+int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* bytes) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (n < 1 || n > 4096 || !ms) return fail(UE_ERR_ARG, "n_steps must be in 1..4096 and ms non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(4 * n, nullptr);
+    int rc = UE_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            rc = fail(UE_ERR_CUDA, "cudaEventCreate");
+            break;
+        }
+    for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
+        for (int p = 0; p < 3 && rc == UE_OK; ++p) {
+            cudaEventRecord(ev[4 * i + p], s);
+            cudaError_t e = ue::launch_step_part(m->dm, p, s);
+            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
+        }
+        cudaEventRecord(ev[4 * i + 3], s);
+    }
+    double acc[3] = {0, 0, 0};
+    if (rc == UE_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile sync: ") + cudaGetErrorString(e));
+        for (int64_t i = 0; i < n && rc == UE_OK; ++i)
+            for (int p = 0; p < 3; ++p) {
+                float t = 0;
+                cudaEventElapsedTime(&t, ev[4 * i + p], ev[4 * i + p + 1]);
+                acc[p] += t;
+            }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc != UE_OK) return rc;
+    for (int p = 0; p < 3; ++p) ms[p] = acc[p] / (double)n;
+    m->steps_done += n;
+    m->launches += n * kernels_per_step(m);
+    if (bytes) {
+        const double f = m->precision == UE_PREC_FP64 ? 2.0 : 1.0;
+        const HostMesh& h = m->hm;
+        bytes[0] = (8.0 + f * 12.0 + (m->dm.plasma ? f * 12.0 : 0.0)) * (double)h.n_ei;
+        bytes[1] = (double)m->dm.n_src * (4.0 + f * 12.0);
+        bytes[2] = (16.0 + f * 8.0 + (m->precision == UE_PREC_FP64 ? 8.0 : 0.0)) * (double)h.n_tris;
+    }
+    return UE_OK;
+}
+
+int ue_stats(const ue_mesh* m, ue_stats_t* out) {
+    if (!m || !out) return fail(UE_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    const HostMesh& h = m->hm;
+    out->n_nodes = h.n_nodes;
+    out->n_tris = h.n_tris;
+    out->n_edges = h.n_edges;
+    out->n_interior_edges = h.n_ei;
+    out->steps_done = m->steps_done;
+    out->dt = m->dt;
+    out->rho = m->rho;
+    out->rho_source = m->rho_source;
+    out->precision = m->precision;
+    const double f = m->precision == UE_PREC_FP64 ? 2.0 : 1.0;
+    // per edge: (R,L) 8 B, coefficient, U read + write; per triangle: 3 codes + dt/S record
+    // (16 B; fp64 adds an 8 B dt/S), B read + write; plasma: J read + write and its coefficient
+    double per_edge = 8.0 + f * 12.0 + (m->dm.plasma ? f * 12.0 : 0.0);
+    double per_tri = 16.0 + f * 8.0 + (m->precision == UE_PREC_FP64 ? 8.0 : 0.0);
+    out->bytes_per_step = per_edge * (double)h.n_ei + per_tri * (double)h.n_tris;
+    out->kernel_launches = m->launches;
+    return UE_OK;
+}
+
+void ue_mesh_free(ue_mesh* m) {
+    if (!m) return;
+    drop_graph(m);
+    cudaDeviceSynchronize();
+    dev_free_all(m, nullptr);
+    if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+"""C-ABI checks that need no GPU: symbol exports and the host ingest tables (bit-exact)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import mesh as om, rcm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ue():
+    from paper_1812_01448_gb300 import build
+    build.build()
+    import paper_1812_01448_gb300 as ue
+    return ue
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ue.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ue_[a-z_0-9]+)\s*\(", src)) - {"ue_alloc_fn", "ue_free_fn"})
+
+
+def test_library_exports_every_declared_symbol(ue):
+    from paper_1812_01448_gb300 import _native
+    L = ctypes.CDLL(_native.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(s[0] for s in _native.SIGNATURES) == names
+
+
+def _meshes():
+    yield "cavity", meshgen.cavity_te11_mesh()
+    yield "random", meshgen.random_delaunay(2000, seed=21)
+    yield "hole", meshgen.graded_square(0.01, 0.03, grade=0.3,
+                                         holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=9)
+
+
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_tables_bit_exact_against_oracle(ue, reorder):
+    for name, ms in _meshes():
+        # shuffle caller numbering and flip half the triangles to exercise orientation
+        rng = np.random.default_rng(1)
+        tris = ms.tris[rng.permutation(ms.n_tris)].copy()
+        flip = rng.random(ms.n_tris) < 0.5
+        tris[flip] = tris[flip][:, [0, 2, 1]]
+        m = ue.Mesh(ms.xy, tris, reorder=reorder)
+        t = m.tables()
+        om_ = om.canonicalize(ms.xy, tris)
+        order = rcm.rcm_order(om_) if reorder == 1 else np.arange(om_.n_tris)
+        ref = rcm.device_tables(om_, order)
+        assert m.n_edges == om_.n_edges and m.n_ei == ref["n_ei"], name
+        assert np.array_equal(t["perm_tri"], ref["perm_tri"]), name
+        assert np.array_equal(t["edge_caller"], ref["edge_caller"]), name
+        assert np.array_equal(t["edge_tri"], ref["edge_tri"]), name
+        assert np.array_equal(t["tri_code"], ref["tri_code"]), name
+        m.close()
+
+
+@pytest.mark.parametrize("tris,code", [
+    ([[0, 1, 4]], -1),
+    ([[0, 1, 1]], -3),
+    ([[0, 1, 2], [0, 1, 3]], -2),
+])
+def test_ingest_errors_match_oracle_classification(ue, tris, code):
+    xy = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    with pytest.raises(ue.UEError) as ei:
+        ue.Mesh(xy, np.array(tris))
+    assert ei.value.code == code
+    with pytest.raises(om.MeshError) as eo:
+        om.canonicalize(xy, np.array(tris))
+    assert eo.value.code == code
+
+
+def test_collinear_and_nonmanifold_rejected(ue):
+    with pytest.raises(ue.UEError) as ei:
+        ue.Mesh(np.array([[0, 0], [1, 0], [2, 0]], float), np.array([[0, 1, 2]]))
+    assert ei.value.code == -3
+    xy = np.array([[0, 0], [1, 0], [0.5, 1], [0.5, -1], [0.5, 2]], float)
+    with pytest.raises(ue.UEError) as ei:
+        ue.Mesh(xy, np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]]))
+    assert ei.value.code == -2

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same inputs.
+
+Tolerances: FP32 product <= 1e-4 relative L2 of each field after the stated number of steps;
+FP64 check build <= 1e-12; geometry and power iteration are FP64 on both sides; connectivity,
+graph replay and checkpoint/resume are bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import leapfrog as lf, mesh as om, operators, spectral
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ue():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01448_gb300 import build
+    build.build()
+    import paper_1812_01448_gb300 as ue
+    return ue
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle(ms):
+    return operators.Operators(om.canonicalize(ms.xy, ms.tris))
+
+
+@pytest.fixture(scope="module")
+def cavity(cavity_mesh):
+    return cavity_mesh, _oracle(cavity_mesh)
+
+
+def test_geometry_matches_oracle(ue, cavity):
+    ms, ops = cavity
+    for mesh in (ms, meshgen.graded_square(0.01, 0.03, grade=0.3, seed=9,
+                                           holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)])):
+        o = ops if mesh is ms else _oracle(mesh)
+        m = ue.Mesh(mesh.xy, mesh.tris)
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-3)
+        g = m.geometry()
+        np.testing.assert_allclose(g["O"], o.geom.O, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(g["S"], o.geom.S, rtol=1e-12)
+        ie = o.ie
+        np.testing.assert_allclose(g["elen"][ie], o.geom.elen[ie], rtol=1e-14)
+        np.testing.assert_allclose(g["d"][ie], o.geom.d[ie], rtol=1e-9)
+        assert rel_l2(g["d"][ie], o.geom.d[ie]) < 1e-12
+        assert np.all(np.isnan(g["d"][~o.mesh.interior]))
+        m.close()
+
+
+def test_power_iteration_matches_oracle(ue, cavity):
+    ms, ops = cavity
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(power_iters=200, power_seed=7, safety=0.5)
+    dt, rho, src = m.get_dt()
+    rho_o, _ = spectral.power_iteration(ops, 200, seed=7)
+    assert src == 1
+    assert abs(rho / rho_o - 1) < 1e-10
+    assert abs(dt - 1.0 / rho) < 1e-15 / rho
+    lo, hi = spectral.certified_bracket(ops)
+    assert lo <= rho <= hi
+
+
+def _cavity_run(ue, ms, ops, precision, nsteps, graph_chunk=0, reorder=1):
+    rho, _ = spectral.power_iteration(ops, 200)
+    dt = 1.0 / rho
+    B0 = meshgen.te_mode_b(ops.geom.O, 1, 1, 1.0, 0.5)
+    m = ue.Mesh(ms.xy, ms.tris, reorder=reorder)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, precision=precision, graph_chunk=graph_chunk)
+    m.write_fields(E=np.zeros(m.n_edges), B=B0)
+    m.step_n(nsteps)
+    E, B, _ = m.read_fields()
+    m.close()
+    st = lf.run(ops, lf.initial_state(ops, B=B0), dt, nsteps)
+    return E, B, ops.extend(st.E), st.B
+
+
+def test_cavity_te11_fp32_1000_steps(ue, cavity):
+    ms, ops = cavity
+    E, B, Eo, Bo = _cavity_run(ue, ms, ops, ue.UE_PREC_FP32, 1000)
+    eE, eB = rel_l2(E, Eo), rel_l2(B, Bo)
+    print(f"cavity fp32 1000 steps: rel L2 E {eE:.2e} B {eB:.2e}")
+    assert eE <= 1e-4 and eB <= 1e-4
+    assert np.all(E[~ops.mesh.interior] == 0)
+
+
+def test_cavity_te11_fp64_check_1000_steps(ue, cavity):
+    ms, ops = cavity
+    E, B, Eo, Bo = _cavity_run(ue, ms, ops, ue.UE_PREC_FP64, 1000)
+    eE, eB = rel_l2(E, Eo), rel_l2(B, Bo)
+    print(f"cavity fp64 1000 steps: rel L2 E {eE:.2e} B {eB:.2e}")
+    assert eE <= 1e-12 and eB <= 1e-12
+
+
+def test_graph_replay_is_bit_identical_to_plain_launches(ue, cavity):
+    ms, ops = cavity
+    a = _cavity_run(ue, ms, ops, ue.UE_PREC_FP32, 100, graph_chunk=32)
+    b = _cavity_run(ue, ms, ops, ue.UE_PREC_FP32, 100, graph_chunk=-1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_reorder_does_not_change_results_beyond_rounding(ue, cavity):
+    ms, ops = cavity
+    a = _cavity_run(ue, ms, ops, ue.UE_PREC_FP64, 300, reorder=0)
+    b = _cavity_run(ue, ms, ops, ue.UE_PREC_FP64, 300, reorder=1)
+    assert rel_l2(a[0], b[0]) < 1e-13 and rel_l2(a[1], b[1]) < 1e-13
+
+
+def _plasma_case(n_tris=20000, seed=1003):
+    ms = meshgen.plasma_square_mesh(n_tris, seed=seed)
+    ops = _oracle(ms)
+    w0 = 2 * math.pi * 20
+    dens = meshgen.plasma_density_nodes(ms.xy, w0)
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    return ms, ops, w0, dens, ids, amp
+
+
+@pytest.mark.parametrize("precision,nsteps,tol", [(0, 20000, 1e-4), (1, 2000, 1e-12)])
+def test_plasma_with_source_downscale(ue, precision, nsteps, tol):
+    """Plasma workload at 20k triangles: Gaussian density, nu = 0.01 w0, line source."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 200)
+    pl = lf.Plasma(dens, 0.01 * w0)
+    dt = spectral.stable_dt(rho, 0.5, pl.nbar(ops).max())
+    src = lf.Source(ids, amp, w0, 0.1, 0.05)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, precision=precision)
+    m.set_plasma(dens, 0.01 * w0)
+    m.set_source(ids, amp, w0, 0.1, 0.05)
+    m.step_n(nsteps)
+    E, B, J = m.read_fields(j=True)
+    assert m.get_step() == nsteps
+    m.close()
+    st = lf.run(ops, lf.initial_state(ops), dt, nsteps, plasma=pl, source=src)
+    Eo, Bo, Jo = ops.extend(st.E), st.B, ops.extend(st.j)
+    assert np.linalg.norm(Bo) > 0 and np.linalg.norm(Jo) > 0
+    errs = rel_l2(E, Eo), rel_l2(B, Bo), rel_l2(J, Jo)
+    print(f"plasma prec={precision} {nsteps} steps: rel L2 E {errs[0]:.2e} B {errs[1]:.2e} j {errs[2]:.2e}")
+    assert max(errs) <= tol
+
+
+def test_checkpoint_resume_is_bit_identical(ue):
+    ms, ops, w0, dens, ids, amp = _plasma_case(5000, seed=77)
+    rho, _ = spectral.power_iteration(ops, 100)
+    dt = 0.5 / rho
+
+    def fresh():
+        m = ue.Mesh(ms.xy, ms.tris)
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt)
+        m.set_plasma(dens, 0.01 * w0)
+        m.set_source(ids, amp, w0, 0.1, 0.05)
+        return m
+
+    a = fresh()
+    a.step_n(400)
+    Ea, Ba, Ja = a.read_fields(j=True)
+    b = fresh()
+    b.step_n(200)
+    E1, B1, J1 = b.read_fields(j=True)
+    step = b.get_step()
+    b.close()
+    c = fresh()
+    c.write_fields(E1, B1, J1)
+    c.set_step(step)
+    c.step_n(200)
+    Ec, Bc, Jc = c.read_fields(j=True)
+    assert np.array_equal(Ea, Ec) and np.array_equal(Ba, Bc) and np.array_equal(Ja, Jc)
+
+
+def test_non_delaunay_mesh_is_rejected(ue):
+    # a quad split along its long diagonal: the two opposite angles sum to more than pi
+    xy = np.array([[0, 0], [2, 0], [2.2, 1], [0.2, 1]], float) * [1, 0.3]
+    m = ue.Mesh(xy, np.array([[0, 1, 2], [0, 2, 3]]))
+    with pytest.raises(ue.UEError) as ei:
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-3)
+    assert ei.value.code == -4
+
+
+@pytest.mark.slow
+def test_full_size_scatterer_window(ue):
+    """The benchmarked workload (~4M triangles, RCM, FP32, graph launches) over a 200-step
+    window with the line source, against the oracle on the whole mesh."""
+    ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
+    ops = _oracle(ms)
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, 2e-4)
+    w0 = 2 * math.pi * 20
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build()
+    dt, rho, _ = m.get_dt()
+    m.set_source(ids, amp, w0, 0.1, 0.05)
+    m.set_step(5000)     # mid-pulse, so that the source is far from zero
+    m.step_n(200)
+    E, B, _ = m.read_fields()
+    m.close()
+    src = lf.Source(ids, amp, w0, 0.1, 0.05)
+    st = lf.initial_state(ops)
+    st.n = 5000
+    st = lf.run(ops, st, dt, 200, source=src)
+    eE, eB = rel_l2(E, ops.extend(st.E)), rel_l2(B, st.B)
+    print(f"scatterer n_t={ms.n_tris} 200 steps: rel L2 E {eE:.2e} B {eB:.2e}")
+    assert np.linalg.norm(st.B) > 0
+    assert eE <= 1e-4 and eB <= 1e-4
