@@ -179,7 +179,12 @@ def run_native(args):
     ms, ids, amp, w0, t0, tau = load_workload()
     stream = torch.cuda.current_stream()
     m = ue.Mesh(ms.xy, ms.tris)
-    m.geometry_build(stream=stream)
+    if args.quick_setup:
+        # profiling runs: a fixed dt instead of the 200-iteration power iteration, so that few
+        # kernel launches precede the captured ones
+        m.geometry_build(stream=stream, dt_mode=ue.UE_DT_GIVEN, dt=1e-5)
+    else:
+        m.geometry_build(stream=stream)
     dt, rho, _ = m.get_dt()
     m.set_source(ids, amp, w0, t0, tau)
     st = m.stats()
@@ -282,6 +287,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--quick-setup", action="store_true",
+                    help="fixed dt instead of power iteration (for profiler runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
