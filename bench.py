@@ -178,13 +178,17 @@ def run_native(args):
 
     ms, ids, amp, w0, t0, tau = load_workload()
     stream = torch.cuda.current_stream()
-    m = ue.Mesh(ms.xy, ms.tris)
+    blocked = args.variant == "blocked"
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
+                tile_tris=args.tile_tris)
+    vopt = dict(variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
+                block_depth=args.block_depth, graph_chunk=args.graph_chunk)
     if args.quick_setup:
         # profiling runs: a fixed dt instead of the 200-iteration power iteration, so that few
         # kernel launches precede the captured ones
-        m.geometry_build(stream=stream, dt_mode=ue.UE_DT_GIVEN, dt=1e-5)
+        m.geometry_build(stream=stream, dt_mode=ue.UE_DT_GIVEN, dt=1e-5, **vopt)
     else:
-        m.geometry_build(stream=stream)
+        m.geometry_build(stream=stream, **vopt)
     dt, rho, _ = m.get_dt()
     m.set_source(ids, amp, w0, t0, tau)
     st = m.stats()
@@ -218,8 +222,13 @@ def run_native(args):
     value = world * n_t * args.steps / (ms_total * 1e-3)
 
     # per-kernel device times, CUDA events on the launch stream, right after the timed region
-    prof_ms, prof_bytes = m.profile_steps(min(200, max(20, args.steps // 10)), stream)
-    names = ["E half-step (eq. 3)", "source", "B half-step (eq. 4)"]
+    nprof = min(200, max(20, args.steps // 10))
+    if blocked:
+        nprof = max(4, nprof // args.block_depth)
+    prof_ms, prof_bytes = m.profile_steps(nprof, stream)
+    names = ["k_edge_half: E half-step (eq. 3)", "k_source", "k_tri_half: B half-step (eq. 4)"]
+    if blocked:
+        names[0] = f"k_tb: {args.block_depth} leap-frog steps per launch on KD tiles"
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
@@ -231,6 +240,11 @@ def run_native(args):
             "step": {"bytes": step_bytes, "achieved_gbs": step_bytes * args.steps / (ms_total * 1e-3) / 1e9,
                      "frac": step_bytes * args.steps / (ms_total * 1e-3) / 1e9 / peak,
                      "kernel_ms": [float(x) for x in prof_ms]}}
+    if blocked:
+        roof["algorithmic_bytes_note"] = ("bytes of the same steps done by the plain kernels; the "
+                                          "blocked kernel streams streamed_bytes_per_launch")
+        roof["streamed_bytes_per_launch"] = prof_bytes[1]
+        roof["streamed_gbs"] = prof_bytes[1] / (prof_ms[0] * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
     E0 = torch.zeros(m.n_edges, dtype=torch.float64, pin_memory=True).numpy()
@@ -267,7 +281,9 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_tris": n_t, "n_interior_edges": n_ei,
-                       "n_edges": m.n_edges, "dt": dt, "rho": rho, "variant": "plain, CUDA graph of 32 steps",
+                       "n_edges": m.n_edges, "dt": dt, "rho": rho,
+                       "variant": (f"blocked k={args.block_depth} tiles<={args.tile_tris}" if blocked
+                                   else "plain") + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -287,6 +303,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--variant", choices=["plain", "blocked"], default="plain")
+    ap.add_argument("--tile-tris", type=int, default=2048)
+    ap.add_argument("--block-depth", type=int, default=4)
+    ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--quick-setup", action="store_true",
                     help="fixed dt instead of power iteration (for profiler runs)")
     args = ap.parse_args(argv)

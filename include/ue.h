@@ -45,6 +45,7 @@ extern "C" {
 
 #define UE_REORDER_NONE 0        /* triangles in caller order                                 */
 #define UE_REORDER_RCM 1         /* reverse Cuthill-McKee on the dual graph (default)         */
+#define UE_REORDER_KD 2          /* KD tiles of <= tile_tris triangles, RCM order inside      */
 
 #define UE_PREC_FP32 0           /* FP32 fields and coefficients (product)                    */
 #define UE_PREC_FP64 1           /* FP64 fields and coefficients (check build)                */
@@ -53,6 +54,8 @@ extern "C" {
 #define UE_DT_POWER 1            /* dt = safety * 2 / rho(M), rho by FP64 power iteration     */
 
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
+#define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
+                                 /* recomputed in shared memory; FP32; needs UE_REORDER_KD    */
 
 #define UE_RHO_GIVEN 0
 #define UE_RHO_POWER 1
@@ -70,8 +73,10 @@ typedef struct ue_options {
     int32_t dt_mode;       /* UE_DT_*                                                        */
     int32_t power_iters;   /* power-iteration steps (default 200)                            */
     uint32_t power_seed;   /* start vector: SplitMix64(seed * 2^32 + caller triangle id)     */
-    int32_t variant;       /* UE_VARIANT_* (0 = default)                                     */
+    int32_t variant;       /* UE_VARIANT_* (0 = default: plain)                              */
     int32_t graph_chunk;   /* steps per captured CUDA graph launch; 0 = default, <0 = none   */
+    int32_t tile_tris;     /* UE_REORDER_KD: maximum triangles per tile (ue_mesh_load)       */
+    int32_t block_depth;   /* UE_VARIANT_BLOCKED: steps per launch, 1..15                    */
     int32_t reserved0;
     double dt;             /* UE_DT_GIVEN: the time step                                     */
     double safety;         /* UE_DT_POWER: dt = safety * 2 / rho (default 0.5)               */
@@ -153,10 +158,13 @@ int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int
  * lengths (NaN on boundary edges).  Any pointer may be NULL. */
 int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
 
-/* Time the kernels of the plain step with CUDA events: n_steps steps (1..4096) launched one by
- * one on `stream` (no graph), then synchronised.  ms[0], ms[1], ms[2] receive the mean device
- * duration in milliseconds of the E half-step (eq. 3 / eqs. 5-6), the source and the B half-step
- * (eq. 4) kernels; bytes[0..2] their algorithmic HBM bytes per launch.  The fields advance. */
+/* Time the step kernels with CUDA events: n_steps (1..4096) launches one by one on `stream`
+ * (no graph), then synchronised; the fields advance.
+ * Plain variant: ms[0], ms[1], ms[2] = mean device milliseconds of the E half-step (eq. 3 /
+ * eqs. 5-6), source and B half-step (eq. 4) kernels; bytes[0..2] = their algorithmic HBM bytes
+ * per launch.  Blocked variant: each launch advances block_depth steps; ms[0] = mean per launch,
+ * bytes[0] = algorithmic bytes of the same number of plain steps, bytes[1] = bytes the blocked
+ * kernel streams per launch (tile records, local field reads, owned writes); ms[1..2] = 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
 int ue_stats(const ue_mesh* m, ue_stats_t* out);

@@ -12,6 +12,9 @@ no tie-break rules; the ones used here (and, independently, by the library) are:
   (degree, caller id);
 * the concatenated order is reversed at the end.
 
+For the temporally blocked variant the triangles are further grouped into KD parts
+(``kd_order``), keeping the RCM order inside each part.
+
 From an order the tables follow (same definitions in the library, separate code):
 
 * ``perm_tri[new] = caller triangle id``;
@@ -74,6 +77,36 @@ def rcm_order(mesh: Mesh) -> np.ndarray:
                 seen[w] = True
                 q.append(w)
     return np.asarray(order[::-1], np.int64)
+
+
+def kd_order(mesh: Mesh, rcm: np.ndarray, tile_tris: int):
+    """KD partition of the "Divide and conqueror" section: split a part at the median of its
+    triangle centroids along the longer side of their bounding box (ties by RCM position)
+    until it has at most tile_tris triangles.  Parts in depth-first order (left first), RCM
+    order inside a part.  Returns (order, tile offsets)."""
+    t = mesh.tris
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    cx = (x[t[:, 0]] + x[t[:, 1]] + x[t[:, 2]]) / 3.0
+    cy = (y[t[:, 0]] + y[t[:, 1]] + y[t[:, 2]]) / 3.0
+    pos = np.empty(mesh.n_tris, np.int64)
+    pos[rcm] = np.arange(mesh.n_tris)
+    order, offs = [], [0]
+
+    def part(ids):
+        if ids.size <= tile_tris:
+            order.extend(ids[np.argsort(pos[ids], kind="stable")].tolist())
+            offs.append(len(order))
+            return
+        ex = cx[ids].max() - cx[ids].min()
+        ey = cy[ids].max() - cy[ids].min()
+        key = cx if ex >= ey else cy
+        srt = ids[np.lexsort((pos[ids], key[ids]))]
+        mid = ids.size // 2
+        part(srt[:mid])
+        part(srt[mid:])
+
+    part(np.asarray(rcm, np.int64))
+    return np.asarray(order, np.int64), np.asarray(offs, np.int64)
 
 
 def device_tables(mesh: Mesh, perm_tri: np.ndarray):

@@ -10,10 +10,10 @@ LIB_PATH = os.path.join(_HERE, "libue.so")
 UE_OK = 0
 UE_ERR = {-1: "UE_ERR_ARG", -2: "UE_ERR_NONMANIFOLD", -3: "UE_ERR_DEGENERATE", -4: "UE_ERR_DUAL",
           -5: "UE_ERR_CUDA", -6: "UE_ERR_ALLOC", -7: "UE_ERR_UNSTABLE", -8: "UE_ERR_TIMEOUT"}
-UE_REORDER_NONE, UE_REORDER_RCM = 0, 1
+UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD = 0, 1, 2
 UE_PREC_FP32, UE_PREC_FP64 = 0, 1
 UE_DT_GIVEN, UE_DT_POWER = 0, 1
-UE_VARIANT_PLAIN = 1
+UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED = 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -22,7 +22,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 class Options(C.Structure):
     _fields_ = [("reorder", C.c_int32), ("precision", C.c_int32), ("dt_mode", C.c_int32),
                 ("power_iters", C.c_int32), ("power_seed", C.c_uint32), ("variant", C.c_int32),
-                ("graph_chunk", C.c_int32), ("reserved0", C.c_int32), ("dt", C.c_double),
+                ("graph_chunk", C.c_int32), ("tile_tris", C.c_int32), ("block_depth", C.c_int32),
+                ("reserved0", C.c_int32), ("dt", C.c_double),
                 ("safety", C.c_double)]
 
 

@@ -65,7 +65,8 @@ class _TorchAllocator:
 class Mesh:
     """A loaded mesh (``ue_mesh``).  Methods mirror the C calls of include/ue.h."""
 
-    def __init__(self, xy, tris, reorder: int = N.UE_REORDER_RCM, torch_alloc: bool = False):
+    def __init__(self, xy, tris, reorder: int = N.UE_REORDER_RCM, torch_alloc: bool = False,
+                 tile_tris: int = 2048):
         L = N.lib()
         self._xy = np.ascontiguousarray(xy, dtype=np.float64)
         t = np.ascontiguousarray(tris, dtype=np.int32)
@@ -73,7 +74,7 @@ class Mesh:
             raise ValueError("xy must be [n,2], tris [m,3]")
         self._allocator = _TorchAllocator() if torch_alloc else None
         h = C.c_void_p()
-        o = options(reorder=reorder)
+        o = options(reorder=reorder, tile_tris=tile_tris)
         a = self._allocator.alloc if self._allocator else N.ALLOC_FN()
         f = self._allocator.free if self._allocator else N.FREE_FN()
         N.check(L.ue_mesh_load(_dptr(self._xy), self._xy.shape[0], t.ctypes.data_as(N.PI32),

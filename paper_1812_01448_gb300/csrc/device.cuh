@@ -20,6 +20,15 @@ __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
 
+// g(t) of the soft source at t = (n + 1/2) dt, in FP64: sin(w0 t) exp(-((t - t0)/tau)^2).
+// One out-of-line definition with explicit rounding, shared by every variant of the step.
+static __device__ __noinline__ double source_g(long long n, double dt, double w0, double t0,
+                                               double tau) {
+    const double t = __dmul_rn(__dadd_rn((double)n, 0.5), dt);
+    const double x = __ddiv_rn(__dsub_rn(t, t0), tau);
+    return __dmul_rn(sin(__dmul_rn(w0, t)), exp(-__dmul_rn(x, x)));
+}
+
 // Everything the step kernels need, in the stored numbering.
 struct DevMesh {
     int precision = 0;            // UE_PREC_*
@@ -41,6 +50,28 @@ struct DevMesh {
     long long* step = nullptr;    // device step counter (source time)
     double dt = 0;
 };
+
+// Device side of the temporal-blocking tiles (kernels_tb.cu, tiles_host.cpp).
+struct TBDev {
+    int64_t n_tiles = 0;
+    int* hdr = nullptr;           // n_tiles * 48 ints
+    int4* trec = nullptr;         // local triangle records {gid, codes01, code2, bits of dt/S}
+    int64_t n_trec = 0;
+    int4* erec = nullptr;         // local edge records {gid, R | L << 16, bits of cU, bits of pb}
+    int64_t n_erec = 0;
+    int2* tsrc = nullptr;         // per-tile source records {local edge, source index}
+    int max_tri_loc = 0, max_edge_loc = 0;
+    void* B[2] = {nullptr, nullptr};
+    void* U[2] = {nullptr, nullptr};
+    void* J[2] = {nullptr, nullptr};
+    unsigned* done = nullptr;     // CTA completion counter (step counter hand-off)
+};
+
+int tb_threads();
+bool tb_fits(int max_tri_loc, int max_edge_loc);
+cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
+// k steps of the blocked kernel reading buffer `cur`, writing buffer cur ^ 1.
+cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, cudaStream_t s);
 
 // Launchers (kernels_step.cu).
 cudaError_t launch_step_plain(const DevMesh& m, cudaStream_t s);

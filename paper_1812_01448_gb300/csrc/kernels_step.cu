@@ -44,9 +44,7 @@ __global__ void k_source(const int32_t* __restrict__ sk, const T* __restrict__ s
                          double w0, double t0, double tau) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
-    const double t = ((double)*step + 0.5) * dt;
-    const double x = (t - t0) / tau;
-    const T g = (T)(sin(w0 * t) * exp(-x * x));
+    const T g = (T)source_g(*step, dt, w0, t0, tau);
     const int k = sk[i];
     U[k] = rn_fma(sc[i], g, U[k]);
 }

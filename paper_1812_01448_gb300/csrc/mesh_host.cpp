@@ -168,10 +168,59 @@ std::vector<int64_t> rcm(const Canon& c, int64_t nt) {
     return order;
 }
 
+// KD partition (the paper's "KD tree idea": recursive bisection into parts of equal size
+// along x or y): split at the median of the triangle centroids along the longer extent of
+// their bounding box, ties by RCM position, until a part has at most tile_tris triangles.
+// Parts are emitted depth-first (left before right); inside a part the RCM order is kept.
+void kd_order(const Canon& c, const double* xy, const std::vector<int64_t>& rcm_order,
+              int64_t tile_tris, std::vector<int64_t>& order, std::vector<int64_t>& tile_off) {
+    const int64_t nt = (int64_t)rcm_order.size();
+    std::vector<int64_t> pos(nt);
+    for (int64_t i = 0; i < nt; ++i) pos[rcm_order[i]] = i;
+    std::vector<double> cx(nt), cy(nt);
+    for (int64_t j = 0; j < nt; ++j) {
+        const int64_t a = c.tri[3 * j], b = c.tri[3 * j + 1], d = c.tri[3 * j + 2];
+        cx[j] = (xy[2 * a] + xy[2 * b] + xy[2 * d]) / 3.0;
+        cy[j] = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * d + 1]) / 3.0;
+    }
+    std::vector<int64_t> ids(rcm_order);
+    order.clear();
+    tile_off.assign(1, 0);
+    struct Part { int64_t lo, hi; };
+    std::vector<Part> stack{{0, nt}};
+    while (!stack.empty()) {
+        Part p = stack.back();
+        stack.pop_back();
+        const int64_t n = p.hi - p.lo;
+        if (n <= tile_tris) {
+            std::sort(ids.begin() + p.lo, ids.begin() + p.hi,
+                      [&](int64_t u, int64_t v) { return pos[u] < pos[v]; });
+            order.insert(order.end(), ids.begin() + p.lo, ids.begin() + p.hi);
+            tile_off.push_back((int64_t)order.size());
+            continue;
+        }
+        double x0 = cx[ids[p.lo]], x1 = x0, y0 = cy[ids[p.lo]], y1 = y0;
+        for (int64_t i = p.lo; i < p.hi; ++i) {
+            const int64_t j = ids[i];
+            x0 = std::min(x0, cx[j]);
+            x1 = std::max(x1, cx[j]);
+            y0 = std::min(y0, cy[j]);
+            y1 = std::max(y1, cy[j]);
+        }
+        const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? cx : cy;
+        std::sort(ids.begin() + p.lo, ids.begin() + p.hi, [&](int64_t u, int64_t v) {
+            return key[u] != key[v] ? key[u] < key[v] : pos[u] < pos[v];
+        });
+        const int64_t mid = p.lo + n / 2;
+        stack.push_back({mid, p.hi});   // right part, processed after the left one
+        stack.push_back({p.lo, mid});
+    }
+}
+
 }  // namespace
 
 int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
-                    int reorder, HostMesh& hm, std::string& err) {
+                    int reorder, int tile_tris, HostMesh& hm, std::string& err) {
     if (!xy || !tris || n_nodes < 3 || n_tris < 1 || n_nodes > INT32_MAX || n_tris > (INT32_MAX / 4)) {
         err = "bad mesh arguments (null pointer or size out of range)";
         return UE_ERR_ARG;
@@ -191,8 +240,16 @@ int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int6
     hm.xy.assign(xy, xy + 2 * n_nodes);
     hm.edges = c.edges;
     // triangle order
+    hm.tile_tri_off.clear();
     if (reorder == UE_REORDER_RCM) {
         hm.perm_tri = rcm(c, n_tris);
+    } else if (reorder == UE_REORDER_KD) {
+        if (tile_tris < 16) {
+            err = "tile_tris must be >= 16";
+            return UE_ERR_ARG;
+        }
+        std::vector<int64_t> r = rcm(c, n_tris);
+        kd_order(c, xy, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
     } else {
         hm.perm_tri.resize(n_tris);
         std::iota(hm.perm_tri.begin(), hm.perm_tri.end(), 0);

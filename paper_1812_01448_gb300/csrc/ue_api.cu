@@ -62,11 +62,19 @@ struct ue_mesh {
     std::vector<int32_t> src_k;
     std::vector<double> src_amp;
 
-    // captured step graph
+    // captured step graph (plain: one; blocked: one per starting buffer parity)
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_version = -1;
+    cudaGraphExec_t gexec_tb[2] = {nullptr, nullptr};
+    int64_t graph_version_tb[2] = {-1, -1};
     int64_t version = 0;
     cudaStream_t capture_stream = nullptr;
+
+    // temporally blocked variant
+    ue::TileSet ts;
+    ue::TBDev tb;
+    int block_depth = 4;
+    int cur = 0;                     // buffer holding the current fields
 };
 
 namespace {
@@ -109,7 +117,59 @@ void drop_graph(ue_mesh* m) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
     m->graph_version = -1;
+    for (int p = 0; p < 2; ++p) {
+        if (m->gexec_tb[p]) cudaGraphExecDestroy(m->gexec_tb[p]);
+        m->gexec_tb[p] = nullptr;
+        m->graph_version_tb[p] = -1;
+    }
 }
+
+// Point the plain-kernel view of the fields at buffer c.
+void set_current(ue_mesh* m, int c) {
+    m->cur = c;
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        m->dm.B = m->tb.B[c];
+        m->dm.U = m->tb.U[c];
+        m->dm.J = m->tb.J[c];
+    }
+}
+
+int tb_chunk_launches(const ue_mesh* m) {
+    const int per = m->graph_chunk / (2 * m->block_depth);
+    return 2 * (per < 1 ? 1 : per);
+}
+
+int ensure_graph_tb(ue_mesh* m, int parity) {
+    if (m->gexec_tb[parity] && m->graph_version_tb[parity] == m->version) return UE_OK;
+    if (m->gexec_tb[parity]) cudaGraphExecDestroy(m->gexec_tb[parity]);
+    m->gexec_tb[parity] = nullptr;
+    if (!m->capture_stream)
+        UE_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    UE_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    int c = parity;
+    for (int i = 0; i < tb_chunk_launches(m) && le == cudaSuccess; ++i) {
+        le = ue::launch_tb(m->tb, m->dm, m->block_depth, c, m->capture_stream);
+        c ^= 1;
+    }
+    cudaError_t ce = cudaStreamEndCapture(m->capture_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(UE_ERR_CUDA, std::string("blocked step capture: ") + cudaGetErrorString(le));
+    }
+    if (ce != cudaSuccess) return fail(UE_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&m->gexec_tb[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        m->gexec_tb[parity] = nullptr;
+        return fail(UE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    m->graph_version_tb[parity] = m->version;
+    return UE_OK;
+}
+
+int upload_tiles(ue_mesh* m, cudaStream_t s);
 
 int ensure_graph(ue_mesh* m) {
     if (m->gexec && m->graph_version == m->version) return UE_OK;
@@ -155,6 +215,17 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(ue::launch_plasma_coeff(dm, d_n, m->d_edge_nodes, m->plasma_nu, m->dt, s));
     dm.pa = (1.0 - 0.5 * m->plasma_nu * m->dt) / (1.0 + 0.5 * m->plasma_nu * m->dt);
     dm.plasma = true;
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        if (!m->tb.J[0]) {
+            m->tb.J[m->cur] = dm.J;
+            void* other = nullptr;
+            if (!alloc_into(m, other, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
+            m->tb.J[m->cur ^ 1] = other;
+        }
+        UE_CUDA(cudaMemsetAsync(m->tb.J[0], 0, esz * (m->hm.n_ei + 1), s));
+        UE_CUDA(cudaMemsetAsync(m->tb.J[1], 0, esz * (m->hm.n_ei + 1), s));
+        UE_CUDA(ue::launch_tb_fill(m->tb, dm, s));
+    }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
 }
@@ -175,7 +246,68 @@ int bake_source(ue_mesh* m, cudaStream_t s) {
     dm.src_k = k;
     dm.src_c = c;
     UE_CUDA(ue::launch_source_coeff(dm, amp, m->d_elen, m->dt, s));
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        // per-tile source records: (local edge, source index) for every local copy of a source edge
+        std::vector<int32_t> src_of(m->hm.n_ei, -1);
+        for (size_t i = 0; i < m->src_k.size(); ++i) src_of[m->src_k[i]] = (int32_t)i;
+        std::vector<int32_t> rec;
+        ue::TileSet& ts = m->ts;
+        int maxn = 0;
+        for (int64_t t = 0; t < ts.n_tiles; ++t) {
+            int32_t* h = &ts.hdr[t * ue::TileSet::kHdr];
+            h[8] = (int32_t)(rec.size() / 2);
+            const int64_t off = h[7], nel = h[5];
+            for (int64_t l = 0; l < nel; ++l) {
+                const int32_t src = src_of[ts.erec[4 * (off + l)]];
+                if (src >= 0) {
+                    rec.push_back((int32_t)l);
+                    rec.push_back(src);
+                }
+            }
+            h[9] = (int32_t)(rec.size() / 2) - h[8];
+            if (h[9] > maxn) maxn = h[9];
+        }
+        ts.max_src = maxn;
+        int2* d = nullptr;
+        if (!alloc_into(m, d, rec.size() / 2 + 1, 8, s)) return fail(UE_ERR_ALLOC, "tile source records");
+        if (!rec.empty()) UE_CUDA(cudaMemcpyAsync(d, rec.data(), 4 * rec.size(), cudaMemcpyHostToDevice, s));
+        m->tb.tsrc = d;
+        UE_CUDA(cudaMemcpyAsync(m->tb.hdr, ts.hdr.data(), 4 * ts.hdr.size(), cudaMemcpyHostToDevice, s));
+    }
     UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int upload_tiles(ue_mesh* m, cudaStream_t s) {
+    std::string err;
+    int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
+    if (rc != UE_OK) return fail(rc, err);
+    ue::TileSet& ts = m->ts;
+    if (!ue::tb_fits(ts.max_tri_loc, ts.max_edge_loc))
+        return fail(UE_ERR_ARG, "tiles with halo too large for the blocked kernel (" +
+                                    std::to_string(ts.max_tri_loc) + " triangles, " +
+                                    std::to_string(ts.max_edge_loc) + " edges): lower tile_tris or block_depth");
+    ue::TBDev& tb = m->tb;
+    tb = ue::TBDev();
+    tb.n_tiles = ts.n_tiles;
+    tb.n_trec = (int64_t)ts.trec.size() / 4;
+    tb.n_erec = (int64_t)ts.erec.size() / 4;
+    tb.max_tri_loc = ts.max_tri_loc;
+    tb.max_edge_loc = ts.max_edge_loc;
+    const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
+    bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
+              alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 1, 4, s) &&
+              alloc_into(m, tb.B[1], nt, 4, s) && alloc_into(m, tb.U[1], nei + 1, 4, s);
+    if (!ok) return fail(UE_ERR_ALLOC, "tile arrays");
+    tb.B[0] = m->dm.B;
+    tb.U[0] = m->dm.U;
+    UE_CUDA(cudaMemcpyAsync(tb.hdr, ts.hdr.data(), 4 * ts.hdr.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(tb.trec, ts.trec.data(), 4 * ts.trec.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(tb.erec, ts.erec.data(), 4 * ts.erec.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemsetAsync(tb.done, 0, 4, s));
+    UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * nt, s));
+    UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * (nei + 1), s));
+    UE_CUDA(ue::launch_tb_fill(tb, m->dm, s));
     return UE_OK;
 }
 
@@ -193,6 +325,8 @@ void ue_options_default(ue_options* o) {
     o->power_seed = 0;
     o->variant = UE_VARIANT_PLAIN;
     o->graph_chunk = 32;
+    o->tile_tris = 2048;
+    o->block_depth = 4;
     o->dt = 0.0;
     o->safety = 0.5;
 }
@@ -209,14 +343,14 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
     ue_options d;
     ue_options_default(&d);
     const ue_options& o = opt ? *opt : d;
-    if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM)
+    if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM && o.reorder != UE_REORDER_KD)
         return fail(UE_ERR_ARG, "unknown reorder option");
     ue_mesh* m = new (std::nothrow) ue_mesh();
     if (!m) return fail(UE_ERR_ARG, "out of host memory");
     std::string err;
     int rc;
     try {
-        rc = ue::build_host_mesh(xy, n_nodes, tris, n_tris, o.reorder, m->hm, err);
+        rc = ue::build_host_mesh(xy, n_nodes, tris, n_tris, o.reorder, o.tile_tris, m->hm, err);
     } catch (const std::bad_alloc&) {
         rc = UE_ERR_ARG;
         err = "out of host memory";
@@ -243,7 +377,13 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (o.dt_mode != UE_DT_GIVEN && o.dt_mode != UE_DT_POWER) return fail(UE_ERR_ARG, "unknown dt mode");
     if (o.dt_mode == UE_DT_POWER && (o.power_iters < 1 || !(o.safety > 0)))
         return fail(UE_ERR_ARG, "power iteration needs iters >= 1 and safety > 0");
-    if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN) return fail(UE_ERR_ARG, "unknown variant");
+    if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN && o.variant != UE_VARIANT_BLOCKED)
+        return fail(UE_ERR_ARG, "unknown variant");
+    if (o.variant == UE_VARIANT_BLOCKED) {
+        if (o.precision != UE_PREC_FP32) return fail(UE_ERR_ARG, "the blocked variant is FP32 only");
+        if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs UE_REORDER_KD");
+        if (o.block_depth < 1 || o.block_depth > 15) return fail(UE_ERR_ARG, "block_depth must be in 1..15");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
     // a rebuild starts from scratch
@@ -252,6 +392,10 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     dev_free_all(m, s);
     m->built = false;
     m->dm = DevMesh();
+    m->tb = ue::TBDev();
+    m->cur = 0;
+    m->variant = o.variant == 0 ? UE_VARIANT_PLAIN : o.variant;
+    m->block_depth = o.block_depth;
     m->precision = o.precision;
     m->graph_chunk = o.graph_chunk == 0 ? 32 : o.graph_chunk;
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
@@ -331,6 +475,10 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * (nei + 1), s));
     UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * nt, s));
     UE_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        int trc = upload_tiles(m, s);
+        if (trc != UE_OK) return trc;
+    }
     UE_CUDA(cudaStreamSynchronize(s));
     m->steps_done = 0;
     m->built = true;
@@ -408,6 +556,30 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
     if (n < 0) return fail(UE_ERR_ARG, "n_steps < 0");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t left = n;
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        const int64_t k = m->block_depth;
+        const int64_t chunk = (int64_t)tb_chunk_launches(m) * k;
+        int64_t launched = 0;
+        if (m->graph_chunk > 0 && left >= chunk) {
+            int rc = ensure_graph_tb(m, m->cur);
+            if (rc != UE_OK) return rc;
+            while (left >= chunk) {
+                UE_CUDA(cudaGraphLaunch(m->gexec_tb[m->cur], s));
+                left -= chunk;
+                launched += tb_chunk_launches(m);
+            }
+        }
+        while (left > 0) {
+            const int kk = (int)(left < k ? left : k);
+            UE_CUDA(ue::launch_tb(m->tb, m->dm, kk, m->cur, s));
+            set_current(m, m->cur ^ 1);
+            left -= kk;
+            ++launched;
+        }
+        m->steps_done += n;
+        m->launches += launched;
+        return UE_OK;
+    }
     if (m->graph_chunk > 0 && n >= m->graph_chunk) {
         int rc = ensure_graph(m);
         if (rc != UE_OK) return rc;
@@ -495,6 +667,49 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 1 || n > 4096 || !ms) return fail(UE_ERR_ARG, "n_steps must be in 1..4096 and ms non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        std::vector<cudaEvent_t> ev(n + 1, nullptr);
+        int rc = UE_OK;
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                rc = fail(UE_ERR_CUDA, "cudaEventCreate");
+                break;
+            }
+        for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
+            cudaEventRecord(ev[i], s);
+            cudaError_t e = ue::launch_tb(m->tb, m->dm, m->block_depth, m->cur, s);
+            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
+            else set_current(m, m->cur ^ 1);
+        }
+        if (rc == UE_OK) cudaEventRecord(ev[n], s);
+        double acc = 0;
+        if (rc == UE_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile sync: ") + cudaGetErrorString(e));
+            for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
+                float t = 0;
+                cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+                acc += t;
+            }
+        }
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (rc != UE_OK) return rc;
+        ms[0] = acc / (double)n;
+        ms[1] = ms[2] = 0;
+        m->steps_done += n * m->block_depth;
+        m->launches += n;
+        if (bytes) {
+            const HostMesh& h = m->hm;
+            const double pl = m->dm.plasma ? 1.0 : 0.0;
+            bytes[0] = (double)m->block_depth *
+                       ((20.0 + 12.0 * pl) * (double)h.n_ei + 24.0 * (double)h.n_tris);
+            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec +
+                       4.0 * (double)h.n_tris + (4.0 + 4.0 * pl) * (double)h.n_ei;
+            bytes[2] = 0;
+        }
+        return UE_OK;
+    }
     std::vector<cudaEvent_t> ev(4 * n, nullptr);
     int rc = UE_OK;
     for (auto& e : ev)

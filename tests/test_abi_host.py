@@ -64,6 +64,19 @@ def test_tables_bit_exact_against_oracle(ue, reorder):
         m.close()
 
 
+def test_kd_tiles_bit_exact_against_oracle(ue):
+    for name, ms in _meshes():
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=300)
+        t = m.tables()
+        om_ = om.canonicalize(ms.xy, ms.tris)
+        order, offs = rcm.kd_order(om_, rcm.rcm_order(om_), 300)
+        ref = rcm.device_tables(om_, order)
+        assert np.diff(offs).max() <= 300
+        for k in ("perm_tri", "edge_caller", "edge_tri", "tri_code"):
+            assert np.array_equal(t[k], ref[k]), (name, k)
+        m.close()
+
+
 @pytest.mark.parametrize("tris,code", [
     ([[0, 1, 4]], -1),
     ([[0, 1, 1]], -3),

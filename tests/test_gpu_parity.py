@@ -209,3 +209,55 @@ def test_full_size_scatterer_window(ue):
     print(f"scatterer n_t={ms.n_tris} 200 steps: rel L2 E {eE:.2e} B {eB:.2e}")
     assert np.linalg.norm(st.B) > 0
     assert eE <= 1e-4 and eB <= 1e-4
+
+
+def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=None, graph_chunk=0,
+                 B0=None):
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=tile)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=variant, block_depth=k,
+                     graph_chunk=graph_chunk)
+    if dens is not None:
+        m.set_plasma(dens, nu)
+    if src is not None:
+        m.set_source(*src)
+    if B0 is not None:
+        m.write_fields(B=B0)
+    m.step_n(nsteps)
+    out = m.read_fields(j=dens is not None)
+    step = m.get_step()
+    m.close()
+    return out, step
+
+
+@pytest.mark.parametrize("tile,k,nsteps", [(512, 4, 14), (1024, 8, 40), (300, 1, 5), (2048, 3, 64)])
+@pytest.mark.parametrize("plasma", [False, True])
+def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, plasma):
+    """Temporal blocking on KD tiles reproduces the plain two-kernel step bit for bit
+    (partial last launch, double buffering, halo recompute, source and current included)."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 50)
+    dt = 0.45 / rho
+    kw = dict(dens=dens if plasma else None, nu=0.01 * w0, src=(ids, amp, w0, 0.0, 0.05),
+              B0=np.sin(7 * ms.xy[ms.tris].mean(axis=1)[:, 0]))
+    (Ep, Bp, Jp), sp = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
+    for gc in (0, -1):
+        (Eb, Bb, Jb), sb = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k,
+                                        graph_chunk=gc, **kw)
+        assert sp == sb == nsteps
+        assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb)
+        if plasma:
+            assert np.array_equal(Jp, Jb)
+
+
+def test_blocked_against_oracle(ue):
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 200)
+    pl = lf.Plasma(dens, 0.01 * w0)
+    dt = spectral.stable_dt(rho, 0.5, pl.nbar(ops).max())
+    (E, B, J), _ = _run_variant(ue, ms, dt, 3001, ue.UE_VARIANT_BLOCKED, 1024, 4, dens=dens,
+                                nu=0.01 * w0, src=(ids, amp, w0, 0.1, 0.05))
+    st = lf.run(ops, lf.initial_state(ops), dt, 3001, plasma=pl,
+                source=lf.Source(ids, amp, w0, 0.1, 0.05))
+    errs = rel_l2(E, ops.extend(st.E)), rel_l2(B, st.B), rel_l2(J, ops.extend(st.j))
+    print(f"blocked plasma 3001 steps: rel L2 E {errs[0]:.2e} B {errs[1]:.2e} j {errs[2]:.2e}")
+    assert max(errs) <= 1e-4
