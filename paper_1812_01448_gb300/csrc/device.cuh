@@ -33,19 +33,25 @@ static __device__ __noinline__ double source_g(long long n, double dt, double w0
 struct DevMesh {
     int precision = 0;            // UE_PREC_*
     int64_t n_t = 0, n_ei = 0, n_nodes = 0;
-    const int2* rl = nullptr;     // [n_ei] (R, L)
-    int4* tri = nullptr;          // [n_t] {code0, code1, code2, bits of dt/S (fp32) | 0}
-    void* cU = nullptr;           // [n_ei] dt*|e|/d, field precision
-    void* cB = nullptr;           // [n_t] dt/S (fp64 check build only)
-    void* U = nullptr;            // [n_ei + 1] circulation |e| E; slot n_ei stays 0
-    void* B = nullptr;            // [n_t]
+    int64_t n_ei_pad = 0;         // round_up(n_ei + 1, 4): edge arrays, incl. the zero slot
+    int64_t n_t_pad = 0;          // round_up(n_t, 4): triangle arrays
+    const int2* rl = nullptr;     // [n_ei_pad] (R, L); padding (0, 0)
+    int4* tri = nullptr;          // [n_t_pad] {code0, code1, code2, bits of dt/S (fp32) | 0}
+    void* cU = nullptr;           // [n_ei_pad] dt*|e|/d (sign bit set on source edges); pad 0
+    void* cB = nullptr;           // [n_t_pad] dt/S (fp64 check build only)
+    void* U = nullptr;            // [n_ei_pad] circulation |e| E; slot n_ei stays 0
+    void* B = nullptr;            // [n_t_pad]
     bool plasma = false;
-    void* J = nullptr;            // [n_ei + 1] circulation |e| j
-    void* pb = nullptr;           // [n_ei] dt*nbar/(1 + nu dt/2)
+    void* J = nullptr;            // [n_ei_pad] circulation |e| j
+    void* pb = nullptr;           // [n_ei_pad] dt*nbar/(1 + nu dt/2)
     double pa = 1.0;              // (1 - nu dt/2)/(1 + nu dt/2)
     int64_t n_src = 0;
     int32_t* src_k = nullptr;     // [n_src] stored edge ids
     void* src_c = nullptr;        // [n_src] dt*|e|*amp
+    int2* src_hash = nullptr;     // open-addressing table {edge id, source index}
+    int src_bits = 0;             // table size 2^src_bits
+    double* gtab = nullptr;       // g(t) for the steps of the current chunk
+    int gtab_size = 0;
     double w0 = 0, t0 = 0, tau = 1;
     long long* step = nullptr;    // device step counter (source time)
     double dt = 0;
@@ -70,19 +76,27 @@ struct TBDev {
 int tb_threads();
 bool tb_fits(int max_tri_loc, int max_edge_loc);
 cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
-// k steps of the blocked kernel reading buffer `cur`, writing buffer cur ^ 1.
-cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, cudaStream_t s);
+// k steps of the blocked kernel reading buffer `cur`, writing buffer cur ^ 1; the source uses
+// g-table entries gbase .. gbase + k - 1.
+cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int gbase,
+                      cudaStream_t s);
 
 // Launchers (kernels_step.cu).
-cudaError_t launch_step_plain(const DevMesh& m, cudaStream_t s);
-// One kernel of the plain step: 0 = E half-step, 1 = source, 2 = B half-step.
-cudaError_t launch_step_part(const DevMesh& m, int part, cudaStream_t s);
+// g(t) table for the next `count` steps (no-op without a source).
+cudaError_t launch_gtab(const DevMesh& m, int count, cudaStream_t s);
+// One kernel of the plain step: 0 = E half-step (with current and source), 1 = B half-step;
+// s_index = this step's entry in the g table.
+cudaError_t launch_step_part(const DevMesh& m, int part, int s_index, cudaStream_t s);
+// g table + `count` plain steps (count <= gtab_size).
+cudaError_t launch_steps_plain(const DevMesh& m, int count, cudaStream_t s);
 
 // Geometry, coefficients, power iteration and field transfer (kernels_geom.cu).
 cudaError_t launch_geom_tri(const double* xy, const int32_t* tri_nodes, double* O, double* S,
                             int64_t n_t, cudaStream_t s);
 cudaError_t launch_geom_edge(const double* xy, const int32_t* edge_nodes, const int32_t* edge_opp,
                              double* elen, double* d, int64_t n_ei, cudaStream_t s);
+// cU = dt|e|/d on [0, n_ei), triangle records on [0, n_t) and their padding (codes on the zero
+// slot, coefficient 0).  Edge padding must be zeroed by the caller.
 cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, const double* S,
                          const int32_t* tri_code, double dt, cudaStream_t s);
 // FP64 power iteration on K = -L_E L_B in the S metric; returns rho in *rho (synchronous).
@@ -100,6 +114,9 @@ cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const i
                                 double nu, double dt, cudaStream_t s);
 cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen,
                                 double dt, cudaStream_t s);
+// Set (on = true) or clear the source flag (sign bit of cU) of the listed stored edges.
+cudaError_t launch_source_flags(const DevMesh& m, const int32_t* k, int64_t n, bool on,
+                                cudaStream_t s);
 cudaError_t launch_scatter_geometry(const double* O, const double* S, const double* elen,
                                     const double* d, const int64_t* perm_tri,
                                     const int64_t* edge_caller, int64_t n_t, int64_t n_ei,

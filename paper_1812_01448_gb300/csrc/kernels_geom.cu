@@ -64,19 +64,33 @@ __global__ void k_coeff_edge(const double* __restrict__ elen, const double* __re
 }
 
 // Triangle record {code0, code1, code2, bits of (float)(dt/S)}; FP64 build: separate dt/S.
+// Padding records [n_t, n_t_pad) point all three codes at the zero slot with coefficient 0.
 __global__ void k_coeff_tri(const int32_t* __restrict__ code, const double* __restrict__ S,
                             int4* __restrict__ tri, double* __restrict__ cB64, double dt,
-                            int64_t n_t) {
+                            int64_t n_t, int64_t n_t_pad, int zero_code) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
-    const double c = dt / S[j];
+    if (j >= n_t_pad) return;
     int4 r;
-    r.x = code[3 * j];
-    r.y = code[3 * j + 1];
-    r.z = code[3 * j + 2];
+    double c = 0.0;
+    if (j < n_t) {
+        c = dt / S[j];
+        r.x = code[3 * j];
+        r.y = code[3 * j + 1];
+        r.z = code[3 * j + 2];
+    } else {
+        r.x = r.y = r.z = zero_code;
+    }
     r.w = cB64 ? 0 : __float_as_int((float)c);
     tri[j] = r;
     if (cB64) cB64[j] = c;
+}
+
+template <typename T>
+__global__ void k_source_flags(T* __restrict__ cU, const int32_t* __restrict__ k, int64_t n, bool on) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T v = fabs(cU[k[i]]);
+    cU[k[i]] = on ? -v : v;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -293,8 +307,19 @@ cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, 
         else
             k_coeff_edge<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>(elen, d, (float*)m.cU, dt, m.n_ei);
     }
-    k_coeff_tri<<<blocks_for(m.n_t), kThreads, 0, s>>>(
-        tri_code, S, m.tri, m.precision == UE_PREC_FP64 ? (double*)m.cB : nullptr, dt, m.n_t);
+    k_coeff_tri<<<blocks_for(m.n_t_pad), kThreads, 0, s>>>(
+        tri_code, S, m.tri, m.precision == UE_PREC_FP64 ? (double*)m.cB : nullptr, dt, m.n_t,
+        m.n_t_pad, (int)(2 * m.n_ei));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_flags(const DevMesh& m, const int32_t* k, int64_t n, bool on,
+                                cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (m.precision == UE_PREC_FP64)
+        k_source_flags<double><<<blocks_for(n), kThreads, 0, s>>>((double*)m.cU, k, n, on);
+    else
+        k_source_flags<float><<<blocks_for(n), kThreads, 0, s>>>((float*)m.cU, k, n, on);
     return cudaGetLastError();
 }
 

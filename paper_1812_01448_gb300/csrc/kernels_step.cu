@@ -1,13 +1,19 @@
 // The leap-frog step (eqs. 14-15): the E half-step of eq. 3 (eq. 6 with the current of eq. 5
-// in plasma media) over interior edges, an optional soft source, then the B half-step of
-// eq. 4 over triangles.  Plain form: one thread per edge, then one thread per triangle.
+// in plasma media, plus the soft source) over interior edges, then the B half-step of eq. 4
+// over triangles.  Plain form: two kernels per step, four elements per thread with 16-byte
+// loads of the streamed arrays, so that each thread keeps several independent gathers in
+// flight.
 //
 // Stored variables are circulations U_i = |e_i| E_i (and J_i = |e_i| j_i), so that
 //   E half-step:  U_i += (dt |e_i| / d_i) (B_R - B_L)            [eq. 3 times dt |e_i|]
 //   plasma:       J_i  = pa J_i + pb_i U_i;  U_i -= dt J_i        [eqs. 5-6, trapezoidal in nu]
+//   source:       U_i += (dt |e_i| a_i) g(t_n)                    [g from a per-chunk table]
 //   B half-step:  B_j -= (dt / S_j) (s_0 U_0 + s_1 U_1 + s_2 U_2) [eq. 4]
-// with the sign s(j,q) carried in bit 0 of the edge code and boundary edges pointing at a
-// zero slot (U[n_ei] = 0).  Every operation is explicitly rounded (device.cuh).
+// The sign s(j,q) is bit 0 of the edge code; boundary edges point at a slot that stays 0.
+// Source edges carry the sign bit of their coefficient dt|e|/d (always > 0) as a flag and find
+// their source coefficient through a small open-addressing table.  Arrays are padded to a
+// multiple of four with neutral entries (R = L = 0 and zero coefficients; triangle codes on
+// the zero slot).  Every operation is explicitly rounded (device.cuh).
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -18,35 +24,100 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename T, bool PLASMA>
-__global__ void __launch_bounds__(kThreads)
-k_edge_half(const int2* __restrict__ rl, const T* __restrict__ cU, const T* __restrict__ B,
-            T* __restrict__ U, const T* __restrict__ pb, T* __restrict__ J, T pa, T mdt,
-            int64_t n_ei) {
-    const int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (k >= n_ei) return;
-    const int2 e = __ldg(rl + k);
-    const T b = rn_sub(__ldg(B + e.x), __ldg(B + e.y));
-    const T u = U[k];
-    T un = rn_fma(__ldg(cU + k), b, u);
-    if constexpr (PLASMA) {
-        const T jn = rn_fma(pa, J[k], rn_mul(__ldg(pb + k), u));
-        J[k] = jn;
-        un = rn_fma(mdt, jn, un);
+template <typename T>
+__device__ __forceinline__ void ld4(const T* __restrict__ p, T (&x)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
     }
-    U[k] = un;
 }
 
-// Soft source on its edges: U += dt |e| a g(t), t = (step + 1/2) dt, g in FP64.
+// load/store of read-write arrays (not through the read-only path)
 template <typename T>
-__global__ void k_source(const int32_t* __restrict__ sk, const T* __restrict__ sc, int64_t n,
-                         T* __restrict__ U, const long long* __restrict__ step, double dt,
-                         double w0, double t0, double tau) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const T g = (T)source_g(*step, dt, w0, t0, tau);
-    const int k = sk[i];
-    U[k] = rn_fma(sc[i], g, U[k]);
+__device__ __forceinline__ void ldw4(const T* p, T (&x)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&x)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+    }
+}
+
+__device__ __forceinline__ bool flagged(float c) { return __float_as_uint(c) >> 31; }
+__device__ __forceinline__ bool flagged(double c) {
+    return (unsigned long long)__double_as_longlong(c) >> 63;
+}
+
+template <typename T>
+struct SrcArgs {
+    const int2* hash;       // {edge id, source index}, empty slots have edge id -1
+    unsigned bits;          // table size 2^bits
+    const T* c;             // dt |e| a per source index
+    const double* g;        // g(t) per step of the current chunk
+    int s;                  // this step's index in the chunk table
+};
+
+template <typename T>
+__device__ __forceinline__ T source_term(const SrcArgs<T>& src, int k, T u) {
+    unsigned h = ((unsigned)k * 2654435761u) >> (32 - src.bits);
+    int2 e = __ldg(src.hash + h);
+    while (e.x != k) {
+        h = (h + 1) & ((1u << src.bits) - 1);
+        e = __ldg(src.hash + h);
+    }
+    return rn_fma(__ldg(src.c + e.y), (T)__ldg(src.g + src.s), u);
+}
+
+template <typename T, bool PLASMA, bool SRC>
+__global__ void __launch_bounds__(kThreads)
+k_edge_half(const int4* __restrict__ rl4, const T* __restrict__ cU, const T* __restrict__ B,
+            T* __restrict__ U, const T* __restrict__ pb, T* __restrict__ J, T pa, T mdt,
+            int64_t n_vec, SrcArgs<T> src) {
+    const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (v >= n_vec) return;
+    const int4 ra = __ldg(rl4 + 2 * v), rb = __ldg(rl4 + 2 * v + 1);
+    const int R[4] = {ra.x, ra.z, rb.x, rb.z};
+    const int L[4] = {ra.y, ra.w, rb.y, rb.w};
+    T c[4], u[4], b[4], un[4];
+    ld4(cU + 4 * v, c);
+    ldw4(U + 4 * v, u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = rn_sub(__ldg(B + R[i]), __ldg(B + L[i]));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) un[i] = rn_fma(fabs(c[i]), b[i], u[i]);
+    if constexpr (PLASMA) {
+        T jj[4], p[4];
+        ldw4(J + 4 * v, jj);
+        ld4(pb + 4 * v, p);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            jj[i] = rn_fma(pa, jj[i], rn_mul(p[i], u[i]));
+            un[i] = rn_fma(mdt, jj[i], un[i]);
+        }
+        st4(J + 4 * v, jj);
+    }
+    if constexpr (SRC) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (flagged(c[i])) un[i] = source_term(src, (int)(4 * v + i), un[i]);
+    }
+    st4(U + 4 * v, un);
 }
 
 template <typename T>
@@ -58,63 +129,84 @@ __device__ __forceinline__ T signed_load(const T* __restrict__ U, int code) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
-           const T* __restrict__ U, T* __restrict__ B, int64_t n_t, long long* __restrict__ step) {
-    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (j == 0) *step += 1;
-    if (j >= n_t) return;
-    const int4 t = __ldg(tri + j);
-    const T s = rn_add(rn_add(signed_load(U, t.x), signed_load(U, t.y)), signed_load(U, t.z));
-    T c;
-    if constexpr (sizeof(T) == 4) c = __int_as_float(t.w);
-    else c = __ldg(cB64 + j);
-    B[j] = rn_fma(-c, s, B[j]);
+           const T* __restrict__ U, T* __restrict__ B, int64_t n_vec, long long* __restrict__ step) {
+    const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (v == 0) *step += 1;
+    if (v >= n_vec) return;
+    int4 t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = __ldg(tri + 4 * v + i);
+    T bo[4];
+    ldw4(B + 4 * v, bo);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T s = rn_add(rn_add(signed_load(U, t[i].x), signed_load(U, t[i].y)),
+                           signed_load(U, t[i].z));
+        T c;
+        if constexpr (sizeof(T) == 4) c = __int_as_float(t[i].w);
+        else c = __ldg(cB64 + 4 * v + i);
+        bo[i] = rn_fma(-c, s, bo[i]);
+    }
+    st4(B + 4 * v, bo);
+}
+
+// g(t_n) for the next `count` steps, n = *step + i.
+__global__ void k_gtab(double* __restrict__ g, const long long* __restrict__ step, int count,
+                       double dt, double w0, double t0, double tau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) g[i] = source_g(*step + i, dt, w0, t0, tau);
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-template <typename T>
-void edge_half_t(const DevMesh& m, cudaStream_t s) {
-    if (m.n_ei == 0) return;
-    if (m.plasma)
-        k_edge_half<T, true><<<blocks_for(m.n_ei), kThreads, 0, s>>>(
-            m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, (T)m.pa,
-            (T)(-m.dt), m.n_ei);
-    else
-        k_edge_half<T, false><<<blocks_for(m.n_ei), kThreads, 0, s>>>(
-            m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, nullptr, nullptr, (T)0, (T)0, m.n_ei);
-}
-
-template <typename T>
-void source_t(const DevMesh& m, cudaStream_t s) {
+template <typename T, bool PLASMA>
+void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
+    const int64_t n_vec = m.n_ei_pad / 4;
+    SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.gtab, s_index};
+    const T pa = PLASMA ? (T)m.pa : (T)0, mdt = PLASMA ? (T)(-m.dt) : (T)0;
     if (m.n_src > 0)
-        k_source<T><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, (const T*)m.src_c, m.n_src,
-                                                             (T*)m.U, m.step, m.dt, m.w0, m.t0, m.tau);
+        k_edge_half<T, PLASMA, true><<<blocks_for(n_vec), kThreads, 0, s>>>(
+            (const int4*)m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J,
+            pa, mdt, n_vec, src);
+    else
+        k_edge_half<T, PLASMA, false><<<blocks_for(n_vec), kThreads, 0, s>>>(
+            (const int4*)m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J,
+            pa, mdt, n_vec, src);
 }
 
 template <typename T>
 void tri_half_t(const DevMesh& m, cudaStream_t s) {
-    k_tri_half<T><<<blocks_for(m.n_t), kThreads, 0, s>>>(m.tri, (const double*)m.cB,
-                                                         (const T*)m.U, (T*)m.B, m.n_t, m.step);
+    const int64_t n_vec = m.n_t_pad / 4;
+    k_tri_half<T><<<blocks_for(n_vec), kThreads, 0, s>>>(m.tri, (const double*)m.cB,
+                                                         (const T*)m.U, (T*)m.B, n_vec, m.step);
 }
 
 }  // namespace
 
-cudaError_t launch_step_part(const DevMesh& m, int part, cudaStream_t s) {
+cudaError_t launch_gtab(const DevMesh& m, int count, cudaStream_t s) {
+    if (m.n_src == 0 || count <= 0) return cudaSuccess;
+    k_gtab<<<(count + 63) / 64, 64, 0, s>>>(m.gtab, m.step, count, m.dt, m.w0, m.t0, m.tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_part(const DevMesh& m, int part, int s_index, cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
-    switch (part) {
-        case 0: f64 ? edge_half_t<double>(m, s) : edge_half_t<float>(m, s); break;
-        case 1: f64 ? source_t<double>(m, s) : source_t<float>(m, s); break;
-        default: f64 ? tri_half_t<double>(m, s) : tri_half_t<float>(m, s); break;
+    if (part == 0) {
+        if (f64) m.plasma ? edge_half_p<double, true>(m, s_index, s) : edge_half_p<double, false>(m, s_index, s);
+        else m.plasma ? edge_half_p<float, true>(m, s_index, s) : edge_half_p<float, false>(m, s_index, s);
+    } else {
+        f64 ? tri_half_t<double>(m, s) : tri_half_t<float>(m, s);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_plain(const DevMesh& m, cudaStream_t s) {
-    for (int p = 0; p < 3; ++p) {
-        cudaError_t e = launch_step_part(m, p, s);
-        if (e != cudaSuccess) return e;
+cudaError_t launch_steps_plain(const DevMesh& m, int count, cudaStream_t s) {
+    cudaError_t e = launch_gtab(m, count, s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        e = launch_step_part(m, 0, i, s);
+        if (e == cudaSuccess) e = launch_step_part(m, 1, i, s);
     }
-    return cudaSuccess;
+    return e;
 }
 
 }  // namespace ue

@@ -30,6 +30,8 @@ struct TBArgs {
     float* Uout;
     float* Jout;
     const float* src_c;
+    const double* gtab;
+    int gbase;
     long long* step;
     unsigned* done;
     int ksteps;
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
         if constexpr (SRC) {
             if (h[9] > 0) {
                 __syncthreads();
-                const float g = (float)source_g(n0 + s - 1, a.dt, a.w0, a.t0, a.tau);
+                const float g = (float)__ldg(a.gtab + a.gbase + s - 1);
                 for (int i = tid; i < h[9]; i += kNT) {
                     const int2 q = __ldg(a.tsrc + h[8] + i);
                     if (q.x < eend) Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
@@ -167,7 +169,7 @@ __global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restr
     if (i < n_trec) trec[i].w = tri[trec[i].x].w;
     if (i < n_erec) {
         const int g = erec[i].x;
-        erec[i].z = __float_as_int(cU[g]);
+        erec[i].z = __float_as_int(fabsf(cU[g]));   // without the source flag
         erec[i].w = pb ? __float_as_int(pb[g]) : 0;
     }
 }
@@ -207,7 +209,8 @@ cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, cudaStream_t s) {
+cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int gbase,
+                      cudaStream_t s) {
     TBArgs a;
     a.hdr = t.hdr;
     a.trec = t.trec;
@@ -220,6 +223,8 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, cud
     a.Uout = (float*)t.U[cur ^ 1];
     a.Jout = (float*)t.J[cur ^ 1];
     a.src_c = (const float*)m.src_c;
+    a.gtab = m.gtab;
+    a.gbase = gbase;
     a.step = m.step;
     a.done = t.done;
     a.ksteps = ksteps;

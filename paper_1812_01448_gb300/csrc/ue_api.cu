@@ -147,10 +147,10 @@ int ensure_graph_tb(ue_mesh* m, int parity) {
         UE_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     UE_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = cudaSuccess;
+    cudaError_t le = ue::launch_gtab(m->dm, tb_chunk_launches(m) * m->block_depth, m->capture_stream);
     int c = parity;
     for (int i = 0; i < tb_chunk_launches(m) && le == cudaSuccess; ++i) {
-        le = ue::launch_tb(m->tb, m->dm, m->block_depth, c, m->capture_stream);
+        le = ue::launch_tb(m->tb, m->dm, m->block_depth, c, i * m->block_depth, m->capture_stream);
         c ^= 1;
     }
     cudaError_t ce = cudaStreamEndCapture(m->capture_stream, &g);
@@ -178,9 +178,7 @@ int ensure_graph(ue_mesh* m) {
         UE_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     UE_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = cudaSuccess;
-    for (int i = 0; i < m->graph_chunk && le == cudaSuccess; ++i)
-        le = ue::launch_step_plain(m->dm, m->capture_stream);
+    cudaError_t le = ue::launch_steps_plain(m->dm, m->graph_chunk, m->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(m->capture_stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -197,7 +195,11 @@ int ensure_graph(ue_mesh* m) {
     return UE_OK;
 }
 
-int kernels_per_step(const ue_mesh* m) { return 2 + (m->dm.n_src > 0 ? 1 : 0); }
+// kernels launched for `steps` plain steps issued in batches of `batch` (one g-table kernel
+// per batch when a source is set)
+int64_t plain_launches(const ue_mesh* m, int64_t steps, int64_t batch) {
+    return 2 * steps + (m->dm.n_src > 0 ? (steps + batch - 1) / batch : 0);
+}
 
 int bake_plasma(ue_mesh* m, cudaStream_t s) {
     DevMesh& dm = m->dm;
@@ -206,12 +208,13 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
         return UE_OK;
     }
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
-    if (!dm.J && !alloc_into(m, dm.J, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
-    if (!dm.pb && !alloc_into(m, dm.pb, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma coefficient");
+    if (!dm.J && !alloc_into(m, dm.J, dm.n_ei_pad, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
+    if (!dm.pb && !alloc_into(m, dm.pb, dm.n_ei_pad, esz, s)) return fail(UE_ERR_ALLOC, "plasma coefficient");
+    UE_CUDA(cudaMemsetAsync(dm.pb, 0, esz * dm.n_ei_pad, s));
     double* d_n = nullptr;
     if (!alloc_into(m, d_n, m->hm.n_nodes, 8, s)) return fail(UE_ERR_ALLOC, "plasma density");
     UE_CUDA(cudaMemcpyAsync(d_n, m->plasma_n.data(), 8 * m->hm.n_nodes, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemsetAsync(dm.J, 0, esz * (m->hm.n_ei + 1), s));
+    UE_CUDA(cudaMemsetAsync(dm.J, 0, esz * dm.n_ei_pad, s));
     UE_CUDA(ue::launch_plasma_coeff(dm, d_n, m->d_edge_nodes, m->plasma_nu, m->dt, s));
     dm.pa = (1.0 - 0.5 * m->plasma_nu * m->dt) / (1.0 + 0.5 * m->plasma_nu * m->dt);
     dm.plasma = true;
@@ -219,11 +222,11 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
         if (!m->tb.J[0]) {
             m->tb.J[m->cur] = dm.J;
             void* other = nullptr;
-            if (!alloc_into(m, other, m->hm.n_ei + 1, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
+            if (!alloc_into(m, other, dm.n_ei_pad, esz, s)) return fail(UE_ERR_ALLOC, "plasma current");
             m->tb.J[m->cur ^ 1] = other;
         }
-        UE_CUDA(cudaMemsetAsync(m->tb.J[0], 0, esz * (m->hm.n_ei + 1), s));
-        UE_CUDA(cudaMemsetAsync(m->tb.J[1], 0, esz * (m->hm.n_ei + 1), s));
+        UE_CUDA(cudaMemsetAsync(m->tb.J[0], 0, esz * dm.n_ei_pad, s));
+        UE_CUDA(cudaMemsetAsync(m->tb.J[1], 0, esz * dm.n_ei_pad, s));
         UE_CUDA(ue::launch_tb_fill(m->tb, dm, s));
     }
     UE_CUDA(cudaStreamSynchronize(s));
@@ -232,8 +235,12 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
 
 int bake_source(ue_mesh* m, cudaStream_t s) {
     DevMesh& dm = m->dm;
+    if (dm.n_src > 0 && dm.src_k) UE_CUDA(ue::launch_source_flags(dm, dm.src_k, dm.n_src, false, s));
     dm.n_src = (int64_t)m->src_k.size();
-    if (dm.n_src == 0) return UE_OK;
+    if (dm.n_src == 0) {
+        UE_CUDA(cudaStreamSynchronize(s));
+        return UE_OK;
+    }
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
     int32_t* k = nullptr;
     double* amp = nullptr;
@@ -246,6 +253,23 @@ int bake_source(ue_mesh* m, cudaStream_t s) {
     dm.src_k = k;
     dm.src_c = c;
     UE_CUDA(ue::launch_source_coeff(dm, amp, m->d_elen, m->dt, s));
+    UE_CUDA(ue::launch_source_flags(dm, k, dm.n_src, true, s));
+    // open-addressing table {stored edge id, source index}, load factor <= 1/2
+    int bits = 4;
+    while ((int64_t(1) << bits) < 2 * dm.n_src) ++bits;
+    const uint32_t size = 1u << bits;
+    std::vector<int32_t> tab(2 * (size_t)size, -1);
+    for (int64_t i = 0; i < dm.n_src; ++i) {
+        uint32_t h = ((uint32_t)m->src_k[i] * 2654435761u) >> (32 - bits);
+        while (tab[2 * h] != -1) h = (h + 1) & (size - 1);
+        tab[2 * h] = m->src_k[i];
+        tab[2 * h + 1] = (int32_t)i;
+    }
+    int2* dh = nullptr;
+    if (!alloc_into(m, dh, size, 8, s)) return fail(UE_ERR_ALLOC, "source table");
+    UE_CUDA(cudaMemcpyAsync(dh, tab.data(), 8 * (size_t)size, cudaMemcpyHostToDevice, s));
+    dm.src_hash = dh;
+    dm.src_bits = bits;
     if (m->variant == UE_VARIANT_BLOCKED) {
         // per-tile source records: (local edge, source index) for every local copy of a source edge
         std::vector<int32_t> src_of(m->hm.n_ei, -1);
@@ -297,7 +321,7 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
               alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 1, 4, s) &&
-              alloc_into(m, tb.B[1], nt, 4, s) && alloc_into(m, tb.U[1], nei + 1, 4, s);
+              alloc_into(m, tb.B[1], m->dm.n_t_pad, 4, s) && alloc_into(m, tb.U[1], m->dm.n_ei_pad, 4, s);
     if (!ok) return fail(UE_ERR_ALLOC, "tile arrays");
     tb.B[0] = m->dm.B;
     tb.U[0] = m->dm.U;
@@ -305,8 +329,8 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemcpyAsync(tb.trec, ts.trec.data(), 4 * ts.trec.size(), cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(tb.erec, ts.erec.data(), 4 * ts.erec.size(), cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemsetAsync(tb.done, 0, 4, s));
-    UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * nt, s));
-    UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * (nei + 1), s));
+    UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * m->dm.n_t_pad, s));
+    UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * m->dm.n_ei_pad, s));
     UE_CUDA(ue::launch_tb_fill(tb, m->dm, s));
     return UE_OK;
 }
@@ -403,7 +427,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     bool ok = alloc_into(m, m->d_xy, 2 * nn, 8, s) && alloc_into(m, m->d_tri_nodes, 3 * nt, 4, s) &&
               alloc_into(m, m->d_edge_nodes, 2 * nei + 2, 4, s) &&
               alloc_into(m, m->d_edge_opp, 2 * nei + 2, 4, s) &&
-              alloc_into(m, m->d_tri_code, 3 * nt, 4, s) && alloc_into(m, m->d_rl, nei + 1, 8, s) &&
+              alloc_into(m, m->d_tri_code, 3 * nt, 4, s) &&
+              alloc_into(m, m->d_rl, (nei + 4) / 4 * 4, 8, s) &&
               alloc_into(m, m->d_perm, nt, 8, s) && alloc_into(m, m->d_ecaller, nei + 1, 8, s) &&
               alloc_into(m, m->d_O, 2 * nt, 8, s) && alloc_into(m, m->d_S, nt, 8, s) &&
               alloc_into(m, m->d_elen, nei + 1, 8, s) && alloc_into(m, m->d_d, nei + 1, 8, s) &&
@@ -414,15 +439,27 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     dm.n_t = nt;
     dm.n_ei = nei;
     dm.n_nodes = nn;
-    ok = ok && alloc_into(m, dm.tri, nt, 16, s) && alloc_into(m, dm.cU, nei + 1, esz, s) &&
-         alloc_into(m, dm.U, nei + 1, esz, s) && alloc_into(m, dm.B, nt, esz, s) &&
+    dm.n_ei_pad = (nei + 4) / 4 * 4;
+    dm.n_t_pad = (nt + 3) / 4 * 4;
+    ok = ok && alloc_into(m, dm.tri, dm.n_t_pad, 16, s) && alloc_into(m, dm.cU, dm.n_ei_pad, esz, s) &&
+         alloc_into(m, dm.U, dm.n_ei_pad, esz, s) && alloc_into(m, dm.B, dm.n_t_pad, esz, s) &&
          alloc_into(m, dm.step, 1, 8, s);
-    if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, nt, 8, s);
+    if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, dm.n_t_pad, 8, s);
+    {
+        int g = 64;
+        if (m->graph_chunk > g) g = m->graph_chunk;
+        if (m->variant == UE_VARIANT_BLOCKED && tb_chunk_launches(m) * m->block_depth > g)
+            g = tb_chunk_launches(m) * m->block_depth;
+        dm.gtab_size = g;
+        ok = ok && alloc_into(m, dm.gtab, g, 8, s);
+    }
     if (!ok) {
         dev_free_all(m, s);
         return fail(UE_ERR_ALLOC, "device allocation failed");
     }
     dm.rl = m->d_rl;
+    UE_CUDA(cudaMemsetAsync(m->d_rl, 0, 8 * dm.n_ei_pad, s));
+    UE_CUDA(cudaMemsetAsync(dm.cU, 0, esz * dm.n_ei_pad, s));
     UE_CUDA(cudaMemcpyAsync(m->d_xy, h.xy.data(), 16 * nn, cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(m->d_tri_nodes, h.tri_nodes.data(), 12 * nt, cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
@@ -472,8 +509,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     }
     dm.dt = m->dt;
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, m->dt, s));
-    UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * (nei + 1), s));
-    UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * nt, s));
+    UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * dm.n_ei_pad, s));
+    UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
     if (m->variant == UE_VARIANT_BLOCKED) {
         int trc = upload_tiles(m, s);
@@ -532,7 +569,6 @@ int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, 
     m->dm.w0 = w0;
     m->dm.t0 = t0;
     m->dm.tau = tau;
-    m->dm.n_src = 0;
     m->version++;
     return bake_source(m, nullptr);
 }
@@ -566,15 +602,23 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             while (left >= chunk) {
                 UE_CUDA(cudaGraphLaunch(m->gexec_tb[m->cur], s));
                 left -= chunk;
-                launched += tb_chunk_launches(m);
+                launched += tb_chunk_launches(m) + (m->dm.n_src > 0 ? 1 : 0);
             }
         }
         while (left > 0) {
-            const int kk = (int)(left < k ? left : k);
-            UE_CUDA(ue::launch_tb(m->tb, m->dm, kk, m->cur, s));
-            set_current(m, m->cur ^ 1);
-            left -= kk;
-            ++launched;
+            // a batch of launches sharing one g table
+            const int64_t batch = left < chunk ? left : chunk;
+            UE_CUDA(ue::launch_gtab(m->dm, (int)batch, s));
+            if (m->dm.n_src > 0) ++launched;
+            int64_t done = 0;
+            while (done < batch) {
+                const int kk = (int)(batch - done < k ? batch - done : k);
+                UE_CUDA(ue::launch_tb(m->tb, m->dm, kk, m->cur, (int)done, s));
+                set_current(m, m->cur ^ 1);
+                done += kk;
+                ++launched;
+            }
+            left -= batch;
         }
         m->steps_done += n;
         m->launches += launched;
@@ -588,9 +632,16 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             left -= m->graph_chunk;
         }
     }
-    for (; left > 0; --left) UE_CUDA(ue::launch_step_plain(m->dm, s));
+    int64_t launched = 0;
+    if (m->graph_chunk > 0 && n >= m->graph_chunk) launched += plain_launches(m, n - left, m->graph_chunk);
+    while (left > 0) {
+        const int batch = (int)(left < m->dm.gtab_size ? left : m->dm.gtab_size);
+        UE_CUDA(ue::launch_steps_plain(m->dm, batch, s));
+        launched += plain_launches(m, batch, batch);
+        left -= batch;
+    }
     m->steps_done += n;
-    m->launches += n * kernels_per_step(m);
+    m->launches += launched;
     return UE_OK;
 }
 
@@ -667,49 +718,9 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 1 || n > 4096 || !ms) return fail(UE_ERR_ARG, "n_steps must be in 1..4096 and ms non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    if (m->variant == UE_VARIANT_BLOCKED) {
-        std::vector<cudaEvent_t> ev(n + 1, nullptr);
-        int rc = UE_OK;
-        for (auto& e : ev)
-            if (cudaEventCreate(&e) != cudaSuccess) {
-                rc = fail(UE_ERR_CUDA, "cudaEventCreate");
-                break;
-            }
-        for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
-            cudaEventRecord(ev[i], s);
-            cudaError_t e = ue::launch_tb(m->tb, m->dm, m->block_depth, m->cur, s);
-            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
-            else set_current(m, m->cur ^ 1);
-        }
-        if (rc == UE_OK) cudaEventRecord(ev[n], s);
-        double acc = 0;
-        if (rc == UE_OK) {
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile sync: ") + cudaGetErrorString(e));
-            for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
-                float t = 0;
-                cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
-                acc += t;
-            }
-        }
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
-        if (rc != UE_OK) return rc;
-        ms[0] = acc / (double)n;
-        ms[1] = ms[2] = 0;
-        m->steps_done += n * m->block_depth;
-        m->launches += n;
-        if (bytes) {
-            const HostMesh& h = m->hm;
-            const double pl = m->dm.plasma ? 1.0 : 0.0;
-            bytes[0] = (double)m->block_depth *
-                       ((20.0 + 12.0 * pl) * (double)h.n_ei + 24.0 * (double)h.n_tris);
-            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec +
-                       4.0 * (double)h.n_tris + (4.0 + 4.0 * pl) * (double)h.n_ei;
-            bytes[2] = 0;
-        }
-        return UE_OK;
-    }
+    const bool blocked = m->variant == UE_VARIANT_BLOCKED;
+    // events: plain step i = [gtab | E half-step | B half-step] at 4i..4i+3;
+    // blocked launch i = [g table (untimed) ... | k_tb] at 4i+1..4i+2
     std::vector<cudaEvent_t> ev(4 * n, nullptr);
     int rc = UE_OK;
     for (auto& e : ev)
@@ -718,36 +729,56 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
             break;
         }
     for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
-        for (int p = 0; p < 3 && rc == UE_OK; ++p) {
-            cudaEventRecord(ev[4 * i + p], s);
-            cudaError_t e = ue::launch_step_part(m->dm, p, s);
-            if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
+        cudaError_t e = cudaEventRecord(ev[4 * i], s);
+        if (e == cudaSuccess) e = ue::launch_gtab(m->dm, blocked ? m->block_depth : 1, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 1], s);
+        if (blocked) {
+            if (e == cudaSuccess) e = ue::launch_tb(m->tb, m->dm, m->block_depth, m->cur, 0, s);
+            if (e == cudaSuccess) set_current(m, m->cur ^ 1);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 2], s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 3], s);
+        } else {
+            if (e == cudaSuccess) e = ue::launch_step_part(m->dm, 0, 0, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 2], s);
+            if (e == cudaSuccess) e = ue::launch_step_part(m->dm, 1, 0, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 3], s);
         }
-        cudaEventRecord(ev[4 * i + 3], s);
+        if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
     }
     double acc[3] = {0, 0, 0};
     if (rc == UE_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(UE_ERR_CUDA, std::string("profile sync: ") + cudaGetErrorString(e));
-        for (int64_t i = 0; i < n && rc == UE_OK; ++i)
-            for (int p = 0; p < 3; ++p) {
-                float t = 0;
-                cudaEventElapsedTime(&t, ev[4 * i + p], ev[4 * i + p + 1]);
-                acc[p] += t;
-            }
+        for (int64_t i = 0; i < n && rc == UE_OK; ++i) {
+            float t[3] = {0, 0, 0};
+            for (int p = 0; p < 3; ++p) cudaEventElapsedTime(&t[p], ev[4 * i + p], ev[4 * i + p + 1]);
+            acc[0] += t[1];   // E half-step, or the blocked kernel
+            acc[1] += t[0];   // g table
+            acc[2] += t[2];   // B half-step
+        }
     }
     for (auto& e : ev)
         if (e) cudaEventDestroy(e);
     if (rc != UE_OK) return rc;
     for (int p = 0; p < 3; ++p) ms[p] = acc[p] / (double)n;
-    m->steps_done += n;
-    m->launches += n * kernels_per_step(m);
+    const int64_t per = blocked ? m->block_depth : 1;
+    m->steps_done += n * per;
+    m->launches += blocked ? n * (1 + (m->dm.n_src > 0 ? 1 : 0)) : plain_launches(m, n, 1);
     if (bytes) {
         const double f = m->precision == UE_PREC_FP64 ? 2.0 : 1.0;
         const HostMesh& h = m->hm;
-        bytes[0] = (8.0 + f * 12.0 + (m->dm.plasma ? f * 12.0 : 0.0)) * (double)h.n_ei;
-        bytes[1] = (double)m->dm.n_src * (4.0 + f * 12.0);
-        bytes[2] = (16.0 + f * 8.0 + (m->precision == UE_PREC_FP64 ? 8.0 : 0.0)) * (double)h.n_tris;
+        const double pl = m->dm.plasma ? 1.0 : 0.0;
+        if (blocked) {
+            ms[2] = 0;
+            bytes[0] = (double)per * ((20.0 + 12.0 * pl) * (double)h.n_ei + 24.0 * (double)h.n_tris);
+            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec +
+                       4.0 * (double)h.n_tris + (4.0 + 4.0 * pl) * (double)h.n_ei;
+            bytes[2] = 0;
+        } else {
+            bytes[0] = (8.0 + f * 12.0 + pl * f * 12.0) * (double)h.n_ei;
+            bytes[1] = 8.0 * (m->dm.n_src > 0 ? 1.0 : 0.0);
+            bytes[2] = (16.0 + f * 8.0 + (m->precision == UE_PREC_FP64 ? 8.0 : 0.0)) * (double)h.n_tris;
+        }
     }
     return UE_OK;
 }
