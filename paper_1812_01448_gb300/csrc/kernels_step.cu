@@ -75,13 +75,15 @@ struct SrcArgs {
 
 template <typename T>
 __device__ __forceinline__ T source_term(const SrcArgs<T>& src, int k, T u) {
+    const unsigned size = 1u << src.bits;
     unsigned h = ((unsigned)k * 2654435761u) >> (32 - src.bits);
     int2 e = __ldg(src.hash + h);
-    while (e.x != k) {
-        h = (h + 1) & ((1u << src.bits) - 1);
+    // linear probing; a flagged edge is always in the table, the bound only guards the loop
+    for (unsigned p = 1; e.x != k && p < size; ++p) {
+        h = (h + 1) & (size - 1);
         e = __ldg(src.hash + h);
     }
-    return rn_fma(__ldg(src.c + e.y), (T)__ldg(src.g + src.s), u);
+    return e.x == k ? rn_fma(__ldg(src.c + e.y), (T)__ldg(src.g + src.s), u) : u;
 }
 
 template <typename T, bool PLASMA, bool SRC>
