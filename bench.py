@@ -182,7 +182,8 @@ def run_native(args):
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
                 tile_tris=args.tile_tris)
     vopt = dict(variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
-                block_depth=args.block_depth, graph_chunk=args.graph_chunk)
+                block_depth=args.block_depth, graph_chunk=args.graph_chunk,
+                tb_threads=args.tb_threads)
     if args.quick_setup:
         # profiling runs: a fixed dt instead of the 200-iteration power iteration, so that few
         # kernel launches precede the captured ones
@@ -282,7 +283,8 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_tris": n_t, "n_interior_edges": n_ei,
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
-                       "variant": (f"blocked k={args.block_depth} tiles<={args.tile_tris}" if blocked
+                       "variant": (f"blocked k={args.block_depth} tiles<={args.tile_tris} "
+                                f"threads={args.tb_threads or 512}" if blocked
                                    else "plain") + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
@@ -293,6 +295,83 @@ def run_native(args):
     m.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _time_steps(fn, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def run_batch(args):
+    """Many independent meshes: one launch per half-step for all of them (batched, inside CUDA
+    graphs) against the plain form (each mesh stepped alone: its own E and B launches, no
+    graph).  Both with every mesh's own dt and line source."""
+    import multiprocessing as mp
+
+    import meshgen
+    specs = meshgen.batch_specs(args.batch_meshes)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        meshes = pool.map(meshgen.batch_mesh, specs, chunksize=2)
+    t_gen = time.perf_counter() - t0
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    stream = torch.cuda.current_stream()
+    singles = []
+    for sp, ms in zip(specs, meshes):
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=args.tile_tris)
+        m.geometry_build(stream=stream, graph_chunk=-1)
+        ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+        m.set_source(ids, amp, sp["omega0"], 0.1, 0.05)
+        singles.append(m)
+    n_t = sum(m.n_tris for m in singles)
+    # plain form: every mesh alone, E and B launches per mesh per step (plus its g-table launch)
+    for m in singles:
+        m.step_n(2, stream)
+    sp_steps = max(3, args.steps // 50)
+
+    def plain():
+        for _ in range(sp_steps):
+            for m in singles:
+                m.step_n(1, stream)
+    t_plain = _time_steps(plain, stream)
+    rate_plain = n_t * sp_steps / t_plain
+    res = {"plain_per_mesh": rate_plain}
+    for variant in ("plain", "blocked"):
+        # rebuild every mesh for this variant (sources and dt carry over)
+        for m in singles:
+            m.geometry_build(stream=stream, graph_chunk=args.graph_chunk,
+                             variant=ue.UE_VARIANT_BLOCKED if variant == "blocked" else ue.UE_VARIANT_PLAIN,
+                             block_depth=args.block_depth, tb_threads=args.tb_threads)
+        bt = ue.batch_create(singles, stream)
+        bt.step_n(args.warmup, stream)
+        t = _time_steps(lambda: bt.step_n(args.steps, stream), stream)
+        res[f"batched_{variant}"] = n_t * args.steps / t
+        bt.close()
+    line = {
+        "metric": "cell-updates/s (batch of independent meshes)", "unit": UNIT,
+        "value": res["batched_blocked"], "n_meshes": len(singles), "n_tris_total": n_t,
+        "steps": args.steps, "plain_steps": sp_steps, "results": res,
+        "ratio_batched_blocked_vs_plain": res["batched_blocked"] / rate_plain,
+        "ratio_batched_plain_vs_plain": res["batched_plain"] / rate_plain,
+        "config": {"workload": f"{len(singles)} meshes, log-uniform 5k-200k triangles, random "
+                               "scatterer each, own dt and source frequency",
+                   "tile_tris": args.tile_tris, "block_depth": args.block_depth,
+                   "mesh_generation_s": t_gen},
+    }
+    print(json.dumps(line), flush=True)
+    for m in singles:
+        m.close()
 
 
 def main(argv=None):
@@ -307,6 +386,9 @@ def main(argv=None):
     ap.add_argument("--tile-tris", type=int, default=2048)
     ap.add_argument("--block-depth", type=int, default=4)
     ap.add_argument("--graph-chunk", type=int, default=32)
+    ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
+    ap.add_argument("--workload", choices=["scatterer", "batch"], default="scatterer")
+    ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--quick-setup", action="store_true",
                     help="fixed dt instead of power iteration (for profiler runs)")
     args = ap.parse_args(argv)
@@ -314,6 +396,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_native(args)
 

@@ -77,7 +77,7 @@ typedef struct ue_options {
     int32_t graph_chunk;   /* steps per captured CUDA graph launch; 0 = default, <0 = none   */
     int32_t tile_tris;     /* UE_REORDER_KD: maximum triangles per tile (ue_mesh_load)       */
     int32_t block_depth;   /* UE_VARIANT_BLOCKED: steps per launch, 1..15                    */
-    int32_t reserved0;
+    int32_t tb_threads;    /* UE_VARIANT_BLOCKED: CTA size, 0 = 512 (default) or 1024        */
     double dt;             /* UE_DT_GIVEN: the time step                                     */
     double safety;         /* UE_DT_POWER: dt = safety * 2 / rho (default 0.5)               */
 } ue_options;
@@ -109,6 +109,18 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
  * (eq. 4) rounded to the field precision, and zeroed fields.  Synchronous.
  * Errors: UE_ERR_DUAL if some interior edge has d <= 1e-12*|e|; UE_ERR_CUDA; UE_ERR_ALLOC. */
 int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream);
+
+/* Batch of independent meshes advanced together: one E and one B half-step launch per step for
+ * all of them (or one blocked launch per block_depth steps over all their tiles), inside the
+ * same CUDA graphs.  meshes[0..n): built meshes (ue_geometry_build done) with the same
+ * precision and variant (blocked: same block_depth and tb_threads) and no plasma medium.  The
+ * batch copies their device tables, coefficients, current fields and sources; the meshes stay
+ * valid and independent.  Each mesh keeps its own dt and source (its coefficients and source
+ * group); the batch's step counter starts at 0.  Caller numbering of the batch is the
+ * mesh-major concatenation of the meshes' nodes, triangles and edges.  After k batched steps
+ * the fields of every mesh are bit-identical to k steps of that mesh alone.  Free the batch
+ * with ue_mesh_free.  ue_set_source and ue_set_plasma are rejected on a batch. */
+int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** out_batch);
 
 /* dt, rho(M) and how rho was obtained (UE_RHO_*). */
 int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* rho_source);

@@ -24,6 +24,8 @@ from .configs import (  # noqa: F401
     scatterer_mesh,
     plasma_square_mesh,
     batch_meshes,
+    batch_specs,
+    batch_mesh,
     source_line_amplitudes,
     plasma_density_nodes,
     te_mode_b,

@@ -79,36 +79,49 @@ def source_line_amplitudes(xy: np.ndarray, tris: np.ndarray, x_s: float, h: floa
     return ids.astype(np.int32), a.astype(np.float64)
 
 
-def batch_meshes(n_meshes: int = 512, seed: int = 1004, n_min: int = 5_000, n_max: int = 200_000):
-    """Independent meshes: log-uniform sizes, one random scatterer each, jitter U[0, 0.3].
-
-    Yields dicts with the mesh and its own source frequency omega0 = 2 pi U[10, 30].
-    """
+def batch_specs(n_meshes: int = 512, seed: int = 1004, n_min: int = 5_000, n_max: int = 200_000):
+    """Parameters of a batch of independent meshes: log-uniform sizes, one random scatterer
+    each (triangle, ellipse or rotated rectangle of size U[0.1, 0.3]), jitter U[0, 0.3] h, and
+    a source frequency omega0 = 2 pi U[10, 30].  All draws come from one seeded stream."""
     rng = np.random.default_rng(seed)
+    specs = []
     for k in range(n_meshes):
         n_t = float(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))
         kind = int(rng.integers(3))
         size = float(rng.uniform(0.1, 0.3))
         ang = float(rng.uniform(0, 2 * math.pi))
         c = (0.5 + float(rng.uniform(-0.1, 0.1)), 0.5 + float(rng.uniform(-0.1, 0.1)))
-        if kind == 0:
-            hole = polygon_triangle(c, size, ang)
-            area = math.sqrt(3) / 4 * size ** 2
-        elif kind == 1:
-            ra, rb = size / 2, size / 2 * float(rng.uniform(0.5, 1.0))
-            hole = polygon_ellipse(c, ra, rb, ang, n_vertices=48)
-            area = math.pi * ra * rb
-        else:
-            w, hh = size, size * float(rng.uniform(0.4, 1.0))
-            hole = polygon_rectangle(c, w, hh, ang)
-            area = w * hh
-        h = uniform_spacing_for(n_t, 1.0 - area)
+        aspect = float(rng.uniform(0.5, 1.0)) if kind == 1 else float(rng.uniform(0.4, 1.0))
         jit = float(rng.uniform(0.0, 0.3))
         omega0 = 2 * math.pi * float(rng.uniform(10, 30))
-        mesh = graded_square(h, h, grade=0.0, holes=[hole], jitter=jit,
-                             seed=int(rng.integers(1 << 31)))
-        yield dict(mesh=mesh, omega0=omega0, kind=("triangle", "ellipse", "rectangle")[kind],
-                   size=size, jitter=jit)
+        specs.append(dict(index=k, n_tris=n_t, kind=("triangle", "ellipse", "rectangle")[kind],
+                          size=size, angle=ang, center=c, aspect=aspect, jitter=jit,
+                          omega0=omega0, seed=int(rng.integers(1 << 31))))
+    return specs
+
+
+def batch_mesh(spec) -> MeshArrays:
+    """Build one mesh of ``batch_specs``."""
+    size, ang, c = spec["size"], spec["angle"], spec["center"]
+    if spec["kind"] == "triangle":
+        hole = polygon_triangle(c, size, ang)
+        area = math.sqrt(3) / 4 * size ** 2
+    elif spec["kind"] == "ellipse":
+        ra, rb = size / 2, size / 2 * spec["aspect"]
+        hole = polygon_ellipse(c, ra, rb, ang, n_vertices=48)
+        area = math.pi * ra * rb
+    else:
+        w, hh = size, size * spec["aspect"]
+        hole = polygon_rectangle(c, w, hh, ang)
+        area = w * hh
+    h = uniform_spacing_for(spec["n_tris"], 1.0 - area)
+    return graded_square(h, h, grade=0.0, holes=[hole], jitter=spec["jitter"], seed=spec["seed"])
+
+
+def batch_meshes(n_meshes: int = 512, seed: int = 1004, n_min: int = 5_000, n_max: int = 200_000):
+    """Yield dict(mesh=..., **spec) for each mesh of the batch (sequentially)."""
+    for spec in batch_specs(n_meshes, seed, n_min, n_max):
+        yield dict(mesh=batch_mesh(spec), **spec)
 
 
 def cached(name: str, make, cache_dir: str | None = None) -> MeshArrays:

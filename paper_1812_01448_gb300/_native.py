@@ -23,7 +23,7 @@ class Options(C.Structure):
     _fields_ = [("reorder", C.c_int32), ("precision", C.c_int32), ("dt_mode", C.c_int32),
                 ("power_iters", C.c_int32), ("power_seed", C.c_uint32), ("variant", C.c_int32),
                 ("graph_chunk", C.c_int32), ("tile_tris", C.c_int32), ("block_depth", C.c_int32),
-                ("reserved0", C.c_int32), ("dt", C.c_double),
+                ("tb_threads", C.c_int32), ("dt", C.c_double),
                 ("safety", C.c_double)]
 
 
@@ -45,6 +45,7 @@ SIGNATURES = [
     ("ue_options_default", None, [C.POINTER(Options)]),
     ("ue_mesh_load", C.c_int, [PD, I64, PI32, I64, C.POINTER(Options), ALLOC_FN, FREE_FN, P, C.POINTER(P)]),
     ("ue_geometry_build", C.c_int, [P, C.POINTER(Options), P]),
+    ("ue_batch_create", C.c_int, [C.POINTER(P), C.c_int32, P, C.POINTER(P)]),
     ("ue_get_dt", C.c_int, [P, PD, PD, PI32]),
     ("ue_set_plasma", C.c_int, [P, PD, C.c_double]),
     ("ue_set_source", C.c_int, [P, PI32, PD, I64, C.c_double, C.c_double, C.c_double]),

@@ -85,6 +85,19 @@ class Mesh:
         self.n_nodes, self.n_tris, self.n_edges, self.n_ei = nn.value, nt.value, ne.value, nei.value
         self.precision = N.UE_PREC_FP32
 
+    @classmethod
+    def _wrap(cls, handle, keep=()):
+        obj = cls.__new__(cls)
+        obj._h = handle
+        obj._keep = keep
+        obj._allocator = None
+        nn, nt, ne, nei = (C.c_int64() for _ in range(4))
+        N.check(N.lib().ue_get_sizes(handle, C.byref(nn), C.byref(nt), C.byref(ne), C.byref(nei)),
+                "ue_get_sizes")
+        obj.n_nodes, obj.n_tris, obj.n_edges, obj.n_ei = nn.value, nt.value, ne.value, nei.value
+        obj.precision = N.UE_PREC_FP32
+        return obj
+
     def close(self):
         if getattr(self, "_h", None):
             N.lib().ue_mesh_free(self._h)
@@ -184,3 +197,17 @@ class Mesh:
         s = N.Stats()
         N.check(N.lib().ue_stats(self._h, C.byref(s)), "ue_stats")
         return {k: getattr(s, k) for k, _ in N.Stats._fields_}
+
+
+def batch_create(meshes, stream=None) -> Mesh:
+    """ue_batch_create: one Mesh object advancing all the given built meshes together.
+
+    Its caller numbering is the mesh-major concatenation of the meshes' nodes, triangles and
+    edges; each mesh keeps its own dt and source."""
+    arr = (C.c_void_p * len(meshes))(*[m._h.value if isinstance(m._h, C.c_void_p) else m._h
+                                      for m in meshes])
+    h = C.c_void_p()
+    N.check(N.lib().ue_batch_create(arr, len(meshes), _stream(stream), C.byref(h)), "ue_batch_create")
+    b = Mesh._wrap(h, keep=tuple(meshes))
+    b.precision = meshes[0].precision
+    return b

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "../../include/ue.h"
 
@@ -47,12 +48,14 @@ struct DevMesh {
     double pa = 1.0;              // (1 - nu dt/2)/(1 + nu dt/2)
     int64_t n_src = 0;
     int32_t* src_k = nullptr;     // [n_src] stored edge ids
+    int32_t* src_grp = nullptr;   // [n_src] source group (one per mesh of a batch)
     void* src_c = nullptr;        // [n_src] dt*|e|*amp
     int2* src_hash = nullptr;     // open-addressing table {edge id, source index}
     int src_bits = 0;             // table size 2^src_bits
-    double* gtab = nullptr;       // g(t) for the steps of the current chunk
+    int n_grp = 0;
+    double* grp_par = nullptr;    // [4 * n_grp] per group: dt, omega0, t0, tau
+    double* gtab = nullptr;       // [n_grp * gtab_size]: g(t) per group for the current chunk
     int gtab_size = 0;
-    double w0 = 0, t0 = 0, tau = 1;
     long long* step = nullptr;    // device step counter (source time)
     double dt = 0;
 };
@@ -67,6 +70,7 @@ struct TBDev {
     int64_t n_erec = 0;
     int2* tsrc = nullptr;         // per-tile source records {local edge, source index}
     int max_tri_loc = 0, max_edge_loc = 0;
+    int threads = 512;            // CTA size of the blocked kernel (512 or 1024)
     void* B[2] = {nullptr, nullptr};
     void* U[2] = {nullptr, nullptr};
     void* J[2] = {nullptr, nullptr};
@@ -74,7 +78,7 @@ struct TBDev {
 };
 
 int tb_threads();
-bool tb_fits(int max_tri_loc, int max_edge_loc);
+bool tb_fits(int max_tri_loc, int max_edge_loc, int threads);
 cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
 // k steps of the blocked kernel reading buffer `cur`, writing buffer cur ^ 1; the source uses
 // g-table entries gbase .. gbase + k - 1.
@@ -112,8 +116,18 @@ cudaError_t launch_fields_out(const DevMesh& m, double* E_caller, double* B_call
                               const int64_t* perm_tri, const double* elen, cudaStream_t s);
 cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const int32_t* edge_nodes,
                                 double nu, double dt, cudaStream_t s);
+// src_c[i] = dt_grp * |e| * amp[i], dt of the source's group.
 cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen,
-                                double dt, cudaStream_t s);
+                                cudaStream_t s);
+// Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
+size_t energy_parts(int64_t n_ei, int64_t n_t);
+cudaError_t launch_energy(const DevMesh& m, const double* elen, const double* d, const double* S,
+                          double* part, double* wd, cudaStream_t s);
+// Batch assembly: dst[i] = |src[i]| (coefficients without source flags), and triangle
+// records re-pointed at the batch's edge numbering.
+cudaError_t launch_copy_abs(void* dst, const void* src, int64_t n, bool f64, cudaStream_t s);
+cudaError_t launch_tri_offset(int4* dst, const int4* src, int64_t n, int64_t ei_off, int64_t nei_m,
+                              int64_t nei_all, cudaStream_t s);
 // Set (on = true) or clear the source flag (sign bit of cU) of the listed stored edges.
 cudaError_t launch_source_flags(const DevMesh& m, const int32_t* k, int64_t n, bool on,
                                 cudaStream_t s);

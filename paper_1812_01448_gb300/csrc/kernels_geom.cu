@@ -249,11 +249,12 @@ __global__ void k_plasma_coeff(const double* __restrict__ nn, const int32_t* __r
 }
 
 template <typename T>
-__global__ void k_source_coeff(const int32_t* __restrict__ sk, const double* __restrict__ amp,
-                               const double* __restrict__ elen, T* __restrict__ sc, double dt,
-                               int64_t n) {
+__global__ void k_source_coeff(const int32_t* __restrict__ sk, const int32_t* __restrict__ grp,
+                               const double* __restrict__ par, const double* __restrict__ amp,
+                               const double* __restrict__ elen, T* __restrict__ sc, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double dt = par[4 * grp[i]];
     sc[i] = (T)(dt * elen[sk[i]] * amp[i]);
 }
 
@@ -310,6 +311,120 @@ cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, 
     k_coeff_tri<<<blocks_for(m.n_t_pad), kThreads, 0, s>>>(
         tri_code, S, m.tri, m.precision == UE_PREC_FP64 ? (double*)m.cB : nullptr, dt, m.n_t,
         m.n_t_pad, (int)(2 * m.n_ei));
+    return cudaGetLastError();
+}
+
+namespace {
+
+template <typename T>
+__global__ void k_copy_abs(T* __restrict__ dst, const T* __restrict__ src, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = fabs(src[i]);
+}
+
+// Triangle records of one mesh placed in a batch: edge codes shifted by the mesh's first
+// stored edge; the mesh's zero slot (code 2*nei_m) becomes the batch's zero slot.
+__global__ void k_tri_offset(int4* __restrict__ dst, const int4* __restrict__ src, int64_t n,
+                             int ei_off, int nei_m, int nei_all) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int4 r = src[j];
+    r.x = (r.x >> 1) == nei_m ? 2 * nei_all : r.x + 2 * ei_off;
+    r.y = (r.y >> 1) == nei_m ? 2 * nei_all : r.y + 2 * ei_off;
+    r.z = (r.z >> 1) == nei_m ? 2 * nei_all : r.z + 2 * ei_off;
+    dst[j] = r;
+}
+
+}  // namespace
+
+namespace {
+
+// Energy of eq. 8 with the eq. 7 weights, in circulation variables:
+//   W = sum_i (d_i / |e_i|) U_i^2 + sum_j S_j B_j^2   (U = |e| E).
+// Blocks [0, nbe) cover edges, [nbe, nbe + nbt) triangles; fixed-order partial sums.
+template <typename T>
+__global__ void k_energy_parts(const T* __restrict__ U, const T* __restrict__ B,
+                               const double* __restrict__ elen, const double* __restrict__ d,
+                               const double* __restrict__ S, int64_t n_ei, int64_t n_t, int nbe,
+                               double* __restrict__ part) {
+    __shared__ double a[kThreads];
+    double x = 0.0;
+    if ((int)blockIdx.x < nbe) {
+        const int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        if (k < n_ei) {
+            const double u = (double)U[k];
+            x = d[k] / elen[k] * u * u;
+        }
+    } else {
+        const int64_t j = (int64_t)(blockIdx.x - nbe) * kThreads + threadIdx.x;
+        if (j < n_t) {
+            const double b = (double)B[j];
+            x = S[j] * b * b;
+        }
+    }
+    a[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) a[threadIdx.x] += a[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = a[0];
+}
+
+// wd = {W at the previous check, W now, growth factor, flag}: flag 1 = non-finite energy,
+// 2 = energy grew by more than the factor since the previous check.  A set flag stays set.
+__global__ void k_energy_check(const double* __restrict__ part, int nb, double* __restrict__ wd) {
+    __shared__ double a[kThreads];
+    double x = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kThreads) x += part[i];
+    a[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) a[threadIdx.x] += a[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double W = a[0];
+        wd[1] = W;
+        if (wd[3] == 0.0) {
+            if (!isfinite(W)) wd[3] = 1.0;
+            else if (wd[2] > 0.0 && wd[0] > 0.0 && W > wd[2] * wd[0]) wd[3] = 2.0;
+        }
+        wd[0] = W;
+    }
+}
+
+}  // namespace
+
+size_t energy_parts(int64_t n_ei, int64_t n_t) {
+    return (size_t)((n_ei + kThreads - 1) / kThreads + (n_t + kThreads - 1) / kThreads);
+}
+
+cudaError_t launch_energy(const DevMesh& m, const double* elen, const double* d, const double* S,
+                          double* part, double* wd, cudaStream_t s) {
+    const int nbe = (int)((m.n_ei + kThreads - 1) / kThreads);
+    const int nbt = (int)((m.n_t + kThreads - 1) / kThreads);
+    if (m.precision == UE_PREC_FP64)
+        k_energy_parts<double><<<nbe + nbt, kThreads, 0, s>>>((const double*)m.U, (const double*)m.B,
+                                                              elen, d, S, m.n_ei, m.n_t, nbe, part);
+    else
+        k_energy_parts<float><<<nbe + nbt, kThreads, 0, s>>>((const float*)m.U, (const float*)m.B,
+                                                             elen, d, S, m.n_ei, m.n_t, nbe, part);
+    k_energy_check<<<1, kThreads, 0, s>>>(part, nbe + nbt, wd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_abs(void* dst, const void* src, int64_t n, bool f64, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (f64) k_copy_abs<double><<<blocks_for(n), kThreads, 0, s>>>((double*)dst, (const double*)src, n);
+    else k_copy_abs<float><<<blocks_for(n), kThreads, 0, s>>>((float*)dst, (const float*)src, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_offset(int4* dst, const int4* src, int64_t n, int64_t ei_off, int64_t nei_m,
+                              int64_t nei_all, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_tri_offset<<<blocks_for(n), kThreads, 0, s>>>(dst, src, n, (int)ei_off, (int)nei_m, (int)nei_all);
     return cudaGetLastError();
 }
 
@@ -406,13 +521,13 @@ cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen, double dt,
+cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen,
                                 cudaStream_t s) {
     if (m.n_src == 0) return cudaSuccess;
     if (m.precision == UE_PREC_FP64)
-        k_source_coeff<double><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, amp, elen, (double*)m.src_c, dt, m.n_src);
+        k_source_coeff<double><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, m.src_grp, m.grp_par, amp, elen, (double*)m.src_c, m.n_src);
     else
-        k_source_coeff<float><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, amp, elen, (float*)m.src_c, dt, m.n_src);
+        k_source_coeff<float><<<blocks_for(m.n_src), kThreads, 0, s>>>(m.src_k, m.src_grp, m.grp_par, amp, elen, (float*)m.src_c, m.n_src);
     return cudaGetLastError();
 }
 

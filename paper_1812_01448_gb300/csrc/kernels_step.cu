@@ -69,7 +69,9 @@ struct SrcArgs {
     const int2* hash;       // {edge id, source index}, empty slots have edge id -1
     unsigned bits;          // table size 2^bits
     const T* c;             // dt |e| a per source index
-    const double* g;        // g(t) per step of the current chunk
+    const int32_t* grp;     // group of each source index
+    const double* g;        // g(t) per group and step of the current chunk
+    int stride;             // table entries per group
     int s;                  // this step's index in the chunk table
 };
 
@@ -83,7 +85,9 @@ __device__ __forceinline__ T source_term(const SrcArgs<T>& src, int k, T u) {
         h = (h + 1) & (size - 1);
         e = __ldg(src.hash + h);
     }
-    return e.x == k ? rn_fma(__ldg(src.c + e.y), (T)__ldg(src.g + src.s), u) : u;
+    if (e.x != k) return u;
+    const double g = __ldg(src.g + (size_t)__ldg(src.grp + e.y) * src.stride + src.s);
+    return rn_fma(__ldg(src.c + e.y), (T)g, u);
 }
 
 template <typename T, bool PLASMA, bool SRC>
@@ -152,11 +156,14 @@ k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
     st4(B + 4 * v, bo);
 }
 
-// g(t_n) for the next `count` steps, n = *step + i.
+// g(t_n) of every source group for the next `count` steps, n = *step + i.
 __global__ void k_gtab(double* __restrict__ g, const long long* __restrict__ step, int count,
-                       double dt, double w0, double t0, double tau) {
+                       int stride, const double* __restrict__ par, int n_grp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) g[i] = source_g(*step + i, dt, w0, t0, tau);
+    const int grp = blockIdx.y;
+    if (i < count && grp < n_grp)
+        g[(size_t)grp * stride + i] = source_g(*step + i, par[4 * grp], par[4 * grp + 1],
+                                               par[4 * grp + 2], par[4 * grp + 3]);
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -164,7 +171,8 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / k
 template <typename T, bool PLASMA>
 void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
     const int64_t n_vec = m.n_ei_pad / 4;
-    SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.gtab, s_index};
+    SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.src_grp, m.gtab,
+                   m.gtab_size, s_index};
     const T pa = PLASMA ? (T)m.pa : (T)0, mdt = PLASMA ? (T)(-m.dt) : (T)0;
     if (m.n_src > 0)
         k_edge_half<T, PLASMA, true><<<blocks_for(n_vec), kThreads, 0, s>>>(
@@ -187,7 +195,8 @@ void tri_half_t(const DevMesh& m, cudaStream_t s) {
 
 cudaError_t launch_gtab(const DevMesh& m, int count, cudaStream_t s) {
     if (m.n_src == 0 || count <= 0) return cudaSuccess;
-    k_gtab<<<(count + 63) / 64, 64, 0, s>>>(m.gtab, m.step, count, m.dt, m.w0, m.t0, m.tau);
+    k_gtab<<<dim3((count + 63) / 64, m.n_grp), 64, 0, s>>>(m.gtab, m.step, count, m.gtab_size,
+                                                          m.grp_par, m.n_grp);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ namespace ue {
 namespace {
 
 constexpr int kNT = 512;
+constexpr int kG = 3;   // slots whose shared-memory gathers are issued together
 
 struct TBArgs {
     const int* hdr;
@@ -30,17 +31,22 @@ struct TBArgs {
     float* Uout;
     float* Jout;
     const float* src_c;
+    const int32_t* src_grp;
     const double* gtab;
+    int gstride;
     int gbase;
     long long* step;
     unsigned* done;
     int ksteps;
     float pa, mdt;
-    double dt, w0, t0, tau;
 };
 
-template <int TS, int ES, bool PLASMA, bool SRC>
-__global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
+// NT threads; each thread owns local triangle slots tid + i*NT (i < TS) and local edge slots
+// tid + i*NT (i < ES), whose records it keeps in registers for all k steps.  In every phase a
+// thread takes its slots kG at a time: it issues the group's shared-memory gathers, then
+// computes and stores, so that a group's loads are in flight together.
+template <int NT, int TS, int ES, int MINB, bool PLASMA, bool SRC>
+__global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     extern __shared__ float sm[];
     __shared__ int h[48];
     const int tid = threadIdx.x;
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
     const int4* er = a.erec + h[7];
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
-        const int l = tid + i * kNT;
+        const int l = tid + i * NT;
         if (l < ntl) {
             const int4 r = __ldg(tr + l);
             tc01[i] = r.y;
@@ -70,7 +76,7 @@ __global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
     }
 #pragma unroll
     for (int i = 0; i < ES; ++i) {
-        const int l = tid + i * kNT;
+        const int l = tid + i * NT;
         if (l < nel) {
             const int4 r = __ldg(er + l);
             erl[i] = r.y;
@@ -93,44 +99,71 @@ __global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
         const int lim = a.ksteps - s;
         const int eend = h[32 + lim];
 #pragma unroll
-        for (int i = 0; i < ES; ++i) {
-            const int l = tid + i * kNT;
-            if (l < eend) {
-                const int rl = erl[i];
-                const float b = rn_sub(Bl[rl & 0xFFFF], Bl[(unsigned)rl >> 16]);
-                const float u = Ul[l];
-                float un = rn_fma(ecu[i], b, u);
-                if constexpr (PLASMA) {
-                    const float jn = rn_fma(a.pa, Jl[l], rn_mul(epb[i], u));
-                    Jl[l] = jn;
-                    un = rn_fma(a.mdt, jn, un);
+        for (int g0 = 0; g0 < ES; g0 += kG) {
+            float bR[kG], bL[kG], uo[kG], jo[kG];
+#pragma unroll
+            for (int q = 0; q < kG; ++q) {
+                const int i = g0 + q, l = tid + i * NT;
+                if (i < ES && l < eend) {
+                    bR[q] = Bl[erl[i] & 0xFFFF];
+                    bL[q] = Bl[(unsigned)erl[i] >> 16];
+                    uo[q] = Ul[l];
+                    if constexpr (PLASMA) jo[q] = Jl[l];
                 }
-                Ul[l] = un;
+            }
+#pragma unroll
+            for (int q = 0; q < kG; ++q) {
+                const int i = g0 + q, l = tid + i * NT;
+                if (i < ES && l < eend) {
+                    float un = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo[q]);
+                    if constexpr (PLASMA) {
+                        const float jn = rn_fma(a.pa, jo[q], rn_mul(epb[i], uo[q]));
+                        Jl[l] = jn;
+                        un = rn_fma(a.mdt, jn, un);
+                    }
+                    Ul[l] = un;
+                }
             }
         }
         if constexpr (SRC) {
             if (h[9] > 0) {
                 __syncthreads();
-                const float g = (float)__ldg(a.gtab + a.gbase + s - 1);
-                for (int i = tid; i < h[9]; i += kNT) {
+                for (int i = tid; i < h[9]; i += NT) {
                     const int2 q = __ldg(a.tsrc + h[8] + i);
-                    if (q.x < eend) Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
+                    if (q.x < eend) {
+                        const float g = (float)__ldg(a.gtab + (size_t)__ldg(a.src_grp + q.y) * a.gstride +
+                                                     a.gbase + s - 1);
+                        Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
+                    }
                 }
             }
         }
         __syncthreads();
         const int tend = h[16 + lim];
 #pragma unroll
-        for (int i = 0; i < TS; ++i) {
-            const int l = tid + i * kNT;
-            if (l < tend) {
-                const int c0 = tc01[i] & 0xFFFF, c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
-                float u0 = Ul[c0 >> 1], u1 = Ul[c1 >> 1], u2 = Ul[c2 >> 1];
-                if (c0 & 1) u0 = -u0;
-                if (c1 & 1) u1 = -u1;
-                if (c2 & 1) u2 = -u2;
-                const float sum = rn_add(rn_add(u0, u1), u2);
-                Bl[l] = rn_fma(-tcb[i], sum, Bl[l]);
+        for (int g0 = 0; g0 < TS; g0 += kG) {
+            float u0[kG], u1[kG], u2[kG], bo[kG];
+#pragma unroll
+            for (int q = 0; q < kG; ++q) {
+                const int i = g0 + q, l = tid + i * NT;
+                if (i < TS && l < tend) {
+                    const int c0 = tc01[i] & 0xFFFF, c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
+                    u0[q] = Ul[c0 >> 1];
+                    u1[q] = Ul[c1 >> 1];
+                    u2[q] = Ul[c2 >> 1];
+                    bo[q] = Bl[l];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kG; ++q) {
+                const int i = g0 + q, l = tid + i * NT;
+                if (i < TS && l < tend) {
+                    const int c0 = tc01[i], c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
+                    const float x0 = (c0 & 1) ? -u0[q] : u0[q];
+                    const float x1 = (c1 & 1) ? -u1[q] : u1[q];
+                    const float x2 = (c2 & 1) ? -u2[q] : u2[q];
+                    Bl[l] = rn_fma(-tcb[i], rn_add(rn_add(x0, x1), x2), bo[q]);
+                }
             }
         }
         __syncthreads();
@@ -138,12 +171,12 @@ __global__ void __launch_bounds__(kNT, 1) k_tb(TBArgs a) {
     const int nto = h[1], neo = h[3];
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
-        const int l = tid + i * kNT;
+        const int l = tid + i * NT;
         if (l < nto) a.Bout[h[0] + l] = Bl[l];
     }
 #pragma unroll
     for (int i = 0; i < ES; ++i) {
-        const int l = tid + i * kNT;
+        const int l = tid + i * NT;
         if (l < neo) {
             a.Uout[h[2] + l] = Ul[l];
             if constexpr (PLASMA) a.Jout[h[2] + l] = Jl[l];
@@ -174,29 +207,32 @@ __global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restr
     }
 }
 
-template <int TS, int ES, bool PLASMA, bool SRC>
+template <int NT, int TS, int ES, int MINB, bool PLASMA, bool SRC>
 cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t s) {
-    auto kern = k_tb<TS, ES, PLASMA, SRC>;
+    auto kern = k_tb<NT, TS, ES, MINB, PLASMA, SRC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<n_tiles, kNT, smem, s>>>(a);
+    kern<<<n_tiles, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TS, int ES>
+template <int NT, int TS, int ES, int MINB>
 cudaError_t launch_tb_ps(const TBArgs& a, bool plasma, bool src, int n_tiles, size_t smem,
                          cudaStream_t s) {
-    if (plasma) return src ? launch_tb_t<TS, ES, true, true>(a, n_tiles, smem, s)
-                           : launch_tb_t<TS, ES, true, false>(a, n_tiles, smem, s);
-    return src ? launch_tb_t<TS, ES, false, true>(a, n_tiles, smem, s)
-               : launch_tb_t<TS, ES, false, false>(a, n_tiles, smem, s);
+    if (plasma) return src ? launch_tb_t<NT, TS, ES, MINB, true, true>(a, n_tiles, smem, s)
+                           : launch_tb_t<NT, TS, ES, MINB, true, false>(a, n_tiles, smem, s);
+    return src ? launch_tb_t<NT, TS, ES, MINB, false, true>(a, n_tiles, smem, s)
+               : launch_tb_t<NT, TS, ES, MINB, false, false>(a, n_tiles, smem, s);
 }
 
 }  // namespace
 
 int tb_threads() { return kNT; }
 
-bool tb_fits(int max_tri_loc, int max_edge_loc) {
+// Register-slot configurations, smallest first: (threads, triangle slots, edge slots, CTAs
+// per SM the register budget is sized for).
+bool tb_fits(int max_tri_loc, int max_edge_loc, int threads) {
+    if (threads == 1024) return max_tri_loc <= 4 * 1024 && max_edge_loc <= 6 * 1024;
     return max_tri_loc <= 8 * kNT && max_edge_loc <= 12 * kNT;
 }
 
@@ -223,23 +259,25 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     a.Uout = (float*)t.U[cur ^ 1];
     a.Jout = (float*)t.J[cur ^ 1];
     a.src_c = (const float*)m.src_c;
+    a.src_grp = m.src_grp;
     a.gtab = m.gtab;
+    a.gstride = m.gtab_size;
     a.gbase = gbase;
     a.step = m.step;
     a.done = t.done;
     a.ksteps = ksteps;
     a.pa = (float)m.pa;
     a.mdt = (float)(-m.dt);
-    a.dt = m.dt;
-    a.w0 = m.w0;
-    a.t0 = m.t0;
-    a.tau = m.tau;
     const bool src = m.n_src > 0;
     const size_t smem = sizeof(float) * ((size_t)t.max_tri_loc + t.max_edge_loc + 1 +
                                          (m.plasma ? (size_t)t.max_edge_loc + 1 : 0));
+    if (t.threads == 1024)
+        return launch_tb_ps<1024, 4, 6, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
     if (t.max_tri_loc <= 4 * kNT && t.max_edge_loc <= 6 * kNT)
-        return launch_tb_ps<4, 6>(a, m.plasma, src, (int)t.n_tiles, smem, s);
-    return launch_tb_ps<8, 12>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+        return launch_tb_ps<kNT, 4, 6, 2>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+    if (t.max_tri_loc <= 6 * kNT && t.max_edge_loc <= 9 * kNT)
+        return launch_tb_ps<kNT, 6, 9, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+    return launch_tb_ps<kNT, 8, 12, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
 }
 
 }  // namespace ue

@@ -3,6 +3,7 @@
 // kernels_geom.cu and kernels_step.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -59,8 +60,11 @@ struct ue_mesh {
     // plasma and source, kept on the host so that a rebuild can re-bake them
     std::vector<double> plasma_n;
     double plasma_nu = 0;
-    std::vector<int32_t> src_k;
+    std::vector<int32_t> src_k;       // stored edge ids
     std::vector<double> src_amp;
+    std::vector<int32_t> src_grp;     // source group of each entry (0 for a single mesh)
+    std::vector<double> grp_par;      // per group: dt, omega0, t0, tau
+    bool is_batch = false;
 
     // captured step graph (plain: one; blocked: one per starting buffer parity)
     cudaGraphExec_t gexec = nullptr;
@@ -74,6 +78,7 @@ struct ue_mesh {
     ue::TileSet ts;
     ue::TBDev tb;
     int block_depth = 4;
+    int tb_threads = 512;
     int cur = 0;                     // buffer holding the current fields
 };
 
@@ -104,6 +109,19 @@ template <typename P>
 bool alloc_into(ue_mesh* m, P*& out, size_t count, size_t elem, cudaStream_t s) {
     out = (P*)dev_alloc(m, count * elem, s);
     return out != nullptr;
+}
+
+// Release one allocation made by dev_alloc (no-op for NULL).
+void dev_release(ue_mesh* m, void* p, cudaStream_t s) {
+    if (!p) return;
+    for (size_t i = 0; i < m->allocs.size(); ++i)
+        if (m->allocs[i] == p) {
+            if (m->free_fn) m->free_fn(p, (void*)s, m->alloc_ctx);
+            else cudaFree(p);
+            m->allocs[i] = m->allocs.back();
+            m->allocs.pop_back();
+            return;
+        }
 }
 
 #define UE_CUDA(call)                                                                   \
@@ -170,6 +188,7 @@ int ensure_graph_tb(ue_mesh* m, int parity) {
 }
 
 int upload_tiles(ue_mesh* m, cudaStream_t s);
+int upload_tileset(ue_mesh* m, cudaStream_t s);
 
 int ensure_graph(ue_mesh* m) {
     if (m->gexec && m->graph_version == m->version) return UE_OK;
@@ -236,23 +255,38 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
 int bake_source(ue_mesh* m, cudaStream_t s) {
     DevMesh& dm = m->dm;
     if (dm.n_src > 0 && dm.src_k) UE_CUDA(ue::launch_source_flags(dm, dm.src_k, dm.n_src, false, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    for (void* p : {(void*)dm.src_k, (void*)dm.src_grp, dm.src_c, (void*)dm.src_hash,
+                    (void*)dm.grp_par, (void*)dm.gtab})
+        dev_release(m, p, s);
+    dm.src_k = dm.src_grp = nullptr;
+    dm.src_c = nullptr;
+    dm.src_hash = nullptr;
+    dm.grp_par = dm.gtab = nullptr;
     dm.n_src = (int64_t)m->src_k.size();
-    if (dm.n_src == 0) {
-        UE_CUDA(cudaStreamSynchronize(s));
-        return UE_OK;
-    }
+    dm.n_grp = 0;
+    if (dm.n_src == 0) return UE_OK;
+    if (!m->is_batch) m->grp_par[0] = m->dt;   // a rebuild may have changed dt
+    dm.n_grp = (int)(m->grp_par.size() / 4);
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
-    int32_t* k = nullptr;
-    double* amp = nullptr;
+    int32_t *k = nullptr, *grp = nullptr;
+    double *amp = nullptr, *par = nullptr, *gt = nullptr;
     void* c = nullptr;
     if (!alloc_into(m, k, dm.n_src, 4, s) || !alloc_into(m, amp, dm.n_src, 8, s) ||
-        !alloc_into(m, c, dm.n_src, esz, s))
+        !alloc_into(m, c, dm.n_src, esz, s) || !alloc_into(m, grp, dm.n_src, 4, s) ||
+        !alloc_into(m, par, m->grp_par.size(), 8, s) ||
+        !alloc_into(m, gt, (size_t)dm.gtab_size * dm.n_grp, 8, s))
         return fail(UE_ERR_ALLOC, "source arrays");
     UE_CUDA(cudaMemcpyAsync(k, m->src_k.data(), 4 * dm.n_src, cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(amp, m->src_amp.data(), 8 * dm.n_src, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(grp, m->src_grp.data(), 4 * dm.n_src, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(par, m->grp_par.data(), 8 * m->grp_par.size(), cudaMemcpyHostToDevice, s));
     dm.src_k = k;
     dm.src_c = c;
-    UE_CUDA(ue::launch_source_coeff(dm, amp, m->d_elen, m->dt, s));
+    dm.src_grp = grp;
+    dm.grp_par = par;
+    dm.gtab = gt;
+    UE_CUDA(ue::launch_source_coeff(dm, amp, m->d_elen, s));
     UE_CUDA(ue::launch_source_flags(dm, k, dm.n_src, true, s));
     // open-addressing table {stored edge id, source index}, load factor <= 1/2
     int bits = 4;
@@ -270,6 +304,8 @@ int bake_source(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemcpyAsync(dh, tab.data(), 8 * (size_t)size, cudaMemcpyHostToDevice, s));
     dm.src_hash = dh;
     dm.src_bits = bits;
+    UE_CUDA(cudaStreamSynchronize(s));
+    dev_release(m, amp, s);
     if (m->variant == UE_VARIANT_BLOCKED) {
         // per-tile source records: (local edge, source index) for every local copy of a source edge
         std::vector<int32_t> src_of(m->hm.n_ei, -1);
@@ -302,12 +338,19 @@ int bake_source(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
+int upload_tileset(ue_mesh* m, cudaStream_t s);
+
 int upload_tiles(ue_mesh* m, cudaStream_t s) {
     std::string err;
     int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
     if (rc != UE_OK) return fail(rc, err);
+    return upload_tileset(m, s);
+}
+
+// Device copy of m->ts, second field buffers, and the coefficient slots of the records.
+int upload_tileset(ue_mesh* m, cudaStream_t s) {
     ue::TileSet& ts = m->ts;
-    if (!ue::tb_fits(ts.max_tri_loc, ts.max_edge_loc))
+    if (!ue::tb_fits(ts.max_tri_loc, ts.max_edge_loc, m->tb_threads))
         return fail(UE_ERR_ARG, "tiles with halo too large for the blocked kernel (" +
                                     std::to_string(ts.max_tri_loc) + " triangles, " +
                                     std::to_string(ts.max_edge_loc) + " edges): lower tile_tris or block_depth");
@@ -318,6 +361,7 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     tb.n_erec = (int64_t)ts.erec.size() / 4;
     tb.max_tri_loc = ts.max_tri_loc;
     tb.max_edge_loc = ts.max_edge_loc;
+    tb.threads = m->tb_threads;
     const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
               alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 1, 4, s) &&
@@ -332,6 +376,60 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * m->dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * m->dm.n_ei_pad, s));
     UE_CUDA(ue::launch_tb_fill(tb, m->dm, s));
+    return UE_OK;
+}
+
+// Allocate the device arrays of a mesh (variant, precision, graph_chunk and block_depth set)
+// and upload its connectivity tables.  Coefficients are zeroed.
+int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
+    const HostMesh& h = m->hm;
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    const int64_t nt = h.n_tris, nei = h.n_ei, nn = h.n_nodes, ne = h.n_edges;
+    bool ok = alloc_into(m, m->d_xy, 2 * nn, 8, s) && alloc_into(m, m->d_tri_nodes, 3 * nt, 4, s) &&
+              alloc_into(m, m->d_edge_nodes, 2 * nei + 2, 4, s) &&
+              alloc_into(m, m->d_edge_opp, 2 * nei + 2, 4, s) &&
+              alloc_into(m, m->d_tri_code, 3 * nt, 4, s) &&
+              alloc_into(m, m->d_rl, (nei + 4) / 4 * 4, 8, s) &&
+              alloc_into(m, m->d_perm, nt, 8, s) && alloc_into(m, m->d_ecaller, nei + 1, 8, s) &&
+              alloc_into(m, m->d_O, 2 * nt, 8, s) && alloc_into(m, m->d_S, nt, 8, s) &&
+              alloc_into(m, m->d_elen, nei + 1, 8, s) && alloc_into(m, m->d_d, nei + 1, 8, s) &&
+              alloc_into(m, m->d_Ec, ne, 8, s) && alloc_into(m, m->d_Bc, nt, 8, s) &&
+              alloc_into(m, m->d_Jc, ne, 8, s);
+    DevMesh& dm = m->dm;
+    dm.precision = m->precision;
+    dm.n_t = nt;
+    dm.n_ei = nei;
+    dm.n_nodes = nn;
+    dm.n_ei_pad = (nei + 4) / 4 * 4;
+    dm.n_t_pad = (nt + 3) / 4 * 4;
+    ok = ok && alloc_into(m, dm.tri, dm.n_t_pad, 16, s) && alloc_into(m, dm.cU, dm.n_ei_pad, esz, s) &&
+         alloc_into(m, dm.U, dm.n_ei_pad, esz, s) && alloc_into(m, dm.B, dm.n_t_pad, esz, s) &&
+         alloc_into(m, dm.step, 1, 8, s);
+    if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, dm.n_t_pad, 8, s);
+    {
+        int g = 64;
+        if (m->graph_chunk > g) g = m->graph_chunk;
+        if (m->variant == UE_VARIANT_BLOCKED && tb_chunk_launches(m) * m->block_depth > g)
+            g = tb_chunk_launches(m) * m->block_depth;
+        dm.gtab_size = g;
+    }
+    if (!ok) {
+        dev_free_all(m, s);
+        return fail(UE_ERR_ALLOC, "device allocation failed");
+    }
+    dm.rl = m->d_rl;
+    UE_CUDA(cudaMemsetAsync(m->d_rl, 0, 8 * dm.n_ei_pad, s));
+    UE_CUDA(cudaMemsetAsync(dm.cU, 0, esz * dm.n_ei_pad, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_xy, h.xy.data(), 16 * nn, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_tri_nodes, h.tri_nodes.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_perm, h.perm_tri.data(), 8 * nt, cudaMemcpyHostToDevice, s));
+    if (nei > 0) {
+        UE_CUDA(cudaMemcpyAsync(m->d_edge_nodes, h.edge_nodes.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_edge_opp, h.edge_opp.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_rl, h.edge_tri.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(m->d_ecaller, h.edge_caller.data(), 8 * nei, cudaMemcpyHostToDevice, s));
+    }
     return UE_OK;
 }
 
@@ -407,6 +505,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         if (o.precision != UE_PREC_FP32) return fail(UE_ERR_ARG, "the blocked variant is FP32 only");
         if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs UE_REORDER_KD");
         if (o.block_depth < 1 || o.block_depth > 15) return fail(UE_ERR_ARG, "block_depth must be in 1..15");
+        if (o.tb_threads != 0 && o.tb_threads != 512 && o.tb_threads != 1024)
+            return fail(UE_ERR_ARG, "tb_threads must be 0, 512 or 1024");
     }
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
@@ -420,56 +520,14 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->cur = 0;
     m->variant = o.variant == 0 ? UE_VARIANT_PLAIN : o.variant;
     m->block_depth = o.block_depth;
+    m->tb_threads = o.tb_threads == 1024 ? 1024 : 512;
     m->precision = o.precision;
     m->graph_chunk = o.graph_chunk == 0 ? 32 : o.graph_chunk;
-    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
-    const int64_t nt = h.n_tris, nei = h.n_ei, nn = h.n_nodes, ne = h.n_edges;
-    bool ok = alloc_into(m, m->d_xy, 2 * nn, 8, s) && alloc_into(m, m->d_tri_nodes, 3 * nt, 4, s) &&
-              alloc_into(m, m->d_edge_nodes, 2 * nei + 2, 4, s) &&
-              alloc_into(m, m->d_edge_opp, 2 * nei + 2, 4, s) &&
-              alloc_into(m, m->d_tri_code, 3 * nt, 4, s) &&
-              alloc_into(m, m->d_rl, (nei + 4) / 4 * 4, 8, s) &&
-              alloc_into(m, m->d_perm, nt, 8, s) && alloc_into(m, m->d_ecaller, nei + 1, 8, s) &&
-              alloc_into(m, m->d_O, 2 * nt, 8, s) && alloc_into(m, m->d_S, nt, 8, s) &&
-              alloc_into(m, m->d_elen, nei + 1, 8, s) && alloc_into(m, m->d_d, nei + 1, 8, s) &&
-              alloc_into(m, m->d_Ec, ne, 8, s) && alloc_into(m, m->d_Bc, nt, 8, s) &&
-              alloc_into(m, m->d_Jc, ne, 8, s);
+    int arc = alloc_and_upload(m, s);
+    if (arc != UE_OK) return arc;
     DevMesh& dm = m->dm;
-    dm.precision = m->precision;
-    dm.n_t = nt;
-    dm.n_ei = nei;
-    dm.n_nodes = nn;
-    dm.n_ei_pad = (nei + 4) / 4 * 4;
-    dm.n_t_pad = (nt + 3) / 4 * 4;
-    ok = ok && alloc_into(m, dm.tri, dm.n_t_pad, 16, s) && alloc_into(m, dm.cU, dm.n_ei_pad, esz, s) &&
-         alloc_into(m, dm.U, dm.n_ei_pad, esz, s) && alloc_into(m, dm.B, dm.n_t_pad, esz, s) &&
-         alloc_into(m, dm.step, 1, 8, s);
-    if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, dm.n_t_pad, 8, s);
-    {
-        int g = 64;
-        if (m->graph_chunk > g) g = m->graph_chunk;
-        if (m->variant == UE_VARIANT_BLOCKED && tb_chunk_launches(m) * m->block_depth > g)
-            g = tb_chunk_launches(m) * m->block_depth;
-        dm.gtab_size = g;
-        ok = ok && alloc_into(m, dm.gtab, g, 8, s);
-    }
-    if (!ok) {
-        dev_free_all(m, s);
-        return fail(UE_ERR_ALLOC, "device allocation failed");
-    }
-    dm.rl = m->d_rl;
-    UE_CUDA(cudaMemsetAsync(m->d_rl, 0, 8 * dm.n_ei_pad, s));
-    UE_CUDA(cudaMemsetAsync(dm.cU, 0, esz * dm.n_ei_pad, s));
-    UE_CUDA(cudaMemcpyAsync(m->d_xy, h.xy.data(), 16 * nn, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(m->d_tri_nodes, h.tri_nodes.data(), 12 * nt, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(m->d_perm, h.perm_tri.data(), 8 * nt, cudaMemcpyHostToDevice, s));
-    if (nei > 0) {
-        UE_CUDA(cudaMemcpyAsync(m->d_edge_nodes, h.edge_nodes.data(), 8 * nei, cudaMemcpyHostToDevice, s));
-        UE_CUDA(cudaMemcpyAsync(m->d_edge_opp, h.edge_opp.data(), 8 * nei, cudaMemcpyHostToDevice, s));
-        UE_CUDA(cudaMemcpyAsync(m->d_rl, h.edge_tri.data(), 8 * nei, cudaMemcpyHostToDevice, s));
-        UE_CUDA(cudaMemcpyAsync(m->d_ecaller, h.edge_caller.data(), 8 * nei, cudaMemcpyHostToDevice, s));
-    }
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    const int64_t nt = h.n_tris, nei = h.n_ei;
     UE_CUDA(ue::launch_geom_tri(m->d_xy, m->d_tri_nodes, m->d_O, m->d_S, nt, s));
     UE_CUDA(ue::launch_geom_edge(m->d_xy, m->d_edge_nodes, m->d_edge_opp, m->d_elen, m->d_d, nei, s));
     // dual lengths must be positive (eq. 3 divides by |O_R O_L|)
@@ -525,6 +583,184 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     return bake_source(m, s);
 }
 
+int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** out) {
+    if (!out || !meshes || n < 1) return fail(UE_ERR_ARG, "need at least one mesh and an output");
+    *out = nullptr;
+    const ue_mesh* m0 = meshes[0];
+    for (int32_t i = 0; i < n; ++i) {
+        const ue_mesh* m = meshes[i];
+        if (!m || !m->built) return fail(UE_ERR_ARG, "mesh " + std::to_string(i) + " is not built");
+        if (m->is_batch) return fail(UE_ERR_ARG, "a batch cannot contain a batch");
+        if (m->precision != m0->precision || m->variant != m0->variant)
+            return fail(UE_ERR_ARG, "all meshes of a batch need the same precision and variant");
+        if (m->variant == UE_VARIANT_BLOCKED &&
+            (m->block_depth != m0->block_depth || m->tb_threads != m0->tb_threads))
+            return fail(UE_ERR_ARG, "all blocked meshes of a batch need the same block_depth and tb_threads");
+        if (m->dm.plasma) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    ue_mesh* B = new (std::nothrow) ue_mesh();
+    if (!B) return fail(UE_ERR_ARG, "out of host memory");
+    B->alloc = m0->alloc;
+    B->free_fn = m0->free_fn;
+    B->alloc_ctx = m0->alloc_ctx;
+    B->is_batch = true;
+    B->precision = m0->precision;
+    B->variant = m0->variant;
+    B->block_depth = m0->block_depth;
+    B->tb_threads = m0->tb_threads;
+    B->graph_chunk = m0->graph_chunk;
+    B->dt = m0->dt;
+    B->rho = 0;
+    B->rho_source = m0->rho_source;
+    // host tables: mesh-major concatenation
+    HostMesh& H = B->hm;
+    std::vector<int64_t> t_off(n + 1, 0), e_off(n + 1, 0), k_off(n + 1, 0), v_off(n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        const HostMesh& h = meshes[i]->hm;
+        t_off[i + 1] = t_off[i] + h.n_tris;
+        e_off[i + 1] = e_off[i] + h.n_edges;
+        k_off[i + 1] = k_off[i] + h.n_ei;
+        v_off[i + 1] = v_off[i] + h.n_nodes;
+    }
+    H.n_tris = t_off[n];
+    H.n_edges = e_off[n];
+    H.n_ei = k_off[n];
+    H.n_nodes = v_off[n];
+    if (H.n_tris > (INT32_MAX / 4) || H.n_nodes > INT32_MAX) {
+        delete B;
+        return fail(UE_ERR_ARG, "batch too large for 32-bit indices");
+    }
+    const int64_t NEI = H.n_ei;
+    for (int32_t i = 0; i < n; ++i) {
+        const HostMesh& h = meshes[i]->hm;
+        H.xy.insert(H.xy.end(), h.xy.begin(), h.xy.end());
+        for (int64_t x : h.edges) H.edges.push_back(x + v_off[i]);
+        for (int64_t x : h.perm_tri) H.perm_tri.push_back(x + t_off[i]);
+        for (int64_t x : h.edge_caller) H.edge_caller.push_back(x + e_off[i]);
+        for (int64_t x : h.k_of_edge) H.k_of_edge.push_back(x < 0 ? -1 : x + k_off[i]);
+        for (int32_t x : h.edge_tri) H.edge_tri.push_back((int32_t)(x + t_off[i]));
+        for (int32_t c : h.tri_code)
+            H.tri_code.push_back((c >> 1) == h.n_ei ? (int32_t)(2 * NEI) : (int32_t)(c + 2 * k_off[i]));
+        for (int32_t x : h.tri_nodes) H.tri_nodes.push_back((int32_t)(x + v_off[i]));
+        for (int32_t x : h.edge_nodes) H.edge_nodes.push_back((int32_t)(x + v_off[i]));
+        for (int32_t x : h.edge_opp) H.edge_opp.push_back((int32_t)(x + v_off[i]));
+        if (B->variant == UE_VARIANT_BLOCKED) {
+            if (H.tile_tri_off.empty()) H.tile_tri_off.push_back(0);
+            for (size_t t = 1; t < h.tile_tri_off.size(); ++t)
+                H.tile_tri_off.push_back(h.tile_tri_off[t] + t_off[i]);
+        }
+    }
+    int rc = alloc_and_upload(B, s);
+    if (rc != UE_OK) {
+        ue_mesh_free(B);
+        return rc;
+    }
+    DevMesh& dm = B->dm;
+    const bool f64 = B->precision == UE_PREC_FP64;
+    const size_t esz = f64 ? 8 : 4;
+#define UE_BATCH_CUDA(call)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            ue_mesh_free(B);                                                                      \
+            return fail(UE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                         \
+    } while (0)
+    for (int32_t i = 0; i < n; ++i) {
+        const ue_mesh* m = meshes[i];
+        const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei, to = t_off[i], ko = k_off[i];
+        UE_BATCH_CUDA(cudaMemcpyAsync(B->d_O + 2 * to, m->d_O, 16 * nt, cudaMemcpyDeviceToDevice, s));
+        UE_BATCH_CUDA(cudaMemcpyAsync(B->d_S + to, m->d_S, 8 * nt, cudaMemcpyDeviceToDevice, s));
+        UE_BATCH_CUDA(cudaMemcpyAsync((char*)dm.B + esz * to, m->dm.B, esz * nt, cudaMemcpyDeviceToDevice, s));
+        UE_BATCH_CUDA(ue::launch_tri_offset(dm.tri + to, m->dm.tri, nt, ko, nei, NEI, s));
+        if (f64)
+            UE_BATCH_CUDA(cudaMemcpyAsync((double*)dm.cB + to, m->dm.cB, 8 * nt, cudaMemcpyDeviceToDevice, s));
+        if (nei > 0) {
+            UE_BATCH_CUDA(cudaMemcpyAsync(B->d_elen + ko, m->d_elen, 8 * nei, cudaMemcpyDeviceToDevice, s));
+            UE_BATCH_CUDA(cudaMemcpyAsync(B->d_d + ko, m->d_d, 8 * nei, cudaMemcpyDeviceToDevice, s));
+            UE_BATCH_CUDA(ue::launch_copy_abs((char*)dm.cU + esz * ko, m->dm.cU, nei, f64, s));
+            UE_BATCH_CUDA(cudaMemcpyAsync((char*)dm.U + esz * ko, m->dm.U, esz * nei, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    {
+        // padding records of the batch point at its zero slot with coefficient 0
+        std::vector<int4> pad(dm.n_t_pad - H.n_tris);
+        for (auto& r : pad) r = make_int4((int)(2 * NEI), (int)(2 * NEI), (int)(2 * NEI), 0);
+        if (!pad.empty())
+            UE_BATCH_CUDA(cudaMemcpyAsync(dm.tri + H.n_tris, pad.data(), 16 * pad.size(), cudaMemcpyHostToDevice, s));
+        UE_BATCH_CUDA(cudaMemsetAsync((char*)dm.U + esz * NEI, 0, esz * (dm.n_ei_pad - NEI), s));
+        UE_BATCH_CUDA(cudaMemsetAsync((char*)dm.B + esz * H.n_tris, 0, esz * (dm.n_t_pad - H.n_tris), s));
+        UE_BATCH_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
+        UE_BATCH_CUDA(cudaStreamSynchronize(s));
+    }
+#undef UE_BATCH_CUDA
+    dm.dt = B->dt;
+    if (B->variant == UE_VARIANT_BLOCKED) {
+        ue::TileSet& T = B->ts;
+        T = ue::TileSet();
+        T.k_max = m0->ts.k_max;
+        for (int32_t i = 0; i < n; ++i) {
+            const ue::TileSet& ts = meshes[i]->ts;
+            const int64_t tr0 = (int64_t)T.trec.size() / 4, er0 = (int64_t)T.erec.size() / 4;
+            for (int64_t t = 0; t < ts.n_tiles; ++t) {
+                const int32_t* h = &ts.hdr[t * ue::TileSet::kHdr];
+                std::vector<int32_t> hh(h, h + ue::TileSet::kHdr);
+                hh[0] += (int32_t)t_off[i];
+                hh[2] += (int32_t)k_off[i];
+                hh[6] += (int32_t)tr0;
+                hh[7] += (int32_t)er0;
+                hh[8] = hh[9] = 0;
+                T.hdr.insert(T.hdr.end(), hh.begin(), hh.end());
+            }
+            for (size_t r = 0; r < ts.trec.size(); r += 4) {
+                T.trec.push_back(ts.trec[r] + (int32_t)t_off[i]);
+                T.trec.push_back(ts.trec[r + 1]);
+                T.trec.push_back(ts.trec[r + 2]);
+                T.trec.push_back(0);
+            }
+            for (size_t r = 0; r < ts.erec.size(); r += 4) {
+                T.erec.push_back(ts.erec[r] + (int32_t)k_off[i]);
+                T.erec.push_back(ts.erec[r + 1]);
+                T.erec.push_back(0);
+                T.erec.push_back(0);
+            }
+            for (int64_t x : ts.erec_tile) T.erec_tile.push_back(x + T.n_tiles);
+            T.n_tiles += ts.n_tiles;
+            T.max_tri_loc = std::max(T.max_tri_loc, ts.max_tri_loc);
+            T.max_edge_loc = std::max(T.max_edge_loc, ts.max_edge_loc);
+        }
+        rc = upload_tileset(B, s);
+        if (rc != UE_OK) {
+            ue_mesh_free(B);
+            return rc;
+        }
+        UE_CUDA(cudaStreamSynchronize(s));
+    }
+    // sources: one group per mesh that has a source
+    for (int32_t i = 0; i < n; ++i) {
+        const ue_mesh* m = meshes[i];
+        if (m->src_k.empty()) continue;
+        const int32_t g = (int32_t)(B->grp_par.size() / 4);
+        B->grp_par.insert(B->grp_par.end(), {m->dt, m->grp_par[1], m->grp_par[2], m->grp_par[3]});
+        for (size_t q = 0; q < m->src_k.size(); ++q) {
+            B->src_k.push_back((int32_t)(m->src_k[q] + k_off[i]));
+            B->src_amp.push_back(m->src_amp[q]);
+            B->src_grp.push_back(g);
+        }
+    }
+    B->built = true;
+    B->steps_done = 0;
+    B->version++;
+    rc = bake_source(B, s);
+    if (rc != UE_OK) {
+        ue_mesh_free(B);
+        return rc;
+    }
+    *out = B;
+    return UE_OK;
+}
+
 int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (dt) *dt = m->dt;
@@ -535,6 +771,7 @@ int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
 
 int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (m->is_batch) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
     if (n && !(nu >= 0)) return fail(UE_ERR_ARG, "collision rate must be >= 0");
     if (n) {
         for (int64_t v = 0; v < m->hm.n_nodes; ++v)
@@ -551,6 +788,7 @@ int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
 int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, double w0,
                   double t0, double tau) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (m->is_batch) return fail(UE_ERR_ARG, "a batch takes its sources from its meshes");
     if (n < 0 || (n > 0 && (!ids || !amp))) return fail(UE_ERR_ARG, "bad source arrays");
     if (n > 0 && !(tau > 0)) return fail(UE_ERR_ARG, "tau must be > 0");
     std::vector<int32_t> ks(n);
@@ -566,9 +804,8 @@ int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, 
     }
     m->src_k = ks;
     m->src_amp.assign(amp, amp + n);
-    m->dm.w0 = w0;
-    m->dm.t0 = t0;
-    m->dm.tau = tau;
+    m->src_grp.assign(n, 0);
+    m->grp_par = {m->dt, w0, t0, tau};
     m->version++;
     return bake_source(m, nullptr);
 }

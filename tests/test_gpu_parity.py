@@ -212,10 +212,10 @@ def test_full_size_scatterer_window(ue):
 
 
 def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=None, graph_chunk=0,
-                 B0=None):
+                 B0=None, threads=0):
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=tile)
     m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=variant, block_depth=k,
-                     graph_chunk=graph_chunk)
+                     graph_chunk=graph_chunk, tb_threads=threads)
     if dens is not None:
         m.set_plasma(dens, nu)
     if src is not None:
@@ -229,9 +229,10 @@ def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=No
     return out, step
 
 
-@pytest.mark.parametrize("tile,k,nsteps", [(512, 4, 14), (1024, 8, 40), (300, 1, 5), (2048, 3, 64)])
+@pytest.mark.parametrize("tile,k,nsteps,threads", [(512, 4, 14, 0), (1024, 8, 40, 0), (300, 1, 5, 0),
+                                                   (2048, 3, 64, 0), (1500, 6, 23, 1024)])
 @pytest.mark.parametrize("plasma", [False, True])
-def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, plasma):
+def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, threads, plasma):
     """Temporal blocking on KD tiles reproduces the plain two-kernel step bit for bit
     (partial last launch, double buffering, halo recompute, source and current included)."""
     ms, ops, w0, dens, ids, amp = _plasma_case()
@@ -242,7 +243,7 @@ def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, plasma):
     (Ep, Bp, Jp), sp = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
     for gc in (0, -1):
         (Eb, Bb, Jb), sb = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k,
-                                        graph_chunk=gc, **kw)
+                                        graph_chunk=gc, threads=threads, **kw)
         assert sp == sb == nsteps
         assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb)
         if plasma:
@@ -261,3 +262,49 @@ def test_blocked_against_oracle(ue):
     errs = rel_l2(E, ops.extend(st.E)), rel_l2(B, st.B), rel_l2(J, ops.extend(st.j))
     print(f"blocked plasma 3001 steps: rel L2 E {errs[0]:.2e} B {errs[1]:.2e} j {errs[2]:.2e}")
     assert max(errs) <= 1e-4
+
+
+def _batch_members():
+    specs = meshgen.batch_specs(5, seed=31, n_min=1500, n_max=12000)
+    out = []
+    for sp in specs:
+        ms = meshgen.batch_mesh(sp)
+        ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.3, ms.h)
+        out.append((ms, ids, amp, sp["omega0"]))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_batch_is_bit_identical_to_single_meshes(ue, variant):
+    """Every mesh of a batch (own dt from its own power iteration, own source frequency) ends
+    bit-identical to the same mesh stepped alone; sizes and scatterers differ per mesh."""
+    blocked = variant == "blocked"
+    singles = []
+    for i, (ms, ids, amp, w0) in enumerate(_batch_members()):
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
+                    tile_tris=400)
+        m.geometry_build(power_iters=60, variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
+                         block_depth=3)
+        m.set_source(ids, amp, w0, 0.0, 0.05)
+        m.write_fields(B=np.cos(3.0 * ms.xy[ms.tris].mean(axis=1)[:, 1] + i))
+        singles.append(m)
+    dts = [m.get_dt()[0] for m in singles]
+    assert len(set(dts)) == len(dts)
+    b = ue.batch_create(singles)
+    assert b.n_tris == sum(m.n_tris for m in singles)
+    for n in (37, 64):        # plain launches, then graph chunks
+        for m in singles:
+            m.step_n(n)
+        b.step_n(n)
+    E, B, _ = b.read_fields()
+    eo = to = 0
+    for m in singles:
+        Es, Bs, _ = m.read_fields()
+        assert np.array_equal(E[eo:eo + m.n_edges], Es)
+        assert np.array_equal(B[to:to + m.n_tris], Bs)
+        assert np.linalg.norm(Es) > 0
+        eo += m.n_edges
+        to += m.n_tris
+    b.close()
+    for m in singles:
+        m.close()
