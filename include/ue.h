@@ -179,6 +179,30 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
  * kernel streams per launch (tile records, local field reads, owned writes); ms[1..2] = 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
+/* Power iteration for rho(M) that allocates no device memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate device memory
+ * while they run (a memory budget fixed up front, a host process that owns the allocator, or
+ * code that must avoid cudaMalloc's implicit synchronisation).  It computes the same
+ * S-normalised power iteration as ue_geometry_build (same SplitMix64 start vector, iteration
+ * count, reduction order), with its work vectors in one device array that the library holds
+ * for the life of the process: at most UE_STATIC_MAX_TRIS triangles and UE_STATIC_MAX_EDGES
+ * interior edges (8.4 MB, on every GPU that loads the library).  Larger sizes return
+ * UE_ERR_ARG.
+ * Inputs are DEVICE pointers owned by the caller, in the stored numbering of ue_get_tables:
+ *   edge_tri[2*n_ei] (R, L); elen[n_ei], d[n_ei] (|e| and |O_R O_L| per stored edge);
+ *   tri_code[3*n_tris]; S[n_tris]; tri_caller[n_tris] (caller id of each stored triangle,
+ *   which keys the start vector).
+ * Output: *rho (host).  Synchronous on `stream`.  All calls share the work array: calls that
+ * overlap on the GPU race, so serialise them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call outside any stream capture.  No cudaMalloc, cudaFree or allocating routine is used. */
+#define UE_STATIC_MAX_TRIS (1 << 18)
+#define UE_STATIC_MAX_EDGES (1 << 19)
+int ue_power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,
+                              const int32_t* tri_code, const double* S,
+                              const int64_t* tri_caller, int64_t n_tris, int64_t n_interior_edges,
+                              int32_t iters, uint32_t seed, void* stream, double* rho);
+
 int ue_stats(const ue_mesh* m, ue_stats_t* out);
 const char* ue_last_error(void);
 void ue_mesh_free(ue_mesh* m);

@@ -10,4 +10,4 @@ does, and fails loudly if the library was not built.
 from ._native import (UE_DT_GIVEN, UE_DT_POWER, UE_PREC_FP32, UE_PREC_FP64,  # noqa: F401
                       UE_REORDER_KD, UE_REORDER_NONE, UE_REORDER_RCM, UE_VARIANT_BLOCKED,
                       UE_VARIANT_PLAIN, UEError)
-from .api import Mesh, batch_create, options  # noqa: F401
+from .api import Mesh, batch_create, options, power_iteration_static  # noqa: F401

@@ -14,6 +14,7 @@ UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD = 0, 1, 2
 UE_PREC_FP32, UE_PREC_FP64 = 0, 1
 UE_DT_GIVEN, UE_DT_POWER = 0, 1
 UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED = 1, 2
+UE_STATIC_MAX_TRIS, UE_STATIC_MAX_EDGES = 1 << 18, 1 << 19
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -58,6 +59,7 @@ SIGNATURES = [
     ("ue_get_tables", C.c_int, [P, PI64, PI64, PI32, PI32]),
     ("ue_get_geometry", C.c_int, [P, PD, PD, PD, PD]),
     ("ue_profile_steps", C.c_int, [P, I64, P, PD, PD]),
+    ("ue_power_iteration_static", C.c_int, [P, P, P, P, P, P, I64, I64, C.c_int32, C.c_uint32, P, PD]),
     ("ue_stats", C.c_int, [P, C.POINTER(Stats)]),
     ("ue_last_error", C.c_char_p, []),
     ("ue_mesh_free", None, [P]),

@@ -199,6 +199,25 @@ class Mesh:
         return {k: getattr(s, k) for k, _ in N.Stats._fields_}
 
 
+def power_iteration_static(edge_tri, elen, d, tri_code, S, tri_caller, iters: int = 200,
+                           seed: int = 0, stream=None) -> float:
+    """rho(M) by power iteration without any device allocation (ue_power_iteration_static).
+
+    For callers that cannot allocate device memory while they run.  Arguments are CUDA
+    tensors in the stored numbering (see ``Mesh.tables``): edge_tri int32 [n_ei, 2], elen and
+    d float64 [n_ei], tri_code int32 [n_tris, 3], S float64 [n_tris], tri_caller int64
+    [n_tris].  Sizes are limited to UE_STATIC_MAX_TRIS / UE_STATIC_MAX_EDGES.
+    """
+    n_t = int(S.shape[0])
+    n_ei = int(elen.shape[0])
+    rho = C.c_double()
+    N.check(N.lib().ue_power_iteration_static(
+        C.c_void_p(edge_tri.data_ptr()), C.c_void_p(elen.data_ptr()), C.c_void_p(d.data_ptr()),
+        C.c_void_p(tri_code.data_ptr()), C.c_void_p(S.data_ptr()), C.c_void_p(tri_caller.data_ptr()),
+        n_t, n_ei, int(iters), int(seed), _stream(stream), C.byref(rho)), "ue_power_iteration_static")
+    return rho.value
+
+
 def batch_create(meshes, stream=None) -> Mesh:
     """ue_batch_create: one Mesh object advancing all the given built meshes together.
 

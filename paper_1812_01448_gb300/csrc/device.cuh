@@ -137,4 +137,10 @@ cudaError_t launch_scatter_geometry(const double* O, const double* S, const doub
                                     int64_t n_e, double* O_c, double* S_c, double* elen_c,
                                     double* d_c, cudaStream_t s);
 
+// Power iteration with a file-scope work array (noalloc.cu).
+int power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,
+                           const int32_t* tri_code, const double* S, const int64_t* tri_caller,
+                           int64_t n_t, int64_t n_ei, int iters, uint32_t seed, cudaStream_t s,
+                           double* rho, std::string& err);
+
 }  // namespace ue

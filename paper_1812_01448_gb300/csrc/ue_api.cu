@@ -1020,6 +1020,17 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     return UE_OK;
 }
 
+int ue_power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,
+                              const int32_t* tri_code, const double* S,
+                              const int64_t* tri_caller, int64_t n_tris, int64_t n_ei,
+                              int32_t iters, uint32_t seed, void* stream, double* rho) {
+    std::string err;
+    const int rc = ue::power_iteration_static(edge_tri, elen, d, tri_code, S, tri_caller, n_tris,
+                                              n_ei, iters, seed, (cudaStream_t)stream, rho, err);
+    if (rc != UE_OK) return fail(rc, err);
+    return UE_OK;
+}
+
 int ue_stats(const ue_mesh* m, ue_stats_t* out) {
     if (!m || !out) return fail(UE_ERR_ARG, "NULL argument");
     std::memset(out, 0, sizeof(*out));
