@@ -80,6 +80,10 @@ typedef struct ue_options {
     int32_t tb_threads;    /* UE_VARIANT_BLOCKED: CTA size, 0 = 512 (default) or 1024        */
     double dt;             /* UE_DT_GIVEN: the time step                                     */
     double safety;         /* UE_DT_POWER: dt = safety * 2 / rho (default 0.5)               */
+    double watchdog_growth;/* energy watchdog: flag growth by more than this factor between  */
+                           /* two checks (default 10)                                        */
+    int32_t watchdog_every;/* steps between energy checks inside ue_step_n (0 = off)         */
+    int32_t reserved1;
 } ue_options;
 
 typedef struct ue_stats_t {
@@ -146,8 +150,18 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
 int ue_step_n(ue_mesh* m, int64_t n_steps, void* stream);
 
 /* Copy the fields back in the caller's numbering (synchronous).  E, j: n_edges values (0 on
- * boundary edges); B: n_tris values.  Any pointer may be NULL. */
+ * boundary edges); B: n_tris values.  Any pointer may be NULL.  Returns UE_ERR_UNSTABLE (after
+ * copying) if the energy watchdog has flagged the run. */
 int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream);
+
+/* Energy W = sum d_i |e_i| E_i^2 + sum S_j B_j^2 of eq. 8 (eq. 7 metric) of the current fields,
+ * reduced on the device in FP64 (synchronous).  Also a watchdog check (see ue_check). */
+int ue_energy(ue_mesh* m, double* W, void* stream);
+
+/* Watchdog state (synchronous): *W = energy at the last check, *flag = 0 ok, 1 non-finite
+ * energy, 2 energy grew by more than watchdog_growth between two checks.  Returns
+ * UE_ERR_UNSTABLE when the flag is set.  ue_write_fields re-arms the watchdog. */
+int ue_check(ue_mesh* m, double* W, int32_t* flag);
 
 /* Step counter used by the source time t = (n + 1/2) dt (checkpoint / resume). */
 int ue_get_step(const ue_mesh* m, int64_t* step);

@@ -25,7 +25,8 @@ class Options(C.Structure):
                 ("power_iters", C.c_int32), ("power_seed", C.c_uint32), ("variant", C.c_int32),
                 ("graph_chunk", C.c_int32), ("tile_tris", C.c_int32), ("block_depth", C.c_int32),
                 ("tb_threads", C.c_int32), ("dt", C.c_double),
-                ("safety", C.c_double)]
+                ("safety", C.c_double), ("watchdog_growth", C.c_double),
+                ("watchdog_every", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -53,6 +54,8 @@ SIGNATURES = [
     ("ue_write_fields", C.c_int, [P, PD, PD, PD, P]),
     ("ue_step_n", C.c_int, [P, I64, P]),
     ("ue_read_fields", C.c_int, [P, PD, PD, PD, P]),
+    ("ue_energy", C.c_int, [P, PD, P]),
+    ("ue_check", C.c_int, [P, PD, PI32]),
     ("ue_get_step", C.c_int, [P, PI64]),
     ("ue_set_step", C.c_int, [P, I64]),
     ("ue_get_sizes", C.c_int, [P, PI64, PI64, PI64, PI64]),

@@ -158,6 +158,19 @@ class Mesh:
                 "ue_read_fields")
         return Ea, Ba, ja
 
+    def energy(self, stream=None) -> float:
+        w = C.c_double()
+        N.check(N.lib().ue_energy(self._h, C.byref(w), _stream(stream)), "ue_energy")
+        return w.value
+
+    def check(self):
+        """(ok, energy at last check, flag); ok is False when the watchdog flagged the run."""
+        w, f = C.c_double(), C.c_int32()
+        rc = N.lib().ue_check(self._h, C.byref(w), C.byref(f))
+        if rc not in (0, -7):
+            N.check(rc, "ue_check")
+        return rc == 0, w.value, f.value
+
     def get_step(self) -> int:
         v = C.c_int64()
         N.check(N.lib().ue_get_step(self._h, C.byref(v)), "ue_get_step")

@@ -194,6 +194,132 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     }
 }
 
+// Shared-memory-record form: the tile's records are staged in shared memory next to its
+// fields, so that registers stay few and 1024 threads (or two CTAs) fit per SM.  Threads
+// stride over the local elements, two at a time (gathers of both issued before either store).
+template <bool PLASMA, bool SRC>
+__global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
+    constexpr int NT = 1024;
+    extern __shared__ float sm[];
+    __shared__ int h[48];
+    const int tid = threadIdx.x;
+    if (tid < 48) h[tid] = a.hdr[(size_t)blockIdx.x * 48 + tid];
+    __syncthreads();
+    const int ntl = h[4], nel = h[5];
+    float* Bl = sm;
+    float* Ul = Bl + ntl;
+    float* Jl = Ul + nel + 1;
+    int2* Tc = reinterpret_cast<int2*>(Ul + (PLASMA ? 2 * (nel + 1) : nel + 1) + 1);   // 8-B aligned below
+    Tc = reinterpret_cast<int2*>((reinterpret_cast<uintptr_t>(Tc) + 7) & ~uintptr_t(7));
+    float* Tb = reinterpret_cast<float*>(Tc + ntl);
+    int* Erl = reinterpret_cast<int*>(Tb + ntl);
+    float* Ecu = reinterpret_cast<float*>(Erl + nel);
+    float* Epb = Ecu + nel;
+    const int4* tr = a.trec + h[6];
+    const int4* er = a.erec + h[7];
+    for (int l = tid; l < ntl; l += NT) {
+        const int4 r = __ldg(tr + l);
+        Tc[l] = make_int2(r.y, r.z);
+        Tb[l] = __int_as_float(r.w);
+        Bl[l] = __ldg(a.Bin + r.x);
+    }
+    for (int l = tid; l < nel; l += NT) {
+        const int4 r = __ldg(er + l);
+        Erl[l] = r.y;
+        Ecu[l] = __int_as_float(r.z);
+        Ul[l] = __ldg(a.Uin + r.x);
+        if constexpr (PLASMA) {
+            Epb[l] = __int_as_float(r.w);
+            Jl[l] = __ldg(a.Jin + r.x);
+        }
+    }
+    if (tid == 0) {
+        Ul[nel] = 0.f;
+        if constexpr (PLASMA) Jl[nel] = 0.f;
+    }
+    const long long n0 = *a.step;
+    __syncthreads();
+    for (int s = 1; s <= a.ksteps; ++s) {
+        const int lim = a.ksteps - s;
+        const int eend = h[32 + lim];
+        for (int l0 = tid; l0 < eend; l0 += 2 * NT) {
+            const int l1 = l0 + NT;
+            const bool v1 = l1 < eend;
+            const int r0 = Erl[l0], r1 = v1 ? Erl[l1] : 0;
+            const float a0 = Bl[r0 & 0xFFFF], b0 = Bl[(unsigned)r0 >> 16], u0 = Ul[l0];
+            const float a1 = Bl[r1 & 0xFFFF], b1 = Bl[(unsigned)r1 >> 16], u1 = v1 ? Ul[l1] : 0.f;
+            float j0 = 0.f, j1 = 0.f;
+            if constexpr (PLASMA) {
+                j0 = Jl[l0];
+                if (v1) j1 = Jl[l1];
+            }
+            float n0v = rn_fma(Ecu[l0], rn_sub(a0, b0), u0);
+            if constexpr (PLASMA) {
+                const float jn = rn_fma(a.pa, j0, rn_mul(Epb[l0], u0));
+                Jl[l0] = jn;
+                n0v = rn_fma(a.mdt, jn, n0v);
+            }
+            Ul[l0] = n0v;
+            if (v1) {
+                float n1v = rn_fma(Ecu[l1], rn_sub(a1, b1), u1);
+                if constexpr (PLASMA) {
+                    const float jn = rn_fma(a.pa, j1, rn_mul(Epb[l1], u1));
+                    Jl[l1] = jn;
+                    n1v = rn_fma(a.mdt, jn, n1v);
+                }
+                Ul[l1] = n1v;
+            }
+        }
+        if constexpr (SRC) {
+            if (h[9] > 0) {
+                __syncthreads();
+                for (int i = tid; i < h[9]; i += NT) {
+                    const int2 q = __ldg(a.tsrc + h[8] + i);
+                    if (q.x < eend) {
+                        const float g = (float)__ldg(a.gtab + (size_t)__ldg(a.src_grp + q.y) * a.gstride +
+                                                     a.gbase + s - 1);
+                        Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int tend = h[16 + lim];
+        for (int l0 = tid; l0 < tend; l0 += 2 * NT) {
+            const int l1 = l0 + NT;
+            const bool v1 = l1 < tend;
+            const int2 c0 = Tc[l0];
+            const int2 c1 = v1 ? Tc[l1] : make_int2(nel << 1 | (nel << 17), nel << 1);
+            const int p0 = c0.x & 0xFFFF, q0 = (unsigned)c0.x >> 16, w0 = c0.y;
+            const int p1 = c1.x & 0xFFFF, q1 = (unsigned)c1.x >> 16, w1 = c1.y;
+            const float x0 = Ul[p0 >> 1], y0 = Ul[q0 >> 1], z0 = Ul[w0 >> 1], bo0 = Bl[l0];
+            const float x1 = Ul[p1 >> 1], y1 = Ul[q1 >> 1], z1 = Ul[w1 >> 1];
+            const float bo1 = v1 ? Bl[l1] : 0.f;
+            const float s0 = rn_add(rn_add((p0 & 1) ? -x0 : x0, (q0 & 1) ? -y0 : y0), (w0 & 1) ? -z0 : z0);
+            Bl[l0] = rn_fma(-Tb[l0], s0, bo0);
+            if (v1) {
+                const float s1 = rn_add(rn_add((p1 & 1) ? -x1 : x1, (q1 & 1) ? -y1 : y1), (w1 & 1) ? -z1 : z1);
+                Bl[l1] = rn_fma(-Tb[l1], s1, bo1);
+            }
+        }
+        __syncthreads();
+    }
+    for (int l = tid; l < h[1]; l += NT) a.Bout[h[0] + l] = Bl[l];
+    for (int l = tid; l < h[3]; l += NT) {
+        a.Uout[h[2] + l] = Ul[l];
+        if constexpr (PLASMA) a.Jout[h[2] + l] = Jl[l];
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(a.done, 1u);
+        if (t == gridDim.x - 1) {
+            *a.step = n0 + a.ksteps;
+            *a.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
 // Fill the coefficient slots of the tile records from the global coefficient arrays.
 __global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restrict__ erec,
                           int64_t n_erec, const int4* __restrict__ tri, const float* __restrict__ cU,
@@ -216,6 +342,15 @@ cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t 
     return cudaGetLastError();
 }
 
+template <bool PLASMA, bool SRC>
+cudaError_t launch_tbs_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t s) {
+    auto kern = k_tbs<PLASMA, SRC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<n_tiles, 1024, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NT, int TS, int ES, int MINB>
 cudaError_t launch_tb_ps(const TBArgs& a, bool plasma, bool src, int n_tiles, size_t smem,
                          cudaStream_t s) {
@@ -231,8 +366,14 @@ int tb_threads() { return kNT; }
 
 // Register-slot configurations, smallest first: (threads, triangle slots, edge slots, CTAs
 // per SM the register budget is sized for).
+size_t tbs_smem(int ntl, int nel, bool plasma) {
+    return 4 * ((size_t)ntl + nel + 1) + (plasma ? 4 * ((size_t)nel + 1) : 0) + 8 +
+           12 * (size_t)ntl + (plasma ? 12 : 8) * (size_t)nel;
+}
+
 bool tb_fits(int max_tri_loc, int max_edge_loc, int threads) {
-    if (threads == 1024) return max_tri_loc <= 4 * 1024 && max_edge_loc <= 6 * 1024;
+    // 1024 threads: records in shared memory (227 KB per CTA, plasma included)
+    if (threads == 1024) return tbs_smem(max_tri_loc, max_edge_loc, true) <= 227 * 1024;
     return max_tri_loc <= 8 * kNT && max_edge_loc <= 12 * kNT;
 }
 
@@ -271,8 +412,13 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     const bool src = m.n_src > 0;
     const size_t smem = sizeof(float) * ((size_t)t.max_tri_loc + t.max_edge_loc + 1 +
                                          (m.plasma ? (size_t)t.max_edge_loc + 1 : 0));
-    if (t.threads == 1024)
-        return launch_tb_ps<1024, 4, 6, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+    if (t.threads == 1024) {
+        const size_t sm2 = tbs_smem(t.max_tri_loc, t.max_edge_loc, m.plasma);
+        if (m.plasma) return src ? launch_tbs_t<true, true>(a, (int)t.n_tiles, sm2, s)
+                                 : launch_tbs_t<true, false>(a, (int)t.n_tiles, sm2, s);
+        return src ? launch_tbs_t<false, true>(a, (int)t.n_tiles, sm2, s)
+                   : launch_tbs_t<false, false>(a, (int)t.n_tiles, sm2, s);
+    }
     if (t.max_tri_loc <= 4 * kNT && t.max_edge_loc <= 6 * kNT)
         return launch_tb_ps<kNT, 4, 6, 2>(a, m.plasma, src, (int)t.n_tiles, smem, s);
     if (t.max_tri_loc <= 6 * kNT && t.max_edge_loc <= 9 * kNT)

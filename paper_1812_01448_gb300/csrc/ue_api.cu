@@ -80,6 +80,13 @@ struct ue_mesh {
     int block_depth = 4;
     int tb_threads = 512;
     int cur = 0;                     // buffer holding the current fields
+
+    // energy watchdog
+    double* wd = nullptr;            // {W previous check, W last, growth factor, flag}
+    double* wd_part = nullptr;
+    int watchdog_every = 0;
+    double watchdog_growth = 10.0;
+    int64_t since_check = 0;
 };
 
 namespace {
@@ -212,6 +219,17 @@ int ensure_graph(ue_mesh* m) {
     }
     m->graph_version = m->version;
     return UE_OK;
+}
+
+// After `steps` more steps: run the energy check whenever watchdog_every steps have passed.
+// Returns the number of kernels launched.
+cudaError_t watchdog_tick(ue_mesh* m, int64_t steps, cudaStream_t s, int64_t* launched) {
+    if (m->watchdog_every <= 0) return cudaSuccess;
+    m->since_check += steps;
+    if (m->since_check < m->watchdog_every) return cudaSuccess;
+    m->since_check = 0;
+    *launched += 2;
+    return ue::launch_energy(m->dm, m->d_elen, m->d_d, m->d_S, m->wd_part, m->wd, s);
 }
 
 // kernels launched for `steps` plain steps issued in batches of `batch` (one g-table kernel
@@ -413,9 +431,17 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
             g = tb_chunk_launches(m) * m->block_depth;
         dm.gtab_size = g;
     }
+    ok = ok && alloc_into(m, m->wd, 4, 8, s) &&
+         alloc_into(m, m->wd_part, ue::energy_parts(nei, nt), 8, s);
     if (!ok) {
         dev_free_all(m, s);
         return fail(UE_ERR_ALLOC, "device allocation failed");
+    }
+    {
+        const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
+        UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+        m->since_check = 0;
     }
     dm.rl = m->d_rl;
     UE_CUDA(cudaMemsetAsync(m->d_rl, 0, 8 * dm.n_ei_pad, s));
@@ -451,6 +477,8 @@ void ue_options_default(ue_options* o) {
     o->block_depth = 4;
     o->dt = 0.0;
     o->safety = 0.5;
+    o->watchdog_growth = 10.0;
+    o->watchdog_every = 0;
 }
 
 const char* ue_last_error(void) { return g_err.c_str(); }
@@ -523,6 +551,10 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->tb_threads = o.tb_threads == 1024 ? 1024 : 512;
     m->precision = o.precision;
     m->graph_chunk = o.graph_chunk == 0 ? 32 : o.graph_chunk;
+    if (o.watchdog_every < 0 || !(o.watchdog_growth > 1.0))
+        return fail(UE_ERR_ARG, "watchdog_every must be >= 0 and watchdog_growth > 1");
+    m->watchdog_every = o.watchdog_every;
+    m->watchdog_growth = o.watchdog_growth;
     int arc = alloc_and_upload(m, s);
     if (arc != UE_OK) return arc;
     DevMesh& dm = m->dm;
@@ -610,6 +642,8 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
     B->block_depth = m0->block_depth;
     B->tb_threads = m0->tb_threads;
     B->graph_chunk = m0->graph_chunk;
+    B->watchdog_every = m0->watchdog_every;
+    B->watchdog_growth = m0->watchdog_growth;
     B->dt = m0->dt;
     B->rho = 0;
     B->rho_source = m0->rho_source;
@@ -820,6 +854,11 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
     UE_CUDA(ue::launch_fields_in(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
                                  (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
                                  m->d_elen, s));
+    {
+        const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
+        UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
+        m->since_check = 0;
+    }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
 }
@@ -840,6 +879,7 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
                 UE_CUDA(cudaGraphLaunch(m->gexec_tb[m->cur], s));
                 left -= chunk;
                 launched += tb_chunk_launches(m) + (m->dm.n_src > 0 ? 1 : 0);
+                UE_CUDA(watchdog_tick(m, chunk, s, &launched));
             }
         }
         while (left > 0) {
@@ -856,29 +896,33 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
                 ++launched;
             }
             left -= batch;
+            UE_CUDA(watchdog_tick(m, batch, s, &launched));
         }
         m->steps_done += n;
         m->launches += launched;
         return UE_OK;
     }
+    int64_t glaunched = 0;
     if (m->graph_chunk > 0 && n >= m->graph_chunk) {
         int rc = ensure_graph(m);
         if (rc != UE_OK) return rc;
         while (left >= m->graph_chunk) {
             UE_CUDA(cudaGraphLaunch(m->gexec, s));
             left -= m->graph_chunk;
+            glaunched += plain_launches(m, m->graph_chunk, m->graph_chunk);
+            UE_CUDA(watchdog_tick(m, m->graph_chunk, s, &glaunched));
         }
     }
     int64_t launched = 0;
-    if (m->graph_chunk > 0 && n >= m->graph_chunk) launched += plain_launches(m, n - left, m->graph_chunk);
     while (left > 0) {
         const int batch = (int)(left < m->dm.gtab_size ? left : m->dm.gtab_size);
         UE_CUDA(ue::launch_steps_plain(m->dm, batch, s));
         launched += plain_launches(m, batch, batch);
         left -= batch;
+        UE_CUDA(watchdog_tick(m, batch, s, &launched));
     }
     m->steps_done += n;
-    m->launches += launched;
+    m->launches += launched + glaunched;
     return UE_OK;
 }
 
@@ -894,7 +938,36 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
     if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
     if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+    double wd[4];
+    UE_CUDA(cudaMemcpyAsync(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost, s));
     UE_CUDA(cudaStreamSynchronize(s));
+    if (wd[3] != 0.0)
+        return fail(UE_ERR_UNSTABLE, std::string("energy watchdog: ") +
+                                         (wd[3] == 1.0 ? "non-finite energy" : "energy growth beyond the limit") +
+                                         " (W = " + std::to_string(wd[1]) + ")");
+    return UE_OK;
+}
+
+int ue_energy(ue_mesh* m, double* W, void* stream) {
+    if (!m || !m->built || !W) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    UE_CUDA(ue::launch_energy(m->dm, m->d_elen, m->d_d, m->d_S, m->wd_part, m->wd, s));
+    double wd[4];
+    UE_CUDA(cudaMemcpyAsync(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    *W = wd[1];
+    return UE_OK;
+}
+
+int ue_check(ue_mesh* m, double* W, int32_t* flag) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    double wd[4];
+    UE_CUDA(cudaMemcpy(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost));
+    if (W) *W = wd[1];
+    if (flag) *flag = (int32_t)wd[3];
+    if (wd[3] != 0.0)
+        return fail(UE_ERR_UNSTABLE, std::string("energy watchdog: ") +
+                                         (wd[3] == 1.0 ? "non-finite energy" : "energy growth beyond the limit"));
     return UE_OK;
 }
 
