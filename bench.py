@@ -374,6 +374,61 @@ def run_batch(args):
         m.close()
 
 
+def run_learned(args):
+    """Learned rho (shipped weights) against the 200-iteration power iteration on held-out
+    meshes (sizes log-uniform up to --learned-max triangles, plus the 4M scatterer mesh):
+    dt-selection time, accuracy, acceptance by the certified bracket, stability."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import meshgen
+    specs = meshgen.learned_specs(args.learned_meshes, seed=2200, n_min=10_000,
+                                  n_max=args.learned_max)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        meshes = pool.map(meshgen.learned_mesh, specs, chunksize=1)
+    meshes.append(meshgen.cached("scatterer_1002", meshgen.scatterer_mesh))
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    from paper_1812_01448_gb300 import learned
+    p = learned.load_weights()
+    rows = []
+    for ms in meshes:
+        a = ue.Mesh(ms.xy, ms.tris)
+        a.geometry_build()
+        _, rho_pi, _ = a.get_dt()
+        t_pi = a.stats()["dt_setup_ms"]
+        a.close()
+        m = ue.Mesh(ms.xy, ms.tris)
+        m.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p, watchdog_every=100)
+        dt, rho, src = m.get_dt()
+        st = m.stats()
+        rng = np.random.default_rng(0)
+        m.write_fields(E=rng.standard_normal(m.n_edges), B=rng.standard_normal(m.n_tris))
+        m.step_n(2000)
+        ok = m.check()[0]
+        m.close()
+        rows.append(dict(n_tris=ms.n_tris, rho_pi=rho_pi, rho_hat=st["rho_hat"], rho_lo=st["rho_lo"],
+                         rho_hi=st["rho_hi"], accepted=src == ue.UE_RHO_LEARNED,
+                         ms_learned=st["dt_setup_ms"], ms_power=t_pi, stable=bool(ok)))
+    err = np.array([abs(r["rho_hat"] / r["rho_pi"] - 1) for r in rows])
+    acc = [r for r in rows if r["accepted"]]
+    big = [r for r in rows if r["n_tris"] >= 1_000_000 and r["accepted"]]
+    line = {
+        "metric": "learned dt: setup time vs 200-iteration power iteration", "n_meshes": len(rows),
+        "median_rel_err": float(np.median(err)), "max_rel_err": float(err.max()),
+        "within_2pct": int((err <= 0.02).sum()), "accepted": len(acc),
+        "unstable_runs": sum(not r["stable"] for r in rows),
+        "median_speedup_accepted": float(np.median([r["ms_power"] / r["ms_learned"] for r in acc])) if acc else None,
+        "speedup_largest": (big[-1]["ms_power"] / big[-1]["ms_learned"]) if big else None,
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,7 +442,9 @@ def main(argv=None):
     ap.add_argument("--block-depth", type=int, default=4)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
-    ap.add_argument("--workload", choices=["scatterer", "batch"], default="scatterer")
+    ap.add_argument("--workload", choices=["scatterer", "batch", "learned"], default="scatterer")
+    ap.add_argument("--learned-meshes", type=int, default=40)
+    ap.add_argument("--learned-max", type=int, default=1_000_000)
     ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--quick-setup", action="store_true",
                     help="fixed dt instead of power iteration (for profiler runs)")
@@ -398,6 +455,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_native(args)
 

@@ -52,6 +52,7 @@ extern "C" {
 
 #define UE_DT_GIVEN 0            /* use ue_options.dt                                         */
 #define UE_DT_POWER 1            /* dt = safety * 2 / rho(M), rho by FP64 power iteration     */
+#define UE_DT_LEARNED 2          /* rho from the learned predictor if certified, else power   */
 
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
 #define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
@@ -59,6 +60,10 @@ extern "C" {
 
 #define UE_RHO_GIVEN 0
 #define UE_RHO_POWER 1
+#define UE_RHO_LEARNED 2         /* learned prediction accepted                               */
+#define UE_RHO_POWER_FALLBACK 3  /* learned prediction outside the bracket: power iteration   */
+
+#define UE_MLP_PARAMS 5057       /* W1[64x12], b1[64], W2[64x64], b2[64], w3[64], b3          */
 
 typedef struct ue_mesh ue_mesh;  /* opaque, owned by the library until ue_mesh_free        */
 
@@ -84,6 +89,8 @@ typedef struct ue_options {
                            /* two checks (default 10)                                        */
     int32_t watchdog_every;/* steps between energy checks inside ue_step_n (0 = off)         */
     int32_t reserved1;
+    const float* mlp_params;/* UE_DT_LEARNED: host array of UE_MLP_PARAMS floats             */
+    double learned_margin; /* UE_DT_LEARNED: accept rho_hat in [margin*rho_lo, rho_hi] (1.05)*/
 } ue_options;
 
 typedef struct ue_stats_t {
@@ -94,6 +101,9 @@ typedef struct ue_stats_t {
     int32_t precision;
     double bytes_per_step;       /* algorithmic HBM bytes of one plain step                   */
     int64_t kernel_launches;     /* kernels the library launched so far                       */
+    double dt_setup_ms;          /* wall time of the dt selection in ue_geometry_build        */
+    double rho_lo, rho_hi;       /* certified bracket (UE_DT_LEARNED), 0 otherwise            */
+    double rho_hat;              /* learned prediction (UE_DT_LEARNED), 0 otherwise           */
 } ue_stats_t;
 
 /* Fill *opt with defaults (RCM, FP32, power-iteration dt, safety 0.5, 200 iterations). */
@@ -183,6 +193,29 @@ int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int
  * O[2*n_tris] circumcentres, S[n_tris] areas, elen[n_edges] lengths, d[n_edges] signed dual
  * lengths (NaN on boundary edges).  Any pointer may be NULL. */
 int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
+
+/* Learned spectral radius (device pointers, caller-owned; the paper's eq. 20 sets dt from the
+ * highest mode, which the network predicts per triangle).
+ * ue_rho_features: X[12*n_tris] (float, stored triangle order) and logS[n_tris] of a built mesh.
+ * ue_mlp_forward: z[n] for rows X[12*n]; bf16 = 1 tensor cores (BF16 in, FP32 accumulate),
+ *   0 = FP32 debug path.  params: UE_MLP_PARAMS floats on the device.
+ * ue_mlp_backward: grad[UE_MLP_PARAMS] = sum over m rows of dz[i] * dz_i/dparams for rows[i]
+ *   (same rounding as the forward); work holds m * UE_MLP_PARAMS floats.
+ * ue_adam: one Adam step (t >= 1) on n floats.
+ * ue_seg_argmax: per segment s of rows [off[s], off[s+1]): best = max (z - logS/2), arg.
+ * ue_rho_loss: dz[s] = 2 (best[s] - target[s]), loss[s] = (best[s] - target[s])^2.
+ * All asynchronous on `stream`. */
+int ue_rho_features(ue_mesh* m, float* X, float* logS, void* stream);
+int ue_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16, float* z,
+                   void* stream);
+int ue_mlp_backward(const float* params, const float* X, const int64_t* rows, const float* dz,
+                    int64_t m, int32_t bf16, float* work, float* grad, void* stream);
+int ue_adam(float* params, const float* grad, float* m1, float* m2, int32_t n, float lr,
+            float beta1, float beta2, float eps, int32_t t, void* stream);
+int ue_seg_argmax(const float* z, const float* logS, const int64_t* off, int32_t n_seg,
+                  float* best, int64_t* arg, void* stream);
+int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz, float* loss,
+                void* stream);
 
 /* Time the step kernels with CUDA events: n_steps (1..4096) launches one by one on `stream`
  * (no graph), then synchronised; the fields advance.

@@ -26,6 +26,8 @@ from .configs import (  # noqa: F401
     batch_meshes,
     batch_specs,
     batch_mesh,
+    learned_specs,
+    learned_mesh,
     source_line_amplitudes,
     plasma_density_nodes,
     te_mode_b,

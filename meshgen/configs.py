@@ -124,6 +124,45 @@ def batch_meshes(n_meshes: int = 512, seed: int = 1004, n_min: int = 5_000, n_ma
         yield dict(mesh=batch_mesh(spec), **spec)
 
 
+def learned_specs(n_meshes: int, seed: int = 1005, n_min: int = 1_000, n_max: int = 50_000):
+    """Corpus for the learned spectral-radius predictor: log-uniform sizes, jitter U[0, 0.3] h,
+    grading ratio h_max/h_min U[1, 8] around one random scatterer (triangle, ellipse or rotated
+    rectangle of size U[0.1, 0.3]).  All draws come from one seeded stream."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for k in range(n_meshes):
+        n_t = float(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))
+        kind = int(rng.integers(3))
+        size = float(rng.uniform(0.1, 0.3))
+        ang = float(rng.uniform(0, 2 * math.pi))
+        c = (0.5 + float(rng.uniform(-0.1, 0.1)), 0.5 + float(rng.uniform(-0.1, 0.1)))
+        aspect = float(rng.uniform(0.5, 1.0)) if kind == 1 else float(rng.uniform(0.4, 1.0))
+        specs.append(dict(index=k, n_tris=n_t, kind=("triangle", "ellipse", "rectangle")[kind],
+                          size=size, angle=ang, center=c, aspect=aspect,
+                          jitter=float(rng.uniform(0.0, 0.3)), ratio=float(rng.uniform(1.0, 8.0)),
+                          omega0=2 * math.pi * 20, seed=int(rng.integers(1 << 31))))
+    return specs
+
+
+def learned_mesh(spec) -> MeshArrays:
+    """Build one mesh of ``learned_specs``: spacing graded from h at the scatterer to ratio*h
+    over a band of width 0.2, h chosen so that a uniform mesh of h_max would have n_tris / ratio
+    triangles (the graded mesh then lands near n_tris)."""
+    size, ang, c = spec["size"], spec["angle"], spec["center"]
+    if spec["kind"] == "triangle":
+        hole = polygon_triangle(c, size, ang)
+    elif spec["kind"] == "ellipse":
+        hole = polygon_ellipse(c, size / 2, size / 2 * spec["aspect"], ang, n_vertices=48)
+    else:
+        hole = polygon_rectangle(c, size, size * spec["aspect"], ang)
+    ratio = spec["ratio"]
+    h_max = uniform_spacing_for(spec["n_tris"] / max(1.0, ratio ** 0.5))
+    h_min = h_max / ratio
+    grade = (h_max - h_min) / 0.2
+    return graded_square(h_min, h_max, grade=grade, holes=[hole], jitter=spec["jitter"],
+                         seed=spec["seed"])
+
+
 def cached(name: str, make, cache_dir: str | None = None) -> MeshArrays:
     """Return make() memoised in an .npz under $UE_MESH_CACHE (default: the system temp dir).
 

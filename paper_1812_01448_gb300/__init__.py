@@ -7,7 +7,9 @@ radius of M (eq. 20).  The work is done by ``libue.so`` (C ABI in include/ue.h, 
 csrc/); this package is its binding.  Importing it does not load the library; the first call
 does, and fails loudly if the library was not built.
 """
-from ._native import (UE_DT_GIVEN, UE_DT_POWER, UE_PREC_FP32, UE_PREC_FP64,  # noqa: F401
+from ._native import (UE_DT_GIVEN, UE_DT_LEARNED, UE_DT_POWER, UE_PREC_FP32,  # noqa: F401
+                      UE_PREC_FP64, UE_RHO_LEARNED, UE_RHO_POWER, UE_RHO_POWER_FALLBACK,
                       UE_REORDER_KD, UE_REORDER_NONE, UE_REORDER_RCM, UE_VARIANT_BLOCKED,
                       UE_VARIANT_PLAIN, UEError)
-from .api import Mesh, batch_create, options, power_iteration_static  # noqa: F401
+from .api import (Mesh, adam, batch_create, mlp_backward, mlp_forward, options,  # noqa: F401
+                  power_iteration_static, rho_loss, seg_argmax)

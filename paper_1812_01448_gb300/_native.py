@@ -12,7 +12,9 @@ UE_ERR = {-1: "UE_ERR_ARG", -2: "UE_ERR_NONMANIFOLD", -3: "UE_ERR_DEGENERATE", -
           -5: "UE_ERR_CUDA", -6: "UE_ERR_ALLOC", -7: "UE_ERR_UNSTABLE", -8: "UE_ERR_TIMEOUT"}
 UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD = 0, 1, 2
 UE_PREC_FP32, UE_PREC_FP64 = 0, 1
-UE_DT_GIVEN, UE_DT_POWER = 0, 1
+UE_DT_GIVEN, UE_DT_POWER, UE_DT_LEARNED = 0, 1, 2
+UE_RHO_GIVEN, UE_RHO_POWER, UE_RHO_LEARNED, UE_RHO_POWER_FALLBACK = 0, 1, 2, 3
+UE_MLP_PARAMS = 5057
 UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED = 1, 2
 UE_STATIC_MAX_TRIS, UE_STATIC_MAX_EDGES = 1 << 18, 1 << 19
 
@@ -26,14 +28,17 @@ class Options(C.Structure):
                 ("graph_chunk", C.c_int32), ("tile_tris", C.c_int32), ("block_depth", C.c_int32),
                 ("tb_threads", C.c_int32), ("dt", C.c_double),
                 ("safety", C.c_double), ("watchdog_growth", C.c_double),
-                ("watchdog_every", C.c_int32), ("reserved1", C.c_int32)]
+                ("watchdog_every", C.c_int32), ("reserved1", C.c_int32),
+                ("mlp_params", C.c_void_p), ("learned_margin", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("n_edges", C.c_int64),
                 ("n_interior_edges", C.c_int64), ("steps_done", C.c_int64), ("dt", C.c_double),
                 ("rho", C.c_double), ("rho_source", C.c_int32), ("precision", C.c_int32),
-                ("bytes_per_step", C.c_double), ("kernel_launches", C.c_int64)]
+                ("bytes_per_step", C.c_double), ("kernel_launches", C.c_int64),
+                ("dt_setup_ms", C.c_double), ("rho_lo", C.c_double), ("rho_hi", C.c_double),
+                ("rho_hat", C.c_double)]
 
 
 P = C.c_void_p
@@ -61,6 +66,12 @@ SIGNATURES = [
     ("ue_get_sizes", C.c_int, [P, PI64, PI64, PI64, PI64]),
     ("ue_get_tables", C.c_int, [P, PI64, PI64, PI32, PI32]),
     ("ue_get_geometry", C.c_int, [P, PD, PD, PD, PD]),
+    ("ue_rho_features", C.c_int, [P, P, P, P]),
+    ("ue_mlp_forward", C.c_int, [P, P, I64, C.c_int32, P, P]),
+    ("ue_mlp_backward", C.c_int, [P, P, P, P, I64, C.c_int32, P, P, P]),
+    ("ue_adam", C.c_int, [P, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32, P]),
+    ("ue_seg_argmax", C.c_int, [P, P, P, C.c_int32, P, P, P]),
+    ("ue_rho_loss", C.c_int, [P, P, C.c_int32, P, P, P]),
     ("ue_profile_steps", C.c_int, [P, I64, P, PD, PD]),
     ("ue_power_iteration_static", C.c_int, [P, P, P, P, P, P, I64, I64, C.c_int32, C.c_uint32, P, PD]),
     ("ue_stats", C.c_int, [P, C.POINTER(Stats)]),

@@ -110,7 +110,13 @@ class Mesh:
             pass
 
     def geometry_build(self, stream=None, **opts):
+        params = opts.pop("mlp_params", None)
         o = options(**opts)
+        if params is not None:
+            self._mlp_params = np.ascontiguousarray(params, dtype=np.float32)
+            if self._mlp_params.shape != (N.UE_MLP_PARAMS,):
+                raise ValueError(f"mlp_params must hold {N.UE_MLP_PARAMS} values")
+            o.mlp_params = self._mlp_params.ctypes.data_as(C.c_void_p)
         self.precision = o.precision
         N.check(N.lib().ue_geometry_build(self._h, C.byref(o), _stream(stream)), "ue_geometry_build")
 
@@ -198,6 +204,12 @@ class Mesh:
                 "ue_get_geometry")
         return dict(O=O, S=S, elen=le, d=d)
 
+    def rho_features(self, X, logS, stream=None):
+        """Learned-rho features (ue_rho_features) into CUDA tensors X [n_tris, 12] float32 and
+        logS [n_tris] float32, stored triangle order."""
+        N.check(N.lib().ue_rho_features(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(logS.data_ptr()),
+                                        _stream(stream)), "ue_rho_features")
+
     def profile_steps(self, n: int, stream=None):
         """Mean per-kernel device time (ms) and algorithmic bytes per launch, n plain steps."""
         ms = np.zeros(3)
@@ -243,3 +255,36 @@ def batch_create(meshes, stream=None) -> Mesh:
     b = Mesh._wrap(h, keep=tuple(meshes))
     b.precision = meshes[0].precision
     return b
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params, X, z, bf16: bool = True, stream=None):
+    """z[i] = MLP(X[i]) on the device (ue_mlp_forward); CUDA tensors."""
+    N.check(N.lib().ue_mlp_forward(_p(params), _p(X), int(X.shape[0]), int(bool(bf16)), _p(z),
+                                   _stream(stream)), "ue_mlp_forward")
+
+
+def mlp_backward(params, X, rows, dz, grad, work, bf16: bool = True, stream=None):
+    """grad = sum_i dz[i] d z(X[rows[i]]) / d params (ue_mlp_backward); CUDA tensors."""
+    N.check(N.lib().ue_mlp_backward(_p(params), _p(X), _p(rows), _p(dz), int(rows.shape[0]),
+                                    int(bool(bf16)), _p(work), _p(grad), _stream(stream)),
+            "ue_mlp_backward")
+
+
+def adam(params, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+         eps: float = 1e-8, stream=None):
+    N.check(N.lib().ue_adam(_p(params), _p(grad), _p(m1), _p(m2), int(params.shape[0]), lr, beta1,
+                            beta2, eps, int(t), _stream(stream)), "ue_adam")
+
+
+def seg_argmax(z, logS, off, best, arg, stream=None):
+    N.check(N.lib().ue_seg_argmax(_p(z), _p(logS), _p(off), int(off.shape[0] - 1), _p(best), _p(arg),
+                                  _stream(stream)), "ue_seg_argmax")
+
+
+def rho_loss(best, target, dz, loss, stream=None):
+    N.check(N.lib().ue_rho_loss(_p(best), _p(target), int(best.shape[0]), _p(dz), _p(loss),
+                                _stream(stream)), "ue_rho_loss")

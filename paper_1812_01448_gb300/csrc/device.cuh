@@ -119,6 +119,28 @@ cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const i
 // src_c[i] = dt_grp * |e| * amp[i], dt of the source's group.
 cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const double* elen,
                                 cudaStream_t s);
+// Learned spectral radius (kernels_mlp.cu).
+int mlp_n_params();
+cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
+                            const int2* rl, const double* elen, const double* d, const double* S,
+                            int64_t n_t, int64_t n_ei, float* X, float* logS, double* kdiag,
+                            double* gersh, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, int bf16, float* z,
+                               cudaStream_t s);
+cudaError_t launch_mlp_backward(const float* P, const float* X, const int64_t* rows, const float* dz,
+                                int64_t m, int bf16, float* work, float* grad, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1,
+                        float b2, float eps, int t, cudaStream_t s);
+cudaError_t launch_seg_argmax(const float* z, const float* logS, const int64_t* off, int n_seg,
+                              float* best, int64_t* arg, cudaStream_t s);
+cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, float* dz,
+                            float* loss, cudaStream_t s);
+cudaError_t launch_max(const double* a, int64_t n, double* part, int n_part, double* out,
+                       cudaStream_t s);
+cudaError_t launch_local_rq(const int32_t* code, const int2* rl, const double* elen, const double* d,
+                            const double* S, int64_t n_ei, const int64_t* j0, double* out,
+                            cudaStream_t s);
+
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);
 cudaError_t launch_energy(const DevMesh& m, const double* elen, const double* d, const double* S,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -80,6 +81,9 @@ struct ue_mesh {
     int block_depth = 4;
     int tb_threads = 512;
     int cur = 0;                     // buffer holding the current fields
+
+    // dt selection
+    double dt_setup_ms = 0, rho_lo = 0, rho_hi = 0, rho_hat = 0;
 
     // energy watchdog
     double* wd = nullptr;            // {W previous check, W last, growth factor, flag}
@@ -397,6 +401,44 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
+// Learned rho: features, BF16 MLP, max aggregation, certified bracket (synchronous).
+// Sets m->rho_hat, m->rho_lo, m->rho_hi.
+int learned_rho(ue_mesh* m, const ue_options& o, cudaStream_t s) {
+    const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
+    const int np = ue::mlp_n_params();
+    const int n_part = 1024;
+    float *X = nullptr, *logS = nullptr, *z = nullptr, *P = nullptr, *best = nullptr;
+    double *kd = nullptr, *ge = nullptr, *part = nullptr, *res = nullptr;
+    int64_t *off = nullptr, *arg = nullptr;
+    if (!alloc_into(m, X, 12 * nt, 4, s) || !alloc_into(m, logS, nt, 4, s) || !alloc_into(m, z, nt, 4, s) ||
+        !alloc_into(m, P, np, 4, s) || !alloc_into(m, best, 1, 4, s) || !alloc_into(m, kd, nt, 8, s) ||
+        !alloc_into(m, ge, nt, 8, s) || !alloc_into(m, part, n_part, 8, s) || !alloc_into(m, res, 3, 8, s) ||
+        !alloc_into(m, off, 2, 8, s) || !alloc_into(m, arg, 1, 8, s))
+        return fail(UE_ERR_ALLOC, "learned dt work space");
+    const int64_t offh[2] = {0, nt};
+    UE_CUDA(cudaMemcpyAsync(P, o.mlp_params, 4 * np, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(off, offh, sizeof(offh), cudaMemcpyHostToDevice, s));
+    UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
+                                m->d_S, nt, nei, X, logS, kd, ge, s));
+    UE_CUDA(ue::launch_mlp_forward(P, X, nt, 1, z, s));
+    UE_CUDA(ue::launch_seg_argmax(z, logS, off, 1, best, arg, s));
+    UE_CUDA(ue::launch_max(kd, nt, part, n_part, res, s));
+    UE_CUDA(ue::launch_max(ge, nt, part, n_part, res + 1, s));
+    UE_CUDA(ue::launch_local_rq(m->d_tri_code, m->d_rl, m->d_elen, m->d_d, m->d_S, nei, arg, res + 2, s));
+    float bh = 0;
+    double rh[3] = {0, 0, 0};
+    UE_CUDA(cudaMemcpyAsync(&bh, best, 4, cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaMemcpyAsync(rh, res, sizeof(rh), cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    for (void* p : {(void*)X, (void*)logS, (void*)z, (void*)P, (void*)best, (void*)kd, (void*)ge,
+                    (void*)part, (void*)res, (void*)off, (void*)arg})
+        dev_release(m, p, s);
+    m->rho_hat = std::exp((double)bh);
+    m->rho_lo = std::sqrt(std::max(rh[0], rh[2]));
+    m->rho_hi = std::sqrt(rh[1]);
+    return UE_OK;
+}
+
 // Allocate the device arrays of a mesh (variant, precision, graph_chunk and block_depth set)
 // and upload its connectivity tables.  Coefficients are zeroed.
 int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
@@ -479,6 +521,8 @@ void ue_options_default(ue_options* o) {
     o->safety = 0.5;
     o->watchdog_growth = 10.0;
     o->watchdog_every = 0;
+    o->mlp_params = nullptr;
+    o->learned_margin = 1.05;
 }
 
 const char* ue_last_error(void) { return g_err.c_str(); }
@@ -524,9 +568,12 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (o.precision != UE_PREC_FP32 && o.precision != UE_PREC_FP64)
         return fail(UE_ERR_ARG, "unknown precision");
     if (o.dt_mode == UE_DT_GIVEN && !(o.dt > 0)) return fail(UE_ERR_ARG, "dt must be > 0");
-    if (o.dt_mode != UE_DT_GIVEN && o.dt_mode != UE_DT_POWER) return fail(UE_ERR_ARG, "unknown dt mode");
-    if (o.dt_mode == UE_DT_POWER && (o.power_iters < 1 || !(o.safety > 0)))
+    if (o.dt_mode != UE_DT_GIVEN && o.dt_mode != UE_DT_POWER && o.dt_mode != UE_DT_LEARNED)
+        return fail(UE_ERR_ARG, "unknown dt mode");
+    if (o.dt_mode != UE_DT_GIVEN && (o.power_iters < 1 || !(o.safety > 0)))
         return fail(UE_ERR_ARG, "power iteration needs iters >= 1 and safety > 0");
+    if (o.dt_mode == UE_DT_LEARNED && (!o.mlp_params || !(o.learned_margin >= 1.0)))
+        return fail(UE_ERR_ARG, "learned dt needs mlp_params and learned_margin >= 1");
     if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN && o.variant != UE_VARIANT_BLOCKED)
         return fail(UE_ERR_ARG, "unknown variant");
     if (o.variant == UE_VARIANT_BLOCKED) {
@@ -581,17 +628,38 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     }
     // triangle records first with dt = 0: the power iteration reads only their edge codes
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, 0.0, s));
-    if (o.dt_mode == UE_DT_POWER) {
+    UE_CUDA(cudaStreamSynchronize(s));
+    const auto t_dt0 = std::chrono::steady_clock::now();
+    m->rho_lo = m->rho_hi = m->rho_hat = 0;
+    bool need_power = o.dt_mode == UE_DT_POWER;
+    if (o.dt_mode == UE_DT_LEARNED) {
+        int lrc = learned_rho(m, o, s);
+        if (lrc != UE_OK) return lrc;
+        const bool ok = m->rho_hat >= o.learned_margin * m->rho_lo && m->rho_hat <= m->rho_hi &&
+                        std::isfinite(m->rho_hat);
+        if (ok) {
+            m->rho = m->rho_hat;
+            m->rho_source = UE_RHO_LEARNED;
+            m->dt = o.safety * 2.0 / m->rho;
+        } else {
+            need_power = true;
+        }
+    }
+    if (need_power) {
         double* work = nullptr;
         if (!alloc_into(m, work, ue::power_iteration_work_doubles(nt, nei), 8, s))
             return fail(UE_ERR_ALLOC, "power iteration work space");
         double rho = 0;
         UE_CUDA(ue::power_iteration(m->d_rl, dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei,
                                     o.power_iters, o.power_seed, work, &rho, s));
+        dev_release(m, work, s);
         if (!(rho > 0) || !std::isfinite(rho)) return fail(UE_ERR_DUAL, "power iteration gave rho <= 0");
         m->rho = rho;
-        m->rho_source = UE_RHO_POWER;
+        m->rho_source = o.dt_mode == UE_DT_LEARNED ? UE_RHO_POWER_FALLBACK : UE_RHO_POWER;
         m->dt = o.safety * 2.0 / rho;
+    }
+    if (o.dt_mode != UE_DT_GIVEN) {
+        m->dt_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_dt0).count();
     } else {
         m->rho = 0;
         m->rho_source = UE_RHO_GIVEN;
@@ -1024,6 +1092,53 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
     return UE_OK;
 }
 
+int ue_rho_features(ue_mesh* m, float* X, float* logS, void* stream) {
+    if (!m || !m->built || !X || !logS) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nt = m->hm.n_tris;
+    double *kd = nullptr, *ge = nullptr;
+    if (!alloc_into(m, kd, nt, 8, s) || !alloc_into(m, ge, nt, 8, s)) return fail(UE_ERR_ALLOC, "feature work space");
+    UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
+                                m->d_S, nt, m->hm.n_ei, X, logS, kd, ge, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    dev_release(m, kd, s);
+    dev_release(m, ge, s);
+    return UE_OK;
+}
+
+int ue_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16, float* z, void* stream) {
+    if (!params || !X || !z || n < 0) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_mlp_forward(params, X, n, bf16 ? 1 : 0, z, (cudaStream_t)stream));
+    return UE_OK;
+}
+
+int ue_mlp_backward(const float* params, const float* X, const int64_t* rows, const float* dz,
+                    int64_t m, int32_t bf16, float* work, float* grad, void* stream) {
+    if (!params || !X || !grad || m < 0 || (m > 0 && (!rows || !dz || !work))) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_mlp_backward(params, X, rows, dz, m, bf16 ? 1 : 0, work, grad, (cudaStream_t)stream));
+    return UE_OK;
+}
+
+int ue_adam(float* params, const float* grad, float* m1, float* m2, int32_t n, float lr, float beta1,
+            float beta2, float eps, int32_t t, void* stream) {
+    if (!params || !grad || !m1 || !m2 || n < 1 || t < 1) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_adam(params, grad, m1, m2, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream));
+    return UE_OK;
+}
+
+int ue_seg_argmax(const float* z, const float* logS, const int64_t* off, int32_t n_seg, float* best,
+                  int64_t* arg, void* stream) {
+    if (!z || !logS || !off || !best || !arg || n_seg < 0) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_seg_argmax(z, logS, off, n_seg, best, arg, (cudaStream_t)stream));
+    return UE_OK;
+}
+
+int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz, float* loss, void* stream) {
+    if (!best || !target || !dz || !loss || n_seg < 0) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_rho_loss(best, target, n_seg, dz, loss, (cudaStream_t)stream));
+    return UE_OK;
+}
+
 int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* bytes) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 1 || n > 4096 || !ms) return fail(UE_ERR_ARG, "n_steps must be in 1..4096 and ms non-NULL");
@@ -1124,6 +1239,10 @@ int ue_stats(const ue_mesh* m, ue_stats_t* out) {
     double per_tri = 16.0 + f * 8.0 + (m->precision == UE_PREC_FP64 ? 8.0 : 0.0);
     out->bytes_per_step = per_edge * (double)h.n_ei + per_tri * (double)h.n_tris;
     out->kernel_launches = m->launches;
+    out->dt_setup_ms = m->dt_setup_ms;
+    out->rho_lo = m->rho_lo;
+    out->rho_hi = m->rho_hi;
+    out->rho_hat = m->rho_hat;
     return UE_OK;
 }
 

@@ -1,0 +1,134 @@
+"""Learned spectral radius on the GPU: features, forward and backward against the FP64 oracle,
+training by the library's own kernels, and what the trained network gains over the power
+iteration (setup time) without losing stability (eq. 20 with the certified bracket)."""
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import geometry, mesh as om, mlp, rcm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ue():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01448_gb300 import build
+    build.build()
+    import paper_1812_01448_gb300 as ue
+    return ue
+
+
+def _gpu_features(ue, ms):
+    import torch
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-3)
+    X = torch.empty((m.n_tris, 12), dtype=torch.float32, device="cuda")
+    L = torch.empty(m.n_tris, dtype=torch.float32, device="cuda")
+    m.rho_features(X, L)
+    t = m.tables()
+    m.close()
+    return X, L, t
+
+
+def test_features_match_oracle(ue):
+    ms = meshgen.learned_mesh(meshgen.learned_specs(1, seed=8)[0])
+    X, L, t = _gpu_features(ue, ms)
+    m = om.canonicalize(ms.xy, ms.tris)
+    ref = rcm.device_tables(m, t["perm_tri"])
+    g = geometry.Geometry(m)
+    Xo, So = mlp.features(ms.xy, ref["tri_nodes"], ref["tri_code"], ref["n_ei"], ref["edge_tri"],
+                          g.d[ref["edge_caller"]])
+    np.testing.assert_allclose(X.cpu().numpy(), Xo, rtol=2e-6, atol=2e-6)
+    np.testing.assert_allclose(L.cpu().numpy(), np.log(So), rtol=1e-6, atol=1e-6)
+
+
+def _rand_rows(n, seed):
+    rng = np.random.default_rng(seed)
+    X = np.abs(rng.standard_normal((n, 12))) + 0.1
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_matches_oracle(ue, bf16):
+    import torch
+    p = mlp.init_params(11) + 0.05 * np.random.default_rng(2).standard_normal(mlp.N_PARAMS)
+    p32 = p.astype(np.float32)
+    X = _rand_rows(1000, 3)
+    z = torch.empty(1000, dtype=torch.float32, device="cuda")
+    ue.mlp_forward(torch.from_numpy(p32).cuda(), torch.from_numpy(X).cuda(), z, bf16=bf16)
+    zo, _ = mlp.forward(p32.astype(np.float64), X.astype(np.float64), round_bf16=bf16)
+    err = np.abs(z.cpu().numpy() - zo).max() / np.abs(zo).max()
+    assert err < (2e-4 if bf16 else 2e-6), err
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_backward_matches_oracle(ue, bf16):
+    """Gradients of sum_i dz_i z(x_rows[i]) against the oracle's analytic backward (which is
+    pinned to central finite differences on the CPU)."""
+    import torch
+    p32 = (mlp.init_params(12) + 0.05 * np.random.default_rng(4).standard_normal(mlp.N_PARAMS)).astype(np.float32)
+    X = _rand_rows(64, 5)
+    rows = np.array([3, 17, 17, 40, 63], np.int64)
+    dz = np.array([0.5, -1.0, 0.25, 2.0, -0.75], np.float32)
+    g = torch.empty(mlp.N_PARAMS, dtype=torch.float32, device="cuda")
+    work = torch.empty((len(rows), mlp.N_PARAMS), dtype=torch.float32, device="cuda")
+    ue.mlp_backward(torch.from_numpy(p32).cuda(), torch.from_numpy(X).cuda(),
+                    torch.from_numpy(rows).cuda(), torch.from_numpy(dz).cuda(), g, work, bf16=bf16)
+    _, cache = mlp.forward(p32.astype(np.float64), X[rows].astype(np.float64), round_bf16=bf16)
+    go = mlp.backward(p32.astype(np.float64), cache, dz.astype(np.float64))
+    gg = g.cpu().numpy()
+    rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    assert rel < (1e-3 if bf16 else 1e-6), rel
+
+
+def _corpus_meshes(n, seed, n_min=1000, n_max=20000):
+    specs = meshgen.learned_specs(n, seed=seed, n_min=n_min, n_max=n_max)
+    with mp.get_context("spawn").Pool(8) as pool:
+        return pool.map(meshgen.learned_mesh, specs)
+
+
+def test_training_gains_over_power_iteration(ue):
+    """Train on 150 meshes with the library's kernels; on 20 held-out meshes the certified
+    prediction replaces the power iteration: within 2% of rho_PI, accepted by the bracket,
+    several times faster, and 2000 steps at dt = 2 * 0.5 / rho_hat stay stable."""
+    from paper_1812_01448_gb300 import learned
+    train_m = _corpus_meshes(150, seed=2101)
+    test_m = _corpus_meshes(20, seed=2102, n_min=5000, n_max=40000)
+    corpus = learned.build_corpus(train_m)
+    p, hist = learned.train(corpus, epochs=1500, seed=3)
+    assert hist[-1] < hist[0] / 10
+    errs, acc, t_pi, t_ml = [], 0, [], []
+    for ms in test_m:
+        a = ue.Mesh(ms.xy, ms.tris)
+        a.geometry_build()
+        _, rho_pi, _ = a.get_dt()
+        t_pi.append(a.stats()["dt_setup_ms"])
+        b = ue.Mesh(ms.xy, ms.tris)
+        b.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p, watchdog_every=50)
+        dt, rho, src = b.get_dt()
+        st = b.stats()
+        errs.append(abs(st["rho_hat"] / rho_pi - 1))
+        if src == ue.UE_RHO_LEARNED:
+            acc += 1
+            t_ml.append(st["dt_setup_ms"])
+        rng = np.random.default_rng(0)
+        E0 = rng.standard_normal(b.n_edges)
+        b.write_fields(E=E0, B=rng.standard_normal(b.n_tris))
+        b.step_n(2000)
+        ok, W, flag = b.check()
+        assert ok, (rho, rho_pi, W, flag)
+        a.close()
+        b.close()
+    errs = np.array(errs)
+    print(f"learned rho: median |rho_hat/rho_PI - 1| = {np.median(errs):.4f}, max {errs.max():.4f}, "
+          f"accepted {acc}/{len(test_m)}, setup {np.median(t_ml) if t_ml else float('nan'):.3f} ms vs "
+          f"power iteration {np.median(t_pi):.3f} ms")
+    assert np.median(errs) < 0.02
+    assert acc >= len(test_m) // 2
+    assert np.median(t_ml) * 5 < np.median(t_pi)
