@@ -17,7 +17,6 @@ namespace ue {
 namespace {
 
 constexpr int kNT = 512;
-constexpr int kG = 3;   // slots whose shared-memory gathers are issued together
 
 struct TBArgs {
     const int* hdr;
@@ -44,8 +43,9 @@ struct TBArgs {
 // NT threads; each thread owns local triangle slots tid + i*NT (i < TS) and local edge slots
 // tid + i*NT (i < ES), whose records it keeps in registers for all k steps.  In every phase a
 // thread takes its slots kG at a time: it issues the group's shared-memory gathers, then
-// computes and stores, so that a group's loads are in flight together.
-template <int NT, int TS, int ES, int MINB, bool PLASMA, bool SRC>
+// computes and stores, so that a group's loads are in flight together (kG = 1: slot by slot,
+// which measured best for the largest slot counts).
+template <int NT, int TS, int ES, int MINB, int kG, bool PLASMA, bool SRC>
 __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     extern __shared__ float sm[];
     __shared__ int h[48];
@@ -333,9 +333,9 @@ __global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restr
     }
 }
 
-template <int NT, int TS, int ES, int MINB, bool PLASMA, bool SRC>
+template <int NT, int TS, int ES, int MINB, int G, bool PLASMA, bool SRC>
 cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t s) {
-    auto kern = k_tb<NT, TS, ES, MINB, PLASMA, SRC>;
+    auto kern = k_tb<NT, TS, ES, MINB, G, PLASMA, SRC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<n_tiles, NT, smem, s>>>(a);
@@ -351,13 +351,13 @@ cudaError_t launch_tbs_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t
     return cudaGetLastError();
 }
 
-template <int NT, int TS, int ES, int MINB>
+template <int NT, int TS, int ES, int MINB, int G>
 cudaError_t launch_tb_ps(const TBArgs& a, bool plasma, bool src, int n_tiles, size_t smem,
                          cudaStream_t s) {
-    if (plasma) return src ? launch_tb_t<NT, TS, ES, MINB, true, true>(a, n_tiles, smem, s)
-                           : launch_tb_t<NT, TS, ES, MINB, true, false>(a, n_tiles, smem, s);
-    return src ? launch_tb_t<NT, TS, ES, MINB, false, true>(a, n_tiles, smem, s)
-               : launch_tb_t<NT, TS, ES, MINB, false, false>(a, n_tiles, smem, s);
+    if (plasma) return src ? launch_tb_t<NT, TS, ES, MINB, G, true, true>(a, n_tiles, smem, s)
+                           : launch_tb_t<NT, TS, ES, MINB, G, true, false>(a, n_tiles, smem, s);
+    return src ? launch_tb_t<NT, TS, ES, MINB, G, false, true>(a, n_tiles, smem, s)
+               : launch_tb_t<NT, TS, ES, MINB, G, false, false>(a, n_tiles, smem, s);
 }
 
 }  // namespace
@@ -420,10 +420,10 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
                    : launch_tbs_t<false, false>(a, (int)t.n_tiles, sm2, s);
     }
     if (t.max_tri_loc <= 4 * kNT && t.max_edge_loc <= 6 * kNT)
-        return launch_tb_ps<kNT, 4, 6, 2>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+        return launch_tb_ps<kNT, 4, 6, 2, 3>(a, m.plasma, src, (int)t.n_tiles, smem, s);
     if (t.max_tri_loc <= 6 * kNT && t.max_edge_loc <= 9 * kNT)
-        return launch_tb_ps<kNT, 6, 9, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
-    return launch_tb_ps<kNT, 8, 12, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+        return launch_tb_ps<kNT, 6, 9, 1, 3>(a, m.plasma, src, (int)t.n_tiles, smem, s);
+    return launch_tb_ps<kNT, 8, 12, 1, 1>(a, m.plasma, src, (int)t.n_tiles, smem, s);
 }
 
 }  // namespace ue
