@@ -45,6 +45,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Maximum of x over all ranks (x itself without a process group).  Uses a CUDA tensor
+    under NCCL and a CPU tensor under gloo."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,11 +227,7 @@ def run_native(args):
         torch.cuda.synchronize()
         barrier()
     launches = m.stats()["kernel_launches"] - launches0
-    ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist)
     value = world * n_t * args.steps / (ms_total * 1e-3)
 
     # per-kernel device times, CUDA events on the launch stream, right after the timed region
@@ -259,11 +267,7 @@ def run_native(args):
     m.set_step(0)
     m.step_n(args.steps, stream)
     m.read_fields(out={"E": Eo, "B": Bo}, stream=stream)
-    t_e2e = time.perf_counter() - t_e2e
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t_e2e, dist)
     io = 8.0 * (m.n_edges + m.n_tris)
     e2e = {"value": world * n_t * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
