@@ -193,8 +193,9 @@ def run_native(args):
     blocked = args.variant == "blocked"
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
                 tile_tris=args.tile_tris)
-    vopt = dict(variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
-                block_depth=args.block_depth, graph_chunk=args.graph_chunk,
+    variant = {"plain": ue.UE_VARIANT_PLAIN, "blocked": ue.UE_VARIANT_BLOCKED,
+               "persistent": ue.UE_VARIANT_PERSISTENT}[args.variant]
+    vopt = dict(variant=variant, block_depth=args.block_depth, graph_chunk=args.graph_chunk,
                 tb_threads=args.tb_threads)
     if args.quick_setup:
         # profiling runs: a fixed dt instead of the 200-iteration power iteration, so that few
@@ -289,7 +290,7 @@ def run_native(args):
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
                        "variant": (f"blocked k={args.block_depth} tiles<={args.tile_tris} "
                                 f"threads={args.tb_threads or 512}" if blocked
-                                   else "plain") + f", CUDA graph chunk {args.graph_chunk} steps",
+                                else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -441,7 +442,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--variant", choices=["plain", "blocked"], default="plain")
+    ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="plain")
     ap.add_argument("--tile-tris", type=int, default=2048)
     ap.add_argument("--block-depth", type=int, default=4)
     ap.add_argument("--graph-chunk", type=int, default=32)

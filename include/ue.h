@@ -57,6 +57,8 @@ extern "C" {
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
 #define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
                                  /* recomputed in shared memory; FP32; needs UE_REORDER_KD    */
+#define UE_VARIANT_PERSISTENT 3  /* one cooperative launch per chunk of steps, timed grid     */
+                                 /* barriers between half-steps; FP32                         */
 
 #define UE_RHO_GIVEN 0
 #define UE_RHO_POWER 1
@@ -91,6 +93,8 @@ typedef struct ue_options {
     int32_t reserved1;
     const float* mlp_params;/* UE_DT_LEARNED: host array of UE_MLP_PARAMS floats             */
     double learned_margin; /* UE_DT_LEARNED: accept rho_hat in [margin*rho_lo, rho_hi] (1.05)*/
+    int32_t timeout_ms;    /* UE_VARIANT_PERSISTENT: grid-barrier wait limit (default 2000)  */
+    int32_t test_skip_cta; /* UE_VARIANT_PERSISTENT, tests only: this CTA never arrives (-1) */
 } ue_options;
 
 typedef struct ue_stats_t {
@@ -170,7 +174,8 @@ int ue_energy(ue_mesh* m, double* W, void* stream);
 
 /* Watchdog state (synchronous): *W = energy at the last check, *flag = 0 ok, 1 non-finite
  * energy, 2 energy grew by more than watchdog_growth between two checks.  Returns
- * UE_ERR_UNSTABLE when the flag is set.  ue_write_fields re-arms the watchdog. */
+ * UE_ERR_UNSTABLE when the flag is set, UE_ERR_TIMEOUT (flag 3) when a grid barrier of the
+ * persistent variant ran out of time.  ue_write_fields re-arms both. */
 int ue_check(ue_mesh* m, double* W, int32_t* flag);
 
 /* Step counter used by the source time t = (n + 1/2) dt (checkpoint / resume). */
@@ -196,23 +201,24 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
 
 /* Learned spectral radius (device pointers, caller-owned; the paper's eq. 20 sets dt from the
  * highest mode, which the network predicts per triangle).
- * ue_rho_features: X[12*n_tris] (float, stored triangle order) and logS[n_tris] of a built mesh.
+ * ue_rho_features: X[12*n_tris] (float, stored triangle order) and base[n_tris] = log sqrt(K_jj),
+ *   K = -L_E L_B, of a built mesh; log rho_hat = max_j (z_j + base_j).
  * ue_mlp_forward: z[n] for rows X[12*n]; bf16 = 1 tensor cores (BF16 in, FP32 accumulate),
  *   0 = FP32 debug path.  params: UE_MLP_PARAMS floats on the device.
  * ue_mlp_backward: grad[UE_MLP_PARAMS] = sum over m rows of dz[i] * dz_i/dparams for rows[i]
  *   (same rounding as the forward); work holds m * UE_MLP_PARAMS floats.
  * ue_adam: one Adam step (t >= 1) on n floats.
- * ue_seg_argmax: per segment s of rows [off[s], off[s+1]): best = max (z - logS/2), arg.
+ * ue_seg_argmax: per segment s of rows [off[s], off[s+1]): best = max (z + base), arg.
  * ue_rho_loss: dz[s] = 2 (best[s] - target[s]), loss[s] = (best[s] - target[s])^2.
  * All asynchronous on `stream`. */
-int ue_rho_features(ue_mesh* m, float* X, float* logS, void* stream);
+int ue_rho_features(ue_mesh* m, float* X, float* base, void* stream);
 int ue_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16, float* z,
                    void* stream);
 int ue_mlp_backward(const float* params, const float* X, const int64_t* rows, const float* dz,
                     int64_t m, int32_t bf16, float* work, float* grad, void* stream);
 int ue_adam(float* params, const float* grad, float* m1, float* m2, int32_t n, float lr,
             float beta1, float beta2, float eps, int32_t t, void* stream);
-int ue_seg_argmax(const float* z, const float* logS, const int64_t* off, int32_t n_seg,
+int ue_seg_argmax(const float* z, const float* base, const int64_t* off, int32_t n_seg,
                   float* best, int64_t* arg, void* stream);
 int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz, float* loss,
                 void* stream);

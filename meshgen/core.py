@@ -341,7 +341,25 @@ class _Quads:
 
 
 def graded_square(h_min: float, h_max: float, grade: float = 0.0, holes=(), jitter: float = 0.2,
-                  dual_floor: float = 0.005, seed: int = 0, repair_rounds: int = 200) -> MeshArrays:
+                  dual_floor: float = 0.005, seed: int = 0, repair_rounds: int = 200,
+                  attempts: int = 8) -> MeshArrays:
+    """Graded Delaunay mesh of the unit square around convex polygonal holes (see
+    ``_graded_square_once``).  A draw whose repair cannot reach a positive margin everywhere is
+    discarded and redrawn with the next seed (seed + 1, seed + 2, ...)."""
+    last = None
+    for a in range(attempts):
+        try:
+            m = _graded_square_once(h_min, h_max, grade, holes, jitter, dual_floor, seed + a,
+                                    repair_rounds)
+            m.info["attempt"] = a
+            return m
+        except RuntimeError as e:
+            last = e
+    raise last
+
+
+def _graded_square_once(h_min: float, h_max: float, grade: float = 0.0, holes=(), jitter: float = 0.2,
+                        dual_floor: float = 0.005, seed: int = 0, repair_rounds: int = 200) -> MeshArrays:
     """Graded Delaunay mesh of the unit square around convex polygonal holes.
 
     Target spacing h(x) = clip(h_min + grade * dist(x, holes), h_min, h_max) (h_max

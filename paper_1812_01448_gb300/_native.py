@@ -15,7 +15,7 @@ UE_PREC_FP32, UE_PREC_FP64 = 0, 1
 UE_DT_GIVEN, UE_DT_POWER, UE_DT_LEARNED = 0, 1, 2
 UE_RHO_GIVEN, UE_RHO_POWER, UE_RHO_LEARNED, UE_RHO_POWER_FALLBACK = 0, 1, 2, 3
 UE_MLP_PARAMS = 5057
-UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED = 1, 2
+UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED, UE_VARIANT_PERSISTENT = 1, 2, 3
 UE_STATIC_MAX_TRIS, UE_STATIC_MAX_EDGES = 1 << 18, 1 << 19
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -29,7 +29,8 @@ class Options(C.Structure):
                 ("tb_threads", C.c_int32), ("dt", C.c_double),
                 ("safety", C.c_double), ("watchdog_growth", C.c_double),
                 ("watchdog_every", C.c_int32), ("reserved1", C.c_int32),
-                ("mlp_params", C.c_void_p), ("learned_margin", C.c_double)]
+                ("mlp_params", C.c_void_p), ("learned_margin", C.c_double),
+                ("timeout_ms", C.c_int32), ("test_skip_cta", C.c_int32)]
 
 
 class Stats(C.Structure):

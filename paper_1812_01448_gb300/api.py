@@ -170,10 +170,11 @@ class Mesh:
         return w.value
 
     def check(self):
-        """(ok, energy at last check, flag); ok is False when the watchdog flagged the run."""
+        """(ok, energy at last check, flag); ok is False when the watchdog flagged the run
+        (flag 1 or 2) or a grid barrier of the persistent variant timed out (flag 3)."""
         w, f = C.c_double(), C.c_int32()
         rc = N.lib().ue_check(self._h, C.byref(w), C.byref(f))
-        if rc not in (0, -7):
+        if rc not in (0, -7, -8):
             N.check(rc, "ue_check")
         return rc == 0, w.value, f.value
 
@@ -204,10 +205,10 @@ class Mesh:
                 "ue_get_geometry")
         return dict(O=O, S=S, elen=le, d=d)
 
-    def rho_features(self, X, logS, stream=None):
+    def rho_features(self, X, base, stream=None):
         """Learned-rho features (ue_rho_features) into CUDA tensors X [n_tris, 12] float32 and
-        logS [n_tris] float32, stored triangle order."""
-        N.check(N.lib().ue_rho_features(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(logS.data_ptr()),
+        base [n_tris] float32 (log sqrt K_jj), stored triangle order."""
+        N.check(N.lib().ue_rho_features(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(base.data_ptr()),
                                         _stream(stream)), "ue_rho_features")
 
     def profile_steps(self, n: int, stream=None):
@@ -280,8 +281,8 @@ def adam(params, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, bet
                             beta2, eps, int(t), _stream(stream)), "ue_adam")
 
 
-def seg_argmax(z, logS, off, best, arg, stream=None):
-    N.check(N.lib().ue_seg_argmax(_p(z), _p(logS), _p(off), int(off.shape[0] - 1), _p(best), _p(arg),
+def seg_argmax(z, base, off, best, arg, stream=None):
+    N.check(N.lib().ue_seg_argmax(_p(z), _p(base), _p(off), int(off.shape[0] - 1), _p(best), _p(arg),
                                   _stream(stream)), "ue_seg_argmax")
 
 

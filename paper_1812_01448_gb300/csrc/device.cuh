@@ -85,6 +85,11 @@ cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
 cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int gbase,
                       cudaStream_t s);
 
+// Persistent cooperative step (kernels_persistent.cu).
+int persistent_grid(int device);
+cudaError_t launch_persistent(const DevMesh& m, int n_steps, unsigned* sync, int* err,
+                              long long budget, int skip_cta, int grid, cudaStream_t s);
+
 // Launchers (kernels_step.cu).
 // g(t) table for the next `count` steps (no-op without a source).
 cudaError_t launch_gtab(const DevMesh& m, int count, cudaStream_t s);
@@ -123,7 +128,7 @@ cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const doubl
 int mlp_n_params();
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                             const int2* rl, const double* elen, const double* d, const double* S,
-                            int64_t n_t, int64_t n_ei, float* X, float* logS, double* kdiag,
+                            int64_t n_t, int64_t n_ei, float* X, float* base, double* kdiag,
                             double* gersh, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, int bf16, float* z,
                                cudaStream_t s);
@@ -131,7 +136,7 @@ cudaError_t launch_mlp_backward(const float* P, const float* X, const int64_t* r
                                 int64_t m, int bf16, float* work, float* grad, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1,
                         float b2, float eps, int t, cudaStream_t s);
-cudaError_t launch_seg_argmax(const float* z, const float* logS, const int64_t* off, int n_seg,
+cudaError_t launch_seg_argmax(const float* z, const float* base, const int64_t* off, int n_seg,
                               float* best, int64_t* arg, cudaStream_t s);
 cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, float* dz,
                             float* loss, cudaStream_t s);

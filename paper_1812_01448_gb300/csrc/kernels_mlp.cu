@@ -1,10 +1,15 @@
+// Features (per triangle, stored order; lengths over sqrt(S_j), ratios as logarithms):
+// angles opposite the three edges, log(|e_q|/sqrt S), log(d_q/sqrt S) (4 on a boundary edge),
+// log(S_neighbour/S) (0 on a boundary edge).
+//
 // Learned spectral radius: features, the 12-64-64-1 MLP (forward on BF16 tensor cores with
 // FP32 accumulation, or an FP32 debug path), its backward pass on the argmax rows, Adam, the
 // per-mesh max aggregation, and the certified bracket used to accept a prediction.
 //
 // The paper fixes dt by the highest mode, dt < 2/omega_max (eq. 20), found by the "complex
-// time" power iteration (Section 2).  The network predicts z_j per triangle from scale-free
-// geometry; rho_hat = max_j exp(z_j)/sqrt(S_j).  A prediction is used only inside the bracket
+// time" power iteration (Section 2).  The network predicts a correction z_j per triangle from
+// scale-free geometry on top of base_j = log sqrt(K_jj) (K = -L_E L_B): rho_hat =
+// max_j exp(z_j + base_j).  A prediction is used only inside the bracket
 // [1.05 rho_lo, rho_hi]: rho_lo from max_j K_jj and a Rayleigh quotient of K^5 delta_j* near
 // the argmax triangle, rho_hi from Gershgorin on S^{1/2} K S^{-1/2} (K = -L_E L_B).
 //
@@ -33,7 +38,7 @@ __global__ void k_features(const double* __restrict__ xy, const int32_t* __restr
                            const int32_t* __restrict__ code, const int2* __restrict__ rl,
                            const double* __restrict__ elen, const double* __restrict__ d,
                            const double* __restrict__ S, int64_t n_t, int64_t n_ei,
-                           float* __restrict__ X, float* __restrict__ logS,
+                           float* __restrict__ X, float* __restrict__ base,
                            double* __restrict__ kdiag, double* __restrict__ gersh) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_t) return;
@@ -51,24 +56,24 @@ __global__ void k_features(const double* __restrict__ xy, const int32_t* __restr
         const int a = q, b = (q + 1) % 3, o = (q + 2) % 3;
         const double ux = px[a] - px[o], uy = py[a] - py[o], vx = px[b] - px[o], vy = py[b] - py[o];
         f[q] = (float)atan2(fabs(ux * vy - uy * vx), ux * vx + uy * vy);
-        f[3 + q] = (float)(hypot(px[b] - px[a], py[b] - py[a]) * rs);
+        f[3 + q] = (float)log(hypot(px[b] - px[a], py[b] - py[a]) * rs);
         const int c = code[3 * j + q];
         const int64_t k = c >> 1;
         if (k < n_ei) {
             const int2 e = rl[k];
             const int64_t nb = e.x == j ? e.y : e.x;
             const double w = elen[k] / d[k];
-            f[6 + q] = (float)(d[k] * rs);
-            f[9 + q] = (float)(S[nb] / Sj);
+            f[6 + q] = (float)log(d[k] * rs);
+            f[9 + q] = (float)log(S[nb] / Sj);
             kd += w;
             off += w / sqrt(Sj * S[nb]);
         } else {
-            f[6 + q] = 0.f;
-            f[9 + q] = 1.f;
+            f[6 + q] = 4.f;    // boundary: a dual so long the edge adds nothing to K
+            f[9 + q] = 0.f;
         }
     }
     for (int i = 0; i < kD; ++i) X[j * kD + i] = f[i];
-    logS[j] = (float)log(Sj);
+    base[j] = kd > 0.0 ? (float)(0.5 * log(kd / Sj)) : -1e30f;   // log sqrt(K_jj)
     kdiag[j] = kd / Sj;
     gersh[j] = kd / Sj + off;
 }
@@ -260,8 +265,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// Per segment (mesh): best = max_j (z_j - logS_j / 2) and its row (first on ties).
-__global__ void k_seg_argmax(const float* __restrict__ z, const float* __restrict__ logS,
+// Per segment (mesh): best = max_j (z_j + base_j) and its row (first on ties).
+__global__ void k_seg_argmax(const float* __restrict__ z, const float* __restrict__ base,
                              const int64_t* __restrict__ off, int n_seg, float* __restrict__ best,
                              int64_t* __restrict__ arg) {
     const int s = blockIdx.x;
@@ -271,7 +276,7 @@ __global__ void k_seg_argmax(const float* __restrict__ z, const float* __restric
     float v = -INFINITY;
     int64_t a = -1;
     for (int64_t j = off[s] + threadIdx.x; j < off[s + 1]; j += blockDim.x) {
-        const float x = z[j] - 0.5f * logS[j];
+        const float x = z[j] + base[j];
         if (x > v) {
             v = x;
             a = j;
@@ -416,10 +421,10 @@ int mlp_n_params() { return kNParams; }
 
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                             const int2* rl, const double* elen, const double* d, const double* S,
-                            int64_t n_t, int64_t n_ei, float* X, float* logS, double* kdiag,
+                            int64_t n_t, int64_t n_ei, float* X, float* base, double* kdiag,
                             double* gersh, cudaStream_t s) {
     k_features<<<(unsigned)((n_t + 255) / 256), 256, 0, s>>>(xy, tri_nodes, tri_code, rl, elen, d, S,
-                                                             n_t, n_ei, X, logS, kdiag, gersh);
+                                                             n_t, n_ei, X, base, kdiag, gersh);
     return cudaGetLastError();
 }
 
@@ -452,10 +457,10 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_argmax(const float* z, const float* logS, const int64_t* off, int n_seg,
+cudaError_t launch_seg_argmax(const float* z, const float* base, const int64_t* off, int n_seg,
                               float* best, int64_t* arg, cudaStream_t s) {
     if (n_seg <= 0) return cudaSuccess;
-    k_seg_argmax<<<n_seg, 256, 0, s>>>(z, logS, off, n_seg, best, arg);
+    k_seg_argmax<<<n_seg, 256, 0, s>>>(z, base, off, n_seg, best, arg);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,13 @@ struct ue_mesh {
     int watchdog_every = 0;
     double watchdog_growth = 10.0;
     int64_t since_check = 0;
+
+    // persistent variant: {count, gen} barrier words, error word, wait budget (cycles)
+    unsigned* p_sync = nullptr;
+    int* p_err = nullptr;
+    long long p_budget = 0;
+    int p_skip = -1;
+    int p_grid = 0;
 };
 
 namespace {
@@ -523,6 +530,8 @@ void ue_options_default(ue_options* o) {
     o->watchdog_every = 0;
     o->mlp_params = nullptr;
     o->learned_margin = 1.05;
+    o->timeout_ms = 2000;
+    o->test_skip_cta = -1;
 }
 
 const char* ue_last_error(void) { return g_err.c_str(); }
@@ -574,8 +583,11 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         return fail(UE_ERR_ARG, "power iteration needs iters >= 1 and safety > 0");
     if (o.dt_mode == UE_DT_LEARNED && (!o.mlp_params || !(o.learned_margin >= 1.0)))
         return fail(UE_ERR_ARG, "learned dt needs mlp_params and learned_margin >= 1");
-    if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN && o.variant != UE_VARIANT_BLOCKED)
+    if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN && o.variant != UE_VARIANT_BLOCKED &&
+        o.variant != UE_VARIANT_PERSISTENT)
         return fail(UE_ERR_ARG, "unknown variant");
+    if (o.variant == UE_VARIANT_PERSISTENT && (o.precision != UE_PREC_FP32 || o.timeout_ms < 1))
+        return fail(UE_ERR_ARG, "the persistent variant is FP32 only and needs timeout_ms >= 1");
     if (o.variant == UE_VARIANT_BLOCKED) {
         if (o.precision != UE_PREC_FP32) return fail(UE_ERR_ARG, "the blocked variant is FP32 only");
         if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs UE_REORDER_KD");
@@ -673,6 +685,18 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (m->variant == UE_VARIANT_BLOCKED) {
         int trc = upload_tiles(m, s);
         if (trc != UE_OK) return trc;
+    }
+    if (m->variant == UE_VARIANT_PERSISTENT) {
+        if (!alloc_into(m, m->p_sync, 2, 4, s) || !alloc_into(m, m->p_err, 1, 4, s))
+            return fail(UE_ERR_ALLOC, "persistent barrier words");
+        UE_CUDA(cudaMemsetAsync(m->p_sync, 0, 8, s));
+        UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
+        int dev = 0, khz = 0;
+        UE_CUDA(cudaGetDevice(&dev));
+        UE_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+        m->p_budget = (long long)o.timeout_ms * (long long)khz;   // kHz * ms = cycles
+        m->p_skip = o.test_skip_cta;
+        m->p_grid = ue::persistent_grid(dev);
     }
     UE_CUDA(cudaStreamSynchronize(s));
     m->steps_done = 0;
@@ -926,6 +950,7 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
         const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
         UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
         m->since_check = 0;
+        if (m->p_err) UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
     }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
@@ -936,6 +961,22 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
     if (n < 0) return fail(UE_ERR_ARG, "n_steps < 0");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t left = n;
+    if (m->variant == UE_VARIANT_PERSISTENT) {
+        int64_t launched = 0;
+        while (left > 0) {
+            const int batch = (int)(left < m->dm.gtab_size ? left : m->dm.gtab_size);
+            UE_CUDA(ue::launch_gtab(m->dm, batch, s));
+            UE_CUDA(cudaMemsetAsync(m->p_sync, 0, 8, s));
+            UE_CUDA(ue::launch_persistent(m->dm, batch, m->p_sync, m->p_err, m->p_budget, m->p_skip,
+                                          m->p_grid, s));
+            launched += 1 + (m->dm.n_src > 0 ? 1 : 0);
+            left -= batch;
+            UE_CUDA(watchdog_tick(m, batch, s, &launched));
+        }
+        m->steps_done += n;
+        m->launches += launched;
+        return UE_OK;
+    }
     if (m->variant == UE_VARIANT_BLOCKED) {
         const int64_t k = m->block_depth;
         const int64_t chunk = (int64_t)tb_chunk_launches(m) * k;
@@ -1033,6 +1074,14 @@ int ue_check(ue_mesh* m, double* W, int32_t* flag) {
     UE_CUDA(cudaMemcpy(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost));
     if (W) *W = wd[1];
     if (flag) *flag = (int32_t)wd[3];
+    if (m->p_err) {
+        int e = 0;
+        UE_CUDA(cudaMemcpy(&e, m->p_err, 4, cudaMemcpyDeviceToHost));
+        if (e) {
+            if (flag) *flag = 3;
+            return fail(UE_ERR_TIMEOUT, "a grid barrier of the persistent kernel ran out of time");
+        }
+    }
     if (wd[3] != 0.0)
         return fail(UE_ERR_UNSTABLE, std::string("energy watchdog: ") +
                                          (wd[3] == 1.0 ? "non-finite energy" : "energy growth beyond the limit"));
@@ -1092,14 +1141,14 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
     return UE_OK;
 }
 
-int ue_rho_features(ue_mesh* m, float* X, float* logS, void* stream) {
-    if (!m || !m->built || !X || !logS) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+int ue_rho_features(ue_mesh* m, float* X, float* base, void* stream) {
+    if (!m || !m->built || !X || !base) return fail(UE_ERR_ARG, "geometry not built or NULL output");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nt = m->hm.n_tris;
     double *kd = nullptr, *ge = nullptr;
     if (!alloc_into(m, kd, nt, 8, s) || !alloc_into(m, ge, nt, 8, s)) return fail(UE_ERR_ALLOC, "feature work space");
     UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
-                                m->d_S, nt, m->hm.n_ei, X, logS, kd, ge, s));
+                                m->d_S, nt, m->hm.n_ei, X, base, kd, ge, s));
     UE_CUDA(cudaStreamSynchronize(s));
     dev_release(m, kd, s);
     dev_release(m, ge, s);
@@ -1126,10 +1175,10 @@ int ue_adam(float* params, const float* grad, float* m1, float* m2, int32_t n, f
     return UE_OK;
 }
 
-int ue_seg_argmax(const float* z, const float* logS, const int64_t* off, int32_t n_seg, float* best,
+int ue_seg_argmax(const float* z, const float* base, const int64_t* off, int32_t n_seg, float* best,
                   int64_t* arg, void* stream) {
-    if (!z || !logS || !off || !best || !arg || n_seg < 0) return fail(UE_ERR_ARG, "bad arguments");
-    UE_CUDA(ue::launch_seg_argmax(z, logS, off, n_seg, best, arg, (cudaStream_t)stream));
+    if (!z || !base || !off || !best || !arg || n_seg < 0) return fail(UE_ERR_ARG, "bad arguments");
+    UE_CUDA(ue::launch_seg_argmax(z, base, off, n_seg, best, arg, (cudaStream_t)stream));
     return UE_OK;
 }
 

@@ -26,12 +26,13 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rho_mlp.npy"
 
 
 def init_params(seed: int = 0) -> np.ndarray:
-    """Seeded He initialisation (host), b3 = log 3 (a typical rho * sqrt(S))."""
+    """Seeded He initialisation (host).  The network is a correction on top of log sqrt(K_jj):
+    w3 starts small and b3 at log 1.25, a typical rho / sqrt(max K_jj)."""
     rng = np.random.default_rng(seed)
     W1 = rng.standard_normal((H, D)) * math.sqrt(2.0 / D)
     W2 = rng.standard_normal((H, H)) * math.sqrt(2.0 / H)
-    w3 = rng.standard_normal(H) * math.sqrt(1.0 / H) * 0.1
-    p = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), w3, [math.log(3.0)]])
+    w3 = rng.standard_normal(H) * math.sqrt(1.0 / H) * 0.01
+    p = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), w3, [math.log(1.25)]])
     return p.astype(np.float32)
 
 
@@ -43,7 +44,7 @@ def load_weights(path: str = WEIGHTS) -> np.ndarray:
 
 
 def build_corpus(meshes, stream=None, power_iters: int = 200):
-    """Features, log S, segment offsets and log rho_PI labels of a list of MeshArrays."""
+    """Features, base terms, segment offsets and log rho_PI labels of a list of MeshArrays."""
     import torch
     Xs, Ls, offs, labels = [], [], [0], []
     for ms in meshes:
@@ -58,7 +59,7 @@ def build_corpus(meshes, stream=None, power_iters: int = 200):
         Ls.append(L)
         offs.append(offs[-1] + X.shape[0])
         labels.append(math.log(rho))
-    return dict(X=torch.cat(Xs), logS=torch.cat(Ls),
+    return dict(X=torch.cat(Xs), base=torch.cat(Ls),
                 off=torch.tensor(offs, dtype=torch.int64, device="cuda"),
                 target=torch.tensor(labels, dtype=torch.float32, device="cuda"))
 
@@ -67,7 +68,7 @@ def train(corpus, epochs: int = 2000, lr: float = 3e-3, seed: int = 0, bf16: boo
           stream=None, params0: np.ndarray | None = None):
     """Adam on the mean over meshes of (log rho_hat - log rho_PI)^2.  Returns (params, losses)."""
     import torch
-    X, logS, off, target = corpus["X"], corpus["logS"], corpus["off"], corpus["target"]
+    X, base, off, target = corpus["X"], corpus["base"], corpus["off"], corpus["target"]
     M = target.shape[0]
     p = torch.from_numpy(params0 if params0 is not None else init_params(seed)).cuda()
     m1 = torch.zeros_like(p)
@@ -82,7 +83,7 @@ def train(corpus, epochs: int = 2000, lr: float = 3e-3, seed: int = 0, bf16: boo
     hist = []
     for t in range(1, epochs + 1):
         mlp_forward(p, X, z, bf16, stream)
-        seg_argmax(z, logS, off, best, arg, stream)
+        seg_argmax(z, base, off, best, arg, stream)
         rho_loss(best, target, dz, loss, stream)
         mlp_backward(p, X, arg, dz, g, work, bf16, stream)
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (t - 1) / epochs))   # cosine decay

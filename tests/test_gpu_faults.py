@@ -105,3 +105,23 @@ def test_allocator_returning_null_is_reported(ue, small):
     assert L.ue_geometry_build(h, C.byref(o), None) == 0
     L.ue_mesh_free(h)
     assert not state["live"]
+
+
+def test_persistent_barrier_timeout_is_reported(ue, small):
+    """A CTA that never reaches the grid barrier (test hook): the others give up after
+    timeout_ms, the launch ends, UE_ERR_TIMEOUT is reported, and the context stays usable."""
+    ms, ops, rho = small
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=0.5 / rho, variant=ue.UE_VARIANT_PERSISTENT,
+                     timeout_ms=50, test_skip_cta=3)
+    m.write_fields(B=np.ones(m.n_tris))
+    m.step_n(5)
+    ok, W, flag = m.check()
+    assert not ok and flag == 3
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=0.5 / rho, variant=ue.UE_VARIANT_PERSISTENT)
+    m.write_fields(B=np.ones(m.n_tris))
+    m.step_n(5)
+    assert m.check() [0]
+    E, B, _ = m.read_fields()
+    assert np.all(np.isfinite(B))
+    m.close()

@@ -308,3 +308,29 @@ def test_batch_is_bit_identical_to_single_meshes(ue, variant):
     b.close()
     for m in singles:
         m.close()
+
+
+@pytest.mark.parametrize("plasma", [False, True])
+def test_persistent_is_bit_identical_to_plain(ue, plasma):
+    """One cooperative launch per chunk with timed grid barriers between the half-steps gives
+    the plain kernels' results bit for bit."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 50)
+    dt = 0.45 / rho
+    out = []
+    for variant in (ue.UE_VARIANT_PLAIN, ue.UE_VARIANT_PERSISTENT):
+        m = ue.Mesh(ms.xy, ms.tris)
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=variant)
+        if plasma:
+            m.set_plasma(dens, 0.01 * w0)
+        m.set_source(ids, amp, w0, 0.0, 0.05)
+        m.write_fields(B=np.sin(5 * ms.xy[ms.tris].mean(axis=1)[:, 1]))
+        m.step_n(101)
+        assert m.check()[0]
+        out.append(m.read_fields(j=plasma) + (m.get_step(),))
+        m.close()
+    (Ea, Ba, Ja, sa), (Eb, Bb, Jb, sb) = out
+    assert sa == sb == 101
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ba, Bb)
+    if plasma:
+        assert np.array_equal(Ja, Jb)

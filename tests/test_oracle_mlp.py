@@ -12,30 +12,46 @@ def _stored(ms):
     g = geometry.Geometry(m)
     t = rcm.device_tables(m, np.arange(m.n_tris))
     d = g.d[t["edge_caller"]]
-    X, S = mlp.features(ms.xy, t["tri_nodes"], t["tri_code"], t["n_ei"], t["edge_tri"], d)
-    return X, S, t
+    X, S, base = mlp.features(ms.xy, t["tri_nodes"], t["tri_code"], t["n_ei"], t["edge_tri"], d)
+    return X, S, t, base
 
 
 def test_equilateral_features_closed_form():
     ms = meshgen.equilateral_lattice(6, h=0.3)
-    X, S, t = _stored(ms)
+    X, S, t, base = _stored(ms)
     np.testing.assert_allclose(X[:, 0:3], math.pi / 3, rtol=1e-12)
     e_over = math.sqrt(4 / math.sqrt(3))                 # |e| / sqrt(sqrt(3)/4 |e|^2)
-    np.testing.assert_allclose(X[:, 3:6], e_over, rtol=1e-12)
+    np.testing.assert_allclose(X[:, 3:6], math.log(e_over), rtol=1e-12)
     np.testing.assert_allclose(S, math.sqrt(3) / 4 * 0.09, rtol=1e-12)
     inner = (t["tri_code"] >> 1) < t["n_ei"]
-    np.testing.assert_allclose(X[:, 6:9][inner], e_over / math.sqrt(3), rtol=1e-11)
-    assert np.all(X[:, 6:9][~inner] == 0)
-    np.testing.assert_allclose(X[:, 9:12], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(X[:, 6:9][inner], math.log(e_over / math.sqrt(3)), rtol=1e-11)
+    assert np.all(X[:, 6:9][~inner] == mlp.BOUNDARY_LOG_D)
+    np.testing.assert_allclose(X[:, 9:12], 0.0, atol=1e-12)
+    # K_jj = (1/S) sum over interior edges of |e|/d = n_inner sqrt(3) / S
+    n_inner = inner.sum(axis=1)
+    ok = n_inner > 0
+    np.testing.assert_allclose(base[ok], 0.5 * np.log(n_inner[ok] * math.sqrt(3) / S[ok]), rtol=1e-12)
 
 
 def test_features_are_scale_free_and_angles_sum_to_pi():
     ms = meshgen.cavity_te11_mesh()
-    X, S, _ = _stored(ms)
+    X, S, _, base = _stored(ms)
     ms2 = meshgen.MeshArrays(ms.xy * 7.5, ms.tris, ms.h * 7.5, ms.boundary_node, {})
-    X2, S2, _ = _stored(ms2)
+    X2, S2, _, base2 = _stored(ms2)
     np.testing.assert_allclose(X2, X, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(base2, base - math.log(7.5), rtol=1e-12)   # K scales as 1/L^2
     np.testing.assert_allclose(X[:, 0:3].sum(1), math.pi, rtol=1e-12)
+
+
+def test_base_term_is_a_certified_lower_bound():
+    """max_j exp(2 base_j) = max_j K_jj <= rho(M)^2 (Rayleigh quotient of a unit vector)."""
+    from oracle import operators, spectral
+    ms = meshgen.cavity_lattice(17, 9, 1.0, 0.5, seed=7)
+    X, S, t, base = _stored(ms)
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    rho = spectral.dense_rho(ops)
+    assert math.exp(2 * base.max()) <= rho ** 2 * (1 + 1e-12)
+    np.testing.assert_allclose(np.sort(np.exp(2 * base)), np.sort(spectral.diag_K(ops)), rtol=1e-12)
 
 
 def test_forward_on_hand_set_weights():
@@ -77,16 +93,16 @@ def test_backward_matches_central_differences():
 
 def test_mesh_loss_gradient_matches_central_differences():
     ms = meshgen.cavity_te11_mesh()
-    X, S, _ = _stored(ms)
+    X, S, _, base = _stored(ms)
     p = mlp.init_params(5)
-    L, g = mlp.mesh_loss_grad(p, X, S, math.log(400.0))
+    L, g = mlp.mesh_loss_grad(p, X, base, math.log(400.0))
     rng = np.random.default_rng(1)
     h = 1e-6
     for i in rng.choice(mlp.N_PARAMS, 40, replace=False):
         e = np.zeros(mlp.N_PARAMS)
         e[i] = h
-        fd = (mlp.mesh_loss_grad(p + e, X, S, math.log(400.0))[0] -
-              mlp.mesh_loss_grad(p - e, X, S, math.log(400.0))[0]) / (2 * h)
+        fd = (mlp.mesh_loss_grad(p + e, X, base, math.log(400.0))[0] -
+              mlp.mesh_loss_grad(p - e, X, base, math.log(400.0))[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (i, fd, g[i])
 
 
