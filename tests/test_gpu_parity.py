@@ -185,29 +185,43 @@ def test_non_delaunay_mesh_is_rejected(ue):
     assert ei.value.code == -4
 
 
-@pytest.mark.slow
-def test_full_size_scatterer_window(ue):
-    """The benchmarked workload (~4M triangles, RCM, FP32, graph launches) over a 200-step
-    window with the line source, against the oracle on the whole mesh."""
+@pytest.fixture(scope="module")
+def scatterer_window():
+    """The benchmarked workload (~4M triangles) and the oracle's 200-step window from step 5000
+    (mid-pulse, so that the line source is far from zero)."""
     ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
     ops = _oracle(ms)
     ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, 2e-4)
     w0 = 2 * math.pi * 20
-    m = ue.Mesh(ms.xy, ms.tris)
-    m.geometry_build()
-    dt, rho, _ = m.get_dt()
-    m.set_source(ids, amp, w0, 0.1, 0.05)
-    m.set_step(5000)     # mid-pulse, so that the source is far from zero
-    m.step_n(200)
-    E, B, _ = m.read_fields()
-    m.close()
+    rho, _ = spectral.power_iteration(ops, 200)
+    dt = 1.0 / rho
     src = lf.Source(ids, amp, w0, 0.1, 0.05)
     st = lf.initial_state(ops)
     st.n = 5000
     st = lf.run(ops, st, dt, 200, source=src)
-    eE, eB = rel_l2(E, ops.extend(st.E)), rel_l2(B, st.B)
-    print(f"scatterer n_t={ms.n_tris} 200 steps: rel L2 E {eE:.2e} B {eB:.2e}")
-    assert np.linalg.norm(st.B) > 0
+    return ms, ops, ids, amp, w0, dt, ops.extend(st.E), st.B
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_full_size_scatterer_window(ue, scatterer_window, variant):
+    """Full size in the bench's launch configurations (plain: RCM, graphs of 32 steps;
+    blocked: KD tiles of <= 2048, k = 8, 512 threads) against the oracle on the whole mesh."""
+    ms, ops, ids, amp, w0, dt, Eo, Bo = scatterer_window
+    blocked = variant == "blocked"
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
+                tile_tris=2048)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt,
+                     variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
+                     block_depth=8)
+    m.set_source(ids, amp, w0, 0.1, 0.05)
+    m.set_step(5000)
+    m.step_n(200)
+    E, B, _ = m.read_fields()
+    m.close()
+    eE, eB = rel_l2(E, Eo), rel_l2(B, Bo)
+    print(f"scatterer {variant} n_t={ms.n_tris} 200 steps: rel L2 E {eE:.2e} B {eB:.2e}")
+    assert np.linalg.norm(Bo) > 0
     assert eE <= 1e-4 and eB <= 1e-4
 
 
