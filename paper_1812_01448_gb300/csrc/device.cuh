@@ -142,6 +142,13 @@ cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, f
                             float* loss, cudaStream_t s);
 cudaError_t launch_max(const double* a, int64_t n, double* part, int n_part, double* out,
                        cudaStream_t s);
+// Fused learned-rho inference: part needs 4 * rho_infer_blocks() doubles; out[4] = {log rho_hat,
+// argmax row, max K_jj, max Gershgorin bound}, *arg = the argmax row.
+int rho_infer_blocks();
+cudaError_t launch_rho_infer(const float* P, const double* xy, const int32_t* tri_nodes,
+                             const int32_t* tri_code, const int2* rl, const double* elen,
+                             const double* d, const double* S, int64_t n_t, int64_t n_ei,
+                             double* part, double* out, int64_t* arg, cudaStream_t s);
 cudaError_t launch_local_rq(const int32_t* code, const int2* rl, const double* elen, const double* d,
                             const double* S, int64_t n_ei, const int64_t* j0, double* out,
                             cudaStream_t s);

@@ -181,6 +181,200 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_bf16(const float* __restrict__ 
     }
 }
 
+// Fused inference for one mesh: features -> BF16 MLP -> z_j + base_j, with per-block maxima
+// of that score (and its row), of K_jj and of the Gershgorin row bound.  One warp handles 16
+// triangles at a time: lanes 0..15 build one triangle's features each (FP64 geometry) in
+// shared memory, then the warp runs the same tensor-core layers as k_mlp_fwd_bf16.  No
+// feature array is written.  part[4 * block] = {best score, row (as double), max K_jj, max
+// Gershgorin bound}.
+__device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
+                                                  const int32_t* __restrict__ tn,
+                                                  const int32_t* __restrict__ code,
+                                                  const int2* __restrict__ rl,
+                                                  const double* __restrict__ elen,
+                                                  const double* __restrict__ d,
+                                                  const double* __restrict__ S, int64_t j,
+                                                  int64_t n_ei, float* f, double& kdiag,
+                                                  double& gersh) {
+    double px[3], py[3];
+    for (int q = 0; q < 3; ++q) {
+        const int v = tn[3 * j + q];
+        px[q] = xy[2 * v];
+        py[q] = xy[2 * v + 1];
+    }
+    const double Sj = S[j];
+    const double rs = 1.0 / sqrt(Sj);
+    double kd = 0.0, off = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        const int a = q, b = (q + 1) % 3, o = (q + 2) % 3;
+        const double ux = px[a] - px[o], uy = py[a] - py[o], vx = px[b] - px[o], vy = py[b] - py[o];
+        f[q] = (float)atan2(fabs(ux * vy - uy * vx), ux * vx + uy * vy);
+        f[3 + q] = (float)log(hypot(px[b] - px[a], py[b] - py[a]) * rs);
+        const int c = code[3 * j + q];
+        const int64_t k = c >> 1;
+        if (k < n_ei) {
+            const int2 e = rl[k];
+            const int64_t nb = e.x == j ? e.y : e.x;
+            const double w = elen[k] / d[k];
+            f[6 + q] = (float)log(d[k] * rs);
+            f[9 + q] = (float)log(S[nb] / Sj);
+            kd += w;
+            off += w / sqrt(Sj * S[nb]);
+        } else {
+            f[6 + q] = 4.f;
+            f[9 + q] = 0.f;
+        }
+    }
+    kdiag = kd / Sj;
+    gersh = kd / Sj + off;
+    f[12] = kd > 0.0 ? (float)(0.5 * log(kd / Sj)) : -1e30f;   // base = log sqrt(K_jj)
+}
+
+__global__ void __launch_bounds__(128) k_rho_infer(const float* __restrict__ P,
+                                                   const double* __restrict__ xy,
+                                                   const int32_t* __restrict__ tn,
+                                                   const int32_t* __restrict__ code,
+                                                   const int2* __restrict__ rl,
+                                                   const double* __restrict__ elen,
+                                                   const double* __restrict__ d,
+                                                   const double* __restrict__ S, int64_t n,
+                                                   int64_t n_ei, double* __restrict__ part) {
+    __shared__ __nv_bfloat16 w1[kH * kW1S];
+    __shared__ __nv_bfloat16 w2[kH * kW2S];
+    __shared__ float bias1[kH], bias2[kH], w3[kH];
+    __shared__ float feat[4][16][13];
+    __shared__ double red[4][4];
+    for (int i = threadIdx.x; i < kH * kW1S; i += blockDim.x) {
+        const int r = i / kW1S, c = i % kW1S;
+        w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH * kW2S; i += blockDim.x) {
+        const int r = i / kW2S, c = i % kW2S;
+        w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        bias1[i] = P[kOffB1 + i];
+        bias2[i] = P[kOffB2 + i];
+        w3[i] = P[kOffW3 + i];
+    }
+    const float b3 = P[kOffB3];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float (*F)[13] = feat[warp];
+    double best = -1e300, arg = -1.0, kmax = 0.0, gmax = 0.0;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile * 16 < n; tile += warps) {
+        if (lane < 16) {
+            const int64_t j = tile * 16 + lane;
+            if (j < n) {
+                double kd, ge;
+                triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, F[lane], kd, ge);
+                kmax = fmax(kmax, kd);
+                gmax = fmax(gmax, ge);
+            } else {
+                for (int i = 0; i < 12; ++i) F[lane][i] = 0.f;
+                F[lane][12] = -1e30f;
+            }
+        }
+        __syncwarp();
+        auto xv = [&](int r, int c) { return c < kD ? F[r][c] : 0.f; };
+        const uint32_t a0 = pack_bf16(xv(g, 2 * t), xv(g, 2 * t + 1));
+        const uint32_t a1 = pack_bf16(xv(g + 8, 2 * t), xv(g + 8, 2 * t + 1));
+        const uint32_t a2 = pack_bf16(xv(g, 2 * t + 8), xv(g, 2 * t + 9));
+        const uint32_t a3 = pack_bf16(xv(g + 8, 2 * t + 8), xv(g + 8, 2 * t + 9));
+        float h1[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + 2 * t;
+            h1[nt][0] = h1[nt][1] = h1[nt][2] = h1[nt][3] = 0.f;
+            const __nv_bfloat16* wr = w1 + (nt * 8 + g) * kW1S;
+            mma_bf16(h1[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
+                     *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
+            h1[nt][0] = fmaxf(h1[nt][0] + bias1[col], 0.f);
+            h1[nt][1] = fmaxf(h1[nt][1] + bias1[col + 1], 0.f);
+            h1[nt][2] = fmaxf(h1[nt][2] + bias1[col], 0.f);
+            h1[nt][3] = fmaxf(h1[nt][3] + bias1[col + 1], 0.f);
+        }
+        float h2[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const uint32_t c0 = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
+            const uint32_t c1 = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
+            const uint32_t c2 = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
+            const uint32_t c3 = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const __nv_bfloat16* wr = w2 + (nt * 8 + g) * kW2S + kt * 16;
+                mma_bf16(h2[nt], c0, c1, c2, c3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
+                         *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
+            }
+        }
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + 2 * t;
+            s0 += w3[col] * fmaxf(h2[nt][0] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][1] + bias2[col + 1], 0.f);
+            s1 += w3[col] * fmaxf(h2[nt][2] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][3] + bias2[col + 1], 0.f);
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (t == 0) {
+            const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+            const double v0 = (double)(s0 + b3 + F[g][12]), v1 = (double)(s1 + b3 + F[g + 8][12]);
+            if (r0 < n && v0 > best) { best = v0; arg = (double)r0; }
+            if (r1 < n && v1 > best) { best = v1; arg = (double)r1; }
+        }
+        __syncwarp();
+    }
+    // warp then block maxima (ties: smaller row)
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o), oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa >= 0 && (arg < 0 || oa < arg))) { best = ob; arg = oa; }
+        kmax = fmax(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    }
+    if (lane == 0) {
+        red[warp][0] = best;
+        red[warp][1] = arg;
+        red[warp][2] = kmax;
+        red[warp][3] = gmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 4; ++w) {
+            if (red[w][0] > red[0][0] || (red[w][0] == red[0][0] && red[w][1] >= 0 && (red[0][1] < 0 || red[w][1] < red[0][1]))) {
+                red[0][0] = red[w][0];
+                red[0][1] = red[w][1];
+            }
+            red[0][2] = fmax(red[0][2], red[w][2]);
+            red[0][3] = fmax(red[0][3], red[w][3]);
+        }
+        for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = red[0][i];
+    }
+}
+
+// out = {best score, row, max K_jj, max Gershgorin} over the block partials; row also as int64.
+__global__ void k_rho_reduce(const double* __restrict__ part, int nb, double* __restrict__ out,
+                             int64_t* __restrict__ arg) {
+    if (threadIdx.x != 0) return;
+    double b = -1e300, a = -1.0, k = 0.0, g = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double pb = part[4 * i], pa = part[4 * i + 1];
+        if (pb > b || (pb == b && pa >= 0 && (a < 0 || pa < a))) { b = pb; a = pa; }
+        k = fmax(k, part[4 * i + 2]);
+        g = fmax(g, part[4 * i + 3]);
+    }
+    out[0] = b;
+    out[1] = a;
+    out[2] = k;
+    out[3] = g;
+    *arg = (int64_t)a;
+}
+
 // FP32 debug forward: one thread per row, CUDA cores.
 __global__ void k_mlp_fwd_f32(const float* __restrict__ P, const float* __restrict__ X, int64_t n,
                               float* __restrict__ z) {
@@ -475,6 +669,18 @@ cudaError_t launch_max(const double* a, int64_t n, double* part, int n_part, dou
                        cudaStream_t s) {
     k_max_parts<<<n_part, 256, 0, s>>>(a, n, part);
     k_max_parts<<<1, 256, 0, s>>>(part, n_part, out);
+    return cudaGetLastError();
+}
+
+int rho_infer_blocks() { return 152 * 4; }
+
+cudaError_t launch_rho_infer(const float* P, const double* xy, const int32_t* tri_nodes,
+                             const int32_t* tri_code, const int2* rl, const double* elen,
+                             const double* d, const double* S, int64_t n_t, int64_t n_ei,
+                             double* part, double* out, int64_t* arg, cudaStream_t s) {
+    const int nb = rho_infer_blocks();
+    k_rho_infer<<<nb, 128, 0, s>>>(P, xy, tri_nodes, tri_code, rl, elen, d, S, n_t, n_ei, part);
+    k_rho_reduce<<<1, 32, 0, s>>>(part, nb, out, arg);
     return cudaGetLastError();
 }
 

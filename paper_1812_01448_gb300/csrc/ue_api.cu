@@ -408,41 +408,31 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
-// Learned rho: features, BF16 MLP, max aggregation, certified bracket (synchronous).
-// Sets m->rho_hat, m->rho_lo, m->rho_hi.
+// Learned rho: one fused pass (features -> BF16 MLP -> max of z + base, max K_jj, max
+// Gershgorin bound), then the local Rayleigh quotient near the argmax triangle (synchronous).
+// Sets m->rho_hat, m->rho_lo, m->rho_hi.  One small work allocation.
 int learned_rho(ue_mesh* m, const ue_options& o, cudaStream_t s) {
     const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
     const int np = ue::mlp_n_params();
-    const int n_part = 1024;
-    float *X = nullptr, *logS = nullptr, *z = nullptr, *P = nullptr, *best = nullptr;
-    double *kd = nullptr, *ge = nullptr, *part = nullptr, *res = nullptr;
-    int64_t *off = nullptr, *arg = nullptr;
-    if (!alloc_into(m, X, 12 * nt, 4, s) || !alloc_into(m, logS, nt, 4, s) || !alloc_into(m, z, nt, 4, s) ||
-        !alloc_into(m, P, np, 4, s) || !alloc_into(m, best, 1, 4, s) || !alloc_into(m, kd, nt, 8, s) ||
-        !alloc_into(m, ge, nt, 8, s) || !alloc_into(m, part, n_part, 8, s) || !alloc_into(m, res, 3, 8, s) ||
-        !alloc_into(m, off, 2, 8, s) || !alloc_into(m, arg, 1, 8, s))
-        return fail(UE_ERR_ALLOC, "learned dt work space");
-    const int64_t offh[2] = {0, nt};
+    const int nb = ue::rho_infer_blocks();
+    const size_t n_dbl = 4 * (size_t)nb + 8 + 1 + (np + 1) / 2;
+    double* w = nullptr;
+    if (!alloc_into(m, w, n_dbl, 8, s)) return fail(UE_ERR_ALLOC, "learned dt work space");
+    double* part = w;
+    double* out = part + 4 * nb;                 // 4 results + the RQ
+    int64_t* arg = reinterpret_cast<int64_t*>(out + 8);
+    float* P = reinterpret_cast<float*>(out + 9);
     UE_CUDA(cudaMemcpyAsync(P, o.mlp_params, 4 * np, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(off, offh, sizeof(offh), cudaMemcpyHostToDevice, s));
-    UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
-                                m->d_S, nt, nei, X, logS, kd, ge, s));
-    UE_CUDA(ue::launch_mlp_forward(P, X, nt, 1, z, s));
-    UE_CUDA(ue::launch_seg_argmax(z, logS, off, 1, best, arg, s));
-    UE_CUDA(ue::launch_max(kd, nt, part, n_part, res, s));
-    UE_CUDA(ue::launch_max(ge, nt, part, n_part, res + 1, s));
-    UE_CUDA(ue::launch_local_rq(m->d_tri_code, m->d_rl, m->d_elen, m->d_d, m->d_S, nei, arg, res + 2, s));
-    float bh = 0;
-    double rh[3] = {0, 0, 0};
-    UE_CUDA(cudaMemcpyAsync(&bh, best, 4, cudaMemcpyDeviceToHost, s));
-    UE_CUDA(cudaMemcpyAsync(rh, res, sizeof(rh), cudaMemcpyDeviceToHost, s));
+    UE_CUDA(ue::launch_rho_infer(P, m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen,
+                                 m->d_d, m->d_S, nt, nei, part, out, arg, s));
+    UE_CUDA(ue::launch_local_rq(m->d_tri_code, m->d_rl, m->d_elen, m->d_d, m->d_S, nei, arg, out + 4, s));
+    double rh[5] = {0, 0, 0, 0, 0};
+    UE_CUDA(cudaMemcpyAsync(rh, out, sizeof(rh), cudaMemcpyDeviceToHost, s));
     UE_CUDA(cudaStreamSynchronize(s));
-    for (void* p : {(void*)X, (void*)logS, (void*)z, (void*)P, (void*)best, (void*)kd, (void*)ge,
-                    (void*)part, (void*)res, (void*)off, (void*)arg})
-        dev_release(m, p, s);
-    m->rho_hat = std::exp((double)bh);
-    m->rho_lo = std::sqrt(std::max(rh[0], rh[2]));
-    m->rho_hi = std::sqrt(rh[1]);
+    dev_release(m, w, s);
+    m->rho_hat = std::exp(rh[0]);
+    m->rho_lo = std::sqrt(std::max(rh[2], rh[4]));
+    m->rho_hi = std::sqrt(rh[3]);
     return UE_OK;
 }
 

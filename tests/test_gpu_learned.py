@@ -132,3 +132,31 @@ def test_training_gains_over_power_iteration(ue):
     assert np.median(errs) < 0.02
     assert acc >= len(test_m) // 2
     assert np.median(t_ml) * 5 < np.median(t_pi)
+
+
+def test_fused_inference_matches_the_separate_kernels(ue):
+    """UE_DT_LEARNED runs one fused features+MLP+max pass; its rho_hat equals the max over
+    triangles of exp(z + base) from ue_rho_features / ue_mlp_forward / ue_seg_argmax, and its
+    bracket brackets the power-iteration rho."""
+    import torch
+    ms = meshgen.learned_mesh(meshgen.learned_specs(1, seed=19)[0])
+    p32 = (mlp.init_params(7) + 0.02 * np.random.default_rng(1).standard_normal(mlp.N_PARAMS)).astype(np.float32)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p32)
+    st = m.stats()
+    X = torch.empty((m.n_tris, 12), dtype=torch.float32, device="cuda")
+    base = torch.empty(m.n_tris, dtype=torch.float32, device="cuda")
+    m.rho_features(X, base)
+    z = torch.empty(m.n_tris, dtype=torch.float32, device="cuda")
+    ue.mlp_forward(torch.from_numpy(p32).cuda(), X, z, bf16=True)
+    off = torch.tensor([0, m.n_tris], dtype=torch.int64, device="cuda")
+    best = torch.empty(1, dtype=torch.float32, device="cuda")
+    arg = torch.empty(1, dtype=torch.int64, device="cuda")
+    ue.seg_argmax(z, base, off, best, arg)
+    assert abs(st["rho_hat"] / math.exp(float(best)) - 1) < 1e-5
+    m2 = ue.Mesh(ms.xy, ms.tris)
+    m2.geometry_build()
+    _, rho_pi, _ = m2.get_dt()
+    assert st["rho_lo"] <= rho_pi * (1 + 1e-9) and rho_pi <= st["rho_hi"] * (1 + 1e-9)
+    m.close()
+    m2.close()
