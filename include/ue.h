@@ -52,7 +52,10 @@ extern "C" {
 
 #define UE_DT_GIVEN 0            /* use ue_options.dt                                         */
 #define UE_DT_POWER 1            /* dt = safety * 2 / rho(M), rho by FP64 power iteration     */
-#define UE_DT_LEARNED 2          /* rho from the learned predictor if certified, else power   */
+#define UE_DT_LEARNED 2          /* rho from the learned predictor if certified, else power:  */
+                                 /* rho~ = max(rho_hat, rho_lo) is used when rho~ <= rho_hi   */
+                                 /* and safety * rho_hi * learned_margin <= rho~, i.e. the    */
+                                 /* dt it gives stays a margin below 2/rho_hi (eq. 20)        */
 
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
 #define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
@@ -92,7 +95,7 @@ typedef struct ue_options {
     int32_t watchdog_every;/* steps between energy checks inside ue_step_n (0 = off)         */
     int32_t reserved1;
     const float* mlp_params;/* UE_DT_LEARNED: host array of UE_MLP_PARAMS floats             */
-    double learned_margin; /* UE_DT_LEARNED: accept rho_hat in [margin*rho_lo, rho_hi] (1.05)*/
+    double learned_margin; /* UE_DT_LEARNED: certified stability margin (default 1.05)       */
     int32_t timeout_ms;    /* UE_VARIANT_PERSISTENT: grid-barrier wait limit (default 2000)  */
     int32_t test_skip_cta; /* UE_VARIANT_PERSISTENT, tests only: this CTA never arrives (-1) */
 } ue_options;

@@ -637,10 +637,13 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (o.dt_mode == UE_DT_LEARNED) {
         int lrc = learned_rho(m, o, s);
         if (lrc != UE_OK) return lrc;
-        const bool ok = m->rho_hat >= o.learned_margin * m->rho_lo && m->rho_hat <= m->rho_hi &&
-                        std::isfinite(m->rho_hat);
+        // the prediction, raised to the certified lower bound, must keep the chosen dt at least
+        // learned_margin below the stability limit of eq. 20 even for rho = rho_hi
+        const double rt = std::max(m->rho_hat, m->rho_lo);
+        const bool ok = std::isfinite(rt) && rt <= m->rho_hi &&
+                        rt >= o.learned_margin * o.safety * m->rho_hi;
         if (ok) {
-            m->rho = m->rho_hat;
+            m->rho = rt;
             m->rho_source = UE_RHO_LEARNED;
             m->dt = o.safety * 2.0 / m->rho;
         } else {

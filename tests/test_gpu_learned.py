@@ -114,6 +114,7 @@ def test_training_gains_over_power_iteration(ue):
         dt, rho, src = b.get_dt()
         st = b.stats()
         errs.append(abs(st["rho_hat"] / rho_pi - 1))
+        assert st["rho_lo"] <= rho_pi * (1 + 1e-9) <= st["rho_hi"] * (1 + 2e-9)
         if src == ue.UE_RHO_LEARNED:
             acc += 1
             t_ml.append(st["dt_setup_ms"])
