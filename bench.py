@@ -400,6 +400,11 @@ def run_learned(args):
     import paper_1812_01448_gb300 as ue
     from paper_1812_01448_gb300 import learned
     p = learned.load_weights()
+    # first launches of each path (module load) outside the measurement
+    for mode in (ue.UE_DT_POWER, ue.UE_DT_LEARNED):
+        w = ue.Mesh(meshes[0].xy, meshes[0].tris)
+        w.geometry_build(dt_mode=mode, mlp_params=p)
+        w.close()
     rows = []
     for ms in meshes:
         a = ue.Mesh(ms.xy, ms.tris)

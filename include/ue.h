@@ -108,7 +108,8 @@ typedef struct ue_stats_t {
     int32_t precision;
     double bytes_per_step;       /* algorithmic HBM bytes of one plain step                   */
     int64_t kernel_launches;     /* kernels the library launched so far                       */
-    double dt_setup_ms;          /* wall time of the dt selection in ue_geometry_build        */
+    double dt_setup_ms;          /* wall time of the dt selection in ue_geometry_build (work  */
+                                 /* space allocated before it starts)                          */
     double rho_lo, rho_hi;       /* certified bracket (UE_DT_LEARNED), 0 otherwise            */
     double rho_hat;              /* learned prediction (UE_DT_LEARNED), 0 otherwise           */
 } ue_stats_t;
@@ -128,6 +129,9 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
  * |O_R O_L| of eq. 3 in the cotangent form), the time step (eq. 20 with rho(M) from FP64 power
  * iteration, Section 2, or the given dt), the update coefficients dt*|e|/d (eq. 3) and dt/S
  * (eq. 4) rounded to the field precision, and zeroed fields.  Synchronous.
+ * UE_DT_LEARNED: one fused launch on parameters kept resident on the device (uploaded again
+ * only when opt->mlp_params holds other values than the last call on this device); such
+ * calls serialise on a library mutex.  The first one per device pins a 64-byte host buffer.
  * Errors: UE_ERR_DUAL if some interior edge has d <= 1e-12*|e|; UE_ERR_CUDA; UE_ERR_ALLOC. */
 int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream);
 

@@ -13,6 +13,9 @@ Hence rho(M) = sqrt(lambda_max(K)).
 * ``certified_bracket``: max_j K_jj <= lambda_max (Rayleigh quotient of a unit vector) and
   Gershgorin on the symmetric S^{1/2} K S^{-1/2}: lambda_max <= max_j (K_jj + sum_q |e_q| /
   (d_q sqrt(S_j S_j'))).
+* ``local_rayleigh``: the S-weighted Rayleigh quotient of K^p delta_j (p power steps of the
+  same iteration, started at one triangle).  Like any Rayleigh quotient of K it is a lower
+  bound of lambda_max; the learned-dt bracket takes it at the predicted argmax triangle.
 * ``stable_dt``: eq. 20: the leap-frog step is stable for w dt < 2 for every mode, so
   dt = safety * 2 / rho.  With a plasma density the current adds up to max(nbar) to w^2.
 * ``start_vector``: the start vector of the power iteration, drawn per caller triangle id from
@@ -21,7 +24,9 @@ Hence rho(M) = sqrt(lambda_max(K)).
 
 Parity: pinned by tests/test_oracle_spectral.py (dense eigenvalues on small meshes, bracket
 containment, Yee closed form on the merged right-split lattice, stability at 0.99 / 1.01 of
-the bound, dispersion relation).
+the bound, dispersion relation; the local Rayleigh quotient against its spectral form
+sum c_i^2 lambda_i^(2p+1) / sum c_i^2 lambda_i^2p from a dense eigendecomposition, and K_jj =
+12/a^2 on an equilateral lattice at p = 0).
 """
 from __future__ import annotations
 
@@ -70,6 +75,17 @@ def power_iteration(ops, iters: int = 200, v0: np.ndarray | None = None, seed: i
         hist.append(lam)
         v = w / np.sqrt(np.dot(S * w, w))
     return float(np.sqrt(lam)), np.asarray(hist)
+
+
+def local_rayleigh(ops, j0: int, p: int = 5) -> float:
+    """<v, K v>_S / <v, v>_S for v = K^p delta_j0."""
+    v = np.zeros(ops.L_B.shape[1])
+    v[j0] = 1.0
+    for _ in range(p):
+        v = apply_K(ops, v)
+    Kv = apply_K(ops, v)
+    S = ops.w_B
+    return float(np.dot(S * v, Kv) / np.dot(S * v, v))
 
 
 def diag_K(ops) -> np.ndarray:

@@ -128,8 +128,7 @@ cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const doubl
 int mlp_n_params();
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                             const int2* rl, const double* elen, const double* d, const double* S,
-                            int64_t n_t, int64_t n_ei, float* X, float* base, double* kdiag,
-                            double* gersh, cudaStream_t s);
+                            int64_t n_t, int64_t n_ei, float* X, float* base, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, int bf16, float* z,
                                cudaStream_t s);
 cudaError_t launch_mlp_backward(const float* P, const float* X, const int64_t* rows, const float* dz,
@@ -140,18 +139,14 @@ cudaError_t launch_seg_argmax(const float* z, const float* base, const int64_t* 
                               float* best, int64_t* arg, cudaStream_t s);
 cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, float* dz,
                             float* loss, cudaStream_t s);
-cudaError_t launch_max(const double* a, int64_t n, double* part, int n_part, double* out,
-                       cudaStream_t s);
-// Fused learned-rho inference: part needs 4 * rho_infer_blocks() doubles; out[4] = {log rho_hat,
-// argmax row, max K_jj, max Gershgorin bound}, *arg = the argmax row.
-int rho_infer_blocks();
-cudaError_t launch_rho_infer(const float* P, const double* xy, const int32_t* tri_nodes,
-                             const int32_t* tri_code, const int2* rl, const double* elen,
-                             const double* d, const double* S, int64_t n_t, int64_t n_ei,
-                             double* part, double* out, int64_t* arg, cudaStream_t s);
-cudaError_t launch_local_rq(const int32_t* code, const int2* rl, const double* elen, const double* d,
-                            const double* S, int64_t n_ei, const int64_t* j0, double* out,
-                            cudaStream_t s);
+// Fused learned-rho inference, one launch, on device-resident parameters, partials and
+// counter (one set per device: callers serialise).  rho_infer_upload copies the 5,057
+// parameters in.  out[5] (device-visible) = {log rho_hat, argmax row, max K_jj rounded down,
+// max Gershgorin bound rounded up, local Rayleigh quotient}.
+cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s);
+cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
+                             const int2* rl, const double* elen, const double* d, const double* S,
+                             int64_t n_t, int64_t n_ei, double* out, cudaStream_t s);
 
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 
 #include "device.cuh"
 
@@ -32,50 +33,83 @@ constexpr int kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH, kNParams = kOffB3 + 1;
 static_assert(kNParams == 5057, "parameter count");
 
 // ---------------------------------------------------------------------------------------
-// features (FP64 geometry, FP32 output) and the per-triangle bracket terms
+// features (FP32, from FP64 geometry) and the per-triangle bracket terms
 // ---------------------------------------------------------------------------------------
-__global__ void k_features(const double* __restrict__ xy, const int32_t* __restrict__ tn,
-                           const int32_t* __restrict__ code, const int2* __restrict__ rl,
-                           const double* __restrict__ elen, const double* __restrict__ d,
-                           const double* __restrict__ S, int64_t n_t, int64_t n_ei,
-                           float* __restrict__ X, float* __restrict__ base,
-                           double* __restrict__ kdiag, double* __restrict__ gersh) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
+// Rounding slack of the FP32 bracket terms.  K_jj and the Gershgorin row bound are sums,
+// products, quotients and square roots of positive values, formed from FP64 inputs with at
+// most 12 conversions and correctly rounded FP32 operations on any path (relative error
+// <= 2^-24 each), so the computed value lies within a factor 1 +- 12 * 2^-24 of the exact
+// one.  Scaling by 1 -+ 2^-16 keeps the bounds certified with 20x room.  Outside the normal
+// FP32 range the terms give no bound (K_jj -> 0, Gershgorin -> +inf).
+constexpr double kBracketSlack = 1.0 / 65536.0;
+
+// One triangle's features, FP32 (coordinate differences taken in FP64 first, so that small
+// triangles far from the origin lose nothing; GB300's FP64 pipes are few, and every feature
+// ends in FP32 or BF16 anyway).  f[12] = base = log sqrt(K_jj).  kdiag = K_jj and gersh = the
+// Gershgorin row bound of S^{1/2} K S^{-1/2}, both before the slack above.
+__device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
+                                                  const int32_t* __restrict__ tn,
+                                                  const int32_t* __restrict__ code,
+                                                  const int2* __restrict__ rl,
+                                                  const double* __restrict__ elen,
+                                                  const double* __restrict__ d,
+                                                  const double* __restrict__ S, int64_t j,
+                                                  int64_t n_ei, float* f, float& kdiag,
+                                                  float& gersh) {
     double px[3], py[3];
     for (int q = 0; q < 3; ++q) {
         const int v = tn[3 * j + q];
         px[q] = xy[2 * v];
         py[q] = xy[2 * v + 1];
     }
-    const double Sj = S[j];
-    const double rs = 1.0 / sqrt(Sj);
-    double kd = 0.0, off = 0.0;
-    float f[kD];
+    const float Sj = (float)S[j];
+    const float sq = __fsqrt_rn(Sj);
+    const float rs = 1.f / sq;
+    float kd = 0.f, off = 0.f;
+    bool normal = Sj >= 1e-30f;
     for (int q = 0; q < 3; ++q) {
         const int a = q, b = (q + 1) % 3, o = (q + 2) % 3;
-        const double ux = px[a] - px[o], uy = py[a] - py[o], vx = px[b] - px[o], vy = py[b] - py[o];
-        f[q] = (float)atan2(fabs(ux * vy - uy * vx), ux * vx + uy * vy);
-        f[3 + q] = (float)log(hypot(px[b] - px[a], py[b] - py[a]) * rs);
+        const float ux = (float)(px[a] - px[o]), uy = (float)(py[a] - py[o]);
+        const float vx = (float)(px[b] - px[o]), vy = (float)(py[b] - py[o]);
+        f[q] = atan2f(fabsf(ux * vy - uy * vx), ux * vx + uy * vy);
+        f[3 + q] = logf(hypotf((float)(px[b] - px[a]), (float)(py[b] - py[a])) * rs);
         const int c = code[3 * j + q];
         const int64_t k = c >> 1;
         if (k < n_ei) {
             const int2 e = rl[k];
             const int64_t nb = e.x == j ? e.y : e.x;
-            const double w = elen[k] / d[k];
-            f[6 + q] = (float)log(d[k] * rs);
-            f[9 + q] = (float)log(S[nb] / Sj);
-            kd += w;
-            off += w / sqrt(Sj * S[nb]);
+            const float dk = (float)d[k], Sn = (float)S[nb];
+            const float w = __fdiv_rn((float)elen[k], dk);
+            f[6 + q] = logf(dk * rs);
+            f[9 + q] = logf(Sn / Sj);
+            kd = __fadd_rn(kd, w);
+            off = __fadd_rn(off, __fdiv_rn(w, __fmul_rn(sq, __fsqrt_rn(Sn))));
+            normal = normal && Sn >= 1e-30f && dk >= 1e-30f;
         } else {
             f[6 + q] = 4.f;    // boundary: a dual so long the edge adds nothing to K
             f[9 + q] = 0.f;
         }
     }
+    kdiag = __fdiv_rn(kd, Sj);
+    gersh = __fadd_rn(kdiag, off);
+    f[12] = kd > 0.f ? 0.5f * logf(kdiag) : -1e30f;
+    if (!normal || !(kdiag <= 1e37f) || !(gersh <= 1e37f)) {
+        kdiag = 0.f;
+        gersh = INFINITY;
+    }
+}
+
+__global__ void k_features(const double* __restrict__ xy, const int32_t* __restrict__ tn,
+                           const int32_t* __restrict__ code, const int2* __restrict__ rl,
+                           const double* __restrict__ elen, const double* __restrict__ d,
+                           const double* __restrict__ S, int64_t n_t, int64_t n_ei,
+                           float* __restrict__ X, float* __restrict__ base) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    float f[kD + 1], kd, ge;
+    triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, f, kd, ge);
     for (int i = 0; i < kD; ++i) X[j * kD + i] = f[i];
-    base[j] = kd > 0.0 ? (float)(0.5 * log(kd / Sj)) : -1e30f;   // log sqrt(K_jj)
-    kdiag[j] = kd / Sj;
-    gersh[j] = kd / Sj + off;
+    base[j] = f[kD];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -181,198 +215,412 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_bf16(const float* __restrict__ 
     }
 }
 
-// Fused inference for one mesh: features -> BF16 MLP -> z_j + base_j, with per-block maxima
-// of that score (and its row), of K_jj and of the Gershgorin row bound.  One warp handles 16
-// triangles at a time: lanes 0..15 build one triangle's features each (FP64 geometry) in
-// shared memory, then the warp runs the same tensor-core layers as k_mlp_fwd_bf16.  No
-// feature array is written.  part[4 * block] = {best score, row (as double), max K_jj, max
-// Gershgorin bound}.
-__device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
-                                                  const int32_t* __restrict__ tn,
-                                                  const int32_t* __restrict__ code,
-                                                  const int2* __restrict__ rl,
-                                                  const double* __restrict__ elen,
-                                                  const double* __restrict__ d,
-                                                  const double* __restrict__ S, int64_t j,
-                                                  int64_t n_ei, float* f, double& kdiag,
-                                                  double& gersh) {
-    double px[3], py[3];
-    for (int q = 0; q < 3; ++q) {
-        const int v = tn[3 * j + q];
-        px[q] = xy[2 * v];
-        py[q] = xy[2 * v + 1];
+// Fused inference for one mesh, one launch: features -> BF16 MLP -> score z_j + base_j, the
+// per-block maxima of the score (with its row), of K_jj and of the Gershgorin row bound; the
+// last block to finish (counter in the work space) reduces the block partials and computes the
+// Rayleigh quotient lower bound near the argmax triangle.  Each warp takes 32 triangles at a
+// time: every lane builds one triangle's features in shared memory, then the warp runs the
+// tensor-core layers of k_mlp_fwd_bf16 on the two 16-row halves.  No feature array is written.
+constexpr int kInferWarps = 4, kInferThreads = 32 * kInferWarps;
+constexpr int kRing = 6, kLoc = 256;
+
+// The network as the tensor-core layers read it (BF16 weights padded to the smem row strides,
+// FP32 biases): packed once per parameter upload, brought into shared memory by one TMA bulk
+// copy per block.
+struct PackedNet {
+    __nv_bfloat16 w1[kH * kW1S];
+    __nv_bfloat16 w2[kH * kW2S];
+    float b1[kH], b2[kH], w3[kH];
+    float b3[4];
+};
+static_assert(sizeof(PackedNet) % 16 == 0, "bulk copies move multiples of 16 bytes");
+struct InferSmem {
+    PackedNet net;
+    float feat[kInferWarps][32][kD + 1];
+};
+static_assert(offsetof(InferSmem, feat) == sizeof(PackedNet), "packed net leads the block's smem");
+constexpr int kHash = 1024;      // open-addressing table of the neighbourhood, > 4 kLoc slots
+struct RqSmem {
+    int32_t ids[kLoc];          // triangles of rings 0..6 around the argmax, ring by ring
+    int32_t hkey[kHash];        // triangle id, -1 empty
+    int32_t hval[kHash];        // >= 0: the smallest candidate index naming the key in the
+                                // current ring; < 0: in the set, at local index -1 - hval
+    union {
+        int32_t cslot[3 * kLoc];    // while building: hash slot of each candidate, -1 none
+        int32_t nbr[kLoc][3];       // then: local index of each neighbour, -1 outside the set
+    } u;
+    double a[kLoc][3];          // |e| / (d S_i) of each interior edge (K's off-diagonal weight)
+    double sv[kLoc], v[kLoc], kv[kLoc];
+};
+union RhoSmem {
+    InferSmem a;
+    RqSmem b;
+};
+
+struct RhoPart {
+    float best;
+    int32_t arg;
+    float kmax, gmax;
+};
+
+// max of the score, ties to the smaller row (rows < 0 are empty)
+__device__ __forceinline__ void better(float& b, int32_t& a, float ob, int32_t oa) {
+    if (oa >= 0 && (a < 0 || ob > b || (ob == b && oa < a))) {
+        b = ob;
+        a = oa;
     }
-    const double Sj = S[j];
-    const double rs = 1.0 / sqrt(Sj);
-    double kd = 0.0, off = 0.0;
-    for (int q = 0; q < 3; ++q) {
-        const int a = q, b = (q + 1) % 3, o = (q + 2) % 3;
-        const double ux = px[a] - px[o], uy = py[a] - py[o], vx = px[b] - px[o], vy = py[b] - py[o];
-        f[q] = (float)atan2(fabs(ux * vy - uy * vx), ux * vx + uy * vy);
-        f[3 + q] = (float)log(hypot(px[b] - px[a], py[b] - py[a]) * rs);
-        const int c = code[3 * j + q];
-        const int64_t k = c >> 1;
-        if (k < n_ei) {
-            const int2 e = rl[k];
-            const int64_t nb = e.x == j ? e.y : e.x;
-            const double w = elen[k] / d[k];
-            f[6 + q] = (float)log(d[k] * rs);
-            f[9 + q] = (float)log(S[nb] / Sj);
-            kd += w;
-            off += w / sqrt(Sj * S[nb]);
-        } else {
-            f[6 + q] = 4.f;
-            f[9 + q] = 0.f;
-        }
-    }
-    kdiag = kd / Sj;
-    gersh = kd / Sj + off;
-    f[12] = kd > 0.0 ? (float)(0.5 * log(kd / Sj)) : -1e30f;   // base = log sqrt(K_jj)
 }
 
-__global__ void __launch_bounds__(128) k_rho_infer(const float* __restrict__ P,
-                                                   const double* __restrict__ xy,
-                                                   const int32_t* __restrict__ tn,
-                                                   const int32_t* __restrict__ code,
-                                                   const int2* __restrict__ rl,
-                                                   const double* __restrict__ elen,
-                                                   const double* __restrict__ d,
-                                                   const double* __restrict__ S, int64_t n,
-                                                   int64_t n_ei, double* __restrict__ part) {
-    __shared__ __nv_bfloat16 w1[kH * kW1S];
-    __shared__ __nv_bfloat16 w2[kH * kW2S];
-    __shared__ float bias1[kH], bias2[kH], w3[kH];
-    __shared__ float feat[4][16][13];
-    __shared__ double red[4][4];
-    for (int i = threadIdx.x; i < kH * kW1S; i += blockDim.x) {
-        const int r = i / kW1S, c = i % kW1S;
-        w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
+__device__ __forceinline__ uint32_t hash_slot(int32_t key) {
+    return ((uint32_t)key * 2654435761u) >> 22;   // 10 bits: kHash = 1024
+}
+
+// slot holding key (inserted if absent), -1 when the table is full
+__device__ __forceinline__ int hash_insert(RqSmem& R, int32_t key) {
+    uint32_t h = hash_slot(key);
+    for (int p = 0; p < kHash; ++p, h = (h + 1) & (kHash - 1)) {
+        const int32_t prev = atomicCAS(&R.hkey[h], -1, key);
+        if (prev == -1 || prev == key) return (int)h;
     }
-    for (int i = threadIdx.x; i < kH * kW2S; i += blockDim.x) {
-        const int r = i / kW2S, c = i % kW2S;
-        w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
+    return -1;
+}
+
+__device__ __forceinline__ int hash_find(const RqSmem& R, int32_t key) {
+    uint32_t h = hash_slot(key);
+    for (int p = 0; p < kHash; ++p, h = (h + 1) & (kHash - 1)) {
+        const int32_t k = R.hkey[h];
+        if (k == key) return (int)h;
+        if (k == -1) return -1;
     }
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-        bias1[i] = P[kOffB1 + i];
-        bias2[i] = P[kOffB2 + i];
-        w3[i] = P[kOffW3 + i];
+    return -1;
+}
+
+// Rayleigh quotient <v, K v>_S / <v, v>_S of v = K^5 delta_j0, on the rings 0..6 around j0
+// (exact there: K couples edge neighbours only, so K^5 delta_j0 lives on rings 0..5).  It
+// lower-bounds lambda_max(K) = rho^2.  0 when the neighbourhood exceeds kLoc triangles.
+// The rings are built breadth first; a shared hash table drops triangles already in the set
+// and keeps, of the repeats within a ring, the first in candidate order, so the local order
+// (and the rounding of the sums) does not depend on thread timing.  Runs on all threads of
+// one block; returns the value on every thread.
+__device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
+                                 const int2* __restrict__ rl, const double* __restrict__ elen,
+                                 const double* __restrict__ d, const double* __restrict__ S,
+                                 int64_t n_ei, int32_t j0, double* red) {
+    __shared__ int s_n, s_over;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
+    for (int i = tid; i < kHash; i += nth) {
+        R.hkey[i] = -1;
+        R.hval[i] = 0x7fffffff;
     }
-    const float b3 = P[kOffB3];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float (*F)[13] = feat[warp];
-    double best = -1e300, arg = -1.0, kmax = 0.0, gmax = 0.0;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile * 16 < n; tile += warps) {
-        if (lane < 16) {
-            const int64_t j = tile * 16 + lane;
-            if (j < n) {
-                double kd, ge;
-                triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, F[lane], kd, ge);
-                kmax = fmax(kmax, kd);
-                gmax = fmax(gmax, ge);
-            } else {
-                for (int i = 0; i < 12; ++i) F[lane][i] = 0.f;
-                F[lane][12] = -1e30f;
-            }
-        }
-        __syncwarp();
-        auto xv = [&](int r, int c) { return c < kD ? F[r][c] : 0.f; };
-        const uint32_t a0 = pack_bf16(xv(g, 2 * t), xv(g, 2 * t + 1));
-        const uint32_t a1 = pack_bf16(xv(g + 8, 2 * t), xv(g + 8, 2 * t + 1));
-        const uint32_t a2 = pack_bf16(xv(g, 2 * t + 8), xv(g, 2 * t + 9));
-        const uint32_t a3 = pack_bf16(xv(g + 8, 2 * t + 8), xv(g + 8, 2 * t + 9));
-        float h1[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + 2 * t;
-            h1[nt][0] = h1[nt][1] = h1[nt][2] = h1[nt][3] = 0.f;
-            const __nv_bfloat16* wr = w1 + (nt * 8 + g) * kW1S;
-            mma_bf16(h1[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
-                     *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
-            h1[nt][0] = fmaxf(h1[nt][0] + bias1[col], 0.f);
-            h1[nt][1] = fmaxf(h1[nt][1] + bias1[col + 1], 0.f);
-            h1[nt][2] = fmaxf(h1[nt][2] + bias1[col], 0.f);
-            h1[nt][3] = fmaxf(h1[nt][3] + bias1[col + 1], 0.f);
-        }
-        float h2[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            const uint32_t c0 = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
-            const uint32_t c1 = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
-            const uint32_t c2 = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
-            const uint32_t c3 = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const __nv_bfloat16* wr = w2 + (nt * 8 + g) * kW2S + kt * 16;
-                mma_bf16(h2[nt], c0, c1, c2, c3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
-                         *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
-            }
-        }
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + 2 * t;
-            s0 += w3[col] * fmaxf(h2[nt][0] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][1] + bias2[col + 1], 0.f);
-            s1 += w3[col] * fmaxf(h2[nt][2] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][3] + bias2[col + 1], 0.f);
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-        if (t == 0) {
-            const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-            const double v0 = (double)(s0 + b3 + F[g][12]), v1 = (double)(s1 + b3 + F[g + 8][12]);
-            if (r0 < n && v0 > best) { best = v0; arg = (double)r0; }
-            if (r1 < n && v1 > best) { best = v1; arg = (double)r1; }
-        }
-        __syncwarp();
+    if (tid == 0) {
+        R.hval[hash_insert(R, j0)] = -1;
+        R.ids[0] = j0;
+        s_n = 1;
+        s_over = 0;
     }
-    // warp then block maxima (ties: smaller row)
+    __syncthreads();
+    int start = 0;
+    for (int r = 1; r <= kRing; ++r) {
+        const int end = s_n, cnt = 3 * (end - start);
+        for (int c = tid; c < cnt; c += nth) {
+            const int32_t j = R.ids[start + c / 3];
+            const int64_t k = code[3 * (int64_t)j + c % 3] >> 1;
+            int h = -1;
+            if (k < n_ei) {
+                const int2 e = rl[k];
+                h = hash_insert(R, e.x == j ? e.y : e.x);
+                if (h < 0) s_over = 1;
+                else atomicMin(&R.hval[h], c);
+            }
+            R.u.cslot[c] = h;
+        }
+        __syncthreads();
+        if (tid < 32) {   // warp 0 appends the first naming of each new triangle, in order
+            int n = end;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                const int c = c0 + lane;
+                const int h = c < cnt ? R.u.cslot[c] : -1;
+                const bool keep = h >= 0 && R.hval[h] == c;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                const int pos = n + __popc(m & ((1u << lane) - 1u));
+                if (keep && pos < kLoc) {
+                    R.ids[pos] = R.hkey[h];
+                    R.hval[h] = -1 - pos;
+                }
+                n += __popc(m);
+            }
+            if (lane == 0) {
+                if (n >= kLoc) s_over = 1;
+                s_n = n < kLoc ? n : kLoc;
+            }
+        }
+        __syncthreads();
+        start = end;
+        if (s_over) break;
+    }
+    if (s_over) return 0.0;
+    const int n = s_n;
+    __syncthreads();   // cslot is read no more; nbr takes its place
+    for (int i = tid; i < n; i += nth) {
+        const int32_t j = R.ids[i];
+        const double Sj = S[j];
+        R.sv[i] = Sj;
+        R.v[i] = i == 0 ? 1.0 : 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const int64_t k = code[3 * (int64_t)j + q] >> 1;
+            R.u.nbr[i][q] = -1;
+            R.a[i][q] = 0.0;
+            if (k >= n_ei) continue;
+            const int2 e = rl[k];
+            const int h = hash_find(R, e.x == j ? e.y : e.x);
+            if (h >= 0 && R.hval[h] < 0) R.u.nbr[i][q] = -1 - R.hval[h];
+            R.a[i][q] = elen[k] / (d[k] * Sj);
+        }
+    }
+    __syncthreads();
+    // (K v)_i = sum_q a_iq (v_i - v_nbr), a neighbour outside the set holding 0; six products,
+    // ping-ponging between v and kv, leave K^5 delta in kv and K^6 delta in v
+    double* va = R.v;
+    double* vb = R.kv;
+    for (int it = 0; it < 6; ++it) {
+        for (int i = tid; i < n; i += nth) {
+            const double vi = va[i];
+            double acc = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const int nb = R.u.nbr[i][q];
+                acc = fma(R.a[i][q], vi - (nb >= 0 ? va[nb] : 0.0), acc);
+            }
+            vb[i] = acc;
+        }
+        __syncthreads();
+        double* t = va;
+        va = vb;
+        vb = t;
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = tid; i < n; i += nth) {
+        num += R.sv[i] * R.kv[i] * R.v[i];
+        den += R.sv[i] * R.kv[i] * R.kv[i];
+    }
     for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o), oa = __shfl_xor_sync(0xffffffffu, arg, o);
-        if (ob > best || (ob == best && oa >= 0 && (arg < 0 || oa < arg))) { best = ob; arg = oa; }
-        kmax = fmax(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-        gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
     }
     if (lane == 0) {
-        red[warp][0] = best;
-        red[warp][1] = arg;
-        red[warp][2] = kmax;
-        red[warp][3] = gmax;
+        red[2 * (tid >> 5)] = num;
+        red[2 * (tid >> 5) + 1] = den;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < 4; ++w) {
-            if (red[w][0] > red[0][0] || (red[w][0] == red[0][0] && red[w][1] >= 0 && (red[0][1] < 0 || red[w][1] < red[0][1]))) {
-                red[0][0] = red[w][0];
-                red[0][1] = red[w][1];
-            }
-            red[0][2] = fmax(red[0][2], red[w][2]);
-            red[0][3] = fmax(red[0][3], red[w][3]);
-        }
-        for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = red[0][i];
+    num = den = 0.0;
+    for (int w = 0; w < (nth >> 5); ++w) {
+        num += red[2 * w];
+        den += red[2 * w + 1];
     }
+    return den > 0.0 ? num / den : 0.0;
 }
 
-// out = {best score, row, max K_jj, max Gershgorin} over the block partials; row also as int64.
-__global__ void k_rho_reduce(const double* __restrict__ part, int nb, double* __restrict__ out,
-                             int64_t* __restrict__ arg) {
-    if (threadIdx.x != 0) return;
-    double b = -1e300, a = -1.0, k = 0.0, g = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        const double pb = part[4 * i], pa = part[4 * i + 1];
-        if (pb > b || (pb == b && pa >= 0 && (a < 0 || pa < a))) { b = pb; a = pa; }
-        k = fmax(k, part[4 * i + 2]);
-        g = fmax(g, part[4 * i + 3]);
+// mbarrier and bulk-copy (TMA) helpers.  Waits are bounded: a wait that runs out returns
+// false and the caller poisons its result instead of hanging.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one thread: arm the barrier for `bytes` and start the copy global -> shared (16-byte aligned
+// addresses, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    out[0] = b;
-    out[1] = a;
-    out[2] = k;
-    out[3] = g;
-    *arg = (int64_t)a;
+    return false;
+}
+
+// Resident state of the fused inference (no allocation per call): the parameters, their packed
+// form, the block partials and the completion counter (zero between launches; the last block
+// resets it).
+constexpr int kInferMaxBlocks = 152 * 8;
+__device__ float g_rho_params[kNParams];
+__device__ __align__(128) PackedNet g_rho_packed;
+__device__ RhoPart g_rho_parts[kInferMaxBlocks];
+__device__ unsigned int g_rho_counter;
+
+// out = {log rho_hat, row, max K_jj (rounded down), max Gershgorin (rounded up), Rayleigh
+// quotient}; host-mapped memory in the library's use, any device-visible buffer works.
+__global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
+    const double* __restrict__ xy, const int32_t* __restrict__ tn,
+    const int32_t* __restrict__ code, const int2* __restrict__ rl, const double* __restrict__ elen,
+    const double* __restrict__ d, const double* __restrict__ S, int64_t n, int64_t n_ei,
+    double* __restrict__ out) {
+    __shared__ __align__(128) RhoSmem sm;
+    __shared__ __align__(8) uint64_t net_bar;
+    __shared__ RhoPart red[kInferWarps];
+    __shared__ double dred[2 * kInferWarps];
+    __shared__ int s_last;
+    InferSmem& A = sm.a;
+    unsigned int* counter = &g_rho_counter;
+    RhoPart* part = g_rho_parts;
+    // the packed network arrives by one bulk copy while the first features are gathered
+    if (threadIdx.x == 0) {
+        mbar_init(&net_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bulk_g2s(&A.net, &g_rho_packed, (uint32_t)sizeof(PackedNet), &net_bar);
+    bool net_ready = false;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float (*F)[kD + 1] = A.feat[warp];
+    float best = -INFINITY, kmax = 0.f, gmax = 0.f;
+    int32_t arg = -1;
+    const int64_t warps = (int64_t)gridDim.x * kInferWarps;
+    for (int64_t tile = (int64_t)blockIdx.x * kInferWarps + warp; tile * 32 < n; tile += warps) {
+        const int64_t j = tile * 32 + lane;
+        if (j < n) {
+            float kd, ge;
+            triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, F[lane], kd, ge);
+            kmax = fmaxf(kmax, kd);
+            gmax = fmaxf(gmax, ge);
+        } else {
+            for (int i = 0; i < kD; ++i) F[lane][i] = 0.f;
+            F[lane][kD] = -1e30f;
+        }
+        __syncwarp();
+        if (!net_ready) net_ready = mbar_wait(&net_bar, 0);
+        const float b3 = A.net.b3[0];
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const float* x0 = F[16 * half + g];
+            const float* x1 = F[16 * half + g + 8];
+            auto xv = [&](const float* x, int c) { return c < kD ? x[c] : 0.f; };
+            const uint32_t a0 = pack_bf16(xv(x0, 2 * t), xv(x0, 2 * t + 1));
+            const uint32_t a1 = pack_bf16(xv(x1, 2 * t), xv(x1, 2 * t + 1));
+            const uint32_t a2 = pack_bf16(xv(x0, 2 * t + 8), xv(x0, 2 * t + 9));
+            const uint32_t a3 = pack_bf16(xv(x1, 2 * t + 8), xv(x1, 2 * t + 9));
+            float h1[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = nt * 8 + 2 * t;
+                h1[nt][0] = h1[nt][1] = h1[nt][2] = h1[nt][3] = 0.f;
+                const __nv_bfloat16* wr = A.net.w1 + (nt * 8 + g) * kW1S;
+                mma_bf16(h1[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
+                         *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
+                h1[nt][0] = fmaxf(h1[nt][0] + A.net.b1[col], 0.f);
+                h1[nt][1] = fmaxf(h1[nt][1] + A.net.b1[col + 1], 0.f);
+                h1[nt][2] = fmaxf(h1[nt][2] + A.net.b1[col], 0.f);
+                h1[nt][3] = fmaxf(h1[nt][3] + A.net.b1[col + 1], 0.f);
+            }
+            float h2[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                const uint32_t c0 = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
+                const uint32_t c1 = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
+                const uint32_t c2 = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
+                const uint32_t c3 = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const __nv_bfloat16* wr = A.net.w2 + (nt * 8 + g) * kW2S + kt * 16;
+                    mma_bf16(h2[nt], c0, c1, c2, c3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
+                             *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
+                }
+            }
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = nt * 8 + 2 * t;
+                s0 += A.net.w3[col] * fmaxf(h2[nt][0] + A.net.b2[col], 0.f) + A.net.w3[col + 1] * fmaxf(h2[nt][1] + A.net.b2[col + 1], 0.f);
+                s1 += A.net.w3[col] * fmaxf(h2[nt][2] + A.net.b2[col], 0.f) + A.net.w3[col + 1] * fmaxf(h2[nt][3] + A.net.b2[col + 1], 0.f);
+            }
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            if (t == 0) {
+                const int64_t r0 = tile * 32 + 16 * half + g, r1 = r0 + 8;
+                if (r0 < n) better(best, arg, s0 + b3 + x0[kD], (int32_t)r0);
+                if (r1 < n) better(best, arg, s1 + b3 + x1[kD], (int32_t)r1);
+            }
+        }
+        __syncwarp();
+    }
+    // no thread leaves (and no smem is reused) while the copy may still be writing
+    if (!net_ready) net_ready = mbar_wait(&net_bar, 0);
+    if (!net_ready) best = NAN;   // the wait ran out: poison the prediction (power iteration)
+    for (int o = 16; o > 0; o >>= 1) {
+        better(best, arg, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, arg, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    }
+    if (lane == 0) red[warp] = RhoPart{best, arg, kmax, gmax};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        RhoPart r = red[0];
+        for (int w = 1; w < kInferWarps; ++w) {
+            better(r.best, r.arg, red[w].best, red[w].arg);
+            r.kmax = fmaxf(r.kmax, red[w].kmax);
+            r.gmax = fmaxf(r.gmax, red[w].gmax);
+        }
+        part[blockIdx.x] = r;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last block: every other block's partial is visible (fence before its counter update)
+    __threadfence();
+    best = -INFINITY;
+    arg = -1;
+    kmax = gmax = 0.f;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(part + i));
+        better(best, arg, q.x, __float_as_int(q.y));
+        kmax = fmaxf(kmax, q.z);
+        gmax = fmaxf(gmax, q.w);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        better(best, arg, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, arg, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    }
+    __syncthreads();
+    if (lane == 0) red[warp] = RhoPart{best, arg, kmax, gmax};
+    __syncthreads();
+    RhoPart r = red[0];
+    for (int w = 1; w < kInferWarps; ++w) {
+        better(r.best, r.arg, red[w].best, red[w].arg);
+        r.kmax = fmaxf(r.kmax, red[w].kmax);
+        r.gmax = fmaxf(r.gmax, red[w].gmax);
+    }
+    const double rq = r.arg >= 0 ? local_rayleigh(sm.b, code, rl, elen, d, S, n_ei, r.arg, dred) : 0.0;
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        out[0] = (double)r.best;
+        out[1] = (double)r.arg;
+        out[2] = (double)r.kmax * (1.0 - kBracketSlack);
+        out[3] = (double)r.gmax * (1.0 + kBracketSlack);
+        out[4] = rq;
+    }
 }
 
 // FP32 debug forward: one thread per row, CUDA cores.
@@ -506,119 +754,16 @@ __global__ void k_rho_loss(const float* __restrict__ best, const float* __restri
     loss[s] = r * r;
 }
 
-// max of a double array (block partials, then one block).
-__global__ void k_max_parts(const double* __restrict__ a, int64_t n, double* __restrict__ part) {
-    __shared__ double s[256];
-    double m = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, a[i]);
-    s[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
-}
-
-// Rayleigh quotient of v = K^p delta_j0 (p = 5), computed on the 6-ring neighbourhood of j0
-// (exact: K couples edge neighbours only).  One block; out = {lambda lower bound}.
-constexpr int kRing = 6, kLoc = 512;
-__global__ void k_local_rq(const int32_t* __restrict__ code, const int2* __restrict__ rl,
-                           const double* __restrict__ elen, const double* __restrict__ d,
-                           const double* __restrict__ S, int64_t n_ei, const int64_t* __restrict__ j0p,
-                           double* __restrict__ out) {
-    __shared__ int64_t ids[kLoc];
-    __shared__ int nb[kLoc][3];
-    __shared__ double w[kLoc][3];
-    __shared__ double sv[kLoc], v[kLoc], kv[kLoc];
-    __shared__ int n_loc, ring_end[kRing + 2];
-    __shared__ double red[2][256];
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        // breadth-first rings; linear search keeps this small and deterministic
-        ids[0] = *j0p;
-        int n = 1, start = 0;
-        ring_end[0] = 1;
-        for (int r = 1; r <= kRing && n < kLoc; ++r) {
-            const int end = n;
-            for (int i = start; i < end && n < kLoc; ++i)
-                for (int q = 0; q < 3; ++q) {
-                    const int64_t k = code[3 * ids[i] + q] >> 1;
-                    if (k >= n_ei) continue;
-                    const int2 e = rl[k];
-                    const int64_t o = e.x == ids[i] ? e.y : e.x;
-                    bool seen = false;
-                    for (int s = 0; s < n && !seen; ++s) seen = ids[s] == o;
-                    if (!seen && n < kLoc) ids[n++] = o;
-                }
-            start = end;
-            ring_end[r] = n;
-        }
-        n_loc = n;
-    }
-    __syncthreads();
-    const int n = n_loc;
-    for (int i = tid; i < n; i += blockDim.x) {
-        const int64_t j = ids[i];
-        sv[i] = S[j];
-        v[i] = i == 0 ? 1.0 : 0.0;
-        for (int q = 0; q < 3; ++q) {
-            const int64_t k = code[3 * j + q] >> 1;
-            nb[i][q] = -1;
-            w[i][q] = 0.0;
-            if (k >= n_ei) continue;
-            const int2 e = rl[k];
-            const int64_t o = e.x == j ? e.y : e.x;
-            for (int s = 0; s < n; ++s)
-                if (ids[s] == o) nb[i][q] = s;
-            w[i][q] = elen[k] / d[k];
-        }
-    }
-    __syncthreads();
-    // (K v)_i = (1/S_i) sum_q w_q (v_i - v_nb)  (a neighbour outside the set holds 0)
-    for (int it = 0; it <= 5; ++it) {
-        for (int i = tid; i < n; i += blockDim.x) {
-            double a = 0.0;
-            for (int q = 0; q < 3; ++q)
-                if (w[i][q] != 0.0) a += w[i][q] * (v[i] - (nb[i][q] >= 0 ? v[nb[i][q]] : 0.0));
-            kv[i] = a / sv[i];
-        }
-        __syncthreads();
-        if (it < 5) {
-            for (int i = tid; i < n; i += blockDim.x) v[i] = kv[i];
-            __syncthreads();
-        }
-    }
-    double num = 0.0, den = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) {
-        num += sv[i] * v[i] * kv[i];
-        den += sv[i] * v[i] * v[i];
-    }
-    red[0][tid] = num;
-    red[1][tid] = den;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (tid < o) {
-            red[0][tid] += red[0][tid + o];
-            red[1][tid] += red[1][tid + o];
-        }
-        __syncthreads();
-    }
-    // a truncated neighbourhood (more than kLoc triangles) gives no bound
-    if (tid == 0) out[0] = (ring_end[kRing] <= kLoc && n < kLoc && red[1][0] > 0) ? red[0][0] / red[1][0] : 0.0;
-}
-
 }  // namespace
 
 int mlp_n_params() { return kNParams; }
 
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                             const int2* rl, const double* elen, const double* d, const double* S,
-                            int64_t n_t, int64_t n_ei, float* X, float* base, double* kdiag,
-                            double* gersh, cudaStream_t s) {
+                            int64_t n_t, int64_t n_ei, float* X, float* base, cudaStream_t s) {
+    if (n_t <= 0) return cudaSuccess;
     k_features<<<(unsigned)((n_t + 255) / 256), 256, 0, s>>>(xy, tri_nodes, tri_code, rl, elen, d, S,
-                                                             n_t, n_ei, X, base, kdiag, gersh);
+                                                             n_t, n_ei, X, base);
     return cudaGetLastError();
 }
 
@@ -665,29 +810,47 @@ cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, f
     return cudaGetLastError();
 }
 
-cudaError_t launch_max(const double* a, int64_t n, double* part, int n_part, double* out,
-                       cudaStream_t s) {
-    k_max_parts<<<n_part, 256, 0, s>>>(a, n, part);
-    k_max_parts<<<1, 256, 0, s>>>(part, n_part, out);
+// g_rho_packed from g_rho_params: weights to BF16 (round to nearest even) at the padded smem
+// strides, zeros in the padding.
+__global__ void k_pack_net() {
+    PackedNet& N = g_rho_packed;
+    const float* P = g_rho_params;
+    for (int i = threadIdx.x; i < kH * kW1S; i += blockDim.x) {
+        const int r = i / kW1S, c = i % kW1S;
+        N.w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH * kW2S; i += blockDim.x) {
+        const int r = i / kW2S, c = i % kW2S;
+        N.w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        N.b1[i] = P[kOffB1 + i];
+        N.b2[i] = P[kOffB2 + i];
+        N.w3[i] = P[kOffW3 + i];
+    }
+    if (threadIdx.x < 4) N.b3[threadIdx.x] = threadIdx.x == 0 ? P[kOffB3] : 0.f;
+}
+
+// Blocks of the fused inference: enough for every warp to take one 32-triangle tile, at most
+// 8 resident blocks on each of the 152 SMs.
+static int rho_infer_grid(int64_t n_t) {
+    const int64_t need = (n_t + kInferThreads - 1) / kInferThreads;
+    return (int)(need < 1 ? 1 : need > kInferMaxBlocks ? kInferMaxBlocks : need);
+}
+
+cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_rho_params, P_host, sizeof(float) * kNParams, 0,
+                                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_pack_net<<<1, 256, 0, s>>>();
     return cudaGetLastError();
 }
 
-int rho_infer_blocks() { return 152 * 4; }
-
-cudaError_t launch_rho_infer(const float* P, const double* xy, const int32_t* tri_nodes,
-                             const int32_t* tri_code, const int2* rl, const double* elen,
-                             const double* d, const double* S, int64_t n_t, int64_t n_ei,
-                             double* part, double* out, int64_t* arg, cudaStream_t s) {
-    const int nb = rho_infer_blocks();
-    k_rho_infer<<<nb, 128, 0, s>>>(P, xy, tri_nodes, tri_code, rl, elen, d, S, n_t, n_ei, part);
-    k_rho_reduce<<<1, 32, 0, s>>>(part, nb, out, arg);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_local_rq(const int32_t* code, const int2* rl, const double* elen, const double* d,
-                            const double* S, int64_t n_ei, const int64_t* j0, double* out,
-                            cudaStream_t s) {
-    k_local_rq<<<1, 256, 0, s>>>(code, rl, elen, d, S, n_ei, j0, out);
+cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
+                             const int2* rl, const double* elen, const double* d, const double* S,
+                             int64_t n_t, int64_t n_ei, double* out, cudaStream_t s) {
+    k_rho_infer<<<rho_infer_grid(n_t), kInferThreads, 0, s>>>(xy, tri_nodes, tri_code, rl, elen, d,
+                                                             S, n_t, n_ei, out);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -391,7 +392,6 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     tb.max_tri_loc = ts.max_tri_loc;
     tb.max_edge_loc = ts.max_edge_loc;
     tb.threads = m->tb_threads;
-    const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
               alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 1, 4, s) &&
               alloc_into(m, tb.B[1], m->dm.n_t_pad, 4, s) && alloc_into(m, tb.U[1], m->dm.n_ei_pad, 4, s);
@@ -408,28 +408,55 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
-// Learned rho: one fused pass (features -> BF16 MLP -> max of z + base, max K_jj, max
-// Gershgorin bound), then the local Rayleigh quotient near the argmax triangle (synchronous).
-// Sets m->rho_hat, m->rho_lo, m->rho_hi.  One small work allocation.
-int learned_rho(ue_mesh* m, const ue_options& o, cudaStream_t s) {
-    const int64_t nt = m->hm.n_tris, nei = m->hm.n_ei;
-    const int np = ue::mlp_n_params();
-    const int nb = ue::rho_infer_blocks();
-    const size_t n_dbl = 4 * (size_t)nb + 8 + 1 + (np + 1) / 2;
-    double* w = nullptr;
-    if (!alloc_into(m, w, n_dbl, 8, s)) return fail(UE_ERR_ALLOC, "learned dt work space");
-    double* part = w;
-    double* out = part + 4 * nb;                 // 4 results + the RQ
-    int64_t* arg = reinterpret_cast<int64_t*>(out + 8);
-    float* P = reinterpret_cast<float*>(out + 9);
-    UE_CUDA(cudaMemcpyAsync(P, o.mlp_params, 4 * np, cudaMemcpyHostToDevice, s));
-    UE_CUDA(ue::launch_rho_infer(P, m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen,
-                                 m->d_d, m->d_S, nt, nei, part, out, arg, s));
-    UE_CUDA(ue::launch_local_rq(m->d_tri_code, m->d_rl, m->d_elen, m->d_d, m->d_S, nei, arg, out + 4, s));
-    double rh[5] = {0, 0, 0, 0, 0};
-    UE_CUDA(cudaMemcpyAsync(rh, out, sizeof(rh), cudaMemcpyDeviceToHost, s));
+// Learned-rho resources of one device: a host-mapped pinned result buffer (the kernel writes
+// its five results straight into host memory) and a host mirror of the parameters resident on
+// the device, so that a call with unchanged parameters uploads nothing.  Created once per
+// process and device, on first use, before dt_setup_ms starts; calls serialise on the mutex
+// (the device-side partials and counter are shared).
+struct LearnedRes {
+    double* h_out = nullptr;
+    double* d_out = nullptr;
+    std::vector<float> params;
+};
+constexpr int kMaxDevices = 64;
+std::mutex g_learned_mu;
+LearnedRes g_learned[kMaxDevices];
+
+LearnedRes* learned_res() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    LearnedRes& r = g_learned[dev];
+    if (!r.h_out) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, 8 * sizeof(double), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        void* dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(h);
+            return nullptr;
+        }
+        r.h_out = (double*)h;
+        r.d_out = (double*)dp;
+    }
+    return &r;
+}
+
+// Learned rho: one fused launch (features -> BF16 MLP -> max of z + base, max K_jj, max
+// Gershgorin bound, then the local Rayleigh quotient near the argmax triangle), synchronous.
+// Sets m->rho_hat, m->rho_lo, m->rho_hi.  Caller holds g_learned_mu.
+int learned_rho(ue_mesh* m, const ue_options& o, LearnedRes* r, cudaStream_t s) {
+    const size_t np = (size_t)ue::mlp_n_params();
+    if (r->params.size() != np || std::memcmp(r->params.data(), o.mlp_params, sizeof(float) * np) != 0) {
+        UE_CUDA(ue::rho_infer_upload(o.mlp_params, s));
+        r->params.assign(o.mlp_params, o.mlp_params + np);
+    }
+    UE_CUDA(ue::launch_rho_infer(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen,
+                                 m->d_d, m->d_S, m->hm.n_tris, m->hm.n_ei, r->d_out, s));
     UE_CUDA(cudaStreamSynchronize(s));
-    dev_release(m, w, s);
+    const volatile double* rh = r->h_out;
     m->rho_hat = std::exp(rh[0]);
     m->rho_lo = std::sqrt(std::max(rh[2], rh[4]));
     m->rho_hi = std::sqrt(rh[3]);
@@ -630,12 +657,25 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     }
     // triangle records first with dt = 0: the power iteration reads only their edge codes
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, 0.0, s));
+    // work space of the chosen dt method, allocated before dt_setup_ms starts (the power
+    // iteration's again inside it when a learned prediction falls back)
+    double* pwork = nullptr;
+    LearnedRes* lres = nullptr;
+    std::unique_lock<std::mutex> llock(g_learned_mu, std::defer_lock);
+    if (o.dt_mode == UE_DT_LEARNED) {
+        llock.lock();
+        if (!(lres = learned_res())) return fail(UE_ERR_ALLOC, "learned dt result buffer");
+    } else if (o.dt_mode == UE_DT_POWER) {
+        if (!alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei), 8, s))
+            return fail(UE_ERR_ALLOC, "power iteration work space");
+    }
     UE_CUDA(cudaStreamSynchronize(s));
     const auto t_dt0 = std::chrono::steady_clock::now();
     m->rho_lo = m->rho_hi = m->rho_hat = 0;
     bool need_power = o.dt_mode == UE_DT_POWER;
     if (o.dt_mode == UE_DT_LEARNED) {
-        int lrc = learned_rho(m, o, s);
+        int lrc = learned_rho(m, o, lres, s);
+        llock.unlock();
         if (lrc != UE_OK) return lrc;
         // the prediction, raised to the certified lower bound, must keep the chosen dt at least
         // learned_margin below the stability limit of eq. 20 even for rho = rho_hi
@@ -651,13 +691,11 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         }
     }
     if (need_power) {
-        double* work = nullptr;
-        if (!alloc_into(m, work, ue::power_iteration_work_doubles(nt, nei), 8, s))
+        if (!pwork && !alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei), 8, s))
             return fail(UE_ERR_ALLOC, "power iteration work space");
         double rho = 0;
         UE_CUDA(ue::power_iteration(m->d_rl, dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei,
-                                    o.power_iters, o.power_seed, work, &rho, s));
-        dev_release(m, work, s);
+                                    o.power_iters, o.power_seed, pwork, &rho, s));
         if (!(rho > 0) || !std::isfinite(rho)) return fail(UE_ERR_DUAL, "power iteration gave rho <= 0");
         m->rho = rho;
         m->rho_source = o.dt_mode == UE_DT_LEARNED ? UE_RHO_POWER_FALLBACK : UE_RHO_POWER;
@@ -670,6 +708,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         m->rho_source = UE_RHO_GIVEN;
         m->dt = o.dt;
     }
+    if (pwork) dev_release(m, pwork, s);
     dm.dt = m->dt;
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, m->dt, s));
     UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * dm.n_ei_pad, s));
@@ -1137,14 +1176,9 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
 int ue_rho_features(ue_mesh* m, float* X, float* base, void* stream) {
     if (!m || !m->built || !X || !base) return fail(UE_ERR_ARG, "geometry not built or NULL output");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t nt = m->hm.n_tris;
-    double *kd = nullptr, *ge = nullptr;
-    if (!alloc_into(m, kd, nt, 8, s) || !alloc_into(m, ge, nt, 8, s)) return fail(UE_ERR_ALLOC, "feature work space");
     UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
-                                m->d_S, nt, m->hm.n_ei, X, base, kd, ge, s));
+                                m->d_S, m->hm.n_tris, m->hm.n_ei, X, base, s));
     UE_CUDA(cudaStreamSynchronize(s));
-    dev_release(m, kd, s);
-    dev_release(m, ge, s);
     return UE_OK;
 }
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import meshgen
-from oracle import geometry, mesh as om, mlp, rcm
+from oracle import geometry, mesh as om, mlp, operators, rcm, spectral
 
 pytestmark = pytest.mark.gpu
 
@@ -161,3 +161,65 @@ def test_fused_inference_matches_the_separate_kernels(ue):
     assert st["rho_lo"] <= rho_pi * (1 + 1e-9) and rho_pi <= st["rho_hi"] * (1 + 1e-9)
     m.close()
     m2.close()
+
+
+def test_resident_parameters_follow_the_caller(ue):
+    """The parameters stay on the device between calls; a call with other values must upload
+    them, and going back must give the first prediction again, bit for bit."""
+    ms = meshgen.learned_mesh(meshgen.learned_specs(1, seed=23)[0])
+    p1 = mlp.init_params(5).astype(np.float32)
+    p2 = p1.copy()
+    p2[-1] += np.float32(0.25)                     # b3: log rho_hat moves by exactly 0.25
+    out = []
+    for p in (p1, p2, p1, p1.copy()):
+        m = ue.Mesh(ms.xy, ms.tris)
+        m.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p)
+        out.append(m.stats()["rho_hat"])
+        m.close()
+    assert out[0] == out[2] == out[3]
+    assert abs(math.log(out[1] / out[0]) - 0.25) < 1e-6
+
+
+def test_bracket_matches_oracle(ue):
+    """rho_lo^2 = max(max_j K_jj rounded down, Rayleigh quotient of K^5 delta_j* at the argmax
+    triangle j*) and rho_hi^2 = the Gershgorin bound rounded up, against the FP64 oracle: the
+    FP32 terms within their 2^-16 slack and on the certified side, the quotient to 1e-10."""
+    import torch
+    ms = meshgen.learned_mesh(meshgen.learned_specs(1, seed=29, n_min=3000, n_max=6000)[0])
+    p32 = learned_params(ue)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p32)
+    st = m.stats()
+    X = torch.empty((m.n_tris, 12), dtype=torch.float32, device="cuda")
+    base = torch.empty(m.n_tris, dtype=torch.float32, device="cuda")
+    m.rho_features(X, base)
+    z = torch.empty(m.n_tris, dtype=torch.float32, device="cuda")
+    ue.mlp_forward(torch.from_numpy(p32).cuda(), X, z, bf16=True)
+    off = torch.tensor([0, m.n_tris], dtype=torch.int64, device="cuda")
+    best = torch.empty(1, dtype=torch.float32, device="cuda")
+    arg = torch.empty(1, dtype=torch.int64, device="cuda")
+    ue.seg_argmax(z, base, off, best, arg)
+    j_star = int(m.tables()["perm_tri"][int(arg)])
+    m.close()
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    kd = float(spectral.diag_K(ops).max())
+    _, hi = spectral.certified_bracket(ops)
+    rq = spectral.local_rayleigh(ops, j_star, 5)
+    slack = 2.0 ** -16
+    lo2 = st["rho_lo"] ** 2
+    assert lo2 <= max(kd, rq) * (1 + 1e-12)                      # still a lower bound
+    if rq >= kd:
+        assert abs(lo2 / rq - 1) < 1e-10
+    else:
+        assert abs(lo2 / (kd * (1 - slack)) - 1) < 2e-6
+    assert st["rho_hi"] >= hi                                     # still an upper bound
+    assert st["rho_hi"] ** 2 <= hi * hi * (1 + 2 * slack)
+
+
+def learned_params(ue):
+    """The shipped weights when present, else a seeded initialisation."""
+    from paper_1812_01448_gb300 import learned
+    try:
+        return learned.load_weights()
+    except (OSError, ValueError):
+        return mlp.init_params(29).astype(np.float32)

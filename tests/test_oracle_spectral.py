@@ -28,6 +28,36 @@ def test_power_iteration_and_bracket_against_dense_eigenvalues(small):
     assert np.all(np.diff(hist) >= -1e-9 * hist[-1])    # monotone for a PSD operator
 
 
+def test_local_rayleigh_against_eigendecomposition(small):
+    """v = K^p delta_j: in the symmetric frame u = S^(1/2) v = Kt^p sqrt(S_j) e_j, so the
+    quotient is sum c_i^2 lam_i^(2p+1) / sum c_i^2 lam_i^(2p) with c_i = phi_i[j] (eigh of
+    Kt = S^(1/2) K S^(-1/2)).  It is a lower bound of lambda_max and grows with p."""
+    lam, phi = np.linalg.eigh(spectral.symmetric_K(small))
+    lam = np.clip(lam, 0.0, None)
+    for j in (0, 57, 131, small.n_t - 1):
+        c2 = phi[j] ** 2
+        prev = 0.0
+        for p in (0, 1, 2, 5, 9):
+            ref = np.sum(c2 * lam ** (2 * p + 1)) / np.sum(c2 * lam ** (2 * p))
+            got = spectral.local_rayleigh(small, j, p)
+            assert abs(got / ref - 1) < 1e-10, (j, p, got, ref)
+            assert got <= lam[-1] * (1 + 1e-12)
+            assert got >= prev * (1 - 1e-12)
+            prev = got
+
+
+def test_local_rayleigh_p0_equilateral_closed_form():
+    """p = 0 gives K_jj; for an equilateral triangle of side a with three interior edges,
+    |e|/d = sqrt(3) (d = 2 * inradius = a / sqrt(3)) and S = sqrt(3) a^2 / 4, so K_jj = 12/a^2."""
+    a = 0.1
+    ops = _ops(meshgen.equilateral_lattice(8, a))
+    counts = np.bincount(ops.L_B.tocoo().col, minlength=ops.n_t)   # interior edges per triangle
+    inner = np.where(counts == 3)[0]
+    assert inner.size > 10
+    for j in inner[:: max(1, inner.size // 7)]:
+        assert abs(spectral.local_rayleigh(ops, int(j), 0) * a * a / 12.0 - 1) < 1e-12
+
+
 def test_omegas_are_real_and_zero_modes_exist(small):
     """Section 2: w real (K PSD), and a static subspace (uniform B) of zero eigenvalues."""
     lam = np.linalg.eigvalsh(spectral.symmetric_K(small))
