@@ -126,8 +126,9 @@ cudaError_t launch_source_coeff(const DevMesh& m, const double* amp, const doubl
                                 cudaStream_t s);
 // Learned spectral radius (kernels_mlp.cu).
 int mlp_n_params();
+// tri_nb[3j+q]: the triangle across edge q of triangle j, -1 on the boundary.
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
-                            const int2* rl, const double* elen, const double* d, const double* S,
+                            const int32_t* tri_nb, const double* elen, const double* d, const double* S,
                             int64_t n_t, int64_t n_ei, float* X, float* base, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, int bf16, float* z,
                                cudaStream_t s);
@@ -145,7 +146,7 @@ cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, f
 // max Gershgorin bound rounded up, local Rayleigh quotient}.
 cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s);
 cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
-                             const int2* rl, const double* elen, const double* d, const double* S,
+                             const int32_t* tri_nb, const double* elen, const double* d, const double* S,
                              int64_t n_t, int64_t n_ei, double* out, cudaStream_t s);
 
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).

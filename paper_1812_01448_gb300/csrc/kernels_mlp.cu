@@ -46,23 +46,35 @@ constexpr double kBracketSlack = 1.0 / 65536.0;
 // One triangle's features, FP32 (coordinate differences taken in FP64 first, so that small
 // triangles far from the origin lose nothing; GB300's FP64 pipes are few, and every feature
 // ends in FP32 or BF16 anyway).  f[12] = base = log sqrt(K_jj).  kdiag = K_jj and gersh = the
-// Gershgorin row bound of S^{1/2} K S^{-1/2}, both before the slack above.
+// Gershgorin row bound of S^{1/2} K S^{-1/2}, both before the slack above.  The gathers are
+// issued in two dependent rounds (row j's tables, then what they point to).
 __device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
                                                   const int32_t* __restrict__ tn,
                                                   const int32_t* __restrict__ code,
-                                                  const int2* __restrict__ rl,
+                                                  const int32_t* __restrict__ tnb,
                                                   const double* __restrict__ elen,
                                                   const double* __restrict__ d,
                                                   const double* __restrict__ S, int64_t j,
                                                   int64_t n_ei, float* f, float& kdiag,
                                                   float& gersh) {
-    double px[3], py[3];
+    int vtx[3], nb[3];
+    int64_t k[3];
     for (int q = 0; q < 3; ++q) {
-        const int v = tn[3 * j + q];
-        px[q] = xy[2 * v];
-        py[q] = xy[2 * v + 1];
+        vtx[q] = tn[3 * j + q];
+        k[q] = code[3 * j + q] >> 1;
+        nb[q] = tnb[3 * j + q];
     }
-    const float Sj = (float)S[j];
+    const double Sjd = S[j];
+    double px[3], py[3], el[3], dd[3], sn[3];
+    for (int q = 0; q < 3; ++q) {
+        px[q] = xy[2 * vtx[q]];
+        py[q] = xy[2 * vtx[q] + 1];
+        const bool in = k[q] < n_ei;
+        el[q] = in ? elen[k[q]] : 0.0;
+        dd[q] = in ? d[k[q]] : 1.0;
+        sn[q] = in ? S[nb[q]] : 1.0;
+    }
+    const float Sj = (float)Sjd;
     const float sq = __fsqrt_rn(Sj);
     const float rs = 1.f / sq;
     float kd = 0.f, off = 0.f;
@@ -73,13 +85,9 @@ __device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
         const float vx = (float)(px[b] - px[o]), vy = (float)(py[b] - py[o]);
         f[q] = atan2f(fabsf(ux * vy - uy * vx), ux * vx + uy * vy);
         f[3 + q] = logf(hypotf((float)(px[b] - px[a]), (float)(py[b] - py[a])) * rs);
-        const int c = code[3 * j + q];
-        const int64_t k = c >> 1;
-        if (k < n_ei) {
-            const int2 e = rl[k];
-            const int64_t nb = e.x == j ? e.y : e.x;
-            const float dk = (float)d[k], Sn = (float)S[nb];
-            const float w = __fdiv_rn((float)elen[k], dk);
+        if (k[q] < n_ei) {
+            const float dk = (float)dd[q], Sn = (float)sn[q];
+            const float w = __fdiv_rn((float)el[q], dk);
             f[6 + q] = logf(dk * rs);
             f[9 + q] = logf(Sn / Sj);
             kd = __fadd_rn(kd, w);
@@ -100,14 +108,14 @@ __device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
 }
 
 __global__ void k_features(const double* __restrict__ xy, const int32_t* __restrict__ tn,
-                           const int32_t* __restrict__ code, const int2* __restrict__ rl,
+                           const int32_t* __restrict__ code, const int32_t* __restrict__ tnb,
                            const double* __restrict__ elen, const double* __restrict__ d,
                            const double* __restrict__ S, int64_t n_t, int64_t n_ei,
                            float* __restrict__ X, float* __restrict__ base) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_t) return;
     float f[kD + 1], kd, ge;
-    triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, f, kd, ge);
+    triangle_features(xy, tn, code, tnb, elen, d, S, j, n_ei, f, kd, ge);
     for (int i = 0; i < kD; ++i) X[j * kD + i] = f[i];
     base[j] = f[kD];
 }
@@ -303,7 +311,7 @@ __device__ __forceinline__ int hash_find(const RqSmem& R, int32_t key) {
 // (and the rounding of the sums) does not depend on thread timing.  Runs on all threads of
 // one block; returns the value on every thread.
 __device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
-                                 const int2* __restrict__ rl, const double* __restrict__ elen,
+                                 const int32_t* __restrict__ tnb, const double* __restrict__ elen,
                                  const double* __restrict__ d, const double* __restrict__ S,
                                  int64_t n_ei, int32_t j0, double* red) {
     __shared__ int s_n, s_over;
@@ -324,12 +332,10 @@ __device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
     for (int r = 1; r <= kRing; ++r) {
         const int end = s_n, cnt = 3 * (end - start);
         for (int c = tid; c < cnt; c += nth) {
-            const int32_t j = R.ids[start + c / 3];
-            const int64_t k = code[3 * (int64_t)j + c % 3] >> 1;
+            const int32_t o = tnb[3 * (int64_t)R.ids[start + c / 3] + c % 3];
             int h = -1;
-            if (k < n_ei) {
-                const int2 e = rl[k];
-                h = hash_insert(R, e.x == j ? e.y : e.x);
+            if (o >= 0) {
+                h = hash_insert(R, o);
                 if (h < 0) s_over = 1;
                 else atomicMin(&R.hval[h], c);
             }
@@ -367,15 +373,19 @@ __device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
         const double Sj = S[j];
         R.sv[i] = Sj;
         R.v[i] = i == 0 ? 1.0 : 0.0;
+        int64_t k[3];
+        int32_t o[3];
         for (int q = 0; q < 3; ++q) {
-            const int64_t k = code[3 * (int64_t)j + q] >> 1;
+            k[q] = code[3 * (int64_t)j + q] >> 1;
+            o[q] = tnb[3 * (int64_t)j + q];
+        }
+        for (int q = 0; q < 3; ++q) {
             R.u.nbr[i][q] = -1;
             R.a[i][q] = 0.0;
-            if (k >= n_ei) continue;
-            const int2 e = rl[k];
-            const int h = hash_find(R, e.x == j ? e.y : e.x);
+            if (k[q] >= n_ei) continue;
+            const int h = hash_find(R, o[q]);
             if (h >= 0 && R.hval[h] < 0) R.u.nbr[i][q] = -1 - R.hval[h];
-            R.a[i][q] = elen[k] / (d[k] * Sj);
+            R.a[i][q] = elen[k[q]] / (d[k[q]] * Sj);
         }
     }
     __syncthreads();
@@ -469,7 +479,7 @@ __device__ unsigned int g_rho_counter;
 // quotient}; host-mapped memory in the library's use, any device-visible buffer works.
 __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
     const double* __restrict__ xy, const int32_t* __restrict__ tn,
-    const int32_t* __restrict__ code, const int2* __restrict__ rl, const double* __restrict__ elen,
+    const int32_t* __restrict__ code, const int32_t* __restrict__ tnb, const double* __restrict__ elen,
     const double* __restrict__ d, const double* __restrict__ S, int64_t n, int64_t n_ei,
     double* __restrict__ out) {
     __shared__ __align__(128) RhoSmem sm;
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
         const int64_t j = tile * 32 + lane;
         if (j < n) {
             float kd, ge;
-            triangle_features(xy, tn, code, rl, elen, d, S, j, n_ei, F[lane], kd, ge);
+            triangle_features(xy, tn, code, tnb, elen, d, S, j, n_ei, F[lane], kd, ge);
             kmax = fmaxf(kmax, kd);
             gmax = fmaxf(gmax, ge);
         } else {
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
         r.kmax = fmaxf(r.kmax, red[w].kmax);
         r.gmax = fmaxf(r.gmax, red[w].gmax);
     }
-    const double rq = r.arg >= 0 ? local_rayleigh(sm.b, code, rl, elen, d, S, n_ei, r.arg, dred) : 0.0;
+    const double rq = r.arg >= 0 ? local_rayleigh(sm.b, code, tnb, elen, d, S, n_ei, r.arg, dred) : 0.0;
     if (threadIdx.x == 0) {
         *counter = 0u;
         out[0] = (double)r.best;
@@ -759,10 +769,10 @@ __global__ void k_rho_loss(const float* __restrict__ best, const float* __restri
 int mlp_n_params() { return kNParams; }
 
 cudaError_t launch_features(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
-                            const int2* rl, const double* elen, const double* d, const double* S,
+                            const int32_t* tri_nb, const double* elen, const double* d, const double* S,
                             int64_t n_t, int64_t n_ei, float* X, float* base, cudaStream_t s) {
     if (n_t <= 0) return cudaSuccess;
-    k_features<<<(unsigned)((n_t + 255) / 256), 256, 0, s>>>(xy, tri_nodes, tri_code, rl, elen, d, S,
+    k_features<<<(unsigned)((n_t + 255) / 256), 256, 0, s>>>(xy, tri_nodes, tri_code, tri_nb, elen, d, S,
                                                              n_t, n_ei, X, base);
     return cudaGetLastError();
 }
@@ -847,9 +857,9 @@ cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s) {
 }
 
 cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
-                             const int2* rl, const double* elen, const double* d, const double* S,
+                             const int32_t* tri_nb, const double* elen, const double* d, const double* S,
                              int64_t n_t, int64_t n_ei, double* out, cudaStream_t s) {
-    k_rho_infer<<<rho_infer_grid(n_t), kInferThreads, 0, s>>>(xy, tri_nodes, tri_code, rl, elen, d,
+    k_rho_infer<<<rho_infer_grid(n_t), kInferThreads, 0, s>>>(xy, tri_nodes, tri_code, tri_nb, elen, d,
                                                              S, n_t, n_ei, out);
     return cudaGetLastError();
 }

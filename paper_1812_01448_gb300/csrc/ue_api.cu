@@ -52,6 +52,7 @@ struct ue_mesh {
     int32_t* d_edge_opp = nullptr;
     int32_t* d_tri_code = nullptr;
     int2* d_rl = nullptr;
+    int32_t* d_tri_nb = nullptr;    // 3*n_tris: triangle across each edge, -1 on the boundary
     int64_t* d_perm = nullptr;
     int64_t* d_ecaller = nullptr;
     double *d_O = nullptr, *d_S = nullptr, *d_elen = nullptr, *d_d = nullptr;
@@ -408,6 +409,23 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
+// The triangle-neighbour table (from the R/L table) on the device, made on first use: the
+// learned-rho kernels walk triangle neighbourhoods with it.
+int ensure_tri_nb(ue_mesh* m, cudaStream_t s) {
+    if (m->d_tri_nb) return UE_OK;
+    const HostMesh& h = m->hm;
+    std::vector<int32_t> nb(3 * (size_t)h.n_tris);
+    for (int64_t j = 0; j < h.n_tris; ++j)
+        for (int q = 0; q < 3; ++q) {
+            const int64_t k = h.tri_code[3 * j + q] >> 1;
+            nb[3 * j + q] = k < h.n_ei ? (h.edge_tri[2 * k] == j ? h.edge_tri[2 * k + 1] : h.edge_tri[2 * k]) : -1;
+        }
+    if (!alloc_into(m, m->d_tri_nb, 3 * h.n_tris, 4, s)) return fail(UE_ERR_ALLOC, "triangle neighbour table");
+    UE_CUDA(cudaMemcpyAsync(m->d_tri_nb, nb.data(), 12 * h.n_tris, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
 // Learned-rho resources of one device: a host-mapped pinned result buffer (the kernel writes
 // its five results straight into host memory) and a host mirror of the parameters resident on
 // the device, so that a call with unchanged parameters uploads nothing.  Created once per
@@ -453,7 +471,7 @@ int learned_rho(ue_mesh* m, const ue_options& o, LearnedRes* r, cudaStream_t s) 
         UE_CUDA(ue::rho_infer_upload(o.mlp_params, s));
         r->params.assign(o.mlp_params, o.mlp_params + np);
     }
-    UE_CUDA(ue::launch_rho_infer(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen,
+    UE_CUDA(ue::launch_rho_infer(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_tri_nb, m->d_elen,
                                  m->d_d, m->d_S, m->hm.n_tris, m->hm.n_ei, r->d_out, s));
     UE_CUDA(cudaStreamSynchronize(s));
     const volatile double* rh = r->h_out;
@@ -501,6 +519,7 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
          alloc_into(m, m->wd_part, ue::energy_parts(nei, nt), 8, s);
     if (!ok) {
         dev_free_all(m, s);
+        m->d_tri_nb = nullptr;
         return fail(UE_ERR_ALLOC, "device allocation failed");
     }
     {
@@ -618,6 +637,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     drop_graph(m);
     UE_CUDA(cudaStreamSynchronize(s));
     dev_free_all(m, s);
+    m->d_tri_nb = nullptr;
     m->built = false;
     m->dm = DevMesh();
     m->tb = ue::TBDev();
@@ -663,6 +683,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     LearnedRes* lres = nullptr;
     std::unique_lock<std::mutex> llock(g_learned_mu, std::defer_lock);
     if (o.dt_mode == UE_DT_LEARNED) {
+        const int nrc = ensure_tri_nb(m, s);
+        if (nrc != UE_OK) return nrc;
         llock.lock();
         if (!(lres = learned_res())) return fail(UE_ERR_ALLOC, "learned dt result buffer");
     } else if (o.dt_mode == UE_DT_POWER) {
@@ -1176,7 +1198,9 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
 int ue_rho_features(ue_mesh* m, float* X, float* base, void* stream) {
     if (!m || !m->built || !X || !base) return fail(UE_ERR_ARG, "geometry not built or NULL output");
     cudaStream_t s = (cudaStream_t)stream;
-    UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_rl, m->d_elen, m->d_d,
+    const int nrc = ensure_tri_nb(m, s);
+    if (nrc != UE_OK) return nrc;
+    UE_CUDA(ue::launch_features(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_tri_nb, m->d_elen, m->d_d,
                                 m->d_S, m->hm.n_tris, m->hm.n_ei, X, base, s));
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;

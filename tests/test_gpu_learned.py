@@ -178,6 +178,11 @@ def test_resident_parameters_follow_the_caller(ue):
         m.close()
     assert out[0] == out[2] == out[3]
     assert abs(math.log(out[1] / out[0]) - 0.25) < 1e-6
+    m = ue.Mesh(ms.xy, ms.tris)                    # a rebuild remakes its device tables
+    for _ in range(2):
+        m.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=p1)
+        assert m.stats()["rho_hat"] == out[0]
+    m.close()
 
 
 def test_bracket_matches_oracle(ue):
