@@ -2,7 +2,9 @@
 
 One bench "step" is one full leap-frog step (E half-step over every interior edge, the line
 source, B half-step over every triangle) of the graded unit-square mesh with an equilateral
-PEC hole (h 2e-4 .. 8e-4, ~4M triangles, RCM order, FP32 fields, FP64-built coefficients).
+PEC hole (h 2e-4 .. 8e-4, ~4M triangles, FP32 fields, FP64-built coefficients).  By default
+the steps run temporally blocked: KD tiles of <= 2048 triangles, 8 steps per launch, 512
+threads per tile (--variant plain: two kernels per step in RCM order).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -29,11 +31,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = ("scatterer-4M: unit square, PEC walls and PEC equilateral hole (side 0.2, centre "
-            "(0.5,0.5)), spacing graded 2e-4..8e-4, jitter 0.2h, RCM order, FP32 fields, line "
-            "source x=0.35, w0=2*pi*20")
+            "(0.5,0.5)), spacing graded 2e-4..8e-4, jitter 0.2h, FP32 fields, line source "
+            "x=0.35, w0=2*pi*20")
 METRIC = "cell-updates/s"
 UNIT = "triangle-steps/s"
 L2_BYTES = 129e6
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
+# bench command at its configuration (summary and command in profiles/), keyed by the sha1 of
+# the kernel source it measured: used only while that source is unchanged, else null.
+NCU_TRAFFIC = {
+    # (variant, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
+}
+
+
+def _traffic(key):
+    import hashlib
+    rec = NCU_TRAFFIC.get(key)
+    if rec is None:
+        return None, None
+    nbytes, src, sha, prof = rec
+    with open(os.path.join(ROOT, "paper_1812_01448_gb300", "csrc", src), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != sha:
+            return None, f"{prof}: kernel source changed since the capture"
+    return float(nbytes), prof
 
 
 def _peaks():
@@ -242,9 +264,13 @@ def run_native(args):
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
+    tkey = (args.variant, args.tile_tris if blocked else 0, args.block_depth if blocked else 1,
+            (args.tb_threads or 512) if blocked else 0)
+    traffic, traffic_src = _traffic(tkey)
     step_bytes = st["bytes_per_step"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": names[k],
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+            "kernel": names[k],
             "bytes_per_launch": prof_bytes[k], "ms_per_launch": prof_ms[k],
             "peak_kind": f"{peak_kind} (STREAM-style copy)",
             "step": {"bytes": step_bytes, "achieved_gbs": step_bytes * args.steps / (ms_total * 1e-3) / 1e9,
@@ -315,9 +341,10 @@ def _time_steps(fn, stream):
 
 
 def run_batch(args):
-    """Many independent meshes: one launch per half-step for all of them (batched, inside CUDA
-    graphs) against the plain form (each mesh stepped alone: its own E and B launches, no
-    graph).  Both with every mesh's own dt and line source."""
+    """Many independent meshes advanced together, in the launch form the autotuner picks on a
+    sample of them (tune.autotune_batch), against the plain form: each mesh stepped alone with
+    its own E and B launches, no graph.  Every mesh keeps its own dt (power iteration) and
+    line source."""
     import multiprocessing as mp
 
     import meshgen
@@ -331,13 +358,20 @@ def run_batch(args):
     from paper_1812_01448_gb300 import build as b
     b.build()
     import paper_1812_01448_gb300 as ue
+    from paper_1812_01448_gb300 import tune
     stream = torch.cuda.current_stream()
-    singles = []
+    items = []
     for sp, ms in zip(specs, meshes):
-        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=args.tile_tris)
-        m.geometry_build(stream=stream, graph_chunk=-1)
         ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
-        m.set_source(ids, amp, sp["omega0"], 0.1, 0.05)
+        items.append((ms, ids, amp, sp["omega0"]))
+    best, table = tune.autotune_batch(items, sample=args.tune_sample, stream=stream)
+    variant = {"plain": ue.UE_VARIANT_PLAIN, "persistent": ue.UE_VARIANT_PERSISTENT,
+               "blocked": ue.UE_VARIANT_BLOCKED}[best["variant"]]
+    singles = []
+    for ms, ids, amp, w0 in items:
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=best["tile_tris"])
+        m.geometry_build(stream=stream, graph_chunk=-1)          # own dt: power iteration
+        m.set_source(ids, amp, w0, 0.1, 0.05)
         singles.append(m)
     n_t = sum(m.n_tris for m in singles)
     # plain form: every mesh alone, E and B launches per mesh per step (plus its g-table launch)
@@ -351,27 +385,26 @@ def run_batch(args):
                 m.step_n(1, stream)
     t_plain = _time_steps(plain, stream)
     rate_plain = n_t * sp_steps / t_plain
-    res = {"plain_per_mesh": rate_plain}
-    for variant in ("plain", "blocked"):
-        # rebuild every mesh for this variant (sources and dt carry over)
-        for m in singles:
-            m.geometry_build(stream=stream, graph_chunk=args.graph_chunk,
-                             variant=ue.UE_VARIANT_BLOCKED if variant == "blocked" else ue.UE_VARIANT_PLAIN,
-                             block_depth=args.block_depth, tb_threads=args.tb_threads)
-        bt = ue.batch_create(singles, stream)
-        bt.step_n(args.warmup, stream)
-        t = _time_steps(lambda: bt.step_n(args.steps, stream), stream)
-        res[f"batched_{variant}"] = n_t * args.steps / t
-        bt.close()
+    # the tuned form over the whole batch (rebuilt with each mesh's own dt)
+    for m in singles:
+        dt = m.get_dt()[0]
+        m.geometry_build(stream=stream, dt_mode=ue.UE_DT_GIVEN, dt=dt, graph_chunk=args.graph_chunk,
+                         variant=variant, block_depth=best["block_depth"], tb_threads=best["tb_threads"])
+    bt = ue.batch_create(singles, stream)
+    k = best["block_depth"]
+    bt.step_n(max(k, args.warmup - args.warmup % k), stream)
+    n_steps = max(k, args.steps - args.steps % k)
+    t = _time_steps(lambda: bt.step_n(n_steps, stream), stream)
+    rate = n_t * n_steps / t
+    bt.close()
     line = {
         "metric": "cell-updates/s (batch of independent meshes)", "unit": UNIT,
-        "value": res["batched_blocked"], "n_meshes": len(singles), "n_tris_total": n_t,
-        "steps": args.steps, "plain_steps": sp_steps, "results": res,
-        "ratio_batched_blocked_vs_plain": res["batched_blocked"] / rate_plain,
-        "ratio_batched_plain_vs_plain": res["batched_plain"] / rate_plain,
+        "value": rate, "n_meshes": len(singles), "n_tris_total": n_t, "steps": n_steps,
+        "plain_steps": sp_steps, "plain_per_mesh": rate_plain,
+        "ratio_batched_vs_plain": rate / rate_plain,
+        "tuned": best, "tuning": table,
         "config": {"workload": f"{len(singles)} meshes, log-uniform 5k-200k triangles, random "
                                "scatterer each, own dt and source frequency",
-                   "tile_tris": args.tile_tris, "block_depth": args.block_depth,
                    "mesh_generation_s": t_gen},
     }
     print(json.dumps(line), flush=True)
@@ -447,15 +480,16 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="plain")
+    ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
     ap.add_argument("--tile-tris", type=int, default=2048)
-    ap.add_argument("--block-depth", type=int, default=4)
+    ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
     ap.add_argument("--workload", choices=["scatterer", "batch", "learned"], default="scatterer")
     ap.add_argument("--learned-meshes", type=int, default=40)
     ap.add_argument("--learned-max", type=int, default=1_000_000)
     ap.add_argument("--batch-meshes", type=int, default=512)
+    ap.add_argument("--tune-sample", type=int, default=32)
     ap.add_argument("--quick-setup", action="store_true",
                     help="fixed dt instead of power iteration (for profiler runs)")
     args = ap.parse_args(argv)

@@ -105,103 +105,123 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_pi_init(double* __restrict__ v, const int64_t* __restrict__ perm, uint32_t seed,
-                          int64_t n_t) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
-    const uint64_t z = splitmix64(((uint64_t)seed << 32) + (uint64_t)perm[j]);
-    v[j] = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+// Per edge c_k = |e_k| / d_k and per triangle 1/S_j, once: the iterations then only multiply
+// and add (FP64 division and square root are slow on GB300's few FP64 pipes).
+__global__ void k_pi_prep(const double* __restrict__ elen, const double* __restrict__ d,
+                          const double* __restrict__ S, double* __restrict__ c,
+                          double* __restrict__ invS, int64_t n_ei, int64_t n_t) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_ei) c[i] = elen[i] / d[i];
+    if (i < n_t) invS[i] = 1.0 / S[i];
 }
 
-__global__ void k_pi_edge(const int2* __restrict__ rl, const double* __restrict__ elen,
-                          const double* __restrict__ d, const double* __restrict__ v,
+// Fixed-order sum of the block partials (x_b, y_b) by the last block of a grid (deterministic
+// whichever block finishes last); sc = {sum x, sum y, 1/sqrt(sum y)}.  counter: zero before,
+// zero after.
+__device__ void pi_last_block(const double* __restrict__ part, double* __restrict__ sc,
+                              unsigned int* __restrict__ counter, double* s_a, double* s_b) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double x = 0.0, y = 0.0;
+    for (int64_t i = threadIdx.x; i < gridDim.x; i += kThreads) {
+        x += __ldcg(part + 2 * i);
+        y += __ldcg(part + 2 * i + 1);
+    }
+    s_a[threadIdx.x] = x;
+    s_b[threadIdx.x] = y;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_a[threadIdx.x] += s_a[threadIdx.x + o];
+            s_b[threadIdx.x] += s_b[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sc[0] = s_a[0];
+        sc[1] = s_b[0];
+        sc[2] = s_b[0] > 0.0 ? 1.0 / sqrt(s_b[0]) : 0.0;
+        *counter = 0u;
+    }
+}
+
+// Block tree of (x, y) into part[2 * block], then the last block's fixed-order total.
+__device__ void pi_block_sums(double x, double y, double* __restrict__ part, double* __restrict__ sc,
+                              unsigned int* __restrict__ counter) {
+    __shared__ double s_a[kThreads], s_b[kThreads];
+    s_a[threadIdx.x] = x;
+    s_b[threadIdx.x] = y;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_a[threadIdx.x] += s_a[threadIdx.x + o];
+            s_b[threadIdx.x] += s_b[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s_a[0];
+        part[2 * blockIdx.x + 1] = s_b[0];
+    }
+    __syncthreads();
+    pi_last_block(part, sc, counter, s_a, s_b);
+}
+
+// Start: w = SplitMix64 vector, sc = {0, S-norm^2 of w, 1/S-norm of w}.
+__global__ void k_pi_start(double* __restrict__ w, const int64_t* __restrict__ perm,
+                           const double* __restrict__ S, uint32_t seed, int64_t n_t,
+                           double* __restrict__ part, double* __restrict__ sc,
+                           unsigned int* __restrict__ counter) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double ww = 0.0;
+    if (j < n_t) {
+        const uint64_t z = splitmix64(((uint64_t)seed << 32) + (uint64_t)perm[j]);
+        const double x = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+        w[j] = x;
+        ww = S[j] * x * x;
+    }
+    pi_block_sums(0.0, ww, part, sc, counter);
+}
+
+// g_k = c_k (v_R - v_L) with v = w * sc[2], the S-normalised iterate.
+__global__ void k_pi_edge(const int2* __restrict__ rl, const double* __restrict__ c,
+                          const double* __restrict__ w, const double* __restrict__ sc,
                           double* __restrict__ g, int64_t n_ei) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_ei) return;
+    const double inv = sc[2];
     const int2 e = rl[k];
-    g[k] = elen[k] * (v[e.x] - v[e.y]) / d[k];
+    g[k] = c[k] * (w[e.x] * inv - w[e.y] * inv);
 }
 
-// w = K v and block partial sums of S v w and S w w (fixed-order tree: deterministic).
-__global__ void k_pi_tri(const int4* __restrict__ tri, const double* __restrict__ S,
-                         const double* __restrict__ g, const double* __restrict__ v,
-                         double* __restrict__ w, double* __restrict__ part, int64_t n_t) {
-    __shared__ double s_vw[kThreads], s_ww[kThreads];
+// wn = K v: t_j = signed sum of the three g, wn_j = t_j / S_j.  Sums S v wn = v t (the
+// Rayleigh quotient, v S-normalised) and S wn^2 = wn t go to sc_next with 1/sqrt of the latter.
+__global__ void k_pi_tri(const int4* __restrict__ tri, const double* __restrict__ invS,
+                         const double* __restrict__ g, const double* __restrict__ w,
+                         const double* __restrict__ sc, double* __restrict__ wn,
+                         double* __restrict__ part, double* __restrict__ sc_next,
+                         unsigned int* __restrict__ counter, int64_t n_t) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double vw = 0.0, ww = 0.0;
     if (j < n_t) {
-        const int4 t = tri[j];
-        double a = g[t.x >> 1], b = g[t.y >> 1], c = g[t.z >> 1];
-        if (t.x & 1) a = -a;
-        if (t.y & 1) b = -b;
-        if (t.z & 1) c = -c;
-        const double x = (a + b + c) / S[j];
-        w[j] = x;
-        vw = S[j] * v[j] * x;
-        ww = S[j] * x * x;
+        const int4 q = tri[j];
+        double a = g[q.x >> 1], b = g[q.y >> 1], c = g[q.z >> 1];
+        if (q.x & 1) a = -a;
+        if (q.y & 1) b = -b;
+        if (q.z & 1) c = -c;
+        const double t = a + b + c;
+        const double x = t * invS[j];
+        wn[j] = x;
+        vw = (w[j] * sc[2]) * t;
+        ww = x * t;
     }
-    s_vw[threadIdx.x] = vw;
-    s_ww[threadIdx.x] = ww;
-    __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            s_vw[threadIdx.x] += s_vw[threadIdx.x + o];
-            s_ww[threadIdx.x] += s_ww[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s_vw[0];
-        part[2 * blockIdx.x + 1] = s_ww[0];
-    }
-}
-
-// Sum the block partials in a fixed order (one block), then scal[0] = sum vw, scal[1] = sum ww.
-__global__ void k_pi_reduce(const double* __restrict__ part, int64_t nb, double* __restrict__ scal) {
-    __shared__ double a[kThreads], b[kThreads];
-    double x = 0.0, y = 0.0;
-    for (int64_t i = threadIdx.x; i < nb; i += kThreads) {
-        x += part[2 * i];
-        y += part[2 * i + 1];
-    }
-    a[threadIdx.x] = x;
-    b[threadIdx.x] = y;
-    __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            a[threadIdx.x] += a[threadIdx.x + o];
-            b[threadIdx.x] += b[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        scal[0] = a[0];
-        scal[1] = b[0];
-    }
-}
-
-// v = w / sqrt(scal[1]) (S-normalisation).  Also the initial normalisation (w = v0).
-__global__ void k_pi_scale(const double* __restrict__ w, const double* __restrict__ scal,
-                           double* __restrict__ v, int64_t n_t) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
-    v[j] = w[j] / sqrt(scal[1]);
-}
-
-__global__ void k_pi_norm_parts(const double* __restrict__ S, const double* __restrict__ v,
-                                double* __restrict__ part, int64_t n_t) {
-    __shared__ double s_ww[kThreads];
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    s_ww[threadIdx.x] = j < n_t ? S[j] * v[j] * v[j] : 0.0;
-    __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s_ww[threadIdx.x] += s_ww[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = 0.0;
-        part[2 * blockIdx.x + 1] = s_ww[0];
-    }
+    pi_block_sums(vw, ww, part, sc_next, counter);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -440,33 +460,36 @@ cudaError_t launch_source_flags(const DevMesh& m, const int32_t* k, int64_t n, b
 
 size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei) {
     const int64_t nb = (n_t + kThreads - 1) / kThreads;
-    return (size_t)(2 * n_t + (n_ei + 1) + 2 * nb + 2);
+    return (size_t)(3 * n_t + 2 * n_ei + 1 + 2 * nb + 8 + 2);
 }
 
+// Two launches per iteration (edge, triangle with the reductions in its last block); the
+// iterate is normalised on the fly by the scale its previous reduction left.
 cudaError_t power_iteration(const int2* rl, const int4* tri, const double* elen, const double* d,
                             const double* S, const int64_t* perm_tri, int64_t n_t, int64_t n_ei,
                             int iters, uint32_t seed, double* work, double* rho, cudaStream_t s) {
     const int64_t nb = (n_t + kThreads - 1) / kThreads;
-    double* v = work;
-    double* w = v + n_t;
-    double* g = w + n_t;
-    double* part = g + (n_ei + 1);
-    double* scal = part + 2 * nb;
+    double* w[2] = {work, work + n_t};
+    double* invS = work + 2 * n_t;
+    double* g = invS + n_t;
+    double* c = g + (n_ei + 1);
+    double* part = c + n_ei;
+    double* sc[2] = {part + 2 * nb, part + 2 * nb + 4};
+    unsigned int* counter = reinterpret_cast<unsigned int*>(part + 2 * nb + 8);
     cudaError_t e;
     if ((e = cudaMemsetAsync(g, 0, sizeof(double) * (n_ei + 1), s)) != cudaSuccess) return e;
-    k_pi_init<<<blocks_for(n_t), kThreads, 0, s>>>(w, perm_tri, seed, n_t);
-    k_pi_norm_parts<<<(unsigned)nb, kThreads, 0, s>>>(S, w, part, n_t);
-    k_pi_reduce<<<1, kThreads, 0, s>>>(part, nb, scal);
-    k_pi_scale<<<blocks_for(n_t), kThreads, 0, s>>>(w, scal, v, n_t);
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(double), s)) != cudaSuccess) return e;
+    k_pi_prep<<<blocks_for(n_ei > n_t ? n_ei : n_t), kThreads, 0, s>>>(elen, d, S, c, invS, n_ei, n_t);
+    k_pi_start<<<(unsigned)nb, kThreads, 0, s>>>(w[0], perm_tri, S, seed, n_t, part, sc[0], counter);
     for (int it = 0; it < iters; ++it) {
-        if (n_ei > 0) k_pi_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(rl, elen, d, v, g, n_ei);
-        k_pi_tri<<<(unsigned)nb, kThreads, 0, s>>>(tri, S, g, v, w, part, n_t);
-        k_pi_reduce<<<1, kThreads, 0, s>>>(part, nb, scal);
-        if (it + 1 < iters) k_pi_scale<<<blocks_for(n_t), kThreads, 0, s>>>(w, scal, v, n_t);
+        const int cur = it & 1;
+        if (n_ei > 0) k_pi_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(rl, c, w[cur], sc[cur], g, n_ei);
+        k_pi_tri<<<(unsigned)nb, kThreads, 0, s>>>(tri, invS, g, w[cur], sc[cur], w[cur ^ 1], part,
+                                                  sc[cur ^ 1], counter, n_t);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double h[2];
-    if ((e = cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h, sc[iters & 1], sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     *rho = sqrt(h[0] > 0 ? h[0] : 0.0);
     return cudaSuccess;

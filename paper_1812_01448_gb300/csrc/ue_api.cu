@@ -929,6 +929,20 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
             B->src_grp.push_back(g);
         }
     }
+    if (B->variant == UE_VARIANT_PERSISTENT) {
+        // the batch's own grid-barrier words; wait budget and grid from its first mesh
+        if (!alloc_into(B, B->p_sync, 2, 4, s) || !alloc_into(B, B->p_err, 1, 4, s)) {
+            ue_mesh_free(B);
+            return fail(UE_ERR_ALLOC, "persistent barrier words");
+        }
+        if (cudaMemsetAsync(B->p_sync, 0, 8, s) != cudaSuccess || cudaMemsetAsync(B->p_err, 0, 4, s) != cudaSuccess) {
+            ue_mesh_free(B);
+            return fail(UE_ERR_CUDA, "persistent barrier words");
+        }
+        B->p_budget = m0->p_budget;
+        B->p_skip = -1;
+        B->p_grid = m0->p_grid;
+    }
     B->built = true;
     B->steps_done = 0;
     B->version++;

@@ -288,17 +288,19 @@ def _batch_members():
     return out
 
 
-@pytest.mark.parametrize("variant", ["plain", "blocked"])
+@pytest.mark.parametrize("variant", ["plain", "blocked", "persistent"])
 def test_batch_is_bit_identical_to_single_meshes(ue, variant):
     """Every mesh of a batch (own dt from its own power iteration, own source frequency) ends
-    bit-identical to the same mesh stepped alone; sizes and scatterers differ per mesh."""
+    bit-identical to the same mesh stepped alone; sizes and scatterers differ per mesh.  The
+    persistent batch advances all meshes in one cooperative launch per chunk of steps."""
     blocked = variant == "blocked"
+    code = {"plain": ue.UE_VARIANT_PLAIN, "blocked": ue.UE_VARIANT_BLOCKED,
+            "persistent": ue.UE_VARIANT_PERSISTENT}[variant]
     singles = []
     for i, (ms, ids, amp, w0) in enumerate(_batch_members()):
         m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
                     tile_tris=400)
-        m.geometry_build(power_iters=60, variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
-                         block_depth=3)
+        m.geometry_build(power_iters=60, variant=code, block_depth=3)
         m.set_source(ids, amp, w0, 0.0, 0.05)
         m.write_fields(B=np.cos(3.0 * ms.xy[ms.tris].mean(axis=1)[:, 1] + i))
         singles.append(m)

@@ -1,0 +1,41 @@
+"""Batch autotuner: sampling over the size distribution (host) and a tuned batch on the GPU."""
+import numpy as np
+import pytest
+
+from paper_1812_01448_gb300 import tune
+
+
+def test_spread_covers_the_size_range():
+    sizes = [50, 7, 300, 12, 99, 5, 1000, 64, 20, 8]
+    idx = tune.spread(sizes, 4)
+    assert len(idx) == 4 == len(set(idx))
+    got = sorted(sizes[i] for i in idx)
+    assert got[0] == min(sizes) and got[-1] == max(sizes)
+    assert sorted(tune.spread(sizes, 99)) == list(range(len(sizes)))
+
+
+def test_candidates_are_valid_launch_forms():
+    for variant, tile, depth, threads in tune.DEFAULT_CANDIDATES:
+        assert variant in ("plain", "persistent", "blocked")
+        assert tile >= 256 and threads in (512, 1024)
+        assert depth >= 1 and (variant == "blocked" or depth == 1)
+
+
+@pytest.mark.gpu
+def test_autotune_picks_a_measured_candidate():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import meshgen
+    from paper_1812_01448_gb300 import build
+    build.build()
+    items = []
+    for sp in meshgen.batch_specs(5, seed=77, n_min=3000, n_max=12000):
+        ms = meshgen.batch_mesh(sp)
+        ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.3, ms.h)
+        items.append((ms, ids, amp, sp["omega0"]))
+    cands = (("plain", 512, 1, 512), ("persistent", 512, 1, 512), ("blocked", 512, 4, 512))
+    best, table = tune.autotune_batch(items, candidates=cands, sample=3, steps=48)
+    assert table["sample_meshes"] == 3 and len(table["rows"]) == 3
+    assert all(r["rate"] > 0 and np.isfinite(r["rate"]) for r in table["rows"])
+    assert best["rate"] == max(r["rate"] for r in table["rows"])
