@@ -43,6 +43,8 @@ L2_BYTES = 129e6
 # the kernel source it measured: used only while that source is unchanged, else null.
 NCU_TRAFFIC = {
     # (variant, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
+    ("blocked", 2048, 8, 512): (313517995, "kernels_tb.cu", "343916293d9b5792702ecac381f1e8113735c383",
+                                "profiles/blocked_k_tb_scatterer4M.md"),
 }
 
 
