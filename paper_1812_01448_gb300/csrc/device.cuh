@@ -142,12 +142,14 @@ cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, f
                             float* loss, cudaStream_t s);
 // Fused learned-rho inference, one launch, on device-resident parameters, partials and
 // counter (one set per device: callers serialise).  rho_infer_upload copies the 5,057
-// parameters in.  out[5] (device-visible) = {log rho_hat, argmax row, max K_jj rounded down,
-// max Gershgorin bound rounded up, local Rayleigh quotient}.
+// parameters in.  out[0..4] (device-visible) = {log rho_hat, argmax row, max K_jj rounded
+// down, max Gershgorin bound rounded up, local Rayleigh quotient rounded down}; then the last
+// CTA writes seq into the 8 bytes of out[5], after a system-scope fence.
 cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s);
 cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                              const int32_t* tri_nb, const double* elen, const double* d, const double* S,
-                             int64_t n_t, int64_t n_ei, double* out, cudaStream_t s);
+                             int64_t n_t, int64_t n_ei, double* out, unsigned long long seq,
+                             cudaStream_t s);
 
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);

@@ -35,17 +35,21 @@ static_assert(kNParams == 5057, "parameter count");
 // ---------------------------------------------------------------------------------------
 // features (FP32, from FP64 geometry) and the per-triangle bracket terms
 // ---------------------------------------------------------------------------------------
-// Rounding slack of the FP32 bracket terms.  K_jj and the Gershgorin row bound are sums,
-// products, quotients and square roots of positive values, formed from FP64 inputs with at
-// most 12 conversions and correctly rounded FP32 operations on any path (relative error
-// <= 2^-24 each), so the computed value lies within a factor 1 +- 12 * 2^-24 of the exact
-// one.  Scaling by 1 -+ 2^-16 keeps the bounds certified with 20x room.  Outside the normal
-// FP32 range the terms give no bound (K_jj -> 0, Gershgorin -> +inf).
+// Rounding slack of the FP32 bracket terms.  K_jj and the Gershgorin row bound are sums and
+// products of positive values, formed from FP64 inputs by conversions and correctly rounded
+// adds and multiplies (<= 2^-24 relative each), __frcp_rn (<= 2^-24) and the 2-ulp
+// __fdividef and rsqrtf (<= 2^-22 each).  Along any path the errors add up to at most
+// 20 * 2^-24 (11 for K_jj, 20 for the Gershgorin bound, first order), so the computed values lie
+// within a factor 1 +- 20 * 2^-24 of the exact ones; scaling by 1 -+ 2^-16 keeps the bounds
+// certified with 12x room.  Outside the normal FP32 range the terms give no bound (K_jj -> 0,
+// Gershgorin -> +inf).
 constexpr double kBracketSlack = 1.0 / 65536.0;
 
-// One triangle's features, FP32 (coordinate differences taken in FP64 first, so that small
-// triangles far from the origin lose nothing; GB300's FP64 pipes are few, and every feature
-// ends in FP32 or BF16 anyway).  f[12] = base = log sqrt(K_jj).  kdiag = K_jj and gersh = the
+// One triangle's features, FP32.  The edge vectors are differences taken in FP64 (small
+// triangles far from the origin lose nothing), then rounded; lengths and areas enter as logs
+// of ratios near 1 (fast logs: every feature is rounded to BF16 before the first layer).
+// The angle opposite edge q lies at vertex q+2, between E_{q+2} and -E_{q+1}; the third angle
+// is pi minus the other two.  f[12] = base = log sqrt(K_jj).  kdiag = K_jj and gersh = the
 // Gershgorin row bound of S^{1/2} K S^{-1/2}, both before the slack above.  The gathers are
 // issued in two dependent rounds (row j's tables, then what they point to).
 __device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
@@ -74,33 +78,40 @@ __device__ __forceinline__ void triangle_features(const double* __restrict__ xy,
         dd[q] = in ? d[k[q]] : 1.0;
         sn[q] = in ? S[nb[q]] : 1.0;
     }
+    float ex[3], ey[3];
+    for (int q = 0; q < 3; ++q) {
+        const int b = q == 2 ? 0 : q + 1;
+        ex[q] = (float)(px[b] - px[q]);
+        ey[q] = (float)(py[b] - py[q]);
+    }
     const float Sj = (float)Sjd;
-    const float sq = __fsqrt_rn(Sj);
-    const float rs = 1.f / sq;
+    const float invS = __frcp_rn(Sj);
+    const float rs = rsqrtf(Sj);
+    for (int q = 0; q < 2; ++q) {
+        const int u = q + 2 > 2 ? q - 1 : q + 2, v = q + 1;
+        f[q] = atan2f(fabsf(ex[u] * ey[v] - ey[u] * ex[v]), -(ex[u] * ex[v] + ey[u] * ey[v]));
+    }
+    f[2] = 3.14159265358979f - f[0] - f[1];
     float kd = 0.f, off = 0.f;
     bool normal = Sj >= 1e-30f;
     for (int q = 0; q < 3; ++q) {
-        const int a = q, b = (q + 1) % 3, o = (q + 2) % 3;
-        const float ux = (float)(px[a] - px[o]), uy = (float)(py[a] - py[o]);
-        const float vx = (float)(px[b] - px[o]), vy = (float)(py[b] - py[o]);
-        f[q] = atan2f(fabsf(ux * vy - uy * vx), ux * vx + uy * vy);
-        f[3 + q] = logf(hypotf((float)(px[b] - px[a]), (float)(py[b] - py[a])) * rs);
+        f[3 + q] = 0.5f * __logf((ex[q] * ex[q] + ey[q] * ey[q]) * invS);
         if (k[q] < n_ei) {
             const float dk = (float)dd[q], Sn = (float)sn[q];
-            const float w = __fdiv_rn((float)el[q], dk);
-            f[6 + q] = logf(dk * rs);
-            f[9 + q] = logf(Sn / Sj);
+            const float w = __fdividef((float)el[q], dk);
+            f[6 + q] = __logf(dk * rs);
+            f[9 + q] = __logf(Sn * invS);
             kd = __fadd_rn(kd, w);
-            off = __fadd_rn(off, __fdiv_rn(w, __fmul_rn(sq, __fsqrt_rn(Sn))));
+            off = __fadd_rn(off, __fmul_rn(__fmul_rn(w, rs), rsqrtf(Sn)));
             normal = normal && Sn >= 1e-30f && dk >= 1e-30f;
         } else {
             f[6 + q] = 4.f;    // boundary: a dual so long the edge adds nothing to K
             f[9 + q] = 0.f;
         }
     }
-    kdiag = __fdiv_rn(kd, Sj);
+    kdiag = __fmul_rn(kd, invS);
     gersh = __fadd_rn(kdiag, off);
-    f[12] = kd > 0.f ? 0.5f * logf(kdiag) : -1e30f;
+    f[12] = kd > 0.f ? 0.5f * __logf(kdiag) : -1e30f;
     if (!normal || !(kdiag <= 1e37f) || !(gersh <= 1e37f)) {
         kdiag = 0.f;
         gersh = INFINITY;
@@ -140,27 +151,120 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 constexpr int kW1S = 16 + 8;     // smem row stride (bf16) of W1 padded to K = 16
 constexpr int kW2S = 64 + 8;     // smem row stride (bf16) of W2
 
+// The network as the tensor-core layers read it: BF16 weights at the padded row strides (rows
+// 16-byte aligned and 8 rows of an ldmatrix on distinct banks), FP32 biases.
+struct PackedNet {
+    __nv_bfloat16 w1[kH * kW1S];
+    __nv_bfloat16 w2[kH * kW2S];
+    float b1[kH], b2[kH], w3[kH];
+    float b3[4];
+};
+static_assert(sizeof(PackedNet) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// N from the parameter vector: weights to BF16 (round to nearest even), zeros in the padding.
+__device__ void pack_net(PackedNet& N, const float* __restrict__ P, int tid, int nth) {
+    for (int i = tid; i < kH * kW1S; i += nth) {
+        const int r = i / kW1S, c = i % kW1S;
+        N.w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
+    }
+    for (int i = tid; i < kH * kW2S; i += nth) {
+        const int r = i / kW2S, c = i % kW2S;
+        N.w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
+    }
+    for (int i = tid; i < kH; i += nth) {
+        N.b1[i] = P[kOffB1 + i];
+        N.b2[i] = P[kOffB2 + i];
+        N.w3[i] = P[kOffW3 + i];
+    }
+    if (tid < 4) N.b3[tid] = tid == 0 ? P[kOffB3] : 0.f;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// four 8x8 BF16 matrices from shared memory; lane l supplies row (l & 7) of matrix (l >> 3)
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(row)));
+}
+
+// One 16-row tile through the network on the tensor cores.  a0..a3: the A fragments of the
+// BF16 inputs (rows g and g+8, k 2t.. and 2t+8..).  The accumulators start at the biases; the
+// B fragments of two n-tiles come with one ldmatrix.x4.  Returns w3 . relu(h2) for rows g (s0)
+// and g+8 (s1), without b3, on all four lanes of each quad.
+__device__ __forceinline__ void mlp16(const PackedNet& N, uint32_t a0, uint32_t a1, uint32_t a2,
+                                      uint32_t a3, float& s0, float& s1) {
+    const int lane = threadIdx.x & 31, t = lane & 3, mrow = lane & 7, mi = lane >> 3;
+    float h1[8][4];
+#pragma unroll
+    for (int np = 0; np < 4; ++np) {
+        uint32_t b[4];
+        ldsm_x4(b, N.w1 + ((2 * np + (mi >> 1)) * 8 + mrow) * kW1S + (mi & 1) * 8);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int nt = 2 * np + h;
+            const float2 bb = *reinterpret_cast<const float2*>(N.b1 + nt * 8 + 2 * t);
+            h1[nt][0] = bb.x;
+            h1[nt][1] = bb.y;
+            h1[nt][2] = bb.x;
+            h1[nt][3] = bb.y;
+            mma_bf16(h1[nt], a0, a1, a2, a3, b[2 * h], b[2 * h + 1]);
+        }
+    }
+    // relu, then BF16: the C fragments of layer 1 (n-tiles 2kt, 2kt+1) are the A fragments of
+    // layer 2's k-tile kt
+    uint32_t c[4][4];
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        c[kt][0] = pack_bf16(fmaxf(h1[2 * kt][0], 0.f), fmaxf(h1[2 * kt][1], 0.f));
+        c[kt][1] = pack_bf16(fmaxf(h1[2 * kt][2], 0.f), fmaxf(h1[2 * kt][3], 0.f));
+        c[kt][2] = pack_bf16(fmaxf(h1[2 * kt + 1][0], 0.f), fmaxf(h1[2 * kt + 1][1], 0.f));
+        c[kt][3] = pack_bf16(fmaxf(h1[2 * kt + 1][2], 0.f), fmaxf(h1[2 * kt + 1][3], 0.f));
+    }
+    float h2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float2 bb = *reinterpret_cast<const float2*>(N.b2 + nt * 8 + 2 * t);
+        h2[nt][0] = bb.x;
+        h2[nt][1] = bb.y;
+        h2[nt][2] = bb.x;
+        h2[nt][3] = bb.y;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+        for (int np = 0; np < 4; ++np) {
+            uint32_t b[4];
+            ldsm_x4(b, N.w2 + ((2 * np + (mi >> 1)) * 8 + mrow) * kW2S + kt * 16 + (mi & 1) * 8);
+            mma_bf16(h2[2 * np], c[kt][0], c[kt][1], c[kt][2], c[kt][3], b[0], b[1]);
+            mma_bf16(h2[2 * np + 1], c[kt][0], c[kt][1], c[kt][2], c[kt][3], b[2], b[3]);
+        }
+    }
+    float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float2 w = *reinterpret_cast<const float2*>(N.w3 + nt * 8 + 2 * t);
+        x0 += w.x * fmaxf(h2[nt][0], 0.f) + w.y * fmaxf(h2[nt][1], 0.f);
+        x1 += w.x * fmaxf(h2[nt][2], 0.f) + w.y * fmaxf(h2[nt][3], 0.f);
+    }
+    x0 += __shfl_xor_sync(0xffffffffu, x0, 1);
+    x0 += __shfl_xor_sync(0xffffffffu, x0, 2);
+    x1 += __shfl_xor_sync(0xffffffffu, x1, 1);
+    x1 += __shfl_xor_sync(0xffffffffu, x1, 2);
+    s0 = x0;
+    s1 = x1;
+}
+
+// Forward on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation): one warp per 16 rows.
 __global__ void __launch_bounds__(128) k_mlp_fwd_bf16(const float* __restrict__ P,
                                                       const float* __restrict__ X, int64_t n,
                                                       float* __restrict__ z) {
-    __shared__ __nv_bfloat16 w1[kH * kW1S];
-    __shared__ __nv_bfloat16 w2[kH * kW2S];
-    __shared__ float bias1[kH], bias2[kH], w3[kH];
-    for (int i = threadIdx.x; i < kH * kW1S; i += blockDim.x) {
-        const int r = i / kW1S, c = i % kW1S;
-        w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kH * kW2S; i += blockDim.x) {
-        const int r = i / kW2S, c = i % kW2S;
-        w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-        bias1[i] = P[kOffB1 + i];
-        bias2[i] = P[kOffB2 + i];
-        w3[i] = P[kOffW3 + i];
-    }
-    const float b3 = P[kOffB3];
+    __shared__ __align__(16) PackedNet net;
+    pack_net(net, P, threadIdx.x, blockDim.x);
     __syncthreads();
+    const float b3 = net.b3[0];
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n;
@@ -171,51 +275,8 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_bf16(const float* __restrict__ 
         const uint32_t a1 = pack_bf16(xv(r1, 2 * t), xv(r1, 2 * t + 1));
         const uint32_t a2 = pack_bf16(xv(r0, 2 * t + 8), xv(r0, 2 * t + 9));
         const uint32_t a3 = pack_bf16(xv(r1, 2 * t + 8), xv(r1, 2 * t + 9));
-        // layer 1: [16 x 16] x [16 x 64]
-        float h1[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + 2 * t;
-            h1[nt][0] = h1[nt][1] = h1[nt][2] = h1[nt][3] = 0.f;
-            const __nv_bfloat16* wr = w1 + (nt * 8 + g) * kW1S;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 2 * t);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8);
-            mma_bf16(h1[nt], a0, a1, a2, a3, b0, b1);
-            h1[nt][0] = fmaxf(h1[nt][0] + bias1[col], 0.f);
-            h1[nt][1] = fmaxf(h1[nt][1] + bias1[col + 1], 0.f);
-            h1[nt][2] = fmaxf(h1[nt][2] + bias1[col], 0.f);
-            h1[nt][3] = fmaxf(h1[nt][3] + bias1[col + 1], 0.f);
-        }
-        // layer 2: [16 x 64] x [64 x 64]; C fragments of layer 1 are A fragments here
-        float h2[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            const uint32_t c0 = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
-            const uint32_t c1 = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
-            const uint32_t c2 = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
-            const uint32_t c3 = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const __nv_bfloat16* wr = w2 + (nt * 8 + g) * kW2S + kt * 16;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 2 * t);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8);
-                mma_bf16(h2[nt], c0, c1, c2, c3, b0, b1);
-            }
-        }
-        // layer 3 (FP32): z = w3 . relu(a2 + b2) + b3, rows r0 and r1
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + 2 * t;
-            s0 += w3[col] * fmaxf(h2[nt][0] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][1] + bias2[col + 1], 0.f);
-            s1 += w3[col] * fmaxf(h2[nt][2] + bias2[col], 0.f) + w3[col + 1] * fmaxf(h2[nt][3] + bias2[col + 1], 0.f);
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        float s0, s1;
+        mlp16(net, a0, a1, a2, a3, s0, s1);
         if (t == 0) {
             if (r0 < n) z[r0] = s0 + b3;
             if (r1 < n) z[r1] = s1 + b3;
@@ -232,16 +293,6 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_bf16(const float* __restrict__ 
 constexpr int kInferWarps = 4, kInferThreads = 32 * kInferWarps;
 constexpr int kRing = 6, kLoc = 256;
 
-// The network as the tensor-core layers read it (BF16 weights padded to the smem row strides,
-// FP32 biases): packed once per parameter upload, brought into shared memory by one TMA bulk
-// copy per block.
-struct PackedNet {
-    __nv_bfloat16 w1[kH * kW1S];
-    __nv_bfloat16 w2[kH * kW2S];
-    float b1[kH], b2[kH], w3[kH];
-    float b3[4];
-};
-static_assert(sizeof(PackedNet) % 16 == 0, "bulk copies move multiples of 16 bytes");
 struct InferSmem {
     PackedNet net;
     float feat[kInferWarps][32][kD + 1];
@@ -251,14 +302,12 @@ constexpr int kHash = 1024;      // open-addressing table of the neighbourhood, 
 struct RqSmem {
     int32_t ids[kLoc];          // triangles of rings 0..6 around the argmax, ring by ring
     int32_t hkey[kHash];        // triangle id, -1 empty
-    int32_t hval[kHash];        // >= 0: the smallest candidate index naming the key in the
-                                // current ring; < 0: in the set, at local index -1 - hval
-    union {
-        int32_t cslot[3 * kLoc];    // while building: hash slot of each candidate, -1 none
-        int32_t nbr[kLoc][3];       // then: local index of each neighbour, -1 outside the set
-    } u;
-    double a[kLoc][3];          // |e| / (d S_i) of each interior edge (K's off-diagonal weight)
-    double sv[kLoc], v[kLoc], kv[kLoc];
+    int32_t hval[kHash];        // local index of the member holding the key
+    int32_t nbq[kLoc][3];       // triangle across each edge (-1 boundary); later its local
+                                // index (-1 outside the set)
+    int32_t kq[kLoc][3];        // interior edge index of each edge (>= n_ei: boundary)
+    float a[kLoc][3];           // |e| / (d S_i) of each interior edge (K's off-diagonal weight)
+    float sv[kLoc], v[kLoc], kv[kLoc];
 };
 union RhoSmem {
     InferSmem a;
@@ -303,112 +352,130 @@ __device__ __forceinline__ int hash_find(const RqSmem& R, int32_t key) {
     return -1;
 }
 
-// Rayleigh quotient <v, K v>_S / <v, v>_S of v = K^5 delta_j0, on the rings 0..6 around j0
-// (exact there: K couples edge neighbours only, so K^5 delta_j0 lives on rings 0..5).  It
-// lower-bounds lambda_max(K) = rho^2.  0 when the neighbourhood exceeds kLoc triangles.
-// The rings are built breadth first; a shared hash table drops triangles already in the set
-// and keeps, of the repeats within a ring, the first in candidate order, so the local order
-// (and the rounding of the sums) does not depend on thread timing.  Runs on all threads of
-// one block; returns the value on every thread.
-__device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
-                                 const int32_t* __restrict__ tnb, const double* __restrict__ elen,
-                                 const double* __restrict__ d, const double* __restrict__ S,
-                                 int64_t n_ei, int32_t j0, double* red) {
-    __shared__ int s_n, s_over;
+// Slack of the local Rayleigh quotient.  Any vector's quotient lower-bounds lambda_max(K), so
+// the rounding of the five FP32 power steps costs only accuracy; what must be bounded is the
+// rounding of <v, K v>_S and <v, v>_S for the computed v.  Three FMAs per entry of K v and
+// sums of at most kLoc terms in a tree of depth <= 11 give a relative error below
+// 30 * 2^-24 * G / RQ, where G >= lambda_max is the Gershgorin bound.  Scaling by 1 - 2^-12
+// covers that while G / RQ <= 100; beyond, the quotient is dropped.
+constexpr double kRqSlack = 1.0 / 4096.0;
+constexpr double kRqMaxRatio = 100.0;
+
+// <v, K v>_S / <v, v>_S of v = K^5 delta_j0, on the rings 0..6 around j0 (exact there: K
+// couples edge neighbours only, so K^5 delta_j0 lives on rings 0..5).  Returns 0 when the
+// neighbourhood exceeds kLoc triangles.
+// Warp 0 walks the rings breadth first, without block barriers.  The candidates of a ring are
+// the table rows of its members; their own rows are loaded as soon as they are named, so the
+// deduplication (__match_any_sync keeps the first lane of equal candidates, the shared hash
+// drops members already in the set) runs under the load latency.  The local order (first
+// naming in candidate order, hence the rounding of the sums) does not depend on timing.  Then
+// all threads form K's weights and apply the scaled operator c K (c = 1/K_j0j0, so that FP32
+// does not overflow over five powers) six times.  Returns the value on every thread.
+__device__ float local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
+                                const int32_t* __restrict__ tnb, const double* __restrict__ elen,
+                                const double* __restrict__ d, const double* __restrict__ S,
+                                int64_t n_ei, int32_t j0, float* red) {
+    __shared__ int s_n;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
-    for (int i = tid; i < kHash; i += nth) {
-        R.hkey[i] = -1;
-        R.hval[i] = 0x7fffffff;
-    }
+    for (int i = tid; i < kHash; i += nth) R.hkey[i] = -1;
     __syncthreads();
-    if (tid == 0) {
-        R.hval[hash_insert(R, j0)] = -1;
-        R.ids[0] = j0;
-        s_n = 1;
-        s_over = 0;
-    }
-    __syncthreads();
-    int start = 0;
-    for (int r = 1; r <= kRing; ++r) {
-        const int end = s_n, cnt = 3 * (end - start);
-        for (int c = tid; c < cnt; c += nth) {
-            const int32_t o = tnb[3 * (int64_t)R.ids[start + c / 3] + c % 3];
-            int h = -1;
-            if (o >= 0) {
-                h = hash_insert(R, o);
-                if (h < 0) s_over = 1;
-                else atomicMin(&R.hval[h], c);
+    if (tid < 32) {
+        if (lane == 0) {
+            R.hval[hash_insert(R, j0)] = 0;
+            R.ids[0] = j0;
+            for (int q = 0; q < 3; ++q) {
+                R.nbq[0][q] = tnb[3 * (int64_t)j0 + q];
+                R.kq[0][q] = code[3 * (int64_t)j0 + q] >> 1;
             }
-            R.u.cslot[c] = h;
+            R.sv[0] = (float)S[j0];
         }
-        __syncthreads();
-        if (tid < 32) {   // warp 0 appends the first naming of each new triangle, in order
-            int n = end;
+        __syncwarp();
+        int n = 1, start = 0, end = 1;
+        bool over = false;
+        for (int r = 1; r <= kRing && !over; ++r) {
+            const int cnt = 3 * (end - start);
             for (int c0 = 0; c0 < cnt; c0 += 32) {
                 const int c = c0 + lane;
-                const int h = c < cnt ? R.u.cslot[c] : -1;
-                const bool keep = h >= 0 && R.hval[h] == c;
+                const int32_t o = c < cnt ? R.nbq[start + c / 3][c % 3] : -1;
+                int32_t t[3] = {-1, -1, -1}, kk[3] = {0, 0, 0};
+                double so = 0.0;
+                if (o >= 0) {   // the candidate's rows, in flight during the deduplication
+                    for (int q = 0; q < 3; ++q) {
+                        t[q] = tnb[3 * (int64_t)o + q];
+                        kk[q] = code[3 * (int64_t)o + q];
+                    }
+                    so = S[o];
+                }
+                const unsigned same = __match_any_sync(0xffffffffu, o);
+                const bool keep = o >= 0 && lane == __ffs(same) - 1 && hash_find(R, o) < 0;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 const int pos = n + __popc(m & ((1u << lane) - 1u));
-                if (keep && pos < kLoc) {
-                    R.ids[pos] = R.hkey[h];
-                    R.hval[h] = -1 - pos;
+                if (keep) {
+                    const int h = pos < kLoc ? hash_insert(R, o) : -1;
+                    if (h < 0) {
+                        over = true;
+                    } else {
+                        R.hval[h] = pos;
+                        R.ids[pos] = o;
+                        for (int q = 0; q < 3; ++q) {
+                            R.nbq[pos][q] = t[q];
+                            R.kq[pos][q] = kk[q] >> 1;
+                        }
+                        R.sv[pos] = (float)so;
+                    }
                 }
                 n += __popc(m);
+                over = __any_sync(0xffffffffu, over);
+                __syncwarp();
             }
-            if (lane == 0) {
-                if (n >= kLoc) s_over = 1;
-                s_n = n < kLoc ? n : kLoc;
-            }
+            if (n >= kLoc) over = true;
+            start = end;
+            end = n;
         }
-        __syncthreads();
-        start = end;
-        if (s_over) break;
-    }
-    if (s_over) return 0.0;
-    const int n = s_n;
-    __syncthreads();   // cslot is read no more; nbr takes its place
-    for (int i = tid; i < n; i += nth) {
-        const int32_t j = R.ids[i];
-        const double Sj = S[j];
-        R.sv[i] = Sj;
-        R.v[i] = i == 0 ? 1.0 : 0.0;
-        int64_t k[3];
-        int32_t o[3];
-        for (int q = 0; q < 3; ++q) {
-            k[q] = code[3 * (int64_t)j + q] >> 1;
-            o[q] = tnb[3 * (int64_t)j + q];
-        }
-        for (int q = 0; q < 3; ++q) {
-            R.u.nbr[i][q] = -1;
-            R.a[i][q] = 0.0;
-            if (k[q] >= n_ei) continue;
-            const int h = hash_find(R, o[q]);
-            if (h >= 0 && R.hval[h] < 0) R.u.nbr[i][q] = -1 - R.hval[h];
-            R.a[i][q] = elen[k[q]] / (d[k[q]] * Sj);
-        }
+        if (lane == 0) s_n = over ? -1 : n;
     }
     __syncthreads();
-    // (K v)_i = sum_q a_iq (v_i - v_nbr), a neighbour outside the set holding 0; six products,
-    // ping-ponging between v and kv, leave K^5 delta in kv and K^6 delta in v
-    double* va = R.v;
-    double* vb = R.kv;
+    const int n = s_n;
+    if (n < 0) return 0.f;
+    // local neighbour indices and weights
+    for (int e = tid; e < 3 * n; e += nth) {
+        const int i = e / 3, q = e % 3;
+        const int64_t k = R.kq[i][q];
+        int loc = -1;
+        float w = 0.f;
+        if (k < n_ei) {
+            const int h = hash_find(R, R.nbq[i][q]);
+            if (h >= 0) loc = R.hval[h];
+            w = __fdividef((float)elen[k], (float)d[k] * R.sv[i]);
+        }
+        R.nbq[i][q] = loc;
+        R.a[i][q] = w;
+    }
+    for (int i = tid; i < n; i += nth) R.v[i] = i == 0 ? 1.f : 0.f;
+    __syncthreads();
+    const float kjj = R.a[0][0] + R.a[0][1] + R.a[0][2];
+    if (!(kjj > 0.f)) return 0.f;
+    const float c = 1.f / kjj;
+    // (c K v)_i = c sum_q a_iq (v_i - v_nbr), a neighbour outside the set holding 0; six
+    // products, ping-ponging between v and kv, leave (cK)^5 delta in kv and (cK)^6 delta in v
+    float* va = R.v;
+    float* vb = R.kv;
     for (int it = 0; it < 6; ++it) {
         for (int i = tid; i < n; i += nth) {
-            const double vi = va[i];
-            double acc = 0.0;
+            const float vi = va[i];
+            float acc = 0.f;
             for (int q = 0; q < 3; ++q) {
-                const int nb = R.u.nbr[i][q];
-                acc = fma(R.a[i][q], vi - (nb >= 0 ? va[nb] : 0.0), acc);
+                const int nb = R.nbq[i][q];
+                acc = fmaf(R.a[i][q], vi - (nb >= 0 ? va[nb] : 0.f), acc);
             }
-            vb[i] = acc;
+            vb[i] = acc * c;
         }
         __syncthreads();
-        double* t = va;
+        float* t = va;
         va = vb;
         vb = t;
     }
-    double num = 0.0, den = 0.0;
+    float num = 0.f, den = 0.f;
     for (int i = tid; i < n; i += nth) {
         num += R.sv[i] * R.kv[i] * R.v[i];
         den += R.sv[i] * R.kv[i] * R.kv[i];
@@ -422,19 +489,16 @@ __device__ double local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
         red[2 * (tid >> 5) + 1] = den;
     }
     __syncthreads();
-    num = den = 0.0;
+    num = den = 0.f;
     for (int w = 0; w < (nth >> 5); ++w) {
         num += red[2 * w];
         den += red[2 * w + 1];
     }
-    return den > 0.0 ? num / den : 0.0;
+    return den > 0.f ? num / (den * c) : 0.f;
 }
 
 // mbarrier and bulk-copy (TMA) helpers.  Waits are bounded: a wait that runs out returns
 // false and the caller poisons its result instead of hanging.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
@@ -469,7 +533,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // Resident state of the fused inference (no allocation per call): the parameters, their packed
 // form, the block partials and the completion counter (zero between launches; the last block
 // resets it).
-constexpr int kInferMaxBlocks = 152 * 8;
+constexpr int kInferMaxBlocks = 152 * 6;
 __device__ float g_rho_params[kNParams];
 __device__ __align__(128) PackedNet g_rho_packed;
 __device__ RhoPart g_rho_parts[kInferMaxBlocks];
@@ -477,15 +541,15 @@ __device__ unsigned int g_rho_counter;
 
 // out = {log rho_hat, row, max K_jj (rounded down), max Gershgorin (rounded up), Rayleigh
 // quotient}; host-mapped memory in the library's use, any device-visible buffer works.
-__global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
+__global__ void __launch_bounds__(kInferThreads, 6) k_rho_infer(
     const double* __restrict__ xy, const int32_t* __restrict__ tn,
     const int32_t* __restrict__ code, const int32_t* __restrict__ tnb, const double* __restrict__ elen,
     const double* __restrict__ d, const double* __restrict__ S, int64_t n, int64_t n_ei,
-    double* __restrict__ out) {
+    double* __restrict__ out, unsigned long long seq) {
     __shared__ __align__(128) RhoSmem sm;
     __shared__ __align__(8) uint64_t net_bar;
     __shared__ RhoPart red[kInferWarps];
-    __shared__ double dred[2 * kInferWarps];
+    __shared__ float dred[2 * kInferWarps];
     __shared__ int s_last;
     InferSmem& A = sm.a;
     unsigned int* counter = &g_rho_counter;
@@ -526,46 +590,8 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
             const uint32_t a1 = pack_bf16(xv(x1, 2 * t), xv(x1, 2 * t + 1));
             const uint32_t a2 = pack_bf16(xv(x0, 2 * t + 8), xv(x0, 2 * t + 9));
             const uint32_t a3 = pack_bf16(xv(x1, 2 * t + 8), xv(x1, 2 * t + 9));
-            float h1[8][4];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = nt * 8 + 2 * t;
-                h1[nt][0] = h1[nt][1] = h1[nt][2] = h1[nt][3] = 0.f;
-                const __nv_bfloat16* wr = A.net.w1 + (nt * 8 + g) * kW1S;
-                mma_bf16(h1[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
-                         *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
-                h1[nt][0] = fmaxf(h1[nt][0] + A.net.b1[col], 0.f);
-                h1[nt][1] = fmaxf(h1[nt][1] + A.net.b1[col + 1], 0.f);
-                h1[nt][2] = fmaxf(h1[nt][2] + A.net.b1[col], 0.f);
-                h1[nt][3] = fmaxf(h1[nt][3] + A.net.b1[col + 1], 0.f);
-            }
-            float h2[8][4];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                const uint32_t c0 = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
-                const uint32_t c1 = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
-                const uint32_t c2 = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
-                const uint32_t c3 = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const __nv_bfloat16* wr = A.net.w2 + (nt * 8 + g) * kW2S + kt * 16;
-                    mma_bf16(h2[nt], c0, c1, c2, c3, *reinterpret_cast<const uint32_t*>(wr + 2 * t),
-                             *reinterpret_cast<const uint32_t*>(wr + 2 * t + 8));
-                }
-            }
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = nt * 8 + 2 * t;
-                s0 += A.net.w3[col] * fmaxf(h2[nt][0] + A.net.b2[col], 0.f) + A.net.w3[col + 1] * fmaxf(h2[nt][1] + A.net.b2[col + 1], 0.f);
-                s1 += A.net.w3[col] * fmaxf(h2[nt][2] + A.net.b2[col], 0.f) + A.net.w3[col + 1] * fmaxf(h2[nt][3] + A.net.b2[col + 1], 0.f);
-            }
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            float s0, s1;
+            mlp16(A.net, a0, a1, a2, a3, s0, s1);
             if (t == 0) {
                 const int64_t r0 = tile * 32 + 16 * half + g, r1 = r0 + 8;
                 if (r0 < n) better(best, arg, s0 + b3 + x0[kD], (int32_t)r0);
@@ -602,11 +628,20 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
     best = -INFINITY;
     arg = -1;
     kmax = gmax = 0.f;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        const float4 q = __ldcg(reinterpret_cast<const float4*>(part + i));
-        better(best, arg, q.x, __float_as_int(q.y));
-        kmax = fmaxf(kmax, q.z);
-        gmax = fmaxf(gmax, q.w);
+    // all of a thread's partials in flight at once (at most kInferMaxBlocks / kInferThreads)
+    constexpr int kPer = (kInferMaxBlocks + kInferThreads - 1) / kInferThreads;
+    float4 q[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = threadIdx.x + u * kInferThreads;
+        q[u] = i < (int)gridDim.x ? __ldcg(reinterpret_cast<const float4*>(part + i))
+                                  : make_float4(-INFINITY, __int_as_float(-1), 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        better(best, arg, q[u].x, __float_as_int(q[u].y));
+        kmax = fmaxf(kmax, q[u].z);
+        gmax = fmaxf(gmax, q[u].w);
     }
     for (int o = 16; o > 0; o >>= 1) {
         better(best, arg, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, arg, o));
@@ -622,7 +657,8 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
         r.kmax = fmaxf(r.kmax, red[w].kmax);
         r.gmax = fmaxf(r.gmax, red[w].gmax);
     }
-    const double rq = r.arg >= 0 ? local_rayleigh(sm.b, code, tnb, elen, d, S, n_ei, r.arg, dred) : 0.0;
+    double rq = r.arg >= 0 ? (double)local_rayleigh(sm.b, code, tnb, elen, d, S, n_ei, r.arg, dred) : 0.0;
+    rq = rq > 0.0 && (double)r.gmax <= kRqMaxRatio * rq ? rq * (1.0 - kRqSlack) : 0.0;
     if (threadIdx.x == 0) {
         *counter = 0u;
         out[0] = (double)r.best;
@@ -630,6 +666,9 @@ __global__ void __launch_bounds__(kInferThreads, 8) k_rho_infer(
         out[2] = (double)r.kmax * (1.0 - kBracketSlack);
         out[3] = (double)r.gmax * (1.0 + kBracketSlack);
         out[4] = rq;
+        // completion word last: the host may read out[0..4] once it sees seq
+        __threadfence_system();
+        reinterpret_cast<volatile unsigned long long*>(out)[5] = seq;
     }
 }
 
@@ -822,27 +861,10 @@ cudaError_t launch_rho_loss(const float* best, const float* target, int n_seg, f
 
 // g_rho_packed from g_rho_params: weights to BF16 (round to nearest even) at the padded smem
 // strides, zeros in the padding.
-__global__ void k_pack_net() {
-    PackedNet& N = g_rho_packed;
-    const float* P = g_rho_params;
-    for (int i = threadIdx.x; i < kH * kW1S; i += blockDim.x) {
-        const int r = i / kW1S, c = i % kW1S;
-        N.w1[i] = __float2bfloat16_rn(c < kD ? P[kOffW1 + r * kD + c] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kH * kW2S; i += blockDim.x) {
-        const int r = i / kW2S, c = i % kW2S;
-        N.w2[i] = __float2bfloat16_rn(c < kH ? P[kOffW2 + r * kH + c] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-        N.b1[i] = P[kOffB1 + i];
-        N.b2[i] = P[kOffB2 + i];
-        N.w3[i] = P[kOffW3 + i];
-    }
-    if (threadIdx.x < 4) N.b3[threadIdx.x] = threadIdx.x == 0 ? P[kOffB3] : 0.f;
-}
+__global__ void k_pack_net() { pack_net(g_rho_packed, g_rho_params, threadIdx.x, blockDim.x); }
 
 // Blocks of the fused inference: enough for every warp to take one 32-triangle tile, at most
-// 8 resident blocks on each of the 152 SMs.
+// 6 resident blocks on each of the 152 SMs.
 static int rho_infer_grid(int64_t n_t) {
     const int64_t need = (n_t + kInferThreads - 1) / kInferThreads;
     return (int)(need < 1 ? 1 : need > kInferMaxBlocks ? kInferMaxBlocks : need);
@@ -858,9 +880,10 @@ cudaError_t rho_infer_upload(const float* P_host, cudaStream_t s) {
 
 cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const int32_t* tri_code,
                              const int32_t* tri_nb, const double* elen, const double* d, const double* S,
-                             int64_t n_t, int64_t n_ei, double* out, cudaStream_t s) {
+                             int64_t n_t, int64_t n_ei, double* out, unsigned long long seq,
+                             cudaStream_t s) {
     k_rho_infer<<<rho_infer_grid(n_t), kInferThreads, 0, s>>>(xy, tri_nodes, tri_code, tri_nb, elen, d,
-                                                             S, n_t, n_ei, out);
+                                                             S, n_t, n_ei, out, seq);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -434,6 +435,7 @@ int ensure_tri_nb(ue_mesh* m, cudaStream_t s) {
 struct LearnedRes {
     double* h_out = nullptr;
     double* d_out = nullptr;
+    unsigned long long seq = 0;
     std::vector<float> params;
 };
 constexpr int kMaxDevices = 64;
@@ -456,6 +458,7 @@ LearnedRes* learned_res() {
             cudaFreeHost(h);
             return nullptr;
         }
+        std::memset(h, 0, 8 * sizeof(double));
         r.h_out = (double*)h;
         r.d_out = (double*)dp;
     }
@@ -471,9 +474,26 @@ int learned_rho(ue_mesh* m, const ue_options& o, LearnedRes* r, cudaStream_t s) 
         UE_CUDA(ue::rho_infer_upload(o.mlp_params, s));
         r->params.assign(o.mlp_params, o.mlp_params + np);
     }
+    const unsigned long long seq = ++r->seq;
     UE_CUDA(ue::launch_rho_infer(m->d_xy, m->d_tri_nodes, m->d_tri_code, m->d_tri_nb, m->d_elen,
-                                 m->d_d, m->d_S, m->hm.n_tris, m->hm.n_ei, r->d_out, s));
-    UE_CUDA(cudaStreamSynchronize(s));
+                                 m->d_d, m->d_S, m->hm.n_tris, m->hm.n_ei, r->d_out, seq, s));
+    // The kernel's last write is seq into the mapped buffer: spin on it (up to 2 s, then let
+    // the stream report), which returns sooner than a stream synchronisation.
+    const volatile unsigned long long* flag = reinterpret_cast<const volatile unsigned long long*>(r->h_out + 5);
+    const auto t_spin = std::chrono::steady_clock::now();
+    bool seen = false;
+    for (unsigned it = 1;; ++it) {
+        if (*flag == seq) {
+            seen = true;
+            break;
+        }
+        if ((it & 1023u) == 0 && std::chrono::steady_clock::now() - t_spin > std::chrono::seconds(2)) break;
+    }
+    if (!seen) {
+        UE_CUDA(cudaStreamSynchronize(s));
+        if (*flag != seq) return fail(UE_ERR_CUDA, "learned dt: inference finished without its result");
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
     const volatile double* rh = r->h_out;
     m->rho_hat = std::exp(rh[0]);
     m->rho_lo = std::sqrt(std::max(rh[2], rh[4]));

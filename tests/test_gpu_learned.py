@@ -187,8 +187,9 @@ def test_resident_parameters_follow_the_caller(ue):
 
 def test_bracket_matches_oracle(ue):
     """rho_lo^2 = max(max_j K_jj rounded down, Rayleigh quotient of K^5 delta_j* at the argmax
-    triangle j*) and rho_hi^2 = the Gershgorin bound rounded up, against the FP64 oracle: the
-    FP32 terms within their 2^-16 slack and on the certified side, the quotient to 1e-10."""
+    triangle j* rounded down) and rho_hi^2 = the Gershgorin bound rounded up, against the FP64
+    oracle: each FP32 term within its slack (2^-16 for the bracket terms, 2^-12 for the
+    quotient) and on the certified side."""
     import torch
     ms = meshgen.learned_mesh(meshgen.learned_specs(1, seed=29, n_min=3000, n_max=6000)[0])
     p32 = learned_params(ue)
@@ -210,13 +211,11 @@ def test_bracket_matches_oracle(ue):
     kd = float(spectral.diag_K(ops).max())
     _, hi = spectral.certified_bracket(ops)
     rq = spectral.local_rayleigh(ops, j_star, 5)
-    slack = 2.0 ** -16
+    slack, rq_slack = 2.0 ** -16, 2.0 ** -12
     lo2 = st["rho_lo"] ** 2
     assert lo2 <= max(kd, rq) * (1 + 1e-12)                      # still a lower bound
-    if rq >= kd:
-        assert abs(lo2 / rq - 1) < 1e-10
-    else:
-        assert abs(lo2 / (kd * (1 - slack)) - 1) < 2e-6
+    want = max(kd * (1 - slack), rq * (1 - rq_slack))
+    assert abs(lo2 / want - 1) < 2e-5, (lo2, kd, rq)
     assert st["rho_hi"] >= hi                                     # still an upper bound
     assert st["rho_hi"] ** 2 <= hi * hi * (1 + 2 * slack)
 
