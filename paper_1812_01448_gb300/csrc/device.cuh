@@ -10,6 +10,59 @@
 
 namespace ue {
 
+// Shared-memory copy helpers (inline PTX): mbarriers, TMA bulk copies global -> shared, and
+// 4-byte cp.async gathers.  mbarrier waits are bounded: a wait that runs out returns false and
+// the caller records an error instead of hanging.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// one arrival that expects `bytes` of bulk-copy transactions on bar
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// bulk copy global -> shared completing on bar (16-byte aligned addresses, bytes % 16 == 0)
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// one thread: arm the barrier for `bytes` and start one copy
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    mbar_expect_tx(bar, bytes);
+    bulk_copy_g2s(dst, src, bytes, bar);
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Arithmetic with explicit rounding: every variant of the step evaluates the same sequence of
 // correctly rounded operations, so their results are bit-identical (no contraction choices).
 __device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -74,7 +127,9 @@ struct TBDev {
     void* B[2] = {nullptr, nullptr};
     void* U[2] = {nullptr, nullptr};
     void* J[2] = {nullptr, nullptr};
-    unsigned* done = nullptr;     // CTA completion counter (step counter hand-off)
+    unsigned* done = nullptr;     // [0] CTA completion counter (step counter hand-off),
+                                  // [1] error word (a bounded copy wait of k_tbp ran out)
+    int sms = 0;                  // SMs of the device: CTAs of the pipelined persistent form
 };
 
 int tb_threads();

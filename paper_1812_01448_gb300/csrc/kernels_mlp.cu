@@ -179,10 +179,6 @@ __device__ void pack_net(PackedNet& N, const float* __restrict__ P, int tid, int
     if (tid < 4) N.b3[tid] = tid == 0 ? P[kOffB3] : 0.f;
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 // four 8x8 BF16 matrices from shared memory; lane l supplies row (l & 7) of matrix (l >> 3)
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -495,39 +491,6 @@ __device__ float local_rayleigh(RqSmem& R, const int32_t* __restrict__ code,
         den += red[2 * w + 1];
     }
     return den > 0.f ? num / (den * c) : 0.f;
-}
-
-// mbarrier and bulk-copy (TMA) helpers.  Waits are bounded: a wait that runs out returns
-// false and the caller poisons its result instead of hanging.
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// one thread: arm the barrier for `bytes` and start the copy global -> shared (16-byte aligned
-// addresses, bytes a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 // Resident state of the fused inference (no allocation per call): the parameters, their packed

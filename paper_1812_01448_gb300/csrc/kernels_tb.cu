@@ -36,6 +36,7 @@ struct TBArgs {
     int gbase;
     long long* step;
     unsigned* done;
+    unsigned* err;      // set when a bounded copy wait of k_tbp runs out
     int ksteps;
     float pa, mdt;
 };
@@ -320,6 +321,236 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
     }
 }
 
+// One E half-step and one B half-step over a thread's slots, slots taken G at a time: all
+// gathers of a group are issued before its stores.  B and U are distinct arrays (restrict), so
+// the compiler may also lift the next group's gathers above this group's stores.  The
+// arithmetic is k_tb's, operation for operation.
+template <int NT, int ES, int G>
+__device__ __forceinline__ void tb_edges(const float* __restrict__ B, float* __restrict__ U,
+                                         const int (&erl)[ES], const float (&ecu)[ES], int tid,
+                                         int eend) {
+#pragma unroll
+    for (int g0 = 0; g0 < ES; g0 += G) {
+        float bR[G], bL[G], uo[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = g0 + q, l = tid + i * NT;
+            if (i < ES && l < eend) {
+                bR[q] = B[erl[i] & 0xFFFF];
+                bL[q] = B[(unsigned)erl[i] >> 16];
+                uo[q] = U[l];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = g0 + q, l = tid + i * NT;
+            if (i < ES && l < eend) U[l] = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo[q]);
+        }
+    }
+}
+
+template <int NT, int TS, int G>
+__device__ __forceinline__ void tb_tris(const float* __restrict__ U, float* __restrict__ B,
+                                        const int (&tc01)[TS], const int (&tc2)[TS],
+                                        const float (&tcb)[TS], int tid, int tend) {
+#pragma unroll
+    for (int g0 = 0; g0 < TS; g0 += G) {
+        float u0[G], u1[G], u2[G], bo[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = g0 + q, l = tid + i * NT;
+            if (i < TS && l < tend) {
+                u0[q] = U[(tc01[i] & 0xFFFF) >> 1];
+                u1[q] = U[((unsigned)tc01[i] >> 16) >> 1];
+                u2[q] = U[tc2[i] >> 1];
+                bo[q] = B[l];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = g0 + q, l = tid + i * NT;
+            if (i < TS && l < tend) {
+                const int c0 = tc01[i], c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
+                const float x0 = (c0 & 1) ? -u0[q] : u0[q];
+                const float x1 = (c1 & 1) ? -u1[q] : u1[q];
+                const float x2 = (c2 & 1) ? -u2[q] : u2[q];
+                B[l] = rn_fma(-tcb[i], rn_add(rn_add(x0, x1), x2), bo[q]);
+            }
+        }
+    }
+}
+
+// Slots per gather group in k_tbp's half-steps.
+constexpr int kTbpG = 1;
+// Threads of k_tbp (512: the register-slot layouts of k_tb; 768 and 1024: fewer slots per thread).
+constexpr int kTbpNT = 512;
+
+// Pipelined persistent form (no plasma): one CTA per SM walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  While it advances one tile k steps, the next tile arrives in
+// three stages, each started after a step: its header (TMA bulk copy), its records (TMA bulk
+// copies into a staging area) and its fields (4-byte cp.async gathers into the second field
+// buffer).  The global loads of a tile thus overlap the previous tile's steps instead of
+// stalling the SM.  Each thread keeps its slots' records in registers for the k steps and
+// repeats k_tb's arithmetic slot by slot, so the results are bit-identical.
+// Dynamic shared memory: two field buffers of FB floats (B at 0, U at TL), then the staging
+// records (TL triangle records, EL edge records).
+template <int NT, int TS, int ES, bool SRC>
+__global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, int EL) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(16) int hs[2][48];
+    __shared__ __align__(8) uint64_t bar_h, bar_r;
+    const int tid = threadIdx.x;
+    const int FB = (TL + EL + 1 + 3) & ~3;
+    float* F0 = reinterpret_cast<float*>(smraw);
+    int4* tstage = reinterpret_cast<int4*>(F0 + 2 * FB);
+    int4* estage = tstage + TL;
+    if (tid == 0) {
+        mbar_init(&bar_h, 1);
+        mbar_init(&bar_r, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const long long n0 = *a.step;
+    uint32_t ph_h = 0, ph_r = 0;
+    bool ok = true;
+    auto wait_bar = [&](uint64_t* bar, uint32_t& ph) {
+        if (!mbar_wait(bar, ph)) ok = false;
+        ph ^= 1u;
+    };
+    auto issue_header = [&](int t, int b) {
+        if (tid == 0) {
+            fence_proxy_async();
+            bulk_g2s(hs[b], a.hdr + (size_t)t * 48, 48 * sizeof(int), &bar_h);
+        }
+    };
+    auto issue_records = [&](int b) {
+        if (tid == 0) {
+            const uint32_t tb = 16u * (uint32_t)hs[b][4], eb = 16u * (uint32_t)hs[b][5];
+            fence_proxy_async();
+            mbar_expect_tx(&bar_r, tb + eb);
+            if (tb) bulk_copy_g2s(tstage, a.trec + hs[b][6], tb, &bar_r);
+            if (eb) bulk_copy_g2s(estage, a.erec + hs[b][7], eb, &bar_r);
+        }
+    };
+    auto issue_fields = [&](int b) {
+        const int ntl = hs[b][4], nel = hs[b][5];
+        float* Bn = F0 + b * FB;
+        float* Un = Bn + TL;
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            const int l = tid + i * NT;
+            if (l < ntl) cp_async4(Bn + l, a.Bin + tstage[l].x);
+        }
+#pragma unroll
+        for (int i = 0; i < ES; ++i) {
+            const int l = tid + i * NT;
+            if (l < nel) cp_async4(Un + l, a.Uin + estage[l].x);
+        }
+        if (tid == 0) Un[nel] = 0.f;
+        cp_async_commit();
+    };
+    int cur = 0;
+    int tile = blockIdx.x;
+    if (tile < n_tiles) {
+        issue_header(tile, 0);
+        wait_bar(&bar_h, ph_h);
+        issue_records(0);
+        wait_bar(&bar_r, ph_r);
+        issue_fields(0);
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    int tc01[TS], tc2[TS];
+    float tcb[TS];
+    int erl[ES];
+    float ecu[ES];
+    for (; tile < n_tiles; tile += gridDim.x) {
+        const bool has_next = tile + (int)gridDim.x < n_tiles;
+        const int* h = hs[cur];
+        float* Bl = F0 + cur * FB;
+        float* Ul = Bl + TL;
+        const int ntl = h[4], nel = h[5];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            const int l = tid + i * NT;
+            if (l < ntl) {
+                const int4 r = tstage[l];
+                tc01[i] = r.y;
+                tc2[i] = r.z;
+                tcb[i] = __int_as_float(r.w);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ES; ++i) {
+            const int l = tid + i * NT;
+            if (l < nel) {
+                const int4 r = estage[l];
+                erl[i] = r.y;
+                ecu[i] = __int_as_float(r.z);
+            }
+        }
+        __syncthreads();   // the staging area is free for the next tile's records
+        if (has_next) issue_header(tile + gridDim.x, cur ^ 1);
+        for (int s = 1; s <= a.ksteps; ++s) {
+            const int lim = a.ksteps - s;
+            const int eend = h[32 + lim];
+            tb_edges<NT, ES, kTbpG>(Bl, Ul, erl, ecu, tid, eend);
+            if constexpr (SRC) {
+                if (h[9] > 0) {
+                    __syncthreads();
+                    for (int i = tid; i < h[9]; i += NT) {
+                        const int2 q = __ldg(a.tsrc + h[8] + i);
+                        if (q.x < eend) {
+                            const float g = (float)__ldg(a.gtab + (size_t)__ldg(a.src_grp + q.y) * a.gstride +
+                                                         a.gbase + s - 1);
+                            Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const int tend = h[16 + lim];
+            tb_tris<NT, TS, kTbpG>(Ul, Bl, tc01, tc2, tcb, tid, tend);
+            __syncthreads();
+            if (has_next) {
+                if (s == 1) {
+                    wait_bar(&bar_h, ph_h);
+                    issue_records(cur ^ 1);
+                }
+                if (s == (a.ksteps >= 2 ? 2 : 1)) {
+                    wait_bar(&bar_r, ph_r);
+                    issue_fields(cur ^ 1);
+                }
+            }
+        }
+        const int nto = h[1], neo = h[3];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            const int l = tid + i * NT;
+            if (l < nto) a.Bout[h[0] + l] = Bl[l];
+        }
+#pragma unroll
+        for (int i = 0; i < ES; ++i) {
+            const int l = tid + i * NT;
+            if (l < neo) a.Uout[h[2] + l] = Ul[l];
+        }
+        if (has_next) cp_async_wait_all();
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (!ok) atomicOr(a.err, 1u);
+    // the last CTA to finish advances the step counter (every CTA has read it by then)
+    if (tid == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(a.done, 1u);
+        if (t == gridDim.x - 1) {
+            *a.step = n0 + a.ksteps;
+            *a.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
 // Fill the coefficient slots of the tile records from the global coefficient arrays.
 __global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restrict__ erec,
                           int64_t n_erec, const int4* __restrict__ tri, const float* __restrict__ cU,
@@ -340,6 +571,23 @@ cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t 
     if (e != cudaSuccess) return e;
     kern<<<n_tiles, NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int NT, int TS, int ES, bool SRC>
+cudaError_t launch_tbp_t(const TBArgs& a, int n_tiles, int grid, int TL, int EL, size_t smem,
+                         cudaStream_t s) {
+    auto kern = k_tbp<NT, TS, ES, SRC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, smem, s>>>(a, n_tiles, TL, EL);
+    return cudaGetLastError();
+}
+
+template <int NT, int TS, int ES>
+cudaError_t launch_tbp_s(const TBArgs& a, bool src, int n_tiles, int grid, int TL, int EL,
+                         size_t smem, cudaStream_t s) {
+    return src ? launch_tbp_t<NT, TS, ES, true>(a, n_tiles, grid, TL, EL, smem, s)
+               : launch_tbp_t<NT, TS, ES, false>(a, n_tiles, grid, TL, EL, smem, s);
 }
 
 template <bool PLASMA, bool SRC>
@@ -369,6 +617,14 @@ int tb_threads() { return kNT; }
 size_t tbs_smem(int ntl, int nel, bool plasma) {
     return 4 * ((size_t)ntl + nel + 1) + (plasma ? 4 * ((size_t)nel + 1) : 0) + 8 +
            12 * (size_t)ntl + (plasma ? 12 : 8) * (size_t)nel;
+}
+
+// k_tbp: two field buffers and the staging records, within the opt-in shared memory per CTA
+// (static shared memory of the kernel aside).
+constexpr size_t kTbpSmemMax = 227 * 1024 - 512;
+size_t tbp_smem(int tl, int el) {
+    const size_t fb = ((size_t)tl + el + 1 + 3) & ~(size_t)3;
+    return 2 * 4 * fb + 16 * ((size_t)tl + el);
 }
 
 bool tb_fits(int max_tri_loc, int max_edge_loc, int threads) {
@@ -406,6 +662,7 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     a.gbase = gbase;
     a.step = m.step;
     a.done = t.done;
+    a.err = t.done + 1;
     a.ksteps = ksteps;
     a.pa = (float)m.pa;
     a.mdt = (float)(-m.dt);
@@ -418,6 +675,23 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
                                  : launch_tbs_t<true, false>(a, (int)t.n_tiles, sm2, s);
         return src ? launch_tbs_t<false, true>(a, (int)t.n_tiles, sm2, s)
                    : launch_tbs_t<false, false>(a, (int)t.n_tiles, sm2, s);
+    }
+    // pipelined persistent form when two field buffers and the staging records fit
+    const size_t smem_p = tbp_smem(t.max_tri_loc, t.max_edge_loc);
+    if (!m.plasma && t.sms > 0 && smem_p <= kTbpSmemMax) {
+        const int TL = t.max_tri_loc, EL = t.max_edge_loc, nt = (int)t.n_tiles;
+        const int grid = nt < t.sms ? nt : t.sms;
+        if (kTbpNT == 1024) {
+            if (TL <= 2 * 1024 && EL <= 3 * 1024) return launch_tbp_s<1024, 2, 3>(a, src, nt, grid, TL, EL, smem_p, s);
+            return launch_tbp_s<1024, 4, 6>(a, src, nt, grid, TL, EL, smem_p, s);
+        }
+        if (kTbpNT == 768) {
+            if (TL <= 3 * 768 && EL <= 4 * 768) return launch_tbp_s<768, 3, 4>(a, src, nt, grid, TL, EL, smem_p, s);
+            return launch_tbp_s<768, 6, 8>(a, src, nt, grid, TL, EL, smem_p, s);
+        }
+        if (TL <= 4 * kNT && EL <= 6 * kNT) return launch_tbp_s<kNT, 4, 6>(a, src, nt, grid, TL, EL, smem_p, s);
+        if (TL <= 6 * kNT && EL <= 9 * kNT) return launch_tbp_s<kNT, 6, 9>(a, src, nt, grid, TL, EL, smem_p, s);
+        return launch_tbp_s<kNT, 8, 12>(a, src, nt, grid, TL, EL, smem_p, s);
     }
     if (t.max_tri_loc <= 4 * kNT && t.max_edge_loc <= 6 * kNT)
         return launch_tb_ps<kNT, 4, 6, 2, 3>(a, m.plasma, src, (int)t.n_tiles, smem, s);

@@ -395,7 +395,7 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     tb.max_edge_loc = ts.max_edge_loc;
     tb.threads = m->tb_threads;
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
-              alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 1, 4, s) &&
+              alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 2, 4, s) &&
               alloc_into(m, tb.B[1], m->dm.n_t_pad, 4, s) && alloc_into(m, tb.U[1], m->dm.n_ei_pad, 4, s);
     if (!ok) return fail(UE_ERR_ALLOC, "tile arrays");
     tb.B[0] = m->dm.B;
@@ -403,7 +403,12 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemcpyAsync(tb.hdr, ts.hdr.data(), 4 * ts.hdr.size(), cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(tb.trec, ts.trec.data(), 4 * ts.trec.size(), cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(tb.erec, ts.erec.data(), 4 * ts.erec.size(), cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemsetAsync(tb.done, 0, 4, s));
+    UE_CUDA(cudaMemsetAsync(tb.done, 0, 8, s));
+    {
+        int dev = 0;
+        UE_CUDA(cudaGetDevice(&dev));
+        UE_CUDA(cudaDeviceGetAttribute(&tb.sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * m->dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * m->dm.n_ei_pad, s));
     UE_CUDA(ue::launch_tb_fill(tb, m->dm, s));
@@ -1039,6 +1044,7 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
         UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
         m->since_check = 0;
         if (m->p_err) UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
+        if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) UE_CUDA(cudaMemsetAsync(m->tb.done + 1, 0, 4, s));
     }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
@@ -1168,6 +1174,14 @@ int ue_check(ue_mesh* m, double* W, int32_t* flag) {
         if (e) {
             if (flag) *flag = 3;
             return fail(UE_ERR_TIMEOUT, "a grid barrier of the persistent kernel ran out of time");
+        }
+    }
+    if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) {
+        unsigned e = 0;
+        UE_CUDA(cudaMemcpy(&e, m->tb.done + 1, 4, cudaMemcpyDeviceToHost));
+        if (e) {
+            if (flag) *flag = 3;
+            return fail(UE_ERR_TIMEOUT, "a copy wait of the pipelined blocked kernel ran out of time");
         }
     }
     if (wd[3] != 0.0)

@@ -244,11 +244,14 @@ def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=No
 
 
 @pytest.mark.parametrize("tile,k,nsteps,threads", [(512, 4, 14, 0), (1024, 8, 40, 0), (300, 1, 5, 0),
-                                                   (2048, 3, 64, 0), (1500, 6, 23, 1024)])
+                                                   (2048, 3, 64, 0), (1500, 6, 23, 1024),
+                                                   (64, 5, 31, 0)])
 @pytest.mark.parametrize("plasma", [False, True])
 def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, threads, plasma):
     """Temporal blocking on KD tiles reproduces the plain two-kernel step bit for bit
-    (partial last launch, double buffering, halo recompute, source and current included)."""
+    (partial last launch, double buffering, halo recompute, source and current included).
+    Tiles of 64 triangles give more tiles than SMs, so the pipelined persistent form loads
+    each CTA's next tile while it steps the current one (including a 1-step last launch)."""
     ms, ops, w0, dens, ids, amp = _plasma_case()
     rho, _ = spectral.power_iteration(ops, 50)
     dt = 0.45 / rho
