@@ -43,7 +43,7 @@ L2_BYTES = 129e6
 # the kernel source it measured: used only while that source is unchanged, else null.
 NCU_TRAFFIC = {
     # (variant, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
-    ("blocked", 2048, 8, 512): (313517995, "kernels_tb.cu", "343916293d9b5792702ecac381f1e8113735c383",
+    ("blocked", 2048, 8, 512): (311453696, "kernels_tb.cu", "8fceb69a41dd9bf4ab472e33a4b00697dc157ca1",
                                 "profiles/blocked_k_tb_scatterer4M.md"),
 }
 
@@ -262,7 +262,8 @@ def run_native(args):
     prof_ms, prof_bytes = m.profile_steps(nprof, stream)
     names = ["k_edge_half: E half-step (eq. 3)", "k_source", "k_tri_half: B half-step (eq. 4)"]
     if blocked:
-        names[0] = f"k_tb: {args.block_depth} leap-frog steps per launch on KD tiles"
+        names[0] = (f"k_tbp: {args.block_depth} leap-frog steps per launch on KD tiles, one CTA per SM "
+                    "with the next tile's loads in flight")
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9

@@ -386,21 +386,25 @@ constexpr int kTbpG = 1;
 constexpr int kTbpNT = 512;
 
 // Pipelined persistent form (no plasma): one CTA per SM walks the tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...  While it advances one tile k steps, the next tile arrives in
-// three stages, each started after a step: its header (TMA bulk copy), its records (TMA bulk
-// copies into a staging area) and its fields (4-byte cp.async gathers into the second field
-// buffer).  The global loads of a tile thus overlap the previous tile's steps instead of
-// stalling the SM.  Each thread keeps its slots' records in registers for the k steps and
-// repeats k_tb's arithmetic slot by slot, so the results are bit-identical.
+// blockIdx.x + gridDim.x, ...  Global loads run ahead of the steps:
+// - headers: a ring of three; tile i+2's header is copied (TMA bulk copy) while tile i steps;
+// - records: tile i+1's records are copied (TMA bulk copies) into a staging area as soon as
+//   tile i has moved its own records from there into registers;
+// - fields: after step min(3, k) of tile i, tile i+1's fields are gathered (4-byte cp.async)
+//   into the second field buffer.
+// So a tile's loads overlap the previous tile's steps instead of stalling the SM.  Each thread
+// keeps its slots' records in registers for the k steps and repeats k_tb's arithmetic slot by
+// slot, so the results are bit-identical.
 // Dynamic shared memory: two field buffers of FB floats (B at 0, U at TL), then the staging
 // records (TL triangle records, EL edge records).
 template <int NT, int TS, int ES, bool SRC>
 __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, int EL) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ __align__(16) int hs[2][48];
+    __shared__ __align__(16) int hs[3][48];
     __shared__ __align__(8) uint64_t bar_h, bar_r;
     const int tid = threadIdx.x;
     const int FB = (TL + EL + 1 + 3) & ~3;
+    const int stride = gridDim.x;
     float* F0 = reinterpret_cast<float*>(smraw);
     int4* tstage = reinterpret_cast<int4*>(F0 + 2 * FB);
     int4* estage = tstage + TL;
@@ -417,23 +421,23 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
         if (!mbar_wait(bar, ph)) ok = false;
         ph ^= 1u;
     };
-    auto issue_header = [&](int t, int b) {
+    auto issue_header = [&](int t, int slot) {
         if (tid == 0) {
             fence_proxy_async();
-            bulk_g2s(hs[b], a.hdr + (size_t)t * 48, 48 * sizeof(int), &bar_h);
+            bulk_g2s(hs[slot], a.hdr + (size_t)t * 48, 48 * sizeof(int), &bar_h);
         }
     };
-    auto issue_records = [&](int b) {
+    auto issue_records = [&](int slot) {
         if (tid == 0) {
-            const uint32_t tb = 16u * (uint32_t)hs[b][4], eb = 16u * (uint32_t)hs[b][5];
+            const uint32_t tb = 16u * (uint32_t)hs[slot][4], eb = 16u * (uint32_t)hs[slot][5];
             fence_proxy_async();
             mbar_expect_tx(&bar_r, tb + eb);
-            if (tb) bulk_copy_g2s(tstage, a.trec + hs[b][6], tb, &bar_r);
-            if (eb) bulk_copy_g2s(estage, a.erec + hs[b][7], eb, &bar_r);
+            if (tb) bulk_copy_g2s(tstage, a.trec + hs[slot][6], tb, &bar_r);
+            if (eb) bulk_copy_g2s(estage, a.erec + hs[slot][7], eb, &bar_r);
         }
     };
-    auto issue_fields = [&](int b) {
-        const int ntl = hs[b][4], nel = hs[b][5];
+    auto issue_fields = [&](int slot, int b) {
+        const int ntl = hs[slot][4], nel = hs[slot][5];
         float* Bn = F0 + b * FB;
         float* Un = Bn + TL;
 #pragma unroll
@@ -449,24 +453,27 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
         if (tid == 0) Un[nel] = 0.f;
         cp_async_commit();
     };
-    int cur = 0;
-    int tile = blockIdx.x;
+    int tile = blockIdx.x, it = 0, cur = 0;
+    // prologue: first tile's header, records and fields; the second tile's header
     if (tile < n_tiles) {
         issue_header(tile, 0);
         wait_bar(&bar_h, ph_h);
         issue_records(0);
+        if (tile + stride < n_tiles) issue_header(tile + stride, 1);
         wait_bar(&bar_r, ph_r);
-        issue_fields(0);
+        issue_fields(0, 0);
         cp_async_wait_all();
+        if (tile + stride < n_tiles) wait_bar(&bar_h, ph_h);
     }
     __syncthreads();
     int tc01[TS], tc2[TS];
     float tcb[TS];
     int erl[ES];
     float ecu[ES];
-    for (; tile < n_tiles; tile += gridDim.x) {
-        const bool has_next = tile + (int)gridDim.x < n_tiles;
-        const int* h = hs[cur];
+    for (; tile < n_tiles; tile += stride, ++it) {
+        const bool has_next = tile + stride < n_tiles, has_next2 = tile + 2 * stride < n_tiles;
+        const int slot = it % 3, slot1 = (it + 1) % 3, slot2 = (it + 2) % 3;
+        const int* h = hs[slot];
         float* Bl = F0 + cur * FB;
         float* Ul = Bl + TL;
         const int ntl = h[4], nel = h[5];
@@ -490,7 +497,9 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
             }
         }
         __syncthreads();   // the staging area is free for the next tile's records
-        if (has_next) issue_header(tile + gridDim.x, cur ^ 1);
+        if (has_next) issue_records(slot1);
+        if (has_next2) issue_header(tile + 2 * stride, slot2);
+        const int s_fields = a.ksteps < 3 ? a.ksteps : 3;
         for (int s = 1; s <= a.ksteps; ++s) {
             const int lim = a.ksteps - s;
             const int eend = h[32 + lim];
@@ -512,15 +521,9 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
             const int tend = h[16 + lim];
             tb_tris<NT, TS, kTbpG>(Ul, Bl, tc01, tc2, tcb, tid, tend);
             __syncthreads();
-            if (has_next) {
-                if (s == 1) {
-                    wait_bar(&bar_h, ph_h);
-                    issue_records(cur ^ 1);
-                }
-                if (s == (a.ksteps >= 2 ? 2 : 1)) {
-                    wait_bar(&bar_r, ph_r);
-                    issue_fields(cur ^ 1);
-                }
+            if (has_next && s == s_fields) {
+                wait_bar(&bar_r, ph_r);
+                issue_fields(slot1, cur ^ 1);
             }
         }
         const int nto = h[1], neo = h[3];
@@ -535,6 +538,7 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
             if (l < neo) a.Uout[h[2] + l] = Ul[l];
         }
         if (has_next) cp_async_wait_all();
+        if (has_next2) wait_bar(&bar_h, ph_h);
         __syncthreads();
         cur ^= 1;
     }
