@@ -44,7 +44,7 @@ L2_BYTES = 129e6
 NCU_TRAFFIC = {
     # (variant, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
     ("blocked", 2048, 8, 512): (311453696, "kernels_tb.cu", "8fceb69a41dd9bf4ab472e33a4b00697dc157ca1",
-                                "profiles/blocked_k_tb_scatterer4M.md"),
+                                "profiles/blocked_k_tbp_scatterer4M.md"),
 }
 
 
