@@ -321,70 +321,6 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
     }
 }
 
-// One E half-step and one B half-step over a thread's slots, slots taken G at a time: all
-// gathers of a group are issued before its stores.  B and U are distinct arrays (restrict), so
-// the compiler may also lift the next group's gathers above this group's stores.  The
-// arithmetic is k_tb's, operation for operation.
-template <int NT, int ES, int G>
-__device__ __forceinline__ void tb_edges(const float* __restrict__ B, float* __restrict__ U,
-                                         const int (&erl)[ES], const float (&ecu)[ES], int tid,
-                                         int eend) {
-#pragma unroll
-    for (int g0 = 0; g0 < ES; g0 += G) {
-        float bR[G], bL[G], uo[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int i = g0 + q, l = tid + i * NT;
-            if (i < ES && l < eend) {
-                bR[q] = B[erl[i] & 0xFFFF];
-                bL[q] = B[(unsigned)erl[i] >> 16];
-                uo[q] = U[l];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int i = g0 + q, l = tid + i * NT;
-            if (i < ES && l < eend) U[l] = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo[q]);
-        }
-    }
-}
-
-template <int NT, int TS, int G>
-__device__ __forceinline__ void tb_tris(const float* __restrict__ U, float* __restrict__ B,
-                                        const int (&tc01)[TS], const int (&tc2)[TS],
-                                        const float (&tcb)[TS], int tid, int tend) {
-#pragma unroll
-    for (int g0 = 0; g0 < TS; g0 += G) {
-        float u0[G], u1[G], u2[G], bo[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int i = g0 + q, l = tid + i * NT;
-            if (i < TS && l < tend) {
-                u0[q] = U[(tc01[i] & 0xFFFF) >> 1];
-                u1[q] = U[((unsigned)tc01[i] >> 16) >> 1];
-                u2[q] = U[tc2[i] >> 1];
-                bo[q] = B[l];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int i = g0 + q, l = tid + i * NT;
-            if (i < TS && l < tend) {
-                const int c0 = tc01[i], c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
-                const float x0 = (c0 & 1) ? -u0[q] : u0[q];
-                const float x1 = (c1 & 1) ? -u1[q] : u1[q];
-                const float x2 = (c2 & 1) ? -u2[q] : u2[q];
-                B[l] = rn_fma(-tcb[i], rn_add(rn_add(x0, x1), x2), bo[q]);
-            }
-        }
-    }
-}
-
-// Slots per gather group in k_tbp's half-steps.
-constexpr int kTbpG = 1;
-// Threads of k_tbp (512: the register-slot layouts of k_tb; 768 and 1024: fewer slots per thread).
-constexpr int kTbpNT = 512;
-
 // Pipelined persistent form (no plasma): one CTA per SM walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Global loads run ahead of the steps:
 // - headers: a ring of three; tile i+2's header is copied (TMA bulk copy) while tile i steps;
@@ -503,7 +439,15 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
         for (int s = 1; s <= a.ksteps; ++s) {
             const int lim = a.ksteps - s;
             const int eend = h[32 + lim];
-            tb_edges<NT, ES, kTbpG>(Bl, Ul, erl, ecu, tid, eend);
+#pragma unroll
+            for (int i = 0; i < ES; ++i) {
+                const int l = tid + i * NT;
+                if (l < eend) {
+                    const float bR = Bl[erl[i] & 0xFFFF];
+                    const float bL = Bl[(unsigned)erl[i] >> 16];
+                    Ul[l] = rn_fma(ecu[i], rn_sub(bR, bL), Ul[l]);
+                }
+            }
             if constexpr (SRC) {
                 if (h[9] > 0) {
                     __syncthreads();
@@ -519,7 +463,18 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
             }
             __syncthreads();
             const int tend = h[16 + lim];
-            tb_tris<NT, TS, kTbpG>(Ul, Bl, tc01, tc2, tcb, tid, tend);
+#pragma unroll
+            for (int i = 0; i < TS; ++i) {
+                const int l = tid + i * NT;
+                if (l < tend) {
+                    const int c0 = tc01[i], c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
+                    const float u0 = Ul[(c0 & 0xFFFF) >> 1], u1 = Ul[c1 >> 1], u2 = Ul[c2 >> 1];
+                    const float x0 = (c0 & 1) ? -u0 : u0;
+                    const float x1 = (c1 & 1) ? -u1 : u1;
+                    const float x2 = (c2 & 1) ? -u2 : u2;
+                    Bl[l] = rn_fma(-tcb[i], rn_add(rn_add(x0, x1), x2), Bl[l]);
+                }
+            }
             __syncthreads();
             if (has_next && s == s_fields) {
                 wait_bar(&bar_r, ph_r);
@@ -685,14 +640,6 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     if (!m.plasma && t.sms > 0 && smem_p <= kTbpSmemMax) {
         const int TL = t.max_tri_loc, EL = t.max_edge_loc, nt = (int)t.n_tiles;
         const int grid = nt < t.sms ? nt : t.sms;
-        if (kTbpNT == 1024) {
-            if (TL <= 2 * 1024 && EL <= 3 * 1024) return launch_tbp_s<1024, 2, 3>(a, src, nt, grid, TL, EL, smem_p, s);
-            return launch_tbp_s<1024, 4, 6>(a, src, nt, grid, TL, EL, smem_p, s);
-        }
-        if (kTbpNT == 768) {
-            if (TL <= 3 * 768 && EL <= 4 * 768) return launch_tbp_s<768, 3, 4>(a, src, nt, grid, TL, EL, smem_p, s);
-            return launch_tbp_s<768, 6, 8>(a, src, nt, grid, TL, EL, smem_p, s);
-        }
         if (TL <= 4 * kNT && EL <= 6 * kNT) return launch_tbp_s<kNT, 4, 6>(a, src, nt, grid, TL, EL, smem_p, s);
         if (TL <= 6 * kNT && EL <= 9 * kNT) return launch_tbp_s<kNT, 6, 9>(a, src, nt, grid, TL, EL, smem_p, s);
         return launch_tbp_s<kNT, 8, 12>(a, src, nt, grid, TL, EL, smem_p, s);
