@@ -16,6 +16,9 @@ Hence rho(M) = sqrt(lambda_max(K)).
 * ``local_rayleigh``: the S-weighted Rayleigh quotient of K^p delta_j (p power steps of the
   same iteration, started at one triangle).  Like any Rayleigh quotient of K it is a lower
   bound of lambda_max; the learned-dt bracket takes it at the predicted argmax triangle.
+* ``complex_time_modes``: the m highest modes by the same method with deflation: each next mode
+  is iterated while the components along the modes already found are removed at every step,
+  so that they cannot grow back from round-off; omega_i = sqrt of its Rayleigh quotient.
 * ``stable_dt``: eq. 20: the leap-frog step is stable for w dt < 2 for every mode, so
   dt = safety * 2 / rho.  With a plasma density the current adds up to max(nbar) to w^2.
 * ``start_vector``: the start vector of the power iteration, drawn per caller triangle id from
@@ -24,7 +27,8 @@ Hence rho(M) = sqrt(lambda_max(K)).
 
 Parity: pinned by tests/test_oracle_spectral.py (dense eigenvalues on small meshes, bracket
 containment, Yee closed form on the merged right-split lattice, stability at 0.99 / 1.01 of
-the bound, dispersion relation; the local Rayleigh quotient against its spectral form
+the bound, dispersion relation; the highest modes by deflation against a dense
+eigendecomposition; the local Rayleigh quotient against its spectral form
 sum c_i^2 lambda_i^(2p+1) / sum c_i^2 lambda_i^2p from a dense eigendecomposition, and K_jj =
 12/a^2 on an equilateral lattice at p = 0).
 """
@@ -86,6 +90,30 @@ def local_rayleigh(ops, j0: int, p: int = 5) -> float:
     Kv = apply_K(ops, v)
     S = ops.w_B
     return float(np.dot(S * v, Kv) / np.dot(S * v, v))
+
+
+def complex_time_modes(ops, m: int, iters: int = 2000, seed: int = 0):
+    """(omegas in descending order, modes as S-normalised columns) of the m highest modes."""
+    S = ops.w_B
+    n = ops.L_B.shape[1]
+    found, lams = [], []
+
+    def deflate(v):
+        for phi in found:
+            v = v - np.dot(S * phi, v) * phi
+        return v
+
+    for i in range(m):
+        v = deflate(start_vector(n, seed + i))
+        v = v / np.sqrt(np.dot(S * v, v))
+        lam = 0.0
+        for _ in range(iters):
+            w = deflate(apply_K(ops, v))
+            lam = float(np.dot(S * v, w))
+            v = w / np.sqrt(np.dot(S * w, w))
+        found.append(v)
+        lams.append(lam)
+    return np.sqrt(np.clip(np.array(lams), 0.0, None)), np.stack(found, axis=1)
 
 
 def diag_K(ops) -> np.ndarray:

@@ -28,6 +28,20 @@ def test_power_iteration_and_bracket_against_dense_eigenvalues(small):
     assert np.all(np.diff(hist) >= -1e-9 * hist[-1])    # monotone for a PSD operator
 
 
+def test_complex_time_modes_against_dense_eigenpairs(small):
+    """Section 2's method with deflation: the 6 highest omegas equal the dense ones, the modes
+    are S-orthonormal, and each is an eigenvector of K (a dropped deflation collapses every mode
+    onto the first; an unweighted one breaks the orthonormality)."""
+    w, V = spectral.complex_time_modes(small, 6, iters=2000, seed=1)
+    dense = spectral.dense_omegas(small)[::-1][:6]
+    assert np.abs(w / dense - 1).max() < 1e-12
+    G = V.T @ (small.w_B[:, None] * V)
+    assert np.abs(G - np.eye(6)).max() < 1e-10
+    for i in range(6):
+        r = spectral.apply_K(small, V[:, i]) - w[i] ** 2 * V[:, i]
+        assert np.sqrt(np.dot(small.w_B * r, r)) < 1e-6 * w[i] ** 2
+
+
 def test_local_rayleigh_against_eigendecomposition(small):
     """v = K^p delta_j: in the symmetric frame u = S^(1/2) v = Kt^p sqrt(S_j) e_j, so the
     quotient is sum c_i^2 lam_i^(2p+1) / sum c_i^2 lam_i^(2p) with c_i = phi_i[j] (eigh of
