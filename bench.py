@@ -475,6 +475,44 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_modes(args):
+    """Highest eigenmodes of the scatterer-4M mesh (ue_modes, the complex-time method with
+    deflation in block form): block iterations per second.  Each iteration applies K to the
+    block, forms the S-weighted Gram matrix and re-orthonormalises (Cholesky QR); the Gram
+    matrix and the block update are FP64 multiply-adds, 2 m^2 n_t flops each."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    import meshgen
+    ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-6)
+    n_modes, iters = args.n_modes, max(1, args.steps)
+    m.modes(n_modes, iters=max(3, args.warmup))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    om = m.modes(n_modes, iters=iters)
+    t = time.perf_counter() - t0
+    width = min(32, 2 * n_modes)
+    flops = 4.0 * width * width * m.n_tris * iters
+    fp64_nominal = 1.25e12
+    line = {
+        "metric": "eigenmodes: block iterations/s", "value": iters / t, "unit": "iterations/s",
+        "ms_per_iteration": 1e3 * t / iters, "n_modes": n_modes, "block_width": width, "iters": iters,
+        "omega_top": [float(x) for x in om[:4]], "dtype": "f64", "data": "synthetic",
+        "roofline": {"bound": "alu (fp64)", "achieved": flops / t / 1e12, "peak": fp64_nominal / 1e12,
+                     "unit": "TFLOP/s", "frac": flops / t / fp64_nominal, "traffic": None,
+                     "peak_kind": "nominal FP64 rate of GB300 (no measured FP64 peak)",
+                     "what": "Gram matrix and block update, 2 m^2 n_t flops each per iteration"},
+        "config": {"workload": "scatterer-4M", "n_tris": m.n_tris},
+    }
+    m.close()
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,7 +526,8 @@ def main(argv=None):
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
-    ap.add_argument("--workload", choices=["scatterer", "batch", "learned"], default="scatterer")
+    ap.add_argument("--workload", choices=["scatterer", "batch", "learned", "modes"], default="scatterer")
+    ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)
     ap.add_argument("--learned-max", type=int, default=1_000_000)
     ap.add_argument("--batch-meshes", type=int, default=512)
@@ -502,6 +541,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "modes":
+        run_modes(args)
     elif args.workload == "learned":
         run_learned(args)
     else:

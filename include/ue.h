@@ -239,6 +239,22 @@ int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz
  * kernel streams per launch (tile records, local field reads, owned writes); ms[1..2] = 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
+/* The highest eigenmodes of the semi-discrete system (Section 2): omega_i^2 are the largest
+ * eigenvalues of K = -L_E L_B in the S-weighted product, found by the "complex time" method
+ * with deflation (each mode iterated while the modes above it are kept from growing back),
+ * here with all columns of a block advanced together and re-orthonormalised after every
+ * product, then a Rayleigh-Ritz step.  The block holds min(32, 2 n_modes) columns; modes
+ * beyond n_modes only guard the convergence of the ones returned.  FP64; the error of omega_i
+ * falls like (omega_{m+1} / omega_i)^(4 iters).
+ * n_modes in [1, 24], iters >= 1, seed: start vectors (SplitMix64 of the caller triangle id and
+ * column).  omega: n_modes doubles, descending.  B: NULL or n_modes * n_tris doubles, mode i
+ * at B + i*n_tris in caller triangle order, normalised to sum_j S_j B_j^2 = 1 (sign
+ * arbitrary).  Synchronous; the work space, about (2 n_tris + n_interior_edges) * 2 n_modes
+ * doubles, comes from the mesh's allocator and is returned.
+ * Errors: UE_ERR_ARG; UE_ERR_ALLOC; UE_ERR_DUAL if the block loses rank; UE_ERR_CUDA. */
+int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
+             void* stream);
+
 /* Power iteration for rho(M) that allocates no device memory.
  * The paper has no counterpart: this exists for callers that cannot allocate device memory
  * while they run (a memory budget fixed up front, a host process that owns the allocator, or

@@ -219,6 +219,15 @@ class Mesh:
                 "ue_profile_steps")
         return ms, by
 
+    def modes(self, n_modes: int, iters: int = 1000, seed: int = 0, vectors: bool = False, stream=None):
+        """The n_modes highest modes (ue_modes): omegas in descending order, and with
+        vectors=True their B fields (n_modes x n_tris, caller order, S-normalised)."""
+        om = np.zeros(int(n_modes))
+        B = np.zeros((int(n_modes), self.n_tris)) if vectors else None
+        N.check(N.lib().ue_modes(self._h, int(n_modes), int(iters), int(seed) & 0xFFFFFFFF, _dptr(om),
+                                 _dptr(B), _stream(stream)), "ue_modes")
+        return (om, B) if vectors else om
+
     def stats(self) -> dict:
         s = N.Stats()
         N.check(N.lib().ue_stats(self._h, C.byref(s)), "ue_stats")

@@ -206,6 +206,18 @@ cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const i
                              int64_t n_t, int64_t n_ei, double* out, unsigned long long seq,
                              cudaStream_t s);
 
+// Highest eigenmodes by the complex-time method with deflation, in block form
+// (kernels_modes.cu).  Block width modes_block_size(n_modes) <= 32 columns; work holds
+// modes_work_doubles doubles.  omega: n_modes values, descending.  B_dev: NULL or n_modes *
+// n_t doubles on the device, mode i at B_dev + i*n_t in caller triangle order, S-normalised.
+// *lost_rank is set (and nothing else computed) when the block stops being of full rank.
+int modes_block_size(int n_modes);
+size_t modes_work_doubles(int64_t n_t, int64_t n_ei, int m);
+cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const double* d,
+                      const double* S, const int64_t* perm, int64_t n_t, int64_t n_ei, int n_modes,
+                      int iters, uint32_t seed, double* work, double* omega, double* B_dev,
+                      bool* lost_rank, cudaStream_t s);
+
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);
 cudaError_t launch_energy(const DevMesh& m, const double* elen, const double* d, const double* S,

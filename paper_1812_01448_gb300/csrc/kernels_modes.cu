@@ -1,0 +1,327 @@
+// The highest eigenmodes of the semi-discrete system by the "complex time" method with
+// deflation (Section 2).
+//
+// With t -> i t the modes grow like exp(omega t), so repeated application of K = -L_E L_B to
+// a vector, normalised each time, converges to the top mode; the paper finds the next modes
+// the same way while keeping the ones already found from growing back.  Here the m columns of
+// a block are advanced together: V <- K V, then the block is made S-orthonormal again
+// (Cholesky QR: G = W^T S W = R^T R, V = W R^{-1}).  Column i is thereby kept clear of the
+// directions of columns 0..i-1 at every step, which is the deflation applied to all columns at
+// once.  A final Rayleigh-Ritz step on the block (eigenvectors of V^T S K V) gives the modes.
+// Everything is FP64.  Blocks of vectors are row-major [n_t][m]: a triangle's m values are
+// contiguous, so each gather reads one contiguous row.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device.cuh"
+
+namespace ue {
+
+namespace {
+
+constexpr int kMdThreads = 256;
+
+// SplitMix64 (Steele, Lea, Flood 2014), published constants.
+__device__ __forceinline__ uint64_t md_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+unsigned md_blocks(int64_t n) { return (unsigned)((n + kMdThreads - 1) / kMdThreads); }
+
+// c_k = |e_k| / d_k and 1/S_j (FP64 divisions once, not per product)
+__global__ void k_md_prep(const double* __restrict__ elen, const double* __restrict__ d,
+                          const double* __restrict__ S, double* __restrict__ c,
+                          double* __restrict__ invS, int64_t n_ei, int64_t n_t) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_ei) c[i] = elen[i] / d[i];
+    if (i < n_t) invS[i] = 1.0 / S[i];
+}
+
+// V[j][col] uniform in [-1, 1), keyed by the caller id of triangle j and the column
+__global__ void k_md_init(double* __restrict__ V, const int64_t* __restrict__ perm, uint32_t seed,
+                          int64_t n_t, int m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t * m) return;
+    const int64_t j = i / m;
+    const int col = (int)(i - j * m);
+    const uint64_t z = md_splitmix64(((uint64_t)seed << 32) + (uint64_t)perm[j] * (uint64_t)m + (uint64_t)col);
+    V[i] = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+}
+
+// g[k][col] = c_k (V[R][col] - V[L][col]); row n_ei of g is the zero row of boundary edges
+__global__ void k_md_edge(const int2* __restrict__ rl, const double* __restrict__ c,
+                          const double* __restrict__ V, double* __restrict__ g, int64_t n_ei, int m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ei * m) return;
+    const int64_t k = i / m;
+    const int col = (int)(i - k * m);
+    const int2 e = rl[k];
+    g[i] = c[k] * (V[(int64_t)e.x * m + col] - V[(int64_t)e.y * m + col]);
+}
+
+// W[j][col] = (1/S_j) sum_q s(j,q) g[k_q][col]  (K V)
+__global__ void k_md_tri(const int4* __restrict__ tri, const double* __restrict__ invS,
+                         const double* __restrict__ g, double* __restrict__ W, int64_t n_t, int m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t * m) return;
+    const int64_t j = i / m;
+    const int col = (int)(i - j * m);
+    const int4 q = tri[j];
+    double a = g[(int64_t)(q.x >> 1) * m + col], b = g[(int64_t)(q.y >> 1) * m + col],
+           e = g[(int64_t)(q.z >> 1) * m + col];
+    if (q.x & 1) a = -a;
+    if (q.y & 1) b = -b;
+    if (q.z & 1) e = -e;
+    W[i] = (a + b + e) * invS[j];
+}
+
+// Block partials of G[a][b] = sum_j S_j X[j][a] Y[j][b]: rows in tiles of kMdRows staged in
+// shared memory, each thread owning the pairs tid, tid + 256, ... (m <= 32: at most 4 pairs).
+constexpr int kMdRows = 32, kMdMaxM = 32;
+__global__ void __launch_bounds__(kMdThreads) k_md_gram(const double* __restrict__ S,
+                                                        const double* __restrict__ X,
+                                                        const double* __restrict__ Y, int64_t n_t,
+                                                        int m, double* __restrict__ part) {
+    __shared__ double xs[kMdRows][kMdMaxM + 1], ys[kMdRows][kMdMaxM + 1];
+    const int tid = threadIdx.x, npair = m * m;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t r0 = (int64_t)blockIdx.x * kMdRows; r0 < n_t; r0 += (int64_t)gridDim.x * kMdRows) {
+        const int rows = (int)(n_t - r0 < kMdRows ? n_t - r0 : kMdRows);
+        __syncthreads();
+        for (int e = tid; e < kMdRows * m; e += kMdThreads) {
+            const int r = e / m, col = e - r * m;
+            double x = 0.0, y = 0.0;
+            if (r < rows) {
+                const int64_t j = r0 + r;
+                x = S[j] * X[j * m + col];
+                y = Y[j * m + col];
+            }
+            xs[r][col] = x;
+            ys[r][col] = y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = tid + u * kMdThreads;
+            if (p < npair) {
+                const int a = p / m, b = p - a * m;
+                double s = acc[u];
+                for (int r = 0; r < kMdRows; ++r) s = fma(xs[r][a], ys[r][b], s);
+                acc[u] = s;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int p = tid + u * kMdThreads;
+        if (p < npair) part[(int64_t)blockIdx.x * npair + p] = acc[u];
+    }
+}
+
+// G[p] = sum over blocks of part[b][p], in block order (deterministic)
+__global__ void k_md_sum(const double* __restrict__ part, int nb, int npair, double* __restrict__ G) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npair) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * npair + p];
+    G[p] = s;
+}
+
+// V[j][col] = sum_a W[j][a] T[a][col]  (T is m x m, row-major)
+__global__ void k_md_apply(const double* __restrict__ W, const double* __restrict__ T,
+                           double* __restrict__ V, int64_t n_t, int m) {
+    __shared__ double ts[kMdMaxM * kMdMaxM];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) ts[e] = T[e];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t * m) return;
+    const int64_t j = i / m;
+    const int col = (int)(i - j * m);
+    const double* w = W + j * m;
+    double s = 0.0;
+    for (int a = 0; a < m; ++a) s = fma(w[a], ts[a * m + col], s);
+    V[i] = s;
+}
+
+// out[col * n_t + perm[j]] = V[j][col] for col < n_out (caller triangle order)
+__global__ void k_md_scatter(const double* __restrict__ V, const int64_t* __restrict__ perm,
+                             double* __restrict__ out, int64_t n_t, int m, int n_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t * n_out) return;
+    const int col = (int)(i / n_t);
+    const int64_t j = i - (int64_t)col * n_t;
+    out[(int64_t)col * n_t + perm[j]] = V[j * m + col];
+}
+
+// ---- host: small dense algebra on m x m matrices (m <= 32) --------------------------------
+
+// upper-triangular R with G = R^T R; false if G is not positive definite
+bool cholesky_upper(const std::vector<double>& G, int m, std::vector<double>& R) {
+    R.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        double s = G[(size_t)i * m + i];
+        for (int k = 0; k < i; ++k) s -= R[(size_t)k * m + i] * R[(size_t)k * m + i];
+        if (!(s > 0.0)) return false;
+        const double rii = std::sqrt(s);
+        R[(size_t)i * m + i] = rii;
+        for (int j = i + 1; j < m; ++j) {
+            double t = 0.5 * (G[(size_t)i * m + j] + G[(size_t)j * m + i]);
+            for (int k = 0; k < i; ++k) t -= R[(size_t)k * m + i] * R[(size_t)k * m + j];
+            R[(size_t)i * m + j] = t / rii;
+        }
+    }
+    return true;
+}
+
+// inverse of an upper-triangular matrix (back substitution, column by column)
+void upper_inverse(const std::vector<double>& R, int m, std::vector<double>& T) {
+    T.assign((size_t)m * m, 0.0);
+    for (int c = 0; c < m; ++c) {
+        for (int i = c; i >= 0; --i) {
+            double s = i == c ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) s -= R[(size_t)i * m + k] * T[(size_t)k * m + c];
+            T[(size_t)i * m + c] = s / R[(size_t)i * m + i];
+        }
+    }
+}
+
+// eigenpairs of a symmetric matrix by cyclic Jacobi rotations: values in lam, vectors as the
+// columns of Q (row-major), sorted by decreasing eigenvalue
+void jacobi_eigen(std::vector<double> A, int m, std::vector<double>& lam, std::vector<double>& Q) {
+    Q.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                const double v = A[(size_t)i * m + j] * A[(size_t)i * m + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+                const double theta = 0.5 * (aqq - app) / apq;
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < m; ++k) {   // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+                    A[(size_t)k * m + p] = cs * akp - sn * akq;
+                    A[(size_t)k * m + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < m; ++k) {   // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+                    A[(size_t)p * m + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * m + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < m; ++k) {   // Q <- Q J
+                    const double qkp = Q[(size_t)k * m + p], qkq = Q[(size_t)k * m + q];
+                    Q[(size_t)k * m + p] = cs * qkp - sn * qkq;
+                    Q[(size_t)k * m + q] = sn * qkp + cs * qkq;
+                }
+            }
+    }
+    std::vector<int> ord(m);
+    for (int i = 0; i < m; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return A[(size_t)a * m + a] > A[(size_t)b * m + b]; });
+    std::vector<double> Qs((size_t)m * m);
+    lam.resize(m);
+    for (int c = 0; c < m; ++c) {
+        lam[c] = A[(size_t)ord[c] * m + ord[c]];
+        for (int k = 0; k < m; ++k) Qs[(size_t)k * m + c] = Q[(size_t)k * m + ord[c]];
+    }
+    Q = Qs;
+}
+
+}  // namespace
+
+int modes_block_size(int n_modes) { return std::min(kMdMaxM, 2 * n_modes); }
+
+size_t modes_work_doubles(int64_t n_t, int64_t n_ei, int m) {
+    const int64_t nb = std::min<int64_t>(152 * 4, (n_t + kMdRows - 1) / kMdRows);
+    return (size_t)(2 * n_t * m + (n_ei + 1) * m + n_ei + n_t + nb * (int64_t)m * m + 2 * m * m + 8);
+}
+
+cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const double* d,
+                      const double* S, const int64_t* perm, int64_t n_t, int64_t n_ei, int n_modes,
+                      int iters, uint32_t seed, double* work, double* omega, double* B_dev,
+                      bool* lost_rank, cudaStream_t s) {
+    const int m = modes_block_size(n_modes);
+    const int npair = m * m;
+    const int nb = (int)std::min<int64_t>(152 * 4, (n_t + kMdRows - 1) / kMdRows);
+    double* V = work;
+    double* W = V + n_t * m;
+    double* g = W + n_t * m;
+    double* c = g + (n_ei + 1) * m;
+    double* invS = c + n_ei;
+    double* part = invS + n_t;
+    double* G = part + (int64_t)nb * npair;
+    double* T = G + npair;
+    *lost_rank = false;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g + n_ei * m, 0, sizeof(double) * m, s)) != cudaSuccess) return e;
+    k_md_prep<<<md_blocks(std::max(n_ei, n_t)), kMdThreads, 0, s>>>(elen, d, S, c, invS, n_ei, n_t);
+    k_md_init<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(V, perm, seed, n_t, m);
+    std::vector<double> Gh(npair), R, Th;
+    auto apply_K = [&](const double* X, double* Y) {
+        if (n_ei > 0) k_md_edge<<<md_blocks(n_ei * m), kMdThreads, 0, s>>>(rl, c, X, g, n_ei, m);
+        k_md_tri<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(tri, invS, g, Y, n_t, m);
+    };
+    auto gram = [&](const double* X, const double* Y) -> cudaError_t {
+        k_md_gram<<<nb, kMdThreads, 0, s>>>(S, X, Y, n_t, m, part);
+        k_md_sum<<<(npair + 255) / 256, 256, 0, s>>>(part, nb, npair, G);
+        cudaError_t e2 = cudaMemcpyAsync(Gh.data(), G, sizeof(double) * npair, cudaMemcpyDeviceToHost, s);
+        if (e2 != cudaSuccess) return e2;
+        return cudaStreamSynchronize(s);
+    };
+    auto orthonormalize = [&](const double* X, double* Y) -> cudaError_t {   // Y = X R^{-1}
+        cudaError_t e2 = gram(X, X);
+        if (e2 != cudaSuccess) return e2;
+        if (!cholesky_upper(Gh, m, R)) {
+            *lost_rank = true;
+            return cudaSuccess;
+        }
+        upper_inverse(R, m, Th);
+        if ((e2 = cudaMemcpyAsync(T, Th.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return e2;
+        k_md_apply<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(X, T, Y, n_t, m);
+        return cudaGetLastError();
+    };
+    // start: the random block made S-orthonormal (into W, then copied back by the first step)
+    if ((e = orthonormalize(V, W)) != cudaSuccess || *lost_rank) return e;
+    std::swap(V, W);
+    for (int it = 0; it < iters; ++it) {
+        apply_K(V, W);                                   // W = K V
+        if ((e = orthonormalize(W, V)) != cudaSuccess || *lost_rank) return e;   // V = W R^{-1}
+    }
+    // Rayleigh-Ritz: H = V^T S K V, its eigenvectors rotate V into the modes
+    apply_K(V, W);
+    if ((e = gram(V, W)) != cudaSuccess) return e;
+    std::vector<double> lam, Q;
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) {
+            const double h = 0.5 * (Gh[(size_t)i * m + j] + Gh[(size_t)j * m + i]);
+            Gh[(size_t)i * m + j] = Gh[(size_t)j * m + i] = h;
+        }
+    jacobi_eigen(Gh, m, lam, Q);
+    for (int i = 0; i < n_modes; ++i) omega[i] = std::sqrt(std::max(lam[i], 0.0));
+    if (B_dev) {
+        if ((e = cudaMemcpyAsync(T, Q.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return e;
+        k_md_apply<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(V, T, W, n_t, m);
+        k_md_scatter<<<md_blocks(n_t * n_modes), kMdThreads, 0, s>>>(W, perm, B_dev, n_t, m, n_modes);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace ue

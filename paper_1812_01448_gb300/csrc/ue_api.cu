@@ -1356,6 +1356,35 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     return UE_OK;
 }
 
+int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
+             void* stream) {
+    if (!m || !m->built || !omega) return fail(UE_ERR_ARG, "geometry not built or NULL omega");
+    if (n_modes < 1 || n_modes > 24 || iters < 1)
+        return fail(UE_ERR_ARG, "ue_modes: n_modes must be in [1, 24] and iters >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostMesh& h = m->hm;
+    const int64_t nt = h.n_tris, nei = h.n_ei;
+    if (nt < ue::modes_block_size(n_modes))
+        return fail(UE_ERR_ARG, "ue_modes: the mesh has fewer triangles than the block of vectors");
+    double* work = nullptr;
+    double* Bd = nullptr;
+    if (!alloc_into(m, work, ue::modes_work_doubles(nt, nei, ue::modes_block_size(n_modes)), 8, s) ||
+        (B && !alloc_into(m, Bd, (size_t)n_modes * nt, 8, s)))
+        return fail(UE_ERR_ALLOC, "ue_modes work space");
+    bool lost = false;
+    UE_CUDA(ue::modes_run(m->d_rl, m->dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei, n_modes,
+                          iters, seed, work, omega, Bd, &lost, s));
+    if (lost) {
+        dev_release(m, work, s);
+        if (Bd) dev_release(m, Bd, s);
+        return fail(UE_ERR_DUAL, "ue_modes: the block of vectors lost rank (fewer independent modes than asked)");
+    }
+    if (B) UE_CUDA(cudaMemcpy(B, Bd, sizeof(double) * n_modes * nt, cudaMemcpyDeviceToHost));
+    dev_release(m, work, s);
+    if (Bd) dev_release(m, Bd, s);
+    return UE_OK;
+}
+
 int ue_power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,
                               const int32_t* tri_code, const double* S,
                               const int64_t* tri_caller, int64_t n_tris, int64_t n_ei,
