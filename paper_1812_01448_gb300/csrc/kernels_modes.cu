@@ -81,16 +81,29 @@ __global__ void k_md_tri(const int4* __restrict__ tri, const double* __restrict_
     W[i] = (a + b + e) * invS[j];
 }
 
-// Block partials of G[a][b] = sum_j S_j X[j][a] Y[j][b]: rows in tiles of kMdRows staged in
-// shared memory, each thread owning the pairs tid, tid + 256, ... (m <= 32: at most 4 pairs).
+// Block partials of the upper triangle of G[a][b] = sum_j S_j X[j][a] Y[j][b] (a <= b; G is
+// symmetric for X = Y, and for Y = K X up to rounding): rows in tiles of kMdRows staged in
+// shared memory, each thread owning the pairs tid, tid + 256, ... (m <= 32: at most 3 pairs of
+// the 528).  Pair p enumerates (a, b) row by row.
 constexpr int kMdRows = 32, kMdMaxM = 32;
 __global__ void __launch_bounds__(kMdThreads) k_md_gram(const double* __restrict__ S,
                                                         const double* __restrict__ X,
                                                         const double* __restrict__ Y, int64_t n_t,
                                                         int m, double* __restrict__ part) {
     __shared__ double xs[kMdRows][kMdMaxM + 1], ys[kMdRows][kMdMaxM + 1];
-    const int tid = threadIdx.x, npair = m * m;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int tid = threadIdx.x, npair = m * (m + 1) / 2;
+    int pa[3], pb[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        int p = tid + u * kMdThreads, a = 0;
+        while (a < m && p >= m - a) {
+            p -= m - a;
+            ++a;
+        }
+        pa[u] = a;
+        pb[u] = a + p;
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t r0 = (int64_t)blockIdx.x * kMdRows; r0 < n_t; r0 += (int64_t)gridDim.x * kMdRows) {
         const int rows = (int)(n_t - r0 < kMdRows ? n_t - r0 : kMdRows);
         __syncthreads();
@@ -107,10 +120,9 @@ __global__ void __launch_bounds__(kMdThreads) k_md_gram(const double* __restrict
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int p = tid + u * kMdThreads;
-            if (p < npair) {
-                const int a = p / m, b = p - a * m;
+        for (int u = 0; u < 3; ++u) {
+            if (tid + u * kMdThreads < npair) {
+                const int a = pa[u], b = pb[u];
                 double s = acc[u];
                 for (int r = 0; r < kMdRows; ++r) s = fma(xs[r][a], ys[r][b], s);
                 acc[u] = s;
@@ -118,7 +130,7 @@ __global__ void __launch_bounds__(kMdThreads) k_md_gram(const double* __restrict
         }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 3; ++u) {
         const int p = tid + u * kMdThreads;
         if (p < npair) part[(int64_t)blockIdx.x * npair + p] = acc[u];
     }
@@ -133,20 +145,43 @@ __global__ void k_md_sum(const double* __restrict__ part, int nb, int npair, dou
     G[p] = s;
 }
 
-// V[j][col] = sum_a W[j][a] T[a][col]  (T is m x m, row-major)
-__global__ void k_md_apply(const double* __restrict__ W, const double* __restrict__ T,
-                           double* __restrict__ V, int64_t n_t, int m) {
-    __shared__ double ts[kMdMaxM * kMdMaxM];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) ts[e] = T[e];
+// V[j][col] = sum_a W[j][a] T[a][col] (T is m x m, row-major; upper: T[a][col] = 0 for
+// a > col).  One thread per row: the row sits in registers, T (zero-padded to MW x MW) in
+// shared memory is read by every thread of a warp at the same address, and the sums are
+// unrolled at compile time, so the triangle below the diagonal costs nothing.
+template <int MW, bool UPPER>
+__global__ void __launch_bounds__(kMdThreads) k_md_apply(const double* __restrict__ W,
+                                                         const double* __restrict__ T,
+                                                         double* __restrict__ V, int64_t n_t, int m) {
+    __shared__ double ts[MW * MW];
+    for (int e = threadIdx.x; e < MW * MW; e += blockDim.x) {
+        const int r = e / MW, c = e - r * MW;
+        ts[e] = (r < m && c < m) ? T[r * m + c] : 0.0;
+    }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_t * m) return;
-    const int64_t j = i / m;
-    const int col = (int)(i - j * m);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
     const double* w = W + j * m;
-    double s = 0.0;
-    for (int a = 0; a < m; ++a) s = fma(w[a], ts[a * m + col], s);
-    V[i] = s;
+    double x[MW];
+#pragma unroll
+    for (int a = 0; a < MW; ++a) x[a] = a < m ? w[a] : 0.0;
+    double* v = V + j * m;
+#pragma unroll
+    for (int col = 0; col < MW; ++col) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < (UPPER ? col + 1 : MW); ++a) s = fma(x[a], ts[a * MW + col], s);
+        if (col < m) v[col] = s;
+    }
+}
+
+template <bool UPPER>
+void md_apply(const double* W, const double* T, double* V, int64_t n_t, int m, cudaStream_t s) {
+    const unsigned g = md_blocks(n_t);
+    if (m <= 8) k_md_apply<8, UPPER><<<g, kMdThreads, 0, s>>>(W, T, V, n_t, m);
+    else if (m <= 16) k_md_apply<16, UPPER><<<g, kMdThreads, 0, s>>>(W, T, V, n_t, m);
+    else if (m <= 24) k_md_apply<24, UPPER><<<g, kMdThreads, 0, s>>>(W, T, V, n_t, m);
+    else k_md_apply<32, UPPER><<<g, kMdThreads, 0, s>>>(W, T, V, n_t, m);
 }
 
 // out[col * n_t + perm[j]] = V[j][col] for col < n_out (caller triangle order)
@@ -248,7 +283,7 @@ int modes_block_size(int n_modes) { return std::min(kMdMaxM, 2 * n_modes); }
 
 size_t modes_work_doubles(int64_t n_t, int64_t n_ei, int m) {
     const int64_t nb = std::min<int64_t>(152 * 4, (n_t + kMdRows - 1) / kMdRows);
-    return (size_t)(2 * n_t * m + (n_ei + 1) * m + n_ei + n_t + nb * (int64_t)m * m + 2 * m * m + 8);
+    return (size_t)(2 * n_t * m + (n_ei + 1) * m + n_ei + n_t + nb * (int64_t)m * (m + 1) / 2 + 2 * m * m + 8);
 }
 
 cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const double* d,
@@ -256,7 +291,7 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
                       int iters, uint32_t seed, double* work, double* omega, double* B_dev,
                       bool* lost_rank, cudaStream_t s) {
     const int m = modes_block_size(n_modes);
-    const int npair = m * m;
+    const int npair = m * m, nup = m * (m + 1) / 2;
     const int nb = (int)std::min<int64_t>(152 * 4, (n_t + kMdRows - 1) / kMdRows);
     double* V = work;
     double* W = V + n_t * m;
@@ -264,24 +299,27 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
     double* c = g + (n_ei + 1) * m;
     double* invS = c + n_ei;
     double* part = invS + n_t;
-    double* G = part + (int64_t)nb * npair;
+    double* G = part + (int64_t)nb * nup;
     double* T = G + npair;
     *lost_rank = false;
     cudaError_t e;
     if ((e = cudaMemsetAsync(g + n_ei * m, 0, sizeof(double) * m, s)) != cudaSuccess) return e;
     k_md_prep<<<md_blocks(std::max(n_ei, n_t)), kMdThreads, 0, s>>>(elen, d, S, c, invS, n_ei, n_t);
     k_md_init<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(V, perm, seed, n_t, m);
-    std::vector<double> Gh(npair), R, Th;
+    std::vector<double> Gu(nup), Gh(npair), R, Th;
     auto apply_K = [&](const double* X, double* Y) {
         if (n_ei > 0) k_md_edge<<<md_blocks(n_ei * m), kMdThreads, 0, s>>>(rl, c, X, g, n_ei, m);
         k_md_tri<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(tri, invS, g, Y, n_t, m);
     };
     auto gram = [&](const double* X, const double* Y) -> cudaError_t {
         k_md_gram<<<nb, kMdThreads, 0, s>>>(S, X, Y, n_t, m, part);
-        k_md_sum<<<(npair + 255) / 256, 256, 0, s>>>(part, nb, npair, G);
-        cudaError_t e2 = cudaMemcpyAsync(Gh.data(), G, sizeof(double) * npair, cudaMemcpyDeviceToHost, s);
+        k_md_sum<<<(nup + 255) / 256, 256, 0, s>>>(part, nb, nup, G);
+        cudaError_t e2 = cudaMemcpyAsync(Gu.data(), G, sizeof(double) * nup, cudaMemcpyDeviceToHost, s);
         if (e2 != cudaSuccess) return e2;
-        return cudaStreamSynchronize(s);
+        if ((e2 = cudaStreamSynchronize(s)) != cudaSuccess) return e2;
+        for (int a = 0, p = 0; a < m; ++a)
+            for (int b = a; b < m; ++b, ++p) Gh[(size_t)a * m + b] = Gh[(size_t)b * m + a] = Gu[p];
+        return cudaSuccess;
     };
     auto orthonormalize = [&](const double* X, double* Y) -> cudaError_t {   // Y = X R^{-1}
         cudaError_t e2 = gram(X, X);
@@ -293,7 +331,7 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
         upper_inverse(R, m, Th);
         if ((e2 = cudaMemcpyAsync(T, Th.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return e2;
-        k_md_apply<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(X, T, Y, n_t, m);
+        md_apply<true>(X, T, Y, n_t, m, s);
         return cudaGetLastError();
     };
     // start: the random block made S-orthonormal (into W, then copied back by the first step)
@@ -307,17 +345,12 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
     apply_K(V, W);
     if ((e = gram(V, W)) != cudaSuccess) return e;
     std::vector<double> lam, Q;
-    for (int i = 0; i < m; ++i)
-        for (int j = i + 1; j < m; ++j) {
-            const double h = 0.5 * (Gh[(size_t)i * m + j] + Gh[(size_t)j * m + i]);
-            Gh[(size_t)i * m + j] = Gh[(size_t)j * m + i] = h;
-        }
     jacobi_eigen(Gh, m, lam, Q);
     for (int i = 0; i < n_modes; ++i) omega[i] = std::sqrt(std::max(lam[i], 0.0));
     if (B_dev) {
         if ((e = cudaMemcpyAsync(T, Q.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return e;
-        k_md_apply<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(V, T, W, n_t, m);
+        md_apply<false>(V, T, W, n_t, m, s);
         k_md_scatter<<<md_blocks(n_t * n_modes), kMdThreads, 0, s>>>(W, perm, B_dev, n_t, m, n_modes);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
