@@ -1,0 +1,87 @@
+"""Jello-model relaxation and flip refinement (Section 3) oracle pins."""
+import numpy as np
+
+import meshgen
+from oracle import relax
+
+
+def _mesh_data(ms, h=None):
+    t = relax.orient_ccw(ms.xy, ms.tris)
+    hn = np.full(ms.xy.shape[0], h if h is not None else relax.uniform_size(ms.xy, t))
+    edges, L0, H0 = relax.rest_lengths(t, hn)
+    return t, edges, L0, H0
+
+
+def test_forces_are_minus_the_energy_gradient():
+    """Central differences of E against the forces (no node held fixed)."""
+    ms = meshgen.random_delaunay(40, seed=3)
+    t, edges, L0, H0 = _mesh_data(ms)
+    xy = ms.xy.copy()
+    F = relax.forces(xy, t, edges, L0, H0, np.zeros(xy.shape[0], bool))
+    eps = 1e-6
+    G = np.zeros_like(xy)
+    for i in range(xy.shape[0]):
+        for k in range(2):
+            xp = xy.copy(); xp[i, k] += eps
+            xm = xy.copy(); xm[i, k] -= eps
+            G[i, k] = (relax.energy(xp, t, edges, L0, H0) - relax.energy(xm, t, edges, L0, H0)) / (2 * eps)
+    assert np.abs(F + G).max() < 1e-6 * np.abs(G).max()
+
+
+def test_equilateral_lattice_is_a_fixed_point():
+    ms = meshgen.equilateral_lattice(8, 0.1)
+    out, t, flips = relax.relax(ms.xy, ms.tris, 20, h_nodes=np.full(ms.xy.shape[0], 0.1), flip_every=5)
+    assert np.abs(out - ms.xy).max() < 1e-10 and flips == 0
+
+
+def test_relaxation_lowers_the_energy_and_restores_the_lattice():
+    """A jittered lattice (boundary fixed) flows down E at every step, back towards the lattice."""
+    ms = meshgen.equilateral_lattice(10, 0.1, jitter=0.2, seed=4)
+    ref = meshgen.equilateral_lattice(10, 0.1).xy
+    t, edges, L0, H0 = _mesh_data(ms, 0.1)
+    bnd = relax.boundary_nodes(ms.xy.shape[0], t)
+    xy = ms.xy.copy()
+    E = [relax.energy(xy, t, edges, L0, H0)]
+    for _ in range(400):
+        xy = relax.relax(xy, t, 1, h_nodes=np.full(xy.shape[0], 0.1))[0]
+        E.append(relax.energy(xy, t, edges, L0, H0))
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-14 * E[0])
+    assert E[-1] < 1e-8 * E[0]
+    assert np.abs(xy - ref).max() < 1e-3 * 0.1
+    assert np.array_equal(xy[bnd], ms.xy[bnd])
+
+
+def _scramble(xy, tris, n, seed):
+    """Random flips of interior edges whose quad is convex (Delaunay or not)."""
+    rng = np.random.default_rng(seed)
+    t = [list(r) for r in tris]
+    done = 0
+    while done < n:
+        i = int(rng.integers(len(t)))
+        q = int(rng.integers(3))
+        a, b = t[i][q], t[i][(q + 1) % 3]
+        c = t[i][(q + 2) % 3]
+        js = [j for j in range(len(t)) if j != i and a in t[j] and b in t[j]]
+        if not js:
+            continue
+        j = js[0]
+        d = [x for x in t[j] if x != a and x != b][0]
+        cr = lambda p, r, s: (xy[r][0] - xy[p][0]) * (xy[s][1] - xy[p][1]) - (xy[r][1] - xy[p][1]) * (xy[s][0] - xy[p][0])
+        if cr(a, d, c) <= 0 or cr(d, b, c) <= 0:
+            continue
+        t[i], t[j] = [a, d, c], [d, b, c]
+        done += 1
+    return np.asarray(t)
+
+
+def test_lawson_flips_recover_the_delaunay_triangulation():
+    """Qhull's Delaunay triangulation of random points, scrambled by 150 convex flips, comes
+    back exactly (as a set of triangles) from Lawson's flips."""
+    ms = meshgen.random_delaunay(150, seed=9)
+    ref = {tuple(sorted(r)) for r in ms.tris}
+    bad = _scramble(ms.xy, relax.orient_ccw(ms.xy, ms.tris), 150, seed=2)
+    assert {tuple(sorted(r)) for r in bad} != ref
+    out, flips = relax.lawson_flips(ms.xy, bad)
+    assert flips > 0
+    assert {tuple(sorted(r)) for r in out} == ref
