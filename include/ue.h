@@ -239,6 +239,28 @@ int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz
  * kernel streams per launch (tile records, local field reads, owned writes); ms[1..2] = 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
+/* Mesh optimisation by the jello model with flip refinement (Section 3, "Mesh generation"):
+ * nodes joined by unit springs along the triangle edges (rest length (h_a + h_b)/2) and along
+ * the heights (vertex to the midpoint of its opposite edge, rest length sqrt(3)/2 times the
+ * triangle's mean rest edge) move by strongly damped first-order steps x += tau F,
+ * F = -grad of the spring energy, each step clamped to 0.1 of the node's shortest rest edge and
+ * to 0.3 of the smallest height of its triangles (so that no triangle turns over);
+ * the boundary nodes (on an edge of one triangle: the input geometry) stay.  Every flip_every
+ * steps (0: never) interior edges that are not locally Delaunay are flipped (Lawson), so the
+ * triangulation follows the nodes; boundary edges are never flipped.  On a randomly seeded node
+ * cloud this lowers rho(M) severalfold, allowing a larger dt (eq. 20); nearly cocircular pairs
+ * can remain, so check the result with ue_geometry_build (UE_ERR_DUAL).
+ * xy: n_nodes*2 doubles; tris: n_tris*3 int32, either orientation.  h_nodes: NULL (uniform:
+ * the edge of an equilateral triangle of the mean area) or n_nodes target sizes > 0.
+ * tau in (0, 0.1] (explicit steps of this spring system are stable below about 0.1).
+ * xy_out, tris_out (CCW) have the input sizes; node numbering is kept.  *n_flips (may be NULL):
+ * flips done.  Host arrays; synchronous; device buffers by cudaMalloc, freed on return.
+ * Errors: UE_ERR_ARG; UE_ERR_DEGENERATE (a zero-area input triangle, or a triangle inverted by
+ * the relaxation: lower tau); UE_ERR_CUDA. */
+int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                  const double* h_nodes, int32_t iters, int32_t flip_every, double tau,
+                  double* xy_out, int32_t* tris_out, int64_t* n_flips, void* stream);
+
 /* The highest eigenmodes of the semi-discrete system (Section 2): omega_i^2 are the largest
  * eigenvalues of K = -L_E L_B in the S-weighted product, found by the "complex time" method
  * with deflation (each mode iterated while the modes above it are kept from growing back),

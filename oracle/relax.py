@@ -14,8 +14,10 @@ Readings (where the paper gives the idea but not the formulas):
   length of the triangle's edges;
 * all springs have unit stiffness, so the forces are -grad E for
   E = sum_edges (|ab| - L0)^2 / 2 + sum_heights (|v - m| - H0)^2 / 2;
-* one step: x += tau F, each node's displacement clamped to 0.1 of its shortest rest edge;
-  nodes on the boundary (on an edge of one triangle) do not move;
+* one step: x += tau F, each node's displacement clamped to 0.1 of its shortest rest edge and
+  to 0.3 of the smallest height among its triangles (2 area / longest edge, at the current
+  positions): a triangle whose three vertices all move less than a third of its smallest height
+  cannot turn over; nodes on the boundary (on an edge of one triangle) do not move;
 * remesh: Lawson flips of the interior edges that are not locally Delaunay (the vertex
   opposite in one triangle inside the other's circumcircle, beyond a relative 1e-10 margin),
   until none is left; boundary edges are never flipped, so holes keep their contours.
@@ -111,10 +113,17 @@ def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int
     n_flips = 0
     edges, L0, H0 = rest_lengths(t, h_nodes)
     for it in range(iters):
-        # the cap of a node: 0.1 of its shortest rest edge
+        # the cap of a node: 0.1 of its shortest rest edge, 0.3 of its triangles' smallest height
         cap = np.full(xy.shape[0], np.inf)
         np.minimum.at(cap, edges[:, 0], 0.1 * L0)
         np.minimum.at(cap, edges[:, 1], 0.1 * L0)
+        a, b, c = xy[t[:, 0]], xy[t[:, 1]], xy[t[:, 2]]
+        area2 = np.abs((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]))
+        lmax = np.maximum(np.maximum(np.linalg.norm(b - a, axis=1), np.linalg.norm(c - b, axis=1)),
+                          np.linalg.norm(a - c, axis=1))
+        hmin = area2 / lmax
+        for q in range(3):
+            np.minimum.at(cap, t[:, q], 0.3 * hmin)
         dx = tau * forces(xy, t, edges, L0, H0, bnd)
         n = np.linalg.norm(dx, axis=1)
         scale = np.where(n > cap, cap / np.where(n > 0, n, 1.0), 1.0)

@@ -253,6 +253,25 @@ def power_iteration_static(edge_tri, elen, d, tri_code, S, tri_caller, iters: in
     return rho.value
 
 
+def mesh_relax(xy, tris, iters: int, flip_every: int = 20, tau: float = 0.05, h_nodes=None,
+               stream=None):
+    """Jello-model relaxation with Lawson flips (ue_mesh_relax): (xy, tris CCW, flips)."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    tris = np.ascontiguousarray(tris, np.int32)
+    h = None if h_nodes is None else np.ascontiguousarray(h_nodes, np.float64)
+    if xy.ndim != 2 or xy.shape[1] != 2 or tris.ndim != 2 or tris.shape[1] != 3:
+        raise ValueError("xy must be (n, 2) and tris (m, 3)")
+    if h is not None and h.shape != (xy.shape[0],):
+        raise ValueError("h_nodes must hold one size per node")
+    xo = np.empty_like(xy)
+    to = np.empty_like(tris)
+    nf = C.c_int64()
+    N.check(N.lib().ue_mesh_relax(_dptr(xy), xy.shape[0], tris.ctypes.data_as(N.PI32), tris.shape[0],
+                                  _dptr(h), int(iters), int(flip_every), float(tau), _dptr(xo),
+                                  to.ctypes.data_as(N.PI32), C.byref(nf), _stream(stream)), "ue_mesh_relax")
+    return xo, to, nf.value
+
+
 def batch_create(meshes, stream=None) -> Mesh:
     """ue_batch_create: one Mesh object advancing all the given built meshes together.
 

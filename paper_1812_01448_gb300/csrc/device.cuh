@@ -218,6 +218,11 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
                       int iters, uint32_t seed, double* work, double* omega, double* B_dev,
                       bool* lost_rank, cudaStream_t s);
 
+// Jello-model relaxation with Lawson flips (kernels_relax.cu); see ue_mesh_relax.
+int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const double* h_nodes,
+               int32_t iters, int32_t flip_every, double tau, double* xy_out, int32_t* tris_out,
+               int64_t* n_flips, cudaStream_t s, std::string& err);
+
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);
 cudaError_t launch_energy(const DevMesh& m, const double* elen, const double* d, const double* S,

@@ -1,0 +1,361 @@
+// Mesh optimisation by the jello model with flip refinement (Section 3, "Mesh generation").
+//
+// Nodes joined by springs along the triangle edges and along the heights relax, strongly
+// damped (first order, Euler), towards near-equilateral triangles of a given size; the nodes of
+// the input geometry (the boundary) stay.  Every few steps the triangulation is refreshed by
+// Lawson flips, because deformed triangles stop the relaxation around them.
+// Model: unit springs, so the force is -grad E with
+//   E = sum_edges (|ab| - L0)^2 / 2 + sum_heights (|v - m| - H0)^2 / 2,
+// a height spring joining vertex v to the midpoint m of its opposite edge; L0 = (h_a + h_b)/2,
+// H0 = sqrt(3)/2 times the mean L0 of the triangle's edges.  One step: x += tau F, the
+// displacement clamped to 0.1 of the node's shortest rest edge and to 0.3 of the smallest height
+// of its triangles (a triangle whose vertices all move less than a third of its smallest height
+// cannot turn over).
+// GPU: one thread per node gathers its edge springs and its shares of the height springs of
+// its triangles (node -> edge and node -> triangle lists), FP64, positions double-buffered.
+// Host: the lists, and the flips (a flip changes the lists).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "device.cuh"
+
+namespace ue {
+
+namespace {
+
+constexpr int kRxThreads = 256;
+
+// adjacency of one triangulation, as uploaded
+struct RxLists {
+    std::vector<int32_t> e_off, e_nb;     // node -> (neighbour node) of each incident edge
+    std::vector<double> e_L0;             // rest length of that edge
+    std::vector<int32_t> t_off, t_tri;    // node -> incident triangle
+    std::vector<int32_t> t_loc;           // local index of the node in it (0..2)
+    std::vector<double> H0;               // rest height per triangle
+    std::vector<double> cap;              // displacement cap per node
+    std::vector<uint8_t> fixed;           // boundary node
+};
+
+__global__ void k_rx_step(const double* __restrict__ x, double* __restrict__ xn,
+                          const int32_t* __restrict__ tris, const int32_t* __restrict__ e_off,
+                          const int32_t* __restrict__ e_nb, const double* __restrict__ e_L0,
+                          const int32_t* __restrict__ t_off, const int32_t* __restrict__ t_tri,
+                          const int32_t* __restrict__ t_loc, const double* __restrict__ H0,
+                          const double* __restrict__ cap, const uint8_t* __restrict__ fixed,
+                          double tau, int64_t n_nodes) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    const double vx = x[2 * v], vy = x[2 * v + 1];
+    if (fixed[v]) {
+        xn[2 * v] = vx;
+        xn[2 * v + 1] = vy;
+        return;
+    }
+    double fx = 0.0, fy = 0.0;
+    for (int32_t i = e_off[v]; i < e_off[v + 1]; ++i) {   // edge springs
+        const int32_t b = e_nb[i];
+        const double dx = x[2 * b] - vx, dy = x[2 * b + 1] - vy;
+        const double L = sqrt(dx * dx + dy * dy);
+        const double s = (L - e_L0[i]) / L;
+        fx += s * dx;
+        fy += s * dy;
+    }
+    double c = cap[v];
+    for (int32_t i = t_off[v]; i < t_off[v + 1]; ++i) {   // height springs of its triangles
+        const int32_t t = t_tri[i], l = t_loc[i];
+        double px[3], py[3];
+        for (int q = 0; q < 3; ++q) {
+            const int32_t n = tris[3 * t + q];
+            px[q] = x[2 * n];
+            py[q] = x[2 * n + 1];
+        }
+        {   // 0.3 of the triangle's smallest height (2 area / longest edge) caps the step
+            const double a2 = fabs((px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]));
+            double lm = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const int p = q == 2 ? 0 : q + 1;
+                const double ex = px[p] - px[q], ey = py[p] - py[q];
+                lm = fmax(lm, sqrt(ex * ex + ey * ey));
+            }
+            c = fmin(c, 0.3 * (a2 / lm));
+        }
+        const double h0 = H0[t];
+        for (int q = 0; q < 3; ++q) {   // apex q over the edge (q+1, q+2)
+            const int p = q == 2 ? 0 : q + 1, r = q == 0 ? 2 : q - 1;
+            const double wx = px[q] - 0.5 * (px[p] + px[r]), wy = py[q] - 0.5 * (py[p] + py[r]);
+            const double hm = sqrt(wx * wx + wy * wy);
+            const double s = (hm - h0) / hm;
+            const double w = q == l ? -1.0 : 0.5;   // the apex takes -g, the edge's ends g/2
+            fx += w * s * wx;
+            fy += w * s * wy;
+        }
+    }
+    double dx = tau * fx, dy = tau * fy;
+    const double n = sqrt(dx * dx + dy * dy);
+    if (n > c) {
+        const double k = c / n;
+        dx *= k;
+        dy *= k;
+    }
+    xn[2 * v] = vx + dx;
+    xn[2 * v + 1] = vy + dy;
+}
+
+double orient2d(const std::vector<double>& x, int a, int b, int c) {
+    return (x[2 * b] - x[2 * a]) * (x[2 * c + 1] - x[2 * a + 1]) -
+           (x[2 * b + 1] - x[2 * a + 1]) * (x[2 * c] - x[2 * a]);
+}
+
+// d strictly inside the circumcircle of the CCW triangle abc, beyond a relative 1e-10 margin
+bool in_circle(const std::vector<double>& x, int a, int b, int c, int d) {
+    const double ax = x[2 * a] - x[2 * d], ay = x[2 * a + 1] - x[2 * d + 1];
+    const double bx = x[2 * b] - x[2 * d], by = x[2 * b + 1] - x[2 * d + 1];
+    const double cx = x[2 * c] - x[2 * d], cy = x[2 * c + 1] - x[2 * d + 1];
+    const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    const double det = a2 * (bx * cy - by * cx) - b2 * (ax * cy - ay * cx) + c2 * (ax * by - ay * bx);
+    const double s = std::max(a2, std::max(b2, c2));
+    return det > 1e-10 * s * s;
+}
+
+// Lawson flips until every interior edge is locally Delaunay; returns the number of flips
+int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
+    const int64_t nt = (int64_t)t.size() / 3;
+    std::map<std::pair<int32_t, int32_t>, int64_t> owner;   // directed edge -> triangle (CCW)
+    for (int64_t i = 0; i < nt; ++i)
+        for (int q = 0; q < 3; ++q) owner[{t[3 * i + q], t[3 * i + (q + 1) % 3]}] = i;
+    std::vector<std::pair<int32_t, int32_t>> stack;
+    for (const auto& kv : owner)
+        if (kv.first.first < kv.first.second && owner.count({kv.first.second, kv.first.first}))
+            stack.push_back(kv.first);
+    int64_t flips = 0;
+    auto third = [&](int64_t i, int32_t a, int32_t b) {
+        for (int q = 0; q < 3; ++q)
+            if (t[3 * i + q] != a && t[3 * i + q] != b) return t[3 * i + q];
+        return (int32_t)-1;
+    };
+    while (!stack.empty()) {
+        const auto e = stack.back();
+        stack.pop_back();
+        const int32_t a = e.first, b = e.second;
+        auto ia = owner.find({a, b});
+        auto ib = owner.find({b, a});
+        if (ia == owner.end() || ib == owner.end()) continue;
+        const int64_t i = ia->second, j = ib->second;
+        const int32_t c = third(i, a, b), d = third(j, a, b);
+        if (!in_circle(x, a, b, c, d)) continue;
+        if (orient2d(x, a, d, c) <= 0 || orient2d(x, d, b, c) <= 0) continue;   // not convex
+        for (const auto& k : {std::make_pair(a, b), std::make_pair(b, c), std::make_pair(c, a),
+                              std::make_pair(b, a), std::make_pair(a, d), std::make_pair(d, b)})
+            owner.erase(k);
+        const int32_t ti[3] = {a, d, c}, tj[3] = {d, b, c};
+        for (int q = 0; q < 3; ++q) {
+            t[3 * i + q] = ti[q];
+            t[3 * j + q] = tj[q];
+        }
+        for (int q = 0; q < 3; ++q) {
+            owner[{ti[q], ti[(q + 1) % 3]}] = i;
+            owner[{tj[q], tj[(q + 1) % 3]}] = j;
+        }
+        ++flips;
+        for (const auto& k : {std::make_pair(a, d), std::make_pair(d, b), std::make_pair(b, c),
+                              std::make_pair(c, a)})
+            stack.push_back({std::min(k.first, k.second), std::max(k.first, k.second)});
+    }
+    return flips;
+}
+
+void build_lists(int64_t nn, const std::vector<int32_t>& t, const std::vector<double>& h, RxLists& L) {
+    const int64_t nt = (int64_t)t.size() / 3;
+    // unique edges (low, high) in increasing order, and the number of triangles of each
+    std::vector<std::pair<int32_t, int32_t>> e;
+    e.reserve(3 * nt);
+    for (int64_t i = 0; i < nt; ++i)
+        for (int q = 0; q < 3; ++q) {
+            const int32_t a = t[3 * i + q], b = t[3 * i + (q + 1) % 3];
+            e.push_back({std::min(a, b), std::max(a, b)});
+        }
+    std::sort(e.begin(), e.end());
+    std::vector<std::pair<int32_t, int32_t>> ue;
+    std::vector<int> cnt;
+    for (size_t k = 0; k < e.size(); ++k) {
+        if (k == 0 || e[k] != e[k - 1]) {
+            ue.push_back(e[k]);
+            cnt.push_back(1);
+        } else {
+            ++cnt.back();
+        }
+    }
+    L.fixed.assign(nn, 0);
+    for (size_t k = 0; k < ue.size(); ++k)
+        if (cnt[k] == 1) L.fixed[ue[k].first] = L.fixed[ue[k].second] = 1;
+    // node -> edges, in increasing edge order
+    std::vector<int32_t> deg(nn, 0);
+    for (const auto& p : ue) {
+        ++deg[p.first];
+        ++deg[p.second];
+    }
+    L.e_off.assign(nn + 1, 0);
+    for (int64_t v = 0; v < nn; ++v) L.e_off[v + 1] = L.e_off[v] + deg[v];
+    L.e_nb.assign(L.e_off[nn], 0);
+    L.e_L0.assign(L.e_off[nn], 0.0);
+    L.cap.assign(nn, INFINITY);
+    std::vector<int32_t> pos(L.e_off.begin(), L.e_off.end() - 1);
+    for (const auto& p : ue) {
+        const double l0 = 0.5 * (h[p.first] + h[p.second]);
+        L.e_nb[pos[p.first]] = p.second;
+        L.e_L0[pos[p.first]++] = l0;
+        L.e_nb[pos[p.second]] = p.first;
+        L.e_L0[pos[p.second]++] = l0;
+        L.cap[p.first] = std::min(L.cap[p.first], 0.1 * l0);
+        L.cap[p.second] = std::min(L.cap[p.second], 0.1 * l0);
+    }
+    // node -> triangles, in triangle order
+    std::vector<int32_t> tdeg(nn, 0);
+    for (int32_t n : t) ++tdeg[n];
+    L.t_off.assign(nn + 1, 0);
+    for (int64_t v = 0; v < nn; ++v) L.t_off[v + 1] = L.t_off[v] + tdeg[v];
+    L.t_tri.assign(L.t_off[nn], 0);
+    L.t_loc.assign(L.t_off[nn], 0);
+    std::vector<int32_t> tp(L.t_off.begin(), L.t_off.end() - 1);
+    L.H0.assign(nt, 0.0);
+    for (int64_t i = 0; i < nt; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const int32_t n = t[3 * i + q];
+            L.t_tri[tp[n]] = (int32_t)i;
+            L.t_loc[tp[n]++] = q;
+            s += 0.5 * (h[n] + h[t[3 * i + (q + 1) % 3]]);
+        }
+        L.H0[i] = std::sqrt(3.0) / 2.0 * s / 3.0;
+    }
+}
+
+}  // namespace
+
+// See include/ue.h (ue_mesh_relax).  Device buffers are owned here (cudaMalloc/cudaFree):
+// the call is a one-off preprocessing step outside any mesh.
+int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const double* h_nodes,
+               int32_t iters, int32_t flip_every, double tau, double* xy_out, int32_t* tris_out,
+               int64_t* n_flips, cudaStream_t s, std::string& err) {
+    std::vector<double> x(xy, xy + 2 * nn);
+    std::vector<int32_t> t(tris, tris + 3 * nt);
+    double area = 0.0;
+    for (int64_t i = 0; i < nt; ++i) {
+        int32_t* r = &t[3 * i];
+        for (int q = 0; q < 3; ++q)
+            if (r[q] < 0 || r[q] >= nn) {
+                err = "triangle node index out of range";
+                return UE_ERR_ARG;
+            }
+        double o = orient2d(x, r[0], r[1], r[2]);
+        if (o < 0) {
+            std::swap(r[1], r[2]);
+            o = -o;
+        }
+        if (!(o > 0)) {
+            err = "degenerate triangle " + std::to_string(i);
+            return UE_ERR_DEGENERATE;
+        }
+        area += 0.5 * o;
+    }
+    std::vector<double> h(nn);
+    if (h_nodes) {
+        for (int64_t v = 0; v < nn; ++v) {
+            if (!(h_nodes[v] > 0)) {
+                err = "sizes must be positive";
+                return UE_ERR_ARG;
+            }
+            h[v] = h_nodes[v];
+        }
+    } else {
+        std::fill(h.begin(), h.end(), std::sqrt(4.0 * area / (std::sqrt(3.0) * (double)nt)));
+    }
+    RxLists L;
+    build_lists(nn, t, h, L);
+    // device buffers, sized for the lists (their sizes do not change under flips)
+    double *dx0 = nullptr, *dx1 = nullptr, *dL0 = nullptr, *dH0 = nullptr, *dcap = nullptr;
+    int32_t *dt = nullptr, *deo = nullptr, *den = nullptr, *dto = nullptr, *dtt = nullptr, *dtl = nullptr;
+    uint8_t* dfix = nullptr;
+    const size_t ne2 = L.e_nb.size(), nt3 = L.t_tri.size();
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t r) {
+        if (e == cudaSuccess && r != cudaSuccess) e = r;
+    };
+    ck(cudaMalloc(&dx0, 16 * nn));
+    ck(cudaMalloc(&dx1, 16 * nn));
+    ck(cudaMalloc(&dt, 12 * nt));
+    ck(cudaMalloc(&deo, 4 * (nn + 1)));
+    ck(cudaMalloc(&den, 4 * ne2));
+    ck(cudaMalloc(&dL0, 8 * ne2));
+    ck(cudaMalloc(&dto, 4 * (nn + 1)));
+    ck(cudaMalloc(&dtt, 4 * nt3));
+    ck(cudaMalloc(&dtl, 4 * nt3));
+    ck(cudaMalloc(&dH0, 8 * nt));
+    ck(cudaMalloc(&dcap, 8 * nn));
+    ck(cudaMalloc(&dfix, nn));
+    auto upload_lists = [&]() {
+        ck(cudaMemcpyAsync(dt, t.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(deo, L.e_off.data(), 4 * (nn + 1), cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(den, L.e_nb.data(), 4 * ne2, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dL0, L.e_L0.data(), 8 * ne2, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dto, L.t_off.data(), 4 * (nn + 1), cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dtt, L.t_tri.data(), 4 * nt3, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dtl, L.t_loc.data(), 4 * nt3, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dH0, L.H0.data(), 8 * nt, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dcap, L.cap.data(), 8 * nn, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(dfix, L.fixed.data(), nn, cudaMemcpyHostToDevice, s));
+        ck(cudaStreamSynchronize(s));   // the host lists may change after this
+    };
+    if (e == cudaSuccess) {
+        ck(cudaMemcpyAsync(dx0, x.data(), 16 * nn, cudaMemcpyHostToDevice, s));
+        upload_lists();
+    }
+    int64_t flips = 0;
+    const unsigned grid = (unsigned)((nn + kRxThreads - 1) / kRxThreads);
+    for (int32_t it = 0; it < iters && e == cudaSuccess; ++it) {
+        k_rx_step<<<grid, kRxThreads, 0, s>>>(dx0, dx1, dt, deo, den, dL0, dto, dtt, dtl, dH0, dcap,
+                                               dfix, tau, nn);
+        ck(cudaGetLastError());
+        std::swap(dx0, dx1);
+        if (flip_every > 0 && (it + 1) % flip_every == 0 && e == cudaSuccess) {
+            ck(cudaMemcpyAsync(x.data(), dx0, 16 * nn, cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            if (e != cudaSuccess) break;
+            const int64_t k = lawson(x, t);
+            flips += k;
+            if (k > 0) {
+                build_lists(nn, t, h, L);
+                upload_lists();
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        ck(cudaMemcpyAsync(x.data(), dx0, 16 * nn, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+    }
+    for (void* p : {(void*)dx0, (void*)dx1, (void*)dt, (void*)deo, (void*)den, (void*)dL0, (void*)dto,
+                    (void*)dtt, (void*)dtl, (void*)dH0, (void*)dcap, (void*)dfix})
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) {
+        err = std::string("mesh relaxation: ") + cudaGetErrorString(e);
+        return UE_ERR_CUDA;
+    }
+    for (int64_t i = 0; i < nt; ++i)
+        if (!(orient2d(x, t[3 * i], t[3 * i + 1], t[3 * i + 2]) > 0)) {
+            err = "relaxation inverted triangle " + std::to_string(i) + ": lower tau";
+            return UE_ERR_DEGENERATE;
+        }
+    std::copy(x.begin(), x.end(), xy_out);
+    std::copy(t.begin(), t.end(), tris_out);
+    if (n_flips) *n_flips = flips;
+    return UE_OK;
+}
+
+}  // namespace ue

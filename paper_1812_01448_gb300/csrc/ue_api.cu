@@ -1356,6 +1356,21 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     return UE_OK;
 }
 
+int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                  const double* h_nodes, int32_t iters, int32_t flip_every, double tau,
+                  double* xy_out, int32_t* tris_out, int64_t* n_flips, void* stream) {
+    if (!xy || !tris || !xy_out || !tris_out || n_nodes < 3 || n_tris < 1 || iters < 0 || flip_every < 0)
+        return fail(UE_ERR_ARG, "ue_mesh_relax: bad arguments");
+    if (n_nodes >= (int64_t)1 << 31 || 3 * n_tris >= (int64_t)1 << 31)
+        return fail(UE_ERR_ARG, "ue_mesh_relax: mesh too large for 32-bit indices");
+    if (!(tau > 0.0 && tau <= 0.1)) return fail(UE_ERR_ARG, "ue_mesh_relax: tau must be in (0, 0.1]");
+    std::string err;
+    const int rc = ue::mesh_relax(xy, n_nodes, tris, n_tris, h_nodes, iters, flip_every, tau, xy_out,
+                                  tris_out, n_flips, (cudaStream_t)stream, err);
+    if (rc != UE_OK) return fail(rc, err);
+    return UE_OK;
+}
+
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream) {
     if (!m || !m->built || !omega) return fail(UE_ERR_ARG, "geometry not built or NULL omega");

@@ -1,0 +1,66 @@
+"""Jello-model relaxation with flip refinement on the GPU (ue_mesh_relax) against the oracle."""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import relax
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ue():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01448_gb300 import build
+    build.build()
+    import paper_1812_01448_gb300 as ue
+    return ue
+
+
+def test_relaxation_matches_oracle(ue):
+    """No flips: the positions after 150 steps agree with the oracle's to 1e-10 of the size."""
+    ms = meshgen.equilateral_lattice(20, 0.05, jitter=0.2, seed=11)
+    h = np.full(ms.xy.shape[0], 0.05)
+    xg, tg, fg = ue.mesh_relax(ms.xy, ms.tris, 150, flip_every=0, tau=0.05, h_nodes=h)
+    xo, to, fo = relax.relax(ms.xy, ms.tris, 150, tau=0.05, h_nodes=h)
+    assert fg == fo == 0
+    assert np.array_equal(tg, to)
+    assert np.abs(xg - xo).max() < 1e-10 * 0.05
+
+
+def test_relaxation_with_flips_matches_oracle(ue):
+    """The jittered cavity mesh with flips every 20 steps: the same triangulation (as a set of
+    triangles) and positions within 1e-9 of the size."""
+    ms = meshgen.cavity_te11_mesh()
+    xg, tg, fg = ue.mesh_relax(ms.xy, ms.tris, 200, flip_every=20, tau=0.05)
+    xo, to, fo = relax.relax(ms.xy, ms.tris, 200, tau=0.05, flip_every=20)
+    assert fg > 0 and fo > 0
+    assert {tuple(sorted(r)) for r in tg} == {tuple(sorted(r)) for r in to}
+    assert np.abs(xg - xo).max() < 1e-9 * ms.h
+
+
+def test_relaxation_raises_the_time_step(ue):
+    """A Delaunay mesh of 300 random points, relaxed 200 steps with flips every 20, has less
+    than half the spectral radius (eq. 20: more than twice the dt), as in the oracle."""
+    ms = meshgen.random_delaunay(300, seed=5)
+    xr, tr, _ = ue.mesh_relax(ms.xy, ms.tris, 200, flip_every=20)
+    rho = []
+    for xy, tris in ((ms.xy, ms.tris), (xr, tr)):
+        m = ue.Mesh(xy, tris)
+        m.geometry_build()
+        rho.append(m.get_dt()[1])
+        m.close()
+    assert rho[1] < 0.5 * rho[0], rho
+
+
+def test_relaxation_rejects_bad_arguments(ue):
+    ms = meshgen.equilateral_lattice(4, 0.1)
+    for kw in (dict(tau=0.0), dict(tau=0.5), dict(iters=-1)):
+        args = dict(iters=5, tau=0.05)
+        args.update(kw)
+        with pytest.raises(ue.UEError):
+            ue.mesh_relax(ms.xy, ms.tris, args.pop("iters"), **args)
+    with pytest.raises(ue.UEError):
+        ue.mesh_relax(ms.xy, ms.tris, 5, h_nodes=np.zeros(ms.xy.shape[0]))
