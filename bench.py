@@ -514,6 +514,52 @@ def run_modes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_relax(args):
+    """Mesh optimisation (ue_mesh_relax: jello model, Section 3) on a Delaunay mesh of random
+    points in the unit square: GPU time per relaxation step, the whole call with Lawson flips
+    every 20 steps, and the spectral radius (hence dt, eq. 20) before and after, from the
+    library's power iteration.  The oracle's relaxation, timed for 10 steps, is the CPU line."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    import meshgen
+    from oracle import relax as orelax
+    ms = meshgen.random_delaunay(args.relax_points, seed=1006)
+    iters = max(1, args.steps)
+    ue.mesh_relax(ms.xy, ms.tris, max(3, args.warmup), flip_every=0)     # warm-up
+    t0 = time.perf_counter()
+    ue.mesh_relax(ms.xy, ms.tris, iters, flip_every=0)
+    t_steps = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    xr, tr, flips = ue.mesh_relax(ms.xy, ms.tris, iters, flip_every=20)
+    t_all = time.perf_counter() - t0
+    rho = []
+    for xy, tris in ((ms.xy, ms.tris), (xr, tr)):
+        m = ue.Mesh(xy, tris)
+        m.geometry_build()
+        rho.append(m.get_dt()[1])
+        m.close()
+    t0 = time.perf_counter()
+    orelax.relax(ms.xy, ms.tris, 10, flip_every=0)
+    t_cpu = (time.perf_counter() - t0) / 10
+    n_nodes = ms.xy.shape[0]
+    line = {
+        "metric": "mesh relaxation: node-steps/s", "value": n_nodes * iters / t_steps, "unit": "node-steps/s",
+        "ms_per_step": 1e3 * t_steps / iters, "steps": iters, "n_nodes": n_nodes, "n_tris": int(ms.tris.shape[0]),
+        "with_flips": {"seconds": t_all, "flips": int(flips), "flip_every": 20},
+        "rho_before": rho[0], "rho_after": rho[1], "dt_gain": rho[0] / rho[1],
+        "dtype": "f64", "data": "synthetic",
+        "cpu_baseline": {"value": n_nodes / t_cpu, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "10 relaxation steps of the same mesh (numpy, one thread)"},
+        "config": {"workload": f"Delaunay mesh of {args.relax_points} uniform random points in the unit square, "
+                               "jello-model relaxation, uniform target size"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -527,7 +573,8 @@ def main(argv=None):
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
-    ap.add_argument("--workload", choices=["scatterer", "batch", "learned", "modes"], default="scatterer")
+    ap.add_argument("--workload", choices=["scatterer", "batch", "learned", "modes", "relax"], default="scatterer")
+    ap.add_argument("--relax-points", type=int, default=100_000)
     ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)
     ap.add_argument("--learned-max", type=int, default=1_000_000)
@@ -544,6 +591,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "modes":
         run_modes(args)
+    elif args.workload == "relax":
+        run_relax(args)
     elif args.workload == "learned":
         run_learned(args)
     else:

@@ -244,7 +244,7 @@ int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, doub
  * the heights (vertex to the midpoint of its opposite edge, rest length sqrt(3)/2 times the
  * triangle's mean rest edge) move by strongly damped first-order steps x += tau F,
  * F = -grad of the spring energy, each step clamped to 0.1 of the node's shortest rest edge and
- * to 0.3 of the smallest height of its triangles (so that no triangle turns over);
+ * to 0.15 of the smallest height of its triangles (so that no triangle turns over);
  * the boundary nodes (on an edge of one triangle: the input geometry) stay.  Every flip_every
  * steps (0: never) interior edges that are not locally Delaunay are flipped (Lawson), so the
  * triangulation follows the nodes; boundary edges are never flipped.  On a randomly seeded node

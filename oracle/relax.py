@@ -15,9 +15,10 @@ Readings (where the paper gives the idea but not the formulas):
 * all springs have unit stiffness, so the forces are -grad E for
   E = sum_edges (|ab| - L0)^2 / 2 + sum_heights (|v - m| - H0)^2 / 2;
 * one step: x += tau F, each node's displacement clamped to 0.1 of its shortest rest edge and
-  to 0.3 of the smallest height among its triangles (2 area / longest edge, at the current
-  positions): a triangle whose three vertices all move less than a third of its smallest height
-  cannot turn over; nodes on the boundary (on an edge of one triangle) do not move;
+  to 0.15 of the smallest height h among its triangles (2 area / longest edge L, at the current
+  positions): moves of at most d per vertex change twice a triangle's area by at most
+  3 d L + 4 d^2 <= 0.54 h L, less than the 2 area = h L it has, so no triangle turns over;
+  nodes on the boundary (on an edge of one triangle) do not move;
 * remesh: Lawson flips of the interior edges that are not locally Delaunay (the vertex
   opposite in one triangle inside the other's circumcircle, beyond a relative 1e-10 margin),
   until none is left; boundary edges are never flipped, so holes keep their contours.
@@ -113,7 +114,7 @@ def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int
     n_flips = 0
     edges, L0, H0 = rest_lengths(t, h_nodes)
     for it in range(iters):
-        # the cap of a node: 0.1 of its shortest rest edge, 0.3 of its triangles' smallest height
+        # the cap of a node: 0.1 of its shortest rest edge, 0.15 of its triangles' smallest height
         cap = np.full(xy.shape[0], np.inf)
         np.minimum.at(cap, edges[:, 0], 0.1 * L0)
         np.minimum.at(cap, edges[:, 1], 0.1 * L0)
@@ -123,7 +124,7 @@ def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int
                           np.linalg.norm(a - c, axis=1))
         hmin = area2 / lmax
         for q in range(3):
-            np.minimum.at(cap, t[:, q], 0.3 * hmin)
+            np.minimum.at(cap, t[:, q], 0.15 * hmin)
         dx = tau * forces(xy, t, edges, L0, H0, bnd)
         n = np.linalg.norm(dx, axis=1)
         scale = np.where(n > cap, cap / np.where(n > 0, n, 1.0), 1.0)

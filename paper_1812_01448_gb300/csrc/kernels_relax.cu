@@ -8,9 +8,10 @@
 //   E = sum_edges (|ab| - L0)^2 / 2 + sum_heights (|v - m| - H0)^2 / 2,
 // a height spring joining vertex v to the midpoint m of its opposite edge; L0 = (h_a + h_b)/2,
 // H0 = sqrt(3)/2 times the mean L0 of the triangle's edges.  One step: x += tau F, the
-// displacement clamped to 0.1 of the node's shortest rest edge and to 0.3 of the smallest height
-// of its triangles (a triangle whose vertices all move less than a third of its smallest height
-// cannot turn over).
+// displacement clamped to 0.1 of the node's shortest rest edge and to 0.15 of the smallest
+// height h of its triangles: moves of at most d per vertex change twice a triangle's area by at
+// most 3 d L + 4 d^2 <= 0.54 h L (L its longest edge), less than the h L it has, so no triangle
+// turns over.
 // GPU: one thread per node gathers its edge springs and its shares of the height springs of
 // its triangles (node -> edge and node -> triangle lists), FP64, positions double-buffered.
 // Host: the lists, and the flips (a flip changes the lists).
@@ -76,7 +77,7 @@ __global__ void k_rx_step(const double* __restrict__ x, double* __restrict__ xn,
             px[q] = x[2 * n];
             py[q] = x[2 * n + 1];
         }
-        {   // 0.3 of the triangle's smallest height (2 area / longest edge) caps the step
+        {   // 0.15 of the triangle's smallest height (2 area / longest edge) caps the step
             const double a2 = fabs((px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]));
             double lm = 0.0;
             for (int q = 0; q < 3; ++q) {
@@ -84,7 +85,7 @@ __global__ void k_rx_step(const double* __restrict__ x, double* __restrict__ xn,
                 const double ex = px[p] - px[q], ey = py[p] - py[q];
                 lm = fmax(lm, sqrt(ex * ex + ey * ey));
             }
-            c = fmin(c, 0.3 * (a2 / lm));
+            c = fmin(c, 0.15 * (a2 / lm));
         }
         const double h0 = H0[t];
         for (int q = 0; q < 3; ++q) {   // apex q over the edge (q+1, q+2)
