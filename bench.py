@@ -42,8 +42,8 @@ L2_BYTES = 129e6
 # bench command at its configuration (summary and command in profiles/), keyed by the sha1 of
 # the kernel source it measured: used only while that source is unchanged, else null.
 NCU_TRAFFIC = {
-    # (variant, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
-    ("blocked", 2048, 8, 512): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
+    # (variant, tiler, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
+    ("blocked", "kd", 2048, 8, 512): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
                                 "profiles/blocked_k_tbp_scatterer4M.md"),
 }
 
@@ -58,6 +58,21 @@ def _traffic(key):
         if hashlib.sha1(f.read()).hexdigest() != sha:
             return None, f"{prof}: kernel source changed since the capture"
     return float(nbytes), prof
+
+
+def partition_stats(m):
+    """Fig. 6 quantities of a tiled mesh: parts, triangles per part (mean, rms deviation, max)
+    and the shared boundary l_Sigma, the interior edges whose triangles lie in two parts."""
+    import numpy as np
+
+    off = m.tiles()
+    sizes = np.diff(off)
+    t = m.tables()
+    tile = np.searchsorted(off, np.arange(m.n_tris), side="right") - 1
+    et = t["edge_tri"]
+    shared = int(np.count_nonzero(tile[et[:, 0]] != tile[et[:, 1]]))
+    return {"parts": int(sizes.size), "tris_mean": float(sizes.mean()), "tris_rms": float(sizes.std()),
+            "tris_max": int(sizes.max()), "shared_edges": shared}
 
 
 def _peaks():
@@ -215,7 +230,8 @@ def run_native(args):
     ms, ids, amp, w0, t0, tau = load_workload()
     stream = torch.cuda.current_stream()
     blocked = args.variant == "blocked"
-    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if blocked else ue.UE_REORDER_RCM,
+    tiled = ue.UE_REORDER_GREEDY if args.tiler == "greedy" else ue.UE_REORDER_KD
+    m = ue.Mesh(ms.xy, ms.tris, reorder=tiled if blocked else ue.UE_REORDER_RCM,
                 tile_tris=args.tile_tris)
     variant = {"plain": ue.UE_VARIANT_PLAIN, "blocked": ue.UE_VARIANT_BLOCKED,
                "persistent": ue.UE_VARIANT_PERSISTENT}[args.variant]
@@ -231,6 +247,7 @@ def run_native(args):
     m.set_source(ids, amp, w0, t0, tau)
     st = m.stats()
     n_t, n_ei = st["n_tris"], st["n_interior_edges"]
+    part_stats = partition_stats(m) if blocked else None
 
     # warm-up (also captures the step graph)
     m.step_n(args.warmup, stream)
@@ -262,12 +279,13 @@ def run_native(args):
     prof_ms, prof_bytes = m.profile_steps(nprof, stream)
     names = ["k_edge_half: E half-step (eq. 3)", "k_source", "k_tri_half: B half-step (eq. 4)"]
     if blocked:
-        names[0] = (f"k_tbp: {args.block_depth} leap-frog steps per launch on KD tiles, one CTA per SM "
+        names[0] = (f"k_tbp: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, one CTA per SM "
                     "with the next tile's loads in flight")
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
-    tkey = (args.variant, args.tile_tris if blocked else 0, args.block_depth if blocked else 1,
+    tkey = (args.variant, args.tiler if blocked else "", args.tile_tris if blocked else 0,
+            args.block_depth if blocked else 1,
             (args.tb_threads or 512) if blocked else 0)
     traffic, traffic_src = _traffic(tkey)
     step_bytes = st["bytes_per_step"]
@@ -317,11 +335,12 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_tris": n_t, "n_interior_edges": n_ei,
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
-                       "variant": (f"blocked k={args.block_depth} tiles<={args.tile_tris} "
+                       "variant": (f"blocked k={args.block_depth} {args.tiler} tiles<={args.tile_tris} "
                                 f"threads={args.tb_threads or 512}" if blocked
                                 else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "tiles": part_stats},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,
         }
@@ -570,6 +589,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
     ap.add_argument("--tile-tris", type=int, default=2048)
+    ap.add_argument("--tiler", choices=["kd", "greedy"], default="kd",
+                    help="blocked variant: KD or greedy partition into tiles")
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])

@@ -46,6 +46,9 @@ extern "C" {
 #define UE_REORDER_NONE 0        /* triangles in caller order                                 */
 #define UE_REORDER_RCM 1         /* reverse Cuthill-McKee on the dual graph (default)         */
 #define UE_REORDER_KD 2          /* KD tiles of <= tile_tris triangles, RCM order inside      */
+#define UE_REORDER_GREEDY 3      /* greedy tiles of <= tile_tris triangles, grown breadth     */
+                                 /* first from the sharpest boundary triangle, small parts    */
+                                 /* and hanging triangles joined; RCM order inside            */
 
 #define UE_PREC_FP32 0           /* FP32 fields and coefficients (product)                    */
 #define UE_PREC_FP64 1           /* FP64 fields and coefficients (check build)                */
@@ -59,7 +62,7 @@ extern "C" {
 
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
 #define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
-                                 /* recomputed in shared memory; FP32; needs UE_REORDER_KD    */
+                                 /* recomputed in shared memory; FP32; needs KD or greedy     */
 #define UE_VARIANT_PERSISTENT 3  /* one cooperative launch per chunk of steps, timed grid     */
                                  /* barriers between half-steps; FP32                         */
 
@@ -85,7 +88,7 @@ typedef struct ue_options {
     uint32_t power_seed;   /* start vector: SplitMix64(seed * 2^32 + caller triangle id)     */
     int32_t variant;       /* UE_VARIANT_* (0 = default: plain)                              */
     int32_t graph_chunk;   /* steps per captured CUDA graph launch; 0 = default, <0 = none   */
-    int32_t tile_tris;     /* UE_REORDER_KD: maximum triangles per tile (ue_mesh_load)       */
+    int32_t tile_tris;     /* UE_REORDER_KD / _GREEDY: maximum triangles per tile (ue_mesh_load) */
     int32_t block_depth;   /* UE_VARIANT_BLOCKED: steps per launch, 1..15                    */
     int32_t tb_threads;    /* UE_VARIANT_BLOCKED: CTA size, 0 = 512 (default) or 1024        */
     double dt;             /* UE_DT_GIVEN: the time step                                     */
@@ -200,6 +203,12 @@ int ue_get_sizes(const ue_mesh* m, int64_t* n_nodes, int64_t* n_tris, int64_t* n
  * the vertex triple rotated to start at its smallest caller node id. Any pointer may be NULL. */
 int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int32_t* edge_tri,
                   int32_t* tri_code);
+
+/* Tiles of a UE_REORDER_KD or UE_REORDER_GREEDY mesh ("Divide and conqueror" section):
+ * *n_tiles parts (0 for other orders); tile t holds the stored triangles
+ * tile_off[t] .. tile_off[t+1]-1.  tile_off (host, n_tiles + 1 entries) may be NULL to ask the
+ * count only.  Host only; UE_ERR_ARG if m or n_tiles is NULL. */
+int ue_get_tiles(const ue_mesh* m, int64_t* n_tiles, int64_t* tile_off);
 
 /* FP64 geometry computed on the device, caller numbering (after ue_geometry_build):
  * O[2*n_tris] circumcentres, S[n_tris] areas, elen[n_edges] lengths, d[n_edges] signed dual

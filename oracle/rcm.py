@@ -13,7 +13,7 @@ no tie-break rules; the ones used here (and, independently, by the library) are:
 * the concatenated order is reversed at the end.
 
 For the temporally blocked variant the triangles are further grouped into KD parts
-(``kd_order``), keeping the RCM order inside each part.
+(``kd_order``) or greedy parts (``greedy_order``), keeping the RCM order inside each part.
 
 From an order the tables follow (same definitions in the library, separate code):
 
@@ -107,6 +107,110 @@ def kd_order(mesh: Mesh, rcm: np.ndarray, tile_tris: int):
 
     part(np.asarray(rcm, np.int64))
     return np.asarray(order, np.int64), np.asarray(offs, np.int64)
+
+
+def greedy_order(mesh: Mesh, rcm: np.ndarray, tile_tris: int):
+    """Greedy partition of the "Divide and conqueror" section, with its two refinements.
+    Returns (order, tile offsets); no part holds more than tile_tris triangles.
+
+    Readings (the paper states the ideas, not the rules):
+    * a part is grown from its root, breadth first, each triangle taken from the front adding
+      its unassigned neighbours in RCM order, up to tile_tris - tile_tris // 8 triangles (room
+      left for the refinements) or until the front is empty;
+    * the next root is the "sharpest" triangle on the boundary of what is assigned (or of the
+      mesh): the unassigned triangle with the fewest unassigned neighbours, counting only those
+      with fewer than three, ties by RCM position;
+    * a part of fewer than theta = tile_tris // 8 triangles joins its smallest neighbouring part
+      of at least theta triangles that has room for it (ties by part index); parts are visited in
+      creation order;
+    * a "hanging" triangle (one edge on its own part, its two other edges on one other part Q)
+      moves to Q when Q has room; sweeps over the triangles in RCM order, moving as found, repeat
+      until one moves nothing;
+    * parts are laid out in creation order, RCM order inside each."""
+    n = mesh.n_tris
+    nbr = dual_adjacency(mesh)
+    pos = np.empty(n, np.int64)
+    pos[rcm] = np.arange(n)
+    nbr = [sorted(a, key=lambda w: pos[w]) for a in nbr]
+    theta = tile_tris // 8
+    target = tile_tris - theta
+
+    part = np.full(n, -1, np.int64)
+    n_free = np.array([len(a) for a in nbr], np.int64)
+    parts = []
+    while (part < 0).any():
+        cand = np.flatnonzero((part < 0) & (n_free < 3))
+        if cand.size:
+            root = int(cand[np.lexsort((pos[cand], n_free[cand]))[0]])
+        else:
+            free = np.flatnonzero(part < 0)
+            root = int(free[np.argmin(pos[free])])
+        pid = len(parts)
+        grown = []
+
+        def eat(u):
+            part[u] = pid
+            grown.append(u)
+            for w in nbr[u]:
+                n_free[w] -= 1
+
+        eat(root)
+        front = deque([root])
+        while front and len(grown) < target:
+            u = front.popleft()
+            for w in nbr[u]:
+                if len(grown) >= target:
+                    break
+                if part[w] < 0:
+                    eat(w)
+                    front.append(w)
+        parts.append(grown)
+
+    size = [len(g) for g in parts]
+    for pid, grown in enumerate(parts):
+        if size[pid] == 0 or size[pid] >= theta:
+            continue
+        touching = {int(part[w]) for u in grown for w in nbr[u]} - {pid}
+        ok = [q for q in touching if size[q] >= theta and size[q] + size[pid] <= tile_tris]
+        if not ok:
+            continue
+        q = min(ok, key=lambda r: (size[r], r))
+        part[grown] = q
+        size[q] += size[pid]
+        size[pid] = 0
+
+    while True:
+        moves = 0
+        for u in rcm:
+            if len(nbr[u]) != 3:
+                continue
+            own = int(part[u])
+            others = [int(part[w]) for w in nbr[u] if part[w] != own]
+            if len(others) == 2 and others[0] == others[1] and size[others[0]] < tile_tris:
+                part[u] = others[0]
+                size[own] -= 1
+                size[others[0]] += 1
+                moves += 1
+        if moves == 0:
+            break
+
+    order, offs = [], [0]
+    for pid in range(len(parts)):
+        ids = np.flatnonzero(part == pid)
+        if ids.size:
+            order.extend(ids[np.argsort(pos[ids])].tolist())
+            offs.append(len(order))
+    return np.asarray(order, np.int64), np.asarray(offs, np.int64)
+
+
+def shared_edges(mesh: Mesh, order: np.ndarray, offs: np.ndarray) -> int:
+    """Interior edges whose two triangles lie in different parts: the shared boundary length
+    l_Sigma of Fig. 6, counted in edges."""
+    tile = np.empty(mesh.n_tris, np.int64)
+    for p in range(len(offs) - 1):
+        tile[order[offs[p]:offs[p + 1]]] = p
+    ii = mesh.interior_ids
+    return int(np.count_nonzero(tile[mesh.R[ii]] != tile[mesh.L[ii]]))
 
 
 def device_tables(mesh: Mesh, perm_tri: np.ndarray):

@@ -196,6 +196,15 @@ class Mesh:
                 "ue_get_tables")
         return dict(perm_tri=perm, edge_caller=ec, edge_tri=et, tri_code=tc, n_ei=self.n_ei)
 
+    def tiles(self):
+        """Tile offsets [n_tiles + 1] of a KD or greedy mesh (empty for other orders)."""
+        n = C.c_int64(0)
+        N.check(N.lib().ue_get_tiles(self._h, C.byref(n), None), "ue_get_tiles")
+        off = np.zeros(n.value + 1 if n.value else 0, np.int64)
+        if n.value:
+            N.check(N.lib().ue_get_tiles(self._h, C.byref(n), off.ctypes.data_as(N.PI64)), "ue_get_tiles")
+        return off
+
     def geometry(self):
         O = np.empty((self.n_tris, 2))
         S = np.empty(self.n_tris)

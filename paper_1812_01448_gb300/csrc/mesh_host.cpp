@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <set>
 #include <utility>
 
 #include "ue_internal.h"
@@ -217,6 +218,147 @@ void kd_order(const Canon& c, const double* xy, const std::vector<int64_t>& rcm_
     }
 }
 
+// Greedy partition (the paper's "greedy" method of the "Divide and conqueror" section) with its
+// two refinements.  No part ever holds more than tile_tris triangles.
+// * Growth: a part grows breadth first from its root, each dequeued triangle adding its
+//   unassigned neighbours in RCM-position order, until it has target = tile_tris - tile_tris/8
+//   triangles or its front is used up.  The next root is the "sharpest" unassigned triangle of
+//   the current boundary: among the unassigned triangles with fewer than 3 unassigned neighbours,
+//   one with the fewest, ties by RCM position.
+// * Small parts: in creation order, a part of fewer than theta = tile_tris/8 triangles joins the
+//   smallest neighbouring part of at least theta triangles (ties by part index) that can take it.
+// * Hanging triangles: a triangle with one edge on its own part and its two other edges on one
+//   other part Q moves to Q if Q has room.  Sweeps in RCM order, moving as found, until a sweep
+//   moves none; each move adds a same-part adjacency, so the sweeps end.
+// Parts are emitted in index order, RCM order inside each.
+void greedy_order(const Canon& c, int64_t nt, const std::vector<int64_t>& rcm_order, int64_t tile_tris,
+                  std::vector<int64_t>& order, std::vector<int64_t>& tile_off) {
+    const int64_t theta = tile_tris / 8, target = tile_tris - theta;
+    std::vector<int64_t> pos(nt);
+    for (int64_t i = 0; i < nt; ++i) pos[rcm_order[i]] = i;
+    std::vector<int64_t> ptr(nt + 1, 0);
+    const int64_t ne = (int64_t)c.R.size();
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            ++ptr[c.R[e] + 1];
+            ++ptr[c.L[e] + 1];
+        }
+    for (int64_t j = 0; j < nt; ++j) ptr[j + 1] += ptr[j];
+    std::vector<int64_t> adj(ptr[nt]);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            adj[fill[c.R[e]]++] = c.L[e];
+            adj[fill[c.L[e]]++] = c.R[e];
+        }
+    for (int64_t j = 0; j < nt; ++j)   // neighbours in RCM-position order
+        std::sort(adj.begin() + ptr[j], adj.begin() + ptr[j + 1],
+                  [&](int64_t a, int64_t b) { return pos[a] < pos[b]; });
+
+    // growth
+    std::vector<int> free_cnt(nt);
+    std::vector<int64_t> part_of(nt, -1);
+    std::set<std::pair<int64_t, int64_t>> bucket[3];   // (RCM position, triangle) by free count
+    for (int64_t j = 0; j < nt; ++j) {
+        free_cnt[j] = (int)(ptr[j + 1] - ptr[j]);
+        if (free_cnt[j] < 3) bucket[free_cnt[j]].insert({pos[j], j});
+    }
+    std::vector<int64_t> psize;
+    std::vector<std::vector<int64_t>> members;
+    auto take = [&](int64_t u, int64_t p) {
+        part_of[u] = p;
+        if (free_cnt[u] < 3) bucket[free_cnt[u]].erase({pos[u], u});
+        for (int64_t k = ptr[u]; k < ptr[u + 1]; ++k) {
+            const int64_t w = adj[k];
+            if (part_of[w] >= 0) continue;
+            if (free_cnt[w] < 3) bucket[free_cnt[w]].erase({pos[w], w});
+            --free_cnt[w];
+            bucket[free_cnt[w]].insert({pos[w], w});
+        }
+    };
+    int64_t left = nt, next_free = 0;   // next_free: fallback scan in RCM order
+    while (left > 0) {
+        int64_t root = -1;
+        for (int k = 0; k < 3 && root < 0; ++k)
+            if (!bucket[k].empty()) root = bucket[k].begin()->second;
+        if (root < 0) {
+            while (part_of[rcm_order[next_free]] >= 0) ++next_free;
+            root = rcm_order[next_free];
+        }
+        const int64_t p = (int64_t)psize.size();
+        members.emplace_back();
+        std::vector<int64_t>& q = members.back();   // the part, in BFS order, is its own queue
+        take(root, p);
+        q.push_back(root);
+        for (size_t qh = 0; qh < q.size() && (int64_t)q.size() < target; ++qh) {
+            const int64_t u = q[qh];
+            for (int64_t k = ptr[u]; k < ptr[u + 1] && (int64_t)q.size() < target; ++k) {
+                const int64_t w = adj[k];
+                if (part_of[w] >= 0) continue;
+                take(w, p);
+                q.push_back(w);
+            }
+        }
+        psize.push_back((int64_t)q.size());
+        left -= (int64_t)q.size();
+    }
+    const int64_t np = (int64_t)psize.size();
+
+    // small parts (a receiver has >= theta triangles, so it is never small itself)
+    for (int64_t p = 0; p < np; ++p) {
+        if (psize[p] == 0 || psize[p] >= theta) continue;
+        int64_t best = -1;
+        for (int64_t u : members[p])
+            for (int64_t k = ptr[u]; k < ptr[u + 1]; ++k) {
+                const int64_t o = part_of[adj[k]];
+                if (o == p || psize[o] < theta || psize[o] + psize[p] > tile_tris) continue;
+                if (best < 0 || psize[o] < psize[best] || (psize[o] == psize[best] && o < best)) best = o;
+            }
+        if (best < 0) continue;
+        for (int64_t u : members[p]) part_of[u] = best;
+        psize[best] += psize[p];
+        psize[p] = 0;
+    }
+
+    // hanging triangles
+    for (bool moved = true; moved;) {
+        moved = false;
+        for (int64_t i = 0; i < nt; ++i) {
+            const int64_t u = rcm_order[i];
+            if (ptr[u + 1] - ptr[u] != 3) continue;
+            const int64_t p = part_of[u];
+            int own = 0;
+            int64_t q = -1;
+            bool one_other = true;
+            for (int64_t k = ptr[u]; k < ptr[u + 1]; ++k) {
+                const int64_t o = part_of[adj[k]];
+                if (o == p) ++own;
+                else if (q < 0) q = o;
+                else if (o != q) one_other = false;
+            }
+            if (own != 1 || !one_other || psize[q] >= tile_tris) continue;
+            part_of[u] = q;
+            --psize[p];
+            ++psize[q];
+            moved = true;
+        }
+    }
+
+    // emit: parts in index order, RCM order inside
+    std::vector<int64_t> start(np + 1, 0);
+    for (int64_t j = 0; j < nt; ++j) ++start[part_of[j] + 1];
+    for (int64_t p = 0; p < np; ++p) start[p + 1] += start[p];
+    order.assign(nt, -1);
+    std::vector<int64_t> at(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < nt; ++i) {
+        const int64_t u = rcm_order[i];
+        order[at[part_of[u]]++] = u;
+    }
+    tile_off.assign(1, 0);
+    for (int64_t p = 0; p < np; ++p)
+        if (start[p + 1] > start[p]) tile_off.push_back(start[p + 1]);
+}
+
 }  // namespace
 
 int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
@@ -243,13 +385,14 @@ int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int6
     hm.tile_tri_off.clear();
     if (reorder == UE_REORDER_RCM) {
         hm.perm_tri = rcm(c, n_tris);
-    } else if (reorder == UE_REORDER_KD) {
+    } else if (reorder == UE_REORDER_KD || reorder == UE_REORDER_GREEDY) {
         if (tile_tris < 16) {
             err = "tile_tris must be >= 16";
             return UE_ERR_ARG;
         }
         std::vector<int64_t> r = rcm(c, n_tris);
-        kd_order(c, xy, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
+        if (reorder == UE_REORDER_KD) kd_order(c, xy, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
+        else greedy_order(c, n_tris, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
     } else {
         hm.perm_tri.resize(n_tris);
         std::iota(hm.perm_tri.begin(), hm.perm_tri.end(), 0);

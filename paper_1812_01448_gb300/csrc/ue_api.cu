@@ -607,7 +607,8 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
     ue_options d;
     ue_options_default(&d);
     const ue_options& o = opt ? *opt : d;
-    if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM && o.reorder != UE_REORDER_KD)
+    if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM && o.reorder != UE_REORDER_KD &&
+        o.reorder != UE_REORDER_GREEDY)
         return fail(UE_ERR_ARG, "unknown reorder option");
     ue_mesh* m = new (std::nothrow) ue_mesh();
     if (!m) return fail(UE_ERR_ARG, "out of host memory");
@@ -651,7 +652,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         return fail(UE_ERR_ARG, "the persistent variant is FP32 only and needs timeout_ms >= 1");
     if (o.variant == UE_VARIANT_BLOCKED) {
         if (o.precision != UE_PREC_FP32) return fail(UE_ERR_ARG, "the blocked variant is FP32 only");
-        if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs UE_REORDER_KD");
+        if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs tiles (UE_REORDER_KD or UE_REORDER_GREEDY)");
         if (o.block_depth < 1 || o.block_depth > 15) return fail(UE_ERR_ARG, "block_depth must be in 1..15");
         if (o.tb_threads != 0 && o.tb_threads != 512 && o.tb_threads != 1024)
             return fail(UE_ERR_ARG, "tb_threads must be 0, 512 or 1024");
@@ -1223,6 +1224,14 @@ int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int
     if (edge_caller) std::memcpy(edge_caller, h.edge_caller.data(), 8 * h.n_ei);
     if (edge_tri) std::memcpy(edge_tri, h.edge_tri.data(), 8 * h.n_ei);
     if (tri_code) std::memcpy(tri_code, h.tri_code.data(), 12 * h.n_tris);
+    return UE_OK;
+}
+
+int ue_get_tiles(const ue_mesh* m, int64_t* n_tiles, int64_t* tile_off) {
+    if (!m || !n_tiles) return fail(UE_ERR_ARG, "mesh or n_tiles is NULL");
+    const std::vector<int64_t>& o = m->hm.tile_tri_off;
+    *n_tiles = o.size() < 2 ? 0 : (int64_t)o.size() - 1;
+    if (tile_off && *n_tiles > 0) std::memcpy(tile_off, o.data(), 8 * o.size());
     return UE_OK;
 }
 

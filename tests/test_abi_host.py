@@ -74,7 +74,31 @@ def test_kd_tiles_bit_exact_against_oracle(ue):
         assert np.diff(offs).max() <= 300
         for k in ("perm_tri", "edge_caller", "edge_tri", "tri_code"):
             assert np.array_equal(t[k], ref[k]), (name, k)
+        assert np.array_equal(m.tiles(), offs), name
         m.close()
+
+
+@pytest.mark.parametrize("tile", [16, 97, 300])
+def test_greedy_tiles_bit_exact_against_oracle(ue, tile):
+    for name, ms in _meshes():
+        rng = np.random.default_rng(2)
+        tris = ms.tris[rng.permutation(ms.n_tris)].copy()
+        m = ue.Mesh(ms.xy, tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=tile)
+        t = m.tables()
+        om_ = om.canonicalize(ms.xy, tris)
+        order, offs = rcm.greedy_order(om_, rcm.rcm_order(om_), tile)
+        ref = rcm.device_tables(om_, order)
+        for k in ("perm_tri", "edge_caller", "edge_tri", "tri_code"):
+            assert np.array_equal(t[k], ref[k]), (name, tile, k)
+        assert np.array_equal(m.tiles(), offs), (name, tile)
+        m.close()
+
+
+def test_tiles_empty_without_partition(ue):
+    ms = meshgen.cavity_te11_mesh()
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_RCM)
+    assert m.tiles().size == 0
+    m.close()
 
 
 @pytest.mark.parametrize("tris,code", [

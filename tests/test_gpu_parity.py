@@ -226,8 +226,9 @@ def test_full_size_scatterer_window(ue, scatterer_window, variant):
 
 
 def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=None, graph_chunk=0,
-                 B0=None, threads=0):
-    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=tile)
+                 B0=None, threads=0, reorder=None):
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if reorder is None else reorder,
+                tile_tris=tile)
     m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=variant, block_depth=k,
                      graph_chunk=graph_chunk, tb_threads=threads)
     if dens is not None:
@@ -265,6 +266,27 @@ def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, threads, plasma)
         assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb)
         if plasma:
             assert np.array_equal(Jp, Jb)
+
+
+@pytest.mark.parametrize("tile,k,nsteps", [(64, 5, 31), (1024, 8, 40), (300, 3, 13)])
+def test_blocked_on_greedy_tiles_is_bit_identical_to_plain(ue, tile, k, nsteps):
+    """Greedy tiles (connected parts of any size up to the cap, small parts and hanging
+    triangles joined) feed the same blocked kernel; it must reproduce the plain step on the
+    same stored order bit for bit, with plasma, source and current."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 50)
+    dt = 0.45 / rho
+    kw = dict(dens=dens, nu=0.01 * w0, src=(ids, amp, w0, 0.0, 0.05),
+              B0=np.sin(7 * ms.xy[ms.tris].mean(axis=1)[:, 0]), reorder=ue.UE_REORDER_GREEDY)
+    (Ep, Bp, Jp), sp = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
+    (Eb, Bb, Jb), sb = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k, **kw)
+    assert sp == sb == nsteps
+    assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb) and np.array_equal(Jp, Jb)
+    kw.pop("dens")
+    kw["reorder"] = ue.UE_REORDER_GREEDY
+    (Ep, Bp, _), _ = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
+    (Eb, Bb, _), _ = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k, **kw)
+    assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb)
 
 
 def test_blocked_against_oracle(ue):

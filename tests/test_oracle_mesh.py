@@ -129,3 +129,123 @@ def test_device_tables_are_consistent():
     hi = np.maximum(R, L)
     key = lo * m.n_tris + hi
     assert np.all(np.diff(key) > 0)
+
+
+def _parts(order, offs):
+    return [order[offs[p]:offs[p + 1]] for p in range(len(offs) - 1)]
+
+
+def _connected(m, ids):
+    nbr = rcm.dual_adjacency(m)
+    inside = set(int(i) for i in ids)
+    seen, stack = {int(ids[0])}, [int(ids[0])]
+    while stack:
+        u = stack.pop()
+        for w in nbr[u]:
+            if w in inside and w not in seen:
+                seen.add(w)
+                stack.append(w)
+    return len(seen) == len(inside)
+
+
+def test_greedy_on_a_strip_cuts_consecutive_segments():
+    """On a strip the dual graph is a path and every triangle has at most two neighbours, so
+    the sharpest triangle is always the end of what is left: parts are consecutive segments of
+    target = T - T//8 triangles in RCM order; a last segment of fewer than T//8 triangles joins
+    the one before it (room for it by construction); no triangle can hang (degree < 3)."""
+    ms = meshgen.right_split_lattice(30, 2, 29.0, 1.0)          # 58 triangles
+    m = om.canonicalize(ms.xy, ms.tris)
+    r = rcm.rcm_order(m)
+    order, offs = rcm.greedy_order(m, r, 32)                     # target 28, theta 4
+    assert order.tolist() == r.tolist()
+    assert offs.tolist() == [0, 28, 58]                          # 28 + 28 + 2, the 2 joined
+    assert rcm.shared_edges(m, order, offs) == 1
+    order, offs = rcm.greedy_order(m, r, 16)                     # target 14, theta 2
+    assert offs.tolist() == [0, 14, 28, 42, 56, 58]              # last 2 >= theta: kept
+    assert rcm.shared_edges(m, order, offs) == 4                 # 5 segments of a path
+
+
+def _holed():
+    return meshgen.graded_square(0.01, 0.03, grade=0.3,
+                                 holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=9)
+
+
+@pytest.mark.parametrize("tile", [16, 64, 333])
+def test_greedy_parts_are_connected_capped_and_without_hanging_triangles(tile):
+    ms = _holed()
+    m = om.canonicalize(ms.xy, ms.tris)
+    order, offs = rcm.greedy_order(m, rcm.rcm_order(m), tile)
+    assert np.array_equal(np.sort(order), np.arange(m.n_tris))
+    sizes = np.diff(offs)
+    assert sizes.min() >= 1 and sizes.max() <= tile
+    part = np.empty(m.n_tris, np.int64)
+    for p, ids in enumerate(_parts(order, offs)):
+        assert _connected(m, ids), (tile, p)
+        part[ids] = p
+    # no triangle left hanging on a part that still has room
+    for u, ws in enumerate(rcm.dual_adjacency(m)):
+        if len(ws) != 3:
+            continue
+        other = [int(part[w]) for w in ws if part[w] != part[u]]
+        if len(other) == 2 and other[0] == other[1]:
+            assert sizes[other[0]] == tile
+    # shared boundary from its definition: edges whose two triangles sit in different parts
+    cut = sum(1 for i in m.interior_ids if part[m.R[i]] != part[m.L[i]])
+    assert rcm.shared_edges(m, order, offs) == cut
+
+
+def test_greedy_hanging_refinement_cuts_shared_edges():
+    """Moving a hanging triangle turns its two edges on Q into inner edges and its one edge on
+    its own part into a shared one: each move removes one shared edge, so the refined partition
+    never shares more edges than the parts before the sweep.  The unrefined parts are rebuilt
+    here from the growth rules alone (no joins happen at this size on this mesh)."""
+    ms = _holed()
+    m = om.canonicalize(ms.xy, ms.tris)
+    r = rcm.rcm_order(m)
+    order, offs = rcm.greedy_order(m, r, 64)
+    refined = rcm.shared_edges(m, order, offs)
+    # growth only: the hanging and small-part steps switched off by a tile cap they never meet
+    nbr = rcm.dual_adjacency(m)
+    pos = np.empty(m.n_tris, np.int64)
+    pos[r] = np.arange(m.n_tris)
+    part = np.full(m.n_tris, -1)
+    free = np.array([len(a) for a in nbr])
+    pid = 0
+    while (part < 0).any():
+        c = np.flatnonzero((part < 0) & (free < 3))
+        root = int(c[np.lexsort((pos[c], free[c]))[0]])
+        grown, front = [root], [root]
+        part[root] = pid
+        for w in nbr[root]:
+            free[w] -= 1
+        while front and len(grown) < 56:
+            u = front.pop(0)
+            for w in sorted(nbr[u], key=lambda x: pos[x]):
+                if len(grown) < 56 and part[w] < 0:
+                    part[w] = pid
+                    grown.append(w)
+                    front.append(w)
+                    for x in nbr[w]:
+                        free[x] -= 1
+        pid += 1
+    raw = sum(1 for i in m.interior_ids if part[m.R[i]] != part[m.L[i]])
+    assert refined < raw
+
+
+def test_greedy_and_kd_share_about_the_same_boundary():
+    """Fig. 6: at nearly the same number of parts KD and greedy give nearly the same shared
+    boundary; greedy reaches part counts that are not powers of two."""
+    ms = meshgen.cavity_lattice(65, 33, 1.0, 0.5, jitter=0.2, seed=4)
+    m = om.canonicalize(ms.xy, ms.tris)
+    r = rcm.rcm_order(m)
+    ko, koffs = rcm.kd_order(m, r, 256)
+    n_kd = len(koffs) - 1
+    tile = int(round(m.n_tris / n_kd * 8 / 7))
+    go, goffs = rcm.greedy_order(m, r, tile)
+    n_gr = len(goffs) - 1
+    assert abs(n_gr - n_kd) <= n_kd // 4
+    lk, lg = rcm.shared_edges(m, ko, koffs), rcm.shared_edges(m, go, goffs)
+    assert 0.67 * lk < lg < 1.5 * lk, (lk, lg)
+    _, o3 = rcm.greedy_order(m, r, 200)
+    n3 = len(o3) - 1
+    assert n3 & (n3 - 1) != 0
