@@ -3,8 +3,8 @@
 One bench "step" is one full leap-frog step (E half-step over every interior edge, the line
 source, B half-step over every triangle) of the graded unit-square mesh with an equilateral
 PEC hole (h 2e-4 .. 8e-4, ~4M triangles, FP32 fields, FP64-built coefficients).  By default
-the steps run temporally blocked: KD tiles of <= 2048 triangles, 8 steps per launch, 512
-threads per tile (--variant plain: two kernels per step in RCM order).
+the steps run temporally blocked: greedy tiles of <= 2560 triangles (--tiler kd: KD tiles),
+8 steps per launch, 512 threads per tile (--variant plain: two kernels per step in RCM order).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -43,8 +43,11 @@ L2_BYTES = 129e6
 # the kernel source it measured: used only while that source is unchanged, else null.
 NCU_TRAFFIC = {
     # (variant, tiler, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
+    ("blocked", "greedy", 2560, 8, 512): (304521643, "kernels_tb.cu",
+                                          "74268af160169826e19cf8973928e739eb32c11d",
+                                          "profiles/blocked_k_tbp_scatterer4M.md"),
     ("blocked", "kd", 2048, 8, 512): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
-                                "profiles/blocked_k_tbp_scatterer4M.md"),
+                                      "profiles/blocked_k_tbp_scatterer4M.md"),
 }
 
 
@@ -391,7 +394,7 @@ def run_batch(args):
                "blocked": ue.UE_VARIANT_BLOCKED}[best["variant"]]
     singles = []
     for ms, ids, amp, w0 in items:
-        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD, tile_tris=best["tile_tris"])
+        m = ue.Mesh(ms.xy, ms.tris, reorder=tune.TILERS[best["tiler"]], tile_tris=best["tile_tris"])
         m.geometry_build(stream=stream, graph_chunk=-1)          # own dt: power iteration
         m.set_source(ids, amp, w0, 0.1, 0.05)
         singles.append(m)
@@ -588,8 +591,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
-    ap.add_argument("--tile-tris", type=int, default=2048)
-    ap.add_argument("--tiler", choices=["kd", "greedy"], default="kd",
+    ap.add_argument("--tile-tris", type=int, default=2560)
+    ap.add_argument("--tiler", choices=["kd", "greedy"], default="greedy",
                     help="blocked variant: KD or greedy partition into tiles")
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)

@@ -20,7 +20,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
-#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -125,49 +124,72 @@ bool in_circle(const std::vector<double>& x, int a, int b, int c, int d) {
     return det > 1e-10 * s * s;
 }
 
-// Lawson flips until every interior edge is locally Delaunay; returns the number of flips
+// Lawson flips until every interior edge is locally Delaunay; returns the number of flips.
+// nb[3 i + q] is the triangle across edge q = (t[q], t[q+1]) of triangle i (-1 on the boundary).
+// The stack holds (triangle, a, b) for a directed CCW edge a->b; an entry whose triangle no longer
+// holds that edge is stale and skipped: every flip pushes its four outer edges with their current
+// triangles, so no live edge is lost.
 int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
     const int64_t nt = (int64_t)t.size() / 3;
-    std::map<std::pair<int32_t, int32_t>, int64_t> owner;   // directed edge -> triangle (CCW)
-    for (int64_t i = 0; i < nt; ++i)
-        for (int q = 0; q < 3; ++q) owner[{t[3 * i + q], t[3 * i + (q + 1) % 3]}] = i;
-    std::vector<std::pair<int32_t, int32_t>> stack;
-    for (const auto& kv : owner)
-        if (kv.first.first < kv.first.second && owner.count({kv.first.second, kv.first.first}))
-            stack.push_back(kv.first);
-    int64_t flips = 0;
-    auto third = [&](int64_t i, int32_t a, int32_t b) {
+    std::vector<int64_t> nb(3 * nt, -1);
+    {
+        std::vector<std::pair<uint64_t, int64_t>> de(3 * nt);   // (undirected key, slot)
+        for (int64_t s = 0; s < 3 * nt; ++s) {
+            const int64_t i = s / 3, q = s % 3;
+            const uint32_t a = (uint32_t)t[s], b = (uint32_t)t[3 * i + (q + 1) % 3];
+            de[s] = {((uint64_t)std::min(a, b) << 32) | std::max(a, b), s};
+        }
+        std::sort(de.begin(), de.end());
+        for (size_t k = 0; k + 1 < de.size(); ++k)
+            if (de[k].first == de[k + 1].first) {
+                nb[de[k].second] = de[k + 1].second / 3;
+                nb[de[k + 1].second] = de[k].second / 3;
+                ++k;
+            }
+    }
+    struct Item { int64_t tri; int32_t a, b; };
+    std::vector<Item> stack;
+    stack.reserve(3 * nt);
+    for (int64_t s = 3 * nt - 1; s >= 0; --s)
+        if (nb[s] > s / 3) stack.push_back({s / 3, t[s], t[3 * (s / 3) + (s % 3 + 1) % 3]});
+    auto slot_of = [&](int64_t i, int32_t a, int32_t b) -> int {
         for (int q = 0; q < 3; ++q)
-            if (t[3 * i + q] != a && t[3 * i + q] != b) return t[3 * i + q];
-        return (int32_t)-1;
+            if (t[3 * i + q] == a && t[3 * i + (q + 1) % 3] == b) return q;
+        return -1;
     };
+    int64_t flips = 0;
     while (!stack.empty()) {
-        const auto e = stack.back();
+        const Item it = stack.back();
         stack.pop_back();
-        const int32_t a = e.first, b = e.second;
-        auto ia = owner.find({a, b});
-        auto ib = owner.find({b, a});
-        if (ia == owner.end() || ib == owner.end()) continue;
-        const int64_t i = ia->second, j = ib->second;
-        const int32_t c = third(i, a, b), d = third(j, a, b);
+        const int64_t i = it.tri;
+        const int qi = slot_of(i, it.a, it.b);
+        if (qi < 0) continue;                       // stale: the edge left this triangle
+        const int64_t j = nb[3 * i + qi];
+        if (j < 0) continue;
+        const int32_t a = it.a, b = it.b, c = t[3 * i + (qi + 2) % 3];
+        const int qj = slot_of(j, b, a);
+        const int32_t d = t[3 * j + (qj + 2) % 3];
         if (!in_circle(x, a, b, c, d)) continue;
         if (orient2d(x, a, d, c) <= 0 || orient2d(x, d, b, c) <= 0) continue;   // not convex
-        for (const auto& k : {std::make_pair(a, b), std::make_pair(b, c), std::make_pair(c, a),
-                              std::make_pair(b, a), std::make_pair(a, d), std::make_pair(d, b)})
-            owner.erase(k);
-        const int32_t ti[3] = {a, d, c}, tj[3] = {d, b, c};
-        for (int q = 0; q < 3; ++q) {
-            t[3 * i + q] = ti[q];
-            t[3 * j + q] = tj[q];
-        }
-        for (int q = 0; q < 3; ++q) {
-            owner[{ti[q], ti[(q + 1) % 3]}] = i;
-            owner[{tj[q], tj[(q + 1) % 3]}] = j;
-        }
+        const int64_t X_bc = nb[3 * i + (qi + 1) % 3], X_ca = nb[3 * i + (qi + 2) % 3];
+        const int64_t X_ad = nb[3 * j + (qj + 1) % 3], X_db = nb[3 * j + (qj + 2) % 3];
+        // new i = (a, d, c), new j = (d, b, c)
+        t[3 * i] = a; t[3 * i + 1] = d; t[3 * i + 2] = c;
+        t[3 * j] = d; t[3 * j + 1] = b; t[3 * j + 2] = c;
+        nb[3 * i] = X_ad; nb[3 * i + 1] = j; nb[3 * i + 2] = X_ca;
+        nb[3 * j] = X_db; nb[3 * j + 1] = X_bc; nb[3 * j + 2] = i;
+        auto repoint = [&](int64_t X, int64_t from, int64_t to) {
+            if (X < 0) return;
+            for (int q = 0; q < 3; ++q)
+                if (nb[3 * X + q] == from) { nb[3 * X + q] = to; return; }
+        };
+        repoint(X_ad, j, i);
+        repoint(X_bc, i, j);
         ++flips;
-        for (const auto& k : {std::make_pair(a, d), std::make_pair(d, b), std::make_pair(b, c),
-                              std::make_pair(c, a)})
-            stack.push_back({std::min(k.first, k.second), std::max(k.first, k.second)});
+        stack.push_back({i, a, d});
+        stack.push_back({j, d, b});
+        stack.push_back({j, b, c});
+        stack.push_back({i, c, a});
     }
     return flips;
 }

@@ -1,9 +1,10 @@
-"""Autotuner for batched stepping: variant, KD tile size, threads per tile, blocking depth.
+"""Autotuner for batched stepping: variant, tiler and tile size, threads per tile, blocking depth.
 
 Many independent meshes advance together (ue_batch_create).  Which launch form is fastest
 depends on the meshes' sizes and on the GPU: one E and one B launch per step over the whole
-batch, one cooperative persistent launch per chunk of steps, or temporal blocking (KD tiles
-of ``tile_tris`` triangles advanced ``block_depth`` steps per launch by 512 or 1024 threads).
+batch, one cooperative persistent launch per chunk of steps, or temporal blocking (KD or
+greedy tiles of at most ``tile_tris`` triangles advanced ``block_depth`` steps per launch by 512
+or 1024 threads).
 The tuner times each candidate on a sample of the meshes, spread over their size
 distribution, as a real batch: built by the library, stepped inside its CUDA graphs, timed
 with CUDA events on the launching stream.  Each mesh keeps its own source; a fixed small dt
@@ -20,16 +21,20 @@ import numpy as np
 from .api import Mesh, batch_create
 from . import _native as N
 
-# (variant, tile_tris, block_depth, tb_threads); plain and persistent use the KD order too.
+# (variant, tiler, tile_tris, block_depth, tb_threads); plain and persistent use the tiled
+# order too.
 DEFAULT_CANDIDATES = (
-    ("plain", 2048, 1, 512),
-    ("persistent", 2048, 1, 512),
-    ("blocked", 1024, 4, 512),
-    ("blocked", 2048, 4, 512),
-    ("blocked", 2048, 6, 512),
-    ("blocked", 2048, 8, 512),
-    ("blocked", 2048, 8, 1024),
+    ("plain", "kd", 2048, 1, 512),
+    ("persistent", "kd", 2048, 1, 512),
+    ("blocked", "kd", 1024, 4, 512),
+    ("blocked", "kd", 2048, 4, 512),
+    ("blocked", "kd", 2048, 6, 512),
+    ("blocked", "kd", 2048, 8, 512),
+    ("blocked", "kd", 2048, 8, 1024),
+    ("blocked", "greedy", 2560, 8, 512),
 )
+
+TILERS = {"kd": N.UE_REORDER_KD, "greedy": N.UE_REORDER_GREEDY}
 
 _VARIANT = {"plain": N.UE_VARIANT_PLAIN, "persistent": N.UE_VARIANT_PERSISTENT,
             "blocked": N.UE_VARIANT_BLOCKED}
@@ -50,14 +55,14 @@ def _steps_for(steps: int, depth: int) -> int:
 
 
 def time_batch(items, variant: str, tile_tris: int, block_depth: int, tb_threads: int,
-               steps: int = 192, warmup: int = 48, stream=None, meshes=None) -> float:
+               steps: int = 192, warmup: int = 48, stream=None, meshes=None, tiler: str = "kd") -> float:
     """Triangle-steps/s of one configuration on a batch of ``items`` = (MeshArrays, source
     edge ids, amplitudes, omega0).  ``meshes`` may hold already loaded Mesh objects of the same
-    items and tile size (they are rebuilt for this variant)."""
+    items, tiler and tile size (they are rebuilt for this variant)."""
     import torch
     own = meshes is None
     if own:
-        meshes = [Mesh(ms.xy, ms.tris, reorder=N.UE_REORDER_KD, tile_tris=tile_tris) for ms, *_ in items]
+        meshes = [Mesh(ms.xy, ms.tris, reorder=TILERS[tiler], tile_tris=tile_tris) for ms, *_ in items]
     for m, (ms, ids, amp, w0) in zip(meshes, items):
         m.geometry_build(stream=stream, dt_mode=N.UE_DT_GIVEN, dt=1e-7, variant=_VARIANT[variant],
                          block_depth=block_depth, tb_threads=tb_threads, graph_chunk=32)
@@ -87,21 +92,22 @@ def autotune_batch(items, candidates=DEFAULT_CANDIDATES, sample: int = 32, steps
                    stream=None):
     """Time every candidate on a spread sample of ``items``; return (best, table).  ``best``
     and each row of ``table`` are dicts with variant, tile_tris, block_depth, tb_threads and
-    rate (triangle-steps/s on the sample); the table also records the tuning time."""
+    rate (triangle-steps/s on the sample), plus the tiler; the table also records the tuning
+    time."""
     idx = spread([ms.n_tris for ms, *_ in items], sample)
     sub = [items[i] for i in idx]
     t0 = time.perf_counter()
     table = []
-    by_tile: dict[int, list] = {}
+    by_tile: dict[tuple, list] = {}
     for c in candidates:
-        by_tile.setdefault(int(c[1]), []).append(c)
-    for tile, cands in by_tile.items():
-        meshes = [Mesh(ms.xy, ms.tris, reorder=N.UE_REORDER_KD, tile_tris=tile) for ms, *_ in sub]
+        by_tile.setdefault((c[1], int(c[2])), []).append(c)
+    for (tiler, tile), cands in by_tile.items():
+        meshes = [Mesh(ms.xy, ms.tris, reorder=TILERS[tiler], tile_tris=tile) for ms, *_ in sub]
         try:
-            for variant, _, depth, threads in cands:
+            for variant, _, _, depth, threads in cands:
                 rate = time_batch(sub, variant, tile, depth, threads, steps=steps, stream=stream,
-                                  meshes=meshes)
-                table.append(dict(variant=variant, tile_tris=tile, block_depth=depth,
+                                  meshes=meshes, tiler=tiler)
+                table.append(dict(variant=variant, tiler=tiler, tile_tris=tile, block_depth=depth,
                                   tb_threads=threads, rate=rate))
         finally:
             for m in meshes:

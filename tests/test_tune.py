@@ -15,8 +15,8 @@ def test_spread_covers_the_size_range():
 
 
 def test_candidates_are_valid_launch_forms():
-    for variant, tile, depth, threads in tune.DEFAULT_CANDIDATES:
-        assert variant in ("plain", "persistent", "blocked")
+    for variant, tiler, tile, depth, threads in tune.DEFAULT_CANDIDATES:
+        assert variant in ("plain", "persistent", "blocked") and tiler in tune.TILERS
         assert tile >= 256 and threads in (512, 1024)
         assert depth >= 1 and (variant == "blocked" or depth == 1)
 
@@ -34,8 +34,9 @@ def test_autotune_picks_a_measured_candidate():
         ms = meshgen.batch_mesh(sp)
         ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.3, ms.h)
         items.append((ms, ids, amp, sp["omega0"]))
-    cands = (("plain", 512, 1, 512), ("persistent", 512, 1, 512), ("blocked", 512, 4, 512))
+    cands = (("plain", "kd", 512, 1, 512), ("persistent", "kd", 512, 1, 512),
+             ("blocked", "kd", 512, 4, 512), ("blocked", "greedy", 600, 4, 512))
     best, table = tune.autotune_batch(items, candidates=cands, sample=3, steps=48)
-    assert table["sample_meshes"] == 3 and len(table["rows"]) == 3
+    assert table["sample_meshes"] == 3 and len(table["rows"]) == 4
     assert all(r["rate"] > 0 and np.isfinite(r["rate"]) for r in table["rows"])
     assert best["rate"] == max(r["rate"] for r in table["rows"])
