@@ -102,8 +102,17 @@ def test_pml_matches_a_large_domain_until_its_echo_returns():
     assert e_none > 0.1
 
 
+def _not_a_divided_rectangle():
+    """A rotated cavity (sides not along the axes) and a square whose bottom nodes are not
+    uniformly spaced."""
+    c = meshgen.cavity_te11_mesh()
+    R = np.array([[math.cos(0.5), -math.sin(0.5)], [math.sin(0.5), math.cos(0.5)]])
+    xy = np.array([[0, 0], [1, 0], [1, 1], [0, 1], [0.3, 0], [0.5, 1], [0, 0.5], [1, 0.5], [0.5, 0.5]])
+    from scipy.spatial import Delaunay
+    return [(c.xy @ R.T, c.tris), (xy, Delaunay(xy).simplices.astype(np.int32))]
+
+
 def test_frame_needs_a_uniform_rectangular_boundary():
-    ms = meshgen.random_delaunay(200, seed=3)
-    m = om.canonicalize(ms.xy, ms.tris)
-    with pytest.raises(ValueError):
-        pml.FramedOperators(m, 4)
+    for xy, tris in _not_a_divided_rectangle():
+        with pytest.raises(ValueError):
+            pml.FramedOperators(om.canonicalize(xy, tris), 4)
