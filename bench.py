@@ -236,6 +236,8 @@ def run_native(args):
     tiled = ue.UE_REORDER_GREEDY if args.tiler == "greedy" else ue.UE_REORDER_KD
     m = ue.Mesh(ms.xy, ms.tris, reorder=tiled if blocked else ue.UE_REORDER_RCM,
                 tile_tris=args.tile_tris)
+    if args.frame > 0:
+        m.frame_attach(args.frame)
     variant = {"plain": ue.UE_VARIANT_PLAIN, "blocked": ue.UE_VARIANT_BLOCKED,
                "persistent": ue.UE_VARIANT_PERSISTENT}[args.variant]
     vopt = dict(variant=variant, block_depth=args.block_depth, graph_chunk=args.graph_chunk,
@@ -251,6 +253,7 @@ def run_native(args):
     st = m.stats()
     n_t, n_ei = st["n_tris"], st["n_interior_edges"]
     part_stats = partition_stats(m) if blocked else None
+    frame = m.frame_info() if args.frame > 0 else None
 
     # warm-up (also captures the step graph)
     m.step_n(args.warmup, stream)
@@ -343,7 +346,8 @@ def run_native(args):
                                 else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
                        "parallelism": f"replicas x{world}",
-                       "tiles": part_stats},
+                       "tiles": part_stats,
+                       "pml_frame": frame},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,
         }
@@ -592,6 +596,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
     ap.add_argument("--tile-tris", type=int, default=2560)
+    ap.add_argument("--frame", type=int, default=0,
+                    help="scatterer workload, plain variant: PML frame of this many cells (open "
+                         "boundary instead of the PEC walls)")
     ap.add_argument("--tiler", choices=["kd", "greedy"], default="greedy",
                     help="blocked variant: KD or greedy partition into tiles")
     ap.add_argument("--block-depth", type=int, default=8)
@@ -609,6 +616,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.frame > 0 and args.variant != "plain":
+        ap.error("--frame needs --variant plain")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

@@ -286,6 +286,47 @@ int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream);
 
+/* Open boundaries: a PML frame (the paper's conclusion: a mesh with a rectangular boundary tied
+ * to a structured frame of rectangular cells carrying PML layers).  The frame is `width` square
+ * cells of side h around the mesh's bounding box [X0, X1] x [Y0, Y1], h being the spacing of
+ * the mesh's outer boundary nodes, which must be uniform and the same on all four sides (the
+ * box a whole number nx x ny of them); holes stay PEC.  Cells carry B at their centres, E lives
+ * on their sides (Yee); the mesh's 2 nx + 2 ny outer edges become unknowns coupling a triangle
+ * and a frame cell, with dual length d = (O_tri - C_e) . n_in + h/2 (eq. 3; the two centres on
+ * the edge's perpendicular bisector).  The frame's own outer boundary is PEC.
+ * PML: Berenger's split field B = Bx + By in every frame cell, Bx fed by the cell's vertical
+ * sides and decaying at sigma_x(x), By by its horizontal sides at sigma_y(y); E on horizontal
+ * sides decays at sigma_y, on vertical sides at sigma_x; sigma(delta) = sigma_max
+ * (delta / (width h))^order, delta the distance beyond the box along that axis, taken at the
+ * field's position; the decay is trapezoidal in time.  sigma_max < 0 selects
+ * (order + 1) ln(1e6) / (2 width h) (a continuous layer reflecting 1e-6 at normal incidence);
+ * 0 gives an undamped frame.
+ * Host call on a loaded mesh; it takes effect at the next ue_geometry_build (width 0 removes
+ * the frame).  A framed mesh steps with the plain variant only (UE_VARIANT_PLAIN, with CUDA
+ * graphs); dt modes UE_DT_GIVEN and UE_DT_POWER, the power iteration then covering the whole
+ * framed system (eq. 20 for the coupled operator).  Its sources must be interior edges.
+ * ue_write_fields zeroes the frame's fields; ue_read_fields returns E on the mesh's outer
+ * edges too; the energy watchdog and ue_energy cover the mesh only.
+ * width in [1, 256], order in [1, 8].  Errors: UE_ERR_ARG (arguments, a batch, or an outer
+ * boundary that is not a uniformly divided axis-aligned rectangle). */
+int ue_frame_attach(ue_mesh* m, int32_t width, double sigma_max, int32_t order);
+
+/* Frame layout (host): dims = {width, nx, ny, NX = nx + 2 width, NY = ny + 2 width, n_cells,
+ * n_interface}, geom = {h, X0, Y0, sigma_max}.  Frame cells are numbered in strip order: the
+ * `width` bottom rows (NX cells each), then per middle row the `width` cells left of the mesh
+ * and the `width` right of it, then the `width` top rows; cell (I, J) of the NX x NY grid
+ * covers [X0 + (I - width) h, X0 + (I - width + 1) h] x [Y0 + (J - width) h, ...].
+ * Either pointer may be NULL.  UE_ERR_ARG without a frame. */
+int ue_frame_get(const ue_mesh* m, int64_t* dims, double* geom);
+
+/* Frame fields (synchronous, after ue_geometry_build): B[n_cells] = Bx + By per frame cell in
+ * strip order; Ex[NX * (NY + 1)]: E on the horizontal side at height J between columns I and
+ * I + 1, at Ex[J * NX + I]; Ey[(NX + 1) * NY]: E on the vertical side at column I between rows J
+ * and J + 1, at Ey[J * (NX + 1) + I]; sides along +x and +y; 0 on sides that are not frame
+ * unknowns (the PEC outer wall, the mesh's outer edges, which ue_read_fields returns, and sides
+ * inside the mesh).  Any pointer may be NULL. */
+int ue_frame_fields(ue_mesh* m, double* B, double* Ex, double* Ey, void* stream);
+
 /* Power iteration for rho(M) that allocates no device memory.
  * The paper has no counterpart: this exists for callers that cannot allocate device memory
  * while they run (a memory budget fixed up front, a host process that owns the allocator, or

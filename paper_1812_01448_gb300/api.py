@@ -196,6 +196,32 @@ class Mesh:
                 "ue_get_tables")
         return dict(perm_tri=perm, edge_caller=ec, edge_tri=et, tri_code=tc, n_ei=self.n_ei)
 
+    def frame_attach(self, width: int, sigma_max: float = -1.0, order: int = 3):
+        """PML frame of ``width`` square cells around the rectangular outer boundary
+        (ue_frame_attach); takes effect at the next geometry_build.  width 0 removes it."""
+        N.check(N.lib().ue_frame_attach(self._h, int(width), float(sigma_max), int(order)),
+                "ue_frame_attach")
+
+    def frame_info(self):
+        """dict(W, nx, ny, NX, NY, n_cells, n_interface, h, X0, Y0, sigma_max)."""
+        d = np.zeros(7, np.int64)
+        g = np.zeros(4)
+        N.check(N.lib().ue_frame_get(self._h, d.ctypes.data_as(N.PI64), _dptr(g)), "ue_frame_get")
+        keys = ("W", "nx", "ny", "NX", "NY", "n_cells", "n_interface")
+        out = {k: int(v) for k, v in zip(keys, d)}
+        out.update(h=float(g[0]), X0=float(g[1]), Y0=float(g[2]), sigma_max=float(g[3]))
+        return out
+
+    def frame_fields(self, stream=None):
+        """(B per frame cell in strip order, Ex [NY+1, NX], Ey [NY, NX+1]) (ue_frame_fields)."""
+        f = self.frame_info()
+        B = np.empty(f["n_cells"])
+        Ex = np.empty((f["NY"] + 1, f["NX"]))
+        Ey = np.empty((f["NY"], f["NX"] + 1))
+        N.check(N.lib().ue_frame_fields(self._h, _dptr(B), _dptr(Ex), _dptr(Ey), _stream(stream)),
+                "ue_frame_fields")
+        return B, Ex, Ey
+
     def tiles(self):
         """Tile offsets [n_tiles + 1] of a KD or greedy mesh (empty for other orders)."""
         n = C.c_int64(0)

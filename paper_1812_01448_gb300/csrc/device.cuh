@@ -83,7 +83,58 @@ static __device__ __noinline__ double source_g(long long n, double dt, double w0
     return __dmul_rn(sin(__dmul_rn(w0, t)), exp(-__dmul_rn(x, x)));
 }
 
-// Everything the step kernels need, in the stored numbering.
+// PML frame (kernels_frame.cu): W cells of side h around the mesh's bounding box, grid of
+// NX x NY cells, the mesh filling cells W..W+nx-1 x W..W+ny-1.  Frame cells are numbered in
+// strip order (bottom W rows, then per middle row W left and W right cells, then the top W
+// rows).  Frame sides: H(I, J) at height J between columns I and I+1 (along +x), stored at
+// H[J * NX + I]; V(I, J) at column I between rows J and J+1 (along +y), at V[J * (NX + 1) + I].
+// Interface edge k (the mesh's outer edges): k < nx bottom (cell (W + k, W - 1) below it),
+// then nx top (cell above), ny left (cell to the left), ny right; its circulation lives in the
+// mesh's U array at u_off + k, in the mesh edge's direction.
+struct FrameDev {
+    int W = 0, nx = 0, ny = 0, NX = 0, NY = 0;
+    int64_t n_fc = 0, n_if = 0;
+    int64_t u_off = 0;            // first interface slot in the mesh's edge arrays (= n_ei_pad)
+    double h = 0;
+    void* H = nullptr;            // T [NX * (NY + 1)] circulation h E_x
+    void* V = nullptr;            // T [(NX + 1) * NY] circulation h E_y
+    void* Bx = nullptr;           // T [n_fc]
+    void* By = nullptr;           // T [n_fc]
+    int32_t* itri = nullptr;      // [n_if] stored triangle t if it is R of the edge, else ~t
+    int32_t* icell = nullptr;     // [n_if] frame cell
+    void* icU = nullptr;          // T [n_if] dt |e| / d
+    double* ic = nullptr;         // [n_if] |e| / d (power iteration)
+    void* tab = nullptr;          // T: aH, bH [NY+1]; aV, bV [NX+1]; axc, bxc [NX]; ayc, byc [NY]
+};
+
+__host__ __device__ __forceinline__ bool frame_is_cell(const FrameDev& f, int I, int J) {
+    if (I < 0 || J < 0 || I >= f.NX || J >= f.NY) return false;
+    return !(I >= f.W && I < f.W + f.nx && J >= f.W && J < f.W + f.ny);
+}
+__host__ __device__ __forceinline__ int64_t frame_cell(const FrameDev& f, int I, int J) {
+    if (J < f.W) return (int64_t)J * f.NX + I;
+    if (J < f.W + f.ny)
+        return (int64_t)f.W * f.NX + (int64_t)(J - f.W) * 2 * f.W + (I < f.W ? I : I - f.nx);
+    return (int64_t)f.W * f.NX + (int64_t)2 * f.W * f.ny + (int64_t)(J - f.W - f.ny) * f.NX + I;
+}
+__host__ __device__ __forceinline__ void frame_ij(const FrameDev& f, int64_t c, int& I, int& J) {
+    const int64_t bot = (int64_t)f.W * f.NX, mid = (int64_t)2 * f.W * f.ny;
+    if (c < bot) {
+        J = (int)(c / f.NX);
+        I = (int)(c % f.NX);
+    } else if (c < bot + mid) {
+        const int64_t r = c - bot;
+        J = f.W + (int)(r / (2 * f.W));
+        const int q = (int)(r % (2 * f.W));
+        I = q < f.W ? q : f.nx + q;
+    } else {
+        const int64_t r = c - bot - mid;
+        J = f.W + f.ny + (int)(r / f.NX);
+        I = (int)(r % f.NX);
+    }
+}
+
+// Everything the step kernels need, in the stored numbering.// Everything the step kernels need, in the stored numbering.
 struct DevMesh {
     int precision = 0;            // UE_PREC_*
     int64_t n_t = 0, n_ei = 0, n_nodes = 0;
@@ -111,6 +162,7 @@ struct DevMesh {
     int gtab_size = 0;
     long long* step = nullptr;    // device step counter (source time)
     double dt = 0;
+    const FrameDev* frame = nullptr;   // PML frame stepped with the plain kernels, or none
 };
 
 // Device side of the temporal-blocking tiles (kernels_tb.cu, tiles_host.cpp).
@@ -164,10 +216,13 @@ cudaError_t launch_geom_edge(const double* xy, const int32_t* edge_nodes, const 
 cudaError_t launch_coeff(const DevMesh& m, const double* elen, const double* d, const double* S,
                          const int32_t* tri_code, double dt, cudaStream_t s);
 // FP64 power iteration on K = -L_E L_B in the S metric; returns rho in *rho (synchronous).
+// With a frame, the iterate covers the triangles and the frame cells (start vector keyed by
+// n_t + frame cell), and K is the operator of the coupled system.
 cudaError_t power_iteration(const int2* rl, const int4* tri, const double* elen, const double* d,
                             const double* S, const int64_t* perm_tri, int64_t n_t, int64_t n_ei,
-                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s);
-size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei);
+                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s,
+                            const FrameDev* frame = nullptr);
+size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei, const FrameDev* frame = nullptr);
 cudaError_t launch_fields_in(const DevMesh& m, const double* E_caller, const double* B_caller,
                              const double* J_caller, const int64_t* edge_caller,
                              const int64_t* perm_tri, const double* elen, cudaStream_t s);
@@ -240,6 +295,21 @@ cudaError_t launch_scatter_geometry(const double* O, const double* S, const doub
                                     const int64_t* edge_caller, int64_t n_t, int64_t n_ei,
                                     int64_t n_e, double* O_c, double* S_c, double* elen_c,
                                     double* d_c, cudaStream_t s);
+
+// PML frame (kernels_frame.cu).  Interface geometry: d_k = (O_tri - C_e) . n_in + h/2 from the
+// triangles' circumcentres O (stored order), icU = dt |e| / d rounded to the field type, ic =
+// |e| / d (the host checks d > 0 through ic).  iface: 6 doubles per interface edge
+// {x_a, y_a, x_b, y_b, n_in x, n_in y}.
+cudaError_t launch_frame_geom(const FrameDev& f, const double* O, const double* iface, double dt,
+                              bool f64, cudaStream_t s);
+// Fields: interface E out to / in from caller edges (iedge: caller id per interface edge,
+// ielen: |e|), frame B and E out (caller layout of ue_frame_fields).
+cudaError_t launch_frame_iface_out(const FrameDev& f, const DevMesh& m, const int64_t* iedge,
+                                   const double* ielen, double* E_caller, cudaStream_t s);
+cudaError_t launch_frame_iface_in(const FrameDev& f, const DevMesh& m, const int64_t* iedge,
+                                  const double* ielen, const double* E_caller, cudaStream_t s);
+cudaError_t launch_frame_out(const FrameDev& f, bool f64, double* B, double* Ex, double* Ey,
+                             cudaStream_t s);
 
 // Power iteration with a file-scope work array (noalloc.cu).
 int power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,

@@ -116,10 +116,12 @@ __global__ void k_pi_prep(const double* __restrict__ elen, const double* __restr
 }
 
 // Fixed-order sum of the block partials (x_b, y_b) by the last block of a grid (deterministic
-// whichever block finishes last); sc = {sum x, sum y, 1/sqrt(sum y)}.  counter: zero before,
-// zero after.
+// whichever block finishes last); sc = {sum x, sum y, 1/sqrt(sum y)}.  The sum covers this
+// grid's partials and `extra` more after them, written by an earlier launch (a frame's cells).
+// counter: zero before, zero after.
 __device__ void pi_last_block(const double* __restrict__ part, double* __restrict__ sc,
-                              unsigned int* __restrict__ counter, double* s_a, double* s_b) {
+                              unsigned int* __restrict__ counter, double* s_a, double* s_b,
+                              int64_t extra) {
     __shared__ int last;
     if (threadIdx.x == 0) {
         __threadfence();
@@ -129,7 +131,7 @@ __device__ void pi_last_block(const double* __restrict__ part, double* __restric
     if (!last) return;
     __threadfence();
     double x = 0.0, y = 0.0;
-    for (int64_t i = threadIdx.x; i < gridDim.x; i += kThreads) {
+    for (int64_t i = threadIdx.x; i < (int64_t)gridDim.x + extra; i += kThreads) {
         x += __ldcg(part + 2 * i);
         y += __ldcg(part + 2 * i + 1);
     }
@@ -151,9 +153,10 @@ __device__ void pi_last_block(const double* __restrict__ part, double* __restric
     }
 }
 
-// Block tree of (x, y) into part[2 * block], then the last block's fixed-order total.
+// Block tree of (x, y) into part[2 * block]; then, unless sc is NULL, the last block's
+// fixed-order total.
 __device__ void pi_block_sums(double x, double y, double* __restrict__ part, double* __restrict__ sc,
-                              unsigned int* __restrict__ counter) {
+                              unsigned int* __restrict__ counter, int64_t extra = 0) {
     __shared__ double s_a[kThreads], s_b[kThreads];
     s_a[threadIdx.x] = x;
     s_b[threadIdx.x] = y;
@@ -169,15 +172,16 @@ __device__ void pi_block_sums(double x, double y, double* __restrict__ part, dou
         part[2 * blockIdx.x] = s_a[0];
         part[2 * blockIdx.x + 1] = s_b[0];
     }
+    if (!sc) return;
     __syncthreads();
-    pi_last_block(part, sc, counter, s_a, s_b);
+    pi_last_block(part, sc, counter, s_a, s_b, extra);
 }
 
 // Start: w = SplitMix64 vector, sc = {0, S-norm^2 of w, 1/S-norm of w}.
 __global__ void k_pi_start(double* __restrict__ w, const int64_t* __restrict__ perm,
                            const double* __restrict__ S, uint32_t seed, int64_t n_t,
                            double* __restrict__ part, double* __restrict__ sc,
-                           unsigned int* __restrict__ counter) {
+                           unsigned int* __restrict__ counter, int64_t extra) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double ww = 0.0;
     if (j < n_t) {
@@ -186,7 +190,7 @@ __global__ void k_pi_start(double* __restrict__ w, const int64_t* __restrict__ p
         w[j] = x;
         ww = S[j] * x * x;
     }
-    pi_block_sums(0.0, ww, part, sc, counter);
+    pi_block_sums(0.0, ww, part, sc, counter, extra);
 }
 
 // g_k = c_k (v_R - v_L) with v = w * sc[2], the S-normalised iterate.
@@ -206,7 +210,7 @@ __global__ void k_pi_tri(const int4* __restrict__ tri, const double* __restrict_
                          const double* __restrict__ g, const double* __restrict__ w,
                          const double* __restrict__ sc, double* __restrict__ wn,
                          double* __restrict__ part, double* __restrict__ sc_next,
-                         unsigned int* __restrict__ counter, int64_t n_t) {
+                         unsigned int* __restrict__ counter, int64_t n_t, int64_t extra) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double vw = 0.0, ww = 0.0;
     if (j < n_t) {
@@ -221,7 +225,74 @@ __global__ void k_pi_tri(const int4* __restrict__ tri, const double* __restrict_
         vw = (w[j] * sc[2]) * t;
         ww = x * t;
     }
-    pi_block_sums(vw, ww, part, sc_next, counter);
+    pi_block_sums(vw, ww, part, sc_next, counter, extra);
+}
+
+// Frame cells of the coupled system (see kernels_frame.cu for the layout): the iterate's
+// entries n_t + c, S = h^2, start vector keyed by n_t + c; partials go after the triangles'.
+__global__ void k_fpi_start(FrameDev f, double* __restrict__ w, uint32_t seed, int64_t n_t,
+                            double* __restrict__ part) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double ww = 0.0;
+    if (c < f.n_fc) {
+        const uint64_t z = splitmix64(((uint64_t)seed << 32) + (uint64_t)(n_t + c));
+        const double x = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+        w[n_t + c] = x;
+        ww = f.h * f.h * x * x;
+    }
+    pi_block_sums(0.0, ww, part, nullptr, nullptr);
+}
+
+// g on frame sides (|e| / d = 1: g = v_R - v_L) and on interface edges (ic (v_R - v_L)).
+__global__ void k_fpi_edge(FrameDev f, const double* __restrict__ w, const double* __restrict__ sc,
+                           int64_t n_t, double* __restrict__ g, double* __restrict__ gH,
+                           double* __restrict__ gV) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double inv = sc[2];
+    if (t < f.n_fc) {
+        int I, J;
+        frame_ij(f, t, I, J);
+        const double vc = w[n_t + t] * inv;
+        if (frame_is_cell(f, I, J - 1))
+            gH[(int64_t)J * f.NX + I] = vc - w[n_t + frame_cell(f, I, J - 1)] * inv;
+        if (frame_is_cell(f, I - 1, J))
+            gV[(int64_t)J * (f.NX + 1) + I] = w[n_t + frame_cell(f, I - 1, J)] * inv - vc;
+    } else if (t < f.n_fc + f.n_if) {
+        const int64_t k = t - f.n_fc;
+        const int32_t code = f.itri[k];
+        const double vt = w[code >= 0 ? code : ~code] * inv, vc = w[n_t + f.icell[k]] * inv;
+        g[f.u_off + k] = f.ic[k] * (code >= 0 ? vt - vc : vc - vt);
+    }
+}
+
+// t_c = counter-clockwise signed sum of g over the cell's sides, wn = t_c / h^2; block
+// partials of v t_c and wn t_c after the triangles' (no total here).
+__global__ void k_fpi_cell(FrameDev f, const double* __restrict__ g, const double* __restrict__ gH,
+                           const double* __restrict__ gV, const double* __restrict__ w,
+                           const double* __restrict__ sc, double* __restrict__ wn, int64_t n_t,
+                           double* __restrict__ part) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double vw = 0.0, ww = 0.0;
+    if (c < f.n_fc) {
+        int I, J;
+        frame_ij(f, c, I, J);
+        const bool in_x = I >= f.W && I < f.W + f.nx, in_y = J >= f.W && J < f.W + f.ny;
+        auto iface = [&](int64_t k) { return f.itri[k] >= 0 ? -g[f.u_off + k] : g[f.u_off + k]; };
+        double t = 0.0;
+        if (frame_is_cell(f, I, J - 1)) t += gH[(int64_t)J * f.NX + I];
+        else if (in_x && J == f.W + f.ny) t += iface(f.nx + (I - f.W));
+        if (frame_is_cell(f, I, J + 1)) t -= gH[(int64_t)(J + 1) * f.NX + I];
+        else if (in_x && J == f.W - 1) t += iface(I - f.W);
+        if (frame_is_cell(f, I - 1, J)) t -= gV[(int64_t)J * (f.NX + 1) + I];
+        else if (in_y && I == f.W + f.nx) t += iface(2 * (int64_t)f.nx + f.ny + (J - f.W));
+        if (frame_is_cell(f, I + 1, J)) t += gV[(int64_t)J * (f.NX + 1) + I + 1];
+        else if (in_y && I == f.W - 1) t += iface(2 * (int64_t)f.nx + (J - f.W));
+        const double x = t / (f.h * f.h);
+        wn[n_t + c] = x;
+        vw = (w[n_t + c] * sc[2]) * t;
+        ww = x * t;
+    }
+    pi_block_sums(vw, ww, part, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -458,34 +529,54 @@ cudaError_t launch_source_flags(const DevMesh& m, const int32_t* k, int64_t n, b
     return cudaGetLastError();
 }
 
-size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei) {
+size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei, const FrameDev* f) {
     const int64_t nb = (n_t + kThreads - 1) / kThreads;
-    return (size_t)(3 * n_t + 2 * n_ei + 1 + 2 * nb + 8 + 2);
+    if (!f) return (size_t)(3 * n_t + 2 * n_ei + 1 + 2 * nb + 8 + 2);
+    const int64_t nc = n_t + f->n_fc, nbf = (f->n_fc + kThreads - 1) / kThreads;
+    const int64_t ng = f->u_off + f->n_if;
+    const int64_t nh = (int64_t)f->NX * (f->NY + 1), nv = (int64_t)(f->NX + 1) * f->NY;
+    return (size_t)(2 * nc + n_t + ng + n_ei + nh + nv + 2 * (nb + nbf) + 8 + 2);
 }
 
 // Two launches per iteration (edge, triangle with the reductions in its last block); the
-// iterate is normalised on the fly by the scale its previous reduction left.
+// iterate is normalised on the fly by the scale its previous reduction left.  A frame adds
+// its side and cell launches before them, its cells' partials summed by the triangles' last
+// block after their own.
 cudaError_t power_iteration(const int2* rl, const int4* tri, const double* elen, const double* d,
                             const double* S, const int64_t* perm_tri, int64_t n_t, int64_t n_ei,
-                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s) {
+                            int iters, uint32_t seed, double* work, double* rho, cudaStream_t s,
+                            const FrameDev* f) {
     const int64_t nb = (n_t + kThreads - 1) / kThreads;
-    double* w[2] = {work, work + n_t};
-    double* invS = work + 2 * n_t;
+    const int64_t nbf = f ? (f->n_fc + kThreads - 1) / kThreads : 0;
+    const int64_t nc = n_t + (f ? f->n_fc : 0);
+    const int64_t ng = f ? f->u_off + f->n_if : n_ei + 1;
+    const int64_t nh = f ? (int64_t)f->NX * (f->NY + 1) : 0, nv = f ? (int64_t)(f->NX + 1) * f->NY : 0;
+    double* w[2] = {work, work + nc};
+    double* invS = work + 2 * nc;
     double* g = invS + n_t;
-    double* c = g + (n_ei + 1);
-    double* part = c + n_ei;
-    double* sc[2] = {part + 2 * nb, part + 2 * nb + 4};
-    unsigned int* counter = reinterpret_cast<unsigned int*>(part + 2 * nb + 8);
+    double* c = g + ng;
+    double* gH = c + n_ei;
+    double* gV = gH + nh;
+    double* part = gV + nv;
+    double* sc[2] = {part + 2 * (nb + nbf), part + 2 * (nb + nbf) + 4};
+    unsigned int* counter = reinterpret_cast<unsigned int*>(part + 2 * (nb + nbf) + 8);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(g, 0, sizeof(double) * (n_ei + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(g, 0, sizeof(double) * ng, s)) != cudaSuccess) return e;
+    if (f && (e = cudaMemsetAsync(gH, 0, sizeof(double) * (nh + nv), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(counter, 0, sizeof(double), s)) != cudaSuccess) return e;
     k_pi_prep<<<blocks_for(n_ei > n_t ? n_ei : n_t), kThreads, 0, s>>>(elen, d, S, c, invS, n_ei, n_t);
-    k_pi_start<<<(unsigned)nb, kThreads, 0, s>>>(w[0], perm_tri, S, seed, n_t, part, sc[0], counter);
+    if (f) k_fpi_start<<<(unsigned)nbf, kThreads, 0, s>>>(*f, w[0], seed, n_t, part + 2 * nb);
+    k_pi_start<<<(unsigned)nb, kThreads, 0, s>>>(w[0], perm_tri, S, seed, n_t, part, sc[0], counter, nbf);
     for (int it = 0; it < iters; ++it) {
         const int cur = it & 1;
         if (n_ei > 0) k_pi_edge<<<blocks_for(n_ei), kThreads, 0, s>>>(rl, c, w[cur], sc[cur], g, n_ei);
+        if (f) {
+            k_fpi_edge<<<blocks_for(f->n_fc + f->n_if), kThreads, 0, s>>>(*f, w[cur], sc[cur], n_t, g, gH, gV);
+            k_fpi_cell<<<(unsigned)nbf, kThreads, 0, s>>>(*f, g, gH, gV, w[cur], sc[cur], w[cur ^ 1], n_t,
+                                                         part + 2 * nb);
+        }
         k_pi_tri<<<(unsigned)nb, kThreads, 0, s>>>(tri, invS, g, w[cur], sc[cur], w[cur ^ 1], part,
-                                                  sc[cur ^ 1], counter, n_t);
+                                                  sc[cur ^ 1], counter, n_t, nbf);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double h[2];

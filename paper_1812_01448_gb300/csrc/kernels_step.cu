@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "frame.cuh"
 
 namespace ue {
 
@@ -90,11 +91,19 @@ __device__ __forceinline__ T source_term(const SrcArgs<T>& src, int k, T u) {
     return rn_fma(__ldg(src.c + e.y), (T)g, u);
 }
 
-template <typename T, bool PLASMA, bool SRC>
+// FRAME: blocks from nb_mesh on run a PML frame's sides and interface edges (frame.cuh); they
+// write only the frame's arrays and the interface slots, which no mesh thread touches.
+template <typename T, bool PLASMA, bool SRC, bool FRAME>
 __global__ void __launch_bounds__(kThreads)
 k_edge_half(const int4* __restrict__ rl4, const T* __restrict__ cU, const T* __restrict__ B,
             T* __restrict__ U, const T* __restrict__ pb, T* __restrict__ J, T pa, T mdt,
-            int64_t n_vec, SrcArgs<T> src) {
+            int64_t n_vec, SrcArgs<T> src, FrameDev f, int64_t nb_mesh) {
+    if constexpr (FRAME) {
+        if ((int64_t)blockIdx.x >= nb_mesh) {
+            frame_edge_thread<T>(f, B, U, ((int64_t)blockIdx.x - nb_mesh) * kThreads + threadIdx.x);
+            return;
+        }
+    }
     const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (v >= n_vec) return;
     const int4 ra = __ldg(rl4 + 2 * v), rb = __ldg(rl4 + 2 * v + 1);
@@ -132,10 +141,18 @@ __device__ __forceinline__ T signed_load(const T* __restrict__ U, int code) {
     return (code & 1) ? -u : u;
 }
 
-template <typename T>
+// FRAME: blocks from nb_mesh on update a PML frame's cells (frame.cuh).
+template <typename T, bool FRAME>
 __global__ void __launch_bounds__(kThreads)
 k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
-           const T* __restrict__ U, T* __restrict__ B, int64_t n_vec, long long* __restrict__ step) {
+           const T* __restrict__ U, T* __restrict__ B, int64_t n_vec, long long* __restrict__ step,
+           FrameDev f, int64_t nb_mesh) {
+    if constexpr (FRAME) {
+        if ((int64_t)blockIdx.x >= nb_mesh) {
+            frame_cell_thread<T>(f, U, ((int64_t)blockIdx.x - nb_mesh) * kThreads + threadIdx.x);
+            return;
+        }
+    }
     const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (v == 0) *step += 1;
     if (v >= n_vec) return;
@@ -174,21 +191,42 @@ void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
     SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.src_grp, m.gtab,
                    m.gtab_size, s_index};
     const T pa = PLASMA ? (T)m.pa : (T)0, mdt = PLASMA ? (T)(-m.dt) : (T)0;
-    if (m.n_src > 0)
-        k_edge_half<T, PLASMA, true><<<blocks_for(n_vec), kThreads, 0, s>>>(
-            (const int4*)m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J,
-            pa, mdt, n_vec, src);
-    else
-        k_edge_half<T, PLASMA, false><<<blocks_for(n_vec), kThreads, 0, s>>>(
-            (const int4*)m.rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J,
-            pa, mdt, n_vec, src);
+    const int64_t nb = blocks_for(n_vec);
+    // a frame (never with plasma) adds its blocks to the same launch
+    const FrameDev f = (!PLASMA && m.frame) ? *m.frame : FrameDev();
+    const int64_t nbf = (!PLASMA && m.frame) ? blocks_for(f.n_fc + f.n_if) : 0;
+    const unsigned grid = (unsigned)(nb + nbf);
+    const int4* rl = (const int4*)m.rl;
+    if (nbf > 0) {
+        if constexpr (!PLASMA) {
+            if (m.n_src > 0)
+                k_edge_half<T, false, true, true><<<grid, kThreads, 0, s>>>(
+                    rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+            else
+                k_edge_half<T, false, false, true><<<grid, kThreads, 0, s>>>(
+                    rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+        }
+    } else if (m.n_src > 0) {
+        k_edge_half<T, PLASMA, true, false><<<grid, kThreads, 0, s>>>(
+            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+    } else {
+        k_edge_half<T, PLASMA, false, false><<<grid, kThreads, 0, s>>>(
+            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+    }
 }
 
 template <typename T>
 void tri_half_t(const DevMesh& m, cudaStream_t s) {
     const int64_t n_vec = m.n_t_pad / 4;
-    k_tri_half<T><<<blocks_for(n_vec), kThreads, 0, s>>>(m.tri, (const double*)m.cB,
-                                                         (const T*)m.U, (T*)m.B, n_vec, m.step);
+    const int64_t nb = blocks_for(n_vec);
+    if (m.frame) {
+        const int64_t nbf = blocks_for(m.frame->n_fc);
+        k_tri_half<T, true><<<(unsigned)(nb + nbf), kThreads, 0, s>>>(
+            m.tri, (const double*)m.cB, (const T*)m.U, (T*)m.B, n_vec, m.step, *m.frame, nb);
+    } else {
+        k_tri_half<T, false><<<(unsigned)nb, kThreads, 0, s>>>(m.tri, (const double*)m.cB, (const T*)m.U,
+                                                              (T*)m.B, n_vec, m.step, FrameDev(), nb);
+    }
 }
 
 }  // namespace

@@ -28,6 +28,21 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+// PML frame attached by ue_frame_attach (host side; the kernels are in kernels_frame.cu).
+// Interface edge k: the mesh's outer edges, bottom side first (k = 0 .. nx-1 by x), then top,
+// left (by y), right.
+struct FrameHost {
+    int W = 0, order = 3, nx = 0, ny = 0;
+    double sigma_max = 0, h = 0, X0 = 0, X1 = 0, Y0 = 0, Y1 = 0;
+    std::vector<int32_t> itri;    // stored triangle, or ~t when the triangle is L of the edge
+    std::vector<int32_t> icell;   // frame cell across the edge (strip order)
+    std::vector<int64_t> islot;   // 3 * stored triangle + q of the triangle's code for the edge
+    std::vector<int32_t> ineg;    // that code's sign bit
+    std::vector<int64_t> iedge;   // caller edge id
+    std::vector<double> ielen;    // |e|
+    std::vector<double> iface;    // 6 per edge: x_a, y_a, x_b, y_b, inward normal
+};
+
 }  // namespace
 
 struct ue_mesh {
@@ -101,6 +116,13 @@ struct ue_mesh {
     long long p_budget = 0;
     int p_skip = -1;
     int p_grid = 0;
+
+    // PML frame
+    FrameHost fr;
+    ue::FrameDev fd;
+    int64_t* d_iedge = nullptr;
+    double* d_ielen = nullptr;
+    double* d_iface = nullptr;
 };
 
 namespace {
@@ -529,9 +551,11 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
     dm.n_nodes = nn;
     dm.n_ei_pad = (nei + 4) / 4 * 4;
     dm.n_t_pad = (nt + 3) / 4 * 4;
+    // a frame's interface edges keep their circulation after the zero slot
+    const int64_t n_if = m->fr.W > 0 ? (int64_t)m->fr.itri.size() : 0;
     ok = ok && alloc_into(m, dm.tri, dm.n_t_pad, 16, s) && alloc_into(m, dm.cU, dm.n_ei_pad, esz, s) &&
-         alloc_into(m, dm.U, dm.n_ei_pad, esz, s) && alloc_into(m, dm.B, dm.n_t_pad, esz, s) &&
-         alloc_into(m, dm.step, 1, 8, s);
+         alloc_into(m, dm.U, dm.n_ei_pad + (n_if + 3) / 4 * 4, esz, s) &&
+         alloc_into(m, dm.B, dm.n_t_pad, esz, s) && alloc_into(m, dm.step, 1, 8, s);
     if (ok && m->precision == UE_PREC_FP64) ok = alloc_into(m, dm.cB, dm.n_t_pad, 8, s);
     {
         int g = 64;
@@ -558,7 +582,16 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemsetAsync(dm.cU, 0, esz * dm.n_ei_pad, s));
     UE_CUDA(cudaMemcpyAsync(m->d_xy, h.xy.data(), 16 * nn, cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(m->d_tri_nodes, h.tri_nodes.data(), 12 * nt, cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    if (n_if > 0) {
+        // the triangles' codes of the outer edges point at the interface slots
+        std::vector<int32_t> code(h.tri_code);
+        for (int64_t k = 0; k < n_if; ++k)
+            code[m->fr.islot[k]] = (int32_t)(2 * (dm.n_ei_pad + k) + m->fr.ineg[k]);
+        UE_CUDA(cudaMemcpyAsync(m->d_tri_code, code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+    } else {
+        UE_CUDA(cudaMemcpyAsync(m->d_tri_code, h.tri_code.data(), 12 * nt, cudaMemcpyHostToDevice, s));
+    }
     UE_CUDA(cudaMemcpyAsync(m->d_perm, h.perm_tri.data(), 8 * nt, cudaMemcpyHostToDevice, s));
     if (nei > 0) {
         UE_CUDA(cudaMemcpyAsync(m->d_edge_nodes, h.edge_nodes.data(), 8 * nei, cudaMemcpyHostToDevice, s));
@@ -631,6 +664,78 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
     return UE_OK;
 }
 
+// Frame device arrays: layout, interface tables, zeroed fields (after alloc_and_upload).
+int setup_frame(ue_mesh* m, cudaStream_t s) {
+    const FrameHost& fr = m->fr;
+    ue::FrameDev& f = m->fd;
+    f = ue::FrameDev();
+    const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+    f.W = fr.W;
+    f.nx = fr.nx;
+    f.ny = fr.ny;
+    f.NX = fr.nx + 2 * fr.W;
+    f.NY = fr.ny + 2 * fr.W;
+    f.n_fc = 2 * (int64_t)fr.W * f.NX + 2 * (int64_t)fr.W * fr.ny;
+    f.n_if = (int64_t)fr.itri.size();
+    f.u_off = m->dm.n_ei_pad;
+    f.h = fr.h;
+    const int64_t nh = (int64_t)f.NX * (f.NY + 1), nv = (int64_t)(f.NX + 1) * f.NY;
+    const int64_t ntab = 2 * (f.NY + 1) + 2 * (f.NX + 1) + 2 * f.NX + 2 * f.NY;
+    const bool ok = alloc_into(m, f.H, nh, esz, s) && alloc_into(m, f.V, nv, esz, s) &&
+                    alloc_into(m, f.Bx, f.n_fc, esz, s) && alloc_into(m, f.By, f.n_fc, esz, s) &&
+                    alloc_into(m, f.itri, f.n_if, 4, s) && alloc_into(m, f.icell, f.n_if, 4, s) &&
+                    alloc_into(m, f.icU, f.n_if, esz, s) && alloc_into(m, f.ic, f.n_if, 8, s) &&
+                    alloc_into(m, f.tab, ntab, esz, s) && alloc_into(m, m->d_iedge, f.n_if, 8, s) &&
+                    alloc_into(m, m->d_ielen, f.n_if, 8, s) && alloc_into(m, m->d_iface, 6 * f.n_if, 8, s);
+    if (!ok) return fail(UE_ERR_ALLOC, "frame arrays");
+    UE_CUDA(cudaMemcpyAsync(f.itri, fr.itri.data(), 4 * f.n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(f.icell, fr.icell.data(), 4 * f.n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_iedge, fr.iedge.data(), 8 * f.n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_ielen, fr.ielen.data(), 8 * f.n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(m->d_iface, fr.iface.data(), 48 * f.n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemsetAsync(f.H, 0, esz * nh, s));
+    UE_CUDA(cudaMemsetAsync(f.V, 0, esz * nv, s));
+    UE_CUDA(cudaMemsetAsync(f.Bx, 0, esz * f.n_fc, s));
+    UE_CUDA(cudaMemsetAsync(f.By, 0, esz * f.n_fc, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    m->dm.frame = &m->fd;
+    return UE_OK;
+}
+
+// Decay tables of the frame for time step dt (FP64, rounded once to the field type):
+// a = (1 - sigma dt/2)/(1 + sigma dt/2); b = dt/(1 + sigma dt/2) on sides, (dt/h^2)/(...) on
+// cells; sigma(delta) = sigma_max (delta / (W h))^order at each field's position.
+int frame_tables(ue_mesh* m, double dt, cudaStream_t s) {
+    const FrameHost& fr = m->fr;
+    const ue::FrameDev& f = m->fd;
+    const double h = fr.h;
+    auto sig = [&](double delta) { return fr.sigma_max * std::pow(delta / (fr.W * h), fr.order); };
+    auto dx = [&](double x) { return std::max(0.0, std::max(fr.X0 - x, x - fr.X1)); };
+    auto dy = [&](double y) { return std::max(0.0, std::max(fr.Y0 - y, y - fr.Y1)); };
+    std::vector<double> t;
+    std::vector<double> aH(f.NY + 1), bH(f.NY + 1), aV(f.NX + 1), bV(f.NX + 1), axc(f.NX), bxc(f.NX),
+        ayc(f.NY), byc(f.NY);
+    auto ab = [&](double sg, double b0, double& a, double& b) {
+        a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
+        b = b0 / (1.0 + 0.5 * sg * dt);
+    };
+    for (int J = 0; J <= f.NY; ++J) ab(sig(dy(fr.Y0 + (J - fr.W) * h)), dt, aH[J], bH[J]);
+    for (int I = 0; I <= f.NX; ++I) ab(sig(dx(fr.X0 + (I - fr.W) * h)), dt, aV[I], bV[I]);
+    for (int I = 0; I < f.NX; ++I) ab(sig(dx(fr.X0 + (I - fr.W + 0.5) * h)), dt / (h * h), axc[I], bxc[I]);
+    for (int J = 0; J < f.NY; ++J) ab(sig(dy(fr.Y0 + (J - fr.W + 0.5) * h)), dt / (h * h), ayc[J], byc[J]);
+    for (auto* v : {&aH, &bH, &aV, &bV, &axc, &bxc, &ayc, &byc}) t.insert(t.end(), v->begin(), v->end());
+    if (m->precision == UE_PREC_FP64) {
+        UE_CUDA(cudaMemcpyAsync(f.tab, t.data(), 8 * t.size(), cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::vector<float> tf(t.begin(), t.end());
+        UE_CUDA(cudaMemcpyAsync(f.tab, tf.data(), 4 * tf.size(), cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+    }
+    UE_CUDA(ue::launch_frame_geom(f, m->d_O, m->d_iface, dt, m->precision == UE_PREC_FP64, s));
+    return UE_OK;
+}
+
 int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
     ue_options d;
@@ -657,6 +762,14 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         if (o.tb_threads != 0 && o.tb_threads != 512 && o.tb_threads != 1024)
             return fail(UE_ERR_ARG, "tb_threads must be 0, 512 or 1024");
     }
+    const bool framed = m->fr.W > 0;
+    if (framed) {
+        if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN)
+            return fail(UE_ERR_ARG, "a framed mesh steps with the plain variant only");
+        if (o.dt_mode == UE_DT_LEARNED)
+            return fail(UE_ERR_ARG, "a framed mesh takes its dt from UE_DT_GIVEN or UE_DT_POWER");
+        if (!m->plasma_n.empty()) return fail(UE_ERR_ARG, "plasma media with a frame are not supported");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
     // a rebuild starts from scratch
@@ -667,6 +780,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->built = false;
     m->dm = DevMesh();
     m->tb = ue::TBDev();
+    m->fd = ue::FrameDev();
     m->cur = 0;
     m->variant = o.variant == 0 ? UE_VARIANT_PLAIN : o.variant;
     m->block_depth = o.block_depth;
@@ -679,6 +793,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->watchdog_growth = o.watchdog_growth;
     int arc = alloc_and_upload(m, s);
     if (arc != UE_OK) return arc;
+    if (framed && (arc = setup_frame(m, s)) != UE_OK) return arc;
     DevMesh& dm = m->dm;
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
     const int64_t nt = h.n_tris, nei = h.n_ei;
@@ -701,6 +816,18 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
                                              ") has dual length |O_R O_L| <= 0: mesh is not Delaunay");
             }
     }
+    if (framed) {
+        // the mesh's outer edges face the frame cells: their dual lengths must be positive too
+        const int64_t n_if = m->fd.n_if;
+        UE_CUDA(ue::launch_frame_geom(m->fd, m->d_O, m->d_iface, 0.0, m->precision == UE_PREC_FP64, s));
+        std::vector<double> ic(n_if);
+        UE_CUDA(cudaMemcpyAsync(ic.data(), m->fd.ic, 8 * n_if, cudaMemcpyDeviceToHost, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+        for (int64_t k = 0; k < n_if; ++k)
+            if (!(ic[k] > 0.0 && ic[k] < 1e12))
+                return fail(UE_ERR_DUAL, "outer edge " + std::to_string(m->fr.iedge[k]) +
+                                             " has dual length <= 0 to its frame cell");
+    }
     // triangle records first with dt = 0: the power iteration reads only their edge codes
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, 0.0, s));
     // work space of the chosen dt method, allocated before dt_setup_ms starts (the power
@@ -714,7 +841,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         llock.lock();
         if (!(lres = learned_res())) return fail(UE_ERR_ALLOC, "learned dt result buffer");
     } else if (o.dt_mode == UE_DT_POWER) {
-        if (!alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei), 8, s))
+        if (!alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei, framed ? &m->fd : nullptr), 8, s))
             return fail(UE_ERR_ALLOC, "power iteration work space");
     }
     UE_CUDA(cudaStreamSynchronize(s));
@@ -739,11 +866,12 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         }
     }
     if (need_power) {
-        if (!pwork && !alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei), 8, s))
+        if (!pwork && !alloc_into(m, pwork, ue::power_iteration_work_doubles(nt, nei, framed ? &m->fd : nullptr), 8, s))
             return fail(UE_ERR_ALLOC, "power iteration work space");
         double rho = 0;
         UE_CUDA(ue::power_iteration(m->d_rl, dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei,
-                                    o.power_iters, o.power_seed, pwork, &rho, s));
+                                    o.power_iters, o.power_seed, pwork, &rho, s,
+                                    framed ? &m->fd : nullptr));
         if (!(rho > 0) || !std::isfinite(rho)) return fail(UE_ERR_DUAL, "power iteration gave rho <= 0");
         m->rho = rho;
         m->rho_source = o.dt_mode == UE_DT_LEARNED ? UE_RHO_POWER_FALLBACK : UE_RHO_POWER;
@@ -759,7 +887,11 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     if (pwork) dev_release(m, pwork, s);
     dm.dt = m->dt;
     UE_CUDA(ue::launch_coeff(dm, m->d_elen, m->d_d, m->d_S, m->d_tri_code, m->dt, s));
-    UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * dm.n_ei_pad, s));
+    if (framed) {
+        const int frc = frame_tables(m, m->dt, s);
+        if (frc != UE_OK) return frc;
+    }
+    UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * (dm.n_ei_pad + (framed ? (m->fd.n_if + 3) / 4 * 4 : 0)), s));
     UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
     if (m->variant == UE_VARIANT_BLOCKED) {
@@ -801,6 +933,7 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
             (m->block_depth != m0->block_depth || m->tb_threads != m0->tb_threads))
             return fail(UE_ERR_ARG, "all blocked meshes of a batch need the same block_depth and tb_threads");
         if (m->dm.plasma) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
+        if (m->dm.frame) return fail(UE_ERR_ARG, "batches of framed meshes are not supported");
     }
     cudaStream_t s = (cudaStream_t)stream;
     ue_mesh* B = new (std::nothrow) ue_mesh();
@@ -992,6 +1125,7 @@ int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
 int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (m->is_batch) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
+    if (n && m->dm.frame) return fail(UE_ERR_ARG, "plasma media with a frame are not supported");
     if (n && !(nu >= 0)) return fail(UE_ERR_ARG, "collision rate must be >= 0");
     if (n) {
         for (int64_t v = 0; v < m->hm.n_nodes; ++v)
@@ -1040,6 +1174,15 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
     UE_CUDA(ue::launch_fields_in(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
                                  (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
                                  m->d_elen, s));
+    if (m->dm.frame) {
+        const ue::FrameDev& f = m->fd;
+        const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
+        if (E) UE_CUDA(ue::launch_frame_iface_in(f, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+        UE_CUDA(cudaMemsetAsync(f.H, 0, esz * f.NX * (f.NY + 1), s));
+        UE_CUDA(cudaMemsetAsync(f.V, 0, esz * (f.NX + 1) * f.NY, s));
+        UE_CUDA(cudaMemsetAsync(f.Bx, 0, esz * f.n_fc, s));
+        UE_CUDA(cudaMemsetAsync(f.By, 0, esz * f.n_fc, s));
+    }
     {
         const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
         UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
@@ -1139,6 +1282,7 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
                                   (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
                                   m->d_elen, s));
+    if (E && m->dm.frame) UE_CUDA(ue::launch_frame_iface_out(m->fd, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
     if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
     if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
     if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
@@ -1232,6 +1376,143 @@ int ue_get_tiles(const ue_mesh* m, int64_t* n_tiles, int64_t* tile_off) {
     const std::vector<int64_t>& o = m->hm.tile_tri_off;
     *n_tiles = o.size() < 2 ? 0 : (int64_t)o.size() - 1;
     if (tile_off && *n_tiles > 0) std::memcpy(tile_off, o.data(), 8 * o.size());
+    return UE_OK;
+}
+
+int ue_frame_attach(ue_mesh* m, int32_t width, double sigma_max, int32_t order) {
+    if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
+    if (m->is_batch) return fail(UE_ERR_ARG, "a batch cannot take a frame");
+    if (width == 0) {
+        m->fr = FrameHost();
+        return UE_OK;
+    }
+    if (width < 1 || width > 256 || order < 1 || order > 8 || !std::isfinite(sigma_max))
+        return fail(UE_ERR_ARG, "frame: width in [1, 256], order in [1, 8], finite sigma_max");
+    const HostMesh& h = m->hm;
+    if (h.n_nodes < 3 || h.n_tris < 1) return fail(UE_ERR_ARG, "frame: empty mesh");
+    FrameHost fr;
+    fr.W = width;
+    fr.order = order;
+    fr.X0 = fr.X1 = h.xy[0];
+    fr.Y0 = fr.Y1 = h.xy[1];
+    for (int64_t v = 0; v < h.n_nodes; ++v) {
+        fr.X0 = std::min(fr.X0, h.xy[2 * v]);
+        fr.X1 = std::max(fr.X1, h.xy[2 * v]);
+        fr.Y0 = std::min(fr.Y0, h.xy[2 * v + 1]);
+        fr.Y1 = std::max(fr.Y1, h.xy[2 * v + 1]);
+    }
+    const double tol = 1e-9 * std::max(fr.X1 - fr.X0, fr.Y1 - fr.Y0);
+    // the mesh's boundary edges that lie on a side of the bounding box
+    struct BE {
+        int64_t slot;
+        int32_t a, b;
+        double lo;
+    };
+    std::vector<BE> side[4];   // bottom, top, left, right
+    for (int64_t t = 0; t < h.n_tris; ++t)
+        for (int q = 0; q < 3; ++q) {
+            if ((h.tri_code[3 * t + q] >> 1) != h.n_ei) continue;
+            const int32_t a = h.tri_nodes[3 * t + q], b = h.tri_nodes[3 * t + (q + 1) % 3];
+            const double xa = h.xy[2 * a], ya = h.xy[2 * a + 1], xb = h.xy[2 * b], yb = h.xy[2 * b + 1];
+            int sd = -1;
+            if (std::fabs(ya - fr.Y0) <= tol && std::fabs(yb - fr.Y0) <= tol) sd = 0;
+            else if (std::fabs(ya - fr.Y1) <= tol && std::fabs(yb - fr.Y1) <= tol) sd = 1;
+            else if (std::fabs(xa - fr.X0) <= tol && std::fabs(xb - fr.X0) <= tol) sd = 2;
+            else if (std::fabs(xa - fr.X1) <= tol && std::fabs(xb - fr.X1) <= tol) sd = 3;
+            if (sd < 0) continue;
+            side[sd].push_back({3 * t + q, a, b, sd < 2 ? std::min(xa, xb) : std::min(ya, yb)});
+        }
+    fr.nx = (int)side[0].size();
+    fr.ny = (int)side[2].size();
+    if (fr.nx < 1 || fr.ny < 1 || (int)side[1].size() != fr.nx || (int)side[3].size() != fr.ny)
+        return fail(UE_ERR_ARG, "frame: the outer boundary is not an axis-aligned rectangle");
+    fr.h = (fr.X1 - fr.X0) / fr.nx;
+    if (std::fabs((fr.Y1 - fr.Y0) - fr.ny * fr.h) > 1e-6 * fr.h)
+        return fail(UE_ERR_ARG, "frame: the boundary spacing differs between the x and y sides");
+    ue::FrameDev lay;
+    lay.W = fr.W;
+    lay.nx = fr.nx;
+    lay.ny = fr.ny;
+    lay.NX = fr.nx + 2 * fr.W;
+    lay.NY = fr.ny + 2 * fr.W;
+    const double nin[4][2] = {{0, 1}, {0, -1}, {1, 0}, {-1, 0}};
+    for (int sd = 0; sd < 4; ++sd) {
+        std::vector<BE>& v = side[sd];
+        std::sort(v.begin(), v.end(), [](const BE& p, const BE& q) { return p.lo < q.lo; });
+        const double start = sd < 2 ? fr.X0 : fr.Y0;
+        for (size_t i = 0; i < v.size(); ++i) {
+            const BE& e = v[i];
+            const double lo = start + (double)i * fr.h;
+            const double p0 = sd < 2 ? std::min(h.xy[2 * e.a], h.xy[2 * e.b]) : std::min(h.xy[2 * e.a + 1], h.xy[2 * e.b + 1]);
+            const double p1 = sd < 2 ? std::max(h.xy[2 * e.a], h.xy[2 * e.b]) : std::max(h.xy[2 * e.a + 1], h.xy[2 * e.b + 1]);
+            if (std::fabs(p0 - lo) > 1e-6 * fr.h || std::fabs(p1 - (lo + fr.h)) > 1e-6 * fr.h)
+                return fail(UE_ERR_ARG, "frame: the outer boundary nodes are not uniformly spaced");
+            const int t = (int)(e.slot / 3);
+            const bool triR = e.a < e.b;   // the triangle runs the edge low -> high: it is R
+            int I = 0, J = 0;
+            if (sd == 0) { I = fr.W + (int)i; J = fr.W - 1; }
+            else if (sd == 1) { I = fr.W + (int)i; J = fr.W + fr.ny; }
+            else if (sd == 2) { I = fr.W - 1; J = fr.W + (int)i; }
+            else { I = fr.W + fr.nx; J = fr.W + (int)i; }
+            fr.itri.push_back(triR ? t : ~t);
+            fr.icell.push_back((int32_t)ue::frame_cell(lay, I, J));
+            fr.islot.push_back(e.slot);
+            fr.ineg.push_back(triR ? 0 : 1);
+            const int64_t lo_n = std::min(e.a, e.b), hi_n = std::max(e.a, e.b);
+            int64_t lo_i = 0, hi_i = h.n_edges;   // caller edges are sorted (low, high) pairs
+            while (lo_i < hi_i) {
+                const int64_t mid = (lo_i + hi_i) / 2;
+                const int64_t ma = h.edges[2 * mid], mb = h.edges[2 * mid + 1];
+                if (ma < lo_n || (ma == lo_n && mb < hi_n)) lo_i = mid + 1;
+                else hi_i = mid;
+            }
+            fr.iedge.push_back(lo_i);
+            const double ex = h.xy[2 * e.b] - h.xy[2 * e.a], ey = h.xy[2 * e.b + 1] - h.xy[2 * e.a + 1];
+            fr.ielen.push_back(std::sqrt(ex * ex + ey * ey));
+            const double g[6] = {h.xy[2 * e.a], h.xy[2 * e.a + 1], h.xy[2 * e.b], h.xy[2 * e.b + 1],
+                                 nin[sd][0], nin[sd][1]};
+            fr.iface.insert(fr.iface.end(), g, g + 6);
+        }
+    }
+    fr.sigma_max = sigma_max >= 0 ? sigma_max
+                                  : (order + 1) * std::log(1e6) / (2.0 * width * fr.h);
+    m->fr = std::move(fr);
+    return UE_OK;
+}
+
+int ue_frame_get(const ue_mesh* m, int64_t* dims, double* geom) {
+    if (!m || m->fr.W == 0) return fail(UE_ERR_ARG, "no frame");
+    const FrameHost& fr = m->fr;
+    const int64_t NX = fr.nx + 2 * fr.W, NY = fr.ny + 2 * fr.W;
+    if (dims) {
+        const int64_t d[7] = {fr.W, fr.nx, fr.ny, NX, NY, 2 * fr.W * NX + 2 * (int64_t)fr.W * fr.ny,
+                              (int64_t)fr.itri.size()};
+        std::memcpy(dims, d, sizeof(d));
+    }
+    if (geom) {
+        const double g[4] = {fr.h, fr.X0, fr.Y0, fr.sigma_max};
+        std::memcpy(geom, g, sizeof(g));
+    }
+    return UE_OK;
+}
+
+int ue_frame_fields(ue_mesh* m, double* B, double* Ex, double* Ey, void* stream) {
+    if (!m || !m->built || !m->dm.frame) return fail(UE_ERR_ARG, "no frame built");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ue::FrameDev& f = m->fd;
+    const int64_t nh = (int64_t)f.NX * (f.NY + 1), nv = (int64_t)(f.NX + 1) * f.NY;
+    double *tB = nullptr, *tx = nullptr, *ty = nullptr;
+    if ((B && !alloc_into(m, tB, f.n_fc, 8, s)) || (Ex && !alloc_into(m, tx, nh, 8, s)) ||
+        (Ey && !alloc_into(m, ty, nv, 8, s)))
+        return fail(UE_ERR_ALLOC, "frame export buffers");
+    UE_CUDA(ue::launch_frame_out(f, m->precision == UE_PREC_FP64, tB, tx, ty, s));
+    if (B) UE_CUDA(cudaMemcpyAsync(B, tB, 8 * f.n_fc, cudaMemcpyDeviceToHost, s));
+    if (Ex) UE_CUDA(cudaMemcpyAsync(Ex, tx, 8 * nh, cudaMemcpyDeviceToHost, s));
+    if (Ey) UE_CUDA(cudaMemcpyAsync(Ey, ty, 8 * nv, cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    dev_release(m, tB, s);
+    dev_release(m, tx, s);
+    dev_release(m, ty, s);
     return UE_OK;
 }
 

@@ -124,3 +124,39 @@ def test_collinear_and_nonmanifold_rejected(ue):
     with pytest.raises(ue.UEError) as ei:
         ue.Mesh(xy, np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]]))
     assert ei.value.code == -2
+
+
+def test_frame_layout_matches_oracle(ue):
+    from oracle import pml
+    ms = meshgen.graded_square(1 / 16, 1 / 16, grade=0.0,
+                               holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=5)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.frame_attach(6)
+    info = m.frame_info()
+    fo = pml.FramedOperators(om.canonicalize(ms.xy, ms.tris), 6)
+    assert (info["W"], info["nx"], info["ny"], info["NX"], info["NY"]) == (6, fo.nx, fo.ny, fo.NX, fo.NY)
+    assert info["n_cells"] == fo.n_fc and info["n_interface"] == fo.n_if
+    assert abs(info["h"] - fo.h) <= 1e-12 * fo.h
+    assert abs(info["sigma_max"] - fo.sigma_max) <= 1e-12 * fo.sigma_max
+    m.frame_attach(6, sigma_max=0.0)
+    assert m.frame_info()["sigma_max"] == 0.0
+    m.frame_attach(0)
+    with pytest.raises(ue.UEError):
+        m.frame_info()
+    m.close()
+
+
+def test_frame_refuses_a_boundary_that_is_not_a_divided_rectangle(ue):
+    from test_oracle_pml import _not_a_divided_rectangle
+    for xy, tris in _not_a_divided_rectangle():
+        m = ue.Mesh(xy, tris)
+        with pytest.raises(ue.UEError):
+            m.frame_attach(4)
+        m.close()
+    ms = meshgen.cavity_te11_mesh()                     # boundary spacing 1/32 on all sides
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.frame_attach(4)
+    for bad in ((-1, -1.0, 3), (4, -1.0, 0), (4, float("nan"), 3), (300, -1.0, 3)):
+        with pytest.raises(ue.UEError):
+            m.frame_attach(*bad)
+    m.close()

@@ -1,0 +1,158 @@
+"""PML frame on the GPU (ue_frame_attach) against the oracle's framed operators."""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import geometry, mesh as om, pml, spectral
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ue():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01448_gb300 import build
+    build.build()
+    import paper_1812_01448_gb300 as ue
+    return ue
+
+
+def _square(h=1 / 32, seed=5):
+    ms = meshgen.graded_square(h, h, grade=0.0,
+                               holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=seed)
+    return ms, om.canonicalize(ms.xy, ms.tris)
+
+
+def _pulse(m, x0=(0.3, 0.3)):
+    C = m.xy[m.tris].mean(axis=1)
+    r2 = ((C - np.asarray(x0)) ** 2).sum(axis=1)
+    return (C[:, 0] - x0[0]) * np.exp(-r2 / 0.12 ** 2)
+
+
+def _oracle_fields(fo, E, Bs, n_edges):
+    """Oracle state in the library's output layout: (E per caller edge, B per triangle, frame B
+    in strip order, Ex [NY+1, NX], Ey [NY, NX+1])."""
+    Ec = np.zeros(n_edges)
+    Ec[fo.inner.ie] = E[:fo.inner.n_ei]
+    for k, rec in enumerate(fo.iface):
+        Ec[rec[0]] = E[fo.inner.n_ei + k]
+    B = fo.P @ Bs
+    Ex = np.zeros((fo.NY + 1, fo.NX))
+    Ey = np.zeros((fo.NY, fo.NX + 1))
+    for (I, J), row in fo.H.items():
+        Ex[J, I] = E[row]
+    for (I, J), row in fo.V.items():
+        Ey[J, I] = E[row]
+    return Ec, B[:fo.n_in], B[fo.n_in:], Ex, Ey
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_framed_power_iteration_matches_oracle(ue):
+    """The power iteration covers the coupled system (triangles + frame cells, same start
+    vector keyed by caller triangle id and n_t + frame cell)."""
+    ms, m = _square()
+    fo = pml.FramedOperators(m, 8)
+    rho_o, _ = spectral.power_iteration(fo, 200)
+    mesh = ue.Mesh(ms.xy, ms.tris)
+    mesh.frame_attach(8)
+    mesh.geometry_build(precision=ue.UE_PREC_FP64)
+    dt, rho, src = mesh.get_dt()
+    mesh.close()
+    assert abs(rho - rho_o) <= 1e-10 * rho_o
+    # dense check of the coupled operator's top mode (the iteration converged)
+    lam = np.linalg.eigvalsh(spectral.symmetric_K(fo))
+    assert abs(rho - math.sqrt(lam[-1])) <= 1e-3 * rho
+
+
+@pytest.mark.parametrize("precision,nsteps,tol", [(1, 600, 1e-12), (0, 2000, 1e-4)])
+def test_framed_pulse_matches_oracle(ue, precision, nsteps, tol):
+    """A pulse in the holed square, W = 8 layer with the default decay, against the oracle:
+    mesh E (interior and outer edges), mesh B, frame B and frame E."""
+    ms, m = _square()
+    fo = pml.FramedOperators(m, 8)
+    rho_o, _ = spectral.power_iteration(fo, 200)
+    dt = 0.5 * 2 / rho_o
+    b = _pulse(m)
+    E, Bs = np.zeros(fo.n_ei), fo.start_split(np.concatenate([b, np.zeros(fo.n_fc)]))
+    E, Bs = pml.run(fo, E, Bs, dt, nsteps)
+    ref = _oracle_fields(fo, E, Bs, m.n_edges)
+    mesh = ue.Mesh(ms.xy, ms.tris)
+    mesh.frame_attach(8)
+    mesh.geometry_build(precision=precision, dt_mode=ue.UE_DT_GIVEN, dt=dt)
+    mesh.write_fields(B=b)
+    mesh.step_n(nsteps)
+    Eg, Bg, _ = mesh.read_fields()
+    Bf, Ex, Ey = mesh.frame_fields()
+    mesh.close()
+    got = (Eg, Bg, Bf, Ex, Ey)
+    errs = [_rel(g, r) for g, r in zip(got, ref)]
+    print("framed pulse rel L2 (E, B, frame B, Ex, Ey):", ["%.2e" % e for e in errs])
+    assert np.linalg.norm(ref[2]) > 1e-3 * np.linalg.norm(b)      # the pulse reached the frame
+    assert max(errs) <= tol
+
+
+def test_framed_graphs_are_bit_identical_to_plain_launches(ue):
+    ms, m = _square()
+    b = _pulse(m)
+    out = []
+    for gc in (32, -1):
+        mesh = ue.Mesh(ms.xy, ms.tris)
+        mesh.frame_attach(6)
+        mesh.geometry_build(graph_chunk=gc)
+        mesh.write_fields(B=b)
+        mesh.step_n(100)
+        E, B, _ = mesh.read_fields()
+        Bf, Ex, Ey = mesh.frame_fields()
+        out.append((E, B, Bf, Ex, Ey))
+        mesh.close()
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
+
+
+def test_pml_follows_a_large_undamped_frame_until_its_echo(ue):
+    """The oracle's absorption pin, on the GPU in FP32: a 12-cell layer stays within 5e-4 of the
+    same mesh in a 48-cell undamped frame up to t = 2.4."""
+    ms, m = _square()
+    b = _pulse(m)
+    runs = {}
+    dt = None
+    for W, sm in ((48, 0.0), (12, -1.0)):
+        mesh = ue.Mesh(ms.xy, ms.tris)
+        mesh.frame_attach(W, sigma_max=sm)
+        if dt is None:
+            mesh.geometry_build()
+            dt = mesh.get_dt()[0]
+        mesh.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt)
+        mesh.write_fields(B=b)
+        snaps = []
+        n = int(2.4 / dt)
+        for _ in range(4):
+            mesh.step_n(n // 4)
+            snaps.append(mesh.read_fields()[1])
+        runs[W] = snaps
+        mesh.close()
+    S = geometry.areas(m.xy, m.tris)
+    nb = math.sqrt(np.dot(S, b * b))
+    err = max(math.sqrt(np.dot(S, (p - r) ** 2)) / nb for p, r in zip(runs[12], runs[48]))
+    print(f"PML W=12 vs undamped W=48: {err:.2e}")
+    assert err < 5e-4
+
+
+def test_framed_mesh_refuses_other_variants(ue):
+    ms, m = _square(1 / 16)
+    mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)
+    mesh.frame_attach(4)
+    for kw in (dict(variant=ue.UE_VARIANT_BLOCKED), dict(variant=ue.UE_VARIANT_PERSISTENT)):
+        with pytest.raises(ue.UEError):
+            mesh.geometry_build(**kw)
+    mesh.geometry_build()
+    with pytest.raises(ue.UEError):
+        mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)
+    mesh.close()
