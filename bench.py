@@ -556,9 +556,17 @@ def run_relax(args):
     ms = meshgen.random_delaunay(args.relax_points, seed=1006)
     iters = max(1, args.steps)
     ue.mesh_relax(ms.xy, ms.tris, max(3, args.warmup), flip_every=0)     # warm-up
+    # per-step time without the call's fixed cost (host lists, allocation, transfers): the
+    # difference between calls of N and N/2 steps (without flips, slivers would collapse over
+    # much longer runs: the model needs its flips)
+    half = max(1, iters // 2)
+    t0 = time.perf_counter()
+    ue.mesh_relax(ms.xy, ms.tris, half, flip_every=0)
+    t_half = time.perf_counter() - t0
     t0 = time.perf_counter()
     ue.mesh_relax(ms.xy, ms.tris, iters, flip_every=0)
-    t_steps = time.perf_counter() - t0
+    t_call = time.perf_counter() - t0
+    t_steps = (t_call - t_half) * iters / max(1, iters - half)
     t0 = time.perf_counter()
     xr, tr, flips = ue.mesh_relax(ms.xy, ms.tris, iters, flip_every=20)
     t_all = time.perf_counter() - t0
@@ -574,7 +582,8 @@ def run_relax(args):
     n_nodes = ms.xy.shape[0]
     line = {
         "metric": "mesh relaxation: node-steps/s", "value": n_nodes * iters / t_steps, "unit": "node-steps/s",
-        "ms_per_step": 1e3 * t_steps / iters, "steps": iters, "n_nodes": n_nodes, "n_tris": int(ms.tris.shape[0]),
+        "ms_per_step": 1e3 * t_steps / iters, "steps": iters, "call_seconds": t_call,
+        "n_nodes": n_nodes, "n_tris": int(ms.tris.shape[0]),
         "with_flips": {"seconds": t_all, "flips": int(flips), "flip_every": 20},
         "rho_before": rho[0], "rho_after": rho[1], "dt_gain": rho[0] / rho[1],
         "dtype": "f64", "data": "synthetic",

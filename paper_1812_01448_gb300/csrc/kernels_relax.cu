@@ -12,8 +12,9 @@
 // height h of its triangles: moves of at most d per vertex change twice a triangle's area by at
 // most 3 d L + 4 d^2 <= 0.54 h L (L its longest edge), less than the h L it has, so no triangle
 // turns over.
-// GPU: one thread per node gathers its edge springs and its shares of the height springs of
-// its triangles (node -> edge and node -> triangle lists), FP64, positions double-buffered.
+// GPU, FP64, positions double-buffered: per step one thread per triangle evaluates its three
+// height springs and its cap once, then one thread per node gathers its edge springs and its
+// triangles' shares (node -> edge and node -> triangle lists).
 // Host: the lists, and the flips (a flip changes the lists).
 #include <cuda_runtime.h>
 
@@ -43,13 +44,56 @@ struct RxLists {
     std::vector<uint8_t> fixed;           // boundary node
 };
 
-__global__ void k_rx_step(const double* __restrict__ x, double* __restrict__ xn,
-                          const int32_t* __restrict__ tris, const int32_t* __restrict__ e_off,
-                          const int32_t* __restrict__ e_nb, const double* __restrict__ e_L0,
-                          const int32_t* __restrict__ t_off, const int32_t* __restrict__ t_tri,
-                          const int32_t* __restrict__ t_loc, const double* __restrict__ H0,
-                          const double* __restrict__ cap, const uint8_t* __restrict__ fixed,
-                          double tau, int64_t n_nodes) {
+// Per triangle, once per step: the three height springs' pulls on its vertices and the cap
+// 0.15 * (2 area / longest edge).  Spring q (apex q over the edge (q+1, q+2)) with
+// g_q = ((|w| - H0) / |w|) w, w = x_q - (x_{q+1} + x_{q+2}) / 2, pulls the apex by -g_q and each
+// end of its edge by g_q / 2, so vertex j takes -g_j + (g_{j+1} + g_{j+2}) / 2.
+// out: 8 doubles per triangle {F_0, F_1, F_2 (x, y each), cap, 0}.
+__global__ void k_rx_tri(const double* __restrict__ x, const int32_t* __restrict__ tris,
+                         const double* __restrict__ H0, double* __restrict__ out, int64_t n_tris) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tris) return;
+    double px[3], py[3];
+    for (int q = 0; q < 3; ++q) {
+        const int32_t n = tris[3 * t + q];
+        px[q] = x[2 * n];
+        py[q] = x[2 * n + 1];
+    }
+    const double a2 = fabs((px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]));
+    double lm = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        const int p = q == 2 ? 0 : q + 1;
+        const double ex = px[p] - px[q], ey = py[p] - py[q];
+        lm = fmax(lm, sqrt(ex * ex + ey * ey));
+    }
+    const double h0 = H0[t];
+    double gx[3], gy[3];
+    for (int q = 0; q < 3; ++q) {
+        const int p = q == 2 ? 0 : q + 1, r = q == 0 ? 2 : q - 1;
+        const double wx = px[q] - 0.5 * (px[p] + px[r]), wy = py[q] - 0.5 * (py[p] + py[r]);
+        const double hm = sqrt(wx * wx + wy * wy);
+        const double sc = (hm - h0) / hm;
+        gx[q] = sc * wx;
+        gy[q] = sc * wy;
+    }
+    double* o = out + 8 * t;
+    for (int j = 0; j < 3; ++j) {
+        const int p = j == 2 ? 0 : j + 1, r = j == 0 ? 2 : j - 1;
+        o[2 * j] = 0.5 * (gx[p] + gx[r]) - gx[j];
+        o[2 * j + 1] = 0.5 * (gy[p] + gy[r]) - gy[j];
+    }
+    o[6] = 0.15 * (a2 / lm);
+    o[7] = 0.0;
+}
+
+// Per node: its edge springs, its shares of its triangles' height springs, the smallest cap;
+// then the capped Euler step (fixed nodes copy through).
+__global__ void k_rx_node(const double* __restrict__ x, double* __restrict__ xn,
+                          const int32_t* __restrict__ e_off, const int32_t* __restrict__ e_nb,
+                          const double* __restrict__ e_L0, const int32_t* __restrict__ t_off,
+                          const int32_t* __restrict__ t_tri, const int32_t* __restrict__ t_loc,
+                          const double* __restrict__ tri_out, const double* __restrict__ cap,
+                          const uint8_t* __restrict__ fixed, double tau, int64_t n_nodes) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_nodes) return;
     const double vx = x[2 * v], vy = x[2 * v + 1];
@@ -68,34 +112,12 @@ __global__ void k_rx_step(const double* __restrict__ x, double* __restrict__ xn,
         fy += s * dy;
     }
     double c = cap[v];
-    for (int32_t i = t_off[v]; i < t_off[v + 1]; ++i) {   // height springs of its triangles
-        const int32_t t = t_tri[i], l = t_loc[i];
-        double px[3], py[3];
-        for (int q = 0; q < 3; ++q) {
-            const int32_t n = tris[3 * t + q];
-            px[q] = x[2 * n];
-            py[q] = x[2 * n + 1];
-        }
-        {   // 0.15 of the triangle's smallest height (2 area / longest edge) caps the step
-            const double a2 = fabs((px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]));
-            double lm = 0.0;
-            for (int q = 0; q < 3; ++q) {
-                const int p = q == 2 ? 0 : q + 1;
-                const double ex = px[p] - px[q], ey = py[p] - py[q];
-                lm = fmax(lm, sqrt(ex * ex + ey * ey));
-            }
-            c = fmin(c, 0.15 * (a2 / lm));
-        }
-        const double h0 = H0[t];
-        for (int q = 0; q < 3; ++q) {   // apex q over the edge (q+1, q+2)
-            const int p = q == 2 ? 0 : q + 1, r = q == 0 ? 2 : q - 1;
-            const double wx = px[q] - 0.5 * (px[p] + px[r]), wy = py[q] - 0.5 * (py[p] + py[r]);
-            const double hm = sqrt(wx * wx + wy * wy);
-            const double s = (hm - h0) / hm;
-            const double w = q == l ? -1.0 : 0.5;   // the apex takes -g, the edge's ends g/2
-            fx += w * s * wx;
-            fy += w * s * wy;
-        }
+    for (int32_t i = t_off[v]; i < t_off[v + 1]; ++i) {   // its triangles' height springs
+        const double* o = tri_out + 8 * (int64_t)t_tri[i];
+        const int l = t_loc[i];
+        fx += o[2 * l];
+        fy += o[2 * l + 1];
+        c = fmin(c, o[6]);
     }
     double dx = tau * fx, dy = tau * fy;
     const double n = sqrt(dx * dx + dy * dy);
@@ -129,22 +151,45 @@ bool in_circle(const std::vector<double>& x, int a, int b, int c, int d) {
 // The stack holds (triangle, a, b) for a directed CCW edge a->b; an entry whose triangle no longer
 // holds that edge is stale and skipped: every flip pushes its four outer edges with their current
 // triangles, so no live edge is lost.
+// node -> incident triangles (CSR by counting), in triangle order
+void node_tris(int64_t nn, const std::vector<int32_t>& t, std::vector<int32_t>& off,
+               std::vector<int32_t>& tri, std::vector<int32_t>* loc) {
+    const int64_t nt = (int64_t)t.size() / 3;
+    off.assign(nn + 1, 0);
+    for (int32_t n : t) ++off[n + 1];
+    for (int64_t v = 0; v < nn; ++v) off[v + 1] += off[v];
+    tri.assign(off[nn], 0);
+    if (loc) loc->assign(off[nn], 0);
+    std::vector<int32_t> p(off.begin(), off.end() - 1);
+    for (int64_t i = 0; i < nt; ++i)
+        for (int q = 0; q < 3; ++q) {
+            const int32_t n = t[3 * i + q];
+            if (loc) (*loc)[p[n]] = q;
+            tri[p[n]++] = (int32_t)i;
+        }
+}
+
 int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
     const int64_t nt = (int64_t)t.size() / 3;
+    const int64_t nn = (int64_t)x.size() / 2;
     std::vector<int64_t> nb(3 * nt, -1);
-    {
-        std::vector<std::pair<uint64_t, int64_t>> de(3 * nt);   // (undirected key, slot)
-        for (int64_t s = 0; s < 3 * nt; ++s) {
-            const int64_t i = s / 3, q = s % 3;
-            const uint32_t a = (uint32_t)t[s], b = (uint32_t)t[3 * i + (q + 1) % 3];
-            de[s] = {((uint64_t)std::min(a, b) << 32) | std::max(a, b), s};
-        }
-        std::sort(de.begin(), de.end());
-        for (size_t k = 0; k + 1 < de.size(); ++k)
-            if (de[k].first == de[k + 1].first) {
-                nb[de[k].second] = de[k + 1].second / 3;
-                nb[de[k + 1].second] = de[k].second / 3;
-                ++k;
+    {   // the twin of a -> b in triangle i is b -> a in one of b's other triangles
+        std::vector<int32_t> off, tri;
+        node_tris(nn, t, off, tri, nullptr);
+        for (int64_t i = 0; i < nt; ++i)
+            for (int q = 0; q < 3; ++q) {
+                if (nb[3 * i + q] >= 0) continue;   // found from the other side
+                const int32_t a = t[3 * i + q], b = t[3 * i + (q + 1) % 3];
+                for (int32_t k = off[b]; k < off[b + 1] && nb[3 * i + q] < 0; ++k) {
+                    const int32_t j = tri[k];
+                    if (j == i) continue;
+                    for (int r = 0; r < 3; ++r)
+                        if (t[3 * j + r] == b && t[3 * j + (r + 1) % 3] == a) {
+                            nb[3 * i + q] = j;
+                            nb[3 * j + r] = i;
+                            break;
+                        }
+                }
             }
     }
     struct Item { int64_t tri; int32_t a, b; };
@@ -196,67 +241,42 @@ int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
 
 void build_lists(int64_t nn, const std::vector<int32_t>& t, const std::vector<double>& h, RxLists& L) {
     const int64_t nt = (int64_t)t.size() / 3;
-    // unique edges (low, high) in increasing order, and the number of triangles of each
-    std::vector<std::pair<int32_t, int32_t>> e;
-    e.reserve(3 * nt);
-    for (int64_t i = 0; i < nt; ++i)
-        for (int q = 0; q < 3; ++q) {
-            const int32_t a = t[3 * i + q], b = t[3 * i + (q + 1) % 3];
-            e.push_back({std::min(a, b), std::max(a, b)});
-        }
-    std::sort(e.begin(), e.end());
-    std::vector<std::pair<int32_t, int32_t>> ue;
-    std::vector<int> cnt;
-    for (size_t k = 0; k < e.size(); ++k) {
-        if (k == 0 || e[k] != e[k - 1]) {
-            ue.push_back(e[k]);
-            cnt.push_back(1);
-        } else {
-            ++cnt.back();
-        }
-    }
-    L.fixed.assign(nn, 0);
-    for (size_t k = 0; k < ue.size(); ++k)
-        if (cnt[k] == 1) L.fixed[ue[k].first] = L.fixed[ue[k].second] = 1;
-    // node -> edges, in increasing edge order
-    std::vector<int32_t> deg(nn, 0);
-    for (const auto& p : ue) {
-        ++deg[p.first];
-        ++deg[p.second];
-    }
-    L.e_off.assign(nn + 1, 0);
-    for (int64_t v = 0; v < nn; ++v) L.e_off[v + 1] = L.e_off[v] + deg[v];
-    L.e_nb.assign(L.e_off[nn], 0);
-    L.e_L0.assign(L.e_off[nn], 0.0);
-    L.cap.assign(nn, INFINITY);
-    std::vector<int32_t> pos(L.e_off.begin(), L.e_off.end() - 1);
-    for (const auto& p : ue) {
-        const double l0 = 0.5 * (h[p.first] + h[p.second]);
-        L.e_nb[pos[p.first]] = p.second;
-        L.e_L0[pos[p.first]++] = l0;
-        L.e_nb[pos[p.second]] = p.first;
-        L.e_L0[pos[p.second]++] = l0;
-        L.cap[p.first] = std::min(L.cap[p.first], 0.1 * l0);
-        L.cap[p.second] = std::min(L.cap[p.second], 0.1 * l0);
-    }
-    // node -> triangles, in triangle order
-    std::vector<int32_t> tdeg(nn, 0);
-    for (int32_t n : t) ++tdeg[n];
-    L.t_off.assign(nn + 1, 0);
-    for (int64_t v = 0; v < nn; ++v) L.t_off[v + 1] = L.t_off[v] + tdeg[v];
-    L.t_tri.assign(L.t_off[nn], 0);
-    L.t_loc.assign(L.t_off[nn], 0);
-    std::vector<int32_t> tp(L.t_off.begin(), L.t_off.end() - 1);
+    // node -> triangles (with the node's local index), in triangle order
+    node_tris(nn, t, L.t_off, L.t_tri, &L.t_loc);
     L.H0.assign(nt, 0.0);
     for (int64_t i = 0; i < nt; ++i) {
         double s = 0.0;
-        for (int q = 0; q < 3; ++q) {
-            const int32_t n = t[3 * i + q];
-            L.t_tri[tp[n]] = (int32_t)i;
-            L.t_loc[tp[n]++] = q;
-            s += 0.5 * (h[n] + h[t[3 * i + (q + 1) % 3]]);
-        }
+        for (int q = 0; q < 3; ++q) s += 0.5 * (h[t[3 * i + q]] + h[t[3 * i + (q + 1) % 3]]);
         L.H0[i] = std::sqrt(3.0) / 2.0 * s / 3.0;
+    }
+    // node -> edges in increasing neighbour order (each triangle names each of its vertices'
+    // two neighbours; an edge named once is on the boundary, its ends fixed)
+    L.fixed.assign(nn, 0);
+    L.e_off.assign(nn + 1, 0);
+    L.e_nb.clear();
+    L.e_L0.clear();
+    L.cap.assign(nn, INFINITY);
+    std::vector<int32_t> nbr;
+    for (int64_t v = 0; v < nn; ++v) {
+        nbr.clear();
+        for (int32_t k = L.t_off[v]; k < L.t_off[v + 1]; ++k) {
+            const int32_t i = L.t_tri[k], q = L.t_loc[k];
+            nbr.push_back(t[3 * i + (q + 1) % 3]);
+            nbr.push_back(t[3 * i + (q + 2) % 3]);
+        }
+        std::sort(nbr.begin(), nbr.end());
+        for (size_t k = 0; k < nbr.size();) {
+            size_t r = k + 1;
+            while (r < nbr.size() && nbr[r] == nbr[k]) ++r;
+            const int32_t b = nbr[k];
+            if (r - k == 1) L.fixed[v] = L.fixed[b] = 1;
+            const double l0 = 0.5 * (h[v] + h[b]);
+            L.e_nb.push_back(b);
+            L.e_L0.push_back(l0);
+            L.cap[v] = std::min(L.cap[v], 0.1 * l0);
+            k = r;
+        }
+        L.e_off[v + 1] = (int32_t)L.e_nb.size();
     }
 }
 
@@ -303,7 +323,8 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
     RxLists L;
     build_lists(nn, t, h, L);
     // device buffers, sized for the lists (their sizes do not change under flips)
-    double *dx0 = nullptr, *dx1 = nullptr, *dL0 = nullptr, *dH0 = nullptr, *dcap = nullptr;
+    double *dx0 = nullptr, *dx1 = nullptr, *dL0 = nullptr, *dH0 = nullptr, *dcap = nullptr,
+           *dtri = nullptr;
     int32_t *dt = nullptr, *deo = nullptr, *den = nullptr, *dto = nullptr, *dtt = nullptr, *dtl = nullptr;
     uint8_t* dfix = nullptr;
     const size_t ne2 = L.e_nb.size(), nt3 = L.t_tri.size();
@@ -323,6 +344,7 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
     ck(cudaMalloc(&dH0, 8 * nt));
     ck(cudaMalloc(&dcap, 8 * nn));
     ck(cudaMalloc(&dfix, nn));
+    ck(cudaMalloc(&dtri, 64 * nt));
     auto upload_lists = [&]() {
         ck(cudaMemcpyAsync(dt, t.data(), 12 * nt, cudaMemcpyHostToDevice, s));
         ck(cudaMemcpyAsync(deo, L.e_off.data(), 4 * (nn + 1), cudaMemcpyHostToDevice, s));
@@ -342,9 +364,11 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
     }
     int64_t flips = 0;
     const unsigned grid = (unsigned)((nn + kRxThreads - 1) / kRxThreads);
+    const unsigned grid_t = (unsigned)((nt + kRxThreads - 1) / kRxThreads);
     for (int32_t it = 0; it < iters && e == cudaSuccess; ++it) {
-        k_rx_step<<<grid, kRxThreads, 0, s>>>(dx0, dx1, dt, deo, den, dL0, dto, dtt, dtl, dH0, dcap,
-                                               dfix, tau, nn);
+        k_rx_tri<<<grid_t, kRxThreads, 0, s>>>(dx0, dt, dH0, dtri, nt);
+        k_rx_node<<<grid, kRxThreads, 0, s>>>(dx0, dx1, deo, den, dL0, dto, dtt, dtl, dtri, dcap, dfix,
+                                               tau, nn);
         ck(cudaGetLastError());
         std::swap(dx0, dx1);
         if (flip_every > 0 && (it + 1) % flip_every == 0 && e == cudaSuccess) {
@@ -364,7 +388,7 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
         ck(cudaStreamSynchronize(s));
     }
     for (void* p : {(void*)dx0, (void*)dx1, (void*)dt, (void*)deo, (void*)den, (void*)dL0, (void*)dto,
-                    (void*)dtt, (void*)dtl, (void*)dH0, (void*)dcap, (void*)dfix})
+                    (void*)dtt, (void*)dtl, (void*)dH0, (void*)dcap, (void*)dfix, (void*)dtri})
         if (p) cudaFree(p);
     if (e != cudaSuccess) {
         err = std::string("mesh relaxation: ") + cudaGetErrorString(e);

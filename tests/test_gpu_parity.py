@@ -185,23 +185,6 @@ def test_non_delaunay_mesh_is_rejected(ue):
     assert ei.value.code == -4
 
 
-@pytest.fixture(scope="module")
-def scatterer_window():
-    """The benchmarked workload (~4M triangles) and the oracle's 200-step window from step 5000
-    (mid-pulse, so that the line source is far from zero)."""
-    ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
-    ops = _oracle(ms)
-    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, 2e-4)
-    w0 = 2 * math.pi * 20
-    rho, _ = spectral.power_iteration(ops, 200)
-    dt = 1.0 / rho
-    src = lf.Source(ids, amp, w0, 0.1, 0.05)
-    st = lf.initial_state(ops)
-    st.n = 5000
-    st = lf.run(ops, st, dt, 200, source=src)
-    return ms, ops, ids, amp, w0, dt, ops.extend(st.E), st.B
-
-
 @pytest.mark.slow
 @pytest.mark.parametrize("variant", ["plain", "blocked"])
 def test_full_size_scatterer_window(ue, scatterer_window, variant):
