@@ -165,8 +165,9 @@ int ue_set_plasma(ue_mesh* m, const double* n_nodes_density, double nu);
 int ue_set_source(ue_mesh* m, const int32_t* edge_ids, const double* amp, int64_t n,
                   double omega0, double t0, double tau);
 
-/* Set E^0 (n_edges values; boundary entries ignored), B^{1/2} (n_tris values) and, in plasma,
- * j^{-1/2} (n_edges values, may be NULL = 0).  Any pointer may be NULL to leave that field. */
+/* Set E^0 (n_edges values; boundary entries ignored, except the outer edges of a framed mesh),
+ * B^{1/2} (n_tris values) and, in plasma, j^{-1/2} (n_edges values, may be NULL = 0).  Any
+ * pointer may be NULL to leave that field.  A PML frame's own fields are zeroed. */
 int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream);
 
 /* Advance n_steps leap-frog steps, asynchronously on `stream`.  Errors of the launches are
@@ -174,8 +175,8 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
 int ue_step_n(ue_mesh* m, int64_t n_steps, void* stream);
 
 /* Copy the fields back in the caller's numbering (synchronous).  E, j: n_edges values (0 on
- * boundary edges); B: n_tris values.  Any pointer may be NULL.  Returns UE_ERR_UNSTABLE (after
- * copying) if the energy watchdog has flagged the run. */
+ * boundary edges, except the outer edges of a framed mesh); B: n_tris values.  Any pointer may
+ * be NULL.  Returns UE_ERR_UNSTABLE (after copying) if the energy watchdog has flagged the run. */
 int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream);
 
 /* Energy W = sum d_i |e_i| E_i^2 + sum S_j B_j^2 of eq. 8 (eq. 7 metric) of the current fields,
