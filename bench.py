@@ -284,6 +284,9 @@ def run_native(args):
         nprof = max(4, nprof // args.block_depth)
     prof_ms, prof_bytes = m.profile_steps(nprof, stream)
     names = ["k_edge_half: E half-step (eq. 3)", "k_source", "k_tri_half: B half-step (eq. 4)"]
+    if blocked and args.frame > 0:
+        names[2] = (f"frame region: gather, {args.block_depth} plain steps of the tiles next to the PML "
+                    "frame with the frame, scatter (beside k_tbp on a second stream)")
     if blocked:
         names[0] = (f"k_tbp: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, one CTA per SM "
                     "with the next tile's loads in flight")
@@ -606,8 +609,8 @@ def main(argv=None):
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
     ap.add_argument("--tile-tris", type=int, default=2560)
     ap.add_argument("--frame", type=int, default=0,
-                    help="scatterer workload, plain variant: PML frame of this many cells (open "
-                         "boundary instead of the PEC walls)")
+                    help="scatterer workload: PML frame of this many cells (open boundary instead "
+                         "of the PEC walls)")
     ap.add_argument("--tiler", choices=["kd", "greedy"], default="greedy",
                     help="blocked variant: KD or greedy partition into tiles")
     ap.add_argument("--block-depth", type=int, default=8)
@@ -625,8 +628,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.frame > 0 and args.variant != "plain":
-        ap.error("--frame needs --variant plain")
+    if args.frame > 0 and args.variant == "persistent":
+        ap.error("--frame needs --variant plain or blocked")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

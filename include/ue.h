@@ -245,8 +245,11 @@ int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz
  * Plain variant: ms[0], ms[1], ms[2] = mean device milliseconds of the E half-step (eq. 3 /
  * eqs. 5-6), source and B half-step (eq. 4) kernels; bytes[0..2] = their algorithmic HBM bytes
  * per launch.  Blocked variant: each launch advances block_depth steps; ms[0] = mean per launch,
- * bytes[0] = algorithmic bytes of the same number of plain steps, bytes[1] = bytes the blocked
- * kernel streams per launch (tile records, local field reads, owned writes); ms[1..2] = 0. */
+ * bytes[0] = algorithmic bytes of the same number of plain steps of the triangles and edges it
+ * owns, bytes[1] = bytes the blocked kernel streams per launch (tile records, local field reads,
+ * owned writes), ms[1] = the source table; with a frame, ms[2] = the region next to the frame
+ * (gather, block_depth plain steps with the frame, scatter) and bytes[2] = the plain-kernel bytes
+ * of its local triangles and edges over those steps, else 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
 /* Mesh optimisation by the jello model with flip refinement (Section 3, "Mesh generation"):
@@ -303,9 +306,12 @@ int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* 
  * (order + 1) ln(1e6) / (2 width h) (a continuous layer reflecting 1e-6 at normal incidence);
  * 0 gives an undamped frame.
  * Host call on a loaded mesh; it takes effect at the next ue_geometry_build (width 0 removes
- * the frame).  A framed mesh steps with the plain variant only (UE_VARIANT_PLAIN, with CUDA
- * graphs); dt modes UE_DT_GIVEN and UE_DT_POWER, the power iteration then covering the whole
- * framed system (eq. 20 for the coupled operator).  Its sources must be interior edges.
+ * the frame).  A framed mesh steps with UE_VARIANT_PLAIN or, on a tiled mesh, UE_VARIANT_BLOCKED:
+ * the tiles whose block_depth rings stay off the outer edges run in the blocked kernel, the
+ * others form one region advanced block_depth steps at a time by the plain kernels together
+ * with the frame (the same results, bit for bit).  dt modes UE_DT_GIVEN and UE_DT_POWER, the
+ * power iteration then covering the whole framed system (eq. 20 for the coupled operator).
+ * Its sources must be interior edges.
  * ue_write_fields zeroes the frame's fields; ue_read_fields returns E on the mesh's outer
  * edges too; the energy watchdog and ue_energy cover the mesh only.
  * width in [1, 256], order in [1, 8].  Errors: UE_ERR_ARG (arguments, a batch, or an outer

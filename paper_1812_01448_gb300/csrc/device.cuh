@@ -311,6 +311,24 @@ cudaError_t launch_frame_iface_in(const FrameDev& f, const DevMesh& m, const int
 cudaError_t launch_frame_out(const FrameDev& f, bool f64, double* B, double* Ex, double* Ey,
                              cudaStream_t s);
 
+// Blocked stepping of a framed mesh: the tiles whose k-ring halo stays off the mesh's outer
+// edges run in the blocked kernel; the others form one region (its owned triangles plus k rings,
+// see Region in ue_internal.h) that is gathered into local arrays, advanced k steps by the plain
+// kernels together with the frame, and scattered back (owned values only).  Both read the fields
+// of step n and write step n + k, on disjoint owned sets.
+struct RegionDev {
+    DevMesh dm;                   // local arrays (FP32): rl, tri, cU, U (+ interface slots), B
+    FrameDev f;                   // the frame, with local triangle ids and the region's slots
+    int32_t* tgid = nullptr;      // [n_t] stored triangle per local triangle
+    int32_t* egid = nullptr;      // [n_ei] stored edge per local edge
+    char* upd = nullptr;          // [n_t] local triangle updated (level <= k - 1)
+    int64_t n_own_t = 0, n_own_e = 0;
+};
+// tri.w of updated local triangles and cU of local edges from the mesh's (source flags kept).
+cudaError_t launch_region_coeff(const RegionDev& r, const int4* tri, const float* cU, cudaStream_t s);
+cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, cudaStream_t s);
+cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, cudaStream_t s);
+
 // Power iteration with a file-scope work array (noalloc.cu).
 int power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,
                            const int32_t* tri_code, const double* S, const int64_t* tri_caller,

@@ -65,7 +65,55 @@ __global__ void k_frame_out(FrameDev f, double* __restrict__ B, double* __restri
     }
 }
 
+__global__ void k_region_coeff(int4* __restrict__ rtri, float* __restrict__ rcU, const int32_t* __restrict__ tgid,
+                               const int32_t* __restrict__ egid, const char* __restrict__ upd, int64_t nt,
+                               int64_t ne, const int4* __restrict__ tri, const float* __restrict__ cU) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) rtri[i].w = upd[i] ? tri[tgid[i]].w : 0;
+    if (i < ne) rcU[i] = cU[egid[i]];
+}
+
+__global__ void k_region_gather(float* __restrict__ rB, float* __restrict__ rU, const int32_t* __restrict__ tgid,
+                                const int32_t* __restrict__ egid, int64_t nt, int64_t ne,
+                                const float* __restrict__ B, const float* __restrict__ U) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) rB[i] = B[tgid[i]];
+    if (i < ne) rU[i] = U[egid[i]];
+}
+
+__global__ void k_region_scatter(const float* __restrict__ rB, const float* __restrict__ rU,
+                                 const int32_t* __restrict__ tgid, const int32_t* __restrict__ egid,
+                                 int64_t nt, int64_t ne, float* __restrict__ B, float* __restrict__ U) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) B[tgid[i]] = rB[i];
+    if (i < ne) U[egid[i]] = rU[i];
+}
+
 }  // namespace
+
+cudaError_t launch_region_coeff(const RegionDev& r, const int4* tri, const float* cU, cudaStream_t s) {
+    const int64_t n = r.dm.n_t > r.dm.n_ei ? r.dm.n_t : r.dm.n_ei;
+    if (n == 0) return cudaSuccess;
+    k_region_coeff<<<blocks_for(n), kThreads, 0, s>>>(r.dm.tri, (float*)r.dm.cU, r.tgid, r.egid, r.upd, r.dm.n_t,
+                                                      r.dm.n_ei, tri, cU);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, cudaStream_t s) {
+    const int64_t n = r.dm.n_t > r.dm.n_ei ? r.dm.n_t : r.dm.n_ei;
+    if (n == 0) return cudaSuccess;
+    k_region_gather<<<blocks_for(n), kThreads, 0, s>>>((float*)r.dm.B, (float*)r.dm.U, r.tgid, r.egid, r.dm.n_t,
+                                                       r.dm.n_ei, B, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, cudaStream_t s) {
+    const int64_t n = r.n_own_t > r.n_own_e ? r.n_own_t : r.n_own_e;
+    if (n == 0) return cudaSuccess;
+    k_region_scatter<<<blocks_for(n), kThreads, 0, s>>>((const float*)r.dm.B, (const float*)r.dm.U, r.tgid, r.egid,
+                                                        r.n_own_t, r.n_own_e, B, U);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_frame_geom(const FrameDev& f, const double* O, const double* iface, double dt,
                               bool f64, cudaStream_t s) {

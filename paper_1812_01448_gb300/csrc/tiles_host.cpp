@@ -19,7 +19,8 @@
 
 namespace ue {
 
-int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err) {
+int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,
+                const std::vector<char>* include) {
     if (hm.tile_tri_off.size() < 2) {
         err = "blocked variant needs a mesh loaded with UE_REORDER_KD";
         return UE_ERR_ARG;
@@ -49,7 +50,9 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err) {
     std::vector<int32_t> elvl(nei, -1), eloc(nei, -1);
     std::vector<int64_t> tris, edges;
     std::vector<std::vector<int64_t>> ring(k_max + 1);
+    int64_t out = 0;   // index of the tile in the set (tiles left out by `include` are skipped)
     for (int64_t t = 0; t < ntiles; ++t) {
+        if (include && !(*include)[t]) continue;
         const int64_t a = hm.tile_tri_off[t], b = hm.tile_tri_off[t + 1];
         for (auto& r : ring) r.clear();
         for (int64_t j = a; j < b; ++j) {
@@ -98,7 +101,7 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err) {
             for (int64_t k : edges) elvl[k] = eloc[k] = -1;
             return UE_ERR_ARG;
         }
-        int32_t* h = &ts.hdr[t * TileSet::kHdr];
+        int32_t* h = &ts.hdr[out * TileSet::kHdr];
         h[0] = (int32_t)a;
         h[1] = (int32_t)(b - a);
         h[2] = (int32_t)ea;
@@ -139,13 +142,105 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err) {
             ts.erec.push_back(loc[hm.edge_tri[2 * k]] | (loc[hm.edge_tri[2 * k + 1]] << 16));
             ts.erec.push_back(0);
             ts.erec.push_back(0);
-            ts.erec_tile.push_back(t);
+            ts.erec_tile.push_back(out);
         }
         ts.max_tri_loc = std::max<int>(ts.max_tri_loc, (int)ntl);
         ts.max_edge_loc = std::max<int>(ts.max_edge_loc, (int)nel);
         for (int64_t j : tris) lvl[j] = loc[j] = -1;
         for (int64_t k : edges) elvl[k] = eloc[k] = -1;
+        ++out;
     }
+    ts.n_tiles = out;
+    ts.hdr.resize(out * TileSet::kHdr);
+    return UE_OK;
+}
+
+int build_region(const HostMesh& hm, const std::vector<char>& owned, int k, const std::vector<int64_t>& islot,
+                 const std::vector<int32_t>& ineg, Region& r, std::string& err) {
+    const int64_t nt = hm.n_tris, nei = hm.n_ei;
+    r = Region();
+    std::vector<int32_t> lvl(nt, -1);
+    std::vector<std::vector<int64_t>> ring(k + 1);
+    for (int64_t j = 0; j < nt; ++j)
+        if (owned[j]) {
+            lvl[j] = 0;
+            ring[0].push_back(j);
+        }
+    for (int q = 1; q <= k; ++q) {
+        for (int64_t j : ring[q - 1])
+            for (int c = 0; c < 3; ++c) {
+                const int64_t e = hm.tri_code[3 * j + c] >> 1;
+                if (e >= nei) continue;
+                const int64_t o = hm.edge_tri[2 * e] == j ? hm.edge_tri[2 * e + 1] : hm.edge_tri[2 * e];
+                if (lvl[o] < 0) {
+                    lvl[o] = q;
+                    ring[q].push_back(o);
+                }
+            }
+        std::sort(ring[q].begin(), ring[q].end());
+    }
+    for (int q = 0; q <= k; ++q) r.tgid.insert(r.tgid.end(), ring[q].begin(), ring[q].end());
+    r.n_own_t = (int64_t)ring[0].size();
+    std::vector<int32_t> loc(nt, -1);
+    for (size_t l = 0; l < r.tgid.size(); ++l) loc[r.tgid[l]] = (int32_t)l;
+    // edges with a triangle of level <= k-1, owned ones first (an edge belongs to its smaller
+    // stored triangle), then by level and id
+    std::vector<int32_t> elvl(nei, -1);
+    std::vector<int64_t> edges;
+    for (int64_t j : r.tgid) {
+        if (lvl[j] > k - 1) continue;
+        for (int c = 0; c < 3; ++c) {
+            const int64_t e = hm.tri_code[3 * j + c] >> 1;
+            if (e >= nei || elvl[e] >= 0) continue;
+            elvl[e] = std::min(lvl[hm.edge_tri[2 * e]], lvl[hm.edge_tri[2 * e + 1]]);
+            edges.push_back(e);
+        }
+    }
+    auto own_e = [&](int64_t e) { return (bool)owned[std::min(hm.edge_tri[2 * e], hm.edge_tri[2 * e + 1])]; };
+    std::sort(edges.begin(), edges.end(), [&](int64_t u, int64_t v) {
+        const bool ou = own_e(u), ov = own_e(v);
+        if (ou != ov) return ou;
+        if (elvl[u] != elvl[v]) return elvl[u] < elvl[v];
+        return u < v;
+    });
+    r.n_own_e = 0;
+    for (int64_t e : edges) r.n_own_e += own_e(e);
+    const int64_t nel = (int64_t)edges.size();
+    std::vector<int32_t> eloc(nei, -1);
+    for (size_t l = 0; l < edges.size(); ++l) eloc[edges[l]] = (int32_t)l;
+    r.egid.assign(edges.begin(), edges.end());
+    r.rl.resize(2 * nel);
+    for (int64_t l = 0; l < nel; ++l) {
+        r.rl[2 * l] = loc[hm.edge_tri[2 * edges[l]]];
+        r.rl[2 * l + 1] = loc[hm.edge_tri[2 * edges[l] + 1]];
+        if (r.rl[2 * l] < 0 || r.rl[2 * l + 1] < 0) {
+            err = "internal error: a region edge has a triangle outside the region";
+            return UE_ERR_ARG;
+        }
+    }
+    // triangle codes: local edges; the mesh's outer edges at the interface slots after the
+    // region's zero slot; triangles of level k (read only) on the zero slot
+    const int64_t u_off = (nel + 4) / 4 * 4;   // the padded local edge count
+    std::vector<int64_t> if_of(3 * nt, -1);
+    for (size_t i = 0; i < islot.size(); ++i) if_of[islot[i]] = (int64_t)i;
+    r.code.assign(3 * r.tgid.size(), (int32_t)(2 * nel));
+    r.upd.assign(r.tgid.size(), 0);
+    for (size_t l = 0; l < r.tgid.size(); ++l) {
+        const int64_t j = r.tgid[l];
+        if (lvl[j] > k - 1) continue;
+        r.upd[l] = 1;
+        for (int c = 0; c < 3; ++c) {
+            const int32_t code = hm.tri_code[3 * j + c];
+            const int64_t e = code >> 1;
+            if (e < nei) {
+                r.code[3 * l + c] = (int32_t)((eloc[e] << 1) | (code & 1));
+            } else if (if_of[3 * j + c] >= 0) {
+                const int64_t i = if_of[3 * j + c];
+                r.code[3 * l + c] = (int32_t)(2 * (u_off + i) + ineg[i]);
+            }
+        }
+    }
+    r.tloc.assign(loc.begin(), loc.end());
     return UE_OK;
 }
 

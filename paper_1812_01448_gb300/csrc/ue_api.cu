@@ -120,6 +120,12 @@ struct ue_mesh {
     // PML frame
     FrameHost fr;
     ue::FrameDev fd;
+    // blocked stepping of a framed mesh: the region of the tiles next to the frame
+    bool has_reg = false;
+    ue::Region reg_host;
+    ue::RegionDev reg;
+    cudaStream_t side = nullptr;           // the region's stream, beside the blocked kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t* d_iedge = nullptr;
     double* d_ielen = nullptr;
     double* d_iface = nullptr;
@@ -195,6 +201,9 @@ void set_current(ue_mesh* m, int c) {
     }
 }
 
+cudaError_t blocked_launch(ue_mesh* m, int kk, int cur, int gbase, cudaStream_t s);
+int64_t blocked_launches(const ue_mesh* m, int kk);
+
 int tb_chunk_launches(const ue_mesh* m) {
     const int per = m->graph_chunk / (2 * m->block_depth);
     return 2 * (per < 1 ? 1 : per);
@@ -211,7 +220,7 @@ int ensure_graph_tb(ue_mesh* m, int parity) {
     cudaError_t le = ue::launch_gtab(m->dm, tb_chunk_launches(m) * m->block_depth, m->capture_stream);
     int c = parity;
     for (int i = 0; i < tb_chunk_launches(m) && le == cudaSuccess; ++i) {
-        le = ue::launch_tb(m->tb, m->dm, m->block_depth, c, i * m->block_depth, m->capture_stream);
+        le = blocked_launch(m, m->block_depth, c, i * m->block_depth, m->capture_stream);
         c ^= 1;
     }
     cudaError_t ce = cudaStreamEndCapture(m->capture_stream, &g);
@@ -232,6 +241,117 @@ int ensure_graph_tb(ue_mesh* m, int parity) {
 
 int upload_tiles(ue_mesh* m, cudaStream_t s);
 int upload_tileset(ue_mesh* m, cudaStream_t s);
+
+// The region of a framed blocked mesh on the device (local arrays, the frame re-pointed at
+// them), coefficients from the mesh's.  Sources are set by region_sources.
+int setup_region(ue_mesh* m, const std::vector<char>& owned, cudaStream_t s) {
+    std::string err;
+    ue::Region& R = m->reg_host;
+    int rc = ue::build_region(m->hm, owned, m->block_depth, m->fr.islot, m->fr.ineg, R, err);
+    if (rc != UE_OK) return fail(rc, err);
+    ue::RegionDev& r = m->reg;
+    r = ue::RegionDev();
+    DevMesh& d = r.dm;
+    const int64_t ntl = (int64_t)R.tgid.size(), nel = (int64_t)R.egid.size();
+    const int64_t n_if = (int64_t)m->fr.itri.size();
+    d.precision = UE_PREC_FP32;
+    d.n_t = ntl;
+    d.n_ei = nel;
+    d.n_ei_pad = (nel + 4) / 4 * 4;
+    d.n_t_pad = (ntl + 3) / 4 * 4;
+    d.dt = m->dt;
+    d.gtab_size = m->dm.gtab_size;
+    int32_t* itri = nullptr;
+    int2* rlw = nullptr;
+    const bool ok = alloc_into(m, rlw, d.n_ei_pad, 8, s) && alloc_into(m, d.tri, d.n_t_pad, 16, s) &&
+                    alloc_into(m, d.cU, d.n_ei_pad, 4, s) &&
+                    alloc_into(m, d.U, d.n_ei_pad + (n_if + 3) / 4 * 4, 4, s) &&
+                    alloc_into(m, d.B, d.n_t_pad, 4, s) && alloc_into(m, r.tgid, ntl, 4, s) &&
+                    alloc_into(m, r.egid, nel, 4, s) && alloc_into(m, r.upd, ntl, 1, s) &&
+                    alloc_into(m, itri, n_if, 4, s) &&
+                    (m->tb.n_tiles == 0 || alloc_into(m, d.step, 1, 8, s));
+    if (!ok) return fail(UE_ERR_ALLOC, "frame region arrays");
+    // without blocked tiles the region's step counter is the mesh's (its B half-steps advance it)
+    if (m->tb.n_tiles == 0) d.step = m->dm.step;
+    std::vector<int32_t> rl(2 * d.n_ei_pad, 0), tri(4 * d.n_t_pad, (int32_t)(2 * nel)), tg(ntl), eg(nel), it(n_if);
+    for (int64_t l = 0; l < nel; ++l) {
+        rl[2 * l] = R.rl[2 * l];
+        rl[2 * l + 1] = R.rl[2 * l + 1];
+        eg[l] = (int32_t)R.egid[l];
+    }
+    for (int64_t l = 0; l < d.n_t_pad; ++l) tri[4 * l + 3] = 0;
+    for (int64_t l = 0; l < ntl; ++l) {
+        for (int c = 0; c < 3; ++c) tri[4 * l + c] = R.code[3 * l + c];
+        tg[l] = (int32_t)R.tgid[l];
+    }
+    for (int64_t i = 0; i < n_if; ++i) {
+        const int32_t code = m->fr.itri[i];
+        const int32_t l = R.tloc[code >= 0 ? code : ~code];
+        if (l < 0 || l >= R.n_own_t) return fail(UE_ERR_ARG, "internal error: an outer edge's triangle is not in the frame region");
+        it[i] = code >= 0 ? l : ~l;
+    }
+    UE_CUDA(cudaMemcpyAsync(rlw, rl.data(), 4 * rl.size(), cudaMemcpyHostToDevice, s));
+    d.rl = rlw;
+    UE_CUDA(cudaMemcpyAsync(d.tri, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(r.tgid, tg.data(), 4 * ntl, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(r.egid, eg.data(), 4 * nel, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(r.upd, R.upd.data(), ntl, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(itri, it.data(), 4 * n_if, cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemsetAsync(d.cU, 0, 4 * d.n_ei_pad, s));
+    UE_CUDA(cudaMemsetAsync(d.U, 0, 4 * (d.n_ei_pad + (n_if + 3) / 4 * 4), s));
+    UE_CUDA(cudaMemsetAsync(d.B, 0, 4 * d.n_t_pad, s));
+    if (m->tb.n_tiles > 0) UE_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
+    r.f = m->fd;
+    r.f.itri = itri;
+    r.f.u_off = d.n_ei_pad;
+    d.frame = &r.f;
+    r.n_own_t = R.n_own_t;
+    r.n_own_e = R.n_own_e;
+    UE_CUDA(ue::launch_region_coeff(r, m->dm.tri, (const float*)m->dm.cU, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    if (!m->side) UE_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    if (!m->ev_fork) UE_CUDA(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    if (!m->ev_join) UE_CUDA(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+    m->has_reg = true;
+    return UE_OK;
+}
+
+// One blocked launch of k steps (buffer cur to cur ^ 1): the blocked tiles and, for a framed
+// mesh, the region's gather, k plain steps and scatter.  Both read buffer cur and write
+// disjoint parts of cur ^ 1, so the region runs on a side stream forked from s before the
+// blocked kernel and joined after it (inside a graph capture too): its small kernels fill the
+// room the one-CTA-per-SM blocked kernel leaves on each SM.
+cudaError_t blocked_launch(ue_mesh* m, int kk, int cur, int gbase, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    const bool tiles = m->tb.n_tiles > 0;
+    cudaStream_t rs = s;
+    if (m->has_reg && tiles) {
+        e = cudaEventRecord(m->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->side, m->ev_fork, 0);
+        rs = m->side;
+    }
+    if (e == cudaSuccess && m->has_reg) {
+        ue::RegionDev& r = m->reg;
+        e = ue::launch_region_gather(r, (const float*)m->tb.B[cur], (const float*)m->tb.U[cur], rs);
+        for (int i = 0; i < kk && e == cudaSuccess; ++i) {
+            e = ue::launch_step_part(r.dm, 0, gbase + i, rs);
+            if (e == cudaSuccess) e = ue::launch_step_part(r.dm, 1, gbase + i, rs);
+        }
+        if (e == cudaSuccess)
+            e = ue::launch_region_scatter(r, (float*)m->tb.B[cur ^ 1], (float*)m->tb.U[cur ^ 1], rs);
+    }
+    if (e == cudaSuccess && tiles) e = ue::launch_tb(m->tb, m->dm, kk, cur, gbase, s);
+    if (e == cudaSuccess && m->has_reg && tiles) {
+        e = cudaEventRecord(m->ev_join, m->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_join, 0);
+    }
+    return e;
+}
+
+// Kernels of one blocked launch of kk steps.
+int64_t blocked_launches(const ue_mesh* m, int kk) {
+    return (m->tb.n_tiles > 0 ? 1 : 0) + (m->has_reg ? 2 + 2 * (int64_t)kk : 0);
+}
 
 int ensure_graph(ue_mesh* m) {
     if (m->gexec && m->graph_version == m->version) return UE_OK;
@@ -306,7 +426,65 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
     return UE_OK;
 }
 
+int bake_source_mesh(ue_mesh* m, cudaStream_t s);
+
+// The region of a framed blocked mesh: coefficients again (the mesh's cU carries the source
+// flags) and its own table {local edge, source index}; the rest of the source state is the
+// mesh's.
+int region_sources(ue_mesh* m, cudaStream_t s) {
+    ue::RegionDev& r = m->reg;
+    DevMesh& d = r.dm;
+    const DevMesh& g = m->dm;
+    dev_release(m, d.src_hash, s);
+    d.src_hash = nullptr;
+    d.n_src = 0;
+    d.src_bits = 0;
+    d.src_c = g.src_c;
+    d.src_grp = g.src_grp;
+    d.gtab = g.gtab;
+    d.grp_par = g.grp_par;
+    d.n_grp = g.n_grp;
+    d.gtab_size = g.gtab_size;
+    d.dt = g.dt;
+    UE_CUDA(ue::launch_region_coeff(r, g.tri, (const float*)g.cU, s));
+    std::vector<int32_t> src_of(m->hm.n_ei, -1);
+    for (size_t i = 0; i < m->src_k.size(); ++i) src_of[m->src_k[i]] = (int32_t)i;
+    std::vector<int32_t> lk, li;
+    const std::vector<int64_t>& eg = m->reg_host.egid;
+    for (size_t l = 0; l < eg.size(); ++l)
+        if (src_of[eg[l]] >= 0) {
+            lk.push_back((int32_t)l);
+            li.push_back(src_of[eg[l]]);
+        }
+    if (!lk.empty()) {
+        int bits = 4;
+        while ((int64_t(1) << bits) < 2 * (int64_t)lk.size()) ++bits;
+        const uint32_t size = 1u << bits;
+        std::vector<int32_t> tab(2 * (size_t)size, -1);
+        for (size_t i = 0; i < lk.size(); ++i) {
+            uint32_t h = ((uint32_t)lk[i] * 2654435761u) >> (32 - bits);
+            while (tab[2 * h] != -1) h = (h + 1) & (size - 1);
+            tab[2 * h] = lk[i];
+            tab[2 * h + 1] = li[i];
+        }
+        int2* dh = nullptr;
+        if (!alloc_into(m, dh, size, 8, s)) return fail(UE_ERR_ALLOC, "frame region source table");
+        UE_CUDA(cudaMemcpyAsync(dh, tab.data(), 8 * (size_t)size, cudaMemcpyHostToDevice, s));
+        d.src_hash = dh;
+        d.src_bits = bits;
+        d.n_src = (int64_t)lk.size();
+    }
+    UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
 int bake_source(ue_mesh* m, cudaStream_t s) {
+    const int rc = bake_source_mesh(m, s);
+    if (rc != UE_OK || !m->has_reg) return rc;
+    return region_sources(m, s);
+}
+
+int bake_source_mesh(ue_mesh* m, cudaStream_t s) {
     DevMesh& dm = m->dm;
     if (dm.n_src > 0 && dm.src_k) UE_CUDA(ue::launch_source_flags(dm, dm.src_k, dm.n_src, false, s));
     UE_CUDA(cudaStreamSynchronize(s));
@@ -396,9 +574,53 @@ int upload_tileset(ue_mesh* m, cudaStream_t s);
 
 int upload_tiles(ue_mesh* m, cudaStream_t s) {
     std::string err;
-    int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
+    if (m->fr.W == 0) {
+        int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
+        if (rc != UE_OK) return fail(rc, err);
+        return upload_tileset(m, s);
+    }
+    // framed: a tile whose rings H_0 .. H_{k-1} reach a triangle on the mesh's outer edges
+    // joins the region; the others stay blocked tiles
+    const HostMesh& h = m->hm;
+    const int k = m->block_depth;
+    const int64_t ntiles = (int64_t)h.tile_tri_off.size() - 1;
+    std::vector<int32_t> dist(h.n_tris, -1);
+    std::vector<int64_t> front, next;
+    for (int32_t code : m->fr.itri) {
+        const int64_t t = code >= 0 ? code : ~code;
+        if (dist[t] < 0) {
+            dist[t] = 0;
+            front.push_back(t);
+        }
+    }
+    for (int r = 1; r <= k - 1; ++r) {
+        next.clear();
+        for (int64_t j : front)
+            for (int q = 0; q < 3; ++q) {
+                const int64_t e = h.tri_code[3 * j + q] >> 1;
+                if (e >= h.n_ei) continue;
+                const int64_t o = h.edge_tri[2 * e] == j ? h.edge_tri[2 * e + 1] : h.edge_tri[2 * e];
+                if (dist[o] < 0) {
+                    dist[o] = r;
+                    next.push_back(o);
+                }
+            }
+        front.swap(next);
+    }
+    std::vector<char> interior(ntiles, 1), owned(h.n_tris, 0);
+    for (int64_t t = 0; t < ntiles; ++t)
+        for (int64_t j = h.tile_tri_off[t]; j < h.tile_tri_off[t + 1]; ++j)
+            if (dist[j] >= 0) {
+                interior[t] = 0;
+                break;
+            }
+    for (int64_t t = 0; t < ntiles; ++t)
+        if (!interior[t])
+            for (int64_t j = h.tile_tri_off[t]; j < h.tile_tri_off[t + 1]; ++j) owned[j] = 1;
+    int rc = ue::build_tiles(h, k, m->ts, err, &interior);
     if (rc != UE_OK) return fail(rc, err);
-    return upload_tileset(m, s);
+    if ((rc = upload_tileset(m, s)) != UE_OK) return rc;
+    return setup_region(m, owned, s);
 }
 
 // Device copy of m->ts, second field buffers, and the coefficient slots of the records.
@@ -764,8 +986,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     }
     const bool framed = m->fr.W > 0;
     if (framed) {
-        if (o.variant != 0 && o.variant != UE_VARIANT_PLAIN)
-            return fail(UE_ERR_ARG, "a framed mesh steps with the plain variant only");
+        if (o.variant == UE_VARIANT_PERSISTENT)
+            return fail(UE_ERR_ARG, "a framed mesh steps with the plain or the blocked variant");
         if (o.dt_mode == UE_DT_LEARNED)
             return fail(UE_ERR_ARG, "a framed mesh takes its dt from UE_DT_GIVEN or UE_DT_POWER");
         if (!m->plasma_n.empty()) return fail(UE_ERR_ARG, "plasma media with a frame are not supported");
@@ -781,6 +1003,9 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->dm = DevMesh();
     m->tb = ue::TBDev();
     m->fd = ue::FrameDev();
+    m->has_reg = false;
+    m->reg = ue::RegionDev();
+    m->reg_host = ue::Region();
     m->cur = 0;
     m->variant = o.variant == 0 ? UE_VARIANT_PLAIN : o.variant;
     m->block_depth = o.block_depth;
@@ -1177,7 +1402,10 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
     if (m->dm.frame) {
         const ue::FrameDev& f = m->fd;
         const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
-        if (E) UE_CUDA(ue::launch_frame_iface_in(f, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+        if (E && m->has_reg)
+            UE_CUDA(ue::launch_frame_iface_in(m->reg.f, m->reg.dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+        else if (E)
+            UE_CUDA(ue::launch_frame_iface_in(f, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
         UE_CUDA(cudaMemsetAsync(f.H, 0, esz * f.NX * (f.NY + 1), s));
         UE_CUDA(cudaMemsetAsync(f.V, 0, esz * (f.NX + 1) * f.NY, s));
         UE_CUDA(cudaMemsetAsync(f.Bx, 0, esz * f.n_fc, s));
@@ -1225,7 +1453,7 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             while (left >= chunk) {
                 UE_CUDA(cudaGraphLaunch(m->gexec_tb[m->cur], s));
                 left -= chunk;
-                launched += tb_chunk_launches(m) + (m->dm.n_src > 0 ? 1 : 0);
+                launched += tb_chunk_launches(m) * blocked_launches(m, (int)k) + (m->dm.n_src > 0 ? 1 : 0);
                 UE_CUDA(watchdog_tick(m, chunk, s, &launched));
             }
         }
@@ -1237,10 +1465,10 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             int64_t done = 0;
             while (done < batch) {
                 const int kk = (int)(batch - done < k ? batch - done : k);
-                UE_CUDA(ue::launch_tb(m->tb, m->dm, kk, m->cur, (int)done, s));
+                UE_CUDA(blocked_launch(m, kk, m->cur, (int)done, s));
                 set_current(m, m->cur ^ 1);
                 done += kk;
-                ++launched;
+                launched += blocked_launches(m, kk);
             }
             left -= batch;
             UE_CUDA(watchdog_tick(m, batch, s, &launched));
@@ -1282,7 +1510,10 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
                                   (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
                                   m->d_elen, s));
-    if (E && m->dm.frame) UE_CUDA(ue::launch_frame_iface_out(m->fd, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+    if (E && m->has_reg)
+        UE_CUDA(ue::launch_frame_iface_out(m->reg.f, m->reg.dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+    else if (E && m->dm.frame)
+        UE_CUDA(ue::launch_frame_iface_out(m->fd, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
     if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
     if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
     if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
@@ -1596,9 +1827,16 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
         if (e == cudaSuccess) e = ue::launch_gtab(m->dm, blocked ? m->block_depth : 1, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 1], s);
         if (blocked) {
-            if (e == cudaSuccess) e = ue::launch_tb(m->tb, m->dm, m->block_depth, m->cur, 0, s);
-            if (e == cudaSuccess) set_current(m, m->cur ^ 1);
+            // the blocked tiles, then (framed) the region: timed apart
+            if (e == cudaSuccess && m->tb.n_tiles > 0) e = ue::launch_tb(m->tb, m->dm, m->block_depth, m->cur, 0, s);
             if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 2], s);
+            if (e == cudaSuccess && m->has_reg) {
+                const bool tiles = m->tb.n_tiles > 0;
+                m->tb.n_tiles = 0;   // region part only
+                e = blocked_launch(m, m->block_depth, m->cur, 0, s);
+                m->tb.n_tiles = tiles ? m->ts.n_tiles : 0;
+            }
+            if (e == cudaSuccess) set_current(m, m->cur ^ 1);
             if (e == cudaSuccess) e = cudaEventRecord(ev[4 * i + 3], s);
         } else {
             if (e == cudaSuccess) e = ue::launch_step_part(m->dm, 0, 0, s);
@@ -1626,17 +1864,21 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     for (int p = 0; p < 3; ++p) ms[p] = acc[p] / (double)n;
     const int64_t per = blocked ? m->block_depth : 1;
     m->steps_done += n * per;
-    m->launches += blocked ? n * (1 + (m->dm.n_src > 0 ? 1 : 0)) : plain_launches(m, n, 1);
+    m->launches += blocked ? n * (blocked_launches(m, m->block_depth) + (m->dm.n_src > 0 ? 1 : 0))
+                           : plain_launches(m, n, 1);
     if (bytes) {
         const double f = m->precision == UE_PREC_FP64 ? 2.0 : 1.0;
         const HostMesh& h = m->hm;
         const double pl = m->dm.plasma ? 1.0 : 0.0;
         if (blocked) {
-            ms[2] = 0;
-            bytes[0] = (double)per * ((20.0 + 12.0 * pl) * (double)h.n_ei + 24.0 * (double)h.n_tris);
-            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec +
-                       4.0 * (double)h.n_tris + (4.0 + 4.0 * pl) * (double)h.n_ei;
-            bytes[2] = 0;
+            // the blocked kernel owns what the region (if any) does not
+            const double ot = (double)(h.n_tris - (m->has_reg ? m->reg.n_own_t : 0));
+            const double oe = (double)(h.n_ei - (m->has_reg ? m->reg.n_own_e : 0));
+            bytes[0] = (double)per * ((20.0 + 12.0 * pl) * oe + 24.0 * ot);
+            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec + 4.0 * ot +
+                       (4.0 + 4.0 * pl) * oe;
+            bytes[2] = m->has_reg ? (double)per * (20.0 * (double)m->reg.dm.n_ei + 24.0 * (double)m->reg.dm.n_t) : 0.0;
+            if (!m->has_reg) ms[2] = 0;
         } else {
             bytes[0] = (8.0 + f * 12.0 + pl * f * 12.0) * (double)h.n_ei;
             bytes[1] = 8.0 * (m->dm.n_src > 0 ? 1.0 : 0.0);
@@ -1734,6 +1976,9 @@ void ue_mesh_free(ue_mesh* m) {
     cudaDeviceSynchronize();
     dev_free_all(m, nullptr);
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    if (m->side) cudaStreamDestroy(m->side);
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_join) cudaEventDestroy(m->ev_join);
     delete m;
 }
 

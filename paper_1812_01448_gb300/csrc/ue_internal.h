@@ -38,7 +38,26 @@ struct TileSet {
     std::vector<int64_t> erec_tile;       // per local edge record: its tile (for sources)
 };
 
-int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err);
+// include (may be NULL): build only the tiles t with (*include)[t] != 0, in order.
+int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,
+                const std::vector<char>* include = nullptr);
+
+// A region advanced k steps at once by the plain kernels on local copies: its owned triangles
+// and the rings of edge-neighbours H_1..H_k around them, laid out like a tile (owned first,
+// then by level; owned edges first).  Codes of triangles of level <= k-1 point at local edges,
+// or, for the mesh's outer edges listed in islot (3 * stored triangle + q), at slot
+// u_off + i with sign bit ineg[i], u_off = (nel + 4) / 4 * 4 the padded local edge count;
+// level-k triangles (read only) and other boundary edges point at the zero slot nel.
+struct Region {
+    std::vector<int64_t> tgid, egid;   // stored ids of the local triangles / edges
+    int64_t n_own_t = 0, n_own_e = 0;
+    std::vector<int32_t> rl;           // 2 per local edge: local (R, L)
+    std::vector<int32_t> code;         // 3 per local triangle
+    std::vector<char> upd;             // local triangle updated (level <= k-1)
+    std::vector<int32_t> tloc;         // stored triangle -> local index, or -1
+};
+int build_region(const HostMesh& hm, const std::vector<char>& owned, int k, const std::vector<int64_t>& islot,
+                 const std::vector<int32_t>& ineg, Region& r, std::string& err);
 
 // Returns UE_OK or an error code with a message in err.
 int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
