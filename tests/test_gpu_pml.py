@@ -182,12 +182,10 @@ def test_framed_mesh_refuses_other_variants(ue):
     mesh.close()
 
 
-@pytest.mark.slow
-def test_full_size_scatterer_with_frame(ue, scatterer_window):
-    """The bench's framed configuration at full size (3.96M triangles, 16-cell frame, plain
-    variant, CUDA graphs of 32 steps, FP32, line source from step 5000), started from a smooth
-    field that is non-zero at the outer boundary so that the frame works from the first step:
-    every field within 1e-4 of the oracle after 200 steps."""
+@pytest.fixture(scope="module")
+def framed_window(scatterer_window):
+    """The oracle's 200-step window of the framed scatterer (16-cell frame, line source from step
+    5000) from a smooth field that is non-zero at the outer boundary."""
     ms, ops, ids, amp, w0, dt, _, _ = scatterer_window
     m = ops.mesh
     fo = pml.FramedOperators(m, 16, inner=ops, geom=ops.geom)
@@ -196,10 +194,24 @@ def test_full_size_scatterer_with_frame(ue, scatterer_window):
     src = lf.Source(ids, amp, w0, 0.1, 0.05)
     E, Bs = np.zeros(fo.n_ei), fo.start_split(np.concatenate([b, np.zeros(fo.n_fc)]))
     E, Bs = pml.run(fo, E, Bs, dt, 200, src=(ops.col_of_edge[ids], amp, src.g), n0=5000)
-    ref = _oracle_fields(fo, E, Bs, m.n_edges)
-    mesh = ue.Mesh(ms.xy, ms.tris)
+    return b, _oracle_fields(fo, E, Bs, m.n_edges)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_full_size_scatterer_with_frame(ue, scatterer_window, framed_window, variant):
+    """The bench's framed configurations at full size (3.96M triangles, 16-cell frame, FP32, line
+    source from step 5000; plain: CUDA graphs of 32 steps; blocked: greedy tiles <= 2560, k = 8,
+    the region next to the frame beside the blocked kernel): every field within 1e-4 of the
+    oracle after 200 steps."""
+    ms, ops, ids, amp, w0, dt, _, _ = scatterer_window
+    b, ref = framed_window
+    blocked = variant == "blocked"
+    mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY if blocked else ue.UE_REORDER_RCM,
+                   tile_tris=2560)
     mesh.frame_attach(16)
-    mesh.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt)
+    mesh.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, block_depth=8,
+                        variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN)
     mesh.set_source(ids, amp, w0, 0.1, 0.05)
     mesh.set_step(5000)
     mesh.write_fields(B=b)
@@ -207,6 +219,6 @@ def test_full_size_scatterer_with_frame(ue, scatterer_window):
     got = mesh.read_fields()[:2] + mesh.frame_fields()
     mesh.close()
     errs = [_rel(g, r) for g, r in zip(got, ref)]
-    print("full-size framed window rel L2 (E, B, frame B, Ex, Ey):", ["%.2e" % e for e in errs])
+    print(f"full-size framed window, {variant}, rel L2 (E, B, frame B, Ex, Ey):", ["%.2e" % e for e in errs])
     assert np.linalg.norm(ref[2]) > 1e-3 * np.linalg.norm(b)
     assert max(errs) <= 1e-4
