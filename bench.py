@@ -42,11 +42,12 @@ L2_BYTES = 129e6
 # bench command at its configuration (summary and command in profiles/), keyed by the sha1 of
 # the kernel source it measured: used only while that source is unchanged, else null.
 NCU_TRAFFIC = {
-    # (variant, tiler, tile_tris, block_depth, threads): (bytes per launch, source file, sha1, profile)
-    ("blocked", "greedy", 2560, 8, 512): (304521643, "kernels_tb.cu",
+    # (variant, tiler, tile_tris, block_depth, threads, PML frame cells): (bytes per launch,
+    # source file, sha1, profile)
+    ("blocked", "greedy", 2560, 8, 512, 0): (304521643, "kernels_tb.cu",
                                           "74268af160169826e19cf8973928e739eb32c11d",
                                           "profiles/blocked_k_tbp_scatterer4M.md"),
-    ("blocked", "kd", 2048, 8, 512): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
+    ("blocked", "kd", 2048, 8, 512, 0): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
                                       "profiles/blocked_k_tbp_scatterer4M.md"),
 }
 
@@ -295,7 +296,7 @@ def run_native(args):
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
     tkey = (args.variant, args.tiler if blocked else "", args.tile_tris if blocked else 0,
             args.block_depth if blocked else 1,
-            (args.tb_threads or 512) if blocked else 0)
+            (args.tb_threads or 512) if blocked else 0, args.frame)
     traffic, traffic_src = _traffic(tkey)
     step_bytes = st["bytes_per_step"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
