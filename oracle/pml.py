@@ -30,13 +30,19 @@ Cells: the inner system's cells, then the frame cells in strip order (the W bott
 middle row the W cells left of the mesh and the W right of it, then the W top rows).  The split
 state is [inner cells, Bx of the frame cells, By of the frame cells].
 
+With plasma (``step_plasma``) the current of eqs. 5-6 runs on the mesh's interior edges only; the
+mesh's outer edges and the frame are vacuum.
+
 Parity: pinned by tests/test_oracle_pml.py (Yee's closed form for every mode of a right-split
 lattice framed with sigma = 0, adjointness of the combined operators, exact conservation of the
 staggered energy at sigma = 0, and a pulse that stays within 5e-4 of the same mesh in a large
 undamped frame until that frame's echo returns, while a layer whose Bx and By decay rates are
 swapped is more than 20 times worse).  A PML absorbs travelling waves only: the static charge
 its anisotropic decay leaves behind (div E is not kept inside the layer) and the zero-frequency
-part of a field stay, so the pins compare fields, not the energy left.
+part of a field stay, so the pins compare fields, not the energy left.  The plasma step is
+pinned by the static field: a discrete gradient of a node potential that vanishes on the
+boundary never reaches the frame, and with a uniform density n0 and nu = 0 it obeys
+E^{n+1} + E^{n-1} = (2 - n0 dt^2) E^n exactly while B stays 0.
 """
 from __future__ import annotations
 
@@ -270,6 +276,31 @@ def step(fo: FramedOperators, E: np.ndarray, Bs: np.ndarray, dt: float, src=None
     bB = dt / (1.0 + 0.5 * dt * fo.sigB)
     Bs = aB * Bs + bB * (fo.Ls_E @ E)
     return E, Bs
+
+
+def inner_nbar(fo: FramedOperators, n_nodes: np.ndarray) -> np.ndarray:
+    """Mean density of the two end nodes of each of the mesh's interior edges (eq. 5 reading)."""
+    e = fo.inner.mesh.edges[fo.inner.ie]
+    return 0.5 * (n_nodes[e[:, 0]] + n_nodes[e[:, 1]])
+
+
+def step_plasma(fo: FramedOperators, E, Bs, j, dt: float, nbar, nu: float, src=None, n: int = 0):
+    """One framed step with the cold-plasma current of eqs. 5-6 on the mesh's interior edges,
+    in the order and form of the unframed step: j at half steps, trapezoidal in nu, drains E;
+    the mesh's outer edges and the frame are vacuum.  Returns (E, Bs, j)."""
+    ni = fo.inner.n_ei
+    j = ((1.0 - 0.5 * nu * dt) * j + dt * nbar * E[:ni]) / (1.0 + 0.5 * nu * dt)
+    aE = (1.0 - 0.5 * dt * fo.sigE) / (1.0 + 0.5 * dt * fo.sigE)
+    bE = dt / (1.0 + 0.5 * dt * fo.sigE)
+    E = aE * E + bE * (fo.L_B @ (fo.P @ Bs))
+    E[:ni] -= dt * j
+    if src is not None:
+        rows, amp, g = src
+        E[rows] += dt * amp * g((n + 0.5) * dt)
+    aB = (1.0 - 0.5 * dt * fo.sigB) / (1.0 + 0.5 * dt * fo.sigB)
+    bB = dt / (1.0 + 0.5 * dt * fo.sigB)
+    Bs = aB * Bs + bB * (fo.Ls_E @ E)
+    return E, Bs, j
 
 
 def run(fo: FramedOperators, E, Bs, dt: float, n_steps: int, src=None, n0: int = 0):

@@ -170,6 +170,34 @@ def test_blocked_framed_is_bit_identical_to_plain(ue, tile, k, nsteps):
     assert out[0][5] == out[1][5] == nsteps
 
 
+def test_framed_write_fields_sets_the_outer_edges(ue):
+    """E written on the mesh's outer edges (the frame's interface) reaches the step in both
+    launch forms (in the blocked one it lives in the region's slots): plain and blocked stay
+    bit-identical, and reading back right after writing returns what was written."""
+    ms, m = _square()
+    rng = np.random.default_rng(8)
+    E0 = rng.standard_normal(m.n_edges) * 0.1
+    B0 = _pulse(m)
+    outer = ~m.interior
+    out = []
+    for variant in (ue.UE_VARIANT_PLAIN, ue.UE_VARIANT_BLOCKED):
+        mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)
+        mesh.frame_attach(6)
+        mesh.geometry_build(variant=variant, block_depth=4)
+        info = mesh.frame_info()
+        mesh.write_fields(E=E0, B=B0)
+        E1, _, _ = mesh.read_fields()
+        on_frame = np.abs(E1[outer]) > 0
+        assert on_frame.sum() == info["n_interface"]       # the outer edges that face the frame
+        np.testing.assert_allclose(E1[outer][on_frame], E0[outer][on_frame], rtol=1e-6)
+        mesh.step_n(30)
+        E, B, _ = mesh.read_fields()
+        out.append((E, B) + mesh.frame_fields())
+        mesh.close()
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
+
+
 def test_framed_mesh_refuses_other_variants(ue):
     ms, m = _square(1 / 16)
     mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)

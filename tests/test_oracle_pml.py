@@ -116,3 +116,32 @@ def test_frame_needs_a_uniform_rectangular_boundary():
     for xy, tris in _not_a_divided_rectangle():
         with pytest.raises(ValueError):
             pml.FramedOperators(om.canonicalize(xy, tris), 4)
+
+
+def test_framed_plasma_static_field_closed_form():
+    """A discrete gradient E = G phi (phi zero on every boundary node) is curl-free, so B stays 0
+    and the frame and the outer edges see nothing (to rounding); with uniform density n0 and nu = 0 the
+    current makes every edge oscillate as E^{n+1} + E^{n-1} = (2 - n0 dt^2) E^n."""
+    ms, m = _square(1 / 16, hole=True)
+    fo = pml.FramedOperators(m, 4)
+    rng = np.random.default_rng(6)
+    bnd = np.zeros(m.n_nodes, bool)
+    bnd[m.edges[~m.interior].ravel()] = True
+    phi = np.where(bnd, 0.0, rng.standard_normal(m.n_nodes))
+    e = m.edges[fo.inner.ie]
+    E = np.zeros(fo.n_ei)
+    E[:fo.inner.n_ei] = (phi[e[:, 1]] - phi[e[:, 0]]) / fo.inner.elen
+    n0 = 3.0e3
+    rho, _ = spectral.power_iteration(fo, 300)
+    dt = 0.5 * 2.0 / math.sqrt(rho * rho + n0)
+    nbar = pml.inner_nbar(fo, np.full(m.n_nodes, n0))
+    Bs, j = np.zeros(fo.n_s), np.zeros(fo.inner.n_ei)
+    hist = [E.copy()]
+    for k in range(60):
+        E, Bs, j = pml.step_plasma(fo, E, Bs, j, dt, nbar, 0.0, n=k)
+        hist.append(E.copy())
+    H = np.asarray(hist)
+    assert np.abs(Bs).max() < 1e-12 * np.abs(H).max()
+    assert np.abs(H[:, fo.inner.n_ei:]).max() < 1e-12 * np.abs(H).max()   # rounding only
+    resid = H[2:] + H[:-2] - (2.0 - n0 * dt * dt) * H[1:-1]
+    assert np.abs(resid).max() < 1e-12 * np.abs(H).max()
