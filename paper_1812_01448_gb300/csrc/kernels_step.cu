@@ -192,20 +192,18 @@ void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
                    m.gtab_size, s_index};
     const T pa = PLASMA ? (T)m.pa : (T)0, mdt = PLASMA ? (T)(-m.dt) : (T)0;
     const int64_t nb = blocks_for(n_vec);
-    // a frame (never with plasma) adds its blocks to the same launch
-    const FrameDev f = (!PLASMA && m.frame) ? *m.frame : FrameDev();
-    const int64_t nbf = (!PLASMA && m.frame) ? blocks_for(f.n_fc + f.n_if) : 0;
+    // a frame adds its blocks to the same launch (its sides and the outer edges are vacuum)
+    const FrameDev f = m.frame ? *m.frame : FrameDev();
+    const int64_t nbf = m.frame ? blocks_for(f.n_fc + f.n_if) : 0;
     const unsigned grid = (unsigned)(nb + nbf);
     const int4* rl = (const int4*)m.rl;
     if (nbf > 0) {
-        if constexpr (!PLASMA) {
-            if (m.n_src > 0)
-                k_edge_half<T, false, true, true><<<grid, kThreads, 0, s>>>(
-                    rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
-            else
-                k_edge_half<T, false, false, true><<<grid, kThreads, 0, s>>>(
-                    rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
-        }
+        if (m.n_src > 0)
+            k_edge_half<T, PLASMA, true, true><<<grid, kThreads, 0, s>>>(
+                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+        else
+            k_edge_half<T, PLASMA, false, true><<<grid, kThreads, 0, s>>>(
+                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
     } else if (m.n_src > 0) {
         k_edge_half<T, PLASMA, true, false><<<grid, kThreads, 0, s>>>(
             rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);

@@ -990,7 +990,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
             return fail(UE_ERR_ARG, "a framed mesh steps with the plain or the blocked variant");
         if (o.dt_mode == UE_DT_LEARNED)
             return fail(UE_ERR_ARG, "a framed mesh takes its dt from UE_DT_GIVEN or UE_DT_POWER");
-        if (!m->plasma_n.empty()) return fail(UE_ERR_ARG, "plasma media with a frame are not supported");
+        if (!m->plasma_n.empty() && o.variant == UE_VARIANT_BLOCKED)
+            return fail(UE_ERR_ARG, "plasma media with a frame step with the plain variant");
     }
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
@@ -1350,7 +1351,8 @@ int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
 int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (m->is_batch) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
-    if (n && m->dm.frame) return fail(UE_ERR_ARG, "plasma media with a frame are not supported");
+    if (n && m->dm.frame && m->variant == UE_VARIANT_BLOCKED)
+        return fail(UE_ERR_ARG, "plasma media with a frame step with the plain variant");
     if (n && !(nu >= 0)) return fail(UE_ERR_ARG, "collision rate must be >= 0");
     if (n) {
         for (int64_t v = 0; v < m->hm.n_nodes; ++v)

@@ -198,15 +198,57 @@ def test_framed_write_fields_sets_the_outer_edges(ue):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("precision,nsteps,tol", [(1, 400, 1e-12), (0, 1500, 1e-4)])
+def test_framed_plasma_matches_oracle(ue, precision, nsteps, tol):
+    """Plasma medium (Gaussian density, nu = 0.01 w0, line source) in the holed square with an
+    8-cell PML frame, plain variant: E, B, j and the frame's fields against the oracle's framed
+    plasma step."""
+    ms, m = _square()
+    fo = pml.FramedOperators(m, 8)
+    w0 = 2 * math.pi * 20
+    dens = meshgen.plasma_density_nodes(ms.xy, w0)
+    nu = 0.01 * w0
+    nbar = pml.inner_nbar(fo, dens)
+    rho_o, _ = spectral.power_iteration(fo, 200)
+    dt = 0.5 * 2 / math.sqrt(rho_o ** 2 + nbar.max())
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    src = lf.Source(ids, amp, w0, 0.0, 0.05)
+    b = _pulse(m)
+    E, Bs = np.zeros(fo.n_ei), fo.start_split(np.concatenate([b, np.zeros(fo.n_fc)]))
+    j = np.zeros(fo.inner.n_ei)
+    rows = fo.inner.col_of_edge[ids]
+    for k in range(nsteps):
+        E, Bs, j = pml.step_plasma(fo, E, Bs, j, dt, nbar, nu, src=(rows, amp, src.g), n=k)
+    ref = _oracle_fields(fo, E, Bs, m.n_edges)
+    jref = np.zeros(m.n_edges)
+    jref[fo.inner.ie] = j
+    mesh = ue.Mesh(ms.xy, ms.tris)
+    mesh.frame_attach(8)
+    mesh.geometry_build(precision=precision, dt_mode=ue.UE_DT_GIVEN, dt=dt)
+    mesh.set_plasma(dens, nu)
+    mesh.set_source(ids, amp, w0, 0.0, 0.05)
+    mesh.write_fields(B=b)
+    mesh.step_n(nsteps)
+    Eg, Bg, Jg = mesh.read_fields(j=True)
+    got = (Eg, Bg) + mesh.frame_fields()
+    mesh.close()
+    errs = [_rel(g, r) for g, r in zip(got, ref)] + [_rel(Jg, jref)]
+    print("framed plasma rel L2 (E, B, frame B, Ex, Ey, j):", ["%.2e" % e for e in errs])
+    assert np.linalg.norm(jref) > 0 and np.linalg.norm(ref[2]) > 0
+    assert max(errs) <= tol
+
+
 def test_framed_mesh_refuses_other_variants(ue):
     ms, m = _square(1 / 16)
     mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)
     mesh.frame_attach(4)
     with pytest.raises(ue.UEError):
         mesh.geometry_build(variant=ue.UE_VARIANT_PERSISTENT)
-    mesh.geometry_build()
+    mesh.geometry_build(variant=ue.UE_VARIANT_BLOCKED, block_depth=4)
     with pytest.raises(ue.UEError):
-        mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)
+        mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)     # blocked + frame + plasma
+    mesh.geometry_build()
+    mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)         # plain + frame + plasma
     mesh.close()
 
 
