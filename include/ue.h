@@ -311,8 +311,8 @@ int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* 
  * others form one region advanced block_depth steps at a time by the plain kernels together
  * with the frame (the same results, bit for bit).  dt modes UE_DT_GIVEN and UE_DT_POWER, the
  * power iteration then covering the whole framed system (eq. 20 for the coupled operator).
- * Its sources must be interior edges.  Plasma media (ue_set_plasma) with a frame step with the
- * plain variant; their current runs on the mesh's interior edges, the frame being vacuum.
+ * Its sources must be interior edges.  In plasma media (ue_set_plasma) the current runs on the
+ * mesh's interior edges, the frame and the outer edges being vacuum.
  * ue_write_fields zeroes the frame's fields; ue_read_fields returns E on the mesh's outer
  * edges too; the energy watchdog and ue_energy cover the mesh only.
  * width in [1, 256], order in [1, 8].  Errors: UE_ERR_ARG (arguments, a batch, or an outer

@@ -326,8 +326,13 @@ struct RegionDev {
 };
 // tri.w of updated local triangles and cU of local edges from the mesh's (source flags kept).
 cudaError_t launch_region_coeff(const RegionDev& r, const int4* tri, const float* cU, cudaStream_t s);
-cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, cudaStream_t s);
-cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, cudaStream_t s);
+// Fields of buffer n into the region / the region's owned values into buffer n + k; J (the
+// plasma current) is carried when the region has plasma.
+cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, const float* J,
+                                 cudaStream_t s);
+cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, float* J, cudaStream_t s);
+// pb of the local edges from the mesh's plasma coefficients.
+cudaError_t launch_region_pb(const RegionDev& r, const float* pb, cudaStream_t s);
 
 // Power iteration with a file-scope work array (noalloc.cu).
 int power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,

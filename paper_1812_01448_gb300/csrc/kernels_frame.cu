@@ -73,20 +73,35 @@ __global__ void k_region_coeff(int4* __restrict__ rtri, float* __restrict__ rcU,
     if (i < ne) rcU[i] = cU[egid[i]];
 }
 
-__global__ void k_region_gather(float* __restrict__ rB, float* __restrict__ rU, const int32_t* __restrict__ tgid,
-                                const int32_t* __restrict__ egid, int64_t nt, int64_t ne,
-                                const float* __restrict__ B, const float* __restrict__ U) {
+// rJ / J may be NULL (no plasma)
+__global__ void k_region_gather(float* __restrict__ rB, float* __restrict__ rU, float* __restrict__ rJ,
+                                const int32_t* __restrict__ tgid, const int32_t* __restrict__ egid, int64_t nt,
+                                int64_t ne, const float* __restrict__ B, const float* __restrict__ U,
+                                const float* __restrict__ J) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nt) rB[i] = B[tgid[i]];
-    if (i < ne) rU[i] = U[egid[i]];
+    if (i < ne) {
+        rU[i] = U[egid[i]];
+        if (rJ) rJ[i] = J[egid[i]];
+    }
 }
 
 __global__ void k_region_scatter(const float* __restrict__ rB, const float* __restrict__ rU,
-                                 const int32_t* __restrict__ tgid, const int32_t* __restrict__ egid,
-                                 int64_t nt, int64_t ne, float* __restrict__ B, float* __restrict__ U) {
+                                 const float* __restrict__ rJ, const int32_t* __restrict__ tgid,
+                                 const int32_t* __restrict__ egid, int64_t nt, int64_t ne, float* __restrict__ B,
+                                 float* __restrict__ U, float* __restrict__ J) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nt) B[tgid[i]] = rB[i];
-    if (i < ne) U[egid[i]] = rU[i];
+    if (i < ne) {
+        U[egid[i]] = rU[i];
+        if (rJ) J[egid[i]] = rJ[i];
+    }
+}
+
+__global__ void k_region_pb(float* __restrict__ rpb, const int32_t* __restrict__ egid, int64_t ne,
+                            const float* __restrict__ pb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) rpb[i] = pb[egid[i]];
 }
 
 }  // namespace
@@ -99,19 +114,28 @@ cudaError_t launch_region_coeff(const RegionDev& r, const int4* tri, const float
     return cudaGetLastError();
 }
 
-cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, cudaStream_t s) {
+cudaError_t launch_region_gather(const RegionDev& r, const float* B, const float* U, const float* J,
+                                 cudaStream_t s) {
     const int64_t n = r.dm.n_t > r.dm.n_ei ? r.dm.n_t : r.dm.n_ei;
     if (n == 0) return cudaSuccess;
-    k_region_gather<<<blocks_for(n), kThreads, 0, s>>>((float*)r.dm.B, (float*)r.dm.U, r.tgid, r.egid, r.dm.n_t,
-                                                       r.dm.n_ei, B, U);
+    float* rJ = r.dm.plasma ? (float*)r.dm.J : nullptr;
+    k_region_gather<<<blocks_for(n), kThreads, 0, s>>>((float*)r.dm.B, (float*)r.dm.U, rJ, r.tgid, r.egid,
+                                                       r.dm.n_t, r.dm.n_ei, B, U, J);
     return cudaGetLastError();
 }
 
-cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, cudaStream_t s) {
+cudaError_t launch_region_scatter(const RegionDev& r, float* B, float* U, float* J, cudaStream_t s) {
     const int64_t n = r.n_own_t > r.n_own_e ? r.n_own_t : r.n_own_e;
     if (n == 0) return cudaSuccess;
-    k_region_scatter<<<blocks_for(n), kThreads, 0, s>>>((const float*)r.dm.B, (const float*)r.dm.U, r.tgid, r.egid,
-                                                        r.n_own_t, r.n_own_e, B, U);
+    const float* rJ = r.dm.plasma ? (const float*)r.dm.J : nullptr;
+    k_region_scatter<<<blocks_for(n), kThreads, 0, s>>>((const float*)r.dm.B, (const float*)r.dm.U, rJ, r.tgid,
+                                                        r.egid, r.n_own_t, r.n_own_e, B, U, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_pb(const RegionDev& r, const float* pb, cudaStream_t s) {
+    if (r.dm.n_ei == 0) return cudaSuccess;
+    k_region_pb<<<blocks_for(r.dm.n_ei), kThreads, 0, s>>>((float*)r.dm.pb, r.egid, r.dm.n_ei, pb);
     return cudaGetLastError();
 }
 

@@ -332,13 +332,15 @@ cudaError_t blocked_launch(ue_mesh* m, int kk, int cur, int gbase, cudaStream_t 
     }
     if (e == cudaSuccess && m->has_reg) {
         ue::RegionDev& r = m->reg;
-        e = ue::launch_region_gather(r, (const float*)m->tb.B[cur], (const float*)m->tb.U[cur], rs);
+        e = ue::launch_region_gather(r, (const float*)m->tb.B[cur], (const float*)m->tb.U[cur],
+                                     (const float*)m->tb.J[cur], rs);
         for (int i = 0; i < kk && e == cudaSuccess; ++i) {
             e = ue::launch_step_part(r.dm, 0, gbase + i, rs);
             if (e == cudaSuccess) e = ue::launch_step_part(r.dm, 1, gbase + i, rs);
         }
         if (e == cudaSuccess)
-            e = ue::launch_region_scatter(r, (float*)m->tb.B[cur ^ 1], (float*)m->tb.U[cur ^ 1], rs);
+            e = ue::launch_region_scatter(r, (float*)m->tb.B[cur ^ 1], (float*)m->tb.U[cur ^ 1],
+                                          (float*)m->tb.J[cur ^ 1], rs);
     }
     if (e == cudaSuccess && tiles) e = ue::launch_tb(m->tb, m->dm, kk, cur, gbase, s);
     if (e == cudaSuccess && m->has_reg && tiles) {
@@ -398,6 +400,7 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
     DevMesh& dm = m->dm;
     if (m->plasma_n.empty()) {
         dm.plasma = false;
+        if (m->has_reg) m->reg.dm.plasma = false;
         return UE_OK;
     }
     const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
@@ -421,6 +424,17 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
         UE_CUDA(cudaMemsetAsync(m->tb.J[0], 0, esz * dm.n_ei_pad, s));
         UE_CUDA(cudaMemsetAsync(m->tb.J[1], 0, esz * dm.n_ei_pad, s));
         UE_CUDA(ue::launch_tb_fill(m->tb, dm, s));
+    }
+    if (m->has_reg) {
+        // the region of a framed blocked mesh: its own current and the mesh's coefficients
+        DevMesh& d = m->reg.dm;
+        if (!d.J && !alloc_into(m, d.J, d.n_ei_pad, 4, s)) return fail(UE_ERR_ALLOC, "frame region current");
+        if (!d.pb && !alloc_into(m, d.pb, d.n_ei_pad, 4, s)) return fail(UE_ERR_ALLOC, "frame region coefficient");
+        UE_CUDA(cudaMemsetAsync(d.J, 0, 4 * d.n_ei_pad, s));
+        UE_CUDA(cudaMemsetAsync(d.pb, 0, 4 * d.n_ei_pad, s));
+        UE_CUDA(ue::launch_region_pb(m->reg, (const float*)dm.pb, s));
+        d.pa = dm.pa;
+        d.plasma = true;
     }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
@@ -990,8 +1004,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
             return fail(UE_ERR_ARG, "a framed mesh steps with the plain or the blocked variant");
         if (o.dt_mode == UE_DT_LEARNED)
             return fail(UE_ERR_ARG, "a framed mesh takes its dt from UE_DT_GIVEN or UE_DT_POWER");
-        if (!m->plasma_n.empty() && o.variant == UE_VARIANT_BLOCKED)
-            return fail(UE_ERR_ARG, "plasma media with a frame step with the plain variant");
+
     }
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
@@ -1351,8 +1364,6 @@ int ue_get_dt(const ue_mesh* m, double* dt, double* rho, int32_t* src) {
 int ue_set_plasma(ue_mesh* m, const double* n, double nu) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (m->is_batch) return fail(UE_ERR_ARG, "batches of plasma media are not supported");
-    if (n && m->dm.frame && m->variant == UE_VARIANT_BLOCKED)
-        return fail(UE_ERR_ARG, "plasma media with a frame step with the plain variant");
     if (n && !(nu >= 0)) return fail(UE_ERR_ARG, "collision rate must be >= 0");
     if (n) {
         for (int64_t v = 0; v < m->hm.n_nodes; ++v)

@@ -244,12 +244,32 @@ def test_framed_mesh_refuses_other_variants(ue):
     mesh.frame_attach(4)
     with pytest.raises(ue.UEError):
         mesh.geometry_build(variant=ue.UE_VARIANT_PERSISTENT)
-    mesh.geometry_build(variant=ue.UE_VARIANT_BLOCKED, block_depth=4)
-    with pytest.raises(ue.UEError):
-        mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)     # blocked + frame + plasma
-    mesh.geometry_build()
-    mesh.set_plasma(np.ones(mesh.n_nodes), 0.1)         # plain + frame + plasma
     mesh.close()
+
+
+@pytest.mark.parametrize("tile,k,nsteps", [(256, 4, 45), (4096, 3, 20)])
+def test_blocked_framed_plasma_is_bit_identical_to_plain(ue, tile, k, nsteps):
+    """Plasma with a frame in both launch forms: the region next to the frame carries its own
+    current and the mesh's coefficients; E, B, j and the frame bit for bit."""
+    ms, m = _square()
+    w0 = 2 * math.pi * 20
+    dens = meshgen.plasma_density_nodes(ms.xy, w0)
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    b = _pulse(m)
+    out = []
+    for variant in (ue.UE_VARIANT_PLAIN, ue.UE_VARIANT_BLOCKED):
+        mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=tile)
+        mesh.frame_attach(6)
+        mesh.geometry_build(variant=variant, block_depth=k)
+        mesh.set_plasma(dens, 0.01 * w0)
+        mesh.set_source(ids, amp, w0, 0.0, 0.05)
+        mesh.write_fields(B=b)
+        mesh.step_n(nsteps)
+        out.append(mesh.read_fields(j=True) + mesh.frame_fields())
+        mesh.close()
+    assert np.linalg.norm(out[0][2]) > 0
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
 
 
 @pytest.fixture(scope="module")
