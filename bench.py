@@ -3,7 +3,7 @@
 One bench "step" is one full leap-frog step (E half-step over every interior edge, the line
 source, B half-step over every triangle) of the graded unit-square mesh with an equilateral
 PEC hole (h 2e-4 .. 8e-4, ~4M triangles, FP32 fields, FP64-built coefficients).  By default
-the steps run temporally blocked: greedy tiles of <= 2560 triangles (--tiler kd: KD tiles),
+the steps run temporally blocked: greedy tiles of <= 2500 triangles (--tiler kd: KD tiles),
 8 steps per launch, 512 threads per tile (--variant plain: two kernels per step in RCM order).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
@@ -608,7 +608,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
-    ap.add_argument("--tile-tris", type=int, default=2560)
+    ap.add_argument("--tile-tris", type=int, default=2500)
     ap.add_argument("--frame", type=int, default=0,
                     help="scatterer workload: PML frame of this many cells (open boundary instead "
                          "of the PEC walls)")

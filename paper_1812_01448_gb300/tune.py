@@ -31,7 +31,7 @@ DEFAULT_CANDIDATES = (
     ("blocked", "kd", 2048, 6, 512),
     ("blocked", "kd", 2048, 8, 512),
     ("blocked", "kd", 2048, 8, 1024),
-    ("blocked", "greedy", 2560, 8, 512),
+    ("blocked", "greedy", 2500, 8, 512),
 )
 
 TILERS = {"kd": N.UE_REORDER_KD, "greedy": N.UE_REORDER_GREEDY}

@@ -189,11 +189,11 @@ def test_non_delaunay_mesh_is_rejected(ue):
 @pytest.mark.parametrize("variant", ["plain", "blocked"])
 def test_full_size_scatterer_window(ue, scatterer_window, variant):
     """Full size in the bench's launch configurations (plain: RCM, graphs of 32 steps;
-    blocked: greedy tiles of <= 2560, k = 8, 512 threads) against the oracle on the whole mesh."""
+    blocked: greedy tiles of <= 2500, k = 8, 512 threads) against the oracle on the whole mesh."""
     ms, ops, ids, amp, w0, dt, Eo, Bo = scatterer_window
     blocked = variant == "blocked"
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY if blocked else ue.UE_REORDER_RCM,
-                tile_tris=2560)
+                tile_tris=2500)
     m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt,
                      variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
                      block_depth=8)

@@ -291,14 +291,14 @@ def framed_window(scatterer_window):
 @pytest.mark.parametrize("variant", ["plain", "blocked"])
 def test_full_size_scatterer_with_frame(ue, scatterer_window, framed_window, variant):
     """The bench's framed configurations at full size (3.96M triangles, 16-cell frame, FP32, line
-    source from step 5000; plain: CUDA graphs of 32 steps; blocked: greedy tiles <= 2560, k = 8,
+    source from step 5000; plain: CUDA graphs of 32 steps; blocked: greedy tiles <= 2500, k = 8,
     the region next to the frame beside the blocked kernel): every field within 1e-4 of the
     oracle after 200 steps."""
     ms, ops, ids, amp, w0, dt, _, _ = scatterer_window
     b, ref = framed_window
     blocked = variant == "blocked"
     mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY if blocked else ue.UE_REORDER_RCM,
-                   tile_tris=2560)
+                   tile_tris=2500)
     mesh.frame_attach(16)
     mesh.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, block_depth=8,
                         variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN)
