@@ -44,6 +44,9 @@ L2_BYTES = 129e6
 NCU_TRAFFIC = {
     # (variant, tiler, tile_tris, block_depth, threads, PML frame cells): (bytes per launch,
     # source file, sha1, profile)
+    ("blocked", "greedy", 2500, 8, 512, 0): (306195200, "kernels_tb.cu",
+                                             "74268af160169826e19cf8973928e739eb32c11d",
+                                             "profiles/blocked_k_tbp_scatterer4M.md"),
     ("blocked", "greedy", 2560, 8, 512, 0): (304521643, "kernels_tb.cu",
                                           "74268af160169826e19cf8973928e739eb32c11d",
                                           "profiles/blocked_k_tbp_scatterer4M.md"),
