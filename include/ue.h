@@ -219,7 +219,8 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d);
 /* Learned spectral radius (device pointers, caller-owned; the paper's eq. 20 sets dt from the
  * highest mode, which the network predicts per triangle).
  * ue_rho_features: X[12*n_tris] (float, stored triangle order) and base[n_tris] = log sqrt(K_jj),
- *   K = -L_E L_B, of a built mesh; log rho_hat = max_j (z_j + base_j).
+ *   K = -L_E L_B, of a built mesh without a PML frame (UE_ERR_ARG otherwise);
+ *   log rho_hat = max_j (z_j + base_j).
  * ue_mlp_forward: z[n] for rows X[12*n]; bf16 = 1 tensor cores (BF16 in, FP32 accumulate),
  *   0 = FP32 debug path.  params: UE_MLP_PARAMS floats on the device.
  * ue_mlp_backward: grad[UE_MLP_PARAMS] = sum over m rows of dz[i] * dz_i/dparams for rows[i]
@@ -286,7 +287,8 @@ int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_
  * at B + i*n_tris in caller triangle order, normalised to sum_j S_j B_j^2 = 1 (sign
  * arbitrary).  Synchronous; the work space, about (2 n_tris + n_interior_edges) * 2 n_modes
  * doubles, comes from the mesh's allocator and is returned.
- * Errors: UE_ERR_ARG; UE_ERR_ALLOC; UE_ERR_DUAL if the block loses rank; UE_ERR_CUDA. */
+ * Errors: UE_ERR_ARG (also on a mesh with a PML frame); UE_ERR_ALLOC; UE_ERR_DUAL if the block
+ * loses rank; UE_ERR_CUDA. */
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream);
 

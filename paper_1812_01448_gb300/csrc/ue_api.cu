@@ -1779,6 +1779,8 @@ int ue_get_geometry(ue_mesh* m, double* O, double* S, double* elen, double* d) {
 
 int ue_rho_features(ue_mesh* m, float* X, float* base, void* stream) {
     if (!m || !m->built || !X || !base) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+    // the outer edges of a framed mesh are unknowns the features do not describe
+    if (m->dm.frame) return fail(UE_ERR_ARG, "ue_rho_features: not on a framed mesh");
     cudaStream_t s = (cudaStream_t)stream;
     const int nrc = ensure_tri_nb(m, s);
     if (nrc != UE_OK) return nrc;
@@ -1921,6 +1923,8 @@ int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* 
     if (!m || !m->built || !omega) return fail(UE_ERR_ARG, "geometry not built or NULL omega");
     if (n_modes < 1 || n_modes > 24 || iters < 1)
         return fail(UE_ERR_ARG, "ue_modes: n_modes must be in [1, 24] and iters >= 1");
+    // the modes of the closed cavity; a PML frame makes the operator lossy
+    if (m->dm.frame) return fail(UE_ERR_ARG, "ue_modes: not on a framed mesh");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
     const int64_t nt = h.n_tris, nei = h.n_ei;

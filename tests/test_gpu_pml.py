@@ -244,6 +244,14 @@ def test_framed_mesh_refuses_other_variants(ue):
     mesh.frame_attach(4)
     with pytest.raises(ue.UEError):
         mesh.geometry_build(variant=ue.UE_VARIANT_PERSISTENT)
+    mesh.geometry_build()
+    with pytest.raises(ue.UEError):           # modes of the closed cavity only
+        mesh.modes(2, iters=5)
+    import torch
+    X = torch.empty((mesh.n_tris, 12), dtype=torch.float32, device="cuda")
+    base = torch.empty(mesh.n_tris, dtype=torch.float32, device="cuda")
+    with pytest.raises(ue.UEError):           # features describe unframed meshes
+        mesh.rho_features(X, base)
     mesh.close()
 
 
