@@ -26,7 +26,10 @@ From an order the tables follow (same definitions in the library, separate code)
   (a slot whose value stays 0).
 
 Parity: pinned by tests/test_oracle_mesh.py (valid permutation, contiguous components, a strip
-whose RCM order is known in closed form, bandwidth not above the caller order's on lattices).
+whose RCM order is known in closed form, bandwidth not above the caller order's on lattices; for
+the greedy partition: on a strip the parts are consecutive segments of known sizes with the short
+last one joined, parts are connected and capped with no hanging triangle left where its
+neighbour has room, and at nearly KD's part count the shared boundary is close to KD's, Fig. 6).
 """
 from __future__ import annotations
 
