@@ -11,7 +11,8 @@
 // (dt / h^2) / (1 + sigma dt/2) on cells: the trapezoidal decay of the split-field PML, sigma
 // taken at each field's position.  The mesh's outer edges (interface edges) couple a triangle
 // and a frame cell: U += dt |e| / d (B_R - B_L) in the mesh edge's direction, their values kept
-// in the mesh's U array after its zero slot, where the triangles' edge codes point.
+// after the zero slot of the U array the triangles' edge codes point into: the mesh's, or, in
+// blocked stepping, that of the region stepped with the frame.
 // Every operation is explicitly rounded.
 #pragma once
 
