@@ -160,3 +160,25 @@ def test_frame_refuses_a_boundary_that_is_not_a_divided_rectangle(ue):
         with pytest.raises(ue.UEError):
             m.frame_attach(*bad)
     m.close()
+
+
+@pytest.mark.parametrize("reorder,tile", [(2, 64), (3, 64), (3, 16), (3, 100000)])
+def test_partitions_of_a_mesh_in_two_pieces(ue, reorder, tile):
+    """Two disjoint meshes in one load: RCM runs per component and both partitions cover them;
+    tables and tile offsets bit-exact against the oracle (KD = 2, greedy = 3); a tile larger
+    than the mesh gives one part per the greedy rules."""
+    a = meshgen.cavity_te11_mesh()
+    b = meshgen.random_delaunay(150, seed=12)
+    xy = np.vstack([a.xy, b.xy + [3.0, 0.0]])
+    tris = np.vstack([a.tris, b.tris + a.xy.shape[0]])
+    m = ue.Mesh(xy, tris, reorder=reorder, tile_tris=tile)
+    om_ = om.canonicalize(xy, tris)
+    r = rcm.rcm_order(om_)
+    order, offs = (rcm.kd_order if reorder == 2 else rcm.greedy_order)(om_, r, tile)
+    t = m.tables()
+    ref = rcm.device_tables(om_, order)
+    for k in ("perm_tri", "edge_caller", "edge_tri", "tri_code"):
+        assert np.array_equal(t[k], ref[k]), k
+    assert np.array_equal(m.tiles(), offs)
+    assert np.diff(offs).max() <= tile
+    m.close()
