@@ -329,6 +329,12 @@ int ue_frame_attach(ue_mesh* m, int32_t width, double sigma_max, int32_t order);
  * Either pointer may be NULL.  UE_ERR_ARG without a frame. */
 int ue_frame_get(const ue_mesh* m, int64_t* dims, double* geom);
 
+/* The frame's interface edges (host; after ue_frame_attach): for k in [0, n_interface), in the
+ * order bottom side (by x), top, left (by y), right: edge[k] = the mesh's caller edge id and
+ * cell[k] = the frame cell across it (strip order).  Either pointer may be NULL.  UE_ERR_ARG
+ * without a frame. */
+int ue_frame_interface(const ue_mesh* m, int64_t* edge, int64_t* cell);
+
 /* Frame fields (synchronous, after ue_geometry_build): B[n_cells] = Bx + By per frame cell in
  * strip order; Ex[NX * (NY + 1)]: E on the horizontal side at height J between columns I and
  * I + 1, at Ex[J * NX + I]; Ey[(NX + 1) * NY]: E on the vertical side at column I between rows J

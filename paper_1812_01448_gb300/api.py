@@ -212,6 +212,15 @@ class Mesh:
         out.update(h=float(g[0]), X0=float(g[1]), Y0=float(g[2]), sigma_max=float(g[3]))
         return out
 
+    def frame_interface(self):
+        """(caller edge id, frame cell) per interface edge, in the frame's order."""
+        n = self.frame_info()["n_interface"]
+        e = np.empty(n, np.int64)
+        c = np.empty(n, np.int64)
+        N.check(N.lib().ue_frame_interface(self._h, e.ctypes.data_as(N.PI64), c.ctypes.data_as(N.PI64)),
+                "ue_frame_interface")
+        return e, c
+
     def frame_fields(self, stream=None):
         """(B per frame cell in strip order, Ex [NY+1, NX], Ey [NY, NX+1]) (ue_frame_fields)."""
         f = self.frame_info()

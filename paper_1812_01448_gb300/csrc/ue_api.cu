@@ -1740,6 +1740,16 @@ int ue_frame_get(const ue_mesh* m, int64_t* dims, double* geom) {
     return UE_OK;
 }
 
+int ue_frame_interface(const ue_mesh* m, int64_t* edge, int64_t* cell) {
+    if (!m || m->fr.W == 0) return fail(UE_ERR_ARG, "no frame");
+    const FrameHost& fr = m->fr;
+    for (size_t k = 0; k < fr.itri.size(); ++k) {
+        if (edge) edge[k] = fr.iedge[k];
+        if (cell) cell[k] = fr.icell[k];
+    }
+    return UE_OK;
+}
+
 int ue_frame_fields(ue_mesh* m, double* B, double* Ex, double* Ey, void* stream) {
     if (!m || !m->built || !m->dm.frame) return fail(UE_ERR_ARG, "no frame built");
     cudaStream_t s = (cudaStream_t)stream;

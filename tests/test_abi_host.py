@@ -126,7 +126,7 @@ def test_collinear_and_nonmanifold_rejected(ue):
     assert ei.value.code == -2
 
 
-def test_frame_layout_matches_oracle(ue):
+def test_frame_layout_and_interface_match_oracle(ue):
     from oracle import pml
     ms = meshgen.graded_square(1 / 16, 1 / 16, grade=0.0,
                                holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=5)
@@ -138,6 +138,10 @@ def test_frame_layout_matches_oracle(ue):
     assert info["n_cells"] == fo.n_fc and info["n_interface"] == fo.n_if
     assert abs(info["h"] - fo.h) <= 1e-12 * fo.h
     assert abs(info["sigma_max"] - fo.sigma_max) <= 1e-12 * fo.sigma_max
+    edge, cell = m.frame_interface()
+    cid = {c: k for k, c in enumerate(fo.frame_cells)}
+    assert np.array_equal(edge, [rec[0] for rec in fo.iface])
+    assert np.array_equal(cell, [cid[rec[7]] for rec in fo.iface])
     m.frame_attach(6, sigma_max=0.0)
     assert m.frame_info()["sigma_max"] == 0.0
     m.frame_attach(0)
