@@ -335,6 +335,14 @@ int ue_frame_get(const ue_mesh* m, int64_t* dims, double* geom);
  * without a frame. */
 int ue_frame_interface(const ue_mesh* m, int64_t* edge, int64_t* cell);
 
+/* Blocked stepping of a framed tiled mesh, planned on the host for a given block_depth k:
+ * counts[6] = {tiles, tiles that stay blocked (their rings H_0..H_{k-1} reach no triangle on
+ * the outer edges), triangles owned by the region (the other tiles' triangles), the region's
+ * local triangles (owned plus k rings), its local edges (those with a triangle within k-1
+ * rings), its owned edges (those whose smaller stored triangle it owns)}.  UE_ERR_ARG without a
+ * frame or tiles, or for block_depth outside 1..15. */
+int ue_frame_region(const ue_mesh* m, int32_t block_depth, int64_t* counts);
+
 /* Frame fields (synchronous, after ue_geometry_build): B[n_cells] = Bx + By per frame cell in
  * strip order; Ex[NX * (NY + 1)]: E on the horizontal side at height J between columns I and
  * I + 1, at Ex[J * NX + I]; Ey[(NX + 1) * NY]: E on the vertical side at column I between rows J

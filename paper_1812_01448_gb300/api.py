@@ -221,6 +221,15 @@ class Mesh:
                 "ue_frame_interface")
         return e, c
 
+    def frame_region(self, block_depth: int):
+        """Host plan of blocked stepping with the frame (ue_frame_region): dict of counts."""
+        c = np.zeros(6, np.int64)
+        N.check(N.lib().ue_frame_region(self._h, int(block_depth), c.ctypes.data_as(N.PI64)),
+                "ue_frame_region")
+        keys = ("tiles", "blocked_tiles", "region_owned_tris", "region_tris", "region_edges",
+                "region_owned_edges")
+        return {k: int(v) for k, v in zip(keys, c)}
+
     def frame_fields(self, stream=None):
         """(B per frame cell in strip order, Ex [NY+1, NX], Ey [NY, NX+1]) (ue_frame_fields)."""
         f = self.frame_info()

@@ -586,17 +586,10 @@ int bake_source_mesh(ue_mesh* m, cudaStream_t s) {
 
 int upload_tileset(ue_mesh* m, cudaStream_t s);
 
-int upload_tiles(ue_mesh* m, cudaStream_t s) {
-    std::string err;
-    if (m->fr.W == 0) {
-        int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
-        if (rc != UE_OK) return fail(rc, err);
-        return upload_tileset(m, s);
-    }
-    // framed: a tile whose rings H_0 .. H_{k-1} reach a triangle on the mesh's outer edges
-    // joins the region; the others stay blocked tiles
+// Framed blocked stepping: a tile whose rings H_0 .. H_{k-1} reach a triangle on the mesh's
+// outer edges joins the region (owned[j] for its triangles); the others stay blocked tiles.
+void region_plan(const ue_mesh* m, int k, std::vector<char>& interior, std::vector<char>& owned) {
     const HostMesh& h = m->hm;
-    const int k = m->block_depth;
     const int64_t ntiles = (int64_t)h.tile_tri_off.size() - 1;
     std::vector<int32_t> dist(h.n_tris, -1);
     std::vector<int64_t> front, next;
@@ -621,7 +614,8 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
             }
         front.swap(next);
     }
-    std::vector<char> interior(ntiles, 1), owned(h.n_tris, 0);
+    interior.assign(ntiles, 1);
+    owned.assign(h.n_tris, 0);
     for (int64_t t = 0; t < ntiles; ++t)
         for (int64_t j = h.tile_tri_off[t]; j < h.tile_tri_off[t + 1]; ++j)
             if (dist[j] >= 0) {
@@ -631,6 +625,19 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     for (int64_t t = 0; t < ntiles; ++t)
         if (!interior[t])
             for (int64_t j = h.tile_tri_off[t]; j < h.tile_tri_off[t + 1]; ++j) owned[j] = 1;
+}
+
+int upload_tiles(ue_mesh* m, cudaStream_t s) {
+    std::string err;
+    if (m->fr.W == 0) {
+        int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
+        if (rc != UE_OK) return fail(rc, err);
+        return upload_tileset(m, s);
+    }
+    std::vector<char> interior, owned;
+    region_plan(m, m->block_depth, interior, owned);
+    const HostMesh& h = m->hm;
+    const int k = m->block_depth;
     int rc = ue::build_tiles(h, k, m->ts, err, &interior);
     if (rc != UE_OK) return fail(rc, err);
     if ((rc = upload_tileset(m, s)) != UE_OK) return rc;
@@ -1747,6 +1754,27 @@ int ue_frame_interface(const ue_mesh* m, int64_t* edge, int64_t* cell) {
         if (edge) edge[k] = fr.iedge[k];
         if (cell) cell[k] = fr.icell[k];
     }
+    return UE_OK;
+}
+
+int ue_frame_region(const ue_mesh* m, int32_t block_depth, int64_t* counts) {
+    if (!m || m->fr.W == 0 || !counts) return fail(UE_ERR_ARG, "no frame or NULL counts");
+    if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the mesh has no tiles");
+    if (block_depth < 1 || block_depth > 15) return fail(UE_ERR_ARG, "block_depth must be in 1..15");
+    std::vector<char> interior, owned;
+    region_plan(m, block_depth, interior, owned);
+    ue::Region R;
+    std::string err;
+    const int rc = ue::build_region(m->hm, owned, block_depth, m->fr.islot, m->fr.ineg, R, err);
+    if (rc != UE_OK) return fail(rc, err);
+    int64_t n_int = 0;
+    for (char c : interior) n_int += c;
+    counts[0] = (int64_t)interior.size();
+    counts[1] = n_int;
+    counts[2] = R.n_own_t;
+    counts[3] = (int64_t)R.tgid.size();
+    counts[4] = (int64_t)R.egid.size();
+    counts[5] = R.n_own_e;
     return UE_OK;
 }
 

@@ -186,3 +186,53 @@ def test_partitions_of_a_mesh_in_two_pieces(ue, reorder, tile):
     assert np.array_equal(m.tiles(), offs)
     assert np.diff(offs).max() <= tile
     m.close()
+
+
+@pytest.mark.parametrize("tile,k", [(128, 8), (256, 4), (400, 3), (4096, 4)])
+def test_frame_region_plan(ue, tile, k):
+    """The host plan of blocked stepping with a frame against a breadth-first search written
+    here: tiles within k-1 rings of a triangle on the outer edges form the region; its local
+    triangles are k rings around it, its local edges those with a triangle within k-1 rings."""
+    ms = meshgen.graded_square(1 / 32, 1 / 32, grade=0.0,
+                               holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=5)
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=tile)
+    m.frame_attach(6)
+    got = m.frame_region(k)
+    t = m.tables()
+    off = m.tiles()
+    om_ = om.canonicalize(ms.xy, ms.tris)
+    stored = np.empty(m.n_tris, np.int64)
+    stored[t["perm_tri"]] = np.arange(m.n_tris)
+    edge, _ = m.frame_interface()
+    seeds = {int(stored[om_.R[e] if om_.R[e] >= 0 else om_.L[e]]) for e in edge}
+    R, L = t["edge_tri"][:, 0].astype(np.int64), t["edge_tri"][:, 1].astype(np.int64)
+    nbr = [[] for _ in range(m.n_tris)]
+    for r, l in zip(R, L):
+        nbr[r].append(l)
+        nbr[l].append(r)
+
+    def rings(start, depth):
+        lvl = {s: 0 for s in start}
+        front = list(start)
+        for d in range(1, depth + 1):
+            nxt = []
+            for u in front:
+                for w in nbr[u]:
+                    if w not in lvl:
+                        lvl[w] = d
+                        nxt.append(w)
+            front = nxt
+        return lvl
+
+    near = rings(seeds, k - 1)
+    tile_of = np.searchsorted(off, np.arange(m.n_tris), side="right") - 1
+    region_tiles = {int(tile_of[j]) for j in near}
+    owned = np.isin(tile_of, list(region_tiles))
+    lvl = rings(set(np.flatnonzero(owned).tolist()), k)
+    edges = [i for i in range(len(R)) if min(lvl.get(R[i], 99), lvl.get(L[i], 99)) <= k - 1]
+    own_e = [i for i in edges if owned[min(R[i], L[i])]]
+    want = {"tiles": len(off) - 1, "blocked_tiles": len(off) - 1 - len(region_tiles),
+            "region_owned_tris": int(owned.sum()), "region_tris": len(lvl),
+            "region_edges": len(edges), "region_owned_edges": len(own_e)}
+    assert got == want
+    m.close()
