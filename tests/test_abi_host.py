@@ -236,3 +236,21 @@ def test_frame_region_plan(ue, tile, k):
             "region_edges": len(edges), "region_owned_edges": len(own_e)}
     assert got == want
     m.close()
+
+
+def test_bench_partition_stats_match_the_oracle(ue):
+    """The Fig. 6 quantities the bench reports (parts, part sizes, shared edges) from the
+    library's tables agree with the oracle's definitions on the same partition."""
+    import bench
+    ms = meshgen.graded_square(0.01, 0.03, grade=0.3,
+                               holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=9)
+    for reorder, fn in ((ue.UE_REORDER_KD, rcm.kd_order), (ue.UE_REORDER_GREEDY, rcm.greedy_order)):
+        m = ue.Mesh(ms.xy, ms.tris, reorder=reorder, tile_tris=300)
+        st = bench.partition_stats(m)
+        om_ = om.canonicalize(ms.xy, ms.tris)
+        order, offs = fn(om_, rcm.rcm_order(om_), 300)
+        sizes = np.diff(offs)
+        assert st["parts"] == sizes.size and st["tris_max"] == sizes.max()
+        assert abs(st["tris_mean"] - sizes.mean()) < 1e-9 and abs(st["tris_rms"] - sizes.std()) < 1e-9
+        assert st["shared_edges"] == rcm.shared_edges(om_, order, offs)
+        m.close()
