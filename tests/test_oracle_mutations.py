@@ -44,8 +44,8 @@ def _yee_error(cls):
 
 
 def test_frame_interface_dual_length_is_pinned():
-    """The interface edge's dual length without the frame cell's half (d = (O - C) . n only)
-    breaks Yee's closed form for the framed lattice."""
+    """The interface edge's dual length with the frame cell's half counted twice
+    (d = (O - C) . n + h) breaks Yee's closed form for the framed lattice."""
     assert _yee_error(pml.FramedOperators) < 1e-12
     bad = _mutant(pml.FramedOperators, "d = float(np.dot(geom.O[t] - C, nin) + 0.5 * h)",
                   "d = float(np.dot(geom.O[t] - C, nin) + 1.0 * h)")
