@@ -95,3 +95,65 @@ def test_framed_plasma_drain_sign_is_pinned():
 
     assert resid(pml.step_plasma) < 1e-12
     assert resid(bad) > 1e-6
+
+
+def test_greedy_hanging_refinement_is_pinned():
+    """Without the hanging-triangle moves, triangles hanging on a neighbouring part that has room
+    are left: the invariant the holed-mesh test checks."""
+    bad = _mutant(rcm.greedy_order,
+                  "if len(others) == 2 and others[0] == others[1] and size[others[0]] < tile_tris:",
+                  "if False:")
+
+    def hanging_with_room(fn):
+        ms = meshgen.graded_square(0.01, 0.03, grade=0.3,
+                                   holes=[meshgen.polygon_triangle((0.5, 0.5), 0.2)], seed=9)
+        m = om.canonicalize(ms.xy, ms.tris)
+        order, offs = fn(m, rcm.rcm_order(m), 64)
+        sizes = np.diff(offs)
+        part = np.empty(m.n_tris, np.int64)
+        for p in range(len(offs) - 1):
+            part[order[offs[p]:offs[p + 1]]] = p
+        n = 0
+        for u, ws in enumerate(rcm.dual_adjacency(m)):
+            other = [int(part[w]) for w in ws if part[w] != part[u]]
+            if len(ws) == 3 and len(other) == 2 and other[0] == other[1] and sizes[other[0]] < 64:
+                n += 1
+        return n
+
+    assert hanging_with_room(rcm.greedy_order) == 0
+    assert hanging_with_room(bad) > 0
+
+
+def test_relax_height_spring_sign_is_pinned():
+    """A height spring that pushes the apex the wrong way is not -grad E."""
+    from oracle import relax
+    bad = _mutant(relax.forces, "np.add.at(F, v, -g)", "np.add.at(F, v, g)")
+    ms = meshgen.random_delaunay(40, seed=3)
+    t = relax.orient_ccw(ms.xy, ms.tris)
+    h = np.full(ms.xy.shape[0], relax.uniform_size(ms.xy, t))
+    edges, L0, H0 = relax.rest_lengths(t, h)
+    xy = ms.xy.copy()
+    eps = 1e-6
+    G = np.zeros_like(xy)
+    for i in range(xy.shape[0]):
+        for k in range(2):
+            xp = xy.copy(); xp[i, k] += eps
+            xm = xy.copy(); xm[i, k] -= eps
+            G[i, k] = (relax.energy(xp, t, edges, L0, H0) - relax.energy(xm, t, edges, L0, H0)) / (2 * eps)
+    free = np.zeros(xy.shape[0], bool)
+    for fn, ok in ((relax.forces, True), (bad, False)):
+        F = fn(xy, t, edges, L0, H0, free)
+        assert (np.abs(F + G).max() < 1e-6 * np.abs(G).max()) == ok
+
+
+def test_triangle_operator_sign_is_pinned():
+    """L_E with the orientation signs flipped breaks the adjointness of eq. 10."""
+    bad = _mutant(operators.Operators, "vals = (-mesh.tri_sign * geom.elen[mesh.tri_edge] / geom.S[:, None]).reshape(-1)",
+                  "vals = (mesh.tri_sign * geom.elen[mesh.tri_edge] / geom.S[:, None]).reshape(-1)")
+    ms = meshgen.cavity_te11_mesh()
+    m = om.canonicalize(ms.xy, ms.tris)
+    for cls, ok in ((operators.Operators, True), (bad, False)):
+        o = cls(m)
+        A = (o.L_B.multiply(o.w_E[:, None])).tocsr()
+        Bm = (o.L_E.multiply(o.w_B[:, None])).T.tocsr()
+        assert (np.abs((A + Bm).toarray()).max() <= 1e-15 * np.abs(A.toarray()).max()) == ok
