@@ -157,3 +157,36 @@ def test_triangle_operator_sign_is_pinned():
         A = (o.L_B.multiply(o.w_E[:, None])).tocsr()
         Bm = (o.L_E.multiply(o.w_B[:, None])).T.tocsr()
         assert (np.abs((A + Bm).toarray()).max() <= 1e-15 * np.abs(A.toarray()).max()) == ok
+
+
+def _small_ops():
+    ms = meshgen.cavity_lattice(9, 5, 1.0, 0.5, jitter=0.2, dual_floor=0.05, seed=7)
+    return ms, operators.Operators(om.canonicalize(ms.xy, ms.tris))
+
+
+def test_source_time_is_pinned():
+    """Evaluating the soft source at n dt instead of (n + 1/2) dt changes the first step."""
+    from oracle import leapfrog as lf
+    bad = _mutant(lf.step, "t = (st.n + 0.5) * dt", "t = st.n * dt")
+    ms, ops = _small_ops()
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    src = lf.Source(ids, amp, 2 * math.pi * 3, 0.2, 0.1)
+    dt = 1e-3
+    g = math.sin(src.omega0 * 0.5 * dt) * math.exp(-((0.5 * dt - 0.2) / 0.1) ** 2)
+    exp = np.zeros(ops.mesh.n_edges)
+    exp[ids] = dt * amp * g
+    for fn, ok in ((lf.step, True), (bad, False)):
+        E = ops.extend(fn(ops, lf.initial_state(ops), dt, source=src).E)
+        assert np.allclose(E, exp, rtol=1e-15, atol=0) == ok
+
+
+def test_power_iteration_metric_is_pinned():
+    """A Rayleigh quotient without the S metric of eq. 7 is no longer a lower bound on the
+    dense rho (the operator is self-adjoint only in that metric)."""
+    bad = _mutant(spectral.power_iteration, "lam = float(np.dot(S * v, w))", "lam = float(np.dot(v, w))")
+    ms, ops = _small_ops()
+    rho_dense = spectral.dense_rho(ops)
+    good, _ = spectral.power_iteration(ops, 200, seed=3)
+    assert rho_dense * (1 - 2e-3) <= good <= rho_dense * (1 + 1e-12)
+    worse, _ = bad(ops, 200, seed=3)
+    assert not (rho_dense * (1 - 2e-3) <= worse <= rho_dense * (1 + 1e-12))
