@@ -343,6 +343,14 @@ int ue_frame_interface(const ue_mesh* m, int64_t* edge, int64_t* cell);
  * frame or tiles, or for block_depth outside 1..15. */
 int ue_frame_region(const ue_mesh* m, int32_t block_depth, int64_t* counts);
 
+/* The frame's own state for checkpoint and resume (synchronous, after ue_geometry_build):
+ * Bx, By[n_cells] (strip order), Ex[NX * (NY + 1)], Ey[(NX + 1) * NY] in the layout of
+ * ue_frame_fields (E = circulation / h, 0 on sides that are not frame unknowns).  write = 0
+ * reads them out, write = 1 sets them (call it after ue_write_fields, which zeroes the frame;
+ * the mesh's outer edges travel with ue_read_fields / ue_write_fields).  All four pointers are
+ * required.  UE_ERR_ARG without a built frame. */
+int ue_frame_state(ue_mesh* m, double* Bx, double* By, double* Ex, double* Ey, int32_t write, void* stream);
+
 /* Frame fields (synchronous, after ue_geometry_build): B[n_cells] = Bx + By per frame cell in
  * strip order; Ex[NX * (NY + 1)]: E on the horizontal side at height J between columns I and
  * I + 1, at Ex[J * NX + I]; Ey[(NX + 1) * NY]: E on the vertical side at column I between rows J

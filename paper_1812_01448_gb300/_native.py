@@ -71,6 +71,7 @@ SIGNATURES = [
     ("ue_frame_get", C.c_int, [P, PI64, PD]),
     ("ue_frame_interface", C.c_int, [P, PI64, PI64]),
     ("ue_frame_region", C.c_int, [P, C.c_int32, PI64]),
+    ("ue_frame_state", C.c_int, [P, PD, PD, PD, PD, C.c_int32, P]),
     ("ue_frame_fields", C.c_int, [P, PD, PD, PD, P]),
     ("ue_get_geometry", C.c_int, [P, PD, PD, PD, PD]),
     ("ue_rho_features", C.c_int, [P, P, P, P]),

@@ -230,6 +230,20 @@ class Mesh:
                 "region_owned_edges")
         return {k: int(v) for k, v in zip(keys, c)}
 
+    def frame_state(self, state=None, stream=None):
+        """Without `state`: the frame's (Bx, By, Ex, Ey) for a checkpoint.  With it: set them
+        (after write_fields, which zeroes the frame) (ue_frame_state)."""
+        f = self.frame_info()
+        if state is None:
+            Bx, By = np.empty(f["n_cells"]), np.empty(f["n_cells"])
+            Ex, Ey = np.empty((f["NY"] + 1, f["NX"])), np.empty((f["NY"], f["NX"] + 1))
+            N.check(N.lib().ue_frame_state(self._h, _dptr(Bx), _dptr(By), _dptr(Ex), _dptr(Ey), 0,
+                                           _stream(stream)), "ue_frame_state")
+            return Bx, By, Ex, Ey
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in state]
+        N.check(N.lib().ue_frame_state(self._h, *(_dptr(a) for a in arrs), 1, _stream(stream)),
+                "ue_frame_state")
+
     def frame_fields(self, stream=None):
         """(B per frame cell in strip order, Ex [NY+1, NX], Ey [NY, NX+1]) (ue_frame_fields)."""
         f = self.frame_info()

@@ -310,6 +310,9 @@ cudaError_t launch_frame_iface_in(const FrameDev& f, const DevMesh& m, const int
                                   const double* ielen, const double* E_caller, cudaStream_t s);
 cudaError_t launch_frame_out(const FrameDev& f, bool f64, double* B, double* Ex, double* Ey,
                              cudaStream_t s);
+// The frame's state (Bx, By, E on its sides) out of or into FP64 arrays (device pointers).
+cudaError_t launch_frame_state(const FrameDev& f, bool f64, double* Bx, double* By, double* Ex, double* Ey,
+                               bool write, cudaStream_t s);
 
 // Blocked stepping of a framed mesh: the tiles whose k-ring halo stays off the mesh's outer
 // edges run in the blocked kernel; the others form one region (its owned triangles plus k rings,

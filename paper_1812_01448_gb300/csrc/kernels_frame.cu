@@ -104,7 +104,56 @@ __global__ void k_region_pb(float* __restrict__ rpb, const int32_t* __restrict__
     if (i < ne) rpb[i] = pb[egid[i]];
 }
 
+template <typename T>
+__global__ void k_frame_state(FrameDev f, double* __restrict__ Bx, double* __restrict__ By,
+                              double* __restrict__ Ex, double* __restrict__ Ey, bool write) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T* bx = (T*)f.Bx;
+    T* by = (T*)f.By;
+    T* H = (T*)f.H;
+    T* V = (T*)f.V;
+    if (t < f.n_fc) {
+        if (write) {
+            bx[t] = (T)Bx[t];
+            by[t] = (T)By[t];
+        } else {
+            Bx[t] = (double)bx[t];
+            By[t] = (double)by[t];
+        }
+    }
+    const int64_t nh = (int64_t)f.NX * (f.NY + 1), nv = (int64_t)(f.NX + 1) * f.NY;
+    if (t < nh) {
+        const int I = (int)(t % f.NX), J = (int)(t / f.NX);
+        const bool unk = frame_is_cell(f, I, J - 1) && frame_is_cell(f, I, J);
+        if (write) {
+            if (unk) H[t] = (T)(Ex[t] * f.h);
+        } else {
+            Ex[t] = unk ? (double)H[t] / f.h : 0.0;
+        }
+    }
+    if (t < nv) {
+        const int I = (int)(t % (f.NX + 1)), J = (int)(t / (f.NX + 1));
+        const bool unk = frame_is_cell(f, I - 1, J) && frame_is_cell(f, I, J);
+        if (write) {
+            if (unk) V[t] = (T)(Ey[t] * f.h);
+        } else {
+            Ey[t] = unk ? (double)V[t] / f.h : 0.0;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_frame_state(const FrameDev& f, bool f64, double* Bx, double* By, double* Ex, double* Ey,
+                               bool write, cudaStream_t s) {
+    int64_t n = f.n_fc;
+    const int64_t nh = (int64_t)f.NX * (f.NY + 1), nv = (int64_t)(f.NX + 1) * f.NY;
+    if (nh > n) n = nh;
+    if (nv > n) n = nv;
+    if (f64) k_frame_state<double><<<blocks_for(n), kThreads, 0, s>>>(f, Bx, By, Ex, Ey, write);
+    else k_frame_state<float><<<blocks_for(n), kThreads, 0, s>>>(f, Bx, By, Ex, Ey, write);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_region_coeff(const RegionDev& r, const int4* tri, const float* cU, cudaStream_t s) {
     const int64_t n = r.dm.n_t > r.dm.n_ei ? r.dm.n_t : r.dm.n_ei;

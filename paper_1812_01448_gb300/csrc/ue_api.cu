@@ -1778,6 +1778,35 @@ int ue_frame_region(const ue_mesh* m, int32_t block_depth, int64_t* counts) {
     return UE_OK;
 }
 
+int ue_frame_state(ue_mesh* m, double* Bx, double* By, double* Ex, double* Ey, int32_t write, void* stream) {
+    if (!m || !m->built || !m->dm.frame) return fail(UE_ERR_ARG, "no frame built");
+    if (!Bx || !By || !Ex || !Ey) return fail(UE_ERR_ARG, "ue_frame_state needs all four arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ue::FrameDev& f = m->fd;
+    const int64_t nh = (int64_t)f.NX * (f.NY + 1), nv = (int64_t)(f.NX + 1) * f.NY;
+    double *tx = nullptr, *ty = nullptr, *th = nullptr, *tv = nullptr;
+    if (!alloc_into(m, tx, f.n_fc, 8, s) || !alloc_into(m, ty, f.n_fc, 8, s) || !alloc_into(m, th, nh, 8, s) ||
+        !alloc_into(m, tv, nv, 8, s))
+        return fail(UE_ERR_ALLOC, "frame state buffers");
+    const bool f64 = m->precision == UE_PREC_FP64;
+    if (write) {
+        UE_CUDA(cudaMemcpyAsync(tx, Bx, 8 * f.n_fc, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(ty, By, 8 * f.n_fc, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(th, Ex, 8 * nh, cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(tv, Ey, 8 * nv, cudaMemcpyHostToDevice, s));
+        UE_CUDA(ue::launch_frame_state(f, f64, tx, ty, th, tv, true, s));
+    } else {
+        UE_CUDA(ue::launch_frame_state(f, f64, tx, ty, th, tv, false, s));
+        UE_CUDA(cudaMemcpyAsync(Bx, tx, 8 * f.n_fc, cudaMemcpyDeviceToHost, s));
+        UE_CUDA(cudaMemcpyAsync(By, ty, 8 * f.n_fc, cudaMemcpyDeviceToHost, s));
+        UE_CUDA(cudaMemcpyAsync(Ex, th, 8 * nh, cudaMemcpyDeviceToHost, s));
+        UE_CUDA(cudaMemcpyAsync(Ey, tv, 8 * nv, cudaMemcpyDeviceToHost, s));
+    }
+    UE_CUDA(cudaStreamSynchronize(s));
+    for (double* p : {tx, ty, th, tv}) dev_release(m, p, s);
+    return UE_OK;
+}
+
 int ue_frame_fields(ue_mesh* m, double* B, double* Ex, double* Ey, void* stream) {
     if (!m || !m->built || !m->dm.frame) return fail(UE_ERR_ARG, "no frame built");
     cudaStream_t s = (cudaStream_t)stream;

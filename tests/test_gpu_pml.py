@@ -238,6 +238,41 @@ def test_framed_plasma_matches_oracle(ue, precision, nsteps, tol):
     assert max(errs) <= tol
 
 
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_framed_checkpoint_resume_is_bit_identical(ue, variant):
+    """Fields, step and the frame's own state (ue_frame_state) saved after 23 steps and
+    restored into a fresh mesh continue exactly as the uninterrupted run."""
+    ms, m = _square()
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    code = ue.UE_VARIANT_BLOCKED if variant == "blocked" else ue.UE_VARIANT_PLAIN
+
+    def fresh():
+        mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)
+        mesh.frame_attach(6)
+        mesh.geometry_build(variant=code, block_depth=4)
+        mesh.set_source(ids, amp, 2 * math.pi * 20, 0.0, 0.05)
+        return mesh
+
+    a = fresh()
+    a.write_fields(B=_pulse(m))
+    a.step_n(23)
+    E, B, _ = a.read_fields()
+    state = a.frame_state()
+    step = a.get_step()
+    a.step_n(37)
+    want = a.read_fields()[:2] + a.frame_fields()
+    a.close()
+    b = fresh()
+    b.write_fields(E=E, B=B)
+    b.frame_state(state)
+    b.set_step(step)
+    b.step_n(37)
+    got = b.read_fields()[:2] + b.frame_fields()
+    b.close()
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+
+
 def test_framed_mesh_refuses_other_variants(ue):
     ms, m = _square(1 / 16)
     mesh = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=256)
