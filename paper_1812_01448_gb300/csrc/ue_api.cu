@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device.cuh"
 #include "ue_internal.h"
 
@@ -27,6 +29,14 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+
+// An NVTX range for the life of a scope (a no-op unless a profiler is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // PML frame attached by ue_frame_attach (host side; the kernels are in kernels_frame.cu).
 // Interface edge k: the mesh's outer edges, bottom side first (k = 0 .. nx-1 by x), then top,
@@ -876,6 +886,7 @@ const char* ue_last_error(void) { return g_err.c_str(); }
 int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
                  const ue_options* opt, ue_alloc_fn alloc, ue_free_fn free_fn, void* alloc_ctx,
                  ue_mesh** out) {
+    Range nvtx_range("ue_mesh_load: ingest");
     if (!out) return fail(UE_ERR_ARG, "out is NULL");
     *out = nullptr;
     if ((alloc == nullptr) != (free_fn == nullptr))
@@ -980,6 +991,7 @@ int frame_tables(ue_mesh* m, double dt, cudaStream_t s) {
 }
 
 int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
+    Range nvtx_range("ue_geometry_build");
     if (!m) return fail(UE_ERR_ARG, "mesh is NULL");
     ue_options d;
     ue_options_default(&d);
@@ -1091,6 +1103,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
             return fail(UE_ERR_ALLOC, "power iteration work space");
     }
     UE_CUDA(cudaStreamSynchronize(s));
+    Range nvtx_dt("ue_geometry_build: dt, coefficients, tiles");
     const auto t_dt0 = std::chrono::steady_clock::now();
     m->rho_lo = m->rho_hi = m->rho_hat = 0;
     bool need_power = o.dt_mode == UE_DT_POWER;
@@ -1410,6 +1423,7 @@ int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, 
 }
 
 int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream) {
+    Range nvtx_range("ue_write_fields");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
@@ -1443,6 +1457,7 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
 }
 
 int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
+    Range nvtx_range("ue_step_n");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 0) return fail(UE_ERR_ARG, "n_steps < 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1522,6 +1537,7 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
 }
 
 int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
+    Range nvtx_range("ue_read_fields");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
@@ -1973,6 +1989,7 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
 int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
                   const double* h_nodes, int32_t iters, int32_t flip_every, double tau,
                   double* xy_out, int32_t* tris_out, int64_t* n_flips, void* stream) {
+    Range nvtx_range("ue_mesh_relax");
     if (!xy || !tris || !xy_out || !tris_out || n_nodes < 3 || n_tris < 1 || iters < 0 || flip_every < 0)
         return fail(UE_ERR_ARG, "ue_mesh_relax: bad arguments");
     if (n_nodes >= (int64_t)1 << 31 || 3 * n_tris >= (int64_t)1 << 31)
@@ -1987,6 +2004,7 @@ int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_
 
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream) {
+    Range nvtx_range("ue_modes");
     if (!m || !m->built || !omega) return fail(UE_ERR_ARG, "geometry not built or NULL omega");
     if (n_modes < 1 || n_modes > 24 || iters < 1)
         return fail(UE_ERR_ARG, "ue_modes: n_modes must be in [1, 24] and iters >= 1");
