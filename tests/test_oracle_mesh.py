@@ -249,3 +249,19 @@ def test_greedy_and_kd_share_about_the_same_boundary():
     _, o3 = rcm.greedy_order(m, r, 200)
     n3 = len(o3) - 1
     assert n3 & (n3 - 1) != 0
+
+
+def test_kd_splits_along_the_longer_side():
+    """Median splits along the longer side of the parts' centroid box: on a long thin lattice
+    (16 x 2 squares) four KD parts are disjoint slabs in x, each a quarter of the triangles,
+    sharing only the 2 edges that each of the three cuts crosses."""
+    ms = meshgen.right_split_lattice(17, 3, 16.0, 2.0)      # 64 triangles
+    m = om.canonicalize(ms.xy, ms.tris)
+    order, offs = rcm.kd_order(m, rcm.rcm_order(m), 16)
+    assert offs.tolist() == [0, 16, 32, 48, 64]
+    cx = m.xy[m.tris].mean(axis=1)[:, 0]
+    spans = [(cx[order[a:b]].min(), cx[order[a:b]].max()) for a, b in zip(offs[:-1], offs[1:])]
+    spans.sort()
+    assert all(spans[i][1] < spans[i + 1][0] for i in range(3))
+    # each cut crosses the strip's 2 rows of squares: 2 vertical edges per cut
+    assert rcm.shared_edges(m, order, offs) == 3 * 2

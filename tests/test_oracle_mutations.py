@@ -190,3 +190,33 @@ def test_power_iteration_metric_is_pinned():
     assert rho_dense * (1 - 2e-3) <= good <= rho_dense * (1 + 1e-12)
     worse, _ = bad(ops, 200, seed=3)
     assert not (rho_dense * (1 - 2e-3) <= worse <= rho_dense * (1 + 1e-12))
+
+
+def _kd_slabs_ok(kd):
+    ms = meshgen.right_split_lattice(17, 3, 16.0, 2.0)
+    m = om.canonicalize(ms.xy, ms.tris)
+    order, offs = kd(m, rcm.rcm_order(m), 16)
+    cx = m.xy[m.tris].mean(axis=1)[:, 0]
+    spans = sorted((cx[order[a:b]].min(), cx[order[a:b]].max()) for a, b in zip(offs[:-1], offs[1:]))
+    return (offs.tolist() == [0, 16, 32, 48, 64] and all(spans[i][1] < spans[i + 1][0] for i in range(3))
+            and rcm.shared_edges(m, order, offs) == 6)
+
+
+def test_kd_split_axis_is_pinned():
+    """Splitting along the SHORTER side of the centroid box breaks the slab pin."""
+    assert _kd_slabs_ok(rcm.kd_order)
+    bad = _mutant(rcm.kd_order, "key = cx if ex >= ey else cy", "key = cy if ex >= ey else cx")
+    assert not _kd_slabs_ok(bad)
+
+
+def test_rcm_start_rule_is_pinned():
+    """Starting a component at its triangle of MAXIMUM degree breaks the strip's closed form."""
+    bad = _mutant(rcm.rcm_order, "start = min(comp, key=lambda v: (deg[v], v))",
+                  "start = max(comp, key=lambda v: (deg[v], -v))")
+    ms = meshgen.right_split_lattice(7, 2, 6.0, 1.0)
+    m = om.canonicalize(ms.xy, ms.tris)
+    path = [1, 0]
+    for c in range(1, 6):
+        path += [2 * c + 1, 2 * c]
+    assert rcm.rcm_order(m).tolist() == path[::-1]
+    assert bad(m).tolist() != path[::-1]
