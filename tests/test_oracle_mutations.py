@@ -220,3 +220,52 @@ def test_rcm_start_rule_is_pinned():
         path += [2 * c + 1, 2 * c]
     assert rcm.rcm_order(m).tolist() == path[::-1]
     assert bad(m).tolist() != path[::-1]
+
+
+def test_mlp_backward_layer_transpose_is_pinned():
+    """Back-propagating through W2 transposed (d2 @ W2.T) is caught by central differences of
+    the first layer's gradient."""
+    from oracle import mlp
+    bad = _mutant(mlp.backward, "d1 = (d2 @ W2) * (a1 > 0)", "d1 = (d2 @ W2.T) * (a1 > 0)")
+    rng = np.random.default_rng(0)
+    p = mlp.init_params(3) + 0.01 * rng.standard_normal(mlp.N_PARAMS)
+    X = rng.standard_normal((7, 12))
+    c = rng.standard_normal(7)
+    z, cache = mlp.forward(p, X)
+    idx = range(0, 64 * 12, 37)                       # entries of W1
+    h = 1e-6
+
+    def worst(back):
+        g = back(p, cache, c)
+        err = 0.0
+        for i in idx:
+            e = np.zeros(mlp.N_PARAMS)
+            e[i] = h
+            fd = (np.dot(c, mlp.forward(p + e, X)[0]) - np.dot(c, mlp.forward(p - e, X)[0])) / (2 * h)
+            err = max(err, abs(fd - g[i]) / max(1.0, abs(g[i])))
+        return err
+
+    assert worst(mlp.backward) <= 1e-6
+    assert worst(bad) > 1e-3
+
+
+def test_lawson_incircle_sign_is_pinned():
+    """Flipping edges whose opposite vertex lies OUTSIDE the circumcircle does not reach Qhull's
+    Delaunay triangulation."""
+    from oracle import relax
+    bad_in = _mutant(relax._in_circle, "return det > 1e-10 * s * s", "return det < -1e-10 * s * s")
+    ns = dict(vars(relax))
+    ns["_in_circle"] = bad_in
+    src = textwrap.dedent(inspect.getsource(relax.lawson_flips))
+    exec(compile(src, "<mutant of lawson_flips>", "exec"), ns)
+    bad = ns["lawson_flips"]
+    from test_oracle_relax import _scramble
+    ms = meshgen.random_delaunay(150, seed=9)
+    xy = ms.xy
+    want = {tuple(sorted(r)) for r in ms.tris}
+    start = np.asarray(_scramble(xy, relax.orient_ccw(xy, ms.tris), 150, seed=2))
+    assert {tuple(sorted(r)) for r in start} != want
+    good_t, _ = relax.lawson_flips(xy, start)
+    bad_t, _ = bad(xy, start)
+    assert {tuple(sorted(r)) for r in good_t} == want
+    assert {tuple(sorted(r)) for r in bad_t} != want
