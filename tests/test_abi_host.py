@@ -254,3 +254,24 @@ def test_bench_partition_stats_match_the_oracle(ue):
         assert abs(st["tris_mean"] - sizes.mean()) < 1e-9 and abs(st["tris_rms"] - sizes.std()) < 1e-9
         assert st["shared_edges"] == rcm.shared_edges(om_, order, offs)
         m.close()
+
+
+def test_frame_calls_refuse_bad_arguments(ue):
+    ms = meshgen.graded_square(1 / 16, 1 / 16, grade=0.0, seed=5)
+    plain = ue.Mesh(ms.xy, ms.tris)                                   # no tiles, no frame
+    for call in (lambda: plain.frame_region(4), lambda: plain.frame_interface(), lambda: plain.frame_info()):
+        with pytest.raises(ue.UEError):
+            call()
+    plain.frame_attach(4)
+    with pytest.raises(ue.UEError):                                   # a frame but no tiles
+        plain.frame_region(4)
+    tiled = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=128)
+    tiled.frame_attach(4)
+    for k in (0, 16):
+        with pytest.raises(ue.UEError):
+            tiled.frame_region(k)
+    assert tiled.frame_region(15)["tiles"] == tiled.tiles().size - 1
+    for m in (plain, tiled):
+        with pytest.raises(ue.UEError):                               # nothing built yet
+            m.frame_fields()
+        m.close()
