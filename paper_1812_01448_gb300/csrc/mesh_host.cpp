@@ -54,15 +54,26 @@ int canonicalize(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, 
         c.tri[3 * j + 1] = v1;
         c.tri[3 * j + 2] = v2;
     }
-    // half-edges sorted by (low, high) key
+    // half-edges in (low, high) order: counted by low node, then each node's few sorted by
+    // (high, half-edge), the same order as one sort by (low * nn + high, half-edge)
     const int64_t nh = 3 * nt;
     std::vector<std::pair<int64_t, int64_t>> he(nh);
-    for (int64_t h = 0; h < nh; ++h) {
-        const int64_t j = h / 3, q = h % 3;
-        const int64_t a = c.tri[3 * j + q], b = c.tri[3 * j + (q + 1) % 3];
-        he[h] = {std::min(a, b) * nn + std::max(a, b), h};
+    {
+        std::vector<int64_t> start(nn + 1, 0);
+        for (int64_t h = 0; h < nh; ++h) {
+            const int64_t j = h / 3, q = h % 3;
+            ++start[std::min(c.tri[3 * j + q], c.tri[3 * j + (q + 1) % 3]) + 1];
+        }
+        for (int64_t v = 0; v < nn; ++v) start[v + 1] += start[v];
+        std::vector<int64_t> at(start.begin(), start.end() - 1);
+        for (int64_t h = 0; h < nh; ++h) {
+            const int64_t j = h / 3, q = h % 3;
+            const int64_t a = c.tri[3 * j + q], b = c.tri[3 * j + (q + 1) % 3];
+            const int64_t lo = std::min(a, b);
+            he[at[lo]++] = {lo * nn + std::max(a, b), h};
+        }
+        for (int64_t v = 0; v < nn; ++v) std::sort(he.begin() + start[v], he.begin() + start[v + 1]);
     }
-    std::sort(he.begin(), he.end());
     c.tri_edge.assign(nh, -1);
     c.tri_neg.assign(nh, 0);
     c.edges.clear();
@@ -209,10 +220,13 @@ void kd_order(const Canon& c, const double* xy, const std::vector<int64_t>& rcm_
             y1 = std::max(y1, cy[j]);
         }
         const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? cx : cy;
-        std::sort(ids.begin() + p.lo, ids.begin() + p.hi, [&](int64_t u, int64_t v) {
+        // only the set below the median matters (both halves are split again or sorted by RCM
+        // position), and (key, RCM position) is a strict total order: a selection gives the
+        // same sets as a full sort
+        const int64_t mid = p.lo + n / 2;
+        std::nth_element(ids.begin() + p.lo, ids.begin() + mid, ids.begin() + p.hi, [&](int64_t u, int64_t v) {
             return key[u] != key[v] ? key[u] < key[v] : pos[u] < pos[v];
         });
-        const int64_t mid = p.lo + n / 2;
         stack.push_back({mid, p.hi});   // right part, processed after the left one
         stack.push_back({p.lo, mid});
     }
@@ -399,15 +413,28 @@ int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int6
     }
     std::vector<int64_t> new_of(n_tris);
     for (int64_t j = 0; j < n_tris; ++j) new_of[hm.perm_tri[j]] = j;
-    // interior edges numbered by (min, max) stored triangle id
+    // interior edges numbered by (min, max) stored triangle id: counted by the smaller
+    // triangle (at most 3 edges each), then each bucket sorted by the larger one
     std::vector<std::pair<std::pair<int64_t, int64_t>, int64_t>> ie;
-    ie.reserve(ne);
-    for (int64_t e = 0; e < ne; ++e)
-        if (c.R[e] >= 0 && c.L[e] >= 0) {
-            const int64_t r = new_of[c.R[e]], l = new_of[c.L[e]];
-            ie.push_back({{std::min(r, l), std::max(r, l)}, e});
-        }
-    std::sort(ie.begin(), ie.end());
+    {
+        std::vector<int64_t> start(n_tris + 1, 0);
+        int64_t n_int = 0;
+        for (int64_t e = 0; e < ne; ++e)
+            if (c.R[e] >= 0 && c.L[e] >= 0) {
+                ++start[std::min(new_of[c.R[e]], new_of[c.L[e]]) + 1];
+                ++n_int;
+            }
+        for (int64_t j = 0; j < n_tris; ++j) start[j + 1] += start[j];
+        std::vector<int64_t> at(start.begin(), start.end() - 1);
+        ie.resize(n_int);
+        for (int64_t e = 0; e < ne; ++e)
+            if (c.R[e] >= 0 && c.L[e] >= 0) {
+                const int64_t r = new_of[c.R[e]], l = new_of[c.L[e]];
+                const int64_t lo = std::min(r, l);
+                ie[at[lo]++] = {{lo, std::max(r, l)}, e};
+            }
+        for (int64_t j = 0; j < n_tris; ++j) std::sort(ie.begin() + start[j], ie.begin() + start[j + 1]);
+    }
     const int64_t n_ei = (int64_t)ie.size();
     hm.n_ei = n_ei;
     hm.edge_caller.resize(n_ei);
