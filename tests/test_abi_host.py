@@ -94,6 +94,49 @@ def test_greedy_tiles_bit_exact_against_oracle(ue, tile):
         m.close()
 
 
+@pytest.mark.parametrize("reorder", [0, 1, 2, 3])
+def test_unused_nodes_keep_tables_bit_exact(ue, reorder):
+    # nodes that no triangle uses, before and after the used ones: they shift the caller ids
+    # that order the edges but must create no edge
+    ms = meshgen.random_delaunay(300, seed=3)
+    extra = np.random.default_rng(0).random((50, 2)) * 10 + 5
+    xy = np.vstack([extra[:20], ms.xy, extra[20:]])
+    tris = ms.tris + 20
+    kw = dict(reorder=reorder, tile_tris=40) if reorder >= 2 else dict(reorder=reorder)
+    m = ue.Mesh(xy, tris, **kw)
+    t = m.tables()
+    o = om.canonicalize(xy, tris)
+    if reorder == 0:
+        order = np.arange(o.n_tris)
+    elif reorder == 1:
+        order = rcm.rcm_order(o)
+    elif reorder == 2:
+        order, _ = rcm.kd_order(o, rcm.rcm_order(o), 40)
+    else:
+        order, _ = rcm.greedy_order(o, rcm.rcm_order(o), 40)
+    ref = rcm.device_tables(o, order)
+    assert m.n_edges == o.n_edges == om.canonicalize(ms.xy, ms.tris).n_edges
+    for k in ("perm_tri", "edge_caller", "edge_tri", "tri_code"):
+        assert np.array_equal(t[k], ref[k]), k
+    m.close()
+
+
+def test_smallest_meshes(ue):
+    # no triangle: refused on both sides; one triangle: three PEC edges, no unknown
+    ms = meshgen.cavity_te11_mesh()
+    with pytest.raises(ue.UEError) as ei:
+        ue.Mesh(ms.xy, np.zeros((0, 3), np.int64))
+    assert ei.value.code == -1
+    with pytest.raises(om.MeshError):
+        om.canonicalize(ms.xy, np.zeros((0, 3), np.int64))
+    xy = np.array([[0, 0], [1, 0], [0, 1.0]])
+    m = ue.Mesh(xy, np.array([[0, 2, 1]]))
+    o = om.canonicalize(xy, np.array([[0, 2, 1]]))
+    assert (m.n_tris, m.n_edges, m.n_ei) == (1, 3, 0) == (o.n_tris, o.n_edges, 0)
+    assert m.tables()["edge_caller"].size == 0
+    m.close()
+
+
 def test_tiles_empty_without_partition(ue):
     ms = meshgen.cavity_te11_mesh()
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_RCM)
