@@ -269,3 +269,71 @@ def test_lawson_incircle_sign_is_pinned():
     bad_t, _ = bad(xy, start)
     assert {tuple(sorted(r)) for r in good_t} == want
     assert {tuple(sorted(r)) for r in bad_t} != want
+
+
+def _triangulate_with(**swap):
+    """oracle.triangulate.triangulate compiled with some of its helpers replaced."""
+    from oracle import triangulate as tr
+    ns = dict(vars(tr))
+    ns.update(swap)
+    src = textwrap.dedent(inspect.getsource(tr.triangulate))
+    exec(compile(src, "<mutant of triangulate>", "exec"), ns)
+    return ns["triangulate"]
+
+
+def _refused_by_pins(run, check):
+    try:
+        check(*run())
+    except AssertionError:
+        return True
+    return False
+
+
+def test_lawson_requeue_is_pinned():
+    """A Lawson pass that does not look again at the four edges around each flip stops short
+    of the empty-circle definition."""
+    from oracle import triangulate as tr
+    bad = _triangulate_with(lawson=_mutant(tr.lawson, "todo += [(c, a), (a, d), (d, b), (b, c)]", "pass"))
+    caught = 0
+    for seed in range(6):
+        xy = np.random.default_rng(seed).random((20, 2))
+        want = tr.delaunay_brute(xy)
+        assert np.array_equal(tr.triangulate(xy)[0], want)
+        caught += not np.array_equal(bad(xy)[0], want)
+    assert caught >= 3
+
+
+def test_flip_refinement_retry_is_pinned():
+    """Dropping a crossing edge whose quadrilateral is not convex, instead of trying it again
+    after the others, does not restore the segments of a zigzag through a cloud."""
+    from oracle import triangulate as tr
+    from test_oracle_triangulate import _zigzag_case, check_cdt, hull_area2
+    xy, segs = _zigzag_case()
+    bad = _triangulate_with(recover_segment=_mutant(tr.recover_segment, "queue.append((a, b))", "pass"))
+    check_cdt(xy, tr.triangulate(xy, segs)[0], segs, area2=hull_area2(xy))
+    assert _refused_by_pins(lambda: (xy, bad(xy, segs)[0], segs, hull_area2(xy)), check_cdt)
+
+
+def test_region_flood_stops_at_segments_is_pinned():
+    """A flood that crosses segments empties the whole square instead of the hole."""
+    from oracle import triangulate as tr
+    from test_oracle_triangulate import check_cdt, polygon_area2, square_with_hole
+    xy, segs, ol, hl = square_with_hole()
+    area = polygon_area2(xy, ol) - polygon_area2(xy, hl)
+    bad = _triangulate_with(drop_regions=_mutant(
+        tr.drop_regions, "if j is not None and j not in gone and frozenset((a, b)) not in fixed:",
+        "if j is not None and j not in gone:"))
+    check_cdt(xy, tr.triangulate(xy, segs, holes=[[0.5, 0.5]])[0], segs, area2=area)
+    assert _refused_by_pins(lambda: (xy, bad(xy, segs, holes=[[0.5, 0.5]])[0], segs, area), check_cdt)
+
+
+def test_sweep_strict_visibility_is_pinned():
+    """Joining hull edges that the new node sees only at a grazing angle (collinear) makes flat
+    triangles on a lattice."""
+    from oracle import triangulate as tr
+    from test_oracle_triangulate import check_cdt, hull_area2
+    g = np.stack(np.meshgrid(np.arange(5), np.arange(4)), -1).reshape(-1, 2) * 0.25
+    bad_sweep = _mutant(tr.sweep_triangulation, "p) < 0 for i in range(m)]", "p) <= 0 for i in range(m)]")
+    bad = _triangulate_with(sweep_triangulation=bad_sweep)
+    check_cdt(g, tr.triangulate(g)[0], area2=hull_area2(g))
+    assert _refused_by_pins(lambda: (g, bad(g)[0], (), hull_area2(g)), check_cdt)
