@@ -253,6 +253,26 @@ int ue_rho_loss(const float* best, const float* target, int32_t n_seg, float* dz
  * of its local triangles and edges over those steps, else 0. */
 int ue_profile_steps(ue_mesh* m, int64_t n_steps, void* stream, double* ms, double* bytes);
 
+/* Mesh generation (Section 3, "Mesh generation"; Fig. 5a): the Delaunay triangulation of a
+ * node cloud over its convex hull, with geometry segments restored by flipping the edges that
+ * cross them, then every other edge made locally Delaunay again (Lawson), so that the result is
+ * the constrained Delaunay triangulation; then the triangles reachable from a hole point
+ * without crossing a segment are dropped, and with UE_TRI_DROP_EXTERIOR those reachable from a
+ * hull edge that is not a segment.  Orientation and in-circle tests are exact, so the result is
+ * unique where no four nodes are cocircular, and the same on every host.
+ * xy: n_nodes*2 doubles (n_nodes >= 3, no node repeated, not all collinear); segs: n_segs
+ * pairs of node ids (may be NULL when n_segs = 0); holes: n_holes points (x, y) inside the
+ * regions to drop.  tris (caller-owned, cap_tris*3 int32): the triangles, counter-clockwise;
+ * a triangulation of n nodes has at most 2 n - 5 triangles, so cap_tris = 2 n_nodes always
+ * suffices.  *n_tris: the count written (or needed, when cap_tris is too small: UE_ERR_ARG).
+ * *n_flips (may be NULL): flips made by the segment refinement.  Host only; no GPU call.
+ * Errors: UE_ERR_ARG (sizes, ids, a node on a segment, crossing segments, a hole point outside
+ * the hull, cap_tris too small); UE_ERR_DEGENERATE (a repeated node, all nodes collinear). */
+#define UE_TRI_DROP_EXTERIOR 1
+int ue_triangulate(const double* xy, int64_t n_nodes, const int32_t* segs, int64_t n_segs,
+                   const double* holes, int64_t n_holes, int32_t flags, int32_t* tris, int64_t cap_tris,
+                   int64_t* n_tris, int64_t* n_flips);
+
 /* Mesh optimisation by the jello model with flip refinement (Section 3, "Mesh generation"):
  * nodes joined by unit springs along the triangle edges (rest length (h_a + h_b)/2) and along
  * the heights (vertex to the midpoint of its opposite edge, rest length sqrt(3)/2 times the

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("ue_modes", C.c_int, [P, C.c_int32, C.c_int32, C.c_uint32, PD, PD, P]),
     ("ue_mesh_relax", C.c_int, [PD, I64, PI32, I64, PD, C.c_int32, C.c_int32, C.c_double, PD, PI32,
                                 PI64, P]),
+    ("ue_triangulate", C.c_int, [PD, I64, PI32, I64, PD, I64, C.c_int32, PI32, I64, PI64, PI64]),
     ("ue_stats", C.c_int, [P, C.POINTER(Stats)]),
     ("ue_last_error", C.c_char_p, []),
     ("ue_mesh_free", None, [P]),

@@ -339,6 +339,23 @@ def mesh_relax(xy, tris, iters: int, flip_every: int = 20, tau: float = 0.05, h_
     return xo, to, nf.value
 
 
+def triangulate(xy, segs=None, holes=None, drop_exterior: bool = False):
+    """Constrained Delaunay triangulation of a node cloud (ue_triangulate): (tris CCW, flips)."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    if xy.ndim != 2 or xy.shape[1] != 2:
+        raise ValueError("xy must be (n, 2)")
+    sg = np.ascontiguousarray(np.zeros((0, 2)) if segs is None else segs, np.int32).reshape(-1, 2)
+    ho = np.ascontiguousarray(np.zeros((0, 2)) if holes is None else holes, np.float64).reshape(-1, 2)
+    cap = 2 * xy.shape[0]
+    out = np.empty((cap, 3), np.int32)
+    nt = C.c_int64()
+    nf = C.c_int64()
+    N.check(N.lib().ue_triangulate(_dptr(xy), xy.shape[0], sg.ctypes.data_as(N.PI32), sg.shape[0],
+                                   _dptr(ho), ho.shape[0], 1 if drop_exterior else 0,
+                                   out.ctypes.data_as(N.PI32), cap, C.byref(nt), C.byref(nf)), "ue_triangulate")
+    return out[:nt.value].copy(), nf.value
+
+
 def batch_create(meshes, stream=None) -> Mesh:
     """ue_batch_create: one Mesh object advancing all the given built meshes together.
 

@@ -2002,6 +2002,28 @@ int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_
     return UE_OK;
 }
 
+int ue_triangulate(const double* xy, int64_t n_nodes, const int32_t* segs, int64_t n_segs,
+                   const double* holes, int64_t n_holes, int32_t flags, int32_t* tris, int64_t cap_tris,
+                   int64_t* n_tris, int64_t* n_flips) {
+    Range nvtx_range("ue_triangulate");
+    if (!tris || !n_tris || cap_tris < 0 || (flags & ~UE_TRI_DROP_EXTERIOR))
+        return fail(UE_ERR_ARG, "ue_triangulate: bad arguments");
+    std::vector<int32_t> out;
+    std::string err;
+    int rc;
+    try {
+        rc = ue::triangulate(xy, n_nodes, segs, n_segs, holes, n_holes, flags, out, n_flips, err);
+    } catch (const std::bad_alloc&) {
+        rc = UE_ERR_ARG;
+        err = "ue_triangulate: out of host memory";
+    }
+    if (rc != UE_OK) return fail(rc, err);
+    *n_tris = (int64_t)out.size() / 3;
+    if (*n_tris > cap_tris) return fail(UE_ERR_ARG, "ue_triangulate: cap_tris too small");
+    std::memcpy(tris, out.data(), sizeof(int32_t) * out.size());
+    return UE_OK;
+}
+
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream) {
     Range nvtx_range("ue_modes");

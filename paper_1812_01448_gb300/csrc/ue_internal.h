@@ -63,4 +63,8 @@ int build_region(const HostMesh& hm, const std::vector<char>& owned, int k, cons
 int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
                     int reorder, int tile_tris, HostMesh& hm, std::string& err);
 
+// Constrained Delaunay triangulation of a node cloud (ue_triangulate); out: 3 ids per triangle.
+int triangulate(const double* xy, int64_t nn, const int32_t* segs, int64_t n_segs, const double* holes,
+                int64_t n_holes, int flags, std::vector<int32_t>& out, int64_t* n_flips, std::string& err);
+
 }  // namespace ue
