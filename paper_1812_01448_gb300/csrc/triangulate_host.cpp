@@ -43,65 +43,102 @@ inline void two_prod(double a, double b, double& x, double& y) {
     y = std::fma(a, b, -x);
 }
 
-// Expansions: components of increasing magnitude, non-overlapping, zeros removed.
-using Exp = std::vector<double>;
+// Expansions: components of increasing magnitude, non-overlapping, zeros removed; at most N
+// components, held on the stack (each operation's worst-case length is known statically).
+template <int N>
+struct Exp {
+    double v[N];
+    int n = 0;
+};
 
-// e + b (growing the expansion by one double).
-void grow(const Exp& e, double b, Exp& h) {
-    h.clear();
+template <int N, int M>
+void copy(const Exp<M>& e, Exp<N>& h) {
+    static_assert(N >= M, "expansion capacity");
+    h.n = e.n;
+    std::memcpy(h.v, e.v, sizeof(double) * e.n);
+}
+
+// h = e + b (growing the expansion by one double; h has room for e.n + 1 components)
+template <int N, int M>
+void grow(const Exp<M>& e, double b, Exp<N>& h) {
+    h.n = 0;
     double q = b;
-    for (double ei : e) {
+    for (int i = 0; i < e.n; ++i) {
         double s, t;
-        two_sum(q, ei, s, t);
-        if (t != 0.0) h.push_back(t);
+        two_sum(q, e.v[i], s, t);
+        if (t != 0.0) h.v[h.n++] = t;
         q = s;
     }
-    if (q != 0.0 || h.empty()) h.push_back(q);
+    if (q != 0.0 || h.n == 0) h.v[h.n++] = q;
 }
 
-void add(Exp& e, const Exp& f) {
-    Exp h;
-    for (double fj : f) {
-        grow(e, fj, h);
-        e.swap(h);
+// out = e + f, by growing e with each component of f (two buffers used in turn)
+template <int N, int M, int K>
+void sum(const Exp<M>& e, const Exp<K>& f, Exp<N>& out) {
+    static_assert(N >= M + K, "expansion capacity");
+    if (f.n == 0) {
+        copy(e, out);
+        return;
+    }
+    Exp<N> tmp;
+    Exp<N>* dst = (f.n - 1) % 2 == 0 ? &out : &tmp;   // so that the last grow lands in out
+    Exp<N>* src = dst == &out ? &tmp : &out;
+    grow(e, f.v[0], *dst);
+    for (int j = 1; j < f.n; ++j) {
+        std::swap(dst, src);
+        grow(*src, f.v[j], *dst);
     }
 }
 
-// e * b
-Exp scale(const Exp& e, double b) {
-    Exp r, h;
-    for (double ei : e) {
+// out = e * b
+template <int M>
+void scale(const Exp<M>& e, double b, Exp<2 * M>& out) {
+    Exp<2 * M> tmp;
+    out.n = 0;
+    for (int i = 0; i < e.n; ++i) {
         double p, q;
-        two_prod(ei, b, p, q);
-        grow(r, q, h);
-        grow(h, p, r);
+        two_prod(e.v[i], b, p, q);
+        grow(out, q, tmp);
+        grow(tmp, p, out);
     }
-    return r;
 }
 
-Exp mul(const Exp& e, const Exp& f) {
-    Exp r;
-    for (double fj : f) add(r, scale(e, fj));
-    return r;
+// out = e * f
+template <int M, int K>
+void mul(const Exp<M>& e, const Exp<K>& f, Exp<2 * M * K>& out) {
+    Exp<2 * M * K> tmp;
+    Exp<2 * M> s;
+    Exp<2 * M * K>* acc = &out;
+    Exp<2 * M * K>* nxt = &tmp;
+    out.n = 0;
+    for (int j = 0; j < f.n; ++j) {
+        scale(e, f.v[j], s);
+        for (int i = 0; i < s.n; ++i) {
+            grow(*acc, s.v[i], *nxt);
+            std::swap(acc, nxt);
+        }
+    }
+    if (acc != &out) copy(*acc, out);
 }
 
-Exp diff(double a, double b) {
+Exp<2> diff(double a, double b) {
     double x, y;
     two_sum(a, -b, x, y);
-    Exp e;
-    if (y != 0.0) e.push_back(y);
-    e.push_back(x);
+    Exp<2> e;
+    if (y != 0.0) e.v[e.n++] = y;
+    e.v[e.n++] = x;
     return e;
 }
 
-Exp neg(Exp e) {
-    for (double& x : e) x = -x;
-    return e;
+template <int N>
+void negate(Exp<N>& e) {
+    for (int i = 0; i < e.n; ++i) e.v[i] = -e.v[i];
 }
 
-int sign_of(const Exp& e) {
-    for (size_t i = e.size(); i-- > 0;)
-        if (e[i] != 0.0) return e[i] > 0 ? 1 : -1;
+template <int N>
+int sign_of(const Exp<N>& e) {
+    for (int i = e.n; i-- > 0;)
+        if (e.v[i] != 0.0) return e.v[i] > 0 ? 1 : -1;
     return 0;
 }
 
@@ -111,9 +148,30 @@ int orient(const double* a, const double* b, const double* c) {
     const double l = acx * bcy, r = acy * bcx, det = l - r;
     // relative rounding error of this form is below 4e-16; accept far above it
     if (std::fabs(det) > 1e-14 * (std::fabs(l) + std::fabs(r))) return det > 0 ? 1 : -1;
-    Exp d = mul(diff(a[0], c[0]), diff(b[1], c[1]));
-    add(d, neg(mul(diff(a[1], c[1]), diff(b[0], c[0]))));
+    Exp<8> p, q;
+    mul(diff(a[0], c[0]), diff(b[1], c[1]), p);
+    mul(diff(a[1], c[1]), diff(b[0], c[0]), q);
+    negate(q);
+    Exp<16> d;
+    sum(p, q, d);
     return sign_of(d);
+}
+
+// x1 y2 - y1 x2
+void cross(const Exp<2>& x1, const Exp<2>& y1, const Exp<2>& x2, const Exp<2>& y2, Exp<16>& out) {
+    Exp<8> p, q;
+    mul(x1, y2, p);
+    mul(y1, x2, q);
+    negate(q);
+    sum(p, q, out);
+}
+
+// x^2 + y^2
+void lift(const Exp<2>& x, const Exp<2>& y, Exp<16>& out) {
+    Exp<8> p, q;
+    mul(x, x, p);
+    mul(y, y, q);
+    sum(p, q, out);
 }
 
 // +1 where d lies strictly inside the circle through the CCW triangle (a, b, c).
@@ -128,21 +186,23 @@ int incircle(const double* a, const double* b, const double* c, const double* d)
                         cl * (std::fabs(adx * bdy) + std::fabs(ady * bdx));
     // relative rounding error of this form is below 1.2e-15; accept far above it
     if (std::fabs(det) > 1e-13 * perm) return det > 0 ? 1 : -1;
-    const Exp ax = diff(a[0], d[0]), ay = diff(a[1], d[1]), bx = diff(b[0], d[0]);
-    const Exp by = diff(b[1], d[1]), cx = diff(c[0], d[0]), cy = diff(c[1], d[1]);
-    auto lift = [](const Exp& x, const Exp& y) {
-        Exp r = mul(x, x);
-        add(r, mul(y, y));
-        return r;
-    };
-    auto cross = [](const Exp& x1, const Exp& y1, const Exp& x2, const Exp& y2) {
-        Exp r = mul(x1, y2);
-        add(r, neg(mul(y1, x2)));
-        return r;
-    };
-    Exp s = mul(lift(ax, ay), cross(bx, by, cx, cy));
-    add(s, mul(lift(bx, by), cross(cx, cy, ax, ay)));
-    add(s, mul(lift(cx, cy), cross(ax, ay, bx, by)));
+    const Exp<2> ax = diff(a[0], d[0]), ay = diff(a[1], d[1]), bx = diff(b[0], d[0]);
+    const Exp<2> by = diff(b[1], d[1]), cx = diff(c[0], d[0]), cy = diff(c[1], d[1]);
+    Exp<16> l, x;
+    Exp<512> s0, s1, s2;
+    lift(ax, ay, l);
+    cross(bx, by, cx, cy, x);
+    mul(l, x, s0);
+    lift(bx, by, l);
+    cross(cx, cy, ax, ay, x);
+    mul(l, x, s1);
+    lift(cx, cy, l);
+    cross(ax, ay, bx, by, x);
+    mul(l, x, s2);
+    Exp<1024> s01;
+    Exp<1536> s;
+    sum(s0, s1, s01);
+    sum(s01, s2, s);
     return sign_of(s);
 }
 
