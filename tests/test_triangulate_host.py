@@ -184,3 +184,17 @@ def test_capacity_and_flags_are_checked(ue):
     rc = N.lib().ue_triangulate(xy.ctypes.data_as(N.PD), 50, None, 0, None, 0, 4,
                                 out.ctypes.data_as(N.PI32), 10, ctypes.byref(nt), None)
     assert rc == -1
+
+
+def test_exterior_flag_and_repeated_segments_change_nothing_on_a_closed_hull(ue):
+    # every hull edge of the holed square is a segment: dropping the exterior drops nothing,
+    # and listing segments twice, either way round, changes nothing
+    xy, segs, ol, hl = square_with_hole(seed=15)
+    want, _ = ue.triangulate(xy, segs, holes=[[0.5, 0.5]])
+    got, _ = ue.triangulate(xy, segs, holes=[[0.5, 0.5]], drop_exterior=True)
+    assert np.array_equal(tr.canonical(got), tr.canonical(want))
+    twice = np.vstack([segs, segs[::-1, ::-1]])
+    got, _ = ue.triangulate(xy, twice, holes=[[0.5, 0.5]])
+    assert np.array_equal(tr.canonical(got), tr.canonical(want))
+    o, _ = tr.triangulate(xy, twice, holes=[[0.5, 0.5]], drop_exterior=True)
+    assert np.array_equal(o, tr.canonical(want))
