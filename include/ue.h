@@ -279,9 +279,12 @@ int ue_triangulate(const double* xy, int64_t n_nodes, const int32_t* segs, int64
  * triangle's mean rest edge) move by strongly damped first-order steps x += tau F,
  * F = -grad of the spring energy, each step clamped to 0.1 of the node's shortest rest edge and
  * to 0.15 of the smallest height of its triangles (so that no triangle turns over);
- * the boundary nodes (on an edge of one triangle: the input geometry) stay.  Every flip_every
- * steps (0: never) interior edges that are not locally Delaunay are flipped (Lawson), so the
- * triangulation follows the nodes; boundary edges are never flipped.  On a randomly seeded node
+ * the boundary nodes (on an edge of one triangle: the input geometry) stay, and so do the
+ * n_anchors nodes listed in anchors (the seeding nodes of interior geometry: an object's contour
+ * meshed on both sides, a path; may be NULL when n_anchors = 0).  Every flip_every steps
+ * (0: never) interior edges that are not locally Delaunay are flipped (Lawson), so the
+ * triangulation follows the nodes; boundary edges and the n_segs node-id pairs in segs (the
+ * geometry's edges; may be NULL when n_segs = 0) are never flipped.  On a randomly seeded node
  * cloud this lowers rho(M) severalfold, allowing a larger dt (eq. 20); nearly cocircular pairs
  * can remain, so check the result with ue_geometry_build (UE_ERR_DUAL).
  * xy: n_nodes*2 doubles; tris: n_tris*3 int32, either orientation.  h_nodes: NULL (uniform:
@@ -289,11 +292,22 @@ int ue_triangulate(const double* xy, int64_t n_nodes, const int32_t* segs, int64
  * tau in (0, 0.1] (explicit steps of this spring system are stable below about 0.1).
  * xy_out, tris_out (CCW) have the input sizes; node numbering is kept.  *n_flips (may be NULL):
  * flips done.  Host arrays; synchronous; device buffers by cudaMalloc, freed on return.
- * Errors: UE_ERR_ARG; UE_ERR_DEGENERATE (a zero-area input triangle, or a triangle inverted by
+ * Errors: UE_ERR_ARG (sizes, ids out of range); UE_ERR_DEGENERATE (a zero-area input triangle, or a triangle inverted by
  * the relaxation: lower tau); UE_ERR_CUDA. */
 int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
                   const double* h_nodes, int32_t iters, int32_t flip_every, double tau,
+                  const int32_t* anchors, int64_t n_anchors, const int32_t* segs, int64_t n_segs,
                   double* xy_out, int32_t* tris_out, int64_t* n_flips, void* stream);
+
+/* The remesh step of ue_mesh_relax alone, on the host (Section 3): interior edges that are not
+ * locally Delaunay (the node across one triangle's edge inside its circle, beyond a relative
+ * 1e-10 margin) are flipped until none is left; boundary edges and the n_segs node-id pairs in
+ * segs are kept.  xy: n_nodes*2 doubles; tris: n_tris*3 int32, either orientation; tris_out
+ * (caller-owned, n_tris*3): the triangles, CCW, in the input's slots.  *n_flips (may be NULL):
+ * flips done.  No GPU call.  Errors: UE_ERR_ARG (sizes, ids); UE_ERR_DEGENERATE (a zero-area
+ * triangle). */
+int ue_mesh_flip(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris, const int32_t* segs,
+                 int64_t n_segs, int32_t* tris_out, int64_t* n_flips);
 
 /* The highest eigenmodes of the semi-discrete system (Section 2): omega_i^2 are the largest
  * eigenvalues of K = -L_E L_B in the S-weighted product, found by the "complex time" method

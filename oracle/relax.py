@@ -21,7 +21,10 @@ Readings (where the paper gives the idea but not the formulas):
   nodes on the boundary (on an edge of one triangle) do not move;
 * remesh: Lawson flips of the interior edges that are not locally Delaunay (the vertex
   opposite in one triangle inside the other's circumcircle, beyond a relative 1e-10 margin),
-  until none is left; boundary edges are never flipped, so holes keep their contours.
+  until none is left; boundary edges are never flipped, so holes keep their contours;
+* anchoring: the seeding nodes of the input geometry stay put.  Boundary nodes are anchored
+  always; nodes of interior geometry (an object's contour meshed on both sides, a path) are
+  named by the caller, and so are the geometry edges between them, which the remesh keeps.
 
 Parity: pinned by tests/test_oracle_relax.py (forces against central differences of E, the
 equilateral lattice as a fixed point, E non-increasing along the flow, and Lawson flips of a
@@ -103,14 +106,18 @@ def forces(xy, tris, edges, L0, H0, bnd) -> np.ndarray:
     return F
 
 
-def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int = 0):
+def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int = 0, anchors=(),
+          keep=()):
     """(new positions, new triangles (CCW), number of flips) after `iters` Euler steps, with
-    Lawson flips after every `flip_every` steps (0: never)."""
+    Lawson flips after every `flip_every` steps (0: never).  `anchors`: node ids that stay put
+    besides the boundary nodes (the seeding nodes of interior geometry); `keep`: node-id pairs,
+    edges of the geometry that are never flipped."""
     xy = np.array(xy, np.float64)
     t = orient_ccw(xy, tris)
     if h_nodes is None:
         h_nodes = np.full(xy.shape[0], uniform_size(xy, t))
     bnd = boundary_nodes(xy.shape[0], t)
+    bnd[np.asarray(anchors, np.int64).reshape(-1)] = True
     n_flips = 0
     edges, L0, H0 = rest_lengths(t, h_nodes)
     for it in range(iters):
@@ -130,7 +137,7 @@ def relax(xy, tris, iters: int, tau: float = 0.05, h_nodes=None, flip_every: int
         scale = np.where(n > cap, cap / np.where(n > 0, n, 1.0), 1.0)
         xy = xy + dx * scale[:, None]
         if flip_every > 0 and (it + 1) % flip_every == 0:
-            t, k = lawson_flips(xy, t)
+            t, k = lawson_flips(xy, t, keep)
             n_flips += k
             edges, L0, H0 = rest_lengths(t, h_nodes)
     return xy, t, n_flips
@@ -151,8 +158,10 @@ def _ccw(xy, a, b, c) -> float:
     return (xy[b][0] - xy[a][0]) * (xy[c][1] - xy[a][1]) - (xy[b][1] - xy[a][1]) * (xy[c][0] - xy[a][0])
 
 
-def lawson_flips(xy, tris):
-    """Flip interior edges until every one is locally Delaunay; (triangles, flips)."""
+def lawson_flips(xy, tris, keep=()):
+    """Flip interior edges, except the node-id pairs in `keep`, until every one is locally
+    Delaunay; (triangles, flips)."""
+    fixed = {frozenset((int(u), int(v))) for u, v in np.asarray(keep, np.int64).reshape(-1, 2)}
     t = [list(r) for r in orient_ccw(xy, tris)]
     owner = {}          # directed edge (u, v) -> triangle holding it in CCW order
     for i, (a, b, c) in enumerate(t):
@@ -162,7 +171,7 @@ def lawson_flips(xy, tris):
     flips = 0
     while stack:
         a, b = stack.pop()
-        if (a, b) not in owner or (b, a) not in owner:
+        if (a, b) not in owner or (b, a) not in owner or frozenset((a, b)) in fixed:
             continue
         i, j = owner[(a, b)], owner[(b, a)]
         c = [x for x in t[i] if x != a and x != b][0]      # (a, b, c) CCW

@@ -83,8 +83,9 @@ SIGNATURES = [
     ("ue_profile_steps", C.c_int, [P, I64, P, PD, PD]),
     ("ue_power_iteration_static", C.c_int, [P, P, P, P, P, P, I64, I64, C.c_int32, C.c_uint32, P, PD]),
     ("ue_modes", C.c_int, [P, C.c_int32, C.c_int32, C.c_uint32, PD, PD, P]),
-    ("ue_mesh_relax", C.c_int, [PD, I64, PI32, I64, PD, C.c_int32, C.c_int32, C.c_double, PD, PI32,
-                                PI64, P]),
+    ("ue_mesh_relax", C.c_int, [PD, I64, PI32, I64, PD, C.c_int32, C.c_int32, C.c_double, PI32, I64,
+                                PI32, I64, PD, PI32, PI64, P]),
+    ("ue_mesh_flip", C.c_int, [PD, I64, PI32, I64, PI32, I64, PI32, PI64]),
     ("ue_triangulate", C.c_int, [PD, I64, PI32, I64, PD, I64, C.c_int32, PI32, I64, PI64, PI64]),
     ("ue_stats", C.c_int, [P, C.POINTER(Stats)]),
     ("ue_last_error", C.c_char_p, []),

@@ -320,12 +320,19 @@ def power_iteration_static(edge_tri, elen, d, tri_code, S, tri_caller, iters: in
     return rho.value
 
 
+def _pairs(segs):
+    return np.ascontiguousarray(np.zeros((0, 2)) if segs is None else segs, np.int32).reshape(-1, 2)
+
+
 def mesh_relax(xy, tris, iters: int, flip_every: int = 20, tau: float = 0.05, h_nodes=None,
-               stream=None):
-    """Jello-model relaxation with Lawson flips (ue_mesh_relax): (xy, tris CCW, flips)."""
+               anchors=None, keep=None, stream=None):
+    """Jello-model relaxation with Lawson flips (ue_mesh_relax): (xy, tris CCW, flips).
+    anchors: node ids held in place besides the boundary; keep: node-id pairs never flipped."""
     xy = np.ascontiguousarray(xy, np.float64)
     tris = np.ascontiguousarray(tris, np.int32)
     h = None if h_nodes is None else np.ascontiguousarray(h_nodes, np.float64)
+    an = np.ascontiguousarray(np.zeros(0) if anchors is None else anchors, np.int32).reshape(-1)
+    kp = _pairs(keep)
     if xy.ndim != 2 or xy.shape[1] != 2 or tris.ndim != 2 or tris.shape[1] != 3:
         raise ValueError("xy must be (n, 2) and tris (m, 3)")
     if h is not None and h.shape != (xy.shape[0],):
@@ -334,9 +341,27 @@ def mesh_relax(xy, tris, iters: int, flip_every: int = 20, tau: float = 0.05, h_
     to = np.empty_like(tris)
     nf = C.c_int64()
     N.check(N.lib().ue_mesh_relax(_dptr(xy), xy.shape[0], tris.ctypes.data_as(N.PI32), tris.shape[0],
-                                  _dptr(h), int(iters), int(flip_every), float(tau), _dptr(xo),
+                                  _dptr(h), int(iters), int(flip_every), float(tau),
+                                  an.ctypes.data_as(N.PI32), an.shape[0], kp.ctypes.data_as(N.PI32),
+                                  kp.shape[0], _dptr(xo),
                                   to.ctypes.data_as(N.PI32), C.byref(nf), _stream(stream)), "ue_mesh_relax")
     return xo, to, nf.value
+
+
+def mesh_flip(xy, tris, keep=None):
+    """Lawson flips of a triangulation on the host, keeping node-id pairs (ue_mesh_flip):
+    (tris CCW, flips)."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    tris = np.ascontiguousarray(tris, np.int32)
+    if xy.ndim != 2 or xy.shape[1] != 2 or tris.ndim != 2 or tris.shape[1] != 3:
+        raise ValueError("xy must be (n, 2) and tris (m, 3)")
+    kp = _pairs(keep)
+    out = np.empty_like(tris)
+    nf = C.c_int64()
+    N.check(N.lib().ue_mesh_flip(_dptr(xy), xy.shape[0], tris.ctypes.data_as(N.PI32), tris.shape[0],
+                                 kp.ctypes.data_as(N.PI32), kp.shape[0], out.ctypes.data_as(N.PI32),
+                                 C.byref(nf)), "ue_mesh_flip")
+    return out, nf.value
 
 
 def triangulate(xy, segs=None, holes=None, drop_exterior: bool = False):

@@ -275,8 +275,12 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
 
 // Jello-model relaxation with Lawson flips (kernels_relax.cu); see ue_mesh_relax.
 int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const double* h_nodes,
-               int32_t iters, int32_t flip_every, double tau, double* xy_out, int32_t* tris_out,
-               int64_t* n_flips, cudaStream_t s, std::string& err);
+               int32_t iters, int32_t flip_every, double tau, const int32_t* anchors, int64_t n_anchors,
+               const int32_t* segs, int64_t n_segs, double* xy_out, int32_t* tris_out, int64_t* n_flips,
+               cudaStream_t s, std::string& err);
+// Lawson flips alone, on the host; see ue_mesh_flip.
+int mesh_flip(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const int32_t* segs,
+              int64_t n_segs, int32_t* tris_out, int64_t* n_flips, std::string& err);
 
 // Energy watchdog: W of eq. 8 into wd[1], compared with the previous check (see kernels_geom.cu).
 size_t energy_parts(int64_t n_ei, int64_t n_t);

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <unordered_set>
 #include <utility>
 #include <vector>
 
@@ -169,7 +170,12 @@ void node_tris(int64_t nn, const std::vector<int32_t>& t, std::vector<int32_t>& 
         }
 }
 
-int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
+uint64_t edge_key(int32_t a, int32_t b) {
+    return ((uint64_t)(uint32_t)std::min(a, b) << 32) | (uint32_t)std::max(a, b);
+}
+
+// keep: edges (edge_key) that are never flipped (the input geometry's).
+int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t, const std::unordered_set<uint64_t>& keep) {
     const int64_t nt = (int64_t)t.size() / 3;
     const int64_t nn = (int64_t)x.size() / 2;
     std::vector<int64_t> nb(3 * nt, -1);
@@ -212,6 +218,7 @@ int64_t lawson(const std::vector<double>& x, std::vector<int32_t>& t) {
         const int64_t j = nb[3 * i + qi];
         if (j < 0) continue;
         const int32_t a = it.a, b = it.b, c = t[3 * i + (qi + 2) % 3];
+        if (!keep.empty() && keep.count(edge_key(a, b))) continue;
         const int qj = slot_of(j, b, a);
         const int32_t d = t[3 * j + (qj + 2) % 3];
         if (!in_circle(x, a, b, c, d)) continue;
@@ -284,12 +291,12 @@ void build_lists(int64_t nn, const std::vector<int32_t>& t, const std::vector<do
 
 // See include/ue.h (ue_mesh_relax).  Device buffers are owned here (cudaMalloc/cudaFree):
 // the call is a one-off preprocessing step outside any mesh.
-int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const double* h_nodes,
-               int32_t iters, int32_t flip_every, double tau, double* xy_out, int32_t* tris_out,
-               int64_t* n_flips, cudaStream_t s, std::string& err) {
-    std::vector<double> x(xy, xy + 2 * nn);
-    std::vector<int32_t> t(tris, tris + 3 * nt);
-    double area = 0.0;
+namespace {
+
+// Orients the triangles CCW in t (a copy of tris); accumulates the area.
+int orient_input(const std::vector<double>& x, int64_t nn, std::vector<int32_t>& t, double* area,
+                 std::string& err) {
+    const int64_t nt = (int64_t)t.size() / 3;
     for (int64_t i = 0; i < nt; ++i) {
         int32_t* r = &t[3 * i];
         for (int q = 0; q < 3; ++q)
@@ -306,7 +313,59 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
             err = "degenerate triangle " + std::to_string(i);
             return UE_ERR_DEGENERATE;
         }
-        area += 0.5 * o;
+        *area += 0.5 * o;
+    }
+    return UE_OK;
+}
+
+int keep_set(const int32_t* segs, int64_t n_segs, int64_t nn, std::unordered_set<uint64_t>& keep,
+             std::string& err) {
+    for (int64_t k = 0; k < n_segs; ++k) {
+        const int32_t a = segs[2 * k], b = segs[2 * k + 1];
+        if (a < 0 || b < 0 || a >= nn || b >= nn || a == b) {
+            err = "kept edge " + std::to_string(k) + " has a bad node id";
+            return UE_ERR_ARG;
+        }
+        keep.insert(edge_key(a, b));
+    }
+    return UE_OK;
+}
+
+}  // namespace
+
+// See include/ue.h (ue_mesh_flip): the remesh step alone, on the host.
+int mesh_flip(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const int32_t* segs,
+              int64_t n_segs, int32_t* tris_out, int64_t* n_flips, std::string& err) {
+    std::vector<double> x(xy, xy + 2 * nn);
+    std::vector<int32_t> t(tris, tris + 3 * nt);
+    double area = 0.0;
+    std::unordered_set<uint64_t> keep;
+    int rc = orient_input(x, nn, t, &area, err);
+    if (rc == UE_OK) rc = keep_set(segs, n_segs, nn, keep, err);
+    if (rc != UE_OK) return rc;
+    const int64_t k = lawson(x, t, keep);
+    std::copy(t.begin(), t.end(), tris_out);
+    if (n_flips) *n_flips = k;
+    return UE_OK;
+}
+
+int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, const double* h_nodes,
+               int32_t iters, int32_t flip_every, double tau, const int32_t* anchors, int64_t n_anchors,
+               const int32_t* segs, int64_t n_segs, double* xy_out, int32_t* tris_out, int64_t* n_flips,
+               cudaStream_t s, std::string& err) {
+    std::vector<double> x(xy, xy + 2 * nn);
+    std::vector<int32_t> t(tris, tris + 3 * nt);
+    double area = 0.0;
+    std::unordered_set<uint64_t> keep;
+    {
+        int rc = orient_input(x, nn, t, &area, err);
+        if (rc == UE_OK) rc = keep_set(segs, n_segs, nn, keep, err);
+        if (rc != UE_OK) return rc;
+        for (int64_t k = 0; k < n_anchors; ++k)
+            if (anchors[k] < 0 || anchors[k] >= nn) {
+                err = "anchor " + std::to_string(k) + " is not a node id";
+                return UE_ERR_ARG;
+            }
     }
     std::vector<double> h(nn);
     if (h_nodes) {
@@ -321,7 +380,12 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
         std::fill(h.begin(), h.end(), std::sqrt(4.0 * area / (std::sqrt(3.0) * (double)nt)));
     }
     RxLists L;
-    build_lists(nn, t, h, L);
+    // the boundary nodes are fixed by build_lists; the caller's anchors join them
+    auto lists = [&]() {
+        build_lists(nn, t, h, L);
+        for (int64_t k = 0; k < n_anchors; ++k) L.fixed[anchors[k]] = 1;
+    };
+    lists();
     // device buffers, sized for the lists (their sizes do not change under flips)
     double *dx0 = nullptr, *dx1 = nullptr, *dL0 = nullptr, *dH0 = nullptr, *dcap = nullptr,
            *dtri = nullptr;
@@ -375,10 +439,10 @@ int mesh_relax(const double* xy, int64_t nn, const int32_t* tris, int64_t nt, co
             ck(cudaMemcpyAsync(x.data(), dx0, 16 * nn, cudaMemcpyDeviceToHost, s));
             ck(cudaStreamSynchronize(s));
             if (e != cudaSuccess) break;
-            const int64_t k = lawson(x, t);
+            const int64_t k = lawson(x, t, keep);
             flips += k;
             if (k > 0) {
-                build_lists(nn, t, h, L);
+                lists();
                 upload_lists();
             }
         }

@@ -1986,18 +1986,33 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     return UE_OK;
 }
 
+int ue_mesh_flip(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris, const int32_t* segs,
+                 int64_t n_segs, int32_t* tris_out, int64_t* n_flips) {
+    Range nvtx_range("ue_mesh_flip");
+    if (!xy || !tris || !tris_out || n_nodes < 3 || n_tris < 1 || n_segs < 0 || (n_segs > 0 && !segs))
+        return fail(UE_ERR_ARG, "ue_mesh_flip: bad arguments");
+    if (n_nodes >= (int64_t)1 << 31 || 3 * n_tris >= (int64_t)1 << 31)
+        return fail(UE_ERR_ARG, "ue_mesh_flip: mesh too large for 32-bit indices");
+    std::string err;
+    const int rc = ue::mesh_flip(xy, n_nodes, tris, n_tris, segs, n_segs, tris_out, n_flips, err);
+    if (rc != UE_OK) return fail(rc, "ue_mesh_flip: " + err);
+    return UE_OK;
+}
+
 int ue_mesh_relax(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
                   const double* h_nodes, int32_t iters, int32_t flip_every, double tau,
+                  const int32_t* anchors, int64_t n_anchors, const int32_t* segs, int64_t n_segs,
                   double* xy_out, int32_t* tris_out, int64_t* n_flips, void* stream) {
     Range nvtx_range("ue_mesh_relax");
-    if (!xy || !tris || !xy_out || !tris_out || n_nodes < 3 || n_tris < 1 || iters < 0 || flip_every < 0)
+    if (!xy || !tris || !xy_out || !tris_out || n_nodes < 3 || n_tris < 1 || iters < 0 || flip_every < 0 ||
+        n_anchors < 0 || n_segs < 0 || (n_anchors > 0 && !anchors) || (n_segs > 0 && !segs))
         return fail(UE_ERR_ARG, "ue_mesh_relax: bad arguments");
     if (n_nodes >= (int64_t)1 << 31 || 3 * n_tris >= (int64_t)1 << 31)
         return fail(UE_ERR_ARG, "ue_mesh_relax: mesh too large for 32-bit indices");
     if (!(tau > 0.0 && tau <= 0.1)) return fail(UE_ERR_ARG, "ue_mesh_relax: tau must be in (0, 0.1]");
     std::string err;
-    const int rc = ue::mesh_relax(xy, n_nodes, tris, n_tris, h_nodes, iters, flip_every, tau, xy_out,
-                                  tris_out, n_flips, (cudaStream_t)stream, err);
+    const int rc = ue::mesh_relax(xy, n_nodes, tris, n_tris, h_nodes, iters, flip_every, tau, anchors,
+                                  n_anchors, segs, n_segs, xy_out, tris_out, n_flips, (cudaStream_t)stream, err);
     if (rc != UE_OK) return fail(rc, err);
     return UE_OK;
 }

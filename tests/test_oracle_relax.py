@@ -52,9 +52,11 @@ def test_relaxation_lowers_the_energy_and_restores_the_lattice():
     assert np.array_equal(xy[bnd], ms.xy[bnd])
 
 
-def _scramble(xy, tris, n, seed):
-    """Random flips of interior edges whose quad is convex (Delaunay or not)."""
+def _scramble(xy, tris, n, seed, keep=()):
+    """Random flips of interior edges whose quad is convex (Delaunay or not), never of the
+    node-id pairs in `keep`."""
     rng = np.random.default_rng(seed)
+    fixed = {frozenset((int(u), int(v))) for u, v in np.asarray(keep, np.int64).reshape(-1, 2)}
     t = [list(r) for r in tris]
     done = 0
     while done < n:
@@ -62,6 +64,8 @@ def _scramble(xy, tris, n, seed):
         q = int(rng.integers(3))
         a, b = t[i][q], t[i][(q + 1) % 3]
         c = t[i][(q + 2) % 3]
+        if frozenset((a, b)) in fixed:
+            continue
         js = [j for j in range(len(t)) if j != i and a in t[j] and b in t[j]]
         if not js:
             continue
@@ -85,3 +89,46 @@ def test_lawson_flips_recover_the_delaunay_triangulation():
     out, flips = relax.lawson_flips(ms.xy, bad)
     assert flips > 0
     assert {tuple(sorted(r)) for r in out} == ref
+
+
+def test_kept_edges_give_the_constrained_delaunay_triangulation():
+    """Lawson flips that keep the segments of a zigzag through a cloud, run on a scrambled copy
+    of its constrained Delaunay triangulation (built independently, by flip refinement), come
+    back to that triangulation; without `keep` they leave it."""
+    from oracle import triangulate as tri
+    from test_oracle_triangulate import _zigzag_case
+    xy, segs = _zigzag_case(n=150)
+    cdt, _ = tri.triangulate(xy, segs)
+    bad = _scramble(xy, cdt, 120, seed=4, keep=segs)
+    assert not np.array_equal(tri.canonical(bad), cdt)
+    out, flips = relax.lawson_flips(xy, bad, keep=segs)
+    assert flips > 0 and np.array_equal(tri.canonical(out), cdt)
+    free, _ = relax.lawson_flips(xy, bad)
+    assert np.array_equal(tri.canonical(free), tri.triangulate(xy)[0])
+
+
+def test_anchored_geometry_stays_put():
+    """An interior circle of seeded nodes (an object's contour, meshed on both sides) with its
+    nodes anchored and its edges kept: the nodes do not move and the contour survives the
+    remesh, while the cloud around it relaxes; unanchored, the contour nodes move."""
+    from oracle import triangulate as tri
+    rng = np.random.default_rng(16)
+    k = 24
+    ang = 2 * np.pi * np.arange(k) / k
+    ring = np.stack([0.5 + 0.2 * np.cos(ang), 0.5 + 0.2 * np.sin(ang)], 1)
+    box = np.array([[0, 0], [1, 0], [1, 1], [0, 1.0]])
+    pts = rng.random((500, 2)) * 0.96 + 0.02
+    r = np.linalg.norm(pts - 0.5, axis=1)
+    pts = pts[np.abs(r - 0.2) > 0.02][:300]
+    xy = np.vstack([box, ring, pts])
+    ids = np.arange(4, 4 + k)
+    segs = np.stack([ids, np.roll(ids, -1)], 1)
+    t0, _ = tri.triangulate(xy, segs)
+    x1, t1, flips = relax.relax(xy, t0, 60, flip_every=10, anchors=ids, keep=segs)
+    assert np.array_equal(x1[ids], xy[ids])
+    edges = {frozenset(e) for r in t1 for e in ((r[0], r[1]), (r[1], r[2]), (r[2], r[0]))}
+    assert all(frozenset((int(u), int(v))) in edges for u, v in segs)
+    moved = np.linalg.norm(x1 - xy, axis=1)
+    assert moved[4 + k:].max() > 1e-3 and flips > 0
+    x2, _, _ = relax.relax(xy, t0, 60, flip_every=10)
+    assert np.linalg.norm(x2[ids] - xy[ids], axis=1).max() > 1e-3

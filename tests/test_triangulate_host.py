@@ -198,3 +198,36 @@ def test_exterior_flag_and_repeated_segments_change_nothing_on_a_closed_hull(ue)
     assert np.array_equal(tr.canonical(got), tr.canonical(want))
     o, _ = tr.triangulate(xy, twice, holes=[[0.5, 0.5]], drop_exterior=True)
     assert np.array_equal(o, tr.canonical(want))
+
+
+def test_mesh_flip_equals_the_oracle_lawson_pass(ue):
+    """ue_mesh_flip (the relaxation's remesh step) against the oracle's Lawson flips: a scrambled
+    Delaunay triangulation comes back; with kept edges, a scrambled constrained triangulation
+    comes back to the one flip refinement builds."""
+    from oracle import relax
+    from test_oracle_relax import _scramble
+    ms = meshgen.random_delaunay(300, seed=17)
+    bad = _scramble(ms.xy, relax.orient_ccw(ms.xy, ms.tris), 200, seed=3)
+    got, flips = ue.mesh_flip(ms.xy, bad)
+    want, wflips = relax.lawson_flips(ms.xy, bad)
+    assert flips > 0 and np.array_equal(tr.canonical(got), tr.canonical(want))
+    assert np.array_equal(tr.canonical(got), tr.canonical(relax.orient_ccw(ms.xy, ms.tris)))
+    xy, segs = _zigzag_case(n=200)
+    cdt, _ = tr.triangulate(xy, segs)
+    bad = _scramble(xy, cdt, 150, seed=5, keep=segs)
+    got, flips = ue.mesh_flip(xy, bad, keep=segs)
+    assert flips > 0 and np.array_equal(tr.canonical(got), cdt)
+    want, _ = relax.lawson_flips(xy, bad, keep=segs)
+    assert np.array_equal(tr.canonical(want), cdt)
+
+
+def test_mesh_flip_refuses_bad_input(ue):
+    ms = meshgen.random_delaunay(50, seed=18)
+    with pytest.raises(ue.UEError) as ei:
+        ue.mesh_flip(ms.xy, ms.tris, keep=[[0, ms.xy.shape[0]]])
+    assert ei.value.code == -1
+    flat = ms.tris.copy()
+    flat[0] = [0, 0, 1]
+    with pytest.raises(ue.UEError) as ei:
+        ue.mesh_flip(ms.xy, flat)
+    assert ei.value.code == -3
