@@ -107,28 +107,32 @@ def test_kept_edges_give_the_constrained_delaunay_triangulation():
     assert np.array_equal(tri.canonical(free), tri.triangulate(xy)[0])
 
 
-def test_anchored_geometry_stays_put():
-    """An interior circle of seeded nodes (an object's contour, meshed on both sides) with its
-    nodes anchored and its edges kept: the nodes do not move and the contour survives the
-    remesh, while the cloud around it relaxes; unanchored, the contour nodes move."""
+def ring_case():
+    """A unit square with a circle of 24 seeded nodes inside (an object's contour, meshed on
+    both sides) and 300 random nodes: (xy, its constrained Delaunay triangulation, the contour's
+    node ids, the contour's edges)."""
     from oracle import triangulate as tri
     rng = np.random.default_rng(16)
     k = 24
     ang = 2 * np.pi * np.arange(k) / k
     ring = np.stack([0.5 + 0.2 * np.cos(ang), 0.5 + 0.2 * np.sin(ang)], 1)
-    box = np.array([[0, 0], [1, 0], [1, 1], [0, 1.0]])
     pts = rng.random((500, 2)) * 0.96 + 0.02
-    r = np.linalg.norm(pts - 0.5, axis=1)
-    pts = pts[np.abs(r - 0.2) > 0.02][:300]
-    xy = np.vstack([box, ring, pts])
+    pts = pts[np.abs(np.linalg.norm(pts - 0.5, axis=1) - 0.2) > 0.02][:300]
+    xy = np.vstack([np.array([[0, 0], [1, 0], [1, 1], [0, 1.0]]), ring, pts])
     ids = np.arange(4, 4 + k)
     segs = np.stack([ids, np.roll(ids, -1)], 1)
-    t0, _ = tri.triangulate(xy, segs)
+    return xy, tri.triangulate(xy, segs)[0], ids, segs
+
+
+def test_anchored_geometry_stays_put():
+    """The ring's nodes anchored and its edges kept: the nodes do not move and the contour
+    survives the remesh, while the cloud around it relaxes; unanchored, the contour nodes move."""
+    xy, t0, ids, segs = ring_case()
     x1, t1, flips = relax.relax(xy, t0, 60, flip_every=10, anchors=ids, keep=segs)
     assert np.array_equal(x1[ids], xy[ids])
     edges = {frozenset(e) for r in t1 for e in ((r[0], r[1]), (r[1], r[2]), (r[2], r[0]))}
     assert all(frozenset((int(u), int(v))) in edges for u, v in segs)
     moved = np.linalg.norm(x1 - xy, axis=1)
-    assert moved[4 + k:].max() > 1e-3 and flips > 0
+    assert moved[4 + len(ids):].max() > 1e-3 and flips > 0
     x2, _, _ = relax.relax(xy, t0, 60, flip_every=10)
     assert np.linalg.norm(x2[ids] - xy[ids], axis=1).max() > 1e-3

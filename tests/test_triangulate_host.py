@@ -231,3 +231,27 @@ def test_mesh_flip_refuses_bad_input(ue):
     with pytest.raises(ue.UEError) as ei:
         ue.mesh_flip(ms.xy, flat)
     assert ei.value.code == -3
+
+
+def test_mesh_flip_along_the_oracle_relaxation_of_anchored_geometry(ue):
+    """At every remesh of the oracle's anchored relaxation (contour nodes anchored, contour
+    edges kept), the library's Lawson pass on the same positions gives the oracle's triangles;
+    the flip counts may differ, since they depend on the order flips are taken in."""
+    import oracle.relax as R
+    from test_oracle_relax import ring_case
+    xy, t0, ids, segs = ring_case()
+    seen = []
+    real = R.lawson_flips
+
+    def both(x, t, keep=()):
+        a, ka = real(x, t, keep)
+        b, _ = ue.mesh_flip(x, t, keep=keep)
+        seen.append(np.array_equal(tr.canonical(a), tr.canonical(b)))
+        return a, ka
+
+    R.lawson_flips = both
+    try:
+        R.relax(xy, t0, 60, flip_every=10, anchors=ids, keep=segs)
+    finally:
+        R.lawson_flips = real
+    assert len(seen) == 6 and all(seen)
