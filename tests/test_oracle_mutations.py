@@ -6,7 +6,6 @@ import math
 import textwrap
 
 import numpy as np
-import pytest
 
 import meshgen
 from oracle import mesh as om, operators, pml, rcm, spectral
