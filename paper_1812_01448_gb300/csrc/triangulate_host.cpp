@@ -545,7 +545,7 @@ int triangulate(const double* xy, int64_t nn, const int32_t* segs, int64_t n_seg
     };
     for (int64_t s = 0; s < n_segs; ++s) {
         const int32_t u = segs[2 * s], v = segs[2 * s + 1];
-        int q;
+        int q = 0;
         if (D.find_edge(u, v, &q) >= 0 || D.find_edge(v, u, &q) >= 0) {
             fixed.insert(ekey(u, v));
             continue;
@@ -584,8 +584,12 @@ int triangulate(const double* xy, int64_t nn, const int32_t* segs, int64_t n_seg
                 return UE_ERR_ARG;
             }
             queue.push_back({x, y});
-            int qe;
+            int qe = 0;
             const int32_t ta = D.find_edge(y, x, &qe);   // the triangle beyond (x, y), seen from u
+            if (ta < 0 || D.ghost(ta)) {
+                err = "ue_triangulate: segment " + std::to_string(s) + " walk lost its triangle";
+                return UE_ERR_ARG;
+            }
             const int32_t w = D.T[ta].v[(qe + 2) % 3];
             if (w == v) break;
             const int ow = orient(pu, pv, D.P(w));
@@ -612,8 +616,12 @@ int triangulate(const double* xy, int64_t nn, const int32_t* segs, int64_t n_seg
             }
             const auto e = queue.front();
             queue.pop_front();
-            int q1;
+            int q1 = 0;
             const int32_t t1 = D.find_edge(e.first, e.second, &q1);
+            if (t1 < 0 || D.ghost(t1) || D.ghost(D.T[t1].n[q1])) {
+                err = "ue_triangulate: flip refinement lost a crossing edge";
+                return UE_ERR_ARG;
+            }
             const int32_t t2 = D.T[t1].n[q1];
             const int q2 = D.edge_at(t2, e.second, e.first);
             const int32_t c = D.T[t1].v[(q1 + 2) % 3], d = D.T[t2].v[(q2 + 2) % 3];
@@ -644,7 +652,7 @@ int triangulate(const double* xy, int64_t nn, const int32_t* segs, int64_t n_seg
         const auto e = touched.back();
         touched.pop_back();
         if (e.first == G || e.second == G || fixed.count(ekey(e.first, e.second))) continue;
-        int q1;
+        int q1 = 0;
         const int32_t t1 = D.find_edge(e.first, e.second, &q1);
         if (t1 < 0 || D.ghost(t1)) continue;
         const int32_t t2 = D.T[t1].n[q1];
