@@ -177,7 +177,7 @@ int power_iteration_static(const int32_t* edge_tri, const double* elen, const do
     const unsigned be = (unsigned)((n_ei + kThreads) / kThreads);
     const int2* rl = reinterpret_cast<const int2*>(edge_tri);
     s_init<<<bt, kThreads, 0, s>>>(w, tri_caller, seed, g, n_t, n_ei);
-    s_tri<<<bt, kThreads, 0, s>>>(tri_code, S, g, w, w, part, n_t, 1);
+    s_tri<<<bt, kThreads, 0, s>>>(tri_code, S, g, w, nullptr, part, n_t, 1);   // norm only: no output
     s_reduce<<<1, kThreads, 0, s>>>(part, nb, sums);
     s_scale<<<bt, kThreads, 0, s>>>(w, sums, v, n_t);
     for (int it = 0; it < iters; ++it) {
