@@ -27,8 +27,10 @@ Readings (where the paper gives the idea but not the formulas):
   named by the caller, and so are the geometry edges between them, which the remesh keeps.
 
 Parity: pinned by tests/test_oracle_relax.py (forces against central differences of E, the
-equilateral lattice as a fixed point, E non-increasing along the flow, and Lawson flips of a
-scrambled triangulation of random points giving Qhull's Delaunay triangulation).
+equilateral lattice as a fixed point, E non-increasing along the flow, Lawson flips of a
+scrambled triangulation of random points giving Qhull's Delaunay triangulation, Lawson flips
+with kept edges giving the constrained Delaunay triangulation that flip refinement builds
+independently, and anchored contour nodes and kept contour edges surviving the relaxation).
 """
 from __future__ import annotations
 
