@@ -13,7 +13,7 @@ from fractions import Fraction
 
 import numpy as np
 import pytest
-from scipy.spatial import ConvexHull, Delaunay
+from scipy.spatial import Delaunay
 
 from oracle import triangulate as tr
 
@@ -43,7 +43,20 @@ def polygon_area2(xy, loop):
 
 
 def hull_area2(xy):
-    return polygon_area2(xy, [int(v) for v in ConvexHull(xy).vertices])
+    """Twice the area of the convex hull, exactly (Andrew's monotone chain over fractions)."""
+    P = sorted(set(_q(xy)))
+
+    def chain(pts):
+        h = []
+        for p in pts:
+            while len(h) >= 2 and ((h[-1][0] - h[-2][0]) * (p[1] - h[-2][1])
+                                   - (h[-1][1] - h[-2][1]) * (p[0] - h[-2][0])) <= 0:
+                h.pop()
+            h.append(p)
+        return h
+
+    h = chain(P)[:-1] + chain(P[::-1])[:-1]
+    return sum(h[i][0] * h[(i + 1) % len(h)][1] - h[(i + 1) % len(h)][0] * h[i][1] for i in range(len(h)))
 
 
 def check_cdt(xy, tris, segs=(), area2=None):

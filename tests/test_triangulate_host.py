@@ -255,3 +255,31 @@ def test_mesh_flip_along_the_oracle_relaxation_of_anchored_geometry(ue):
     finally:
         R.lawson_flips = real
     assert len(seen) == 6 and all(seen)
+
+
+@pytest.mark.parametrize("case", ["circle", "circle_centre", "collinear_run", "tiny_box", "clusters",
+                                  "lattice_diagonal"])
+def test_degenerate_and_badly_scaled_clouds(ue, case):
+    """Nodes all (nearly) on one circle, a long collinear run, 98 distinct nodes in a 1e-12 box
+    at 1000, clusters over twelve orders of magnitude, and lattice cell diagonals as segments:
+    the result always has the constrained Delaunay property and covers the hull exactly."""
+    a = 2 * np.pi * np.arange(400) / 400
+    circle = np.stack([np.cos(a), np.sin(a)], 1)
+    x = np.linspace(0, 1, 300)
+    r = np.random.default_rng(2)
+    segs = ()
+    xy = {
+        "circle": circle,
+        "circle_centre": np.vstack([circle, [[0.0, 0.0]]]),
+        "collinear_run": np.vstack([np.stack([x, 0 * x], 1), [[0.3, 0.2], [0.7, -0.1], [0.5, 1e-9]]]),
+        "tiny_box": np.unique(np.random.default_rng(1).random((500, 2)) * 1e-12 + 1e3, axis=0),
+        "clusters": np.vstack([r.normal(0, 1e-6, (200, 2)), r.normal(5, 1, (200, 2)), r.random((50, 2)) * 1e6]),
+        "lattice_diagonal": np.stack(np.meshgrid(np.arange(20), np.arange(20)), -1).reshape(-1, 2) * 0.1,
+    }[case]
+    if case == "lattice_diagonal":
+        segs = [[i * 20 + i, (i + 1) * 20 + i + 1] for i in range(19)]
+    got, _ = ue.triangulate(xy, segs)
+    check_cdt(xy, got, segs, area2=hull_area2(xy))
+    if xy.shape[0] <= 450 and case != "tiny_box":
+        want, _ = tr.triangulate(xy, segs)
+        check_cdt(xy, want, segs, area2=hull_area2(xy))
