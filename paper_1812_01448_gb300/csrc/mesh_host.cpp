@@ -7,7 +7,6 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
-#include <set>
 #include <utility>
 
 #include "ue_internal.h"
@@ -245,6 +244,40 @@ void kd_order(const Canon& c, const double* xy, const std::vector<int64_t>& rcm_
 //   other part Q moves to Q if Q has room.  Sweeps in RCM order, moving as found, until a sweep
 //   moves none; each move adds a same-part adjacency, so the sweeps end.
 // Parts are emitted in index order, RCM order inside each.
+// A set of positions 0..n-1 with a smallest-member query: a 64-ary tree of bit words, a bit of
+// one level set where the word below it is not empty.
+struct PosSet {
+    std::vector<std::vector<uint64_t>> lv;   // lv[0]: one bit per position; the last: one word
+    explicit PosSet(int64_t n) {
+        int64_t m = n;
+        do {
+            m = (m + 63) / 64;
+            lv.emplace_back(m, 0);
+        } while (m > 1);
+    }
+    void insert(int64_t p) {
+        for (auto& w : lv) {
+            const bool had = w[p >> 6] != 0;
+            w[p >> 6] |= 1ull << (p & 63);
+            if (had) return;
+            p >>= 6;
+        }
+    }
+    void erase(int64_t p) {
+        for (auto& w : lv) {
+            w[p >> 6] &= ~(1ull << (p & 63));
+            if (w[p >> 6] != 0) return;
+            p >>= 6;
+        }
+    }
+    int64_t first() const {   // -1 when empty
+        if (lv.back()[0] == 0) return -1;
+        int64_t i = 0;
+        for (size_t l = lv.size(); l-- > 0;) i = i * 64 + __builtin_ctzll(lv[l][i]);
+        return i;
+    }
+};
+
 void greedy_order(const Canon& c, int64_t nt, const std::vector<int64_t>& rcm_order, int64_t tile_tris,
                   std::vector<int64_t>& order, std::vector<int64_t>& tile_off) {
     const int64_t theta = tile_tris / 8, target = tile_tris - theta;
@@ -272,29 +305,31 @@ void greedy_order(const Canon& c, int64_t nt, const std::vector<int64_t>& rcm_or
     // growth
     std::vector<int> free_cnt(nt);
     std::vector<int64_t> part_of(nt, -1);
-    std::set<std::pair<int64_t, int64_t>> bucket[3];   // (RCM position, triangle) by free count
+    PosSet bucket[3] = {PosSet(nt), PosSet(nt), PosSet(nt)};   // RCM positions by free count
     for (int64_t j = 0; j < nt; ++j) {
         free_cnt[j] = (int)(ptr[j + 1] - ptr[j]);
-        if (free_cnt[j] < 3) bucket[free_cnt[j]].insert({pos[j], j});
+        if (free_cnt[j] < 3) bucket[free_cnt[j]].insert(pos[j]);
     }
     std::vector<int64_t> psize;
     std::vector<std::vector<int64_t>> members;
     auto take = [&](int64_t u, int64_t p) {
         part_of[u] = p;
-        if (free_cnt[u] < 3) bucket[free_cnt[u]].erase({pos[u], u});
+        if (free_cnt[u] < 3) bucket[free_cnt[u]].erase(pos[u]);
         for (int64_t k = ptr[u]; k < ptr[u + 1]; ++k) {
             const int64_t w = adj[k];
             if (part_of[w] >= 0) continue;
-            if (free_cnt[w] < 3) bucket[free_cnt[w]].erase({pos[w], w});
+            if (free_cnt[w] < 3) bucket[free_cnt[w]].erase(pos[w]);
             --free_cnt[w];
-            bucket[free_cnt[w]].insert({pos[w], w});
+            bucket[free_cnt[w]].insert(pos[w]);
         }
     };
     int64_t left = nt, next_free = 0;   // next_free: fallback scan in RCM order
     while (left > 0) {
         int64_t root = -1;
-        for (int k = 0; k < 3 && root < 0; ++k)
-            if (!bucket[k].empty()) root = bucket[k].begin()->second;
+        for (int k = 0; k < 3 && root < 0; ++k) {
+            const int64_t f = bucket[k].first();
+            if (f >= 0) root = rcm_order[f];
+        }
         if (root < 0) {
             while (part_of[rcm_order[next_free]] >= 0) ++next_free;
             root = rcm_order[next_free];
