@@ -283,3 +283,51 @@ def test_degenerate_and_badly_scaled_clouds(ue, case):
     if xy.shape[0] <= 450 and case != "tiny_box":
         want, _ = tr.triangulate(xy, segs)
         check_cdt(xy, want, segs, area2=hull_area2(xy))
+
+
+def test_mesh_generation_flow_gives_a_mesh_the_scheme_accepts(ue):
+    """Section 3's flow: contours seeded at spacing h (the unit square, a square hole, and a
+    circular object meshed on both sides), random area nodes, ue_triangulate with flip
+    refinement and the hole dropped, then the jello relaxation (the oracle's: the object's
+    contour anchored and its edges kept, Lawson remeshes every 10 steps).  The mesh loads,
+    both contours are still edges, and every interior edge has a positive dual length (eq. 10
+    needs d > 0), so the scheme can step it."""
+    from oracle import geometry, relax
+    xy0, segs0, ol, hl = square_with_hole(seed=19, n=0)
+    h = 0.05
+    k = 13
+    ang = 2 * np.pi * np.arange(k) / k
+    ring = np.stack([0.18 + 0.1 * np.cos(ang), 0.18 + 0.1 * np.sin(ang)], 1)
+    rng = np.random.default_rng(19)
+    pts = rng.random((3000, 2)) * 0.94 + 0.03
+    keep_pt = ~np.all((pts > 0.33) & (pts < 0.67), 1)
+    keep_pt &= np.abs(np.linalg.norm(pts - 0.18, axis=1) - 0.1) > 0.4 * h
+    pts = pts[keep_pt]
+    # thin the cloud to about the seeding spacing: drop nodes closer than 0.6 h to one kept
+    # before them (contour nodes first)
+    from scipy.spatial import cKDTree
+    base = np.vstack([xy0, ring])
+    chosen = []
+    tree_base = cKDTree(base)
+    for p in pts:
+        if tree_base.query(p)[0] < 0.6 * h:
+            continue
+        if chosen and np.min(np.linalg.norm(np.asarray(chosen) - p, axis=1)) < 0.6 * h:
+            continue
+        chosen.append(p)
+    xy = np.vstack([base, np.asarray(chosen)])
+    rid = np.arange(len(xy0), len(xy0) + k)
+    rsegs = np.stack([rid, np.roll(rid, -1)], 1)
+    segs = np.vstack([segs0, rsegs])
+    tris, flips = ue.triangulate(xy, segs, holes=[[0.5, 0.5]])
+    check_cdt(xy, tris, segs, area2=polygon_area2(xy, ol) - polygon_area2(xy, hl))
+    x1, t1, nf = relax.relax(xy, tris, 80, flip_every=10, anchors=rid, keep=rsegs)
+    assert np.array_equal(x1[rid], xy[rid]) and np.array_equal(x1[:len(xy0)], xy0)
+    edges = {frozenset(e) for r in t1.tolist() for e in ((r[0], r[1]), (r[1], r[2]), (r[2], r[0]))}
+    assert all(frozenset((int(u), int(v))) in edges for u, v in segs)
+    m = ue.Mesh(x1, t1)
+    om_ = om.canonicalize(x1, t1)
+    assert (m.n_tris, m.n_edges) == (om_.n_tris, om_.n_edges)
+    m.close()
+    d = geometry.Geometry(om_).d[om_.interior]
+    assert d.min() > 0
