@@ -369,7 +369,7 @@ def triangulate(xy, segs=None, holes=None, drop_exterior: bool = False):
     xy = np.ascontiguousarray(xy, np.float64)
     if xy.ndim != 2 or xy.shape[1] != 2:
         raise ValueError("xy must be (n, 2)")
-    sg = np.ascontiguousarray(np.zeros((0, 2)) if segs is None else segs, np.int32).reshape(-1, 2)
+    sg = _pairs(segs)
     ho = np.ascontiguousarray(np.zeros((0, 2)) if holes is None else holes, np.float64).reshape(-1, 2)
     cap = 2 * xy.shape[0]
     out = np.empty((cap, 3), np.int32)
