@@ -318,3 +318,51 @@ def test_frame_calls_refuse_bad_arguments(ue):
         with pytest.raises(ue.UEError):                               # nothing built yet
             m.frame_fields()
         m.close()
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ue.h"
+int main(void) {
+    const double xy[8] = {0, 0, 4, 0, 2, 1, 2, -1};
+    const int32_t seg[2] = {0, 1};
+    int32_t tris[8 * 3];
+    int64_t nt = 0, nf = 0;
+    if (ue_triangulate(xy, 4, seg, 1, NULL, 0, 0, tris, 8, &nt, &nf) != UE_OK) return 1;
+    printf("%lld %lld", (long long)nt, (long long)nf);
+    for (int64_t i = 0; i < 3 * nt; ++i) printf(" %d", (int)tris[i]);
+    if (ue_triangulate(xy, 2, NULL, 0, NULL, 0, 0, tris, 8, &nt, NULL) != UE_ERR_ARG) return 2;
+    printf("|%s\n", ue_last_error());
+    return strlen(ue_last_error()) > 0 ? 0 : 3;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(ue, tmp_path):
+    """include/ue.h compiles as C99 with -pedantic-errors, and a C program linked against the
+    library runs a host-only call (the kite of the triangulation pins: one flip restores its
+    long diagonal) and reads the thread's error text after a refused call."""
+    import shutil
+    import subprocess
+    from paper_1812_01448_gb300 import _native
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    lib_dir = os.path.dirname(_native.LIB_PATH)
+    cuda_inc = "/usr/local/cuda/include"
+    exe = tmp_path / "caller"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic-errors", f"-I{ROOT}/include",
+                        f"-I{cuda_inc}", str(src), "-o", str(exe), f"-L{lib_dir}", "-lue",
+                        f"-Wl,-rpath,{lib_dir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    head, err = r.stdout.strip().split("|")
+    vals = [int(v) for v in head.split()]
+    assert vals[:2] == [2, 1]
+    from oracle import triangulate as tr
+    got = tr.canonical(np.array(vals[2:]).reshape(-1, 3))
+    assert got.tolist() == [[0, 1, 2], [0, 3, 1]]
+    assert "ue_triangulate" in err
