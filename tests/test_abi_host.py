@@ -366,3 +366,30 @@ def test_header_is_plain_c_and_the_library_links_from_c(ue, tmp_path):
     got = tr.canonical(np.array(vals[2:]).reshape(-1, 3))
     assert got.tolist() == [[0, 1, 2], [0, 3, 1]]
     assert "ue_triangulate" in err
+
+
+def test_error_text_is_per_thread(ue):
+    """Two threads refused for different reasons, many times over: each reads its own text
+    (the error string is thread-local)."""
+    import threading
+    xy_dup = np.array([[0, 0], [1, 0], [0, 1], [1, 0.0]])
+    xy_ok = np.random.default_rng(20).random((30, 2))
+    seen = {"dup": set(), "seg": set()}
+
+    def run(kind):
+        for _ in range(200):
+            try:
+                if kind == "dup":
+                    ue.triangulate(xy_dup)
+                else:
+                    ue.triangulate(xy_ok, [[0, 0]])
+            except ue.UEError as e:
+                seen[kind].add(str(e).split(": ", 1)[1])
+
+    ts = [threading.Thread(target=run, args=(k,)) for k in ("dup", "seg")]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert len(seen["dup"]) == 1 and "repeats another node" in next(iter(seen["dup"]))
+    assert len(seen["seg"]) == 1 and "bad node id" in next(iter(seen["seg"]))
