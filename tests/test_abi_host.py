@@ -393,3 +393,32 @@ def test_error_text_is_per_thread(ue):
         t.join()
     assert len(seen["dup"]) == 1 and "repeats another node" in next(iter(seen["dup"]))
     assert len(seen["seg"]) == 1 and "bad node id" in next(iter(seen["seg"]))
+
+
+@pytest.mark.parametrize("bad", ["anchor_range", "keep_self", "keep_range", "tau", "iters", "flat", "sizes"])
+def test_mesh_relax_refuses_bad_input_before_the_gpu(ue, bad):
+    """ue_mesh_relax checks its arguments on the host before any device call: each refusal
+    comes back as its error code with no GPU present."""
+    ms = meshgen.random_delaunay(60, seed=21)
+    n = ms.xy.shape[0]
+    tris = ms.tris.copy()
+    kw = dict(iters=5)
+    code = -1
+    if bad == "anchor_range":
+        kw["anchors"] = [n]
+    elif bad == "keep_self":
+        kw["keep"] = [[3, 3]]
+    elif bad == "keep_range":
+        kw["keep"] = [[0, -1]]
+    elif bad == "tau":
+        kw["tau"] = 0.2
+    elif bad == "iters":
+        kw["iters"] = -1
+    elif bad == "flat":
+        tris[0] = [0, 0, 1]
+        code = -3
+    else:
+        kw["h_nodes"] = np.zeros(n)
+    with pytest.raises(ue.UEError) as ei:
+        ue.mesh_relax(ms.xy, tris, kw.pop("iters"), **kw)
+    assert ei.value.code == code
