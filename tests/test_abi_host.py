@@ -422,3 +422,33 @@ def test_mesh_relax_refuses_bad_input_before_the_gpu(ue, bad):
     with pytest.raises(ue.UEError) as ei:
         ue.mesh_relax(ms.xy, tris, kw.pop("iters"), **kw)
     assert ei.value.code == code
+
+
+def test_every_entry_point_refuses_null_arguments(ue):
+    """Each declared function called with NULL pointers and zero sizes returns UE_ERR_ARG (the
+    void ones return, ue_last_error gives text): no call dereferences an absent argument."""
+    import ctypes as C
+    from paper_1812_01448_gb300 import _native as N
+    L = N.lib()
+    checked = 0
+    for name, res, argtypes in N.SIGNATURES:
+        args = []
+        for t in argtypes:
+            if t in (C.c_double, C.c_float):
+                args.append(0.0)
+            elif t in (C.c_int, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t):
+                args.append(0)
+            elif isinstance(t, type) and issubclass(t, C._CFuncPtr):
+                args.append(t())          # a NULL callback
+            else:
+                args.append(None)
+        r = getattr(L, name)(*args)
+        if name in ("ue_options_default", "ue_mesh_free"):
+            assert r is None
+        elif name == "ue_last_error":
+            assert isinstance(r, bytes)
+        else:
+            assert r == -1, name
+            assert L.ue_last_error(), name
+        checked += 1
+    assert checked == len(N.SIGNATURES) >= 38
