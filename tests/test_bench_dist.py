@@ -38,3 +38,22 @@ def test_max_over_ranks_with_gloo():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(0, 7.25, 3.5), (1, 7.25, 7.25)]
+
+
+def test_traffic_is_reported_only_for_the_profiled_source():
+    """The ncu DRAM traffic in the bench line holds while the kernel source is the one that was
+    profiled; a changed source (a table entry with another hash) or an unknown configuration
+    reports none."""
+    sys.path.insert(0, ROOT)
+    import bench
+    key = ("blocked", "greedy", 2500, 8, 512, 0)
+    nbytes, prof = bench._traffic(key)
+    assert nbytes == 306195200.0 and prof.startswith("profiles/")
+    assert bench._traffic(("plain", "rcm", 0, 0, 0, 0)) == (None, None)
+    saved = bench.NCU_TRAFFIC[key]
+    try:
+        bench.NCU_TRAFFIC[key] = saved[:2] + ("0" * 40,) + saved[3:]
+        nbytes, why = bench._traffic(key)
+        assert nbytes is None and "changed" in why
+    finally:
+        bench.NCU_TRAFFIC[key] = saved
