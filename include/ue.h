@@ -398,18 +398,25 @@ int ue_frame_fields(ue_mesh* m, double* B, double* Ex, double* Ey, void* stream)
  * while they run (a memory budget fixed up front, a host process that owns the allocator, or
  * code that must avoid cudaMalloc's implicit synchronisation).  It computes the same
  * S-normalised power iteration as ue_geometry_build (same SplitMix64 start vector, iteration
- * count, reduction order), with its work vectors in one device array that the library holds
- * for the life of the process: at most UE_STATIC_MAX_TRIS triangles and UE_STATIC_MAX_EDGES
- * interior edges (8.4 MB, on every GPU that loads the library).  Larger sizes return
+ * count; the reductions follow ue_geometry_build's order, but each element is divided by d and
+ * S where ue_geometry_build multiplies by precomputed reciprocals, so the two agree to rounding,
+ * not bit for bit), with its work vectors in one file-scope device array of 8.4 MB: at most
+ * UE_STATIC_MAX_TRIS triangles and UE_STATIC_MAX_EDGES interior edges.  Larger sizes return
  * UE_ERR_ARG.
+ * Device memory: under CUDA's default lazy module loading the array is placed on a device by
+ * the first call there, not when the library is loaded, and stays until the process exits.  A
+ * caller whose memory budget is fixed at some point makes one warm-up call on each device
+ * before it (or runs with CUDA_MODULE_LOADING=EAGER).  After that, calls take no device memory.
  * Inputs are DEVICE pointers owned by the caller, in the stored numbering of ue_get_tables:
- *   edge_tri[2*n_ei] (R, L); elen[n_ei], d[n_ei] (|e| and |O_R O_L| per stored edge);
- *   tri_code[3*n_tris]; S[n_tris]; tri_caller[n_tris] (caller id of each stored triangle,
- *   which keys the start vector).
+ *   edge_tri[2*n_ei] (R, L), int32, 8-byte aligned; elen[n_ei], d[n_ei] (|e| and |O_R O_L| per
+ *   stored edge); tri_code[3*n_tris]; S[n_tris]; tri_caller[n_tris] (caller id of each stored
+ *   triangle, which keys the start vector).  An edge_tri entry outside [0, n_tris) or a
+ *   tri_code entry outside [0, 2 n_ei + 1] is not followed: the call returns UE_ERR_ARG.
  * Output: *rho (host).  Synchronous on `stream`.  All calls share the work array: calls that
- * overlap on the GPU race, so serialise them.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call outside any stream capture.  No cudaMalloc, cudaFree or allocating routine is used. */
+ * overlap on the GPU race, so serialise them.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the calling device current; the first call on a device also
+ * loads the module there, so make it before any stream capture.  No cudaMalloc, cudaFree or
+ * allocating routine is used. */
 #define UE_STATIC_MAX_TRIS (1 << 18)
 #define UE_STATIC_MAX_EDGES (1 << 19)
 int ue_power_iteration_static(const int32_t* edge_tri, const double* elen, const double* d,

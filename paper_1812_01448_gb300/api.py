@@ -308,10 +308,26 @@ def power_iteration_static(edge_tri, elen, d, tri_code, S, tri_caller, iters: in
     For callers that cannot allocate device memory while they run.  Arguments are CUDA
     tensors in the stored numbering (see ``Mesh.tables``): edge_tri int32 [n_ei, 2], elen and
     d float64 [n_ei], tri_code int32 [n_tris, 3], S float64 [n_tris], tri_caller int64
-    [n_tris].  Sizes are limited to UE_STATIC_MAX_TRIS / UE_STATIC_MAX_EDGES.
+    [n_tris].  Sizes are limited to UE_STATIC_MAX_TRIS / UE_STATIC_MAX_EDGES.  Type, shape,
+    device, contiguity and alignment are checked here (ValueError); indices that leave the
+    arrays are refused by the library (UEError, UE_ERR_ARG).
     """
-    n_t = int(S.shape[0])
-    n_ei = int(elen.shape[0])
+    import torch
+    n_t = int(S.shape[0]) if getattr(S, "ndim", 0) == 1 else -1
+    n_ei = int(elen.shape[0]) if getattr(elen, "ndim", 0) == 1 else -1
+    want = (("edge_tri", edge_tri, torch.int32, (n_ei, 2)), ("elen", elen, torch.float64, (n_ei,)),
+            ("d", d, torch.float64, (n_ei,)), ("tri_code", tri_code, torch.int32, (n_t, 3)),
+            ("S", S, torch.float64, (n_t,)), ("tri_caller", tri_caller, torch.int64, (n_t,)))
+    for name, x, dtype, shape in want:
+        if not isinstance(x, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if x.dtype != dtype or tuple(x.shape) != shape:
+            raise ValueError(f"{name} must be {dtype} of shape {shape}, got {x.dtype} {tuple(x.shape)}")
+        if not x.is_contiguous() or x.data_ptr() % 8:
+            raise ValueError(f"{name} must be contiguous and 8-byte aligned")
+    for name, x, _, _ in want:
+        if not x.is_cuda or x.device != S.device:
+            raise ValueError(f"{name} must be a CUDA tensor on the device of S")
     rho = C.c_double()
     N.check(N.lib().ue_power_iteration_static(
         C.c_void_p(edge_tri.data_ptr()), C.c_void_p(elen.data_ptr()), C.c_void_p(d.data_ptr()),

@@ -452,3 +452,28 @@ def test_every_entry_point_refuses_null_arguments(ue):
             assert L.ue_last_error(), name
         checked += 1
     assert checked == len(N.SIGNATURES) >= 38
+
+
+@pytest.mark.parametrize("bad", ["dtype", "shape", "strided", "cpu"])
+def test_power_iteration_static_checks_its_tensors_before_the_library(ue, bad):
+    """The binding refuses a wrong dtype, a shape that does not match the sizes taken from S
+    and elen, a strided tensor, and host tensors, with ValueError and before any call into
+    the library (these run without a GPU)."""
+    torch = pytest.importorskip("torch")
+    n_t, n_ei = 8, 6
+    a = dict(edge_tri=torch.zeros((n_ei, 2), dtype=torch.int32), elen=torch.ones(n_ei, dtype=torch.float64),
+             d=torch.ones(n_ei, dtype=torch.float64), tri_code=torch.zeros((n_t, 3), dtype=torch.int32),
+             S=torch.ones(n_t, dtype=torch.float64), tri_caller=torch.arange(n_t, dtype=torch.int64))
+    if bad == "dtype":
+        a["tri_caller"] = a["tri_caller"].to(torch.int32)
+        msg = "tri_caller must be"
+    elif bad == "shape":
+        a["edge_tri"] = torch.zeros((n_ei + 1, 2), dtype=torch.int32)
+        msg = "edge_tri must be"
+    elif bad == "strided":
+        a["d"] = torch.ones(2 * n_ei, dtype=torch.float64)[::2]
+        msg = "d must be contiguous"
+    else:
+        msg = "must be a CUDA tensor"
+    with pytest.raises(ValueError, match=msg):
+        ue.power_iteration_static(**a)

@@ -58,13 +58,55 @@ def test_static_power_iteration_matches_geometry_build(ue, which):
         assert abs(rho / rho_ref - 1.0) <= 1e-12, (rho, rho_ref)
 
 
-def test_static_power_iteration_rejects_oversize(ue):
+def test_static_power_iteration_takes_no_device_memory(ue):
+    """After a warm-up call (which places the work array on the device under lazy module
+    loading), a call changes neither the device's free memory nor torch's allocations."""
     import torch
-    n = ue._native.UE_STATIC_MAX_TRIS + 1
-    z = torch.zeros(1, dtype=torch.float64, device="cuda")
-    big = torch.zeros(n, dtype=torch.float64, device="cuda")
-    i32 = torch.zeros(2, dtype=torch.int32, device="cuda")
-    i64 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = meshgen.cavity_te11_mesh()
+    rho_ref, dev = _device_inputs(ue, ms, seed=3)
+    ue.power_iteration_static(**dev, iters=50, seed=3)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    reserved0 = torch.cuda.memory_reserved()
+    rho = ue.power_iteration_static(**dev, iters=200, seed=3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert (free1, torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == (free0, alloc0, reserved0)
+    assert abs(rho / rho_ref - 1.0) <= 1e-12
+
+
+def _sized(n_t, n_ei):
+    import torch
+    f = dict(dtype=torch.float64, device="cuda")
+    return dict(edge_tri=torch.zeros((n_ei, 2), dtype=torch.int32, device="cuda"),
+                elen=torch.ones(n_ei, **f), d=torch.ones(n_ei, **f),
+                tri_code=torch.zeros((n_t, 3), dtype=torch.int32, device="cuda"),
+                S=torch.ones(n_t, **f), tri_caller=torch.arange(n_t, dtype=torch.int64, device="cuda"))
+
+
+@pytest.mark.parametrize("which", ["tris", "edges"])
+def test_static_power_iteration_rejects_oversize(ue, which):
+    n_t = ue._native.UE_STATIC_MAX_TRIS + (1 if which == "tris" else 0)
+    n_ei = ue._native.UE_STATIC_MAX_EDGES + (1 if which == "edges" else 0)
     with pytest.raises(ue.UEError) as ei:
-        ue.power_iteration_static(i32, z, z, i32, big, i64)
+        ue.power_iteration_static(**_sized(n_t, n_ei))
     assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("bad", ["edge_tri", "tri_code"])
+def test_static_power_iteration_refuses_out_of_range_indices(ue, bad):
+    """Indices that leave the caller's arrays are checked in the kernels before any access
+    (the element is skipped) and the call returns UE_ERR_ARG; the next good call is exact."""
+    a = _sized(64, 32)
+    a["tri_code"].fill_(2 * 32)       # every edge a boundary edge: valid
+    if bad == "edge_tri":
+        a["edge_tri"][5, 1] = 64      # one past the last triangle
+    else:
+        a["tri_code"][7, 2] = 2 * 33  # one past the zero slot
+    with pytest.raises(ue.UEError) as ei:
+        ue.power_iteration_static(**a)
+    assert ei.value.code == -1
+    ms = meshgen.cavity_te11_mesh()
+    rho_ref, dev = _device_inputs(ue, ms, seed=9)
+    assert abs(ue.power_iteration_static(**dev, iters=200, seed=9) / rho_ref - 1.0) <= 1e-12
