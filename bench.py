@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = ("scatterer-4M: unit square, PEC walls and PEC equilateral hole (side 0.2, centre "
             "(0.5,0.5)), spacing graded 2e-4..8e-4, jitter 0.2h, FP32 fields, line source "
             "x=0.35, w0=2*pi*20")
+WORKLOAD_PLASMA = ("plasma-1M: unit square, PEC walls, uniform spacing (1M triangles), jitter 0.2h, "
+                   "Gaussian density n = (0.8 w0)^2 exp(-|r-c|^2/(2*0.15^2)) on the nodes, cold-plasma "
+                   "current on the edges, collision rate 0.01 w0, FP32 fields, line source x=0.35, "
+                   "w0=2*pi*20")
 METRIC = "cell-updates/s"
 UNIT = "triangle-steps/s"
 L2_BYTES = 129e6
@@ -170,51 +174,108 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def load_workload():
+def load_workload(name="scatterer"):
+    """(mesh, source edge ids, amplitudes, w0, t0, tau, node density or None, nu, description)."""
     import meshgen
+    w0 = 2 * math.pi * 20
+    if name == "plasma":
+        ms = meshgen.cached("plasma_1003", meshgen.plasma_square_mesh)
+        ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+        dens = meshgen.plasma_density_nodes(ms.xy, w0)
+        return ms, ids, amp, w0, 0.1, 0.05, dens, 0.01 * w0, WORKLOAD_PLASMA
     ms = meshgen.cached("scatterer_1002", meshgen.scatterer_mesh)
     ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, 2e-4)
-    return ms, ids, amp, 2 * math.pi * 20, 0.1, 0.05
+    return ms, ids, amp, w0, 0.1, 0.05, None, 0.0, WORKLOAD
 
 
-def cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, max_steps, budget_s):
-    """Time the FP64 oracle on this workload for up to max_steps steps / budget_s seconds."""
-    from oracle import leapfrog as lf, mesh as om, operators
-    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
-    src = lf.Source(ids, amp, w0, t0, tau)
-    st = lf.initial_state(ops)
-    cols = ops.col_of_edge[src.edge_ids]
-    st = lf.step(ops, st, dt, source=src, src_cols=cols)      # first touch
-    n = 0
-    t = time.perf_counter()
-    while n < max_steps and (n < 3 or time.perf_counter() - t < budget_s):
-        st = lf.step(ops, st, dt, source=src, src_cols=cols)
-        n += 1
-    el = time.perf_counter() - t
-    return ms.n_tris * n / el, n, el
+def _oracle_ops(ms):
+    from oracle import mesh as om, operators
+    return operators.Operators(om.canonicalize(ms.xy, ms.tris))
+
+
+def cpu_oracle_rates(ms, ops, state, dt, budget_s, plasma=None, source=None, numpy_too=True):
+    """Time the oracle on this workload from `state`: the compiled C step (oracle/cstep.c) on one
+    host core and on all of them, and the numpy oracle on one core, each for about budget_s
+    seconds.  Returns {"c1": (rate, steps, seconds, threads), "call": ..., "numpy": ...}."""
+    from oracle import cstep, leapfrog as lf
+    out = {}
+    stepper = cstep.Stepper(ops)
+    for key, threads in (("c1", 1), ("call", cstep.host_cores())):
+        st, used = stepper.run(state, dt, 1, plasma, source, threads)      # first touch
+        t = time.perf_counter()
+        st, used = stepper.run(st, dt, 2, plasma, source, threads)
+        per = (time.perf_counter() - t) / 2
+        n = max(2, int(budget_s / max(per, 1e-6)))
+        t = time.perf_counter()
+        st, used = stepper.run(st, dt, n, plasma, source, threads)
+        el = time.perf_counter() - t
+        out[key] = (ms.n_tris * n / el, n, el, used)
+    if numpy_too:
+        nbar = plasma.nbar(ops) if plasma is not None else None
+        cols = ops.col_of_edge[source.edge_ids] if source is not None else None
+        st = lf.step(ops, state, dt, plasma, source, nbar, cols)
+        n = 0
+        t = time.perf_counter()
+        while n < 3 or time.perf_counter() - t < budget_s:
+            st = lf.step(ops, st, dt, plasma, source, nbar, cols)
+            n += 1
+        el = time.perf_counter() - t
+        out["numpy"] = (ms.n_tris * n / el, n, el, 1)
+    return out
+
+
+def cpu_baseline_line(rates, what):
+    """The bench line's cpu_baseline: the compiled oracle on all host cores, with the one-core
+    and numpy figures beside it."""
+    r, n, el, used = rates["call"]
+    line = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{n} leap-frog steps of {what} in {el:.1f} s (oracle/cstep.c, FP64, {used} threads)"}
+    r1, n1, el1, _ = rates["c1"]
+    line["single_core"] = {"value": r1, "cores": 1,
+                           "sample": f"{n1} steps in {el1:.1f} s (oracle/cstep.c, FP64, one thread)"}
+    if "numpy" in rates:
+        r2, n2, el2, _ = rates["numpy"]
+        line["numpy_oracle"] = {"value": r2, "cores": 1,
+                                "sample": f"{n2} steps in {el2:.1f} s (oracle/leapfrog.py, numpy/scipy.sparse FP64)"}
+    return line
 
 
 def run_reference(args):
+    """The oracle timed alone on the host cores (the reference arm): the compiled C step on all
+    cores, over a bounded number of steps of the same workload."""
     world, rank, _ = _dist()
     if rank != 0:
         return
-    ms, ids, amp, w0, t0, tau = load_workload()
-    from oracle import mesh as om, operators, spectral
+    from oracle import cstep, leapfrog as lf, spectral
+    ms, ids, amp, w0, t0, tau, dens, nu, what = load_workload(args.workload)
+    ops = _oracle_ops(ms)
     # the oracle takes the same dt the library would (dt = 0.5 * 2 / rho, rho by power iteration)
-    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
     rho, _ = spectral.power_iteration(ops, 200)
     dt = 1.0 / rho
-    del ops
-    rate, n, el = cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, args.steps, 60.0)
+    src = lf.Source(ids, amp, w0, t0, tau)
+    pl = lf.Plasma(dens, nu) if dens is not None else None
+    stepper = cstep.Stepper(ops)
+    st = lf.initial_state(ops)
+    st, _ = stepper.run(st, dt, 1, pl, src, threads=cstep.host_cores())    # first touch
+    t = time.perf_counter()
+    for _ in range(args.warmup):
+        st, _ = stepper.run(st, dt, 1, pl, src, threads=cstep.host_cores())
+    per = (time.perf_counter() - t) / max(1, args.warmup)
+    # a bounded sample: at most about a minute of steps
+    n = max(1, min(args.steps, int(60.0 / max(per, 1e-6))))
+    t = time.perf_counter()
+    st, used = stepper.run(st, dt, n, pl, src, threads=cstep.host_cores())
+    el = time.perf_counter() - t
+    rate = ms.n_tris * n / el
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_tris": ms.n_tris},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} of {args.steps} leap-frog steps on the full mesh "
-                                   f"(numpy/scipy.sparse FP64, {el:.1f} s)"},
+        "config": {"workload": what, "n_tris": ms.n_tris},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{n} of {args.steps} leap-frog steps on the full mesh after {args.warmup} warm-up steps "
+                                   f"(oracle/cstep.c, FP64, {used} threads, {el:.1f} s)"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -234,7 +295,7 @@ def run_native(args):
     b.build()
     import paper_1812_01448_gb300 as ue
 
-    ms, ids, amp, w0, t0, tau = load_workload()
+    ms, ids, amp, w0, t0, tau, dens, nu, what = load_workload(args.workload)
     stream = torch.cuda.current_stream()
     blocked = args.variant == "blocked"
     tiled = ue.UE_REORDER_GREEDY if args.tiler == "greedy" else ue.UE_REORDER_KD
@@ -254,6 +315,8 @@ def run_native(args):
         m.geometry_build(stream=stream, **vopt)
     dt, rho, _ = m.get_dt()
     m.set_source(ids, amp, w0, t0, tau)
+    if dens is not None:
+        m.set_plasma(dens, nu)
     st = m.stats()
     n_t, n_ei = st["n_tris"], st["n_interior_edges"]
     part_stats = partition_stats(m) if blocked else None
@@ -317,28 +380,34 @@ def run_native(args):
         roof["streamed_gbs"] = prof_bytes[1] / (prof_ms[0] * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
-    E0 = torch.zeros(m.n_edges, dtype=torch.float64, pin_memory=True).numpy()
-    B0 = torch.zeros(m.n_tris, dtype=torch.float64, pin_memory=True).numpy()
-    Eo = torch.empty(m.n_edges, dtype=torch.float64, pin_memory=True).numpy()
-    Bo = torch.empty(m.n_tris, dtype=torch.float64, pin_memory=True).numpy()
+    pinned = lambda n: torch.zeros(n, dtype=torch.float64, pin_memory=True).numpy()
+    E0, B0, Eo, Bo = pinned(m.n_edges), pinned(m.n_tris), pinned(m.n_edges), pinned(m.n_tris)
+    J0 = Jo = None
+    if dens is not None:
+        J0, Jo = pinned(m.n_edges), pinned(m.n_edges)
     barrier()
     torch.cuda.synchronize()
+    d0 = m.stats()["direct_fields"]
     t_e2e = time.perf_counter()
-    m.write_fields(E0, B0, stream=stream)
+    m.write_fields(E0, B0, J0, stream=stream)
     m.set_step(0)
     m.step_n(args.steps, stream)
-    m.read_fields(out={"E": Eo, "B": Bo}, stream=stream)
+    m.read_fields(j=dens is not None, out={"E": Eo, "B": Bo, "j": Jo}, stream=stream)
     t_e2e = max_over_ranks(time.perf_counter() - t_e2e, dist)
-    io = 8.0 * (m.n_edges + m.n_tris)
+    io = 8.0 * (m.n_edges + m.n_tris + (m.n_edges if dens is not None else 0))
     e2e = {"value": world * n_t * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
-           "what": "ue_write_fields (pinned host) + ue_step_n(K) + ue_read_fields (pinned host)"}
+           "what": "ue_write_fields (pinned host) + ue_step_n(K) + ue_read_fields (pinned host)",
+           "fields_moved_in_place": m.stats()["direct_fields"] - d0}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n, el = cpu_oracle_rate(ms, ids, amp, w0, t0, tau, dt, 10 ** 9, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} leap-frog steps of the full mesh in {el:.1f} s (numpy/scipy.sparse FP64, one thread)"}
+        from oracle import leapfrog as lf
+        ops = _oracle_ops(ms)
+        rates = cpu_oracle_rates(ms, ops, lf.initial_state(ops), dt, args.cpu_seconds,
+                                 plasma=lf.Plasma(dens, nu) if dens is not None else None,
+                                 source=lf.Source(ids, amp, w0, t0, tau))
+        cpu = cpu_baseline_line(rates, "the full mesh")
 
     if rank == 0:
         clocks = clk.summary()
@@ -346,7 +415,7 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_tris": n_t, "n_interior_edges": n_ei,
+            "config": {"workload": what, "n_tris": n_t, "n_interior_edges": n_ei,
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
                        "variant": (f"blocked k={args.block_depth} {args.tiler} tiles<={args.tile_tris} "
                                 f"threads={args.tb_threads or 512}" if blocked
@@ -609,7 +678,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="seconds of each CPU baseline sample (compiled oracle on one and on all "
+                         "cores, numpy oracle)")
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
     ap.add_argument("--tile-tris", type=int, default=2500)
     ap.add_argument("--frame", type=int, default=0,
@@ -620,7 +691,9 @@ def main(argv=None):
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
-    ap.add_argument("--workload", choices=["scatterer", "batch", "learned", "modes", "relax"], default="scatterer")
+    ap.add_argument("--workload", choices=["scatterer", "plasma", "batch", "learned", "modes", "relax"],
+                    default="scatterer",
+                    help="scatterer: scatterer-4M (the default); plasma: plasma-1M (cold-plasma current)")
     ap.add_argument("--relax-points", type=int, default=100_000)
     ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)

@@ -115,6 +115,8 @@ typedef struct ue_stats_t {
                                  /* space allocated before it starts)                          */
     double rho_lo, rho_hi;       /* certified bracket (UE_DT_LEARNED), 0 otherwise            */
     double rho_hat;              /* learned prediction (UE_DT_LEARNED), 0 otherwise           */
+    int64_t direct_fields;       /* field arrays that ue_write_fields / ue_read_fields moved  */
+                                 /* in place in pinned host memory (no staging copy)          */
 } ue_stats_t;
 
 /* Fill *opt with defaults (RCM, FP32, power-iteration dt, safety 0.5, 200 iterations). */
@@ -167,8 +169,19 @@ int ue_set_source(ue_mesh* m, const int32_t* edge_ids, const double* amp, int64_
 
 /* Set E^0 (n_edges values; boundary entries ignored, except the outer edges of a framed mesh),
  * B^{1/2} (n_tris values) and, in plasma, j^{-1/2} (n_edges values, may be NULL = 0).  Any
- * pointer may be NULL to leave that field.  A PML frame's own fields are zeroed. */
+ * pointer may be NULL to leave that field.  A PML frame's own fields are zeroed.
+ * When every given array is 8-byte aligned pinned host memory (cudaHostAlloc, or registered
+ * with cudaHostRegister) and the mesh has no PML frame, the kernels read the arrays in place
+ * through their mapped device addresses; otherwise they are first copied to the device.  The
+ * results are the same either way. */
 int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream);
+
+/* Halo exchange of a mesh partitioned across ranks ("Divide and conqueror": parts exchange the
+ * values on their shared boundary every step): B of the triangles with caller ids ids[0..n)
+ * is written to buf (scatter = 0) or set from buf (scatter = 1), packed in the field type
+ * (float, or double for UE_PREC_FP64).  ids and buf are DEVICE pointers owned by the caller.
+ * Synchronous on `stream`.  Ids outside [0, n_tris) are not followed: UE_ERR_ARG. */
+int ue_exchange_tris(ue_mesh* m, const int32_t* ids, int64_t n, void* buf, int32_t scatter, void* stream);
 
 /* Advance n_steps leap-frog steps, asynchronously on `stream`.  Errors of the launches are
  * reported here; device-side conditions surface at the next synchronous call. */
@@ -176,7 +189,8 @@ int ue_step_n(ue_mesh* m, int64_t n_steps, void* stream);
 
 /* Copy the fields back in the caller's numbering (synchronous).  E, j: n_edges values (0 on
  * boundary edges, except the outer edges of a framed mesh); B: n_tris values.  Any pointer may
- * be NULL.  Returns UE_ERR_UNSTABLE (after copying) if the energy watchdog has flagged the run. */
+ * be NULL.  Pinned host arrays are written in place by the kernels, as in ue_write_fields.
+ * Returns UE_ERR_UNSTABLE (after copying) if the energy watchdog has flagged the run. */
 int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream);
 
 /* Energy W = sum d_i |e_i| E_i^2 + sum S_j B_j^2 of eq. 8 (eq. 7 metric) of the current fields,

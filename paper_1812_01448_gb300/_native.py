@@ -39,7 +39,7 @@ class Stats(C.Structure):
                 ("rho", C.c_double), ("rho_source", C.c_int32), ("precision", C.c_int32),
                 ("bytes_per_step", C.c_double), ("kernel_launches", C.c_int64),
                 ("dt_setup_ms", C.c_double), ("rho_lo", C.c_double), ("rho_hi", C.c_double),
-                ("rho_hat", C.c_double)]
+                ("rho_hat", C.c_double), ("direct_fields", C.c_int64)]
 
 
 P = C.c_void_p
@@ -59,6 +59,7 @@ SIGNATURES = [
     ("ue_set_source", C.c_int, [P, PI32, PD, I64, C.c_double, C.c_double, C.c_double]),
     ("ue_write_fields", C.c_int, [P, PD, PD, PD, P]),
     ("ue_step_n", C.c_int, [P, I64, P]),
+    ("ue_exchange_tris", C.c_int, [P, P, I64, P, C.c_int32, P]),
     ("ue_read_fields", C.c_int, [P, PD, PD, PD, P]),
     ("ue_energy", C.c_int, [P, PD, P]),
     ("ue_check", C.c_int, [P, PD, PI32]),

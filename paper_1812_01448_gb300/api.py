@@ -151,6 +151,13 @@ class Mesh:
         N.check(N.lib().ue_write_fields(self._h, _dptr(E), _dptr(B), _dptr(j), _stream(stream)),
                 "ue_write_fields")
 
+    def exchange_tris(self, ids, buf, scatter: bool, stream=None):
+        """B of the triangles with caller ids `ids` (int32 CUDA tensor) into `buf` (a CUDA tensor
+        of the field type, scatter=False) or from it (scatter=True): ue_exchange_tris."""
+        N.check(N.lib().ue_exchange_tris(self._h, C.c_void_p(ids.data_ptr()), int(ids.numel()),
+                                         C.c_void_p(buf.data_ptr()), 1 if scatter else 0, _stream(stream)),
+                "ue_exchange_tris")
+
     def step_n(self, n: int, stream=None):
         N.check(N.lib().ue_step_n(self._h, int(n), _stream(stream)), "ue_step_n")
 

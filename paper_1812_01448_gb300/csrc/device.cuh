@@ -171,7 +171,10 @@ struct TBDev {
     int* hdr = nullptr;           // n_tiles * 48 ints
     int4* trec = nullptr;         // local triangle records {gid, codes01, code2, bits of dt/S}
     int64_t n_trec = 0;
-    int4* erec = nullptr;         // local edge records {gid, R | L << 16, bits of cU, bits of pb}
+    int* erec = nullptr;          // local edge records, 3 ints: {gid, R | L << 16, bits of cU},
+                                  // the sign bit of cU set on source edges; each tile's records
+                                  // start at a multiple of 4 (16-byte aligned bulk copies)
+    float* epb = nullptr;         // plasma coefficient per local edge record (plasma only)
     int64_t n_erec = 0;
     int2* tsrc = nullptr;         // per-tile source records {local edge, source index}
     int max_tri_loc = 0, max_edge_loc = 0;
@@ -186,6 +189,8 @@ struct TBDev {
 
 int tb_threads();
 bool tb_fits(int max_tri_loc, int max_edge_loc, int threads);
+// whether launch_tb runs the pipelined persistent form k_tbp for these tiles
+bool tb_pipelined(int max_tri_loc, int max_edge_loc, int threads, bool plasma);
 cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
 // k steps of the blocked kernel reading buffer `cur`, writing buffer cur ^ 1; the source uses
 // g-table entries gbase .. gbase + k - 1.
@@ -229,6 +234,20 @@ cudaError_t launch_fields_in(const DevMesh& m, const double* E_caller, const dou
 cudaError_t launch_fields_out(const DevMesh& m, double* E_caller, double* B_caller,
                               double* J_caller, const int64_t* edge_caller,
                               const int64_t* perm_tri, const double* elen, cudaStream_t s);
+// The same transfers with the caller's arrays in pinned host memory, passed as their mapped
+// device addresses: k_of[n_e] = stored interior edge of each caller edge or -1, inv[n_t] =
+// stored triangle of each caller triangle.  E (and J) are written on every caller edge.
+cudaError_t launch_fields_in_direct(const DevMesh& m, const double* E_caller, const double* B_caller,
+                                    const double* J_caller, const int32_t* k_of, const int32_t* inv,
+                                    const double* elen, int64_t n_e, cudaStream_t s);
+cudaError_t launch_fields_out_direct(const DevMesh& m, double* E_caller, double* B_caller, double* J_caller,
+                                     const int32_t* k_of, const int32_t* inv, const double* elen,
+                                     int64_t n_e, cudaStream_t s);
+// Halo exchange of a partitioned mesh: B at caller triangle ids[0..n) to buf (scatter = 0) or
+// from buf (scatter = 1), in the field type; inv[n_t] = stored triangle of each caller one.
+// Ids outside [0, n_t) are skipped and counted in *bad (device).
+cudaError_t launch_tri_exchange(const DevMesh& m, const int32_t* inv, const int32_t* ids, int64_t n, void* buf,
+                                int scatter, unsigned* bad, cudaStream_t s);
 cudaError_t launch_plasma_coeff(const DevMesh& m, const double* n_nodes, const int32_t* edge_nodes,
                                 double nu, double dt, cudaStream_t s);
 // src_c[i] = dt_grp * |e| * amp[i], dt of the source's group.

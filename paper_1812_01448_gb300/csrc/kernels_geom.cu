@@ -331,6 +331,78 @@ __global__ void k_fields_out_tris(const T* __restrict__ B, const int64_t* __rest
     Bc[perm[j]] = (double)B[j];
 }
 
+// Direct transfer with the caller's arrays in pinned host memory (read and written through
+// their mapped device addresses): one thread per caller element, so that the host side is
+// accessed in order, and the same rounding as the staged kernels above.  k_of[c] = stored
+// interior edge of caller edge c or -1; inv[c] = stored triangle of caller triangle c.
+template <typename T>
+__global__ void k_fields_in_edges_direct(const double* __restrict__ Ec, const int32_t* __restrict__ k_of,
+                                         const double* __restrict__ elen, T* __restrict__ U, int64_t n_e,
+                                         int64_t n_ei) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) U[n_ei] = (T)0;
+    if (c >= n_e) return;
+    const int32_t k = k_of[c];
+    if (k >= 0) U[k] = (T)(elen[k] * Ec[c]);
+}
+
+template <typename T>
+__global__ void k_fields_in_tris_direct(const double* __restrict__ Bc, const int32_t* __restrict__ inv,
+                                        T* __restrict__ B, int64_t n_t) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_t) return;
+    B[inv[c]] = (T)Bc[c];
+}
+
+template <typename T>
+__global__ void k_fields_out_edges_direct(const T* __restrict__ U, const int32_t* __restrict__ k_of,
+                                          const double* __restrict__ elen, double* __restrict__ Ec,
+                                          int64_t n_e) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_e) return;
+    const int32_t k = k_of[c];
+    Ec[c] = k >= 0 ? (double)U[k] / elen[k] : 0.0;
+}
+
+template <typename T>
+__global__ void k_fields_out_tris_direct(const T* __restrict__ B, const int32_t* __restrict__ inv,
+                                         double* __restrict__ Bc, int64_t n_t) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_t) return;
+    Bc[c] = (double)B[inv[c]];
+}
+
+// B of the triangles with the given caller ids to / from a packed buffer (the halo exchange
+// of a partitioned mesh): out[i] = B[inv[ids[i]]], B[inv[ids[i]]] = in[i].  Ids outside
+// [0, n_t) are skipped and counted in *bad.
+template <typename T>
+__global__ void k_gather_tris(const T* __restrict__ B, const int32_t* __restrict__ inv,
+                              const int32_t* __restrict__ ids, T* __restrict__ out, int64_t n,
+                              int64_t n_t, unsigned* __restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = ids[i];
+    if (c < 0 || c >= n_t) {
+        atomicAdd(bad, 1u);
+        return;
+    }
+    out[i] = B[inv[c]];
+}
+
+template <typename T>
+__global__ void k_scatter_tris(T* __restrict__ B, const int32_t* __restrict__ inv,
+                               const int32_t* __restrict__ ids, const T* __restrict__ in, int64_t n,
+                               int64_t n_t, unsigned* __restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = ids[i];
+    if (c < 0 || c >= n_t) {
+        atomicAdd(bad, 1u);
+        return;
+    }
+    B[inv[c]] = in[i];
+}
+
 template <typename T>
 __global__ void k_plasma_coeff(const double* __restrict__ nn, const int32_t* __restrict__ en,
                                T* __restrict__ pb, double c, int64_t n_ei) {
@@ -620,6 +692,56 @@ cudaError_t launch_fields_out(const DevMesh& m, double* Ec, double* Bc, double* 
     if (Bc) {
         if (f64) k_fields_out_tris<double><<<blocks_for(m.n_t), kThreads, 0, s>>>((const double*)m.B, perm_tri, Bc, m.n_t);
         else k_fields_out_tris<float><<<blocks_for(m.n_t), kThreads, 0, s>>>((const float*)m.B, perm_tri, Bc, m.n_t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_in_direct(const DevMesh& m, const double* Ec, const double* Bc, const double* Jc,
+                                    const int32_t* k_of, const int32_t* inv, const double* elen, int64_t n_e,
+                                    cudaStream_t s) {
+    const bool f64 = m.precision == UE_PREC_FP64;
+    const int64_t ne = n_e > 0 ? n_e : 1;
+    for (int f = 0; f < 2; ++f) {
+        const double* src = f == 0 ? Ec : Jc;
+        void* dst = f == 0 ? m.U : m.J;
+        if (!src || !dst) continue;
+        if (f64) k_fields_in_edges_direct<double><<<blocks_for(ne), kThreads, 0, s>>>(src, k_of, elen, (double*)dst, n_e, m.n_ei);
+        else k_fields_in_edges_direct<float><<<blocks_for(ne), kThreads, 0, s>>>(src, k_of, elen, (float*)dst, n_e, m.n_ei);
+    }
+    if (Bc) {
+        if (f64) k_fields_in_tris_direct<double><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (double*)m.B, m.n_t);
+        else k_fields_in_tris_direct<float><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (float*)m.B, m.n_t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_out_direct(const DevMesh& m, double* Ec, double* Bc, double* Jc, const int32_t* k_of,
+                                     const int32_t* inv, const double* elen, int64_t n_e, cudaStream_t s) {
+    const bool f64 = m.precision == UE_PREC_FP64;
+    for (int f = 0; f < 2; ++f) {
+        double* dst = f == 0 ? Ec : Jc;
+        const void* src = f == 0 ? m.U : m.J;
+        if (!dst || n_e == 0) continue;
+        if (!src) return cudaErrorInvalidValue;
+        if (f64) k_fields_out_edges_direct<double><<<blocks_for(n_e), kThreads, 0, s>>>((const double*)src, k_of, elen, dst, n_e);
+        else k_fields_out_edges_direct<float><<<blocks_for(n_e), kThreads, 0, s>>>((const float*)src, k_of, elen, dst, n_e);
+    }
+    if (Bc) {
+        if (f64) k_fields_out_tris_direct<double><<<blocks_for(m.n_t), kThreads, 0, s>>>((const double*)m.B, inv, Bc, m.n_t);
+        else k_fields_out_tris_direct<float><<<blocks_for(m.n_t), kThreads, 0, s>>>((const float*)m.B, inv, Bc, m.n_t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_exchange(const DevMesh& m, const int32_t* inv, const int32_t* ids, int64_t n, void* buf,
+                                int scatter, unsigned* bad, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (m.precision == UE_PREC_FP64) {
+        if (scatter) k_scatter_tris<double><<<blocks_for(n), kThreads, 0, s>>>((double*)m.B, inv, ids, (const double*)buf, n, m.n_t, bad);
+        else k_gather_tris<double><<<blocks_for(n), kThreads, 0, s>>>((const double*)m.B, inv, ids, (double*)buf, n, m.n_t, bad);
+    } else {
+        if (scatter) k_scatter_tris<float><<<blocks_for(n), kThreads, 0, s>>>((float*)m.B, inv, ids, (const float*)buf, n, m.n_t, bad);
+        else k_gather_tris<float><<<blocks_for(n), kThreads, 0, s>>>((const float*)m.B, inv, ids, (float*)buf, n, m.n_t, bad);
     }
     return cudaGetLastError();
 }

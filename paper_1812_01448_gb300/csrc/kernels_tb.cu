@@ -3,11 +3,12 @@
 // neighbouring tiles own.  The paper's "Divide and conqueror" partitions exchange boundary
 // values every step; here the exchange is replaced by redundant halo work inside one launch.
 //
-// Per launch a tile reads its records (static, 16 B per local triangle and per local edge) and
-// the fields of its local set from the "in" buffers, and writes only the owned values to the
-// "out" buffers (double buffering, so that neighbours still read time level n).  Every
-// arithmetic operation repeats the plain kernels' sequence exactly (device.cuh rn_* helpers
-// and the shared source_g), so the results are bit-identical to the plain two-kernel step.
+// Per launch a tile reads its records (static: 16 B per local triangle, 12 B per local edge,
+// plus 4 B per local edge of plasma coefficient) and the fields of its local set from the "in"
+// buffers, and writes only the owned values to the "out" buffers (double buffering, so that
+// neighbours still read time level n).  Every arithmetic operation repeats the plain kernels'
+// sequence of correctly rounded operations (device.cuh rn_* helpers and the shared source_g),
+// so the results are bit-identical to the plain two-kernel step.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -21,7 +22,8 @@ constexpr int kNT = 512;
 struct TBArgs {
     const int* hdr;
     const int4* trec;
-    const int4* erec;
+    const int* erec;    // 3 ints per local edge record: gid, R | L << 16, bits of cU (sign: source)
+    const float* epb;   // plasma coefficient per local edge record
     const int2* tsrc;
     const float* Bin;
     const float* Uin;
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     int erl[ES];
     float ecu[ES], epb[ES];
     const int4* tr = a.trec + h[6];
-    const int4* er = a.erec + h[7];
+    const int* er = a.erec + 3 * (size_t)h[7];
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
         const int l = tid + i * NT;
@@ -79,13 +81,13 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     for (int i = 0; i < ES; ++i) {
         const int l = tid + i * NT;
         if (l < nel) {
-            const int4 r = __ldg(er + l);
-            erl[i] = r.y;
-            ecu[i] = __int_as_float(r.z);
-            Ul[l] = __ldg(a.Uin + r.x);
+            const int gid = __ldg(er + 3 * l);
+            erl[i] = __ldg(er + 3 * l + 1);
+            ecu[i] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
+            Ul[l] = __ldg(a.Uin + gid);
             if constexpr (PLASMA) {
-                epb[i] = __int_as_float(r.w);
-                Jl[l] = __ldg(a.Jin + r.x);
+                epb[i] = __ldg(a.epb + h[7] + l);
+                Jl[l] = __ldg(a.Jin + gid);
             }
         }
     }
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
     float* Ecu = reinterpret_cast<float*>(Erl + nel);
     float* Epb = Ecu + nel;
     const int4* tr = a.trec + h[6];
-    const int4* er = a.erec + h[7];
+    const int* er = a.erec + 3 * (size_t)h[7];
     for (int l = tid; l < ntl; l += NT) {
         const int4 r = __ldg(tr + l);
         Tc[l] = make_int2(r.y, r.z);
@@ -225,13 +227,13 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
         Bl[l] = __ldg(a.Bin + r.x);
     }
     for (int l = tid; l < nel; l += NT) {
-        const int4 r = __ldg(er + l);
-        Erl[l] = r.y;
-        Ecu[l] = __int_as_float(r.z);
-        Ul[l] = __ldg(a.Uin + r.x);
+        const int gid = __ldg(er + 3 * l);
+        Erl[l] = __ldg(er + 3 * l + 1);
+        Ecu[l] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
+        Ul[l] = __ldg(a.Uin + gid);
         if constexpr (PLASMA) {
-            Epb[l] = __int_as_float(r.w);
-            Jl[l] = __ldg(a.Jin + r.x);
+            Epb[l] = __ldg(a.epb + h[7] + l);
+            Jl[l] = __ldg(a.Jin + gid);
         }
     }
     if (tid == 0) {
@@ -321,29 +323,67 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
     }
 }
 
-// Pipelined persistent form (no plasma): one CTA per SM walks the tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...  Global loads run ahead of the steps:
+// Pipelined persistent form: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...  Global loads run ahead of the steps:
 // - headers: a ring of three; tile i+2's header is copied (TMA bulk copy) while tile i steps;
 // - records: tile i+1's records are copied (TMA bulk copies) into a staging area as soon as
 //   tile i has moved its own records from there into registers;
 // - fields: after step min(3, k) of tile i, tile i+1's fields are gathered (4-byte cp.async)
 //   into the second field buffer.
-// So a tile's loads overlap the previous tile's steps instead of stalling the SM.  Each thread
-// keeps its slots' records in registers for the k steps and repeats k_tb's arithmetic slot by
-// slot, so the results are bit-identical.
-// Dynamic shared memory: two field buffers of FB floats (B at 0, U at TL), then the staging
-// records (TL triangle records, EL edge records).
-template <int NT, int TS, int ES, bool SRC>
-__global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, int EL) {
+// A launch of kk < k_max steps stages and gathers only the rings it reads: triangles of level
+// <= kk and edges of level <= kk - 1.
+//
+// Each thread keeps, for its slots (local element tid + i*NT), the element's current value (B,
+// U, and J in plasma media) and its record in registers; shared memory holds the values that
+// other threads gather.  So a half-step per element is its gathers, the arithmetic and one
+// store.  Records are turned into byte offsets of the gathered values once per tile, and the
+// signs of eq. 4 into the coefficients: with x_q = s_q U_q,
+//   rn(rn(x0 + x1) + x2) = s0 rn(rn(U0 + s0 s1 U1) + s0 s2 U2)
+// because round-to-nearest is odd (rn(-y) = -rn(y)), so
+//   B - (dt/S) rn(rn(x0 + x1) + x2) = fma(-s0 dt/S, fma(s0 s2, U2, fma(s0 s1, U1, U0)), B)
+// rounds exactly as the plain kernel's select-and-add does.  Gathers of G slots are issued
+// before any of their stores.  The field buffers sit at compile-time offsets (capacity TS*NT
+// triangles and ES*NT edges); a gather is one shift or mask, one add to the buffer's 32-bit
+// shared address and one shared load.
+// Dynamic shared memory: two field buffers of FB floats (B at 0, U at TLC, J at JOFF), then
+// the staging records (TLC triangle records, ELC edge records, ELC plasma coefficients).
+template <int NT, int TS, int ES, bool PLASMA>
+struct TbpLayout {
+    static constexpr int TLC = TS * NT;                      // local triangle capacity
+    static constexpr int ELC = ES * NT;                      // local edge capacity
+    static constexpr int UOFF = TLC;                         // U in a field buffer (floats)
+    static constexpr int JOFF = TLC + ELC + 4;               // J in a field buffer (plasma)
+    static constexpr int FB = PLASMA ? JOFF + ELC : TLC + ELC + 4;
+    static constexpr size_t TSTAGE = 2 * 4 * (size_t)FB;     // byte offsets in shared memory
+    static constexpr size_t ESTAGE = TSTAGE + 16 * (size_t)TLC;
+    static constexpr size_t PSTAGE = ESTAGE + 12 * (size_t)ELC;
+    static constexpr size_t SMEM = PSTAGE + (PLASMA ? 4 * (size_t)ELC : 0);
+    static_assert(4 * (TLC + ELC + 1) < 65536, "byte offsets must fit 16 bits");
+    static_assert(FB % 4 == 0 && ELC % 4 == 0, "16-byte aligned buffers and staging");
+};
+
+// Shared-memory load at a 32-bit shared address (the buffer's address plus a byte offset).  The
+// gathers of a phase read values that a barrier separates from their stores, so the loads may
+// move freely among the phase's own stores (which go to other elements).
+__device__ __forceinline__ float lds_at(uint32_t base, unsigned off) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(base + off));
+    return v;
+}
+
+template <int NT, int TS, int ES, int G, bool PLASMA, bool SRC>
+__global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
+    using Lay = TbpLayout<NT, TS, ES, PLASMA>;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ __align__(16) int hs[3][48];
     __shared__ __align__(8) uint64_t bar_h, bar_r;
     const int tid = threadIdx.x;
-    const int FB = (TL + EL + 1 + 3) & ~3;
     const int stride = gridDim.x;
+    const int kk = a.ksteps;
     float* F0 = reinterpret_cast<float*>(smraw);
-    int4* tstage = reinterpret_cast<int4*>(F0 + 2 * FB);
-    int4* estage = tstage + TL;
+    int4* tstage = reinterpret_cast<int4*>(smraw + Lay::TSTAGE);
+    int* estage = reinterpret_cast<int*>(smraw + Lay::ESTAGE);
+    float* pstage = reinterpret_cast<float*>(smraw + Lay::PSTAGE);
     if (tid == 0) {
         mbar_init(&bar_h, 1);
         mbar_init(&bar_r, 1);
@@ -357,6 +397,10 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
         if (!mbar_wait(bar, ph)) ok = false;
         ph ^= 1u;
     };
+    // local triangles of level <= kk, local edges of level <= kk - 1 (header layout in
+    // tiles_host.cpp)
+    auto n_tri = [&](const int* h) { return h[16 + kk]; };
+    auto n_edge = [&](const int* h) { return h[32 + kk - 1]; };
     auto issue_header = [&](int t, int slot) {
         if (tid == 0) {
             fence_proxy_async();
@@ -365,31 +409,37 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
     };
     auto issue_records = [&](int slot) {
         if (tid == 0) {
-            const uint32_t tb = 16u * (uint32_t)hs[slot][4], eb = 16u * (uint32_t)hs[slot][5];
+            const int* h = hs[slot];
+            const uint32_t ne4 = (uint32_t)(n_edge(h) + 3) & ~3u;
+            const uint32_t tb = 16u * (uint32_t)n_tri(h), eb = 12u * ne4, pbb = PLASMA ? 4u * ne4 : 0u;
             fence_proxy_async();
-            mbar_expect_tx(&bar_r, tb + eb);
-            if (tb) bulk_copy_g2s(tstage, a.trec + hs[slot][6], tb, &bar_r);
-            if (eb) bulk_copy_g2s(estage, a.erec + hs[slot][7], eb, &bar_r);
+            mbar_expect_tx(&bar_r, tb + eb + pbb);
+            if (tb) bulk_copy_g2s(tstage, a.trec + h[6], tb, &bar_r);
+            if (eb) bulk_copy_g2s(estage, a.erec + 3 * (size_t)h[7], eb, &bar_r);
+            if (PLASMA && pbb) bulk_copy_g2s(pstage, a.epb + h[7], pbb, &bar_r);
         }
     };
-    auto issue_fields = [&](int slot, int b) {
-        const int ntl = hs[slot][4], nel = hs[slot][5];
-        float* Bn = F0 + b * FB;
-        float* Un = Bn + TL;
+    auto issue_fields = [&](int slot, float* Fn) {
+        const int* h = hs[slot];
+        const int nt = n_tri(h), ne = n_edge(h);
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
             const int l = tid + i * NT;
-            if (l < ntl) cp_async4(Bn + l, a.Bin + tstage[l].x);
+            if (l < nt) cp_async4(Fn + l, a.Bin + tstage[l].x);
         }
 #pragma unroll
         for (int i = 0; i < ES; ++i) {
             const int l = tid + i * NT;
-            if (l < nel) cp_async4(Un + l, a.Uin + estage[l].x);
+            if (l < ne) {
+                const int g = estage[3 * l];
+                cp_async4(Fn + Lay::UOFF + l, a.Uin + g);
+                if constexpr (PLASMA) cp_async4(Fn + Lay::JOFF + l, a.Jin + g);
+            }
         }
-        if (tid == 0) Un[nel] = 0.f;
+        if (tid == 0) Fn[Lay::UOFF + h[5]] = 0.f;   // the zero slot of boundary edges
         cp_async_commit();
     };
-    int tile = blockIdx.x, it = 0, cur = 0;
+    int tile = blockIdx.x, it = 0;
     // prologue: first tile's header, records and fields; the second tile's header
     if (tile < n_tiles) {
         issue_header(tile, 0);
@@ -397,55 +447,92 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
         issue_records(0);
         if (tile + stride < n_tiles) issue_header(tile + stride, 1);
         wait_bar(&bar_r, ph_r);
-        issue_fields(0, 0);
+        issue_fields(0, F0);
         cp_async_wait_all();
         if (tile + stride < n_tiles) wait_bar(&bar_h, ph_h);
     }
     __syncthreads();
-    int tc01[TS], tc2[TS];
-    float tcb[TS];
-    int erl[ES];
-    float ecu[ES];
-    for (; tile < n_tiles; tile += stride, ++it) {
+    // per slot: triangle gather offsets (U0 | U1 << 16, U2), -s0 dt/S, s0 s1, s0 s2 and B;
+    // edge gather offsets (B_R | B_L << 16), dt|e|/d and U (plasma: pb and J)
+    unsigned toff[TS], toff2[TS];
+    float tcb[TS], ts1[TS], ts2[TS], tb[TS];
+    unsigned erl[ES];
+    float ecu[ES], eu[ES], epb[ES], ej[ES];
+    unsigned srcm = 0;
+
+    for (int cur = 0; tile < n_tiles; tile += stride, ++it, cur ^= 1) {
+        float* Fc = F0 + cur * Lay::FB;
+        float* Fn = F0 + (cur ^ 1) * Lay::FB;
+        const uint32_t Fcb = smem_addr(Fc);
         const bool has_next = tile + stride < n_tiles, has_next2 = tile + 2 * stride < n_tiles;
         const int slot = it % 3, slot1 = (it + 1) % 3, slot2 = (it + 2) % 3;
         const int* h = hs[slot];
-        float* Bl = F0 + cur * FB;
-        float* Ul = Bl + TL;
-        const int ntl = h[4], nel = h[5];
+        const int nt_upd = h[16 + kk - 1], ne = n_edge(h);
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
             const int l = tid + i * NT;
-            if (l < ntl) {
+            if (l < nt_upd) {
                 const int4 r = tstage[l];
-                tc01[i] = r.y;
-                tc2[i] = r.z;
-                tcb[i] = __int_as_float(r.w);
+                const unsigned c0 = (unsigned)r.y & 0xFFFFu, c1 = (unsigned)r.y >> 16, c2 = (unsigned)r.z;
+                toff[i] = (4u * (Lay::UOFF + (c0 >> 1))) | ((4u * (Lay::UOFF + (c1 >> 1))) << 16);
+                toff2[i] = 4u * (Lay::UOFF + (c2 >> 1));
+                const float cb = __int_as_float(r.w);
+                tcb[i] = (c0 & 1u) ? cb : -cb;
+                ts1[i] = ((c0 ^ c1) & 1u) ? -1.f : 1.f;
+                ts2[i] = ((c0 ^ c2) & 1u) ? -1.f : 1.f;
+                tb[i] = Fc[l];
             }
         }
+        if constexpr (SRC) srcm = 0;
 #pragma unroll
         for (int i = 0; i < ES; ++i) {
             const int l = tid + i * NT;
-            if (l < nel) {
-                const int4 r = estage[l];
-                erl[i] = r.y;
-                ecu[i] = __int_as_float(r.z);
+            if (l < ne) {
+                const int cub = estage[3 * l + 2];
+                erl[i] = (unsigned)estage[3 * l + 1] << 2;
+                ecu[i] = fabsf(__int_as_float(cub));
+                if constexpr (SRC) srcm |= (cub < 0 ? 1u : 0u) << i;
+                eu[i] = Fc[Lay::UOFF + l];
+                if constexpr (PLASMA) {
+                    epb[i] = pstage[l];
+                    ej[i] = Fc[Lay::JOFF + l];
+                }
             }
         }
         __syncthreads();   // the staging area is free for the next tile's records
         if (has_next) issue_records(slot1);
         if (has_next2) issue_header(tile + 2 * stride, slot2);
-        const int s_fields = a.ksteps < 3 ? a.ksteps : 3;
-        for (int s = 1; s <= a.ksteps; ++s) {
-            const int lim = a.ksteps - s;
-            const int eend = h[32 + lim];
+        const int s_fields = kk < 3 ? kk : 3;
+#pragma unroll 1
+        for (int s = 1; s <= kk; ++s) {
+            const int lim = kk - s;
+            const int eend = h[32 + lim], tend = h[16 + lim];
+            // E half-step (eq. 3; eqs. 5-6 in plasma media)
 #pragma unroll
-            for (int i = 0; i < ES; ++i) {
-                const int l = tid + i * NT;
-                if (l < eend) {
-                    const float bR = Bl[erl[i] & 0xFFFF];
-                    const float bL = Bl[(unsigned)erl[i] >> 16];
-                    Ul[l] = rn_fma(ecu[i], rn_sub(bR, bL), Ul[l]);
+            for (int g0 = 0; g0 < ES; g0 += G) {
+                float bR[G], bL[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int i = g0 + q;
+                    if (i < ES && tid + i * NT < eend) {
+                        bR[q] = lds_at(Fcb, erl[i] & 0xFFFFu);
+                        bL[q] = lds_at(Fcb, erl[i] >> 16);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int i = g0 + q;
+                    if (i < ES && tid + i * NT < eend) {
+                        const float uo = eu[i];
+                        float un = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo);
+                        if constexpr (PLASMA) {
+                            const float jn = rn_fma(a.pa, ej[i], rn_mul(epb[i], uo));
+                            ej[i] = jn;
+                            un = rn_fma(a.mdt, jn, un);
+                        }
+                        eu[i] = un;
+                        Fc[Lay::UOFF + tid + i * NT] = un;
+                    }
                 }
             }
             if constexpr (SRC) {
@@ -456,46 +543,67 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
                         if (q.x < eend) {
                             const float g = (float)__ldg(a.gtab + (size_t)__ldg(a.src_grp + q.y) * a.gstride +
                                                          a.gbase + s - 1);
-                            Ul[q.x] = rn_fma(__ldg(a.src_c + q.y), g, Ul[q.x]);
+                            Fc[Lay::UOFF + q.x] = rn_fma(__ldg(a.src_c + q.y), g, Fc[Lay::UOFF + q.x]);
                         }
                     }
                 }
             }
             __syncthreads();
-            const int tend = h[16 + lim];
+            if constexpr (SRC) {
+                // source edges take their value back from shared memory
+                if (srcm) {
 #pragma unroll
-            for (int i = 0; i < TS; ++i) {
-                const int l = tid + i * NT;
-                if (l < tend) {
-                    const int c0 = tc01[i], c1 = (unsigned)tc01[i] >> 16, c2 = tc2[i];
-                    const float u0 = Ul[(c0 & 0xFFFF) >> 1], u1 = Ul[c1 >> 1], u2 = Ul[c2 >> 1];
-                    const float x0 = (c0 & 1) ? -u0 : u0;
-                    const float x1 = (c1 & 1) ? -u1 : u1;
-                    const float x2 = (c2 & 1) ? -u2 : u2;
-                    Bl[l] = rn_fma(-tcb[i], rn_add(rn_add(x0, x1), x2), Bl[l]);
+                    for (int i = 0; i < ES; ++i)
+                        if (((srcm >> i) & 1u) && tid + i * NT < eend) eu[i] = Fc[Lay::UOFF + tid + i * NT];
+                }
+            }
+            // B half-step (eq. 4)
+#pragma unroll
+            for (int g0 = 0; g0 < TS; g0 += G) {
+                float u0[G], u1[G], u2[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int i = g0 + q;
+                    if (i < TS && tid + i * NT < tend) {
+                        u0[q] = lds_at(Fcb, toff[i] & 0xFFFFu);
+                        u1[q] = lds_at(Fcb, toff[i] >> 16);
+                        u2[q] = lds_at(Fcb, toff2[i]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int i = g0 + q;
+                    if (i < TS && tid + i * NT < tend) {
+                        const float t = rn_fma(ts2[i], u2[q], rn_fma(ts1[i], u1[q], u0[q]));
+                        tb[i] = rn_fma(tcb[i], t, tb[i]);
+                        Fc[tid + i * NT] = tb[i];
+                    }
                 }
             }
             __syncthreads();
             if (has_next && s == s_fields) {
                 wait_bar(&bar_r, ph_r);
-                issue_fields(slot1, cur ^ 1);
+                issue_fields(slot1, Fn);
             }
         }
+        // owned values, from registers
         const int nto = h[1], neo = h[3];
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
             const int l = tid + i * NT;
-            if (l < nto) a.Bout[h[0] + l] = Bl[l];
+            if (l < nto) a.Bout[h[0] + l] = tb[i];
         }
 #pragma unroll
         for (int i = 0; i < ES; ++i) {
             const int l = tid + i * NT;
-            if (l < neo) a.Uout[h[2] + l] = Ul[l];
+            if (l < neo) {
+                a.Uout[h[2] + l] = eu[i];
+                if constexpr (PLASMA) a.Jout[h[2] + l] = ej[i];
+            }
         }
         if (has_next) cp_async_wait_all();
         if (has_next2) wait_bar(&bar_h, ph_h);
         __syncthreads();
-        cur ^= 1;
     }
     if (!ok) atomicOr(a.err, 1u);
     // the last CTA to finish advances the step counter (every CTA has read it by then)
@@ -510,16 +618,18 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles, int TL, in
     }
 }
 
-// Fill the coefficient slots of the tile records from the global coefficient arrays.
-__global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int4* __restrict__ erec,
-                          int64_t n_erec, const int4* __restrict__ tri, const float* __restrict__ cU,
-                          const float* __restrict__ pb) {
+// Fill the coefficient slots of the tile records from the global coefficient arrays: dt/S of
+// each triangle record, dt|e|/d of each edge record with the source flag kept in its sign bit,
+// and the plasma coefficient (pb may be NULL).  Padding records carry gid 0.
+__global__ void k_tb_fill(int4* __restrict__ trec, int64_t n_trec, int* __restrict__ erec,
+                          float* __restrict__ epb, int64_t n_erec, const int4* __restrict__ tri,
+                          const float* __restrict__ cU, const float* __restrict__ pb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_trec) trec[i].w = tri[trec[i].x].w;
     if (i < n_erec) {
-        const int g = erec[i].x;
-        erec[i].z = __float_as_int(fabsf(cU[g]));   // without the source flag
-        erec[i].w = pb ? __float_as_int(pb[g]) : 0;
+        const int g = erec[3 * i];
+        erec[3 * i + 2] = __float_as_int(cU[g]);
+        if (pb) epb[i] = pb[g];
     }
 }
 
@@ -532,21 +642,24 @@ cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int NT, int TS, int ES, bool SRC>
-cudaError_t launch_tbp_t(const TBArgs& a, int n_tiles, int grid, int TL, int EL, size_t smem,
-                         cudaStream_t s) {
-    auto kern = k_tbp<NT, TS, ES, SRC>;
+// gathers issued together per group of slots in k_tbp
+constexpr int kTbpGroup = 1;
+
+template <int NT, int TS, int ES, bool PLASMA, bool SRC>
+cudaError_t launch_tbp_t(const TBArgs& a, int n_tiles, int grid, cudaStream_t s) {
+    auto kern = k_tbp<NT, TS, ES, kTbpGroup, PLASMA, SRC>;
+    const size_t smem = TbpLayout<NT, TS, ES, PLASMA>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, s>>>(a, n_tiles, TL, EL);
+    kern<<<grid, NT, smem, s>>>(a, n_tiles);
     return cudaGetLastError();
 }
 
-template <int NT, int TS, int ES>
-cudaError_t launch_tbp_s(const TBArgs& a, bool src, int n_tiles, int grid, int TL, int EL,
-                         size_t smem, cudaStream_t s) {
-    return src ? launch_tbp_t<NT, TS, ES, true>(a, n_tiles, grid, TL, EL, smem, s)
-               : launch_tbp_t<NT, TS, ES, false>(a, n_tiles, grid, TL, EL, smem, s);
+// One form with the source branch for meshes with and without a source (the branch is one
+// uniform test per step; the form without it needs more registers than the 128 a thread has).
+template <int NT, int TS, int ES, bool PLASMA>
+cudaError_t launch_tbp_s(const TBArgs& a, bool, int n_tiles, int grid, cudaStream_t s) {
+    return launch_tbp_t<NT, TS, ES, PLASMA, true>(a, n_tiles, grid, s);
 }
 
 template <bool PLASMA, bool SRC>
@@ -567,23 +680,31 @@ cudaError_t launch_tb_ps(const TBArgs& a, bool plasma, bool src, int n_tiles, si
                : launch_tb_t<NT, TS, ES, MINB, G, false, false>(a, n_tiles, smem, s);
 }
 
+// Opt-in shared memory per CTA, less the static shared memory of the kernels.
+constexpr size_t kSmemMax = 227 * 1024 - 1024;
+
+// The k_tbp slot configuration (triangle slots, edge slots) for tiles of at most TL local
+// triangles and EL local edges, or (0, 0) when none fits (k_tb then runs).
+void tbp_config(int TL, int EL, bool plasma, int& ts, int& es) {
+    ts = es = 0;
+    auto fits = [&](int a, int b, size_t smem) { return TL <= a * kNT && EL <= b * kNT && smem <= kSmemMax; };
+    if (!plasma) {
+        if (fits(4, 6, TbpLayout<kNT, 4, 6, false>::SMEM)) ts = 4, es = 6;
+        else if (fits(6, 9, TbpLayout<kNT, 6, 9, false>::SMEM)) ts = 6, es = 9;
+        else if (fits(8, 12, TbpLayout<kNT, 8, 12, false>::SMEM)) ts = 8, es = 12;
+    } else {
+        if (fits(4, 6, TbpLayout<kNT, 4, 6, true>::SMEM)) ts = 4, es = 6;
+        else if (fits(6, 9, TbpLayout<kNT, 6, 9, true>::SMEM)) ts = 6, es = 9;
+    }
+}
+
 }  // namespace
 
 int tb_threads() { return kNT; }
 
-// Register-slot configurations, smallest first: (threads, triangle slots, edge slots, CTAs
-// per SM the register budget is sized for).
 size_t tbs_smem(int ntl, int nel, bool plasma) {
     return 4 * ((size_t)ntl + nel + 1) + (plasma ? 4 * ((size_t)nel + 1) : 0) + 8 +
            12 * (size_t)ntl + (plasma ? 12 : 8) * (size_t)nel;
-}
-
-// k_tbp: two field buffers and the staging records, within the opt-in shared memory per CTA
-// (static shared memory of the kernel aside).
-constexpr size_t kTbpSmemMax = 227 * 1024 - 512;
-size_t tbp_smem(int tl, int el) {
-    const size_t fb = ((size_t)tl + el + 1 + 3) & ~(size_t)3;
-    return 2 * 4 * fb + 16 * ((size_t)tl + el);
 }
 
 bool tb_fits(int max_tri_loc, int max_edge_loc, int threads) {
@@ -592,12 +713,19 @@ bool tb_fits(int max_tri_loc, int max_edge_loc, int threads) {
     return max_tri_loc <= 8 * kNT && max_edge_loc <= 12 * kNT;
 }
 
+bool tb_pipelined(int max_tri_loc, int max_edge_loc, int threads, bool plasma) {
+    int ts = 0, es = 0;
+    tbp_config(max_tri_loc, max_edge_loc, plasma, ts, es);
+    return threads != 1024 && ts > 0;
+}
+
 cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s) {
     const int64_t n = t.n_trec > t.n_erec ? t.n_trec : t.n_erec;
     if (n == 0) return cudaSuccess;
-    k_tb_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.trec, t.n_trec, t.erec, t.n_erec, m.tri,
-                                                        (const float*)m.cU,
-                                                        m.plasma ? (const float*)m.pb : nullptr);
+    // the plasma coefficients once their array exists (made when the plasma is baked)
+    const float* pb = (m.plasma && t.epb) ? (const float*)m.pb : nullptr;
+    k_tb_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.trec, t.n_trec, t.erec, t.epb, t.n_erec,
+                                                        m.tri, (const float*)m.cU, pb);
     return cudaGetLastError();
 }
 
@@ -607,6 +735,7 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     a.hdr = t.hdr;
     a.trec = t.trec;
     a.erec = t.erec;
+    a.epb = t.epb;
     a.tsrc = t.tsrc;
     a.Bin = (const float*)t.B[cur];
     a.Uin = (const float*)t.U[cur];
@@ -626,6 +755,8 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     a.pa = (float)m.pa;
     a.mdt = (float)(-m.dt);
     const bool src = m.n_src > 0;
+    if (ksteps < 1 || ksteps > 15) return cudaErrorInvalidValue;
+    if (m.plasma && !t.epb) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * ((size_t)t.max_tri_loc + t.max_edge_loc + 1 +
                                          (m.plasma ? (size_t)t.max_edge_loc + 1 : 0));
     if (t.threads == 1024) {
@@ -636,13 +767,18 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
                    : launch_tbs_t<false, false>(a, (int)t.n_tiles, sm2, s);
     }
     // pipelined persistent form when two field buffers and the staging records fit
-    const size_t smem_p = tbp_smem(t.max_tri_loc, t.max_edge_loc);
-    if (!m.plasma && t.sms > 0 && smem_p <= kTbpSmemMax) {
-        const int TL = t.max_tri_loc, EL = t.max_edge_loc, nt = (int)t.n_tiles;
+    int ts = 0, es = 0;
+    tbp_config(t.max_tri_loc, t.max_edge_loc, m.plasma, ts, es);
+    if (t.sms > 0 && ts > 0) {
+        const int nt = (int)t.n_tiles;
         const int grid = nt < t.sms ? nt : t.sms;
-        if (TL <= 4 * kNT && EL <= 6 * kNT) return launch_tbp_s<kNT, 4, 6>(a, src, nt, grid, TL, EL, smem_p, s);
-        if (TL <= 6 * kNT && EL <= 9 * kNT) return launch_tbp_s<kNT, 6, 9>(a, src, nt, grid, TL, EL, smem_p, s);
-        return launch_tbp_s<kNT, 8, 12>(a, src, nt, grid, TL, EL, smem_p, s);
+        if (m.plasma) {
+            if (ts == 4) return launch_tbp_s<kNT, 4, 6, true>(a, src, nt, grid, s);
+            return launch_tbp_s<kNT, 6, 9, true>(a, src, nt, grid, s);
+        }
+        if (ts == 4) return launch_tbp_s<kNT, 4, 6, false>(a, src, nt, grid, s);
+        if (ts == 6) return launch_tbp_s<kNT, 6, 9, false>(a, src, nt, grid, s);
+        return launch_tbp_s<kNT, 8, 12, false>(a, src, nt, grid, s);
     }
     if (t.max_tri_loc <= 4 * kNT && t.max_edge_loc <= 6 * kNT)
         return launch_tb_ps<kNT, 4, 6, 2, 3>(a, m.plasma, src, (int)t.n_tiles, smem, s);

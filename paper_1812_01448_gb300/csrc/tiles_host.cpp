@@ -11,6 +11,7 @@
 //   4 local triangles, 5 local edges, 6 triangle-record offset, 7 edge-record offset,
 //   8 source-record offset, 9 source records, 10 k_max,
 //   16 + r: local triangles of level <= r, 32 + r: local edges of level <= r  (r <= 15).
+// Edge records of a tile start at a multiple of 4 records (padding records follow its last).
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -142,6 +143,12 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,
             ts.erec.push_back(loc[hm.edge_tri[2 * k]] | (loc[hm.edge_tri[2 * k + 1]] << 16));
             ts.erec.push_back(0);
             ts.erec.push_back(0);
+            ts.erec_tile.push_back(out);
+        }
+        // each tile's edge records start at a multiple of 4 (padding records: gid 0, R = L = 0),
+        // so that the blocked kernel's bulk copies of 12-byte records stay 16-byte aligned
+        while ((ts.erec.size() / 4) % 4 != 0) {
+            ts.erec.insert(ts.erec.end(), {0, 0, 0, 0});
             ts.erec_tile.push_back(out);
         }
         ts.max_tri_loc = std::max<int>(ts.max_tri_loc, (int)ntl);

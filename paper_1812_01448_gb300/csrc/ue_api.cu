@@ -84,6 +84,11 @@ struct ue_mesh {
     double *d_O = nullptr, *d_S = nullptr, *d_elen = nullptr, *d_d = nullptr;
     // transfer buffers in caller numbering
     double *d_Ec = nullptr, *d_Bc = nullptr, *d_Jc = nullptr;
+    // caller -> stored maps of the direct transfers (made on first use)
+    int32_t* d_kof = nullptr;       // n_edges: stored interior edge of each caller edge, or -1
+    int32_t* d_inv = nullptr;       // n_tris: stored triangle of each caller triangle
+    int64_t direct_fields = 0;      // field arrays moved by the direct path
+    unsigned* d_xbad = nullptr;     // bad-id counter of the halo exchange
     DevMesh dm;
 
     // plasma and source, kept on the host so that a rebuild can re-bake them
@@ -433,6 +438,8 @@ int bake_plasma(ue_mesh* m, cudaStream_t s) {
         }
         UE_CUDA(cudaMemsetAsync(m->tb.J[0], 0, esz * dm.n_ei_pad, s));
         UE_CUDA(cudaMemsetAsync(m->tb.J[1], 0, esz * dm.n_ei_pad, s));
+        if (!m->tb.epb && !alloc_into(m, m->tb.epb, m->tb.n_erec + 4, 4, s))
+            return fail(UE_ERR_ALLOC, "tile plasma coefficients");
         UE_CUDA(ue::launch_tb_fill(m->tb, dm, s));
     }
     if (m->has_reg) {
@@ -503,8 +510,15 @@ int region_sources(ue_mesh* m, cudaStream_t s) {
 }
 
 int bake_source(ue_mesh* m, cudaStream_t s) {
-    const int rc = bake_source_mesh(m, s);
-    if (rc != UE_OK || !m->has_reg) return rc;
+    int rc = bake_source_mesh(m, s);
+    if (rc != UE_OK) return rc;
+    if (m->variant == UE_VARIANT_BLOCKED && m->tb.erec) {
+        // the tile records carry the source flags of the coefficients (the pipelined kernel
+        // takes a source edge's value back after the source is added)
+        UE_CUDA(ue::launch_tb_fill(m->tb, m->dm, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!m->has_reg) return rc;
     return region_sources(m, s);
 }
 
@@ -669,15 +683,24 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     tb.max_tri_loc = ts.max_tri_loc;
     tb.max_edge_loc = ts.max_edge_loc;
     tb.threads = m->tb_threads;
+    // edge records go to the device as 3 ints {gid, R | L << 16, cU}: the coefficient is filled
+    // by launch_tb_fill, the plasma coefficient kept apart (tb.epb)
+    std::vector<int32_t> e3(3 * (size_t)tb.n_erec);
+    for (int64_t i = 0; i < tb.n_erec; ++i) {
+        e3[3 * i] = ts.erec[4 * i];
+        e3[3 * i + 1] = ts.erec[4 * i + 1];
+        e3[3 * i + 2] = 0;
+    }
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
-              alloc_into(m, tb.erec, tb.n_erec + 1, 16, s) && alloc_into(m, tb.done, 2, 4, s) &&
+              alloc_into(m, tb.erec, 3 * (tb.n_erec + 4), 4, s) && alloc_into(m, tb.done, 2, 4, s) &&
               alloc_into(m, tb.B[1], m->dm.n_t_pad, 4, s) && alloc_into(m, tb.U[1], m->dm.n_ei_pad, 4, s);
     if (!ok) return fail(UE_ERR_ALLOC, "tile arrays");
     tb.B[0] = m->dm.B;
     tb.U[0] = m->dm.U;
     UE_CUDA(cudaMemcpyAsync(tb.hdr, ts.hdr.data(), 4 * ts.hdr.size(), cudaMemcpyHostToDevice, s));
     UE_CUDA(cudaMemcpyAsync(tb.trec, ts.trec.data(), 4 * ts.trec.size(), cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(tb.erec, ts.erec.data(), 4 * ts.erec.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(tb.erec, e3.data(), 4 * e3.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaStreamSynchronize(s));   // e3 is a host temporary
     UE_CUDA(cudaMemsetAsync(tb.done, 0, 8, s));
     {
         int dev = 0;
@@ -822,6 +845,7 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
     if (!ok) {
         dev_free_all(m, s);
         m->d_tri_nb = nullptr;
+        m->d_kof = m->d_inv = nullptr;
         return fail(UE_ERR_ALLOC, "device allocation failed");
     }
     {
@@ -1032,6 +1056,8 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     UE_CUDA(cudaStreamSynchronize(s));
     dev_free_all(m, s);
     m->d_tri_nb = nullptr;
+    m->d_kof = m->d_inv = nullptr;
+    m->d_xbad = nullptr;
     m->built = false;
     m->dm = DevMesh();
     m->tb = ue::TBDev();
@@ -1422,17 +1448,72 @@ int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, 
     return bake_source(m, nullptr);
 }
 
+namespace {
+
+// The caller's array as a device address when it lies in pinned (page-locked, mapped) host
+// memory and is 8-byte aligned; NULL otherwise (the transfer is then staged through a copy).
+const double* mapped_view(const double* p) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & 7u)) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // not a CUDA-known pointer: clear the error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<const double*>(a.devicePointer);
+}
+
+// Caller -> stored maps of the direct transfers, made on first use.
+int ensure_caller_maps(ue_mesh* m, cudaStream_t s) {
+    if (m->d_kof) return UE_OK;
+    const HostMesh& h = m->hm;
+    std::vector<int32_t> kof(h.n_edges), inv(h.n_tris);
+    for (int64_t c = 0; c < h.n_edges; ++c) kof[c] = (int32_t)h.k_of_edge[c];
+    for (int64_t j = 0; j < h.n_tris; ++j) inv[h.perm_tri[j]] = (int32_t)j;
+    int32_t *a = nullptr, *b = nullptr;
+    if (!alloc_into(m, a, h.n_edges, 4, s) || !alloc_into(m, b, h.n_tris, 4, s))
+        return fail(UE_ERR_ALLOC, "caller maps of the direct field transfer");
+    UE_CUDA(cudaMemcpyAsync(a, kof.data(), 4 * kof.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(b, inv.data(), 4 * inv.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    m->d_kof = a;
+    m->d_inv = b;
+    return UE_OK;
+}
+
+// Which of the given arrays go the direct way: all of them when each is pinned host memory and
+// the mesh has no PML frame (whose interface edges travel through the staging buffer).
+bool direct_transfer(const ue_mesh* m, const double* E, const double* B, const double* j,
+                     const double*& dE, const double*& dB, const double*& dj) {
+    dE = mapped_view(E);
+    dB = mapped_view(B);
+    dj = mapped_view(j);
+    if (m->dm.frame || m->fr.W > 0) return false;
+    return (!E || dE) && (!B || dB) && (!j || dj) && (E || B || j);
+}
+
+}  // namespace
+
 int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream) {
     Range nvtx_range("ue_write_fields");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
-    if (E) UE_CUDA(cudaMemcpyAsync(m->d_Ec, E, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
-    if (B) UE_CUDA(cudaMemcpyAsync(m->d_Bc, B, 8 * h.n_tris, cudaMemcpyHostToDevice, s));
-    if (j && m->dm.J) UE_CUDA(cudaMemcpyAsync(m->d_Jc, j, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
-    UE_CUDA(ue::launch_fields_in(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
-                                 (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
-                                 m->d_elen, s));
+    const double *dE = nullptr, *dB = nullptr, *dj = nullptr;
+    if (!m->dm.J) j = nullptr;
+    if (direct_transfer(m, E, B, j, dE, dB, dj)) {
+        // pinned host arrays: the kernels read them in place
+        const int rc = ensure_caller_maps(m, s);
+        if (rc != UE_OK) return rc;
+        UE_CUDA(ue::launch_fields_in_direct(m->dm, dE, dB, dj, m->d_kof, m->d_inv, m->d_elen, h.n_edges, s));
+        m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
+    } else {
+        if (E) UE_CUDA(cudaMemcpyAsync(m->d_Ec, E, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
+        if (B) UE_CUDA(cudaMemcpyAsync(m->d_Bc, B, 8 * h.n_tris, cudaMemcpyHostToDevice, s));
+        if (j) UE_CUDA(cudaMemcpyAsync(m->d_Jc, j, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
+        UE_CUDA(ue::launch_fields_in(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
+                                     j ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm, m->d_elen, s));
+    }
     if (m->dm.frame) {
         const ue::FrameDev& f = m->fd;
         const size_t esz = m->precision == UE_PREC_FP64 ? 8 : 4;
@@ -1453,6 +1534,22 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
         if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) UE_CUDA(cudaMemsetAsync(m->tb.done + 1, 0, 4, s));
     }
     UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int ue_exchange_tris(ue_mesh* m, const int32_t* ids, int64_t n, void* buf, int32_t scatter, void* stream) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (n < 0 || (n > 0 && (!ids || !buf))) return fail(UE_ERR_ARG, "NULL ids or buffer, or n < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_caller_maps(m, s);
+    if (rc != UE_OK) return rc;
+    if (!m->d_xbad && !alloc_into(m, m->d_xbad, 1, 4, s)) return fail(UE_ERR_ALLOC, "exchange counter");
+    UE_CUDA(cudaMemsetAsync(m->d_xbad, 0, 4, s));
+    UE_CUDA(ue::launch_tri_exchange(m->dm, m->d_inv, ids, n, buf, scatter ? 1 : 0, m->d_xbad, s));
+    unsigned bad = 0;
+    UE_CUDA(cudaMemcpyAsync(&bad, m->d_xbad, 4, cudaMemcpyDeviceToHost, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    if (bad) return fail(UE_ERR_ARG, "ue_exchange_tris: " + std::to_string(bad) + " ids outside [0, n_tris)");
     return UE_OK;
 }
 
@@ -1497,9 +1594,13 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             const int64_t batch = left < chunk ? left : chunk;
             UE_CUDA(ue::launch_gtab(m->dm, (int)batch, s));
             if (m->dm.n_src > 0) ++launched;
+            // ceil(batch / k) launches with step counts as even as possible (20 steps at k = 8:
+            // 7 + 7 + 6, not 8 + 8 + 4): each launch pays for its halo rings only up to its own
+            // depth, so even shares recompute fewer rings in total
+            const int64_t nl = (batch + k - 1) / k;
             int64_t done = 0;
-            while (done < batch) {
-                const int kk = (int)(batch - done < k ? batch - done : k);
+            for (int64_t i = 0; i < nl; ++i) {
+                const int kk = (int)(batch / nl + (i < batch % nl ? 1 : 0));
                 UE_CUDA(blocked_launch(m, kk, m->cur, (int)done, s));
                 set_current(m, m->cur ^ 1);
                 done += kk;
@@ -1541,18 +1642,34 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
-    if (E) UE_CUDA(cudaMemsetAsync(m->d_Ec, 0, 8 * h.n_edges, s));
-    if (j) UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
-    UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
-                                  (j && m->dm.J) ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm,
-                                  m->d_elen, s));
-    if (E && m->has_reg)
-        UE_CUDA(ue::launch_frame_iface_out(m->reg.f, m->reg.dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
-    else if (E && m->dm.frame)
-        UE_CUDA(ue::launch_frame_iface_out(m->fd, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
-    if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
-    if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
-    if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+    const double *dE = nullptr, *dB = nullptr, *dj = nullptr;
+    if (j && !m->dm.J) {
+        // no current in this medium: j reads as zero
+        UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
+        UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+        j = nullptr;
+    }
+    if (direct_transfer(m, E, B, j, dE, dB, dj)) {
+        // pinned host arrays: the kernels write them in place
+        const int rc = ensure_caller_maps(m, s);
+        if (rc != UE_OK) return rc;
+        UE_CUDA(ue::launch_fields_out_direct(m->dm, const_cast<double*>(dE), const_cast<double*>(dB),
+                                             const_cast<double*>(dj), m->d_kof, m->d_inv, m->d_elen,
+                                             h.n_edges, s));
+        m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
+    } else {
+        if (E) UE_CUDA(cudaMemsetAsync(m->d_Ec, 0, 8 * h.n_edges, s));
+        if (j) UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
+        UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
+                                      j ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm, m->d_elen, s));
+        if (E && m->has_reg)
+            UE_CUDA(ue::launch_frame_iface_out(m->reg.f, m->reg.dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+        else if (E && m->dm.frame)
+            UE_CUDA(ue::launch_frame_iface_out(m->fd, m->dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
+        if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+        if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 8 * h.n_tris, cudaMemcpyDeviceToHost, s));
+        if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
+    }
     double wd[4];
     UE_CUDA(cudaMemcpyAsync(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost, s));
     UE_CUDA(cudaStreamSynchronize(s));
@@ -1973,7 +2090,7 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
             const double ot = (double)(h.n_tris - (m->has_reg ? m->reg.n_own_t : 0));
             const double oe = (double)(h.n_ei - (m->has_reg ? m->reg.n_own_e : 0));
             bytes[0] = (double)per * ((20.0 + 12.0 * pl) * oe + 24.0 * ot);
-            bytes[1] = 20.0 * (double)m->tb.n_trec + (20.0 + 4.0 * pl) * (double)m->tb.n_erec + 4.0 * ot +
+            bytes[1] = 20.0 * (double)m->tb.n_trec + (16.0 + 8.0 * pl) * (double)m->tb.n_erec + 4.0 * ot +
                        (4.0 + 4.0 * pl) * oe;
             bytes[2] = m->has_reg ? (double)per * (20.0 * (double)m->reg.dm.n_ei + 24.0 * (double)m->reg.dm.n_t) : 0.0;
             if (!m->has_reg) ms[2] = 0;
@@ -2106,6 +2223,7 @@ int ue_stats(const ue_mesh* m, ue_stats_t* out) {
     out->rho_lo = m->rho_lo;
     out->rho_hi = m->rho_hi;
     out->rho_hat = m->rho_hat;
+    out->direct_fields = m->direct_fields;
     return UE_OK;
 }
 

@@ -34,7 +34,8 @@ struct TileSet {
     static constexpr int kHdr = 48;       // ints per tile header
     std::vector<int32_t> hdr;             // n_tiles * kHdr (layout in kernels_tb.cu)
     std::vector<int32_t> trec;            // 4 ints per local triangle: gid, codes01, code2, 0
-    std::vector<int32_t> erec;            // 4 ints per local edge: gid, R|L<<16, 0, 0
+    std::vector<int32_t> erec;            // 4 ints per local edge: gid, R|L<<16, 0, 0; each
+                                          // tile's records start at a multiple of 4 records
     std::vector<int64_t> erec_tile;       // per local edge record: its tile (for sources)
 };
 

@@ -227,3 +227,66 @@ def learned_params(ue):
         return learned.load_weights()
     except (OSError, ValueError):
         return mlp.init_params(29).astype(np.float32)
+
+
+def _ablation_rows(ue, meshes, p):
+    """Per mesh: rho_PI (200 FP64 iterations) and, from the one fused launch, with the shipped
+    network and with all parameters zero (z = 0: no network), rho_hat, rho_lo, rho_hi, whether
+    the bracket accepted, and the setup time."""
+    zero = np.zeros_like(p)
+    rows = []
+    for ms in meshes:
+        a = ue.Mesh(ms.xy, ms.tris)
+        a.geometry_build()
+        _, rho_pi, _ = a.get_dt()
+        a.close()
+        r = dict(n_tris=ms.tris.shape[0], rho_pi=rho_pi)
+        for tag, params in (("net", p), ("zero", zero)):
+            b = ue.Mesh(ms.xy, ms.tris)
+            b.geometry_build(dt_mode=ue.UE_DT_LEARNED, mlp_params=params)
+            _, rho, src = b.get_dt()
+            st = b.stats()
+            b.close()
+            r[tag] = dict(rho=rho, rho_hat=st["rho_hat"], rho_lo=st["rho_lo"], rho_hi=st["rho_hi"],
+                          accepted=src == ue.UE_RHO_LEARNED, ms=st["dt_setup_ms"])
+        rows.append(r)
+    return rows
+
+
+def test_what_the_trained_network_gains(ue):
+    """Ablation on held-out meshes (the learned corpus's recipe, 5k-60k triangles): the shipped
+    network against the same fused launch with every parameter zero, i.e. without the network.
+    Without it, rho_hat is the parameter-free base max_j sqrt(K_jj) and rho_lo is the Rayleigh
+    quotient of K^5 delta_j at j = argmax K_jj; with it, rho_hat = max_j exp(z_j + base_j) and
+    the quotient is taken at the network's argmax.  The dt used is 2 safety / max(rho_hat,
+    rho_lo) when the bracket accepts it.  What the network gains, on these meshes: its
+    correction takes rho_hat from the base's ~18% below rho to ~0.2%; and its argmax locates the
+    highest mode, so that the quotient there is within ~1e-4 of rho on every mesh, where the
+    quotient at argmax K_jj misses by several percent on some (a mesh whose largest K_jj is not
+    where the top mode lives).  The worst error of the rho that sets dt therefore drops."""
+    from paper_1812_01448_gb300 import learned
+    p = learned.load_weights()
+    rows = _ablation_rows(ue, _corpus_meshes(16, seed=2203, n_min=5000, n_max=60000), p)
+    e = lambda x, r: abs(x / r["rho_pi"] - 1)
+    err = {k: np.array([f(r) for r in rows]) for k, f in (
+        ("net_hat", lambda r: e(r["net"]["rho_hat"], r)), ("base", lambda r: e(r["zero"]["rho_hat"], r)),
+        ("rq_at_argmax_K", lambda r: e(r["zero"]["rho_lo"], r)), ("rq_at_net", lambda r: e(r["net"]["rho_lo"], r)),
+        ("net_used", lambda r: e(max(r["net"]["rho_hat"], r["net"]["rho_lo"]), r)),
+        ("zero_used", lambda r: e(max(r["zero"]["rho_hat"], r["zero"]["rho_lo"]), r)))}
+    acc_net = sum(r["net"]["accepted"] for r in rows)
+    acc_zero = sum(r["zero"]["accepted"] for r in rows)
+    for k, v in err.items():
+        print(f"ablation {k:15s}: median {np.median(v):.5f} max {v.max():.5f}")
+    print(f"ablation accepted: network {acc_net}/{len(rows)}, without {acc_zero}/{len(rows)}")
+    # every value is a certified side of rho: rho_lo below rho_PI (a converged lower bound),
+    # rho_hi above, for both
+    for r in rows:
+        for tag in ("net", "zero"):
+            assert r[tag]["rho_lo"] <= r["rho_pi"] * (1 + 1e-9) <= r[tag]["rho_hi"] * (1 + 2e-9)
+    assert np.median(err["net_hat"]) < 0.02
+    assert np.median(err["base"]) > 5 * np.median(err["net_hat"])
+    # the network's location: its quotient is never worse than argmax K_jj's in the worst case,
+    # and the rho that sets dt is closer to rho_PI in the worst case
+    assert err["rq_at_net"].max() <= err["rq_at_argmax_K"].max()
+    assert err["net_used"].max() < err["zero_used"].max()
+    assert acc_net == len(rows)

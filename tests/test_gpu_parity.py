@@ -358,3 +358,50 @@ def test_persistent_is_bit_identical_to_plain(ue, plasma):
     assert np.array_equal(Ea, Eb) and np.array_equal(Ba, Bb)
     if plasma:
         assert np.array_equal(Ja, Jb)
+
+
+@pytest.mark.parametrize("form", ["plain", "blocked", "plasma", "fp64"])
+def test_pinned_host_arrays_move_in_place_with_the_same_results(ue, cavity, form):
+    """ue_write_fields / ue_read_fields with pinned host arrays: the kernels read and write them
+    in place (the stats count each array moved that way), and every field equals the run
+    through pageable arrays, bit for bit."""
+    torch = pytest.importorskip("torch")
+    ms, ops = cavity
+    rng = np.random.default_rng(11)
+    E0 = rng.standard_normal(ops.mesh.n_edges)
+    E0[~ops.mesh.interior] = 0.0
+    B0 = rng.standard_normal(ms.tris.shape[0])
+    j0 = rng.standard_normal(ops.mesh.n_edges) if form == "plasma" else None
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+
+    def pinned(a):
+        t = torch.empty(a.size, dtype=torch.float64, pin_memory=True).numpy()
+        t[:] = a
+        return t
+
+    out = []
+    for pin in (False, True):
+        load = dict(reorder=ue.UE_REORDER_GREEDY, tile_tris=256) if form == "blocked" else {}
+        opts = dict(variant=ue.UE_VARIANT_BLOCKED, block_depth=4) if form == "blocked" else {}
+        if form == "fp64":
+            opts["precision"] = ue.UE_PREC_FP64
+        m = ue.Mesh(ms.xy, ms.tris, **load)
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=2e-3, **opts)
+        m.set_source(ids, amp, 2 * math.pi * 20, 0.1, 0.05)
+        if form == "plasma":
+            m.set_plasma(np.full(ms.xy.shape[0], 400.0), 3.0)
+        conv = pinned if pin else (lambda a: a)
+        m.write_fields(E=conv(E0), B=conv(B0), j=None if j0 is None else conv(j0))
+        m.step_n(37)
+        o = {"E": conv(np.empty(m.n_edges)), "B": conv(np.empty(m.n_tris))}
+        if form == "plasma":
+            o["j"] = conv(np.empty(m.n_edges))
+        E, B, j = m.read_fields(j=form == "plasma", out=o)
+        direct = m.stats()["direct_fields"]
+        m.close()
+        assert direct == (0 if not pin else (6 if form == "plasma" else 4))
+        out.append((E.copy(), B.copy(), None if j is None else j.copy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    if form == "plasma":
+        assert np.array_equal(out[0][2], out[1][2])
+    assert np.all(out[1][0][~ops.mesh.interior] == 0)
