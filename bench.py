@@ -42,33 +42,61 @@ UNIT = "triangle-steps/s"
 L2_BYTES = 129e6
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
-# bench command at its configuration (summary and command in profiles/), keyed by the sha1 of
-# the kernel source it measured: used only while that source is unchanged, else null.
-NCU_TRAFFIC = {
-    # (variant, tiler, tile_tris, block_depth, threads, PML frame cells): (bytes per launch,
-    # source file, sha1, profile)
-    ("blocked", "greedy", 2500, 8, 512, 0): (306195200, "kernels_tb.cu",
-                                             "74268af160169826e19cf8973928e739eb32c11d",
-                                             "profiles/blocked_k_tbp_scatterer4M.md"),
-    ("blocked", "greedy", 2560, 8, 512, 0): (304521643, "kernels_tb.cu",
-                                          "74268af160169826e19cf8973928e739eb32c11d",
-                                          "profiles/blocked_k_tbp_scatterer4M.md"),
-    ("blocked", "kd", 2048, 8, 512, 0): (310911744, "kernels_tb.cu", "74268af160169826e19cf8973928e739eb32c11d",
-                                      "profiles/blocked_k_tbp_scatterer4M.md"),
-}
+# Counters of the dominant kernel per launch (DRAM bytes, shared-memory wavefronts, warp
+# instructions), from one ncu capture of the bench command at its configuration, stored in
+# profiles/ncu_counters.json with the sha1 of the sources they measured: used only while those
+# sources are unchanged, else reported as null.
+COUNTER_FILE = os.path.join(ROOT, "profiles", "ncu_counters.json")
+COUNTER_SOURCES = ("paper_1812_01448_gb300/csrc/kernels_tb.cu", "paper_1812_01448_gb300/csrc/device.cuh",
+                   "paper_1812_01448_gb300/csrc/tiles_host.cpp")
 
 
-def _traffic(key):
+def sources_sha1(paths=COUNTER_SOURCES) -> str:
     import hashlib
-    rec = NCU_TRAFFIC.get(key)
-    if rec is None:
-        return None, None
-    nbytes, src, sha, prof = rec
-    with open(os.path.join(ROOT, "paper_1812_01448_gb300", "csrc", src), "rb") as f:
-        if hashlib.sha1(f.read()).hexdigest() != sha:
-            return None, f"{prof}: kernel source changed since the capture"
-    return float(nbytes), prof
+    h = hashlib.sha1()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _counters(key: dict):
+    """(counters per launch, why-null) for a configuration key, from COUNTER_FILE."""
+    try:
+        with open(COUNTER_FILE) as f:
+            recs = json.load(f)["records"]
+    except (OSError, ValueError, KeyError):
+        return None, "no counter file"
+    sha = sources_sha1()
+    for r in recs:
+        if r["config"] == key:
+            if r["sources_sha1"] != sha:
+                return None, "kernel sources changed since the capture"
+            return r, None
+    return None, "configuration not captured"
+
+
+def onchip_roofline(c: dict, ms_per_launch: float, sm_mhz) -> dict:
+    """The blocked kernel against its on-chip limits, from counters of one launch (ncu) over the
+    launch time measured live: shared-memory wavefronts (one per SM per cycle: 32 banks x 4 B)
+    and warp instructions issued (four schedulers per SM, one each per cycle)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    hz = (sm_mhz or 2070.0) * 1e6
+    t = ms_per_launch * 1e-3
+    wf, ins = float(c["smem_wavefronts"]), float(c["warp_instructions"])
+    ideal = float(c["smem_instructions"])
+    return {
+        "bound": "shared-memory wavefronts",
+        "smem": {"achieved": wf / t, "peak": sms * hz, "unit": "wavefronts/s", "frac": wf / t / (sms * hz),
+                 "wavefronts_per_launch": wf, "conflict_free_wavefronts_per_launch": ideal,
+                 "bank_conflict_factor": wf / ideal if ideal else None},
+        "issue": {"achieved": ins / t, "peak": 4 * sms * hz, "unit": "warp instructions/s",
+                  "frac": ins / t / (4 * sms * hz), "instructions_per_launch": ins},
+        "clock_mhz": hz / 1e6, "sms": sms,
+        "counters": "profiles/ncu_counters.json (one ncu capture of this configuration; "
+                    "time is this run's CUDA-event launch time)",
+    }
 
 
 def partition_stats(m):
@@ -306,7 +334,8 @@ def run_native(args):
     variant = {"plain": ue.UE_VARIANT_PLAIN, "blocked": ue.UE_VARIANT_BLOCKED,
                "persistent": ue.UE_VARIANT_PERSISTENT}[args.variant]
     vopt = dict(variant=variant, block_depth=args.block_depth, graph_chunk=args.graph_chunk,
-                tb_threads=args.tb_threads)
+                tb_threads=args.tb_threads,
+                tb_kernel=ue.UE_TB_FUSED if args.tb_kernel == "fused" else ue.UE_TB_SPLIT)
     if args.quick_setup:
         # profiling runs: a fixed dt instead of the 200-iteration power iteration, so that few
         # kernel launches precede the captured ones
@@ -355,15 +384,19 @@ def run_native(args):
         names[2] = (f"frame region: gather, {args.block_depth} plain steps of the tiles next to the PML "
                     "frame with the frame, scatter (beside k_tbp on a second stream)")
     if blocked:
-        names[0] = (f"k_tbp: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, one CTA per SM "
+        kname = {1: "k_tb", 2: "k_tbs", 3: "k_tbp", 4: "k_tbf", 5: "k_tbf1"}.get(m.stats()["tb_kernel_used"], "?")
+        names[0] = (f"{kname}: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, one CTA per SM "
                     "with the next tile's loads in flight")
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
-    tkey = (args.variant, args.tiler if blocked else "", args.tile_tris if blocked else 0,
-            args.block_depth if blocked else 1,
-            (args.tb_threads or 512) if blocked else 0, args.frame)
-    traffic, traffic_src = _traffic(tkey)
+    ckey = {"workload": args.workload, "variant": args.variant, "tiler": args.tiler if blocked else "",
+            "tile_tris": args.tile_tris if blocked else 0, "block_depth": args.block_depth if blocked else 1,
+            "threads": (args.tb_threads or 512) if blocked else 0, "frame": args.frame,
+            "kernel": args.tb_kernel if blocked else ""}
+    crec, cwhy = _counters(ckey) if k == 0 else (None, "not the profiled kernel")
+    traffic = float(crec["per_launch"]["dram_bytes"]) if crec else None
+    traffic_src = "profiles/ncu_counters.json" if crec else cwhy
     step_bytes = st["bytes_per_step"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
@@ -374,30 +407,40 @@ def run_native(args):
                      "frac": step_bytes * args.steps / (ms_total * 1e-3) / 1e9 / peak,
                      "kernel_ms": [float(x) for x in prof_ms]}}
     if blocked:
-        roof["algorithmic_bytes_note"] = ("bytes of the same steps done by the plain kernels; the "
-                                          "blocked kernel streams streamed_bytes_per_launch")
+        roof["algorithmic_bytes_note"] = ("bytes of the same steps done by the plain kernels (an effective "
+                                          "rate: temporal blocking keeps them on chip, so frac can exceed 1); "
+                                          "the blocked kernel streams streamed_bytes_per_launch, and its "
+                                          "binding resource is in onchip")
         roof["streamed_bytes_per_launch"] = prof_bytes[1]
         roof["streamed_gbs"] = prof_bytes[1] / (prof_ms[0] * 1e-3) / 1e9
+    if crec is not None:
+        roof["onchip"] = onchip_roofline(crec["per_launch"], prof_ms[k], clk.summary().get("sm_mhz"))
 
-    # end to end through the public API with host buffers
-    pinned = lambda n: torch.zeros(n, dtype=torch.float64, pin_memory=True).numpy()
+    # end to end through the public API with host buffers: the fields in the product's
+    # precision (float32, ue_write_fields_f32 / ue_read_fields_f32) by default, or as doubles
+    f32 = args.e2e_fields == "f32"
+    wt = torch.float32 if f32 else torch.float64
+    pinned = lambda n: torch.zeros(n, dtype=wt, pin_memory=True).numpy()
     E0, B0, Eo, Bo = pinned(m.n_edges), pinned(m.n_tris), pinned(m.n_edges), pinned(m.n_tris)
     J0 = Jo = None
     if dens is not None:
         J0, Jo = pinned(m.n_edges), pinned(m.n_edges)
+    write = m.write_fields_f32 if f32 else m.write_fields
+    read = m.read_fields_f32 if f32 else m.read_fields
     barrier()
     torch.cuda.synchronize()
     d0 = m.stats()["direct_fields"]
     t_e2e = time.perf_counter()
-    m.write_fields(E0, B0, J0, stream=stream)
+    write(E0, B0, J0, stream=stream)
     m.set_step(0)
     m.step_n(args.steps, stream)
-    m.read_fields(j=dens is not None, out={"E": Eo, "B": Bo, "j": Jo}, stream=stream)
+    read(j=dens is not None, out={"E": Eo, "B": Bo, "j": Jo}, stream=stream)
     t_e2e = max_over_ranks(time.perf_counter() - t_e2e, dist)
-    io = 8.0 * (m.n_edges + m.n_tris + (m.n_edges if dens is not None else 0))
+    io = (4.0 if f32 else 8.0) * (m.n_edges + m.n_tris + (m.n_edges if dens is not None else 0))
+    api = "ue_write_fields_f32 / ue_read_fields_f32 (float32)" if f32 else "ue_write_fields / ue_read_fields (float64)"
     e2e = {"value": world * n_t * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
-           "what": "ue_write_fields (pinned host) + ue_step_n(K) + ue_read_fields (pinned host)",
+           "what": f"{api}: fields written from pinned host arrays, K steps, fields read into pinned host arrays",
            "fields_moved_in_place": m.stats()["direct_fields"] - d0}
 
     cpu = None
@@ -418,7 +461,7 @@ def run_native(args):
             "config": {"workload": what, "n_tris": n_t, "n_interior_edges": n_ei,
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
                        "variant": (f"blocked k={args.block_depth} {args.tiler} tiles<={args.tile_tris} "
-                                f"threads={args.tb_threads or 512}" if blocked
+                                f"threads={args.tb_threads or 512} {args.tb_kernel} kernel" if blocked
                                 else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
                        "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
                        "parallelism": f"replicas x{world}",
@@ -443,6 +486,67 @@ def _time_steps(fn, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) * 1e-3
+
+
+def run_cavity(args):
+    """The 1,024-triangle PEC cavity (TE(1,1) start, dt = 1/rho) over --steps steps: the whole
+    mesh is one tile without a halo, so all the steps run in one launch of one CTA with the mesh
+    in shared memory; against the plain path (two kernels per step, CUDA graphs).  Both are
+    bound by latency (launches, barriers, dependent shared loads), not by memory: the mesh's
+    step touches 55 KB."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    import meshgen
+    from oracle import leapfrog as lf, mesh as om, operators
+    ms = meshgen.cavity_te11_mesh()
+    stream = torch.cuda.current_stream()
+    probe = ue.Mesh(ms.xy, ms.tris)
+    probe.geometry_build()
+    dt, rho, _ = probe.get_dt()
+    probe.close()
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    B0 = meshgen.te_mode_b(ops.geom.O, 1, 1, 1.0, 0.5)
+    res = {}
+    for name, load, opts in (("one CTA", dict(reorder=ue.UE_REORDER_GREEDY, tile_tris=4096),
+                              dict(variant=ue.UE_VARIANT_BLOCKED, block_depth=8)),
+                             ("plain", dict(), dict(graph_chunk=32))):
+        m = ue.Mesh(ms.xy, ms.tris, **load)
+        m.geometry_build(stream=stream, dt_mode=ue.UE_DT_GIVEN, dt=dt, **opts)
+        m.write_fields(E=np.zeros(m.n_edges), B=B0, stream=stream)
+        m.step_n(args.warmup, stream)
+        l0 = m.stats()["kernel_launches"]
+        t = _time_steps(lambda: m.step_n(args.steps, stream), stream)
+        launches = m.stats()["kernel_launches"] - l0
+        m.write_fields(E=np.zeros(m.n_edges), B=B0, stream=stream)
+        m.set_step(0)
+        m.step_n(args.steps, stream)
+        E, B, _ = m.read_fields(stream=stream)
+        m.close()
+        res[name] = (m.n_tris * args.steps / t, t, launches, E, B)
+    st = lf.run(ops, lf.initial_state(ops, B=B0), dt, args.steps)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    v, t, launches, E, B = res["one CTA"]
+    line = {
+        "metric": "cell-updates/s (cavity, one CTA)", "value": v, "unit": UNIT, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "gpu_launches": launches,
+        "plain": {"value": res["plain"][0], "ms_per_step": 1e3 * res["plain"][1] / args.steps,
+                  "gpu_launches": res["plain"][2]},
+        "ratio_vs_plain": v / res["plain"][0],
+        "vs_oracle": {"E_rel_l2": rel(E, ops.extend(st.E)), "B_rel_l2": rel(B, st.B),
+                      "plain_E_rel_l2": rel(res["plain"][3], ops.extend(st.E))},
+        "roofline": {"bound": "latency", "ns_per_step": 1e9 * t / args.steps,
+                     "what": "one CTA of 512 threads, one barrier per step; the step of the 1,024 triangles "
+                             "is a chain of three shared loads and six floating-point operations per thread"},
+        "config": {"workload": f"cavity-1k: PEC rectangle 1 x 0.5, 33x17 jittered lattice, {ms.tris.shape[0]} "
+                               "triangles, TE(1,1) start, dt = 1/rho", "n_tris": int(ms.tris.shape[0]),
+                   "dt": dt, "rho": rho},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_batch(args):
@@ -691,9 +795,14 @@ def main(argv=None):
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
-    ap.add_argument("--workload", choices=["scatterer", "plasma", "batch", "learned", "modes", "relax"],
+    ap.add_argument("--e2e-fields", choices=["f32", "f64"], default="f32",
+                    help="element type of the host field arrays of the end-to-end measurement")
+    ap.add_argument("--tb-kernel", choices=["split", "fused"], default="split",
+                    help="blocked variant: the split kernel (edges, then triangles) or the fused one")
+    ap.add_argument("--workload", choices=["scatterer", "plasma", "cavity", "batch", "learned", "modes", "relax"],
                     default="scatterer",
-                    help="scatterer: scatterer-4M (the default); plasma: plasma-1M (cold-plasma current)")
+                    help="scatterer: scatterer-4M (the default); plasma: plasma-1M (cold-plasma current); "
+                         "cavity: the 1,024-triangle cavity in one CTA")
     ap.add_argument("--relax-points", type=int, default=100_000)
     ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)
@@ -711,6 +820,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "cavity":
+        run_cavity(args)
     elif args.workload == "modes":
         run_modes(args)
     elif args.workload == "relax":

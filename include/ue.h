@@ -80,6 +80,15 @@ typedef struct ue_mesh ue_mesh;  /* opaque, owned by the library until ue_mesh_f
 typedef void* (*ue_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*ue_free_fn)(void* ptr, void* stream, void* ctx);
 
+/* Kernel of the blocked variant (ue_options.tb_kernel).  Both give the plain step's results bit
+ * for bit.  SPLIT advances each tile's edges, then its triangles (two barriers per step); FUSED
+ * gives each triangle's thread its three edges as well (one barrier per step, half the
+ * shared-memory traffic, more instructions), for vacuum media with tiles of at most 4096
+ * triangles and halo; others run SPLIT.  A mesh that is a single tile without a halo (at most
+ * 2048 triangles) runs all the steps of a call in one launch of one CTA either way. */
+#define UE_TB_SPLIT 0
+#define UE_TB_FUSED 1
+
 typedef struct ue_options {
     int32_t reorder;       /* UE_REORDER_*, used by ue_mesh_load                              */
     int32_t precision;     /* UE_PREC_*                                                      */
@@ -96,11 +105,15 @@ typedef struct ue_options {
     double watchdog_growth;/* energy watchdog: flag growth by more than this factor between  */
                            /* two checks (default 10)                                        */
     int32_t watchdog_every;/* steps between energy checks inside ue_step_n (0 = off)         */
-    int32_t reserved1;
+    int32_t tb_kernel;     /* UE_VARIANT_BLOCKED, vacuum media: UE_TB_SPLIT (default) or     */
+                           /* UE_TB_FUSED (see below)                                        */
     const float* mlp_params;/* UE_DT_LEARNED: host array of UE_MLP_PARAMS floats             */
     double learned_margin; /* UE_DT_LEARNED: certified stability margin (default 1.05)       */
     int32_t timeout_ms;    /* UE_VARIANT_PERSISTENT: grid-barrier wait limit (default 2000)  */
-    int32_t test_skip_cta; /* UE_VARIANT_PERSISTENT, tests only: this CTA never arrives (-1) */
+    int32_t test_skip_cta; /* tests only (-1 otherwise): UE_VARIANT_PERSISTENT: this CTA     */
+                           /* never arrives at the grid barrier; UE_VARIANT_BLOCKED: this CTA */
+                           /* of the pipelined forms waits for record bytes that never come.  */
+                           /* Either way the bounded wait runs out: UE_ERR_TIMEOUT            */
 } ue_options;
 
 typedef struct ue_stats_t {
@@ -117,7 +130,17 @@ typedef struct ue_stats_t {
     double rho_hat;              /* learned prediction (UE_DT_LEARNED), 0 otherwise           */
     int64_t direct_fields;       /* field arrays that ue_write_fields / ue_read_fields moved  */
                                  /* in place in pinned host memory (no staging copy)          */
+    int32_t tb_kernel_used;      /* UE_VARIANT_BLOCKED: the kernel its launches run (UE_TBK_*) */
+    int32_t reserved2;
 } ue_stats_t;
+
+/* Kernels of the blocked variant (ue_stats_t.tb_kernel_used). */
+#define UE_TBK_NONE 0              /* not blocked                                              */
+#define UE_TBK_SPLIT 1             /* one CTA per tile, edges then triangles                    */
+#define UE_TBK_SHARED_RECORDS 2    /* the same with 1024 threads and records in shared memory   */
+#define UE_TBK_SPLIT_PIPELINED 3   /* one CTA per SM walking its tiles, next tile's loads ahead */
+#define UE_TBK_FUSED 4             /* the same, one thread per triangle with its three edges    */
+#define UE_TBK_WHOLE_MESH 5        /* one tile, no halo: every step of a call in one CTA        */
 
 /* Fill *opt with defaults (RCM, FP32, power-iteration dt, safety 0.5, 200 iterations). */
 void ue_options_default(ue_options* opt);
@@ -182,6 +205,15 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
  * (float, or double for UE_PREC_FP64).  ids and buf are DEVICE pointers owned by the caller.
  * Synchronous on `stream`.  Ids outside [0, n_tris) are not followed: UE_ERR_ARG. */
 int ue_exchange_tris(ue_mesh* m, const int32_t* ids, int64_t n, void* buf, int32_t scatter, void* stream);
+
+/* The same transfers with float arrays (the FP32 product's precision, half the bytes):
+ * ue_write_fields_f32 sets U = |e| E and B from them (in FP64, rounded once to the field type),
+ * ue_read_fields_f32 returns E = U / |e| and B rounded to float.  Pinned host arrays are read and
+ * written in place; others go through a device copy.  Synchronous.  UE_ERR_ARG for a mesh with
+ * a PML frame (use the double calls); ue_read_fields_f32 returns UE_ERR_UNSTABLE (after
+ * copying) if the watchdog has flagged the run. */
+int ue_write_fields_f32(ue_mesh* m, const float* E, const float* B, const float* j, void* stream);
+int ue_read_fields_f32(ue_mesh* m, float* E, float* B, float* j, void* stream);
 
 /* Advance n_steps leap-frog steps, asynchronously on `stream`.  Errors of the launches are
  * reported here; device-side conditions surface at the next synchronous call. */

@@ -16,6 +16,7 @@ UE_DT_GIVEN, UE_DT_POWER, UE_DT_LEARNED = 0, 1, 2
 UE_RHO_GIVEN, UE_RHO_POWER, UE_RHO_LEARNED, UE_RHO_POWER_FALLBACK = 0, 1, 2, 3
 UE_MLP_PARAMS = 5057
 UE_VARIANT_PLAIN, UE_VARIANT_BLOCKED, UE_VARIANT_PERSISTENT = 1, 2, 3
+UE_TB_SPLIT, UE_TB_FUSED = 0, 1
 UE_STATIC_MAX_TRIS, UE_STATIC_MAX_EDGES = 1 << 18, 1 << 19
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -28,7 +29,7 @@ class Options(C.Structure):
                 ("graph_chunk", C.c_int32), ("tile_tris", C.c_int32), ("block_depth", C.c_int32),
                 ("tb_threads", C.c_int32), ("dt", C.c_double),
                 ("safety", C.c_double), ("watchdog_growth", C.c_double),
-                ("watchdog_every", C.c_int32), ("reserved1", C.c_int32),
+                ("watchdog_every", C.c_int32), ("tb_kernel", C.c_int32),
                 ("mlp_params", C.c_void_p), ("learned_margin", C.c_double),
                 ("timeout_ms", C.c_int32), ("test_skip_cta", C.c_int32)]
 
@@ -39,7 +40,8 @@ class Stats(C.Structure):
                 ("rho", C.c_double), ("rho_source", C.c_int32), ("precision", C.c_int32),
                 ("bytes_per_step", C.c_double), ("kernel_launches", C.c_int64),
                 ("dt_setup_ms", C.c_double), ("rho_lo", C.c_double), ("rho_hi", C.c_double),
-                ("rho_hat", C.c_double), ("direct_fields", C.c_int64)]
+                ("rho_hat", C.c_double), ("direct_fields", C.c_int64), ("tb_kernel_used", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 P = C.c_void_p
@@ -58,6 +60,8 @@ SIGNATURES = [
     ("ue_set_plasma", C.c_int, [P, PD, C.c_double]),
     ("ue_set_source", C.c_int, [P, PI32, PD, I64, C.c_double, C.c_double, C.c_double]),
     ("ue_write_fields", C.c_int, [P, PD, PD, PD, P]),
+    ("ue_write_fields_f32", C.c_int, [P, P, P, P, P]),
+    ("ue_read_fields_f32", C.c_int, [P, P, P, P, P]),
     ("ue_step_n", C.c_int, [P, I64, P]),
     ("ue_exchange_tris", C.c_int, [P, P, I64, P, C.c_int32, P]),
     ("ue_read_fields", C.c_int, [P, PD, PD, PD, P]),

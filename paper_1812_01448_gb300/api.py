@@ -158,6 +158,34 @@ class Mesh:
                                          C.c_void_p(buf.data_ptr()), 1 if scatter else 0, _stream(stream)),
                 "ue_exchange_tris")
 
+    def write_fields_f32(self, E=None, B=None, j=None, stream=None):
+        """ue_write_fields_f32: fields as float32 arrays in caller numbering."""
+        def chk(x, n):
+            if x is None:
+                return None
+            x = np.ascontiguousarray(x, np.float32)
+            if x.shape != (n,):
+                raise ValueError(f"expected {n} values")
+            return x
+        E, B, j = chk(E, self.n_edges), chk(B, self.n_tris), chk(j, self.n_edges)
+        N.check(N.lib().ue_write_fields_f32(self._h, *(None if a is None else a.ctypes.data_as(C.c_void_p)
+                                                       for a in (E, B, j)), _stream(stream)),
+                "ue_write_fields_f32")
+
+    def read_fields_f32(self, E=True, B=True, j=False, stream=None, out=None):
+        """ue_read_fields_f32: (E, B, j) as float32 arrays in caller numbering."""
+        o = out or {}
+        Ea = o.get("E", np.empty(self.n_edges, np.float32)) if E else None
+        Ba = o.get("B", np.empty(self.n_tris, np.float32)) if B else None
+        ja = o.get("j", np.empty(self.n_edges, np.float32)) if j else None
+        for a in (Ea, Ba, ja):
+            if a is not None and (a.dtype != np.float32 or not a.flags.c_contiguous):
+                raise ValueError("output arrays must be contiguous float32")
+        N.check(N.lib().ue_read_fields_f32(self._h, *(None if a is None else a.ctypes.data_as(C.c_void_p)
+                                                      for a in (Ea, Ba, ja)), _stream(stream)),
+                "ue_read_fields_f32")
+        return Ea, Ba, ja
+
     def step_n(self, n: int, stream=None):
         N.check(N.lib().ue_step_n(self._h, int(n), _stream(stream)), "ue_step_n")
 

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libue.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_step.cu", "kernels_tb.cu", "kernels_geom.cu", "noalloc.cu", "kernels_mlp.cu", "kernels_persistent.cu", "kernels_modes.cu", "kernels_relax.cu", "kernels_frame.cu", "ue_api.cu"]
+CU_SOURCES = ["kernels_step.cu", "kernels_tb.cu", "kernels_tbf.cu", "kernels_geom.cu", "noalloc.cu", "kernels_mlp.cu", "kernels_persistent.cu", "kernels_modes.cu", "kernels_relax.cu", "kernels_frame.cu", "ue_api.cu"]
 CPP_SOURCES = ["mesh_host.cpp", "tiles_host.cpp", "triangulate_host.cpp"]
 
 

@@ -44,8 +44,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
     mbar_expect_tx(bar, bytes);
     bulk_copy_g2s(dst, src, bytes, bar);
 }
+// Waits for the phase of `parity` to complete, for at most about a second of SM clock cycles
+// (copies complete in microseconds); returns false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i) {
+    const long long t0 = clock64();
+    for (int i = 0; i < (1 << 26); ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -54,6 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((i & 255) == 255 && clock64() - t0 > (2LL << 30)) break;
     }
     return false;
 }
@@ -176,6 +180,11 @@ struct TBDev {
                                   // start at a multiple of 4 (16-byte aligned bulk copies)
     float* epb = nullptr;         // plasma coefficient per local edge record (plasma only)
     int64_t n_erec = 0;
+    int* frec = nullptr;          // fused-kernel records (tiles_host.cpp build_fused_records)
+    int64_t n_frec = 0;
+    int* fedge = nullptr;
+    int64_t n_fedge = 0;
+    int max_src = 0;              // most source records of one tile
     int2* tsrc = nullptr;         // per-tile source records {local edge, source index}
     int max_tri_loc = 0, max_edge_loc = 0;
     int threads = 512;            // CTA size of the blocked kernel (512 or 1024)
@@ -185,10 +194,24 @@ struct TBDev {
     unsigned* done = nullptr;     // [0] CTA completion counter (step counter hand-off),
                                   // [1] error word (a bounded copy wait of k_tbp ran out)
     int sms = 0;                  // SMs of the device: CTAs of the pipelined persistent form
+    int test_cta = -1;            // tests only: this CTA of the pipelined forms arms its first
+                                  // record copy for bytes that never arrive
 };
 
 int tb_threads();
 bool tb_fits(int max_tri_loc, int max_edge_loc, int threads);
+// The fused triangle-centric kernel (kernels_tbf.cu, vacuum media): whether tiles of these
+// sizes fit it, its coefficient fill, and one launch of k steps (buffer cur to cur ^ 1).
+bool tbf_fits(int max_tri_loc, int max_edge_loc, int max_src);
+cudaError_t launch_tbf_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
+cudaError_t launch_tbf(const TBDev& t, const DevMesh& m, int ksteps, int cur, int gbase, cudaStream_t s);
+// A mesh that is one tile without a halo (at most 2048 triangles): n steps in one launch of one
+// CTA with the whole mesh in shared memory (buffer cur to cur ^ 1).  hdr_host: the tile's
+// header on the host.
+bool tbf1_fits(const TBDev& t, const int* hdr_host);
+cudaError_t launch_tbf1(const TBDev& t, const DevMesh& m, long long n_steps, int cur, cudaStream_t s);
+// the kernel launch_tb runs for these tiles (UE_TBK_*)
+int tb_kernel_used(const TBDev& t, const DevMesh& m);
 // whether launch_tb runs the pipelined persistent form k_tbp for these tiles
 bool tb_pipelined(int max_tri_loc, int max_edge_loc, int threads, bool plasma);
 cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s);
@@ -234,15 +257,16 @@ cudaError_t launch_fields_in(const DevMesh& m, const double* E_caller, const dou
 cudaError_t launch_fields_out(const DevMesh& m, double* E_caller, double* B_caller,
                               double* J_caller, const int64_t* edge_caller,
                               const int64_t* perm_tri, const double* elen, cudaStream_t s);
-// The same transfers with the caller's arrays in pinned host memory, passed as their mapped
-// device addresses: k_of[n_e] = stored interior edge of each caller edge or -1, inv[n_t] =
-// stored triangle of each caller triangle.  E (and J) are written on every caller edge.
-cudaError_t launch_fields_in_direct(const DevMesh& m, const double* E_caller, const double* B_caller,
-                                    const double* J_caller, const int32_t* k_of, const int32_t* inv,
+// The same transfers in caller order, with the caller's arrays (double, or float when f32) in
+// pinned host memory at their mapped device addresses, or in device memory: k_of[n_e] = stored
+// interior edge of each caller edge or -1, inv[n_t] = stored triangle of each caller triangle.
+// E (and J) are written on every caller edge.
+cudaError_t launch_fields_in_caller(const DevMesh& m, const void* E_caller, const void* B_caller,
+                                    const void* J_caller, bool f32, const int32_t* k_of, const int32_t* inv,
                                     const double* elen, int64_t n_e, cudaStream_t s);
-cudaError_t launch_fields_out_direct(const DevMesh& m, double* E_caller, double* B_caller, double* J_caller,
-                                     const int32_t* k_of, const int32_t* inv, const double* elen,
-                                     int64_t n_e, cudaStream_t s);
+cudaError_t launch_fields_out_caller(const DevMesh& m, void* E_caller, void* B_caller, void* J_caller, bool f32,
+                                     const int32_t* k_of, const int32_t* inv, const double* elen, int64_t n_e,
+                                     cudaStream_t s);
 // Halo exchange of a partitioned mesh: B at caller triangle ids[0..n) to buf (scatter = 0) or
 // from buf (scatter = 1), in the field type; inv[n_t] = stored triangle of each caller one.
 // Ids outside [0, n_t) are skipped and counted in *bad (device).

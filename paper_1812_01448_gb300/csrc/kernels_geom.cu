@@ -331,45 +331,46 @@ __global__ void k_fields_out_tris(const T* __restrict__ B, const int64_t* __rest
     Bc[perm[j]] = (double)B[j];
 }
 
-// Direct transfer with the caller's arrays in pinned host memory (read and written through
-// their mapped device addresses): one thread per caller element, so that the host side is
-// accessed in order, and the same rounding as the staged kernels above.  k_of[c] = stored
-// interior edge of caller edge c or -1; inv[c] = stored triangle of caller triangle c.
-template <typename T>
-__global__ void k_fields_in_edges_direct(const double* __restrict__ Ec, const int32_t* __restrict__ k_of,
-                                         const double* __restrict__ elen, T* __restrict__ U, int64_t n_e,
-                                         int64_t n_ei) {
+// Field transfer in caller order (one thread per caller element, so that the caller's side is
+// read and written in order): from or to the caller's arrays in pinned host memory through
+// their mapped device addresses, or a device copy of them.  H is the caller's element type
+// (double, or float for the FP32 calls); the arithmetic is that of the staged kernels above, in
+// FP64, rounded once to H or T.  k_of[c] = stored interior edge of caller edge c or -1; inv[c] =
+// stored triangle of caller triangle c.
+template <typename T, typename H>
+__global__ void k_fields_in_edges_c(const H* __restrict__ Ec, const int32_t* __restrict__ k_of,
+                                    const double* __restrict__ elen, T* __restrict__ U, int64_t n_e,
+                                    int64_t n_ei) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) U[n_ei] = (T)0;
     if (c >= n_e) return;
     const int32_t k = k_of[c];
-    if (k >= 0) U[k] = (T)(elen[k] * Ec[c]);
+    if (k >= 0) U[k] = (T)(elen[k] * (double)Ec[c]);
 }
 
-template <typename T>
-__global__ void k_fields_in_tris_direct(const double* __restrict__ Bc, const int32_t* __restrict__ inv,
-                                        T* __restrict__ B, int64_t n_t) {
+template <typename T, typename H>
+__global__ void k_fields_in_tris_c(const H* __restrict__ Bc, const int32_t* __restrict__ inv,
+                                   T* __restrict__ B, int64_t n_t) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_t) return;
     B[inv[c]] = (T)Bc[c];
 }
 
-template <typename T>
-__global__ void k_fields_out_edges_direct(const T* __restrict__ U, const int32_t* __restrict__ k_of,
-                                          const double* __restrict__ elen, double* __restrict__ Ec,
-                                          int64_t n_e) {
+template <typename T, typename H>
+__global__ void k_fields_out_edges_c(const T* __restrict__ U, const int32_t* __restrict__ k_of,
+                                     const double* __restrict__ elen, H* __restrict__ Ec, int64_t n_e) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_e) return;
     const int32_t k = k_of[c];
-    Ec[c] = k >= 0 ? (double)U[k] / elen[k] : 0.0;
+    Ec[c] = k >= 0 ? (H)((double)U[k] / elen[k]) : (H)0;
 }
 
-template <typename T>
-__global__ void k_fields_out_tris_direct(const T* __restrict__ B, const int32_t* __restrict__ inv,
-                                         double* __restrict__ Bc, int64_t n_t) {
+template <typename T, typename H>
+__global__ void k_fields_out_tris_c(const T* __restrict__ B, const int32_t* __restrict__ inv,
+                                    H* __restrict__ Bc, int64_t n_t) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_t) return;
-    Bc[c] = (double)B[inv[c]];
+    Bc[c] = (H)B[inv[c]];
 }
 
 // B of the triangles with the given caller ids to / from a packed buffer (the halo exchange
@@ -696,39 +697,52 @@ cudaError_t launch_fields_out(const DevMesh& m, double* Ec, double* Bc, double* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields_in_direct(const DevMesh& m, const double* Ec, const double* Bc, const double* Jc,
+namespace {
+template <typename T, typename H>
+void fields_in_c(const DevMesh& m, const H* Ec, const H* Bc, const H* Jc, const int32_t* k_of, const int32_t* inv,
+                 const double* elen, int64_t n_e, cudaStream_t s) {
+    const int64_t ne = n_e > 0 ? n_e : 1;
+    if (Ec) k_fields_in_edges_c<T, H><<<blocks_for(ne), kThreads, 0, s>>>(Ec, k_of, elen, (T*)m.U, n_e, m.n_ei);
+    if (Jc && m.J) k_fields_in_edges_c<T, H><<<blocks_for(ne), kThreads, 0, s>>>(Jc, k_of, elen, (T*)m.J, n_e, m.n_ei);
+    if (Bc) k_fields_in_tris_c<T, H><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (T*)m.B, m.n_t);
+}
+
+template <typename T, typename H>
+void fields_out_c(const DevMesh& m, H* Ec, H* Bc, H* Jc, const int32_t* k_of, const int32_t* inv,
+                  const double* elen, int64_t n_e, cudaStream_t s) {
+    if (Ec && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for(n_e), kThreads, 0, s>>>((const T*)m.U, k_of, elen, Ec, n_e);
+    if (Jc && m.J && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for(n_e), kThreads, 0, s>>>((const T*)m.J, k_of, elen, Jc, n_e);
+    if (Bc) k_fields_out_tris_c<T, H><<<blocks_for(m.n_t), kThreads, 0, s>>>((const T*)m.B, inv, Bc, m.n_t);
+}
+}  // namespace
+
+cudaError_t launch_fields_in_caller(const DevMesh& m, const void* Ec, const void* Bc, const void* Jc, bool f32,
                                     const int32_t* k_of, const int32_t* inv, const double* elen, int64_t n_e,
                                     cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
-    const int64_t ne = n_e > 0 ? n_e : 1;
-    for (int f = 0; f < 2; ++f) {
-        const double* src = f == 0 ? Ec : Jc;
-        void* dst = f == 0 ? m.U : m.J;
-        if (!src || !dst) continue;
-        if (f64) k_fields_in_edges_direct<double><<<blocks_for(ne), kThreads, 0, s>>>(src, k_of, elen, (double*)dst, n_e, m.n_ei);
-        else k_fields_in_edges_direct<float><<<blocks_for(ne), kThreads, 0, s>>>(src, k_of, elen, (float*)dst, n_e, m.n_ei);
-    }
-    if (Bc) {
-        if (f64) k_fields_in_tris_direct<double><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (double*)m.B, m.n_t);
-        else k_fields_in_tris_direct<float><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (float*)m.B, m.n_t);
+    if (f32) {
+        auto E = (const float*)Ec, B = (const float*)Bc, J = (const float*)Jc;
+        f64 ? fields_in_c<double, float>(m, E, B, J, k_of, inv, elen, n_e, s)
+            : fields_in_c<float, float>(m, E, B, J, k_of, inv, elen, n_e, s);
+    } else {
+        auto E = (const double*)Ec, B = (const double*)Bc, J = (const double*)Jc;
+        f64 ? fields_in_c<double, double>(m, E, B, J, k_of, inv, elen, n_e, s)
+            : fields_in_c<float, double>(m, E, B, J, k_of, inv, elen, n_e, s);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields_out_direct(const DevMesh& m, double* Ec, double* Bc, double* Jc, const int32_t* k_of,
+cudaError_t launch_fields_out_caller(const DevMesh& m, void* Ec, void* Bc, void* Jc, bool f32, const int32_t* k_of,
                                      const int32_t* inv, const double* elen, int64_t n_e, cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
-    for (int f = 0; f < 2; ++f) {
-        double* dst = f == 0 ? Ec : Jc;
-        const void* src = f == 0 ? m.U : m.J;
-        if (!dst || n_e == 0) continue;
-        if (!src) return cudaErrorInvalidValue;
-        if (f64) k_fields_out_edges_direct<double><<<blocks_for(n_e), kThreads, 0, s>>>((const double*)src, k_of, elen, dst, n_e);
-        else k_fields_out_edges_direct<float><<<blocks_for(n_e), kThreads, 0, s>>>((const float*)src, k_of, elen, dst, n_e);
-    }
-    if (Bc) {
-        if (f64) k_fields_out_tris_direct<double><<<blocks_for(m.n_t), kThreads, 0, s>>>((const double*)m.B, inv, Bc, m.n_t);
-        else k_fields_out_tris_direct<float><<<blocks_for(m.n_t), kThreads, 0, s>>>((const float*)m.B, inv, Bc, m.n_t);
+    if (f32) {
+        auto E = (float*)Ec, B = (float*)Bc, J = (float*)Jc;
+        f64 ? fields_out_c<double, float>(m, E, B, J, k_of, inv, elen, n_e, s)
+            : fields_out_c<float, float>(m, E, B, J, k_of, inv, elen, n_e, s);
+    } else {
+        auto E = (double*)Ec, B = (double*)Bc, J = (double*)Jc;
+        f64 ? fields_out_c<double, double>(m, E, B, J, k_of, inv, elen, n_e, s)
+            : fields_out_c<float, double>(m, E, B, J, k_of, inv, elen, n_e, s);
     }
     return cudaGetLastError();
 }

@@ -41,6 +41,8 @@ struct TBArgs {
     unsigned* err;      // set when a bounded copy wait of k_tbp runs out
     int ksteps;
     float pa, mdt;
+    int test_cta;       // tests only (-1 otherwise): this CTA arms its first record copy for
+                        // 16 bytes more than it delivers, so that the wait for it runs out
 };
 
 // NT threads; each thread owns local triangle slots tid + i*NT (i < TS) and local edge slots
@@ -392,28 +394,40 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
     __syncthreads();
     const long long n0 = *a.step;
     uint32_t ph_h = 0, ph_r = 0;
+    int pend_h = 0, pend_r = 0;   // bulk copies issued and not yet waited for (uniform)
     bool ok = true;
+    // a wait that runs out ends this CTA's work: every thread agrees on it before any staged
+    // value is used, and the copies in flight are waited for (bounded) before the CTA exits
     auto wait_bar = [&](uint64_t* bar, uint32_t& ph) {
         if (!mbar_wait(bar, ph)) ok = false;
         ph ^= 1u;
+        if (bar == &bar_h) --pend_h;
+        else --pend_r;
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        return ok;
     };
     // local triangles of level <= kk, local edges of level <= kk - 1 (header layout in
     // tiles_host.cpp)
     auto n_tri = [&](const int* h) { return h[16 + kk]; };
     auto n_edge = [&](const int* h) { return h[32 + kk - 1]; };
     auto issue_header = [&](int t, int slot) {
+        ++pend_h;
         if (tid == 0) {
             fence_proxy_async();
             bulk_g2s(hs[slot], a.hdr + (size_t)t * 48, 48 * sizeof(int), &bar_h);
         }
     };
+    bool first_records = true;
     auto issue_records = [&](int slot) {
+        ++pend_r;
+        const bool extra = first_records && (int)blockIdx.x == a.test_cta;
+        first_records = false;
         if (tid == 0) {
             const int* h = hs[slot];
             const uint32_t ne4 = (uint32_t)(n_edge(h) + 3) & ~3u;
             const uint32_t tb = 16u * (uint32_t)n_tri(h), eb = 12u * ne4, pbb = PLASMA ? 4u * ne4 : 0u;
             fence_proxy_async();
-            mbar_expect_tx(&bar_r, tb + eb + pbb);
+            mbar_expect_tx(&bar_r, tb + eb + pbb + (extra ? 16u : 0u));
             if (tb) bulk_copy_g2s(tstage, a.trec + h[6], tb, &bar_r);
             if (eb) bulk_copy_g2s(estage, a.erec + 3 * (size_t)h[7], eb, &bar_r);
             if (PLASMA && pbb) bulk_copy_g2s(pstage, a.epb + h[7], pbb, &bar_r);
@@ -443,14 +457,17 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
     // prologue: first tile's header, records and fields; the second tile's header
     if (tile < n_tiles) {
         issue_header(tile, 0);
-        wait_bar(&bar_h, ph_h);
-        issue_records(0);
-        if (tile + stride < n_tiles) issue_header(tile + stride, 1);
-        wait_bar(&bar_r, ph_r);
-        issue_fields(0, F0);
-        cp_async_wait_all();
-        if (tile + stride < n_tiles) wait_bar(&bar_h, ph_h);
+        if (wait_bar(&bar_h, ph_h)) {
+            issue_records(0);
+            if (tile + stride < n_tiles) issue_header(tile + stride, 1);
+            if (wait_bar(&bar_r, ph_r)) {
+                issue_fields(0, F0);
+                cp_async_wait_all();
+                if (tile + stride < n_tiles) wait_bar(&bar_h, ph_h);
+            }
+        }
     }
+    if (!ok) tile = n_tiles;
     __syncthreads();
     // per slot: triangle gather offsets (U0 | U1 << 16, U2), -s0 dt/S, s0 s1, s0 s2 and B;
     // edge gather offsets (B_R | B_L << 16), dt|e|/d and U (plasma: pb and J)
@@ -582,10 +599,11 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
             }
             __syncthreads();
             if (has_next && s == s_fields) {
-                wait_bar(&bar_r, ph_r);
+                if (!wait_bar(&bar_r, ph_r)) break;
                 issue_fields(slot1, Fn);
             }
         }
+        if (!ok) break;
         // owned values, from registers
         const int nto = h[1], neo = h[3];
 #pragma unroll
@@ -602,10 +620,17 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
             }
         }
         if (has_next) cp_async_wait_all();
-        if (has_next2) wait_bar(&bar_h, ph_h);
+        if (has_next2 && !wait_bar(&bar_h, ph_h)) break;
         __syncthreads();
     }
-    if (!ok) atomicOr(a.err, 1u);
+    if (!ok) {
+        // this CTA's tiles were not advanced: report it, and let its copies in flight land
+        // before the CTA's shared memory goes (each wait bounded)
+        atomicOr(a.err, 1u);
+        cp_async_wait_all();
+        for (; pend_r > 0; --pend_r, ph_r ^= 1u) mbar_wait(&bar_r, ph_r);
+        for (; pend_h > 0; --pend_h, ph_h ^= 1u) mbar_wait(&bar_h, ph_h);
+    }
     // the last CTA to finish advances the step counter (every CTA has read it by then)
     if (tid == 0) {
         __threadfence();
@@ -729,6 +754,16 @@ cudaError_t launch_tb_fill(const TBDev& t, const DevMesh& m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+int tb_kernel_used(const TBDev& t, const DevMesh& m) {
+    if (t.n_tiles == 0) return UE_TBK_NONE;
+    if (t.threads == 1024) return UE_TBK_SHARED_RECORDS;
+    if (!m.plasma && t.frec && t.sms > 0 && tbf_fits(t.max_tri_loc, t.max_edge_loc, t.max_src)) return UE_TBK_FUSED;
+    int ts = 0, es = 0;
+    tbp_config(t.max_tri_loc, t.max_edge_loc, m.plasma, ts, es);
+    if (t.sms > 0 && ts > 0) return UE_TBK_SPLIT_PIPELINED;
+    return UE_TBK_SPLIT;
+}
+
 cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int gbase,
                       cudaStream_t s) {
     TBArgs a;
@@ -754,6 +789,7 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
     a.ksteps = ksteps;
     a.pa = (float)m.pa;
     a.mdt = (float)(-m.dt);
+    a.test_cta = t.test_cta;
     const bool src = m.n_src > 0;
     if (ksteps < 1 || ksteps > 15) return cudaErrorInvalidValue;
     if (m.plasma && !t.epb) return cudaErrorInvalidValue;
@@ -766,6 +802,9 @@ cudaError_t launch_tb(const TBDev& t, const DevMesh& m, int ksteps, int cur, int
         return src ? launch_tbs_t<false, true>(a, (int)t.n_tiles, sm2, s)
                    : launch_tbs_t<false, false>(a, (int)t.n_tiles, sm2, s);
     }
+    // vacuum media: the fused triangle-centric form when its records exist and the tiles fit
+    if (!m.plasma && t.frec && t.sms > 0 && tbf_fits(t.max_tri_loc, t.max_edge_loc, t.max_src))
+        return launch_tbf(t, m, ksteps, cur, gbase, s);
     // pipelined persistent form when two field buffers and the staging records fit
     int ts = 0, es = 0;
     tbp_config(t.max_tri_loc, t.max_edge_loc, m.plasma, ts, es);

@@ -162,6 +162,75 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,
     return UE_OK;
 }
 
+// Fused records: local triangle l of a tile (levels <= k_max - 1; the outermost ring only
+// needs its gid) with local edge codes c_q = 2 e_q + (s_q < 0) (e_q = nel: boundary); edge
+// records {gid, 0}, then {-1, 0} for the zero slot (and padding):
+//   r0 gid;
+//   r1 bits 0-15: 4 * local id of the triangle across edge 0 (itself on the boundary),
+//      16-31: the same for edge 1;
+//   r2 bits 0-13: 4 * the neighbour across edge 2, 14-26: e_0, 27 / 28: s0 s1 < 0, s0 s2 < 0,
+//      29: s0 < 0;
+//   r3 bits 0-12: e_1, 16-28: e_2, bit 13 / 14 / 29: sign of the signed edge coefficient of
+//      edge 0 / 1 / 2 (see below);
+//   r4 bits of -s0 dt/S (filled on the device).
+// The signed edge coefficient is s0 s_q t_q dt|e|/d, t_q = +1 when the triangle is R of the
+// edge, -1 when it is L; with the edge values held as V_q = s0 s_q U_q it advances V_q by
+// fma(coefficient, B_own - B_nbr, V_q), which rounds exactly as U += (dt|e|/d)(B_R - B_L).
+int build_fused_records(const HostMesh& hm, TileSet& ts, std::string& err) {
+    ts.frec.clear();
+    ts.fedge.clear();
+    (void)hm;
+    for (int64_t t = 0; t < ts.n_tiles; ++t) {
+        int32_t* h = &ts.hdr[t * TileSet::kHdr];
+        const int ntl = h[4], nel = h[5], k = h[10];
+        if (ntl > 4096 || nel + 1 > 8191) {
+            err = "a tile with its halo is too large for the fused records (4096 triangles, 8190 edges)";
+            return UE_ERR_ARG;
+        }
+        const int32_t* tr = &ts.trec[4 * (size_t)h[6]];
+        const int32_t* er = &ts.erec[4 * (size_t)h[7]];
+        h[11] = (int32_t)(ts.frec.size() / 5);
+        h[12] = (int32_t)(ts.fedge.size() / 2);
+        const int nupd = h[16 + k - 1];
+        for (int l = 0; l < ntl; ++l) {
+            int32_t r[5] = {tr[4 * l], 0, 0, 0, 0};
+            if (l < nupd) {
+                const uint32_t code[3] = {(uint32_t)tr[4 * l + 1] & 0xFFFFu, (uint32_t)tr[4 * l + 1] >> 16,
+                                          (uint32_t)tr[4 * l + 2]};
+                uint32_t nb[3], e[3], csign[3];
+                const uint32_t s0 = code[0] & 1u;
+                for (int q = 0; q < 3; ++q) {
+                    e[q] = code[q] >> 1;
+                    if ((int)e[q] >= nel) {          // boundary edge: coefficient 0, itself
+                        nb[q] = (uint32_t)l;
+                        csign[q] = 0;
+                        e[q] = (uint32_t)nel;
+                        continue;
+                    }
+                    const uint32_t R = (uint32_t)er[4 * e[q] + 1] & 0xFFFFu, L = (uint32_t)er[4 * e[q] + 1] >> 16;
+                    if (R != (uint32_t)l && L != (uint32_t)l) {
+                        err = "internal error: a triangle's edge does not name it";
+                        return UE_ERR_ARG;
+                    }
+                    nb[q] = R == (uint32_t)l ? L : R;
+                    const uint32_t neg_t = R == (uint32_t)l ? 0u : 1u;
+                    csign[q] = (s0 ^ (code[q] & 1u)) ^ neg_t;
+                }
+                r[1] = (int32_t)((4u * nb[0]) | ((4u * nb[1]) << 16));
+                r[2] = (int32_t)((4u * nb[2]) | (e[0] << 14) | (((code[1] ^ code[0]) & 1u) << 27) |
+                                 (((code[2] ^ code[0]) & 1u) << 28) | (s0 << 29));
+                r[3] = (int32_t)(e[1] | (csign[0] << 13) | (csign[1] << 14) | (e[2] << 16) | (csign[2] << 29));
+            }
+            ts.frec.insert(ts.frec.end(), r, r + 5);
+        }
+        while ((ts.frec.size() / 5) % 4 != 0) ts.frec.insert(ts.frec.end(), {0, 0, 0, 0, 0});
+        for (int l = 0; l < nel; ++l) ts.fedge.insert(ts.fedge.end(), {er[4 * l], 0});
+        ts.fedge.insert(ts.fedge.end(), {-1, 0});          // the zero slot
+        if ((ts.fedge.size() / 2) % 2 != 0) ts.fedge.insert(ts.fedge.end(), {-1, 0});
+    }
+    return UE_OK;
+}
+
 int build_region(const HostMesh& hm, const std::vector<char>& owned, int k, const std::vector<int64_t>& islot,
                  const std::vector<int32_t>& ineg, Region& r, std::string& err) {
     const int64_t nt = hm.n_tris, nei = hm.n_ei;

@@ -113,6 +113,8 @@ struct ue_mesh {
     ue::TBDev tb;
     int block_depth = 4;
     int tb_threads = 512;
+    int tb_kernel = UE_TB_SPLIT;
+    int tb_test_cta = -1;
     int cur = 0;                     // buffer holding the current fields
 
     // dt selection
@@ -516,6 +518,8 @@ int bake_source(ue_mesh* m, cudaStream_t s) {
         // the tile records carry the source flags of the coefficients (the pipelined kernel
         // takes a source edge's value back after the source is added)
         UE_CUDA(ue::launch_tb_fill(m->tb, m->dm, s));
+        if (m->tb.frec) UE_CUDA(ue::launch_tbf_fill(m->tb, m->dm, s));
+        m->tb.max_src = m->ts.max_src;
         UE_CUDA(cudaStreamSynchronize(s));
     }
     if (!m->has_reg) return rc;
@@ -651,11 +655,25 @@ void region_plan(const ue_mesh* m, int k, std::vector<char>& interior, std::vect
             for (int64_t j = h.tile_tri_off[t]; j < h.tile_tri_off[t + 1]; ++j) owned[j] = 1;
 }
 
+// The fused kernel's records of a built tile set: for UE_TB_FUSED, and for a mesh that is one
+// tile without a halo (run in one CTA); none when the tiles do not fit them.
+void fused_records(ue::TileSet& ts, const HostMesh& hm, int threads, int kernel) {
+    std::string err;
+    const bool whole = ts.n_tiles == 1 && ts.hdr[4] == ts.hdr[1];
+    ts.frec.clear();
+    ts.fedge.clear();
+    if (threads == 1024 || (kernel != UE_TB_FUSED && !whole) || ue::build_fused_records(hm, ts, err) != UE_OK) {
+        ts.frec.clear();
+        ts.fedge.clear();
+    }
+}
+
 int upload_tiles(ue_mesh* m, cudaStream_t s) {
     std::string err;
     if (m->fr.W == 0) {
         int rc = ue::build_tiles(m->hm, m->block_depth, m->ts, err);
         if (rc != UE_OK) return fail(rc, err);
+        fused_records(m->ts, m->hm, m->tb_threads, m->tb_kernel);
         return upload_tileset(m, s);
     }
     std::vector<char> interior, owned;
@@ -664,6 +682,7 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
     const int k = m->block_depth;
     int rc = ue::build_tiles(h, k, m->ts, err, &interior);
     if (rc != UE_OK) return fail(rc, err);
+    fused_records(m->ts, h, m->tb_threads, m->tb_kernel);
     if ((rc = upload_tileset(m, s)) != UE_OK) return rc;
     return setup_region(m, owned, s);
 }
@@ -710,6 +729,19 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     UE_CUDA(cudaMemsetAsync(tb.B[1], 0, 4 * m->dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(tb.U[1], 0, 4 * m->dm.n_ei_pad, s));
     UE_CUDA(ue::launch_tb_fill(tb, m->dm, s));
+    // records of the fused kernel (vacuum media, 512 threads), when the tiles fit it
+    if (m->tb_threads != 1024 && !ts.frec.empty()) {
+        tb.n_frec = (int64_t)ts.frec.size() / 5;
+        tb.n_fedge = (int64_t)ts.fedge.size() / 2;
+        if (!alloc_into(m, tb.frec, ts.frec.size(), 4, s) || !alloc_into(m, tb.fedge, ts.fedge.size(), 4, s))
+            return fail(UE_ERR_ALLOC, "fused tile records");
+        UE_CUDA(cudaMemcpyAsync(tb.frec, ts.frec.data(), 4 * ts.frec.size(), cudaMemcpyHostToDevice, s));
+        UE_CUDA(cudaMemcpyAsync(tb.fedge, ts.fedge.data(), 4 * ts.fedge.size(), cudaMemcpyHostToDevice, s));
+        UE_CUDA(ue::launch_tbf_fill(tb, m->dm, s));
+        UE_CUDA(cudaStreamSynchronize(s));
+    }
+    tb.max_src = ts.max_src;
+    tb.test_cta = m->tb_test_cta;
     return UE_OK;
 }
 
@@ -876,6 +908,105 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
         UE_CUDA(cudaMemcpyAsync(m->d_rl, h.edge_tri.data(), 8 * nei, cudaMemcpyHostToDevice, s));
         UE_CUDA(cudaMemcpyAsync(m->d_ecaller, h.edge_caller.data(), 8 * nei, cudaMemcpyHostToDevice, s));
     }
+    return UE_OK;
+}
+
+
+// The caller's array as a device address when it lies in pinned (page-locked, mapped) host
+// memory and is 8-byte aligned; NULL otherwise (the transfer is then staged through a copy).
+// The caller's array as a device address when it lies in pinned (page-locked, mapped) host
+// memory and is aligned to its element size; NULL otherwise (the transfer is then staged).
+const void* mapped_view(const void* p, size_t elem) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & (elem - 1))) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // not a CUDA-known pointer: clear the error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
+// Caller -> stored maps of the direct transfers (made by ue_geometry_build).
+int ensure_caller_maps(ue_mesh* m, cudaStream_t s) {
+    if (m->d_kof) return UE_OK;
+    const HostMesh& h = m->hm;
+    std::vector<int32_t> kof(h.n_edges), inv(h.n_tris);
+    for (int64_t c = 0; c < h.n_edges; ++c) kof[c] = (int32_t)h.k_of_edge[c];
+    for (int64_t j = 0; j < h.n_tris; ++j) inv[h.perm_tri[j]] = (int32_t)j;
+    int32_t *a = nullptr, *b = nullptr;
+    if (!alloc_into(m, a, h.n_edges, 4, s) || !alloc_into(m, b, h.n_tris, 4, s))
+        return fail(UE_ERR_ALLOC, "caller maps of the direct field transfer");
+    UE_CUDA(cudaMemcpyAsync(a, kof.data(), 4 * kof.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaMemcpyAsync(b, inv.data(), 4 * inv.size(), cudaMemcpyHostToDevice, s));
+    UE_CUDA(cudaStreamSynchronize(s));
+    m->d_kof = a;
+    m->d_inv = b;
+    return UE_OK;
+}
+
+// Which of the given arrays go the direct way: all of them when each is pinned host memory and
+// the mesh has no PML frame (whose interface edges travel through the staging buffer).
+bool direct_transfer(const ue_mesh* m, const void* E, const void* B, const void* j, size_t elem,
+                     const void*& dE, const void*& dB, const void*& dj) {
+    dE = mapped_view(E, elem);
+    dB = mapped_view(B, elem);
+    dj = mapped_view(j, elem);
+    if (m->dm.frame || m->fr.W > 0) return false;
+    return (!E || dE) && (!B || dB) && (!j || dj) && (E || B || j);
+}
+
+// Re-arm the watchdog and the error words after new fields are written.
+int rearm(ue_mesh* m, cudaStream_t s) {
+    const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
+    UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
+    m->since_check = 0;
+    if (m->p_err) UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
+    if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) UE_CUDA(cudaMemsetAsync(m->tb.done + 1, 0, 4, s));
+    return UE_OK;
+}
+
+// Fields in the caller's numbering as float (the product's precision), for meshes without a
+// PML frame: in place when the arrays are pinned host memory, else through a device copy.
+int fields_f32(ue_mesh* m, float* E, float* B, float* j, bool write, cudaStream_t s) {
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    if (m->dm.frame || m->fr.W > 0)
+        return fail(UE_ERR_ARG, "a mesh with a PML frame exchanges its fields through ue_write_fields / ue_read_fields");
+    const HostMesh& h = m->hm;
+    if (!m->dm.J && j) {
+        if (!write) std::memset(j, 0, 4 * (size_t)h.n_edges);   // no current in this medium
+        j = nullptr;
+    }
+    const void *dE = nullptr, *dB = nullptr, *dj = nullptr;
+    const bool direct = direct_transfer(m, E, B, j, 4, dE, dB, dj);
+    if (!direct) {
+        // device copies in the staging buffers (float views of the double ones)
+        dE = E ? m->d_Ec : nullptr;
+        dB = B ? m->d_Bc : nullptr;
+        dj = j ? m->d_Jc : nullptr;
+        if (write) {
+            if (E) UE_CUDA(cudaMemcpyAsync(m->d_Ec, E, 4 * h.n_edges, cudaMemcpyHostToDevice, s));
+            if (B) UE_CUDA(cudaMemcpyAsync(m->d_Bc, B, 4 * h.n_tris, cudaMemcpyHostToDevice, s));
+            if (j) UE_CUDA(cudaMemcpyAsync(m->d_Jc, j, 4 * h.n_edges, cudaMemcpyHostToDevice, s));
+        }
+    } else {
+        m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
+    }
+    if (write) {
+        UE_CUDA(ue::launch_fields_in_caller(m->dm, dE, dB, dj, true, m->d_kof, m->d_inv, m->d_elen, h.n_edges, s));
+        const int rc = rearm(m, s);
+        if (rc != UE_OK) return rc;
+    } else {
+        UE_CUDA(ue::launch_fields_out_caller(m->dm, const_cast<void*>(dE), const_cast<void*>(dB),
+                                             const_cast<void*>(dj), true, m->d_kof, m->d_inv, m->d_elen,
+                                             h.n_edges, s));
+        if (!direct) {
+            if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 4 * h.n_edges, cudaMemcpyDeviceToHost, s));
+            if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 4 * h.n_tris, cudaMemcpyDeviceToHost, s));
+            if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 4 * h.n_edges, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
 }
 
@@ -1069,6 +1200,9 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     m->variant = o.variant == 0 ? UE_VARIANT_PLAIN : o.variant;
     m->block_depth = o.block_depth;
     m->tb_threads = o.tb_threads == 1024 ? 1024 : 512;
+    if (o.tb_kernel != UE_TB_SPLIT && o.tb_kernel != UE_TB_FUSED) return fail(UE_ERR_ARG, "tb_kernel must be UE_TB_SPLIT or UE_TB_FUSED");
+    m->tb_kernel = o.tb_kernel;
+    m->tb_test_cta = m->variant == UE_VARIANT_BLOCKED ? o.test_skip_cta : -1;
     m->precision = o.precision;
     m->graph_chunk = o.graph_chunk == 0 ? 32 : o.graph_chunk;
     if (o.watchdog_every < 0 || !(o.watchdog_growth > 1.0))
@@ -1196,6 +1330,12 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         m->p_grid = ue::persistent_grid(dev);
     }
     UE_CUDA(cudaStreamSynchronize(s));
+    if (m->fr.W == 0) {
+        // the caller -> stored maps of field transfers in place (pinned host arrays), made here
+        // so that the first such transfer does not build them
+        const int mrc = ensure_caller_maps(m, s);
+        if (mrc != UE_OK) return mrc;
+    }
     m->steps_done = 0;
     m->built = true;
     m->version++;
@@ -1324,6 +1464,7 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
         ue::TileSet& T = B->ts;
         T = ue::TileSet();
         T.k_max = m0->ts.k_max;
+        bool all_fused = true;
         for (int32_t i = 0; i < n; ++i) {
             const ue::TileSet& ts = meshes[i]->ts;
             const int64_t tr0 = (int64_t)T.trec.size() / 4, er0 = (int64_t)T.erec.size() / 4;
@@ -1350,9 +1491,31 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
                 T.erec.push_back(0);
             }
             for (int64_t x : ts.erec_tile) T.erec_tile.push_back(x + T.n_tiles);
+            if (!ts.frec.empty()) {
+                const int64_t f0 = (int64_t)T.frec.size() / 5, e0 = (int64_t)T.fedge.size() / 2;
+                for (int64_t t = 0; t < ts.n_tiles; ++t) {
+                    int32_t* hh = &T.hdr[(T.n_tiles + t) * ue::TileSet::kHdr];
+                    hh[11] += (int32_t)f0;
+                    hh[12] += (int32_t)e0;
+                }
+                for (size_t r = 0; r < ts.frec.size(); r += 5) {
+                    T.frec.push_back(ts.frec[r] + (int32_t)t_off[i]);
+                    T.frec.insert(T.frec.end(), ts.frec.begin() + r + 1, ts.frec.begin() + r + 5);
+                }
+                for (size_t r = 0; r < ts.fedge.size(); r += 2) {
+                    T.fedge.push_back(ts.fedge[r] >= 0 ? ts.fedge[r] + (int32_t)k_off[i] : -1);
+                    T.fedge.push_back(0);
+                }
+            } else {
+                all_fused = false;
+            }
             T.n_tiles += ts.n_tiles;
             T.max_tri_loc = std::max(T.max_tri_loc, ts.max_tri_loc);
             T.max_edge_loc = std::max(T.max_edge_loc, ts.max_edge_loc);
+        }
+        if (!all_fused) {
+            T.frec.clear();
+            T.fedge.clear();
         }
         rc = upload_tileset(B, s);
         if (rc != UE_OK) {
@@ -1448,64 +1611,19 @@ int ue_set_source(ue_mesh* m, const int32_t* ids, const double* amp, int64_t n, 
     return bake_source(m, nullptr);
 }
 
-namespace {
-
-// The caller's array as a device address when it lies in pinned (page-locked, mapped) host
-// memory and is 8-byte aligned; NULL otherwise (the transfer is then staged through a copy).
-const double* mapped_view(const double* p) {
-    if (!p || (reinterpret_cast<uintptr_t>(p) & 7u)) return nullptr;
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();   // not a CUDA-known pointer: clear the error
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    return static_cast<const double*>(a.devicePointer);
-}
-
-// Caller -> stored maps of the direct transfers, made on first use.
-int ensure_caller_maps(ue_mesh* m, cudaStream_t s) {
-    if (m->d_kof) return UE_OK;
-    const HostMesh& h = m->hm;
-    std::vector<int32_t> kof(h.n_edges), inv(h.n_tris);
-    for (int64_t c = 0; c < h.n_edges; ++c) kof[c] = (int32_t)h.k_of_edge[c];
-    for (int64_t j = 0; j < h.n_tris; ++j) inv[h.perm_tri[j]] = (int32_t)j;
-    int32_t *a = nullptr, *b = nullptr;
-    if (!alloc_into(m, a, h.n_edges, 4, s) || !alloc_into(m, b, h.n_tris, 4, s))
-        return fail(UE_ERR_ALLOC, "caller maps of the direct field transfer");
-    UE_CUDA(cudaMemcpyAsync(a, kof.data(), 4 * kof.size(), cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaMemcpyAsync(b, inv.data(), 4 * inv.size(), cudaMemcpyHostToDevice, s));
-    UE_CUDA(cudaStreamSynchronize(s));
-    m->d_kof = a;
-    m->d_inv = b;
-    return UE_OK;
-}
-
-// Which of the given arrays go the direct way: all of them when each is pinned host memory and
-// the mesh has no PML frame (whose interface edges travel through the staging buffer).
-bool direct_transfer(const ue_mesh* m, const double* E, const double* B, const double* j,
-                     const double*& dE, const double*& dB, const double*& dj) {
-    dE = mapped_view(E);
-    dB = mapped_view(B);
-    dj = mapped_view(j);
-    if (m->dm.frame || m->fr.W > 0) return false;
-    return (!E || dE) && (!B || dB) && (!j || dj) && (E || B || j);
-}
-
-}  // namespace
 
 int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* j, void* stream) {
     Range nvtx_range("ue_write_fields");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
-    const double *dE = nullptr, *dB = nullptr, *dj = nullptr;
+    const void *dE = nullptr, *dB = nullptr, *dj = nullptr;
     if (!m->dm.J) j = nullptr;
-    if (direct_transfer(m, E, B, j, dE, dB, dj)) {
+    if (direct_transfer(m, E, B, j, 8, dE, dB, dj)) {
         // pinned host arrays: the kernels read them in place
         const int rc = ensure_caller_maps(m, s);
         if (rc != UE_OK) return rc;
-        UE_CUDA(ue::launch_fields_in_direct(m->dm, dE, dB, dj, m->d_kof, m->d_inv, m->d_elen, h.n_edges, s));
+        UE_CUDA(ue::launch_fields_in_caller(m->dm, dE, dB, dj, false, m->d_kof, m->d_inv, m->d_elen, h.n_edges, s));
         m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
     } else {
         if (E) UE_CUDA(cudaMemcpyAsync(m->d_Ec, E, 8 * h.n_edges, cudaMemcpyHostToDevice, s));
@@ -1527,13 +1645,28 @@ int ue_write_fields(ue_mesh* m, const double* E, const double* B, const double* 
         UE_CUDA(cudaMemsetAsync(f.By, 0, esz * f.n_fc, s));
     }
     {
-        const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
-        UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
-        m->since_check = 0;
-        if (m->p_err) UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
-        if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) UE_CUDA(cudaMemsetAsync(m->tb.done + 1, 0, 4, s));
+        const int rc = rearm(m, s);
+        if (rc != UE_OK) return rc;
     }
     UE_CUDA(cudaStreamSynchronize(s));
+    return UE_OK;
+}
+
+int ue_write_fields_f32(ue_mesh* m, const float* E, const float* B, const float* j, void* stream) {
+    Range nvtx_range("ue_write_fields_f32");
+    return fields_f32(m, const_cast<float*>(E), const_cast<float*>(B), const_cast<float*>(j), true,
+                      (cudaStream_t)stream);
+}
+
+int ue_read_fields_f32(ue_mesh* m, float* E, float* B, float* j, void* stream) {
+    Range nvtx_range("ue_read_fields_f32");
+    int rc = fields_f32(m, E, B, j, false, (cudaStream_t)stream);
+    if (rc != UE_OK) return rc;
+    double wd[4];
+    UE_CUDA(cudaMemcpy(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost));
+    if (wd[3] != 0.0)
+        return fail(UE_ERR_UNSTABLE, std::string("energy watchdog: ") +
+                                         (wd[3] == 1.0 ? "non-finite energy" : "energy growth beyond the limit"));
     return UE_OK;
 }
 
@@ -1571,6 +1704,17 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
             left -= batch;
             UE_CUDA(watchdog_tick(m, batch, s, &launched));
         }
+        m->steps_done += n;
+        m->launches += launched;
+        return UE_OK;
+    }
+    if (m->variant == UE_VARIANT_BLOCKED && n > 0 && !m->dm.plasma && !m->has_reg && !m->ts.hdr.empty() &&
+        ue::tbf1_fits(m->tb, m->ts.hdr.data())) {
+        // the whole mesh is one tile without a halo: all n steps in one launch of one CTA
+        UE_CUDA(ue::launch_tbf1(m->tb, m->dm, n, m->cur, s));
+        set_current(m, m->cur ^ 1);
+        int64_t launched = 1;
+        UE_CUDA(watchdog_tick(m, n, s, &launched));
         m->steps_done += n;
         m->launches += launched;
         return UE_OK;
@@ -1642,19 +1786,19 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     cudaStream_t s = (cudaStream_t)stream;
     const HostMesh& h = m->hm;
-    const double *dE = nullptr, *dB = nullptr, *dj = nullptr;
+    const void *dE = nullptr, *dB = nullptr, *dj = nullptr;
     if (j && !m->dm.J) {
         // no current in this medium: j reads as zero
         UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
         UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 8 * h.n_edges, cudaMemcpyDeviceToHost, s));
         j = nullptr;
     }
-    if (direct_transfer(m, E, B, j, dE, dB, dj)) {
+    if (direct_transfer(m, E, B, j, 8, dE, dB, dj)) {
         // pinned host arrays: the kernels write them in place
         const int rc = ensure_caller_maps(m, s);
         if (rc != UE_OK) return rc;
-        UE_CUDA(ue::launch_fields_out_direct(m->dm, const_cast<double*>(dE), const_cast<double*>(dB),
-                                             const_cast<double*>(dj), m->d_kof, m->d_inv, m->d_elen,
+        UE_CUDA(ue::launch_fields_out_caller(m->dm, const_cast<void*>(dE), const_cast<void*>(dB),
+                                             const_cast<void*>(dj), false, m->d_kof, m->d_inv, m->d_elen,
                                              h.n_edges, s));
         m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
     } else {
@@ -2224,6 +2368,10 @@ int ue_stats(const ue_mesh* m, ue_stats_t* out) {
     out->rho_hi = m->rho_hi;
     out->rho_hat = m->rho_hat;
     out->direct_fields = m->direct_fields;
+    if (m->variant == UE_VARIANT_BLOCKED && m->built) {
+        const bool whole = !m->dm.plasma && !m->has_reg && !m->ts.hdr.empty() && ue::tbf1_fits(m->tb, m->ts.hdr.data());
+        out->tb_kernel_used = whole ? UE_TBK_WHOLE_MESH : ue::tb_kernel_used(m->tb, m->dm);
+    }
     return UE_OK;
 }
 

@@ -37,7 +37,15 @@ struct TileSet {
     std::vector<int32_t> erec;            // 4 ints per local edge: gid, R|L<<16, 0, 0; each
                                           // tile's records start at a multiple of 4 records
     std::vector<int64_t> erec_tile;       // per local edge record: its tile (for sources)
+    // records of the fused kernel (build_fused_records; header 11 and 12 hold each tile's
+    // offsets, in records): per local triangle 5 ints, each tile's block a multiple of 4
+    // records; per local edge and the tile's zero slot 2 ints {gid, 0}, a multiple of 2
+    std::vector<int32_t> frec, fedge;
 };
+
+// Records of the fused triangle-centric kernel from a built tile set (layout in kernels_tbf.cu).
+// Fails (UE_ERR_ARG) when a tile is too large for them (4096 local triangles, 8191 edges).
+int build_fused_records(const HostMesh& hm, TileSet& ts, std::string& err);
 
 // include (may be NULL): build only the tiles t with (*include)[t] != 0, in order.
 int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,

@@ -40,26 +40,28 @@ def test_max_over_ranks_with_gloo():
     assert res == [(0, 7.25, 3.5), (1, 7.25, 7.25)]
 
 
-def test_traffic_is_reported_only_for_the_profiled_source():
-    """The ncu DRAM traffic in the bench line holds while the kernel source is the one that was
-    profiled; a changed source (a table entry with another hash) or an unknown configuration
-    reports none."""
+def test_counters_are_reported_only_for_the_profiled_sources(tmp_path, monkeypatch):
+    """The ncu counters in the bench line (DRAM traffic, shared-memory wavefronts, instructions)
+    hold while the kernel's sources hash as they did at the capture; changed sources or an
+    uncaptured configuration report none."""
+    import json
     sys.path.insert(0, ROOT)
     import bench
-    import hashlib
-    key = ("blocked", "greedy", 2500, 8, 512, 0)
-    src = os.path.join(ROOT, "paper_1812_01448_gb300", "csrc", bench.NCU_TRAFFIC[key][1])
-    same = hashlib.sha1(open(src, "rb").read()).hexdigest() == bench.NCU_TRAFFIC[key][2]
-    nbytes, prof = bench._traffic(key)
-    if same:
-        assert nbytes == float(bench.NCU_TRAFFIC[key][0]) and prof.startswith("profiles/")
-    else:
-        assert nbytes is None and "changed" in prof
-    assert bench._traffic(("plain", "rcm", 0, 0, 0, 0)) == (None, None)
-    saved = bench.NCU_TRAFFIC[key]
-    try:
-        bench.NCU_TRAFFIC[key] = saved[:2] + ("0" * 40,) + saved[3:]
-        nbytes, why = bench._traffic(key)
-        assert nbytes is None and "changed" in why
-    finally:
-        bench.NCU_TRAFFIC[key] = saved
+    key = {"workload": "scatterer", "variant": "blocked", "tiler": "greedy", "tile_tris": 2500,
+           "block_depth": 8, "threads": 512, "frame": 0, "kernel": "split"}
+    rec = {"config": key, "sources_sha1": bench.sources_sha1(),
+           "per_launch": {"dram_bytes": 5.0, "smem_wavefronts": 7.0, "smem_instructions": 3.5,
+                          "warp_instructions": 11.0}}
+    f = tmp_path / "counters.json"
+    f.write_text(json.dumps({"records": [rec]}))
+    monkeypatch.setattr(bench, "COUNTER_FILE", str(f))
+    got, why = bench._counters(key)
+    assert why is None and got["per_launch"]["dram_bytes"] == 5.0
+    assert bench._counters(dict(key, tile_tris=2048)) == (None, "configuration not captured")
+    f.write_text(json.dumps({"records": [dict(rec, sources_sha1="0" * 40)]}))
+    got, why = bench._counters(key)
+    assert got is None and "changed" in why
+    # the committed file parses and every record names a configuration and a sources hash
+    with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as fh:
+        for r in json.load(fh)["records"]:
+            assert set(r["config"]) == set(key) and len(r["sources_sha1"]) == 40

@@ -125,3 +125,38 @@ def test_persistent_barrier_timeout_is_reported(ue, small):
     E, B, _ = m.read_fields()
     assert np.all(np.isfinite(B))
     m.close()
+
+
+@pytest.mark.parametrize("kernel", ["split", "fused"])
+def test_blocked_copy_wait_timeout_is_reported(ue, small, kernel):
+    """A CTA of the pipelined blocked kernels whose barrier is armed for record bytes that never
+    arrive (test hook): its bounded wait runs out after about a second, all its threads agree
+    to stop before using the staged records, it waits (bounded) for its copies in flight and
+    returns; the launch ends, UE_ERR_TIMEOUT is reported, and the same mesh then steps
+    normally, equal to the plain step."""
+    ms, ops, rho = small
+    tbk = ue.UE_TB_FUSED if kernel == "fused" else ue.UE_TB_SPLIT
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=64)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=0.5 / rho, variant=ue.UE_VARIANT_BLOCKED,
+                     block_depth=4, tb_kernel=tbk, test_skip_cta=1)
+    assert m.stats()["tb_kernel_used"] == (4 if kernel == "fused" else 3)
+    assert m.tiles().size - 1 > 1
+    m.write_fields(B=np.ones(m.n_tris))
+    m.step_n(4)
+    ok, W, flag = m.check()
+    assert not ok and flag == 3
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=0.5 / rho, variant=ue.UE_VARIANT_BLOCKED,
+                     block_depth=4, tb_kernel=tbk)
+    B0 = np.sin(9 * ms.xy[ms.tris].mean(axis=1)[:, 0])
+    m.write_fields(B=B0)
+    m.step_n(9)
+    assert m.check()[0]
+    E, B, _ = m.read_fields()
+    m.close()
+    p = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY, tile_tris=64)
+    p.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=0.5 / rho)
+    p.write_fields(B=B0)
+    p.step_n(9)
+    Ep, Bp, _ = p.read_fields()
+    p.close()
+    assert np.array_equal(E, Ep) and np.array_equal(B, Bp)
