@@ -47,8 +47,8 @@ L2_BYTES = 129e6
 # profiles/ncu_counters.json with the sha1 of the sources they measured: used only while those
 # sources are unchanged, else reported as null.
 COUNTER_FILE = os.path.join(ROOT, "profiles", "ncu_counters.json")
-COUNTER_SOURCES = ("paper_1812_01448_gb300/csrc/kernels_tb.cu", "paper_1812_01448_gb300/csrc/device.cuh",
-                   "paper_1812_01448_gb300/csrc/tiles_host.cpp")
+COUNTER_SOURCES = ("paper_1812_01448_gb300/csrc/kernels_tb.cu", "paper_1812_01448_gb300/csrc/kernels_tbf.cu",
+                   "paper_1812_01448_gb300/csrc/device.cuh", "paper_1812_01448_gb300/csrc/tiles_host.cpp")
 
 
 def sources_sha1(paths=COUNTER_SOURCES) -> str:
@@ -720,6 +720,48 @@ def run_modes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_spectrum(args):
+    """Both ends of the spectrum of a rectangular resonator of 101 x 70 lattice cells (Section 2,
+    Fig. 4: the mesh's eigenvalues against the analytic ones), jittered and Delaunay-triangulated:
+    the lowest modes from ue_modes_low (Chebyshev-filtered subspace iteration) against the
+    analytic TE(m, n) frequencies pi sqrt((m/a)^2 + (n/b)^2), and the highest from ue_modes (the
+    complex-time method with deflation), which set the stability bound of eq. 20."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_01448_gb300 import build as b
+    b.build()
+    import paper_1812_01448_gb300 as ue
+    import meshgen
+    a_len, b_len = 1.01, 0.70
+    ms = meshgen.cavity_lattice(102, 71, a_len, b_len, seed=1007)
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-5)
+    n_low = 16
+    analytic = np.array(sorted(np.pi * np.hypot(i / a_len, j / b_len)
+                               for i in range(40) for j in range(40) if i or j)[:n_low - 1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    low = m.modes_low(n_low, iters=400, degree=32, seed=2)
+    t_low = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    top = m.modes(4, iters=3000, seed=2)
+    t_top = time.perf_counter() - t0
+    rel = low[1:] / analytic - 1.0
+    line = {
+        "metric": "resonator spectrum (Fig. 4): lowest and highest omegas", "unit": "rad/s (c = 1)",
+        "value": float(low[1]), "dtype": "f64", "data": "synthetic",
+        "omega_low": [float(x) for x in low], "omega_analytic": [0.0] + [float(x) for x in analytic],
+        "rel_err_low": [float(x) for x in rel], "max_rel_err_low": float(np.abs(rel).max()),
+        "omega_top": [float(x) for x in top], "dt_bound_eq20": 2.0 / float(top[0]),
+        "seconds_low": t_low, "seconds_top": t_top,
+        "config": {"workload": "resonator 1.01 x 0.70 (101 x 70 lattice cells, jitter 0.2h, Delaunay)",
+                   "n_tris": m.n_tris, "n_low": n_low, "n_top": 4},
+    }
+    m.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_relax(args):
     """Mesh optimisation (ue_mesh_relax: jello model, Section 3) on a Delaunay mesh of random
     points in the unit square: GPU time per relaxation step, the whole call with Lawson flips
@@ -799,7 +841,8 @@ def main(argv=None):
                     help="element type of the host field arrays of the end-to-end measurement")
     ap.add_argument("--tb-kernel", choices=["split", "fused"], default="split",
                     help="blocked variant: the split kernel (edges, then triangles) or the fused one")
-    ap.add_argument("--workload", choices=["scatterer", "plasma", "cavity", "batch", "learned", "modes", "relax"],
+    ap.add_argument("--workload", choices=["scatterer", "plasma", "cavity", "batch", "learned", "modes", "relax",
+                                           "spectrum"],
                     default="scatterer",
                     help="scatterer: scatterer-4M (the default); plasma: plasma-1M (cold-plasma current); "
                          "cavity: the 1,024-triangle cavity in one CTA")
@@ -824,6 +867,8 @@ def main(argv=None):
         run_cavity(args)
     elif args.workload == "modes":
         run_modes(args)
+    elif args.workload == "spectrum":
+        run_spectrum(args)
     elif args.workload == "relax":
         run_relax(args)
     elif args.workload == "learned":

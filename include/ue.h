@@ -372,6 +372,18 @@ int ue_mesh_flip(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
 int ue_modes(ue_mesh* m, int32_t n_modes, int32_t iters, uint32_t seed, double* omega, double* B,
              void* stream);
 
+/* The lowest eigenmodes (the other end of the spectrum of Section 2, which Fig. 4 plots against
+ * the analytic resonator frequencies): omega[0..n_modes) ascending (omega[0] = 0 for the
+ * static field B = constant of a PEC cavity) and, if B is not NULL, their B fields (n_modes x
+ * n_tris, caller order, S-normalised).  Chebyshev-filtered subspace iteration on a block of
+ * min(32, 2 n_modes) columns: each of at most `iters` filters is the degree-`degree` Chebyshev
+ * polynomial of K that stays within [-1, 1] on [lo, hi] (hi a Gershgorin bound of the largest
+ * eigenvalue, lo the block's largest Ritz value) and grows below lo, followed by Cholesky QR in
+ * the S metric and Rayleigh-Ritz; it stops early when the n_modes Ritz values no longer move.
+ * FP64, synchronous.  n_modes in [1, 16], degree in [2, 200].  Errors as ue_modes. */
+int ue_modes_low(ue_mesh* m, int32_t n_modes, int32_t iters, int32_t degree, uint32_t seed, double* omega,
+                 double* B, void* stream);
+
 /* Open boundaries: a PML frame (the paper's conclusion: a mesh with a rectangular boundary tied
  * to a structured frame of rectangular cells carrying PML layers).  The frame is `width` square
  * cells of side h around the mesh's bounding box [X0, X1] x [Y0, Y1], h being the spacing of

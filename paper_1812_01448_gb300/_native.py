@@ -88,6 +88,7 @@ SIGNATURES = [
     ("ue_profile_steps", C.c_int, [P, I64, P, PD, PD]),
     ("ue_power_iteration_static", C.c_int, [P, P, P, P, P, P, I64, I64, C.c_int32, C.c_uint32, P, PD]),
     ("ue_modes", C.c_int, [P, C.c_int32, C.c_int32, C.c_uint32, PD, PD, P]),
+    ("ue_modes_low", C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, PD, PD, P]),
     ("ue_mesh_relax", C.c_int, [PD, I64, PI32, I64, PD, C.c_int32, C.c_int32, C.c_double, PI32, I64,
                                 PI32, I64, PD, PI32, PI64, P]),
     ("ue_mesh_flip", C.c_int, [PD, I64, PI32, I64, PI32, I64, PI32, PI64]),

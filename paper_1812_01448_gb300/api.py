@@ -330,6 +330,16 @@ class Mesh:
                                  _dptr(B), _stream(stream)), "ue_modes")
         return (om, B) if vectors else om
 
+    def modes_low(self, n_modes: int, iters: int = 200, degree: int = 24, seed: int = 0, vectors: bool = False,
+                  stream=None):
+        """The n_modes lowest modes (ue_modes_low): omegas ascending, and with vectors=True their
+        B fields (n_modes x n_tris, caller order, S-normalised)."""
+        om = np.zeros(int(n_modes))
+        B = np.zeros((int(n_modes), self.n_tris)) if vectors else None
+        N.check(N.lib().ue_modes_low(self._h, int(n_modes), int(iters), int(degree), int(seed) & 0xFFFFFFFF,
+                                     _dptr(om), _dptr(B), _stream(stream)), "ue_modes_low")
+        return (om, B) if vectors else om
+
     def stats(self) -> dict:
         s = N.Stats()
         N.check(N.lib().ue_stats(self._h, C.byref(s)), "ue_stats")

@@ -311,6 +311,13 @@ cudaError_t launch_rho_infer(const double* xy, const int32_t* tri_nodes, const i
 // *lost_rank is set (and nothing else computed) when the block stops being of full rank.
 int modes_block_size(int n_modes);
 size_t modes_work_doubles(int64_t n_t, int64_t n_ei, int m);
+// The lowest modes (Chebyshev-filtered subspace iteration, degree-`degree` filters, at most
+// `iters` of them): omega ascending; work holds modes_low_work_doubles doubles.
+size_t modes_low_work_doubles(int64_t n_t, int64_t n_ei, int m);
+cudaError_t modes_low_run(const int2* rl, const int4* tri, const double* elen, const double* d,
+                          const double* S, const int64_t* perm, int64_t n_t, int64_t n_ei, int n_modes,
+                          int iters, int degree, uint32_t seed, double* work, double* omega,
+                          double* B_dev, bool* lost_rank, cudaStream_t s);
 cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const double* d,
                       const double* S, const int64_t* perm, int64_t n_t, int64_t n_ei, int n_modes,
                       int iters, uint32_t seed, double* work, double* omega, double* B_dev,

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "device.cuh"
@@ -194,6 +195,39 @@ __global__ void k_md_scatter(const double* __restrict__ V, const int64_t* __rest
     out[(int64_t)col * n_t + perm[j]] = V[j * m + col];
 }
 
+// One step of the Chebyshev recurrence on blocks: Y1 = a (W - c Y) + b Y0, with W = K Y.
+__global__ void k_md_cheb(const double* __restrict__ W, const double* __restrict__ Y,
+                          const double* __restrict__ Y0, double* __restrict__ Y1, double a, double c,
+                          double b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double y = a * (W[i] - c * Y[i]);
+    Y1[i] = Y0 ? fma(b, Y0[i], y) : y;
+}
+
+// Gershgorin bound of S^(1/2) K S^(-1/2) (the S-symmetric form of K, same eigenvalues): row j
+// has K_jj = sum_q c_q / S_j and off-diagonal c_q / sqrt(S_j S_k) for the triangle k across
+// interior edge q; the largest row sum bounds lambda_max from above.  Positive doubles order
+// like their bit patterns, so the maximum is an integer atomic.
+__global__ void k_md_gersh(const int4* __restrict__ tri, const int2* __restrict__ rl,
+                           const double* __restrict__ c, const double* __restrict__ S,
+                           int64_t n_t, int64_t n_ei, unsigned long long* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    const int4 q = tri[j];
+    const int code[3] = {q.x, q.y, q.z};
+    const double sj = S[j];
+    double row = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int64_t e = code[k] >> 1;
+        if (e >= n_ei) continue;
+        const int2 t = rl[e];
+        const int64_t o = t.x == j ? t.y : t.x;
+        row += c[e] / sj + c[e] / sqrt(sj * S[o]);
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(row));
+}
+
 // ---- host: small dense algebra on m x m matrices (m <= 32) --------------------------------
 
 // upper-triangular R with G = R^T R; false if G is not positive definite
@@ -353,6 +387,137 @@ cudaError_t modes_run(const int2* rl, const int4* tri, const double* elen, const
         md_apply<false>(V, T, W, n_t, m, s);
         k_md_scatter<<<md_blocks(n_t * n_modes), kMdThreads, 0, s>>>(W, perm, B_dev, n_t, m, n_modes);
     }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+size_t modes_low_work_doubles(int64_t n_t, int64_t n_ei, int m) {
+    return modes_work_doubles(n_t, n_ei, m) + 2 * (size_t)n_t * m + 8;
+}
+
+// The lowest n_modes eigenpairs of K by Chebyshev-filtered subspace iteration: each outer
+// iteration applies to the block the degree-`degree` Chebyshev polynomial that stays within
+// [-1, 1] on [lo, hi] (hi a certified Gershgorin bound of lambda_max, lo the block's largest
+// Ritz value) and grows fast below lo, then makes the block S-orthonormal (Cholesky QR) and
+// rotates it by Rayleigh-Ritz.  The columns beyond n_modes guard the convergence.  Omegas
+// ascending; B_dev as in modes_run.
+cudaError_t modes_low_run(const int2* rl, const int4* tri, const double* elen, const double* d,
+                          const double* S, const int64_t* perm, int64_t n_t, int64_t n_ei, int n_modes,
+                          int iters, int degree, uint32_t seed, double* work, double* omega,
+                          double* B_dev, bool* lost_rank, cudaStream_t s) {
+    const int m = modes_block_size(n_modes);
+    const int npair = m * m, nup = m * (m + 1) / 2;
+    const int nb = (int)std::min<int64_t>(152 * 4, (n_t + kMdRows - 1) / kMdRows);
+    double* V = work;
+    double* W = V + n_t * m;
+    double* g = W + n_t * m;
+    double* c = g + (n_ei + 1) * m;
+    double* invS = c + n_ei;
+    double* part = invS + n_t;
+    double* G = part + (int64_t)nb * nup;
+    double* T = G + npair;
+    double* Y0 = work + modes_work_doubles(n_t, n_ei, m);
+    double* Y1 = Y0 + n_t * m;
+    unsigned long long* gmax = reinterpret_cast<unsigned long long*>(Y1 + n_t * m);
+    *lost_rank = false;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g + n_ei * m, 0, sizeof(double) * m, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(gmax, 0, 8, s)) != cudaSuccess) return e;
+    k_md_prep<<<md_blocks(std::max(n_ei, n_t)), kMdThreads, 0, s>>>(elen, d, S, c, invS, n_ei, n_t);
+    k_md_gersh<<<md_blocks(n_t), kMdThreads, 0, s>>>(tri, rl, c, S, n_t, n_ei, gmax);
+    k_md_init<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(V, perm, seed, n_t, m);
+    unsigned long long hb = 0;
+    if ((e = cudaMemcpyAsync(&hb, gmax, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    double hi;
+    std::memcpy(&hi, &hb, 8);
+    hi *= 1.0 + 1e-12;
+    std::vector<double> Gu(nup), Gh(npair), R, Th, lam, Q;
+    auto apply_K = [&](const double* X, double* Y) {
+        if (n_ei > 0) k_md_edge<<<md_blocks(n_ei * m), kMdThreads, 0, s>>>(rl, c, X, g, n_ei, m);
+        k_md_tri<<<md_blocks(n_t * m), kMdThreads, 0, s>>>(tri, invS, g, Y, n_t, m);
+    };
+    auto gram = [&](const double* X, const double* Y) -> cudaError_t {
+        k_md_gram<<<nb, kMdThreads, 0, s>>>(S, X, Y, n_t, m, part);
+        k_md_sum<<<(nup + 255) / 256, 256, 0, s>>>(part, nb, nup, G);
+        cudaError_t e2 = cudaMemcpyAsync(Gu.data(), G, sizeof(double) * nup, cudaMemcpyDeviceToHost, s);
+        if (e2 != cudaSuccess) return e2;
+        if ((e2 = cudaStreamSynchronize(s)) != cudaSuccess) return e2;
+        for (int a = 0, p = 0; a < m; ++a)
+            for (int b = a; b < m; ++b, ++p) Gh[(size_t)a * m + b] = Gh[(size_t)b * m + a] = Gu[p];
+        return cudaSuccess;
+    };
+    auto orthonormalize = [&](const double* X, double* Y) -> cudaError_t {   // Y = X R^{-1}
+        cudaError_t e2 = gram(X, X);
+        if (e2 != cudaSuccess) return e2;
+        if (!cholesky_upper(Gh, m, R)) {
+            *lost_rank = true;
+            return cudaSuccess;
+        }
+        upper_inverse(R, m, Th);
+        if ((e2 = cudaMemcpyAsync(T, Th.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return e2;
+        md_apply<true>(X, T, Y, n_t, m, s);
+        return cudaGetLastError();
+    };
+    // The block always lives in V (the work space's first n_t * m values), W is scratch; the
+    // filter's recurrence rotates among V, Y0 and Y1.
+    const int64_t n = n_t * m;
+    auto copy_to_V = [&](const double* X) -> cudaError_t {
+        return X == V ? cudaSuccess : cudaMemcpyAsync(V, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    };
+    // V -> its Ritz vectors (V^T S K V diagonal), lam ascending
+    auto rayleigh_ritz = [&]() -> cudaError_t {
+        apply_K(V, W);
+        cudaError_t e2 = gram(V, W);
+        if (e2 != cudaSuccess) return e2;
+        jacobi_eigen(Gh, m, lam, Q);
+        std::reverse(lam.begin(), lam.end());
+        for (int r = 0; r < m; ++r) std::reverse(Q.begin() + (size_t)r * m, Q.begin() + (size_t)(r + 1) * m);
+        if ((e2 = cudaMemcpyAsync(T, Q.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return e2;
+        md_apply<false>(V, T, W, n_t, m, s);
+        return copy_to_V(W);
+    };
+    if ((e = orthonormalize(V, W)) != cudaSuccess || *lost_rank) return e;
+    if ((e = copy_to_V(W)) != cudaSuccess) return e;
+    if ((e = rayleigh_ritz()) != cudaSuccess) return e;
+    std::vector<double> prev(n_modes, -1.0);
+    for (int it = 0; it < iters; ++it) {
+        // the interval to damp: [lo, hi], lo the block's largest Ritz value (at least a small
+        // fraction of hi, so that the first filters, on a random block, damp only the top)
+        const double lo = std::max(lam[m - 1], 1e-3 * hi);
+        const double cc = 0.5 * (hi + lo), ee = 0.5 * (hi - lo);
+        // scaled three-term recurrence: T_k((x - cc)/ee) / T_k((0 - cc)/ee) (Zhou and Saad)
+        const double sig1 = ee / (0.0 - cc);
+        double sig = sig1;
+        apply_K(V, W);
+        k_md_cheb<<<md_blocks(n), kMdThreads, 0, s>>>(W, V, nullptr, Y1, sig1 / ee, cc, 0.0, n);
+        double* Yp = V;    // T_{k-1}
+        double* Yc = Y1;   // T_k
+        double* Yn = Y0;
+        for (int k = 2; k <= degree; ++k) {
+            const double sn = 1.0 / (2.0 / sig1 - sig);
+            apply_K(Yc, W);
+            k_md_cheb<<<md_blocks(n), kMdThreads, 0, s>>>(W, Yc, Yp, Yn, 2.0 * sn / ee, cc, -sig * sn, n);
+            sig = sn;
+            double* t = Yp;
+            Yp = Yc;
+            Yc = Yn;
+            Yn = t;
+        }
+        if ((e = orthonormalize(Yc, W)) != cudaSuccess || *lost_rank) return e;
+        if ((e = copy_to_V(W)) != cudaSuccess) return e;
+        if ((e = rayleigh_ritz()) != cudaSuccess) return e;
+        bool done = true;
+        for (int i = 0; i < n_modes; ++i) {
+            if (std::fabs(lam[i] - prev[i]) > 1e-15 * hi) done = false;
+            prev[i] = lam[i];
+        }
+        if (done && it > 0) break;
+    }
+    for (int i = 0; i < n_modes; ++i) omega[i] = std::sqrt(std::max(lam[i], 0.0));
+    if (B_dev) k_md_scatter<<<md_blocks(n_t * n_modes), kMdThreads, 0, s>>>(V, perm, B_dev, n_t, m, n_modes);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
 }

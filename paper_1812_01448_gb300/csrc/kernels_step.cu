@@ -1,8 +1,7 @@
 // The leap-frog step (eqs. 14-15): the E half-step of eq. 3 (eq. 6 with the current of eq. 5
 // in plasma media, plus the soft source) over interior edges, then the B half-step of eq. 4
-// over triangles.  Plain form: two kernels per step, four elements per thread with 16-byte
-// loads of the streamed arrays, so that each thread keeps several independent gathers in
-// flight.
+// over triangles.  Plain form: two kernels per step, four elements per thread, so that each
+// thread keeps several independent gathers in flight.
 //
 // Stored variables are circulations U_i = |e_i| E_i (and J_i = |e_i| j_i), so that
 //   E half-step:  U_i += (dt |e_i| / d_i) (B_R - B_L)            [eq. 3 times dt |e_i|]
@@ -24,41 +23,6 @@ namespace ue {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <typename T>
-__device__ __forceinline__ void ld4(const T* __restrict__ p, T (&x)[4]) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-    } else {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-    }
-}
-
-// load/store of read-write arrays (not through the read-only path)
-template <typename T>
-__device__ __forceinline__ void ldw4(const T* p, T (&x)[4]) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-    } else {
-        const double2 a = reinterpret_cast<const double2*>(p)[0];
-        const double2 b = reinterpret_cast<const double2*>(p)[1];
-        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void st4(T* p, const T (&x)[4]) {
-    if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-    } else {
-        reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
-        reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
-    }
-}
 
 __device__ __forceinline__ bool flagged(float c) { return __float_as_uint(c) >> 31; }
 __device__ __forceinline__ bool flagged(double c) {
@@ -91,48 +55,57 @@ __device__ __forceinline__ T source_term(const SrcArgs<T>& src, int k, T u) {
     return rn_fma(__ldg(src.c + e.y), (T)g, u);
 }
 
+// Each warp takes 4 x 32 consecutive elements, element 32 i + lane of its run of 128 in pass i:
+// every load instruction of the warp reads 32 consecutive records (coalesced), and its gathers
+// come from 32 neighbouring elements, whose neighbours are close in the stored order.
+constexpr int kPer = 4;
+
+__device__ __forceinline__ int64_t run_base() {
+    return ((int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u)) * kPer + (threadIdx.x & 31u);
+}
+
 // FRAME: blocks from nb_mesh on run a PML frame's sides and interface edges (frame.cuh); they
 // write only the frame's arrays and the interface slots, which no mesh thread touches.
 template <typename T, bool PLASMA, bool SRC, bool FRAME>
 __global__ void __launch_bounds__(kThreads)
-k_edge_half(const int4* __restrict__ rl4, const T* __restrict__ cU, const T* __restrict__ B,
+k_edge_half(const int2* __restrict__ rl, const T* __restrict__ cU, const T* __restrict__ B,
             T* __restrict__ U, const T* __restrict__ pb, T* __restrict__ J, T pa, T mdt,
-            int64_t n_vec, SrcArgs<T> src, FrameDev f, int64_t nb_mesh) {
+            int64_t n_pad, SrcArgs<T> src, FrameDev f, int64_t nb_mesh) {
     if constexpr (FRAME) {
         if ((int64_t)blockIdx.x >= nb_mesh) {
             frame_edge_thread<T>(f, B, U, ((int64_t)blockIdx.x - nb_mesh) * kThreads + threadIdx.x);
             return;
         }
     }
-    const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (v >= n_vec) return;
-    const int4 ra = __ldg(rl4 + 2 * v), rb = __ldg(rl4 + 2 * v + 1);
-    const int R[4] = {ra.x, ra.z, rb.x, rb.z};
-    const int L[4] = {ra.y, ra.w, rb.y, rb.w};
-    T c[4], u[4], b[4], un[4];
-    ld4(cU + 4 * v, c);
-    ldw4(U + 4 * v, u);
+    const int64_t e0 = run_base();
+    if (e0 >= n_pad) return;
+    int2 r[kPer];
+    T c[kPer], u[kPer], b[kPer];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = rn_sub(__ldg(B + R[i]), __ldg(B + L[i]));
+    for (int i = 0; i < kPer; ++i) {
+        const int64_t e = e0 + 32 * i;
+        const bool in = e < n_pad;
+        r[i] = in ? __ldg(rl + e) : make_int2(0, 0);
+        c[i] = in ? __ldg(cU + e) : (T)0;
+        u[i] = in ? U[e] : (T)0;
+    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) un[i] = rn_fma(fabs(c[i]), b[i], u[i]);
-    if constexpr (PLASMA) {
-        T jj[4], p[4];
-        ldw4(J + 4 * v, jj);
-        ld4(pb + 4 * v, p);
+    for (int i = 0; i < kPer; ++i) b[i] = rn_sub(__ldg(B + r[i].x), __ldg(B + r[i].y));
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            jj[i] = rn_fma(pa, jj[i], rn_mul(p[i], u[i]));
-            un[i] = rn_fma(mdt, jj[i], un[i]);
+    for (int i = 0; i < kPer; ++i) {
+        const int64_t e = e0 + 32 * i;
+        if (e >= n_pad) break;
+        T un = rn_fma(fabs(c[i]), b[i], u[i]);
+        if constexpr (PLASMA) {
+            const T jj = rn_fma(pa, J[e], rn_mul(__ldg(pb + e), u[i]));
+            un = rn_fma(mdt, jj, un);
+            J[e] = jj;
         }
-        st4(J + 4 * v, jj);
+        if constexpr (SRC) {
+            if (flagged(c[i])) un = source_term(src, (int)e, un);
+        }
+        U[e] = un;
     }
-    if constexpr (SRC) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (flagged(c[i])) un[i] = source_term(src, (int)(4 * v + i), un[i]);
-    }
-    st4(U + 4 * v, un);
 }
 
 template <typename T>
@@ -145,7 +118,7 @@ __device__ __forceinline__ T signed_load(const T* __restrict__ U, int code) {
 template <typename T, bool FRAME>
 __global__ void __launch_bounds__(kThreads)
 k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
-           const T* __restrict__ U, T* __restrict__ B, int64_t n_vec, long long* __restrict__ step,
+           const T* __restrict__ U, T* __restrict__ B, int64_t n_pad, long long* __restrict__ step,
            FrameDev f, int64_t nb_mesh) {
     if constexpr (FRAME) {
         if ((int64_t)blockIdx.x >= nb_mesh) {
@@ -153,24 +126,29 @@ k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
             return;
         }
     }
-    const int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (v == 0) *step += 1;
-    if (v >= n_vec) return;
-    int4 t[4];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
+    const int64_t j0 = run_base();
+    if (j0 >= n_pad) return;
+    int4 t[kPer];
+    T bo[kPer];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) t[i] = __ldg(tri + 4 * v + i);
-    T bo[4];
-    ldw4(B + 4 * v, bo);
+    for (int i = 0; i < kPer; ++i) {
+        const int64_t j = j0 + 32 * i;
+        const bool in = j < n_pad;
+        t[i] = in ? __ldg(tri + j) : make_int4(0, 0, 0, 0);
+        bo[i] = in ? B[j] : (T)0;
+    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kPer; ++i) {
+        const int64_t j = j0 + 32 * i;
         const T s = rn_add(rn_add(signed_load(U, t[i].x), signed_load(U, t[i].y)),
                            signed_load(U, t[i].z));
+        if (j >= n_pad) break;
         T c;
         if constexpr (sizeof(T) == 4) c = __int_as_float(t[i].w);
-        else c = __ldg(cB64 + 4 * v + i);
-        bo[i] = rn_fma(-c, s, bo[i]);
+        else c = __ldg(cB64 + j);
+        B[j] = rn_fma(-c, s, bo[i]);
     }
-    st4(B + 4 * v, bo);
 }
 
 // g(t_n) of every source group for the next `count` steps, n = *step + i.
@@ -184,46 +162,47 @@ __global__ void k_gtab(double* __restrict__ g, const long long* __restrict__ ste
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+inline unsigned blocks_for_runs(int64_t n_pad) { return blocks_for((n_pad + kPer - 1) / kPer); }
 
 template <typename T, bool PLASMA>
 void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
-    const int64_t n_vec = m.n_ei_pad / 4;
+    const int64_t n_pad = m.n_ei_pad;
     SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.src_grp, m.gtab,
                    m.gtab_size, s_index};
     const T pa = PLASMA ? (T)m.pa : (T)0, mdt = PLASMA ? (T)(-m.dt) : (T)0;
-    const int64_t nb = blocks_for(n_vec);
+    const int64_t nb = blocks_for_runs(n_pad);
     // a frame adds its blocks to the same launch (its sides and the outer edges are vacuum)
     const FrameDev f = m.frame ? *m.frame : FrameDev();
     const int64_t nbf = m.frame ? blocks_for(f.n_fc + f.n_if) : 0;
     const unsigned grid = (unsigned)(nb + nbf);
-    const int4* rl = (const int4*)m.rl;
+    const int2* rl = (const int2*)m.rl;
     if (nbf > 0) {
         if (m.n_src > 0)
             k_edge_half<T, PLASMA, true, true><<<grid, kThreads, 0, s>>>(
-                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
         else
             k_edge_half<T, PLASMA, false, true><<<grid, kThreads, 0, s>>>(
-                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
     } else if (m.n_src > 0) {
         k_edge_half<T, PLASMA, true, false><<<grid, kThreads, 0, s>>>(
-            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
     } else {
         k_edge_half<T, PLASMA, false, false><<<grid, kThreads, 0, s>>>(
-            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_vec, src, f, nb);
+            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
     }
 }
 
 template <typename T>
 void tri_half_t(const DevMesh& m, cudaStream_t s) {
-    const int64_t n_vec = m.n_t_pad / 4;
-    const int64_t nb = blocks_for(n_vec);
+    const int64_t n_pad = m.n_t_pad;
+    const int64_t nb = blocks_for_runs(n_pad);
     if (m.frame) {
         const int64_t nbf = blocks_for(m.frame->n_fc);
         k_tri_half<T, true><<<(unsigned)(nb + nbf), kThreads, 0, s>>>(
-            m.tri, (const double*)m.cB, (const T*)m.U, (T*)m.B, n_vec, m.step, *m.frame, nb);
+            m.tri, (const double*)m.cB, (const T*)m.U, (T*)m.B, n_pad, m.step, *m.frame, nb);
     } else {
         k_tri_half<T, false><<<(unsigned)nb, kThreads, 0, s>>>(m.tri, (const double*)m.cB, (const T*)m.U,
-                                                              (T*)m.B, n_vec, m.step, FrameDev(), nb);
+                                                              (T*)m.B, n_pad, m.step, FrameDev(), nb);
     }
 }
 

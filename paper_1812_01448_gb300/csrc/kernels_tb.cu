@@ -22,7 +22,8 @@ constexpr int kNT = 512;
 struct TBArgs {
     const int* hdr;
     const int4* trec;
-    const int* erec;    // 3 ints per local edge record: gid, R | L << 16, bits of cU (sign: source)
+    const int* erec;    // 3 ints per local edge record: gid, lo | hi << 16 | (R > L) << 31 (the
+                        // slots of its triangles in increasing order), bits of cU (sign: source)
     const float* epb;   // plasma coefficient per local edge record
     const int2* tsrc;
     const float* Bin;
@@ -44,6 +45,14 @@ struct TBArgs {
     int test_cta;       // tests only (-1 otherwise): this CTA arms its first record copy for
                         // 16 bytes more than it delivers, so that the wait for it runs out
 };
+
+// An edge record's slot pair (lo | hi << 16) and its coefficient for B_lo - B_hi: dt|e|/d where
+// R is the lower slot, its negation where R is the higher one (bit 31 of the pair word).
+__device__ __forceinline__ int rec_pair(int w) { return w & 0x7FFFFFFF; }
+__device__ __forceinline__ float rec_coef(int w, int cu_bits) {
+    const float c = fabsf(__int_as_float(cu_bits));
+    return w < 0 ? -c : c;
+}
 
 // NT threads; each thread owns local triangle slots tid + i*NT (i < TS) and local edge slots
 // tid + i*NT (i < ES), whose records it keeps in registers for all k steps.  In every phase a
@@ -83,9 +92,9 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     for (int i = 0; i < ES; ++i) {
         const int l = tid + i * NT;
         if (l < nel) {
-            const int gid = __ldg(er + 3 * l);
-            erl[i] = __ldg(er + 3 * l + 1);
-            ecu[i] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
+            const int gid = __ldg(er + 3 * l), w = __ldg(er + 3 * l + 1);
+            erl[i] = rec_pair(w);
+            ecu[i] = rec_coef(w, __ldg(er + 3 * l + 2));
             Ul[l] = __ldg(a.Uin + gid);
             if constexpr (PLASMA) {
                 epb[i] = __ldg(a.epb + h[7] + l);
@@ -105,13 +114,13 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
         const int eend = h[32 + lim];
 #pragma unroll
         for (int g0 = 0; g0 < ES; g0 += kG) {
-            float bR[kG], bL[kG], uo[kG], jo[kG];
+            float blo[kG], bhi[kG], uo[kG], jo[kG];
 #pragma unroll
             for (int q = 0; q < kG; ++q) {
                 const int i = g0 + q, l = tid + i * NT;
                 if (i < ES && l < eend) {
-                    bR[q] = Bl[erl[i] & 0xFFFF];
-                    bL[q] = Bl[(unsigned)erl[i] >> 16];
+                    blo[q] = Bl[erl[i] & 0xFFFF];
+                    bhi[q] = Bl[(unsigned)erl[i] >> 16];
                     uo[q] = Ul[l];
                     if constexpr (PLASMA) jo[q] = Jl[l];
                 }
@@ -120,7 +129,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
             for (int q = 0; q < kG; ++q) {
                 const int i = g0 + q, l = tid + i * NT;
                 if (i < ES && l < eend) {
-                    float un = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo[q]);
+                    float un = rn_fma(ecu[i], rn_sub(blo[q], bhi[q]), uo[q]);
                     if constexpr (PLASMA) {
                         const float jn = rn_fma(a.pa, jo[q], rn_mul(epb[i], uo[q]));
                         Jl[l] = jn;
@@ -229,9 +238,9 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
         Bl[l] = __ldg(a.Bin + r.x);
     }
     for (int l = tid; l < nel; l += NT) {
-        const int gid = __ldg(er + 3 * l);
-        Erl[l] = __ldg(er + 3 * l + 1);
-        Ecu[l] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
+        const int gid = __ldg(er + 3 * l), w = __ldg(er + 3 * l + 1);
+        Erl[l] = rec_pair(w);
+        Ecu[l] = rec_coef(w, __ldg(er + 3 * l + 2));
         Ul[l] = __ldg(a.Uin + gid);
         if constexpr (PLASMA) {
             Epb[l] = __ldg(a.epb + h[7] + l);
@@ -470,7 +479,7 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
     if (!ok) tile = n_tiles;
     __syncthreads();
     // per slot: triangle gather offsets (U0 | U1 << 16, U2), -s0 dt/S, s0 s1, s0 s2 and B;
-    // edge gather offsets (B_R | B_L << 16), dt|e|/d and U (plasma: pb and J)
+    // edge gather offsets (B_lo | B_hi << 16), +-dt|e|/d and U (plasma: pb and J)
     unsigned toff[TS], toff2[TS];
     float tcb[TS], ts1[TS], ts2[TS], tb[TS];
     unsigned erl[ES];
@@ -505,9 +514,9 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
         for (int i = 0; i < ES; ++i) {
             const int l = tid + i * NT;
             if (l < ne) {
-                const int cub = estage[3 * l + 2];
-                erl[i] = (unsigned)estage[3 * l + 1] << 2;
-                ecu[i] = fabsf(__int_as_float(cub));
+                const int cub = estage[3 * l + 2], w = estage[3 * l + 1];
+                erl[i] = (unsigned)rec_pair(w) << 2;
+                ecu[i] = rec_coef(w, cub);
                 if constexpr (SRC) srcm |= (cub < 0 ? 1u : 0u) << i;
                 eu[i] = Fc[Lay::UOFF + l];
                 if constexpr (PLASMA) {
@@ -527,13 +536,13 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
             // E half-step (eq. 3; eqs. 5-6 in plasma media)
 #pragma unroll
             for (int g0 = 0; g0 < ES; g0 += G) {
-                float bR[G], bL[G];
+                float blo[G], bhi[G];
 #pragma unroll
                 for (int q = 0; q < G; ++q) {
                     const int i = g0 + q;
                     if (i < ES && tid + i * NT < eend) {
-                        bR[q] = lds_at(Fcb, erl[i] & 0xFFFFu);
-                        bL[q] = lds_at(Fcb, erl[i] >> 16);
+                        blo[q] = lds_at(Fcb, erl[i] & 0xFFFFu);
+                        bhi[q] = lds_at(Fcb, erl[i] >> 16);
                     }
                 }
 #pragma unroll
@@ -541,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
                     const int i = g0 + q;
                     if (i < ES && tid + i * NT < eend) {
                         const float uo = eu[i];
-                        float un = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo);
+                        float un = rn_fma(ecu[i], rn_sub(blo[q], bhi[q]), uo);
                         if constexpr (PLASMA) {
                             const float jn = rn_fma(a.pa, ej[i], rn_mul(epb[i], uo));
                             ej[i] = jn;

@@ -702,12 +702,18 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     tb.max_tri_loc = ts.max_tri_loc;
     tb.max_edge_loc = ts.max_edge_loc;
     tb.threads = m->tb_threads;
-    // edge records go to the device as 3 ints {gid, R | L << 16, cU}: the coefficient is filled
-    // by launch_tb_fill, the plasma coefficient kept apart (tb.epb)
+    // edge records go to the device as 3 ints {gid, lo | hi << 16 | (R > L) << 31, cU}: the
+    // local slots of the edge's two triangles in increasing order, so that one gather of a warp
+    // reads the lower-numbered triangles of 32 consecutive edges and the other the higher ones
+    // (two narrow windows of slots, fewer shared-memory bank conflicts than R and L, which mix
+    // both), with bit 31 set where R is the higher slot (the kernels negate the coefficient
+    // there: rn(B_lo - B_hi) = -rn(B_R - B_L) exactly).  The coefficient is filled by
+    // launch_tb_fill, the plasma coefficient kept apart (tb.epb).
     std::vector<int32_t> e3(3 * (size_t)tb.n_erec);
     for (int64_t i = 0; i < tb.n_erec; ++i) {
+        const uint32_t w = (uint32_t)ts.erec[4 * i + 1], R = w & 0xFFFFu, L = w >> 16;
         e3[3 * i] = ts.erec[4 * i];
-        e3[3 * i + 1] = ts.erec[4 * i + 1];
+        e3[3 * i + 1] = (int32_t)(R <= L ? (R | (L << 16)) : (L | (R << 16) | 0x80000000u));
         e3[3 * i + 2] = 0;
     }
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&
@@ -2297,6 +2303,37 @@ int ue_triangulate(const double* xy, int64_t n_nodes, const int32_t* segs, int64
     *n_tris = (int64_t)out.size() / 3;
     if (*n_tris > cap_tris) return fail(UE_ERR_ARG, "ue_triangulate: cap_tris too small");
     std::memcpy(tris, out.data(), sizeof(int32_t) * out.size());
+    return UE_OK;
+}
+
+int ue_modes_low(ue_mesh* m, int32_t n_modes, int32_t iters, int32_t degree, uint32_t seed, double* omega,
+                 double* B, void* stream) {
+    Range nvtx_range("ue_modes_low");
+    if (!m || !m->built || !omega) return fail(UE_ERR_ARG, "geometry not built or NULL omega");
+    if (n_modes < 1 || n_modes > 16 || iters < 1 || degree < 2 || degree > 200)
+        return fail(UE_ERR_ARG, "ue_modes_low: n_modes in [1, 16], iters >= 1, degree in [2, 200]");
+    if (m->dm.frame) return fail(UE_ERR_ARG, "ue_modes_low: not on a framed mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostMesh& h = m->hm;
+    const int64_t nt = h.n_tris, nei = h.n_ei;
+    const int bw = ue::modes_block_size(n_modes);
+    if (nt < bw) return fail(UE_ERR_ARG, "ue_modes_low: the mesh has fewer triangles than the block of vectors");
+    double* work = nullptr;
+    double* Bd = nullptr;
+    if (!alloc_into(m, work, ue::modes_low_work_doubles(nt, nei, bw), 8, s) ||
+        (B && !alloc_into(m, Bd, (size_t)n_modes * nt, 8, s)))
+        return fail(UE_ERR_ALLOC, "ue_modes_low work space");
+    bool lost = false;
+    UE_CUDA(ue::modes_low_run(m->d_rl, m->dm.tri, m->d_elen, m->d_d, m->d_S, m->d_perm, nt, nei, n_modes,
+                              iters, degree, seed, work, omega, Bd, &lost, s));
+    if (lost) {
+        dev_release(m, work, s);
+        if (Bd) dev_release(m, Bd, s);
+        return fail(UE_ERR_DUAL, "ue_modes_low: the block of vectors lost rank");
+    }
+    if (B) UE_CUDA(cudaMemcpy(B, Bd, sizeof(double) * n_modes * nt, cudaMemcpyDeviceToHost));
+    dev_release(m, work, s);
+    if (Bd) dev_release(m, Bd, s);
     return UE_OK;
 }
 

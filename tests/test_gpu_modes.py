@@ -78,3 +78,39 @@ def test_modes_rejects_bad_arguments(ue):
     with pytest.raises(ue.UEError):
         m.modes(4, iters=0)
     m.close()
+
+
+def _analytic_te(a, b, count):
+    """omega of the PEC rectangle's TE(m, n) modes, pi sqrt((m/a)^2 + (n/b)^2), (m, n) != (0, 0),
+    ascending (c = 1)."""
+    w = sorted(np.pi * np.hypot(mm / a, nn / b) for mm in range(12) for nn in range(12) if mm or nn)
+    return np.array(w[:count])
+
+
+@pytest.mark.parametrize("which", ["cavity1024", "cavity4k"])
+def test_lowest_modes_match_dense_and_the_resonator(ue, which):
+    """ue_modes_low: the 10 lowest omegas equal a dense eigendecomposition to 1e-9 (omega_0 = 0,
+    the static field); the modes are S-normalised eigenvectors; and the nonzero omegas approach
+    the rectangle's TE(m, n) frequencies pi sqrt((m/a)^2 + (n/b)^2) (Fig. 4's analytic curve),
+    closer on the finer mesh."""
+    ms = meshgen.cavity_te11_mesh() if which == "cavity1024" else meshgen.cavity_lattice(65, 33, 1.0, 0.5, seed=11)
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    lam, phi = np.linalg.eigh(spectral.symmetric_K(ops))
+    dense = np.sqrt(np.clip(lam, 0.0, None))                      # ascending
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-4)
+    w, B = m.modes_low(10, iters=300, degree=24, seed=4, vectors=True)
+    m.close()
+    assert np.all(np.diff(w) >= -1e-9 * w[-1])
+    assert w[0] < 1e-4 * w[1]                                     # the static field, omega^2 ~ rounding
+    assert np.abs(w[1:] / dense[1:10] - 1).max() < 1e-9
+    S = ops.w_B
+    for i in range(10):
+        b = B[i]
+        assert abs(np.dot(S * b, b) - 1) < 1e-9
+        r = spectral.apply_K(ops, b) - w[i] ** 2 * b
+        assert np.sqrt(np.dot(S * r, r)) < 1e-5 * w[-1] ** 2
+    exact = _analytic_te(1.0, 0.5, 9)
+    err = np.abs(w[1:] / exact - 1)
+    print(f"{which}: lowest omegas {np.round(w[1:6], 4)}, analytic {np.round(exact[:5], 4)}, max rel err {err.max():.2e}")
+    assert err.max() < (0.01 if which == "cavity1024" else 0.003)

@@ -260,6 +260,8 @@ def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, threads, plasma,
     # the fused kernel runs vacuum media with 512 threads; plasma and 1024 threads run the split
     # forms (1: one CTA per tile, 2: records in shared memory, 3: pipelined)
     expect = {4} if (kernel == "fused" and not plasma and threads != 1024) else {1, 2, 3}
+    if tile == 64:
+        expect &= {3, 4}     # more tiles than SMs: the pipelined form (plasma included) or the fused one
     for gc in (0, -1):
         (Eb, Bb, Jb), sb = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k,
                                         graph_chunk=gc, threads=threads, kernel=tbk,
