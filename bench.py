@@ -326,7 +326,7 @@ def run_native(args):
     ms, ids, amp, w0, t0, tau, dens, nu, what = load_workload(args.workload)
     stream = torch.cuda.current_stream()
     blocked = args.variant == "blocked"
-    tiled = ue.UE_REORDER_GREEDY if args.tiler == "greedy" else ue.UE_REORDER_KD
+    tiled = {"greedy": ue.UE_REORDER_GREEDY, "rings": ue.UE_REORDER_GREEDY_RINGS, "kd": ue.UE_REORDER_KD}[args.tiler]
     m = ue.Mesh(ms.xy, ms.tris, reorder=tiled if blocked else ue.UE_REORDER_RCM,
                 tile_tris=args.tile_tris)
     if args.frame > 0:
@@ -463,7 +463,11 @@ def run_native(args):
                        "variant": (f"blocked k={args.block_depth} {args.tiler} tiles<={args.tile_tris} "
                                 f"threads={args.tb_threads or 512} {args.tb_kernel} kernel" if blocked
                                 else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
-                       "l2": f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush",
+                       "l2": (f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush"
+                              if step_bytes > L2_BYTES else
+                              f"working set {step_bytes / 1e6:.0f} MB per step < {L2_BYTES / 1e6:.0f} MB L2: "
+                              "no flush between steps, so the steps run largely from L2, as every step of a "
+                              "long run of this mesh does"),
                        "parallelism": f"replicas x{world}",
                        "tiles": part_stats,
                        "pml_frame": frame},
@@ -641,7 +645,7 @@ def run_learned(args):
     b.build()
     import paper_1812_01448_gb300 as ue
     from paper_1812_01448_gb300 import learned
-    p = learned.load_weights()
+    p = learned.load_weights(args.weights) if args.weights else learned.load_weights()
     # first launches of each path (module load) outside the measurement
     for mode in (ue.UE_DT_POWER, ue.UE_DT_LEARNED):
         w = ue.Mesh(meshes[0].xy, meshes[0].tris)
@@ -832,8 +836,9 @@ def main(argv=None):
     ap.add_argument("--frame", type=int, default=0,
                     help="scatterer workload: PML frame of this many cells (open boundary instead "
                          "of the PEC walls)")
-    ap.add_argument("--tiler", choices=["kd", "greedy"], default="greedy",
-                    help="blocked variant: KD or greedy partition into tiles")
+    ap.add_argument("--tiler", choices=["kd", "greedy", "rings"], default="greedy",
+                    help="blocked variant: KD or greedy partition into tiles; rings: the greedy tiles "
+                         "with each tile's boundary rings stored first, by angle")
     ap.add_argument("--block-depth", type=int, default=8)
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
@@ -850,6 +855,7 @@ def main(argv=None):
     ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)
     ap.add_argument("--learned-max", type=int, default=1_000_000)
+    ap.add_argument("--weights", default="", help="learned workload: a weight file other than the shipped one")
     ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--tune-sample", type=int, default=32)
     ap.add_argument("--quick-setup", action="store_true",

@@ -49,6 +49,11 @@ extern "C" {
 #define UE_REORDER_GREEDY 3      /* greedy tiles of <= tile_tris triangles, grown breadth     */
                                  /* first from the sharpest boundary triangle, small parts    */
                                  /* and hanging triangles joined; RCM order inside            */
+#define UE_REORDER_GREEDY_RINGS 4 /* the same tiles; inside each, the triangles within 15     */
+                                 /* rings of its boundary first, ring by ring, each ring by   */
+                                 /* angle around the tile's centroid (then RCM order), so a   */
+                                 /* neighbour's halo is a few runs of stored ids: the blocked */
+                                 /* kernel's layout (tiles as in the greedy method)           */
 
 #define UE_PREC_FP32 0           /* FP32 fields and coefficients (product)                    */
 #define UE_PREC_FP64 1           /* FP64 fields and coefficients (check build)                */

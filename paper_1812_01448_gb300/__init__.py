@@ -9,7 +9,8 @@ does, and fails loudly if the library was not built.
 """
 from ._native import (UE_DT_GIVEN, UE_DT_LEARNED, UE_DT_POWER, UE_PREC_FP32,  # noqa: F401
                       UE_PREC_FP64, UE_RHO_LEARNED, UE_RHO_POWER, UE_RHO_POWER_FALLBACK,
-                      UE_REORDER_GREEDY, UE_REORDER_KD, UE_REORDER_NONE, UE_REORDER_RCM, UE_VARIANT_BLOCKED,
+                      UE_REORDER_GREEDY, UE_REORDER_GREEDY_RINGS, UE_REORDER_KD, UE_REORDER_NONE,
+                      UE_REORDER_RCM, UE_VARIANT_BLOCKED,
                       UE_TB_FUSED, UE_TB_SPLIT, UE_VARIANT_PERSISTENT, UE_VARIANT_PLAIN, UEError)
 from .api import (Mesh, adam, batch_create, mesh_flip, mesh_relax, mlp_backward, mlp_forward, options,  # noqa: F401
                   power_iteration_static, rho_loss, seg_argmax, triangulate)

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(_HERE, "libue.so")
 UE_OK = 0
 UE_ERR = {-1: "UE_ERR_ARG", -2: "UE_ERR_NONMANIFOLD", -3: "UE_ERR_DEGENERATE", -4: "UE_ERR_DUAL",
           -5: "UE_ERR_CUDA", -6: "UE_ERR_ALLOC", -7: "UE_ERR_UNSTABLE", -8: "UE_ERR_TIMEOUT"}
-UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD, UE_REORDER_GREEDY = 0, 1, 2, 3
+UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD, UE_REORDER_GREEDY, UE_REORDER_GREEDY_RINGS = 0, 1, 2, 3, 4
 UE_PREC_FP32, UE_PREC_FP64 = 0, 1
 UE_DT_GIVEN, UE_DT_POWER, UE_DT_LEARNED = 0, 1, 2
 UE_RHO_GIVEN, UE_RHO_POWER, UE_RHO_LEARNED, UE_RHO_POWER_FALLBACK = 0, 1, 2, 3

@@ -278,6 +278,92 @@ struct PosSet {
     }
 };
 
+// Inside each tile, the triangles within kRingCap rings of the tile's boundary (the triangles
+// with an edge-neighbour in another tile are ring 0) come first, ring by ring, each ring in
+// order of the angle of its centroids around the tile's centroid; deeper triangles keep their
+// order.  A neighbouring tile's halo holds the rings next to their shared boundary: an arc of
+// each ring, which this order stores as one run, so the blocked kernel gathers it from few
+// 32-byte sectors instead of one per value.  The tiles themselves (their sets and offsets) do
+// not change.
+constexpr int kRingCap = 15;
+
+void ring_order_in_tiles(const Canon& c, const double* xy, int64_t nt, std::vector<int64_t>& order,
+                         const std::vector<int64_t>& tile_off) {
+    std::vector<int64_t> ptr(nt + 1, 0);
+    const int64_t ne = (int64_t)c.R.size();
+    for (int64_t e = 0; e < ne; ++e)
+        if (c.R[e] >= 0 && c.L[e] >= 0) {
+            ++ptr[c.R[e] + 1];
+            ++ptr[c.L[e] + 1];
+        }
+    for (int64_t j = 0; j < nt; ++j) ptr[j + 1] += ptr[j];
+    std::vector<int64_t> adj(ptr[nt]);
+    {
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            if (c.R[e] >= 0 && c.L[e] >= 0) {
+                adj[fill[c.R[e]]++] = c.L[e];
+                adj[fill[c.L[e]]++] = c.R[e];
+            }
+    }
+    const int64_t ntiles = (int64_t)tile_off.size() - 1;
+    std::vector<int64_t> tile_of(nt);
+    for (int64_t t = 0; t < ntiles; ++t)
+        for (int64_t i = tile_off[t]; i < tile_off[t + 1]; ++i) tile_of[order[i]] = t;
+    std::vector<int32_t> ring(nt, kRingCap);
+    std::vector<double> cx(nt), cy(nt), ang(nt);
+    for (int64_t j = 0; j < nt; ++j) {
+        double x = 0.0, y = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            x += xy[2 * c.tri[3 * j + q]];
+            y += xy[2 * c.tri[3 * j + q] + 1];
+        }
+        cx[j] = x / 3.0;
+        cy[j] = y / 3.0;
+    }
+    std::vector<int64_t> queue, pos_in_tile(nt);
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t a = tile_off[t], b = tile_off[t + 1];
+        double mx = 0.0, my = 0.0;
+        queue.clear();
+        for (int64_t i = a; i < b; ++i) {
+            const int64_t j = order[i];
+            pos_in_tile[j] = i;
+            mx += cx[j];
+            my += cy[j];
+            for (int64_t p = ptr[j]; p < ptr[j + 1]; ++p)
+                if (tile_of[adj[p]] != t) {
+                    ring[j] = 0;
+                    queue.push_back(j);
+                    break;
+                }
+        }
+        mx /= (double)(b - a);
+        my /= (double)(b - a);
+        for (size_t h = 0; h < queue.size(); ++h) {   // breadth first inside the tile
+            const int64_t j = queue[h];
+            if (ring[j] + 1 >= kRingCap) continue;
+            for (int64_t p = ptr[j]; p < ptr[j + 1]; ++p) {
+                const int64_t o = adj[p];
+                if (tile_of[o] == t && ring[o] > ring[j] + 1) {
+                    ring[o] = ring[j] + 1;
+                    queue.push_back(o);
+                }
+            }
+        }
+        for (int64_t i = a; i < b; ++i) {
+            const int64_t j = order[i];
+            ang[j] = std::atan2(cy[j] - my, cx[j] - mx);
+        }
+        std::stable_sort(order.begin() + a, order.begin() + b, [&](int64_t u, int64_t v) {
+            if (ring[u] != ring[v]) return ring[u] < ring[v];
+            if (ring[u] == kRingCap) return pos_in_tile[u] < pos_in_tile[v];
+            if (ang[u] != ang[v]) return ang[u] < ang[v];
+            return pos_in_tile[u] < pos_in_tile[v];
+        });
+    }
+}
+
 void greedy_order(const Canon& c, int64_t nt, const std::vector<int64_t>& rcm_order, int64_t tile_tris,
                   std::vector<int64_t>& order, std::vector<int64_t>& tile_off) {
     const int64_t theta = tile_tris / 8, target = tile_tris - theta;
@@ -434,7 +520,7 @@ int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int6
     hm.tile_tri_off.clear();
     if (reorder == UE_REORDER_RCM) {
         hm.perm_tri = rcm(c, n_tris);
-    } else if (reorder == UE_REORDER_KD || reorder == UE_REORDER_GREEDY) {
+    } else if (reorder == UE_REORDER_KD || reorder == UE_REORDER_GREEDY || reorder == UE_REORDER_GREEDY_RINGS) {
         if (tile_tris < 16) {
             err = "tile_tris must be >= 16";
             return UE_ERR_ARG;
@@ -442,6 +528,7 @@ int build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tris, int6
         std::vector<int64_t> r = rcm(c, n_tris);
         if (reorder == UE_REORDER_KD) kd_order(c, xy, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
         else greedy_order(c, n_tris, r, tile_tris, hm.perm_tri, hm.tile_tri_off);
+        if (reorder == UE_REORDER_GREEDY_RINGS) ring_order_in_tiles(c, xy, n_tris, hm.perm_tri, hm.tile_tri_off);
     } else {
         hm.perm_tri.resize(n_tris);
         std::iota(hm.perm_tri.begin(), hm.perm_tri.end(), 0);

@@ -1056,7 +1056,7 @@ int ue_mesh_load(const double* xy, int64_t n_nodes, const int32_t* tris, int64_t
     ue_options_default(&d);
     const ue_options& o = opt ? *opt : d;
     if (o.reorder != UE_REORDER_NONE && o.reorder != UE_REORDER_RCM && o.reorder != UE_REORDER_KD &&
-        o.reorder != UE_REORDER_GREEDY)
+        o.reorder != UE_REORDER_GREEDY && o.reorder != UE_REORDER_GREEDY_RINGS)
         return fail(UE_ERR_ARG, "unknown reorder option");
     ue_mesh* m = new (std::nothrow) ue_mesh();
     if (!m) return fail(UE_ERR_ARG, "out of host memory");
@@ -1173,7 +1173,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
         return fail(UE_ERR_ARG, "the persistent variant is FP32 only and needs timeout_ms >= 1");
     if (o.variant == UE_VARIANT_BLOCKED) {
         if (o.precision != UE_PREC_FP32) return fail(UE_ERR_ARG, "the blocked variant is FP32 only");
-        if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs tiles (UE_REORDER_KD or UE_REORDER_GREEDY)");
+        if (m->hm.tile_tri_off.size() < 2) return fail(UE_ERR_ARG, "the blocked variant needs tiles (UE_REORDER_KD, UE_REORDER_GREEDY or UE_REORDER_GREEDY_RINGS)");
         if (o.block_depth < 1 || o.block_depth > 15) return fail(UE_ERR_ARG, "block_depth must be in 1..15");
         if (o.tb_threads != 0 && o.tb_threads != 512 && o.tb_threads != 1024)
             return fail(UE_ERR_ARG, "tb_threads must be 0, 512 or 1024");

@@ -102,17 +102,25 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--seed", type=int, default=1005)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--workers", type=int, default=0, help="mesh generator processes (0: all cores)")
     a = ap.parse_args(argv)
+    import time
+    t0 = time.perf_counter()
     specs = meshgen.learned_specs(a.meshes, seed=a.seed)
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        meshes = pool.map(meshgen.learned_mesh, specs, chunksize=4)
-    import torch
-    torch.cuda.set_device(0)
-    corpus = build_corpus(meshes)
+    # the pool is started (spawn) before the first GPU call; the meshes stream from it into
+    # the corpus, which keeps only their features on the device
+    workers = a.workers or min(32, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        import torch
+        torch.cuda.set_device(0)
+        corpus = build_corpus(pool.imap(meshgen.learned_mesh, specs, chunksize=4))
+    t1 = time.perf_counter()
     p, hist = train(corpus, epochs=a.epochs, seed=a.seed)
+    t2 = time.perf_counter()
     np.save(a.out, p)
-    print(f"trained on {len(meshes)} meshes, {corpus['X'].shape[0]} triangles; "
-          f"loss {hist[0]:.4g} -> {hist[-1]:.4g}; rms log error {math.sqrt(hist[-1]):.4f}")
+    print(f"trained on {a.meshes} meshes, {corpus['X'].shape[0]} triangles; "
+          f"loss {hist[0]:.4g} -> {hist[-1]:.4g}; rms log error {math.sqrt(hist[-1]):.4f}; "
+          f"corpus {t1 - t0:.0f} s ({workers} generator processes), training {t2 - t1:.0f} s")
 
 
 if __name__ == "__main__":

@@ -94,6 +94,58 @@ def test_greedy_tiles_bit_exact_against_oracle(ue, tile):
         m.close()
 
 
+@pytest.mark.parametrize("tile", [40, 300])
+def test_ring_ordered_tiles_follow_their_rule(ue, tile):
+    """UE_REORDER_GREEDY_RINGS: the greedy tiles of the oracle (offsets and sets); inside each
+    tile the ring index (0: a neighbour in another tile; breadth first inside the tile, capped
+    at 15) never decreases; within a ring below the cap the angle of the centroids around the
+    tile's mean centroid never decreases; the triangles at the cap keep the greedy order."""
+    for name, ms in _meshes():
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY_RINGS, tile_tris=tile)
+        perm, offs = m.tables()["perm_tri"], m.tiles()
+        m.close()
+        om_ = om.canonicalize(ms.xy, ms.tris)
+        order, ref_offs = rcm.greedy_order(om_, rcm.rcm_order(om_), tile)
+        assert np.array_equal(offs, ref_offs), name
+        tile_of = np.empty(ms.n_tris, np.int64)
+        rank = np.empty(ms.n_tris, np.int64)
+        rank[order] = np.arange(ms.n_tris)
+        for t in range(offs.size - 1):
+            a, b = offs[t], offs[t + 1]
+            assert set(perm[a:b].tolist()) == set(order[a:b].tolist()), (name, t)
+            tile_of[perm[a:b]] = t
+        nbrs = [[] for _ in range(ms.n_tris)]
+        for R, L in zip(om_.R, om_.L):
+            if R >= 0 and L >= 0:
+                nbrs[R].append(L)
+                nbrs[L].append(R)
+        cen = ms.xy[om_.tris].mean(axis=1)
+        for t in range(offs.size - 1):
+            mem = perm[offs[t]:offs[t + 1]]
+            ring = {j: 15 for j in mem.tolist()}
+            frontier = [j for j in mem.tolist() if any(tile_of[o] != t for o in nbrs[j])]
+            for j in frontier:
+                ring[j] = 0
+            for r in range(1, 15):
+                nxt = []
+                for j in frontier:
+                    for o in nbrs[j]:
+                        if tile_of[o] == t and ring[o] == 15:
+                            ring[o] = r
+                            nxt.append(o)
+                frontier = nxt
+            rr = np.array([ring[j] for j in mem.tolist()])
+            assert np.all(np.diff(rr) >= 0), (name, t)
+            c = cen[mem].mean(axis=0)
+            ang = np.arctan2(cen[mem, 1] - c[1], cen[mem, 0] - c[0])
+            for r in np.unique(rr):
+                sel = rr == r
+                if r < 15:
+                    assert np.all(np.diff(ang[sel]) >= -1e-9), (name, t, r)
+                else:
+                    assert np.all(np.diff(rank[mem[sel]]) > 0), (name, t)
+
+
 @pytest.mark.parametrize("reorder", [0, 1, 2, 3])
 def test_unused_nodes_keep_tables_bit_exact(ue, reorder):
     # nodes that no triangle uses, before and after the used ones: they shift the caller ids

@@ -274,21 +274,24 @@ def test_blocked_is_bit_identical_to_plain(ue, tile, k, nsteps, threads, plasma,
 
 @pytest.mark.parametrize("tile,k,nsteps", [(64, 5, 31), (1024, 8, 40), (300, 3, 13)])
 @pytest.mark.parametrize("kernel", ["split", "fused"])
-def test_blocked_on_greedy_tiles_is_bit_identical_to_plain(ue, tile, k, nsteps, kernel):
+@pytest.mark.parametrize("tiler", ["greedy", "rings"])
+def test_blocked_on_greedy_tiles_is_bit_identical_to_plain(ue, tile, k, nsteps, kernel, tiler):
     """Greedy tiles (connected parts of any size up to the cap, small parts and hanging
-    triangles joined) feed the same blocked kernel; it must reproduce the plain step on the
-    same stored order bit for bit, with plasma, source and current."""
+    triangles joined), also with each tile's boundary rings stored first (rings), feed the
+    same blocked kernel; it must reproduce the plain step on the same stored order bit for
+    bit, with plasma, source and current."""
     ms, ops, w0, dens, ids, amp = _plasma_case()
     rho, _ = spectral.power_iteration(ops, 50)
     dt = 0.45 / rho
+    reorder = ue.UE_REORDER_GREEDY if tiler == "greedy" else ue.UE_REORDER_GREEDY_RINGS
     kw = dict(dens=dens, nu=0.01 * w0, src=(ids, amp, w0, 0.0, 0.05),
-              B0=np.sin(7 * ms.xy[ms.tris].mean(axis=1)[:, 0]), reorder=ue.UE_REORDER_GREEDY)
+              B0=np.sin(7 * ms.xy[ms.tris].mean(axis=1)[:, 0]), reorder=reorder)
     (Ep, Bp, Jp), sp = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
     (Eb, Bb, Jb), sb = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k, **kw)
     assert sp == sb == nsteps
     assert np.array_equal(Ep, Eb) and np.array_equal(Bp, Bb) and np.array_equal(Jp, Jb)
     kw.pop("dens")
-    kw["reorder"] = ue.UE_REORDER_GREEDY
+    kw["reorder"] = reorder
     tbk = ue.UE_TB_FUSED if kernel == "fused" else ue.UE_TB_SPLIT
     (Ep, Bp, _), _ = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_PLAIN, tile, k, **kw)
     (Eb, Bb, _), _ = _run_variant(ue, ms, dt, nsteps, ue.UE_VARIANT_BLOCKED, tile, k, kernel=tbk,

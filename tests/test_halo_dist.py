@@ -149,3 +149,30 @@ def test_two_gloo_ranks_match_the_single_rank_run_bit_for_bit():
     assert np.array_equal(Es, ops.extend(st.E)) and np.array_equal(js, ops.extend(st.j))
     # a stable run (dt rho ~ 0.9 < 2) with fields of order one
     assert 0 < np.abs(st.B).max() < 100 and 0 < np.abs(st.E).max() < 100
+
+
+def test_parts_in_one_process_match_and_a_skipped_exchange_breaks_it():
+    """The same two parts stepped in one process (halo.run with exchange_local) equal the
+    single-rank oracle run bit for bit; with the exchange left out (a planted mistake) the
+    rings go stale and the stitched B differs."""
+    sys.path.insert(0, ROOT)
+    from oracle import leapfrog as lf, mesh as om, operators
+    from paper_1812_01448_gb300 import halo
+    ms, plan, ids, amp, w0, dens = _case()
+    E, B, j = _initial(ms, plan)
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    st = lf.initial_state(ops, E_all=E, B=B, j_all=j)
+    st = lf.run(ops, st, 1.0 / 2200.0, 20, plasma=lf.Plasma(dens, 0.01 * w0),
+                source=lf.Source(ids, amp, w0, 0.1, 0.05))
+
+    def stitched(exchange):
+        parts = [OraclePart(plan, p, 1.0 / 2200.0, E, B, j, ids, amp, w0, dens) for p in range(2)]
+        halo.run(parts, plan, 20, exchange=exchange)
+        Bs = np.full(ms.tris.shape[0], np.nan)
+        for p, e in enumerate(parts):
+            Bs[plan.tris_global[p][plan.owned[p]]] = e.st.B[plan.owned[p]]
+        return Bs
+
+    assert np.array_equal(stitched(halo.exchange_local), st.B)
+    stale = stitched(lambda engines, plan: None)
+    assert not np.array_equal(stale, st.B)
