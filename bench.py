@@ -3,8 +3,9 @@
 One bench "step" is one full leap-frog step (E half-step over every interior edge, the line
 source, B half-step over every triangle) of the graded unit-square mesh with an equilateral
 PEC hole (h 2e-4 .. 8e-4, ~4M triangles, FP32 fields, FP64-built coefficients).  By default
-the steps run temporally blocked: greedy tiles of <= 2500 triangles (--tiler kd: KD tiles),
-8 steps per launch, 512 threads per tile (--variant plain: two kernels per step in RCM order).
+the steps run temporally blocked: greedy tiles of <= 2500 triangles with each tile's boundary
+rings stored first (--tiler greedy: the greedy method's own order; --tiler kd: KD tiles), 8
+steps per launch, 512 threads per tile (--variant plain: two kernels per step in RCM order).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -836,7 +837,7 @@ def main(argv=None):
     ap.add_argument("--frame", type=int, default=0,
                     help="scatterer workload: PML frame of this many cells (open boundary instead "
                          "of the PEC walls)")
-    ap.add_argument("--tiler", choices=["kd", "greedy", "rings"], default="greedy",
+    ap.add_argument("--tiler", choices=["kd", "greedy", "rings"], default="rings",
                     help="blocked variant: KD or greedy partition into tiles; rings: the greedy tiles "
                          "with each tile's boundary rings stored first, by angle")
     ap.add_argument("--block-depth", type=int, default=8)

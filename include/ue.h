@@ -81,7 +81,9 @@ extern "C" {
 typedef struct ue_mesh ue_mesh;  /* opaque, owned by the library until ue_mesh_free        */
 
 /* Device allocator hooks: alloc(bytes, stream, ctx) returns a device pointer or NULL;
- * free(ptr, stream, ctx) releases it.  Both NULL = cudaMalloc / cudaFree. */
+ * free(ptr, stream, ctx) releases it.  Both NULL = cudaMalloc / cudaFree.  Pointers must be
+ * 16-byte aligned (the blocked kernels move records and fields with TMA bulk copies): one that
+ * is not is handed back to free and the call fails with UE_ERR_ALLOC. */
 typedef void* (*ue_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*ue_free_fn)(void* ptr, void* stream, void* ctx);
 

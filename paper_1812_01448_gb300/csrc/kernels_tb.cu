@@ -22,8 +22,7 @@ constexpr int kNT = 512;
 struct TBArgs {
     const int* hdr;
     const int4* trec;
-    const int* erec;    // 3 ints per local edge record: gid, lo | hi << 16 | (R > L) << 31 (the
-                        // slots of its triangles in increasing order), bits of cU (sign: source)
+    const int* erec;    // 3 ints per local edge record: gid, R | L << 16, bits of cU (sign: source)
     const float* epb;   // plasma coefficient per local edge record
     const int2* tsrc;
     const float* Bin;
@@ -46,13 +45,6 @@ struct TBArgs {
                         // 16 bytes more than it delivers, so that the wait for it runs out
 };
 
-// An edge record's slot pair (lo | hi << 16) and its coefficient for B_lo - B_hi: dt|e|/d where
-// R is the lower slot, its negation where R is the higher one (bit 31 of the pair word).
-__device__ __forceinline__ int rec_pair(int w) { return w & 0x7FFFFFFF; }
-__device__ __forceinline__ float rec_coef(int w, int cu_bits) {
-    const float c = fabsf(__int_as_float(cu_bits));
-    return w < 0 ? -c : c;
-}
 
 // NT threads; each thread owns local triangle slots tid + i*NT (i < TS) and local edge slots
 // tid + i*NT (i < ES), whose records it keeps in registers for all k steps.  In every phase a
@@ -92,9 +84,9 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
     for (int i = 0; i < ES; ++i) {
         const int l = tid + i * NT;
         if (l < nel) {
-            const int gid = __ldg(er + 3 * l), w = __ldg(er + 3 * l + 1);
-            erl[i] = rec_pair(w);
-            ecu[i] = rec_coef(w, __ldg(er + 3 * l + 2));
+            const int gid = __ldg(er + 3 * l);
+            erl[i] = __ldg(er + 3 * l + 1);
+            ecu[i] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
             Ul[l] = __ldg(a.Uin + gid);
             if constexpr (PLASMA) {
                 epb[i] = __ldg(a.epb + h[7] + l);
@@ -114,13 +106,13 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
         const int eend = h[32 + lim];
 #pragma unroll
         for (int g0 = 0; g0 < ES; g0 += kG) {
-            float blo[kG], bhi[kG], uo[kG], jo[kG];
+            float bR[kG], bL[kG], uo[kG], jo[kG];
 #pragma unroll
             for (int q = 0; q < kG; ++q) {
                 const int i = g0 + q, l = tid + i * NT;
                 if (i < ES && l < eend) {
-                    blo[q] = Bl[erl[i] & 0xFFFF];
-                    bhi[q] = Bl[(unsigned)erl[i] >> 16];
+                    bR[q] = Bl[erl[i] & 0xFFFF];
+                    bL[q] = Bl[(unsigned)erl[i] >> 16];
                     uo[q] = Ul[l];
                     if constexpr (PLASMA) jo[q] = Jl[l];
                 }
@@ -129,7 +121,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tb(TBArgs a) {
             for (int q = 0; q < kG; ++q) {
                 const int i = g0 + q, l = tid + i * NT;
                 if (i < ES && l < eend) {
-                    float un = rn_fma(ecu[i], rn_sub(blo[q], bhi[q]), uo[q]);
+                    float un = rn_fma(ecu[i], rn_sub(bR[q], bL[q]), uo[q]);
                     if constexpr (PLASMA) {
                         const float jn = rn_fma(a.pa, jo[q], rn_mul(epb[i], uo[q]));
                         Jl[l] = jn;
@@ -238,9 +230,9 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
         Bl[l] = __ldg(a.Bin + r.x);
     }
     for (int l = tid; l < nel; l += NT) {
-        const int gid = __ldg(er + 3 * l), w = __ldg(er + 3 * l + 1);
-        Erl[l] = rec_pair(w);
-        Ecu[l] = rec_coef(w, __ldg(er + 3 * l + 2));
+        const int gid = __ldg(er + 3 * l);
+        Erl[l] = __ldg(er + 3 * l + 1);
+        Ecu[l] = fabsf(__int_as_float(__ldg(er + 3 * l + 2)));
         Ul[l] = __ldg(a.Uin + gid);
         if constexpr (PLASMA) {
             Epb[l] = __ldg(a.epb + h[7] + l);
@@ -514,9 +506,16 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
         for (int i = 0; i < ES; ++i) {
             const int l = tid + i * NT;
             if (l < ne) {
-                const int cub = estage[3 * l + 2], w = estage[3 * l + 1];
-                erl[i] = (unsigned)rec_pair(w) << 2;
-                ecu[i] = rec_coef(w, cub);
+                // the edge's triangles in slot order (lo, hi): one gather of a warp then reads
+                // the lower-numbered triangles of 32 consecutive edges and the other the higher
+                // ones, two narrow windows of slots with fewer bank conflicts than R and L,
+                // which mix both; where R is the higher slot the coefficient changes sign,
+                // since rn(B_lo - B_hi) = -rn(B_R - B_L) exactly
+                const int cub = estage[3 * l + 2];
+                const unsigned w = (unsigned)estage[3 * l + 1], R = w & 0xFFFFu, L = w >> 16;
+                erl[i] = (R < L ? (R | (L << 16)) : (L | (R << 16))) << 2;
+                const float c = fabsf(__int_as_float(cub));
+                ecu[i] = R > L ? -c : c;
                 if constexpr (SRC) srcm |= (cub < 0 ? 1u : 0u) << i;
                 eu[i] = Fc[Lay::UOFF + l];
                 if constexpr (PLASMA) {

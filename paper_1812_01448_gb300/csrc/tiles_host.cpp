@@ -96,8 +96,8 @@ int build_tiles(const HostMesh& hm, int k_max, TileSet& ts, std::string& err,
         });
         for (size_t l = 0; l < edges.size(); ++l) eloc[edges[l]] = (int32_t)l;
         const int64_t ntl = (int64_t)tris.size(), nel = (int64_t)edges.size();
-        if (nel >= 32767 || ntl >= 32767) {
-            err = "a tile with its halo exceeds 32766 triangles or 32766 edges: lower tile_tris or block_depth";
+        if (nel >= 32767 || ntl >= 65535) {
+            err = "a tile with its halo exceeds 65535 triangles or 32767 edges: lower tile_tris or block_depth";
             for (int64_t j : tris) lvl[j] = loc[j] = -1;
             for (int64_t k : edges) elvl[k] = eloc[k] = -1;
             return UE_ERR_ARG;

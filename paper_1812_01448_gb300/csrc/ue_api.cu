@@ -155,6 +155,10 @@ void* dev_alloc(ue_mesh* m, size_t bytes, cudaStream_t s) {
     void* p = nullptr;
     if (m->alloc) {
         p = m->alloc(bytes, (void*)s, m->alloc_ctx);
+        if (p && ((uintptr_t)p & 15u) != 0) {   // TMA bulk copies need 16-byte alignment
+            if (m->free_fn) m->free_fn(p, (void*)s, m->alloc_ctx);
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
@@ -702,18 +706,12 @@ int upload_tileset(ue_mesh* m, cudaStream_t s) {
     tb.max_tri_loc = ts.max_tri_loc;
     tb.max_edge_loc = ts.max_edge_loc;
     tb.threads = m->tb_threads;
-    // edge records go to the device as 3 ints {gid, lo | hi << 16 | (R > L) << 31, cU}: the
-    // local slots of the edge's two triangles in increasing order, so that one gather of a warp
-    // reads the lower-numbered triangles of 32 consecutive edges and the other the higher ones
-    // (two narrow windows of slots, fewer shared-memory bank conflicts than R and L, which mix
-    // both), with bit 31 set where R is the higher slot (the kernels negate the coefficient
-    // there: rn(B_lo - B_hi) = -rn(B_R - B_L) exactly).  The coefficient is filled by
-    // launch_tb_fill, the plasma coefficient kept apart (tb.epb).
+    // edge records go to the device as 3 ints {gid, R | L << 16, cU}: the coefficient is filled
+    // by launch_tb_fill, the plasma coefficient kept apart (tb.epb)
     std::vector<int32_t> e3(3 * (size_t)tb.n_erec);
     for (int64_t i = 0; i < tb.n_erec; ++i) {
-        const uint32_t w = (uint32_t)ts.erec[4 * i + 1], R = w & 0xFFFFu, L = w >> 16;
         e3[3 * i] = ts.erec[4 * i];
-        e3[3 * i + 1] = (int32_t)(R <= L ? (R | (L << 16)) : (L | (R << 16) | 0x80000000u));
+        e3[3 * i + 1] = ts.erec[4 * i + 1];
         e3[3 * i + 2] = 0;
     }
     bool ok = alloc_into(m, tb.hdr, ts.hdr.size(), 4, s) && alloc_into(m, tb.trec, tb.n_trec + 1, 16, s) &&

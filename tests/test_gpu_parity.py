@@ -189,13 +189,13 @@ def test_non_delaunay_mesh_is_rejected(ue):
 @pytest.mark.parametrize("variant", ["plain", "blocked", "blocked-fused"])
 def test_full_size_scatterer_window(ue, scatterer_window, variant):
     """Full size in the bench's launch configurations (plain: RCM, graphs of 32 steps;
-    blocked: greedy tiles of <= 2500, k = 8, 512 threads, split or fused kernel) against the
+    blocked: ring-ordered greedy tiles of <= 2500, k = 8, 512 threads, split or fused kernel) against the
     oracle on the whole mesh: relative L2 of each field, and per element the largest error
     against the field's largest value (an error confined to a few elements, such as the source
     edges or the hole's ring, would not move the L2 norm over 6M edges)."""
     ms, ops, ids, amp, w0, dt, Eo, Bo = scatterer_window
     blocked = variant != "plain"
-    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY if blocked else ue.UE_REORDER_RCM,
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY_RINGS if blocked else ue.UE_REORDER_RCM,
                 tile_tris=2500)
     m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt,
                      variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
