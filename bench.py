@@ -87,11 +87,22 @@ def onchip_roofline(c: dict, ms_per_launch: float, sm_mhz) -> dict:
     t = ms_per_launch * 1e-3
     wf, ins = float(c["smem_wavefronts"]), float(c["warp_instructions"])
     ideal = float(c["smem_instructions"])
+    smem = {"achieved": wf / t, "peak": sms * hz, "unit": "wavefronts/s", "frac": wf / t / (sms * hz),
+            "wavefronts_per_launch": wf}
+    ld, st, misc = (c.get(k) for k in ("pipe_lsu_wavefronts_mem_shared_op_ld", "pipe_lsu_wavefronts_mem_shared_op_st",
+                                       "pipe_lsu_wavefronts_mem_shared_op_misc"))
+    if ld is not None and st is not None:
+        # loads and stores against one wavefront per instruction (no bank conflict); the rest of
+        # the wavefronts are the cp.async gathers' shared-memory writes (LDGSTS, "misc")
+        smem.update({"load_store_wavefronts": ld + st, "load_store_instructions": ideal,
+                     "bank_conflict_factor": (ld + st) / ideal if ideal else None,
+                     "cp_async_wavefronts": misc})
+    else:
+        smem.update({"conflict_free_wavefronts_per_launch": ideal,
+                     "bank_conflict_factor": wf / ideal if ideal else None})
     return {
         "bound": "shared-memory wavefronts",
-        "smem": {"achieved": wf / t, "peak": sms * hz, "unit": "wavefronts/s", "frac": wf / t / (sms * hz),
-                 "wavefronts_per_launch": wf, "conflict_free_wavefronts_per_launch": ideal,
-                 "bank_conflict_factor": wf / ideal if ideal else None},
+        "smem": smem,
         "issue": {"achieved": ins / t, "peak": 4 * sms * hz, "unit": "warp instructions/s",
                   "frac": ins / t / (4 * sms * hz), "instructions_per_launch": ins},
         "clock_mhz": hz / 1e6, "sms": sms,
@@ -355,6 +366,27 @@ def run_native(args):
     # warm-up (also captures the step graph)
     m.step_n(args.warmup, stream)
     torch.cuda.synchronize()
+    if args.step_sweep:
+        # the cost of one ue_step_n(n) call against n (median of 5 calls, CUDA events on the
+        # launch stream): how a launch's fixed cost and its per-step cost split
+        rows = []
+        for n in [int(x) for x in args.step_sweep.split(",")]:
+            ts = []
+            for _ in range(5):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.step_n(n, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rows.append({"steps": n, "ms_per_call": float(np.median(ts)), "us_per_step": 1e3 * float(np.median(ts)) / n})
+        if rank == 0:
+            print(json.dumps({"metric": "ue_step_n call time against its step count", "workload": what,
+                              "variant": args.variant, "tiler": args.tiler, "block_depth": args.block_depth,
+                              "rows": rows}), flush=True)
+        m.close()
+        return
 
     def barrier():
         if dist is not None:
@@ -385,9 +417,13 @@ def run_native(args):
         names[2] = (f"frame region: gather, {args.block_depth} plain steps of the tiles next to the PML "
                     "frame with the frame, scatter (beside k_tbp on a second stream)")
     if blocked:
-        kname = {1: "k_tb", 2: "k_tbs", 3: "k_tbp", 4: "k_tbf", 5: "k_tbf1"}.get(m.stats()["tb_kernel_used"], "?")
-        names[0] = (f"{kname}: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, one CTA per SM "
-                    "with the next tile's loads in flight")
+        used = m.stats()["tb_kernel_used"]
+        kname = {1: "k_tb", 2: "k_tbs", 3: "k_tbp", 4: "k_tbf", 5: "k_tbf1"}.get(used, "?")
+        form = {1: "one CTA per tile", 2: "one CTA per tile, records in shared memory",
+                3: "one CTA per SM with the next tile's loads in flight",
+                4: "fused edge and triangle phases, one CTA per SM with the next tile's loads in flight",
+                5: "the whole mesh in one CTA"}.get(used, "")
+        names[0] = f"{kname}: {args.block_depth} leap-frog steps per launch on {args.tiler} tiles, {form}"
     k = int(np.argmax(prof_ms))
     peak, peak_kind = _peaks()
     achieved = prof_bytes[k] / (prof_ms[k] * 1e-3) / 1e9
@@ -856,6 +892,9 @@ def main(argv=None):
     ap.add_argument("--n-modes", type=int, default=8)
     ap.add_argument("--learned-meshes", type=int, default=40)
     ap.add_argument("--learned-max", type=int, default=1_000_000)
+    ap.add_argument("--step-sweep", default="",
+                    help="comma-separated step counts: time one ue_step_n call of each (after the warm-up) "
+                         "and print that table instead of the bench line")
     ap.add_argument("--weights", default="", help="learned workload: a weight file other than the shipped one")
     ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--tune-sample", type=int, default=32)
