@@ -49,7 +49,8 @@ L2_BYTES = 129e6
 # sources are unchanged, else reported as null.
 COUNTER_FILE = os.path.join(ROOT, "profiles", "ncu_counters.json")
 COUNTER_SOURCES = ("paper_1812_01448_gb300/csrc/kernels_tb.cu", "paper_1812_01448_gb300/csrc/kernels_tbf.cu",
-                   "paper_1812_01448_gb300/csrc/device.cuh", "paper_1812_01448_gb300/csrc/tiles_host.cpp")
+                   "paper_1812_01448_gb300/csrc/device.cuh", "paper_1812_01448_gb300/csrc/tiles_host.cpp",
+                   "paper_1812_01448_gb300/csrc/mesh_host.cpp")
 
 
 def sources_sha1(paths=COUNTER_SOURCES) -> str:
