@@ -870,7 +870,9 @@ def main(argv=None):
                     help="seconds of each CPU baseline sample (compiled oracle on one and on all "
                          "cores, numpy oracle)")
     ap.add_argument("--variant", choices=["plain", "blocked", "persistent"], default="blocked")
-    ap.add_argument("--tile-tris", type=int, default=2500)
+    ap.add_argument("--tile-tris", type=int, default=0,
+                    help="largest tile (owned triangles); 0: 2500, and 2700 for the plasma workload, the "
+                         "fastest measured for each")
     ap.add_argument("--frame", type=int, default=0,
                     help="scatterer workload: PML frame of this many cells (open boundary instead "
                          "of the PEC walls)")
@@ -902,6 +904,8 @@ def main(argv=None):
     ap.add_argument("--quick-setup", action="store_true",
                     help="fixed dt instead of power iteration (for profiler runs)")
     args = ap.parse_args(argv)
+    if args.tile_tris <= 0:
+        args.tile_tris = 2700 if args.workload == "plasma" else 2500
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.frame > 0 and args.variant == "persistent":
