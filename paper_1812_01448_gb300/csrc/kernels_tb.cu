@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
         fence_mbar_init();
     }
     __syncthreads();
-    const long long n0 = *a.step;
+    long long n0 = 0;   // the step counter, read once the previous launch has finished
     uint32_t ph_h = 0, ph_r = 0;
     int pend_h = 0, pend_r = 0;   // bulk copies issued and not yet waited for (uniform)
     bool ok = true;
@@ -462,11 +462,19 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
             issue_records(0);
             if (tile + stride < n_tiles) issue_header(tile + stride, 1);
             if (wait_bar(&bar_r, ph_r)) {
+                // headers and records are static: the fields and the step counter come from the
+                // previous launch, which may still be finishing (programmatic dependent launch)
+                grid_dependency_wait();
+                n0 = *a.step;
                 issue_fields(0, F0);
                 cp_async_wait_all();
                 if (tile + stride < n_tiles) wait_bar(&bar_h, ph_h);
             }
         }
+    }
+    if (tile >= n_tiles || !ok) {
+        grid_dependency_wait();
+        n0 = *a.step;
     }
     if (!ok) tile = n_tiles;
     __syncthreads();
@@ -483,6 +491,8 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
         float* Fn = F0 + (cur ^ 1) * Lay::FB;
         const uint32_t Fcb = smem_addr(Fc);
         const bool has_next = tile + stride < n_tiles, has_next2 = tile + 2 * stride < n_tiles;
+        // this CTA's last tile: the next launch may start its static loads on SMs that free up
+        if (!has_next && tid == 0) grid_dependents_launch();
         const int slot = it % 3, slot1 = (it + 1) % 3, slot2 = (it + 2) % 3;
         const int* h = hs[slot];
         const int nt_upd = h[16 + kk - 1], ne = n_edge(h);
@@ -684,8 +694,19 @@ cudaError_t launch_tbp_t(const TBArgs& a, int n_tiles, int grid, cudaStream_t s)
     const size_t smem = TbpLayout<NT, TS, ES, PLASMA>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, s>>>(a, n_tiles);
-    return cudaGetLastError();
+    // programmatic dependent launch: this launch may begin while the previous kernel of the
+    // stream finishes its last tiles; it waits for that kernel before it reads any field
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a, n_tiles);
 }
 
 // One form with the source branch for meshes with and without a source (the branch is one
