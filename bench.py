@@ -455,8 +455,9 @@ def run_native(args):
         roof["onchip"] = onchip_roofline(crec["per_launch"], prof_ms[k], clk.summary().get("sm_mhz"))
 
     # end to end through the public API with host buffers: the fields in the product's
-    # precision (float32, ue_write_fields_f32 / ue_read_fields_f32) by default, or as doubles
-    f32 = args.e2e_fields == "f32"
+    # precision (float32, ue_write_fields_f32 / ue_read_fields_f32) by default, or as doubles;
+    # a framed mesh moves them as doubles (the float32 calls refuse it)
+    f32 = args.e2e_fields == "f32" and args.frame <= 0
     wt = torch.float32 if f32 else torch.float64
     pinned = lambda n: torch.zeros(n, dtype=wt, pin_memory=True).numpy()
     E0, B0, Eo, Bo = pinned(m.n_edges), pinned(m.n_tris), pinned(m.n_edges), pinned(m.n_tris)

@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(kThreads)
 k_edge_half(const int2* __restrict__ rl, const T* __restrict__ cU, const T* __restrict__ B,
             T* __restrict__ U, const T* __restrict__ pb, T* __restrict__ J, T pa, T mdt,
             int64_t n_pad, SrcArgs<T> src, FrameDev f, int64_t nb_mesh) {
+    // launched as a programmatic dependent of the previous kernel: wait for it, then let the
+    // next kernel's blocks take the places this grid leaves free
+    grid_dependency_wait();
+    grid_dependents_launch();
     if constexpr (FRAME) {
         if ((int64_t)blockIdx.x >= nb_mesh) {
             frame_edge_thread<T>(f, B, U, ((int64_t)blockIdx.x - nb_mesh) * kThreads + threadIdx.x);
@@ -120,6 +124,8 @@ __global__ void __launch_bounds__(kThreads)
 k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
            const T* __restrict__ U, T* __restrict__ B, int64_t n_pad, long long* __restrict__ step,
            FrameDev f, int64_t nb_mesh) {
+    grid_dependency_wait();
+    grid_dependents_launch();
     if constexpr (FRAME) {
         if ((int64_t)blockIdx.x >= nb_mesh) {
             frame_cell_thread<T>(f, U, ((int64_t)blockIdx.x - nb_mesh) * kThreads + threadIdx.x);
@@ -154,6 +160,7 @@ k_tri_half(const int4* __restrict__ tri, const double* __restrict__ cB64,
 // g(t_n) of every source group for the next `count` steps, n = *step + i.
 __global__ void k_gtab(double* __restrict__ g, const long long* __restrict__ step, int count,
                        int stride, const double* __restrict__ par, int n_grp) {
+    grid_dependents_launch();   // the next kernel waits for this one before it reads the table
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int grp = blockIdx.y;
     if (i < count && grp < n_grp)
@@ -162,10 +169,26 @@ __global__ void k_gtab(double* __restrict__ g, const long long* __restrict__ ste
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// A launch that may begin while the previous kernel of the stream finishes (programmatic
+// dependent launch); the kernel waits for that kernel before it reads anything it wrote.
+template <typename... P, typename... A>
+cudaError_t launch_dep(void (*kern)(P...), unsigned grid, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((P)args)...);
+}
 inline unsigned blocks_for_runs(int64_t n_pad) { return blocks_for((n_pad + kPer - 1) / kPer); }
 
 template <typename T, bool PLASMA>
-void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
+cudaError_t edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
     const int64_t n_pad = m.n_ei_pad;
     SrcArgs<T> src{m.src_hash, (unsigned)m.src_bits, (const T*)m.src_c, m.src_grp, m.gtab,
                    m.gtab_size, s_index};
@@ -176,34 +199,23 @@ void edge_half_p(const DevMesh& m, int s_index, cudaStream_t s) {
     const int64_t nbf = m.frame ? blocks_for(f.n_fc + f.n_if) : 0;
     const unsigned grid = (unsigned)(nb + nbf);
     const int2* rl = (const int2*)m.rl;
-    if (nbf > 0) {
-        if (m.n_src > 0)
-            k_edge_half<T, PLASMA, true, true><<<grid, kThreads, 0, s>>>(
-                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
-        else
-            k_edge_half<T, PLASMA, false, true><<<grid, kThreads, 0, s>>>(
-                rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
-    } else if (m.n_src > 0) {
-        k_edge_half<T, PLASMA, true, false><<<grid, kThreads, 0, s>>>(
-            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
-    } else {
-        k_edge_half<T, PLASMA, false, false><<<grid, kThreads, 0, s>>>(
-            rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa, mdt, n_pad, src, f, nb);
-    }
+    auto kern = nbf > 0 ? (m.n_src > 0 ? k_edge_half<T, PLASMA, true, true> : k_edge_half<T, PLASMA, false, true>)
+                        : (m.n_src > 0 ? k_edge_half<T, PLASMA, true, false> : k_edge_half<T, PLASMA, false, false>);
+    return launch_dep(kern, grid, s, rl, (const T*)m.cU, (const T*)m.B, (T*)m.U, (const T*)m.pb, (T*)m.J, pa,
+                      mdt, n_pad, src, f, nb);
 }
 
 template <typename T>
-void tri_half_t(const DevMesh& m, cudaStream_t s) {
+cudaError_t tri_half_t(const DevMesh& m, cudaStream_t s) {
     const int64_t n_pad = m.n_t_pad;
     const int64_t nb = blocks_for_runs(n_pad);
     if (m.frame) {
         const int64_t nbf = blocks_for(m.frame->n_fc);
-        k_tri_half<T, true><<<(unsigned)(nb + nbf), kThreads, 0, s>>>(
-            m.tri, (const double*)m.cB, (const T*)m.U, (T*)m.B, n_pad, m.step, *m.frame, nb);
-    } else {
-        k_tri_half<T, false><<<(unsigned)nb, kThreads, 0, s>>>(m.tri, (const double*)m.cB, (const T*)m.U,
-                                                              (T*)m.B, n_pad, m.step, FrameDev(), nb);
+        return launch_dep(k_tri_half<T, true>, (unsigned)(nb + nbf), s, m.tri, (const double*)m.cB,
+                          (const T*)m.U, (T*)m.B, n_pad, m.step, *m.frame, nb);
     }
+    return launch_dep(k_tri_half<T, false>, (unsigned)nb, s, m.tri, (const double*)m.cB, (const T*)m.U, (T*)m.B,
+                      n_pad, m.step, FrameDev(), nb);
 }
 
 }  // namespace
@@ -217,13 +229,14 @@ cudaError_t launch_gtab(const DevMesh& m, int count, cudaStream_t s) {
 
 cudaError_t launch_step_part(const DevMesh& m, int part, int s_index, cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
+    cudaError_t e;
     if (part == 0) {
-        if (f64) m.plasma ? edge_half_p<double, true>(m, s_index, s) : edge_half_p<double, false>(m, s_index, s);
-        else m.plasma ? edge_half_p<float, true>(m, s_index, s) : edge_half_p<float, false>(m, s_index, s);
+        if (f64) e = m.plasma ? edge_half_p<double, true>(m, s_index, s) : edge_half_p<double, false>(m, s_index, s);
+        else e = m.plasma ? edge_half_p<float, true>(m, s_index, s) : edge_half_p<float, false>(m, s_index, s);
     } else {
-        f64 ? tri_half_t<double>(m, s) : tri_half_t<float>(m, s);
+        e = f64 ? tri_half_t<double>(m, s) : tri_half_t<float>(m, s);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_steps_plain(const DevMesh& m, int count, cudaStream_t s) {
