@@ -215,7 +215,7 @@ int ue_exchange_tris(ue_mesh* m, const int32_t* ids, int64_t n, void* buf, int32
 
 /* The same transfers with float arrays (the FP32 product's precision, half the bytes):
  * ue_write_fields_f32 sets U = |e| E and B from them (in FP64, rounded once to the field type),
- * ue_read_fields_f32 returns E = U / |e| and B rounded to float.  Pinned host arrays are read and
+ * ue_read_fields_f32 returns E = U * (1/|e|) and B rounded to float.  Pinned host arrays are read and
  * written in place; others go through a device copy.  Synchronous.  UE_ERR_ARG for a mesh with
  * a PML frame (use the double calls); ue_read_fields_f32 returns UE_ERR_UNSTABLE (after
  * copying) if the watchdog has flagged the run. */

@@ -261,9 +261,10 @@ size_t power_iteration_work_doubles(int64_t n_t, int64_t n_ei, const FrameDev* f
 cudaError_t launch_fields_in(const DevMesh& m, const double* E_caller, const double* B_caller,
                              const double* J_caller, const int64_t* edge_caller,
                              const int64_t* perm_tri, const double* elen, cudaStream_t s);
+// relen: 1/|e| per interior edge (launch_recip), E = U * (1/|e|)
 cudaError_t launch_fields_out(const DevMesh& m, double* E_caller, double* B_caller,
                               double* J_caller, const int64_t* edge_caller,
-                              const int64_t* perm_tri, const double* elen, cudaStream_t s);
+                              const int64_t* perm_tri, const double* relen, cudaStream_t s);
 // The same transfers in caller order, with the caller's arrays (double, or float when f32) in
 // pinned host memory at their mapped device addresses, or in device memory: k_of[n_e] = stored
 // interior edge of each caller edge or -1, inv[n_t] = stored triangle of each caller triangle.
@@ -272,8 +273,9 @@ cudaError_t launch_fields_in_caller(const DevMesh& m, const void* E_caller, cons
                                     const void* J_caller, bool f32, const int32_t* k_of, const int32_t* inv,
                                     const double* elen, int64_t n_e, cudaStream_t s);
 cudaError_t launch_fields_out_caller(const DevMesh& m, void* E_caller, void* B_caller, void* J_caller, bool f32,
-                                     const int32_t* k_of, const int32_t* inv, const double* elen, int64_t n_e,
+                                     const int32_t* k_of, const int32_t* inv, const double* relen, int64_t n_e,
                                      cudaStream_t s);
+cudaError_t launch_recip(const double* elen, double* relen, int64_t n_ei, cudaStream_t s);
 // Halo exchange of a partitioned mesh: B at caller triangle ids[0..n) to buf (scatter = 0) or
 // from buf (scatter = 1), in the field type; inv[n_t] = stored triangle of each caller one.
 // Ids outside [0, n_t) are skipped and counted in *bad (device).

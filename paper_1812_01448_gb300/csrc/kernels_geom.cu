@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 
 #include "device.cuh"
 
@@ -316,11 +318,11 @@ __global__ void k_fields_in_tris(const double* __restrict__ Bc, const int64_t* _
 
 template <typename T>
 __global__ void k_fields_out_edges(const T* __restrict__ U, const int64_t* __restrict__ ec,
-                                   const double* __restrict__ elen, double* __restrict__ Ec,
+                                   const double* __restrict__ relen, double* __restrict__ Ec,
                                    int64_t n_ei) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_ei) return;
-    Ec[ec[k]] = (double)U[k] / elen[k];
+    Ec[ec[k]] = (double)U[k] * relen[k];
 }
 
 template <typename T>
@@ -331,46 +333,122 @@ __global__ void k_fields_out_tris(const T* __restrict__ B, const int64_t* __rest
     Bc[perm[j]] = (double)B[j];
 }
 
-// Field transfer in caller order (one thread per caller element, so that the caller's side is
-// read and written in order): from or to the caller's arrays in pinned host memory through
-// their mapped device addresses, or a device copy of them.  H is the caller's element type
-// (double, or float for the FP32 calls); the arithmetic is that of the staged kernels above, in
-// FP64, rounded once to H or T.  k_of[c] = stored interior edge of caller edge c or -1; inv[c] =
-// stored triangle of caller triangle c.
+// Field transfer in caller order: from or to the caller's arrays in pinned host memory through
+// their mapped device addresses, or a device copy of them.  Each thread takes V = 16 /
+// sizeof(H) consecutive caller elements, so that the caller's side moves in 16-byte accesses
+// (when the array is 16-byte aligned; element by element otherwise) and in order.  H is the
+// caller's element type (double, or float for the FP32 calls); the arithmetic is that of the
+// staged kernels above, in FP64, rounded once to H or T.  k_of[c] = stored interior edge of
+// caller edge c or -1; inv[c] = stored triangle of caller triangle c.
+template <typename H> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename H>
+__device__ __forceinline__ void load_caller(const H* __restrict__ p, int64_t c0, int64_t n, bool vec,
+                                            H (&x)[16 / sizeof(H)]) {
+    constexpr int V = 16 / sizeof(H);
+    if (vec && c0 + V <= n) {
+        const typename Vec16<H>::type v = *reinterpret_cast<const typename Vec16<H>::type*>(p + c0);
+        memcpy(x, &v, 16);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) x[i] = c0 + i < n ? p[c0 + i] : H(0);
+    }
+}
+
+template <typename H>
+__device__ __forceinline__ void store_caller(H* __restrict__ p, int64_t c0, int64_t n, bool vec,
+                                             const H (&x)[16 / sizeof(H)]) {
+    constexpr int V = 16 / sizeof(H);
+    if (vec && c0 + V <= n) {
+        typename Vec16<H>::type v;
+        memcpy(&v, x, 16);
+        *reinterpret_cast<typename Vec16<H>::type*>(p + c0) = v;
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            if (c0 + i < n) p[c0 + i] = x[i];
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void load_ids(const int32_t* __restrict__ a, int64_t c0, int64_t n, int32_t (&k)[V]) {
+    if constexpr (V == 4) {
+        if (c0 + 4 <= n) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(a + c0));
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+            return;
+        }
+    } else {
+        if (c0 + 2 <= n) {
+            const int2 v = __ldg(reinterpret_cast<const int2*>(a + c0));
+            k[0] = v.x; k[1] = v.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) k[i] = c0 + i < n ? __ldg(a + c0 + i) : -1;
+}
+
 template <typename T, typename H>
 __global__ void k_fields_in_edges_c(const H* __restrict__ Ec, const int32_t* __restrict__ k_of,
                                     const double* __restrict__ elen, T* __restrict__ U, int64_t n_e,
-                                    int64_t n_ei) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) U[n_ei] = (T)0;
-    if (c >= n_e) return;
-    const int32_t k = k_of[c];
-    if (k >= 0) U[k] = (T)(elen[k] * (double)Ec[c]);
+                                    int64_t n_ei, bool vec) {
+    constexpr int V = 16 / sizeof(H);
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 == 0) U[n_ei] = (T)0;
+    if (c0 >= n_e) return;
+    H e[V];
+    int32_t k[V];
+    load_caller(Ec, c0, n_e, vec, e);
+    load_ids<V>(k_of, c0, n_e, k);
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+        if (k[i] >= 0) U[k[i]] = (T)(elen[k[i]] * (double)e[i]);
 }
 
 template <typename T, typename H>
 __global__ void k_fields_in_tris_c(const H* __restrict__ Bc, const int32_t* __restrict__ inv,
-                                   T* __restrict__ B, int64_t n_t) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_t) return;
-    B[inv[c]] = (T)Bc[c];
+                                   T* __restrict__ B, int64_t n_t, bool vec) {
+    constexpr int V = 16 / sizeof(H);
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 >= n_t) return;
+    H b[V];
+    int32_t j[V];
+    load_caller(Bc, c0, n_t, vec, b);
+    load_ids<V>(inv, c0, n_t, j);
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+        if (j[i] >= 0) B[j[i]] = (T)b[i];
 }
 
 template <typename T, typename H>
 __global__ void k_fields_out_edges_c(const T* __restrict__ U, const int32_t* __restrict__ k_of,
-                                     const double* __restrict__ elen, H* __restrict__ Ec, int64_t n_e) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_e) return;
-    const int32_t k = k_of[c];
-    Ec[c] = k >= 0 ? (H)((double)U[k] / elen[k]) : (H)0;
+                                     const double* __restrict__ relen, H* __restrict__ Ec, int64_t n_e, bool vec) {
+    constexpr int V = 16 / sizeof(H);
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 >= n_e) return;
+    int32_t k[V];
+    load_ids<V>(k_of, c0, n_e, k);
+    H e[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) e[i] = k[i] >= 0 ? (H)((double)U[k[i]] * relen[k[i]]) : (H)0;
+    store_caller(Ec, c0, n_e, vec, e);
 }
 
 template <typename T, typename H>
 __global__ void k_fields_out_tris_c(const T* __restrict__ B, const int32_t* __restrict__ inv,
-                                    H* __restrict__ Bc, int64_t n_t) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_t) return;
-    Bc[c] = (H)B[inv[c]];
+                                    H* __restrict__ Bc, int64_t n_t, bool vec) {
+    constexpr int V = 16 / sizeof(H);
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 >= n_t) return;
+    int32_t j[V];
+    load_ids<V>(inv, c0, n_t, j);
+    H b[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) b[i] = j[i] >= 0 ? (H)B[j[i]] : (H)0;
+    store_caller(Bc, c0, n_t, vec, b);
 }
 
 // B of the triangles with the given caller ids to / from a packed buffer (the halo exchange
@@ -454,6 +532,19 @@ __global__ void k_scatter_geom_edge(const double* __restrict__ elen, const doubl
 cudaError_t launch_geom_tri(const double* xy, const int32_t* tri_nodes, double* O, double* S,
                             int64_t n_t, cudaStream_t s) {
     k_geom_tri<<<blocks_for(n_t), kThreads, 0, s>>>(xy, tri_nodes, O, S, n_t);
+    return cudaGetLastError();
+}
+
+// 1/|e| of every interior edge (the zero slot n_ei gets 0): the readout multiplies by it, since
+// an FP64 division per element costs more than the transfer on GB300's FP64 pipes.
+__global__ void k_recip(const double* __restrict__ elen, double* __restrict__ relen, int64_t n_ei) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_ei) relen[k] = 1.0 / elen[k];
+    else if (k == n_ei) relen[k] = 0.0;
+}
+
+cudaError_t launch_recip(const double* elen, double* relen, int64_t n_ei, cudaStream_t s) {
+    k_recip<<<blocks_for(n_ei + 1), kThreads, 0, s>>>(elen, relen, n_ei);
     return cudaGetLastError();
 }
 
@@ -680,15 +771,15 @@ cudaError_t launch_fields_in(const DevMesh& m, const double* Ec, const double* B
 
 cudaError_t launch_fields_out(const DevMesh& m, double* Ec, double* Bc, double* Jc,
                               const int64_t* edge_caller, const int64_t* perm_tri,
-                              const double* elen, cudaStream_t s) {
+                              const double* relen, cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
     if (Ec && m.n_ei > 0) {
-        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.U, edge_caller, elen, Ec, m.n_ei);
-        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.U, edge_caller, elen, Ec, m.n_ei);
+        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.U, edge_caller, relen, Ec, m.n_ei);
+        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.U, edge_caller, relen, Ec, m.n_ei);
     }
     if (Jc && m.J && m.n_ei > 0) {
-        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.J, edge_caller, elen, Jc, m.n_ei);
-        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.J, edge_caller, elen, Jc, m.n_ei);
+        if (f64) k_fields_out_edges<double><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const double*)m.J, edge_caller, relen, Jc, m.n_ei);
+        else k_fields_out_edges<float><<<blocks_for(m.n_ei), kThreads, 0, s>>>((const float*)m.J, edge_caller, relen, Jc, m.n_ei);
     }
     if (Bc) {
         if (f64) k_fields_out_tris<double><<<blocks_for(m.n_t), kThreads, 0, s>>>((const double*)m.B, perm_tri, Bc, m.n_t);
@@ -698,21 +789,26 @@ cudaError_t launch_fields_out(const DevMesh& m, double* Ec, double* Bc, double* 
 }
 
 namespace {
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// threads for n caller elements of type H, V = 16 / sizeof(H) each
+template <typename H>
+inline unsigned blocks_for_vec(int64_t n) { return blocks_for((n + (16 / sizeof(H)) - 1) / (16 / sizeof(H))); }
+
 template <typename T, typename H>
 void fields_in_c(const DevMesh& m, const H* Ec, const H* Bc, const H* Jc, const int32_t* k_of, const int32_t* inv,
                  const double* elen, int64_t n_e, cudaStream_t s) {
     const int64_t ne = n_e > 0 ? n_e : 1;
-    if (Ec) k_fields_in_edges_c<T, H><<<blocks_for(ne), kThreads, 0, s>>>(Ec, k_of, elen, (T*)m.U, n_e, m.n_ei);
-    if (Jc && m.J) k_fields_in_edges_c<T, H><<<blocks_for(ne), kThreads, 0, s>>>(Jc, k_of, elen, (T*)m.J, n_e, m.n_ei);
-    if (Bc) k_fields_in_tris_c<T, H><<<blocks_for(m.n_t), kThreads, 0, s>>>(Bc, inv, (T*)m.B, m.n_t);
+    if (Ec) k_fields_in_edges_c<T, H><<<blocks_for_vec<H>(ne), kThreads, 0, s>>>(Ec, k_of, elen, (T*)m.U, n_e, m.n_ei, aligned16(Ec));
+    if (Jc && m.J) k_fields_in_edges_c<T, H><<<blocks_for_vec<H>(ne), kThreads, 0, s>>>(Jc, k_of, elen, (T*)m.J, n_e, m.n_ei, aligned16(Jc));
+    if (Bc) k_fields_in_tris_c<T, H><<<blocks_for_vec<H>(m.n_t), kThreads, 0, s>>>(Bc, inv, (T*)m.B, m.n_t, aligned16(Bc));
 }
 
 template <typename T, typename H>
 void fields_out_c(const DevMesh& m, H* Ec, H* Bc, H* Jc, const int32_t* k_of, const int32_t* inv,
-                  const double* elen, int64_t n_e, cudaStream_t s) {
-    if (Ec && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for(n_e), kThreads, 0, s>>>((const T*)m.U, k_of, elen, Ec, n_e);
-    if (Jc && m.J && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for(n_e), kThreads, 0, s>>>((const T*)m.J, k_of, elen, Jc, n_e);
-    if (Bc) k_fields_out_tris_c<T, H><<<blocks_for(m.n_t), kThreads, 0, s>>>((const T*)m.B, inv, Bc, m.n_t);
+                  const double* relen, int64_t n_e, cudaStream_t s) {
+    if (Ec && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for_vec<H>(n_e), kThreads, 0, s>>>((const T*)m.U, k_of, relen, Ec, n_e, aligned16(Ec));
+    if (Jc && m.J && n_e > 0) k_fields_out_edges_c<T, H><<<blocks_for_vec<H>(n_e), kThreads, 0, s>>>((const T*)m.J, k_of, relen, Jc, n_e, aligned16(Jc));
+    if (Bc) k_fields_out_tris_c<T, H><<<blocks_for_vec<H>(m.n_t), kThreads, 0, s>>>((const T*)m.B, inv, Bc, m.n_t, aligned16(Bc));
 }
 }  // namespace
 
@@ -733,16 +829,16 @@ cudaError_t launch_fields_in_caller(const DevMesh& m, const void* Ec, const void
 }
 
 cudaError_t launch_fields_out_caller(const DevMesh& m, void* Ec, void* Bc, void* Jc, bool f32, const int32_t* k_of,
-                                     const int32_t* inv, const double* elen, int64_t n_e, cudaStream_t s) {
+                                     const int32_t* inv, const double* relen, int64_t n_e, cudaStream_t s) {
     const bool f64 = m.precision == UE_PREC_FP64;
     if (f32) {
         auto E = (float*)Ec, B = (float*)Bc, J = (float*)Jc;
-        f64 ? fields_out_c<double, float>(m, E, B, J, k_of, inv, elen, n_e, s)
-            : fields_out_c<float, float>(m, E, B, J, k_of, inv, elen, n_e, s);
+        f64 ? fields_out_c<double, float>(m, E, B, J, k_of, inv, relen, n_e, s)
+            : fields_out_c<float, float>(m, E, B, J, k_of, inv, relen, n_e, s);
     } else {
         auto E = (double*)Ec, B = (double*)Bc, J = (double*)Jc;
-        f64 ? fields_out_c<double, double>(m, E, B, J, k_of, inv, elen, n_e, s)
-            : fields_out_c<float, double>(m, E, B, J, k_of, inv, elen, n_e, s);
+        f64 ? fields_out_c<double, double>(m, E, B, J, k_of, inv, relen, n_e, s)
+            : fields_out_c<float, double>(m, E, B, J, k_of, inv, relen, n_e, s);
     }
     return cudaGetLastError();
 }

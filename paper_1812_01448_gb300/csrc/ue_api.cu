@@ -82,6 +82,7 @@ struct ue_mesh {
     int64_t* d_perm = nullptr;
     int64_t* d_ecaller = nullptr;
     double *d_O = nullptr, *d_S = nullptr, *d_elen = nullptr, *d_d = nullptr;
+    double* d_relen = nullptr;   // 1/|e| (the readout of E)
     // transfer buffers in caller numbering
     double *d_Ec = nullptr, *d_Bc = nullptr, *d_Jc = nullptr;
     // caller -> stored maps of the direct transfers (made on first use)
@@ -854,6 +855,7 @@ int alloc_and_upload(ue_mesh* m, cudaStream_t s) {
               alloc_into(m, m->d_perm, nt, 8, s) && alloc_into(m, m->d_ecaller, nei + 1, 8, s) &&
               alloc_into(m, m->d_O, 2 * nt, 8, s) && alloc_into(m, m->d_S, nt, 8, s) &&
               alloc_into(m, m->d_elen, nei + 1, 8, s) && alloc_into(m, m->d_d, nei + 1, 8, s) &&
+              alloc_into(m, m->d_relen, nei + 1, 8, s) &&
               alloc_into(m, m->d_Ec, ne, 8, s) && alloc_into(m, m->d_Bc, nt, 8, s) &&
               alloc_into(m, m->d_Jc, ne, 8, s);
     DevMesh& dm = m->dm;
@@ -1002,7 +1004,7 @@ int fields_f32(ue_mesh* m, float* E, float* B, float* j, bool write, cudaStream_
         if (rc != UE_OK) return rc;
     } else {
         UE_CUDA(ue::launch_fields_out_caller(m->dm, const_cast<void*>(dE), const_cast<void*>(dB),
-                                             const_cast<void*>(dj), true, m->d_kof, m->d_inv, m->d_elen,
+                                             const_cast<void*>(dj), true, m->d_kof, m->d_inv, m->d_relen,
                                              h.n_edges, s));
         if (!direct) {
             if (E) UE_CUDA(cudaMemcpyAsync(E, m->d_Ec, 4 * h.n_edges, cudaMemcpyDeviceToHost, s));
@@ -1221,6 +1223,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     const int64_t nt = h.n_tris, nei = h.n_ei;
     UE_CUDA(ue::launch_geom_tri(m->d_xy, m->d_tri_nodes, m->d_O, m->d_S, nt, s));
     UE_CUDA(ue::launch_geom_edge(m->d_xy, m->d_edge_nodes, m->d_edge_opp, m->d_elen, m->d_d, nei, s));
+    UE_CUDA(ue::launch_recip(m->d_elen, m->d_relen, nei, s));
     // dual lengths must be positive (eq. 3 divides by |O_R O_L|)
     {
         std::vector<double> dd(nei), ll(nei);
@@ -1451,6 +1454,7 @@ int ue_batch_create(ue_mesh* const* meshes, int32_t n, void* stream, ue_mesh** o
             UE_BATCH_CUDA(cudaMemcpyAsync((char*)dm.U + esz * ko, m->dm.U, esz * nei, cudaMemcpyDeviceToDevice, s));
         }
     }
+    UE_BATCH_CUDA(ue::launch_recip(B->d_elen, B->d_relen, NEI, s));   // the readout's 1/|e|
     {
         // padding records of the batch point at its zero slot with coefficient 0
         std::vector<int4> pad(dm.n_t_pad - H.n_tris);
@@ -1802,14 +1806,14 @@ int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
         const int rc = ensure_caller_maps(m, s);
         if (rc != UE_OK) return rc;
         UE_CUDA(ue::launch_fields_out_caller(m->dm, const_cast<void*>(dE), const_cast<void*>(dB),
-                                             const_cast<void*>(dj), false, m->d_kof, m->d_inv, m->d_elen,
+                                             const_cast<void*>(dj), false, m->d_kof, m->d_inv, m->d_relen,
                                              h.n_edges, s));
         m->direct_fields += (E ? 1 : 0) + (B ? 1 : 0) + (j ? 1 : 0);
     } else {
         if (E) UE_CUDA(cudaMemsetAsync(m->d_Ec, 0, 8 * h.n_edges, s));
         if (j) UE_CUDA(cudaMemsetAsync(m->d_Jc, 0, 8 * h.n_edges, s));
         UE_CUDA(ue::launch_fields_out(m->dm, E ? m->d_Ec : nullptr, B ? m->d_Bc : nullptr,
-                                      j ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm, m->d_elen, s));
+                                      j ? m->d_Jc : nullptr, m->d_ecaller, m->d_perm, m->d_relen, s));
         if (E && m->has_reg)
             UE_CUDA(ue::launch_frame_iface_out(m->reg.f, m->reg.dm, m->d_iedge, m->d_ielen, m->d_Ec, s));
         else if (E && m->dm.frame)
