@@ -466,6 +466,10 @@ def run_native(args):
         J0, Jo = pinned(m.n_edges), pinned(m.n_edges)
     write = m.write_fields_f32 if f32 else m.write_fields
     read = m.read_fields_f32 if f32 else m.read_fields
+    # warm-up of the transfer path: one untimed write and read of the same pinned buffers (the
+    # GPU's first touch of freshly pinned pages costs address translation, not bandwidth)
+    write(E0, B0, J0, stream=stream)
+    read(j=dens is not None, out={"E": Eo, "B": Bo, "j": Jo}, stream=stream)
     barrier()
     torch.cuda.synchronize()
     d0 = m.stats()["direct_fields"]
