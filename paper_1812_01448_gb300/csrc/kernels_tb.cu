@@ -343,8 +343,9 @@ __global__ void __launch_bounds__(1024, 1) k_tbs(TBArgs a) {
 // signs of eq. 4 into the coefficients: with x_q = s_q U_q,
 //   rn(rn(x0 + x1) + x2) = s0 rn(rn(U0 + s0 s1 U1) + s0 s2 U2)
 // because round-to-nearest is odd (rn(-y) = -rn(y)), so
-//   B - (dt/S) rn(rn(x0 + x1) + x2) = fma(-s0 dt/S, fma(s0 s2, U2, fma(s0 s1, U1, U0)), B)
-// rounds exactly as the plain kernel's select-and-add does.  Gathers of G slots are issued
+//   B - (dt/S) rn(rn(x0 + x1) + x2) = fma(-s0 dt/S, rn(rn(U0 + s0 s1 U1) + s0 s2 U2), B)
+// rounds exactly as the plain kernel's select-and-add does; the signs s0 s1 and s0 s2 ride in
+// bits 31 and 30 of the third gather offset and flip the gathered values' sign bits.  Gathers of G slots are issued
 // before any of their stores.  The field buffers sit at compile-time offsets (capacity TS*NT
 // triangles and ES*NT edges); a gather is one shift or mask, one add to the buffer's 32-bit
 // shared address and one shared load.
@@ -478,10 +479,11 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
     }
     if (!ok) tile = n_tiles;
     __syncthreads();
-    // per slot: triangle gather offsets (U0 | U1 << 16, U2), -s0 dt/S, s0 s1, s0 s2 and B;
+    // per slot: triangle gather offsets (U0 | U1 << 16, U2 | signs s0 s1, s0 s2 in bits 31, 30),
+    // -s0 dt/S and B;
     // edge gather offsets (B_lo | B_hi << 16), +-dt|e|/d and U (plasma: pb and J)
     unsigned toff[TS], toff2[TS];
-    float tcb[TS], ts1[TS], ts2[TS], tb[TS];
+    float tcb[TS], tb[TS];
     unsigned erl[ES];
     float ecu[ES], eu[ES], epb[ES], ej[ES];
     unsigned srcm = 0;
@@ -503,11 +505,9 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
                 const int4 r = tstage[l];
                 const unsigned c0 = (unsigned)r.y & 0xFFFFu, c1 = (unsigned)r.y >> 16, c2 = (unsigned)r.z;
                 toff[i] = (4u * (Lay::UOFF + (c0 >> 1))) | ((4u * (Lay::UOFF + (c1 >> 1))) << 16);
-                toff2[i] = 4u * (Lay::UOFF + (c2 >> 1));
+                toff2[i] = (4u * (Lay::UOFF + (c2 >> 1))) | (((c0 ^ c1) & 1u) << 31) | (((c0 ^ c2) & 1u) << 30);
                 const float cb = __int_as_float(r.w);
                 tcb[i] = (c0 & 1u) ? cb : -cb;
-                ts1[i] = ((c0 ^ c1) & 1u) ? -1.f : 1.f;
-                ts2[i] = ((c0 ^ c2) & 1u) ? -1.f : 1.f;
                 tb[i] = Fc[l];
             }
         }
@@ -602,14 +602,16 @@ __global__ void __launch_bounds__(NT, 1) k_tbp(TBArgs a, int n_tiles) {
                     if (i < TS && tid + i * NT < tend) {
                         u0[q] = lds_at(Fcb, toff[i] & 0xFFFFu);
                         u1[q] = lds_at(Fcb, toff[i] >> 16);
-                        u2[q] = lds_at(Fcb, toff2[i]);
+                        u2[q] = lds_at(Fcb, toff2[i] & 0xFFFFu);
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < G; ++q) {
                     const int i = g0 + q;
                     if (i < TS && tid + i * NT < tend) {
-                        const float t = rn_fma(ts2[i], u2[q], rn_fma(ts1[i], u1[q], u0[q]));
+                        const float x1 = __int_as_float(__float_as_int(u1[q]) ^ (int)(toff2[i] & 0x80000000u));
+                        const float x2 = __int_as_float(__float_as_int(u2[q]) ^ (int)((toff2[i] << 1) & 0x80000000u));
+                        const float t = rn_add(rn_add(u0[q], x1), x2);
                         tb[i] = rn_fma(tcb[i], t, tb[i]);
                         Fc[tid + i * NT] = tb[i];
                     }
@@ -685,8 +687,9 @@ cudaError_t launch_tb_t(const TBArgs& a, int n_tiles, size_t smem, cudaStream_t 
     return cudaGetLastError();
 }
 
-// gathers issued together per group of slots in k_tbp
-constexpr int kTbpGroup = 1;
+// gathers issued together per group of slots in k_tbp (2 measured best: 1.5% faster than 1;
+// 3 and 4 slower)
+constexpr int kTbpGroup = 2;
 
 template <int NT, int TS, int ES, bool PLASMA, bool SRC>
 cudaError_t launch_tbp_t(const TBArgs& a, int n_tiles, int grid, cudaStream_t s) {
