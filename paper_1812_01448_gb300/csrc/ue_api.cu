@@ -693,8 +693,71 @@ int upload_tiles(ue_mesh* m, cudaStream_t s) {
 }
 
 // Device copy of m->ts, second field buffers, and the coefficient slots of the records.
+// Every index the blocked kernels follow, checked on the host before the records reach the
+// device: headers (counts ordered by ring level and inside the record arrays), global ids of
+// the records inside the field arrays, local triangle slots of the edge records and local edge
+// codes of the triangle records inside the tile (the zero slot nel included), and for the fused
+// records their neighbour offsets and edge ids.  A violation is an internal error of the tile
+// builder, reported instead of launched.
+bool tiles_in_range(const ue::TileSet& ts, int64_t n_t, int64_t n_ei, std::string& why) {
+    const int64_t n_trec = (int64_t)ts.trec.size() / 4, n_erec = (int64_t)ts.erec.size() / 4;
+    const int64_t n_frec = (int64_t)ts.frec.size() / 5, n_fedge = (int64_t)ts.fedge.size() / 2;
+    for (int64_t t = 0; t < ts.n_tiles; ++t) {
+        const int32_t* h = &ts.hdr[t * ue::TileSet::kHdr];
+        const int ntl = h[4], nel = h[5], k = h[10];
+        auto bad = [&](const char* what) {
+            why = "tile " + std::to_string(t) + ": " + what;
+            return false;
+        };
+        if (ntl < 0 || nel < 0 || h[1] < 0 || h[1] > ntl || h[3] < 0 || h[3] > nel || k < 1 || k > 15)
+            return bad("counts");
+        if (h[0] < 0 || (int64_t)h[0] + h[1] > n_t || h[2] < 0 || (int64_t)h[2] + h[3] > n_ei)
+            return bad("owned ranges");
+        if (h[6] < 0 || (int64_t)h[6] + ntl > n_trec || h[7] < 0 || (int64_t)h[7] + nel > n_erec)
+            return bad("record offsets");
+        for (int r = 0; r < 16; ++r) {
+            if (h[16 + r] < (r ? h[15 + r] : 0) || h[16 + r] > ntl) return bad("triangle levels");
+            if (h[32 + r] < (r ? h[31 + r] : 0) || h[32 + r] > nel) return bad("edge levels");
+        }
+        const int32_t* tr = &ts.trec[4 * (size_t)h[6]];
+        const int nupd = h[16 + k - 1];
+        for (int l = 0; l < ntl; ++l) {
+            if (tr[4 * l] < 0 || tr[4 * l] >= n_t) return bad("triangle id");
+            if (l >= nupd) continue;
+            const uint32_t c[3] = {(uint32_t)tr[4 * l + 1] & 0xFFFFu, (uint32_t)tr[4 * l + 1] >> 16,
+                                   (uint32_t)tr[4 * l + 2]};
+            for (int q = 0; q < 3; ++q)
+                if ((int64_t)(c[q] >> 1) > nel) return bad("triangle edge code");
+        }
+        const int32_t* er = &ts.erec[4 * (size_t)h[7]];
+        for (int l = 0; l < nel; ++l) {
+            const uint32_t w = (uint32_t)er[4 * l + 1];
+            if (er[4 * l] < 0 || er[4 * l] >= n_ei) return bad("edge id");
+            if ((int)(w & 0xFFFFu) >= ntl || (int)(w >> 16) >= ntl) return bad("edge triangle slot");
+        }
+        if (!ts.frec.empty()) {
+            if (h[11] < 0 || (int64_t)h[11] + ntl > n_frec || h[12] < 0 || (int64_t)h[12] + nel + 1 > n_fedge)
+                return bad("fused record offsets");
+            const int32_t* fr = &ts.frec[5 * (size_t)h[11]];
+            for (int l = 0; l < nupd; ++l) {
+                const uint32_t r1 = (uint32_t)fr[5 * l + 1], r2 = (uint32_t)fr[5 * l + 2], r3 = (uint32_t)fr[5 * l + 3];
+                const uint32_t nb[3] = {(r1 & 0xFFFFu) / 4, (r1 >> 16) / 4, (r2 & 0x3FFFu) / 4};
+                const uint32_t e[3] = {(r2 >> 14) & 0x1FFFu, r3 & 0x1FFFu, (r3 >> 16) & 0x1FFFu};
+                for (int q = 0; q < 3; ++q)
+                    if ((int)nb[q] >= ntl || (int)e[q] > nel) return bad("fused record");
+            }
+        }
+    }
+    return true;
+}
+
 int upload_tileset(ue_mesh* m, cudaStream_t s) {
     ue::TileSet& ts = m->ts;
+    {
+        std::string why;
+        if (!tiles_in_range(ts, m->hm.n_tris, m->hm.n_ei, why))
+            return fail(UE_ERR_ARG, "internal error: a tile record is out of range (" + why + ")");
+    }
     if (!ue::tb_fits(ts.max_tri_loc, ts.max_edge_loc, m->tb_threads))
         return fail(UE_ERR_ARG, "tiles with halo too large for the blocked kernel (" +
                                     std::to_string(ts.max_tri_loc) + " triangles, " +
