@@ -32,9 +32,10 @@ DEFAULT_CANDIDATES = (
     ("blocked", "kd", 2048, 8, 512),
     ("blocked", "kd", 2048, 8, 1024),
     ("blocked", "greedy", 2500, 8, 512),
+    ("blocked", "rings", 2500, 8, 512),
 )
 
-TILERS = {"kd": N.UE_REORDER_KD, "greedy": N.UE_REORDER_GREEDY}
+TILERS = {"kd": N.UE_REORDER_KD, "greedy": N.UE_REORDER_GREEDY, "rings": N.UE_REORDER_GREEDY_RINGS}
 
 _VARIANT = {"plain": N.UE_VARIANT_PLAIN, "persistent": N.UE_VARIANT_PERSISTENT,
             "blocked": N.UE_VARIANT_BLOCKED}
