@@ -65,3 +65,28 @@ def test_counters_are_reported_only_for_the_profiled_sources(tmp_path, monkeypat
     with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as fh:
         for r in json.load(fh)["records"]:
             assert set(r["config"]) == set(key) and len(r["sources_sha1"]) == 40
+
+
+def test_onchip_roofline_from_counters(monkeypatch):
+    """roofline.onchip: shared-memory wavefronts against one per SM per cycle, warp instructions
+    against four per SM per cycle, and the load/store split against one wavefront per
+    instruction (the cp.async writes reported apart)."""
+    sys.path.insert(0, ROOT)
+    import types
+    import bench
+    fake_props = types.SimpleNamespace(multi_processor_count=100)
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: fake_props)
+    c = {"smem_wavefronts": 2.0e6, "warp_instructions": 8.0e6, "smem_instructions": 1.0e6,
+         "pipe_lsu_wavefronts_mem_shared_op_ld": 1.2e6, "pipe_lsu_wavefronts_mem_shared_op_st": 0.3e6,
+         "pipe_lsu_wavefronts_mem_shared_op_misc": 0.5e6}
+    r = bench.onchip_roofline(c, 0.1, 1000.0)          # 0.1 ms at 1 GHz on 100 SMs
+    assert abs(r["smem"]["frac"] - 2.0e6 / (1e-4 * 100 * 1e9)) < 1e-12
+    assert abs(r["issue"]["frac"] - 8.0e6 / (1e-4 * 4 * 100 * 1e9)) < 1e-12
+    assert abs(r["smem"]["bank_conflict_factor"] - 1.5) < 1e-12
+    assert r["smem"]["cp_async_wavefronts"] == 0.5e6
+    # without the split, the factor falls back to all wavefronts over instructions
+    r = bench.onchip_roofline({k: c[k] for k in ("smem_wavefronts", "warp_instructions", "smem_instructions")},
+                              0.1, None)
+    assert abs(r["smem"]["bank_conflict_factor"] - 2.0) < 1e-12 and r["clock_mhz"] == 2070.0
