@@ -66,8 +66,9 @@ extern "C" {
                                  /* dt it gives stays a margin below 2/rho_hi (eq. 20)        */
 
 #define UE_VARIANT_PLAIN 1       /* two kernels per step (edge half-step, triangle half-step) */
-#define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the KD tiles, halo    */
+#define UE_VARIANT_BLOCKED 2     /* one kernel per block_depth steps on the tiles, halo       */
                                  /* recomputed in shared memory; FP32; needs KD or greedy     */
+                                 /* tiles (UE_REORDER_KD, _GREEDY or _GREEDY_RINGS)           */
 #define UE_VARIANT_PERSISTENT 3  /* one cooperative launch per chunk of steps, timed grid     */
                                  /* barriers between half-steps; FP32                         */
 
@@ -104,7 +105,7 @@ typedef struct ue_options {
     uint32_t power_seed;   /* start vector: SplitMix64(seed * 2^32 + caller triangle id)     */
     int32_t variant;       /* UE_VARIANT_* (0 = default: plain)                              */
     int32_t graph_chunk;   /* steps per captured CUDA graph launch; 0 = default, <0 = none   */
-    int32_t tile_tris;     /* UE_REORDER_KD / _GREEDY: maximum triangles per tile (ue_mesh_load) */
+    int32_t tile_tris;     /* UE_REORDER_KD / _GREEDY / _GREEDY_RINGS: maximum triangles per tile (ue_mesh_load) */
     int32_t block_depth;   /* UE_VARIANT_BLOCKED: steps per launch, 1..15                    */
     int32_t tb_threads;    /* UE_VARIANT_BLOCKED: CTA size, 0 = 512 (default) or 1024        */
     double dt;             /* UE_DT_GIVEN: the time step                                     */
@@ -258,7 +259,8 @@ int ue_get_sizes(const ue_mesh* m, int64_t* n_nodes, int64_t* n_tris, int64_t* n
 int ue_get_tables(const ue_mesh* m, int64_t* perm_tri, int64_t* edge_caller, int32_t* edge_tri,
                   int32_t* tri_code);
 
-/* Tiles of a UE_REORDER_KD or UE_REORDER_GREEDY mesh ("Divide and conqueror" section):
+/* Tiles of a UE_REORDER_KD, UE_REORDER_GREEDY or UE_REORDER_GREEDY_RINGS mesh ("Divide and
+ * conqueror" section):
  * *n_tiles parts (0 for other orders); tile t holds the stored triangles
  * tile_off[t] .. tile_off[t+1]-1.  tile_off (host, n_tiles + 1 entries) may be NULL to ask the
  * count only.  Host only; UE_ERR_ARG if m or n_tiles is NULL. */
