@@ -114,3 +114,27 @@ def test_lowest_modes_match_dense_and_the_resonator(ue, which):
     err = np.abs(w[1:] / exact - 1)
     print(f"{which}: lowest omegas {np.round(w[1:6], 4)}, analytic {np.round(exact[:5], 4)}, max rel err {err.max():.2e}")
     assert err.max() < (0.01 if which == "cavity1024" else 0.003)
+
+
+def test_lowest_modes_on_a_holed_graded_mesh(ue):
+    """ue_modes_low away from the rectangle: a graded square with a PEC hole (no analytic
+    spectrum), the 8 lowest omegas against a dense eigendecomposition to 1e-9, each mode an
+    S-normalised eigenvector, and omega_0 the static field."""
+    ms = meshgen.graded_square(0.03, 0.06, grade=0.3, seed=21,
+                               holes=[meshgen.polygon_triangle((0.5, 0.5), 0.25)])
+    ops = operators.Operators(om.canonicalize(ms.xy, ms.tris))
+    lam = np.linalg.eigvalsh(spectral.symmetric_K(ops))
+    dense = np.sqrt(np.clip(lam, 0.0, None))
+    m = ue.Mesh(ms.xy, ms.tris)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-4)
+    w, B = m.modes_low(8, iters=300, degree=24, seed=9, vectors=True)
+    m.close()
+    assert w[0] < 1e-4 * w[1]
+    assert np.abs(w[1:] / dense[1:8] - 1).max() < 1e-9
+    S = ops.w_B
+    for i in range(8):
+        assert abs(np.dot(S * B[i], B[i]) - 1) < 1e-9
+        r = spectral.apply_K(ops, B[i]) - w[i] ** 2 * B[i]
+        # two pairs of modes lie within 0.5% of each other here: their residuals converge
+        # more slowly than their frequencies
+        assert np.sqrt(np.dot(S * r, r)) < 1e-4 * w[-1] ** 2
