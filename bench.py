@@ -364,8 +364,10 @@ def run_native(args):
     part_stats = partition_stats(m) if blocked else None
     frame = m.frame_info() if args.frame > 0 else None
 
-    # warm-up (also captures the step graph)
+    # warm-up, then the step graphs captured and uploaded (setup, like the tiles: a run of
+    # fewer warm-up steps than one graph chunk would otherwise capture inside the timed call)
     m.step_n(args.warmup, stream)
+    m.step_prepare(stream)
     torch.cuda.synchronize()
     if args.step_sweep:
         # the cost of one ue_step_n(n) call against n (median of 5 calls, CUDA events on the
@@ -884,7 +886,9 @@ def main(argv=None):
     ap.add_argument("--tiler", choices=["kd", "greedy", "rings"], default="rings",
                     help="blocked variant: KD or greedy partition into tiles; rings: the greedy tiles "
                          "with each tile's boundary rings stored first, by angle")
-    ap.add_argument("--block-depth", type=int, default=8)
+    ap.add_argument("--block-depth", type=int, default=0,
+                    help="steps per blocked launch (the tiles' halo depth); 0: 10 on scatterer-4M without a "
+                         "frame, 8 otherwise (plasma tiles of 2700 and the frame region were measured at 8)")
     ap.add_argument("--graph-chunk", type=int, default=32)
     ap.add_argument("--tb-threads", type=int, default=0, choices=[0, 512, 1024])
     ap.add_argument("--e2e-fields", choices=["f32", "f64"], default="f32",
@@ -911,6 +915,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.tile_tris <= 0:
         args.tile_tris = 2700 if args.workload == "plasma" else 2500
+    if args.block_depth <= 0:
+        args.block_depth = 10 if args.workload == "scatterer" and args.frame == 0 else 8
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.frame > 0 and args.variant == "persistent":

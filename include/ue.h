@@ -227,6 +227,15 @@ int ue_read_fields_f32(ue_mesh* m, float* E, float* B, float* j, void* stream);
  * reported here; device-side conditions surface at the next synchronous call. */
 int ue_step_n(ue_mesh* m, int64_t n_steps, void* stream);
 
+/* Capture and instantiate now the CUDA graphs that ue_step_n replays (a blocked mesh: one per
+ * field buffer parity; the plain variant: one), and upload them on `stream`, so that the first
+ * ue_step_n call long enough to use them pays no capture.  Steps nothing and leaves the fields
+ * and the step counter as they are.  A later call that changes what the steps read
+ * (ue_set_source, ue_set_plasma, ue_geometry_build) makes ue_step_n capture again.  No-op for the persistent variant, a mesh stepped
+ * as one tile, or graph_chunk 0.  UE_ERR_ARG before geometry_build; UE_ERR_CUDA if a capture
+ * fails. */
+int ue_step_prepare(ue_mesh* m, void* stream);
+
 /* Copy the fields back in the caller's numbering (synchronous).  E, j: n_edges values (0 on
  * boundary edges, except the outer edges of a framed mesh); B: n_tris values.  Any pointer may
  * be NULL.  Pinned host arrays are written in place by the kernels, as in ue_write_fields.

@@ -63,6 +63,7 @@ SIGNATURES = [
     ("ue_write_fields_f32", C.c_int, [P, P, P, P, P]),
     ("ue_read_fields_f32", C.c_int, [P, P, P, P, P]),
     ("ue_step_n", C.c_int, [P, I64, P]),
+    ("ue_step_prepare", C.c_int, [P, P]),
     ("ue_exchange_tris", C.c_int, [P, P, I64, P, C.c_int32, P]),
     ("ue_read_fields", C.c_int, [P, PD, PD, PD, P]),
     ("ue_energy", C.c_int, [P, PD, P]),

@@ -189,6 +189,10 @@ class Mesh:
     def step_n(self, n: int, stream=None):
         N.check(N.lib().ue_step_n(self._h, int(n), _stream(stream)), "ue_step_n")
 
+    def step_prepare(self, stream=None):
+        """Capture the step graphs now (ue_step_prepare), outside any timed or latency-bound call."""
+        N.check(N.lib().ue_step_prepare(self._h, _stream(stream)), "ue_step_prepare")
+
     def read_fields(self, E=True, B=True, j=False, stream=None, out=None):
         """Return (E, B, j) as float64 arrays in caller numbering (None where not asked)."""
         o = out or {}

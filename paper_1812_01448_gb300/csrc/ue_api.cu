@@ -1852,6 +1852,27 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
     return UE_OK;
 }
 
+int ue_step_prepare(ue_mesh* m, void* stream) {
+    Range nvtx_range("ue_step_prepare");
+    if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->graph_chunk <= 0 || m->variant == UE_VARIANT_PERSISTENT) return UE_OK;
+    if (m->variant == UE_VARIANT_BLOCKED) {
+        if (!m->dm.plasma && !m->has_reg && !m->ts.hdr.empty() && ue::tbf1_fits(m->tb, m->ts.hdr.data()))
+            return UE_OK;   // one launch per call, no graph
+        for (int p = 0; p < 2; ++p) {
+            const int rc = ensure_graph_tb(m, p);
+            if (rc != UE_OK) return rc;
+            UE_CUDA(cudaGraphUpload(m->gexec_tb[p], s));
+        }
+        return UE_OK;
+    }
+    const int rc = ensure_graph(m);
+    if (rc != UE_OK) return rc;
+    UE_CUDA(cudaGraphUpload(m->gexec, s));
+    return UE_OK;
+}
+
 int ue_read_fields(ue_mesh* m, double* E, double* B, double* j, void* stream) {
     Range nvtx_range("ue_read_fields");
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");

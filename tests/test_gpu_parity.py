@@ -186,10 +186,11 @@ def test_non_delaunay_mesh_is_rejected(ue):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["plain", "blocked", "blocked-fused"])
+@pytest.mark.parametrize("variant", ["plain", "blocked", "blocked-k8", "blocked-fused"])
 def test_full_size_scatterer_window(ue, scatterer_window, variant):
     """Full size in the bench's launch configurations (plain: RCM, graphs of 32 steps;
-    blocked: ring-ordered greedy tiles of <= 2500, k = 8, 512 threads, split or fused kernel) against the
+    blocked: ring-ordered greedy tiles of <= 2500, k = 10 (and 8), 512 threads, split or fused
+    kernel, the step graphs captured ahead by step_prepare) against the
     oracle on the whole mesh: relative L2 of each field, and per element the largest error
     against the field's largest value (an error confined to a few elements, such as the source
     edges or the hole's ring, would not move the L2 norm over 6M edges)."""
@@ -199,11 +200,13 @@ def test_full_size_scatterer_window(ue, scatterer_window, variant):
                 tile_tris=2500)
     m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt,
                      variant=ue.UE_VARIANT_BLOCKED if blocked else ue.UE_VARIANT_PLAIN,
-                     block_depth=8, tb_kernel=ue.UE_TB_FUSED if variant == "blocked-fused" else ue.UE_TB_SPLIT)
+                     block_depth=8 if variant == "blocked-k8" else 10,
+                     tb_kernel=ue.UE_TB_FUSED if variant == "blocked-fused" else ue.UE_TB_SPLIT)
     m.set_source(ids, amp, w0, 0.1, 0.05)
     if blocked:
         assert m.stats()["tb_kernel_used"] == (4 if variant == "blocked-fused" else 3)
     m.set_step(5000)
+    m.step_prepare()
     m.step_n(200)
     E, B, _ = m.read_fields()
     m.close()
@@ -238,6 +241,36 @@ def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=No
     step = m.get_step()
     m.close()
     return out, step
+
+
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_step_prepare_is_bit_identical(ue, variant):
+    """Step graphs captured ahead by step_prepare (once before set_plasma and set_source, which
+    make the next step_n capture again, and once after them) give the fields of the lazily
+    captured run bit for bit, over graph chunks and a remainder, plasma current included."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    rho, _ = spectral.power_iteration(ops, 50)
+    dt = 0.45 / rho
+    code = ue.UE_VARIANT_BLOCKED if variant == "blocked" else ue.UE_VARIANT_PLAIN
+    B0 = np.sin(7 * ms.xy[ms.tris].mean(axis=1)[:, 0])
+    out = []
+    for prepare in (False, True):
+        m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY_RINGS, tile_tris=300)
+        m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=code, block_depth=5, graph_chunk=32)
+        if prepare:
+            m.step_prepare()
+        m.set_plasma(dens, 0.01 * w0)
+        m.set_source(ids, amp, w0, 0.0, 0.05)
+        m.write_fields(B=B0)
+        if prepare:
+            m.step_prepare()
+        m.step_n(71)
+        out.append((m.read_fields(j=True), m.get_step()))
+        m.close()
+    (Ea, Ba, Ja), sa = out[0]
+    (Eb, Bb, Jb), sb = out[1]
+    assert sa == sb == 71
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ba, Bb) and np.array_equal(Ja, Jb)
 
 
 @pytest.mark.parametrize("tile,k,nsteps,threads", [(512, 4, 14, 0), (1024, 8, 40, 0), (300, 1, 5, 0),
