@@ -252,7 +252,10 @@ int ue_energy(ue_mesh* m, double* W, void* stream);
  * persistent variant ran out of time.  ue_write_fields re-arms both. */
 int ue_check(ue_mesh* m, double* W, int32_t* flag);
 
-/* Step counter used by the source time t = (n + 1/2) dt (checkpoint / resume). */
+/* Step counter used by the source time t = (n + 1/2) dt (checkpoint / resume).  ue_set_step
+ * returns at once: the value reaches the device in the stream of the next ue_step_n (or
+ * ue_profile_steps), ordered before its kernels; ue_get_step returns it until then.
+ * ue_get_step otherwise reads the device counter (synchronous). */
 int ue_get_step(const ue_mesh* m, int64_t* step);
 int ue_set_step(ue_mesh* m, int64_t step);
 

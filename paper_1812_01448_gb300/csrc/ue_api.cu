@@ -69,6 +69,7 @@ struct ue_mesh {
     double dt = 0, rho = 0;
     int rho_source = UE_RHO_GIVEN;
     int64_t steps_done = 0;
+    int64_t step_pending = -1;   // ue_set_step's value, put on the device by the next call that steps
     int64_t launches = 0;
 
     // device tables and geometry (stored numbering)
@@ -1025,19 +1026,45 @@ bool direct_transfer(const ue_mesh* m, const void* E, const void* B, const void*
     return (!E || dE) && (!B || dB) && (!j || dj) && (E || B || j);
 }
 
+// The watchdog words (energy, reference, growth limit, flag) and the error words reset in one
+// launch: values travel as kernel arguments, so no host buffer outlives the call.
+__global__ void k_rearm(double* wd, double growth, int* p_err, unsigned* tb_err) {
+    if (threadIdx.x != 0) return;
+    wd[0] = 0.0;
+    wd[1] = 0.0;
+    wd[2] = growth;
+    wd[3] = 0.0;
+    if (p_err) *p_err = 0;
+    if (tb_err) *tb_err = 0u;
+}
+
+__global__ void k_put_step(long long* step, long long v) {
+    if (threadIdx.x == 0) *step = v;
+}
+
 // Re-arm the watchdog and the error words after new fields are written.
 int rearm(ue_mesh* m, cudaStream_t s) {
-    const double w0[4] = {0.0, 0.0, m->watchdog_growth, 0.0};
-    UE_CUDA(cudaMemcpyAsync(m->wd, w0, sizeof(w0), cudaMemcpyHostToDevice, s));
     m->since_check = 0;
-    if (m->p_err) UE_CUDA(cudaMemsetAsync(m->p_err, 0, 4, s));
-    if (m->variant == UE_VARIANT_BLOCKED && m->tb.done) UE_CUDA(cudaMemsetAsync(m->tb.done + 1, 0, 4, s));
+    unsigned* tb_err = (m->variant == UE_VARIANT_BLOCKED && m->tb.done) ? m->tb.done + 1 : nullptr;
+    k_rearm<<<1, 32, 0, s>>>(m->wd, m->watchdog_growth, m->p_err, tb_err);
+    UE_CUDA(cudaGetLastError());
+    return UE_OK;
+}
+
+// A step counter set by ue_set_step reaches the device in the stream of the next call that
+// steps, ordered before its kernels.
+int flush_step(ue_mesh* m, cudaStream_t s) {
+    if (m->step_pending < 0) return UE_OK;
+    k_put_step<<<1, 32, 0, s>>>(m->dm.step, (long long)m->step_pending);
+    UE_CUDA(cudaGetLastError());
+    m->step_pending = -1;
     return UE_OK;
 }
 
 // Fields in the caller's numbering as float (the product's precision), for meshes without a
 // PML frame: in place when the arrays are pinned host memory, else through a device copy.
-int fields_f32(ue_mesh* m, float* E, float* B, float* j, bool write, cudaStream_t s) {
+// wd: where a read also copies the watchdog words, in the same stream before its one wait
+int fields_f32(ue_mesh* m, float* E, float* B, float* j, bool write, cudaStream_t s, double* wd = nullptr) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (m->dm.frame || m->fr.W > 0)
         return fail(UE_ERR_ARG, "a mesh with a PML frame exchanges its fields through ue_write_fields / ue_read_fields");
@@ -1074,6 +1101,7 @@ int fields_f32(ue_mesh* m, float* E, float* B, float* j, bool write, cudaStream_
             if (B) UE_CUDA(cudaMemcpyAsync(B, m->d_Bc, 4 * h.n_tris, cudaMemcpyDeviceToHost, s));
             if (j) UE_CUDA(cudaMemcpyAsync(j, m->d_Jc, 4 * h.n_edges, cudaMemcpyDeviceToHost, s));
         }
+        if (wd) UE_CUDA(cudaMemcpyAsync(wd, m->wd, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     UE_CUDA(cudaStreamSynchronize(s));
     return UE_OK;
@@ -1383,6 +1411,7 @@ int ue_geometry_build(ue_mesh* m, const ue_options* opt, void* stream) {
     UE_CUDA(cudaMemsetAsync(dm.U, 0, esz * (dm.n_ei_pad + (framed ? (m->fd.n_if + 3) / 4 * 4 : 0)), s));
     UE_CUDA(cudaMemsetAsync(dm.B, 0, esz * dm.n_t_pad, s));
     UE_CUDA(cudaMemsetAsync(dm.step, 0, 8, s));
+    m->step_pending = -1;
     if (m->variant == UE_VARIANT_BLOCKED) {
         int trc = upload_tiles(m, s);
         if (trc != UE_OK) return trc;
@@ -1731,10 +1760,9 @@ int ue_write_fields_f32(ue_mesh* m, const float* E, const float* B, const float*
 
 int ue_read_fields_f32(ue_mesh* m, float* E, float* B, float* j, void* stream) {
     Range nvtx_range("ue_read_fields_f32");
-    int rc = fields_f32(m, E, B, j, false, (cudaStream_t)stream);
-    if (rc != UE_OK) return rc;
     double wd[4];
-    UE_CUDA(cudaMemcpy(wd, m->wd, sizeof(wd), cudaMemcpyDeviceToHost));
+    int rc = fields_f32(m, E, B, j, false, (cudaStream_t)stream, wd);
+    if (rc != UE_OK) return rc;
     if (wd[3] != 0.0)
         return fail(UE_ERR_UNSTABLE, std::string("energy watchdog: ") +
                                          (wd[3] == 1.0 ? "non-finite energy" : "energy growth beyond the limit"));
@@ -1762,6 +1790,10 @@ int ue_step_n(ue_mesh* m, int64_t n, void* stream) {
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 0) return fail(UE_ERR_ARG, "n_steps < 0");
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        const int rc = flush_step(m, s);
+        if (rc != UE_OK) return rc;
+    }
     int64_t left = n;
     if (m->variant == UE_VARIANT_PERSISTENT) {
         int64_t launched = 0;
@@ -1957,6 +1989,10 @@ int ue_check(ue_mesh* m, double* W, int32_t* flag) {
 
 int ue_get_step(const ue_mesh* m, int64_t* step) {
     if (!m || !m->built || !step) return fail(UE_ERR_ARG, "geometry not built or NULL output");
+    if (m->step_pending >= 0) {   // set and not stepped since
+        *step = m->step_pending;
+        return UE_OK;
+    }
     long long v = 0;
     UE_CUDA(cudaMemcpy(&v, m->dm.step, 8, cudaMemcpyDeviceToHost));
     *step = v;
@@ -1965,8 +2001,7 @@ int ue_get_step(const ue_mesh* m, int64_t* step) {
 
 int ue_set_step(ue_mesh* m, int64_t step) {
     if (!m || !m->built || step < 0) return fail(UE_ERR_ARG, "geometry not built or step < 0");
-    long long v = step;
-    UE_CUDA(cudaMemcpy(m->dm.step, &v, 8, cudaMemcpyHostToDevice));
+    m->step_pending = step;
     m->steps_done = 0;
     return UE_OK;
 }
@@ -2263,6 +2298,10 @@ int ue_profile_steps(ue_mesh* m, int64_t n, void* stream, double* ms, double* by
     if (!m || !m->built) return fail(UE_ERR_ARG, "geometry not built");
     if (n < 1 || n > 4096 || !ms) return fail(UE_ERR_ARG, "n_steps must be in 1..4096 and ms non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        const int frc = flush_step(m, s);
+        if (frc != UE_OK) return frc;
+    }
     const bool blocked = m->variant == UE_VARIANT_BLOCKED;
     // events: plain step i = [gtab | E half-step | B half-step] at 4i..4i+3;
     // blocked launch i = [g table (untimed) ... | k_tb] at 4i+1..4i+2
