@@ -176,6 +176,26 @@ def test_checkpoint_resume_is_bit_identical(ue):
     assert np.array_equal(Ea, Ec) and np.array_equal(Ba, Bc) and np.array_equal(Ja, Jc)
 
 
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_set_step_reaches_the_next_stepping_call(ue, variant):
+    """ue_set_step is recorded on the host and written to the device counter by the next
+    stepping call: get_step reads it back before any step, and after n steps it has advanced
+    by n; a second set before stepping replaces the first."""
+    ms, ops, w0, dens, ids, amp = _plasma_case()
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY_RINGS, tile_tris=300)
+    code = ue.UE_VARIANT_BLOCKED if variant == "blocked" else ue.UE_VARIANT_PLAIN
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=1e-6, variant=code, block_depth=4)
+    assert m.get_step() == 0
+    m.set_step(1000)
+    m.set_step(123)
+    assert m.get_step() == 123
+    m.step_n(7)
+    assert m.get_step() == 130
+    m.step_n(0)
+    assert m.get_step() == 130
+    m.close()
+
+
 def test_non_delaunay_mesh_is_rejected(ue):
     # a quad split along its long diagonal: the two opposite angles sum to more than pi
     xy = np.array([[0, 0], [2, 0], [2.2, 1], [0.2, 1]], float) * [1, 0.3]
