@@ -8,6 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libue.so")
 
 UE_OK = 0
+UE_ERR_ARG = -1
 UE_ERR = {-1: "UE_ERR_ARG", -2: "UE_ERR_NONMANIFOLD", -3: "UE_ERR_DEGENERATE", -4: "UE_ERR_DUAL",
           -5: "UE_ERR_CUDA", -6: "UE_ERR_ALLOC", -7: "UE_ERR_UNSTABLE", -8: "UE_ERR_TIMEOUT"}
 UE_REORDER_NONE, UE_REORDER_RCM, UE_REORDER_KD, UE_REORDER_GREEDY, UE_REORDER_GREEDY_RINGS = 0, 1, 2, 3, 4

@@ -33,6 +33,7 @@ DEFAULT_CANDIDATES = (
     ("blocked", "kd", 2048, 8, 1024),
     ("blocked", "greedy", 2500, 8, 512),
     ("blocked", "rings", 2500, 8, 512),
+    ("blocked", "rings", 2500, 10, 512),
 )
 
 TILERS = {"kd": N.UE_REORDER_KD, "greedy": N.UE_REORDER_GREEDY, "rings": N.UE_REORDER_GREEDY_RINGS}
@@ -106,14 +107,24 @@ def autotune_batch(items, candidates=DEFAULT_CANDIDATES, sample: int = 32, steps
         meshes = [Mesh(ms.xy, ms.tris, reorder=TILERS[tiler], tile_tris=tile) for ms, *_ in sub]
         try:
             for variant, _, _, depth, threads in cands:
-                rate = time_batch(sub, variant, tile, depth, threads, steps=steps, stream=stream,
-                                  meshes=meshes, tiler=tiler)
-                table.append(dict(variant=variant, tiler=tiler, tile_tris=tile, block_depth=depth,
-                                  tb_threads=threads, rate=rate))
+                row = dict(variant=variant, tiler=tiler, tile_tris=tile, block_depth=depth, tb_threads=threads)
+                try:
+                    row["rate"] = time_batch(sub, variant, tile, depth, threads, steps=steps, stream=stream,
+                                             meshes=meshes, tiler=tiler)
+                except N.UEError as e:
+                    # a configuration the library refuses for these meshes (a tile with its halo
+                    # beyond the blocked kernel's capacity): recorded, not chosen
+                    if e.code != N.UE_ERR_ARG:
+                        raise
+                    row["rate"], row["refused"] = 0.0, str(e)
+                table.append(row)
         finally:
             for m in meshes:
                 m.close()
-    best = max(table, key=lambda r: r["rate"])
+    usable = [r for r in table if "refused" not in r]
+    if not usable:
+        raise ValueError("autotune_batch: the library refused every candidate for these meshes")
+    best = max(usable, key=lambda r: r["rate"])
     return dict(best), {"rows": table, "sample_meshes": len(sub),
                         "sample_tris": int(sum(ms.n_tris for ms, *_ in sub)),
                         "seconds": time.perf_counter() - t0}

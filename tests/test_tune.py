@@ -21,6 +21,36 @@ def test_candidates_are_valid_launch_forms():
         assert depth >= 1 and (variant == "blocked" or depth == 1)
 
 
+def test_autotune_skips_a_refused_configuration(monkeypatch):
+    """A candidate the library refuses with UE_ERR_ARG (a tile with its halo too large for the
+    blocked kernel) is recorded as refused and never chosen; other errors propagate (host only:
+    the timing is replaced by a stand-in)."""
+    import meshgen
+    from paper_1812_01448_gb300 import _native as N
+    items = []
+    for sp in meshgen.batch_specs(3, seed=78, n_min=600, n_max=1500):
+        ms = meshgen.batch_mesh(sp)
+        items.append((ms, None, None, sp["omega0"]))
+
+    def fake_time(sub, variant, tile, depth, threads, **kw):
+        if depth == 10:
+            raise N.UEError(N.UE_ERR_ARG, "ue_geometry_build")
+        return 1e9 * depth
+    monkeypatch.setattr(tune, "time_batch", fake_time)
+    cands = (("blocked", "rings", 300, 4, 512), ("blocked", "rings", 300, 10, 512),
+             ("blocked", "rings", 300, 8, 512))
+    best, table = tune.autotune_batch(items, candidates=cands, sample=3)
+    assert best["block_depth"] == 8 and best["rate"] == 8e9
+    refused = [r for r in table["rows"] if "refused" in r]
+    assert len(refused) == 1 and refused[0]["block_depth"] == 10 and refused[0]["rate"] == 0.0
+
+    def broken(*a, **kw):
+        raise N.UEError(-5, "ue_step_n")
+    monkeypatch.setattr(tune, "time_batch", broken)
+    with pytest.raises(N.UEError):
+        tune.autotune_batch(items, candidates=cands[:1], sample=3)
+
+
 @pytest.mark.gpu
 def test_autotune_picks_a_measured_candidate():
     torch = pytest.importorskip("torch")
