@@ -497,6 +497,10 @@ def run_native(args):
                                  source=lf.Source(ids, amp, w0, t0, tau))
         cpu = cpu_baseline_line(rates, "the full mesh")
 
+    # steps per replay of the captured graph: whole blocked launches, an even number of them
+    # (the field buffers swap each launch), as ue_step_n forms them from graph_chunk
+    kd = args.block_depth
+    graph_steps = (2 * max(1, args.graph_chunk // (2 * kd)) * kd) if blocked else args.graph_chunk
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -507,7 +511,7 @@ def run_native(args):
                        "n_edges": m.n_edges, "dt": dt, "rho": rho,
                        "variant": (f"blocked k={args.block_depth} {args.tiler} tiles<={args.tile_tris} "
                                 f"threads={args.tb_threads or 512} {args.tb_kernel} kernel" if blocked
-                                else args.variant) + f", CUDA graph chunk {args.graph_chunk} steps",
+                                else args.variant) + f", CUDA graph chunk {graph_steps} steps",
                        "l2": (f"working set {step_bytes / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2; no flush"
                               if step_bytes > L2_BYTES else
                               f"working set {step_bytes / 1e6:.0f} MB per step < {L2_BYTES / 1e6:.0f} MB L2: "
