@@ -242,6 +242,42 @@ def test_full_size_scatterer_window(ue, scatterer_window, variant):
     assert iE <= 1e-4 and iB <= 1e-4 and iS <= 1e-4
 
 
+@pytest.mark.slow
+def test_full_size_plasma_window(ue):
+    """plasma-1M in the bench's launch configuration (ring-ordered greedy tiles <= 2700, k = 8,
+    the one-CTA-per-tile kernel) against the oracle on the whole mesh over a 200-step window
+    from step 5000 (source mid-pulse, current growing): relative L2 of E, B and j, and per
+    element the largest error against each field's largest value."""
+    ms = meshgen.cached("plasma_1003", meshgen.plasma_square_mesh)
+    ops = _oracle(ms)
+    w0 = 2 * math.pi * 20
+    dens = meshgen.plasma_density_nodes(ms.xy, w0)
+    ids, amp = meshgen.source_line_amplitudes(ms.xy, ms.tris, 0.35, ms.h)
+    rho, _ = spectral.power_iteration(ops, 200)
+    pl = lf.Plasma(dens, 0.01 * w0)
+    dt = spectral.stable_dt(rho, 0.5, pl.nbar(ops).max())
+    st = lf.initial_state(ops)
+    st.n = 5000
+    st = lf.run(ops, st, dt, 200, plasma=pl, source=lf.Source(ids, amp, w0, 0.1, 0.05))
+    Eo, Bo, Jo = ops.extend(st.E), st.B, ops.extend(st.j)
+    m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_GREEDY_RINGS, tile_tris=2700)
+    m.geometry_build(dt_mode=ue.UE_DT_GIVEN, dt=dt, variant=ue.UE_VARIANT_BLOCKED, block_depth=8)
+    m.set_plasma(dens, 0.01 * w0)
+    m.set_source(ids, amp, w0, 0.1, 0.05)
+    assert m.stats()["tb_kernel_used"] == 1
+    m.set_step(5000)
+    m.step_prepare()
+    m.step_n(200)
+    E, B, J = m.read_fields(j=True)
+    m.close()
+    assert np.linalg.norm(Bo) > 0 and np.linalg.norm(Jo) > 0
+    errs = [rel_l2(E, Eo), rel_l2(B, Bo), rel_l2(J, Jo)]
+    maxe = [float(np.abs(x - y).max() / np.abs(y).max()) for x, y in ((E, Eo), (B, Bo), (J, Jo))]
+    print(f"plasma-1M n_t={ms.n_tris} 200 steps: rel L2 E {errs[0]:.2e} B {errs[1]:.2e} j {errs[2]:.2e}; "
+          f"max per element {maxe[0]:.2e} {maxe[1]:.2e} {maxe[2]:.2e}")
+    assert max(errs) <= 1e-4 and max(maxe) <= 1e-4
+
+
 def _run_variant(ue, ms, dt, nsteps, variant, tile, k, dens=None, nu=0.0, src=None, graph_chunk=0,
                  B0=None, threads=0, reorder=None, kernel=0, expect_kernel=None):
     m = ue.Mesh(ms.xy, ms.tris, reorder=ue.UE_REORDER_KD if reorder is None else reorder,
