@@ -174,3 +174,21 @@ def test_cavity_TE_frequency_converges(m, n):
         errs.append(abs(w - exact) / exact)
     assert errs[0] < 0.02
     assert errs[2] < errs[0] / 3
+
+
+def test_splitmix64_published_sequence():
+    """SplitMix64 as in S. Vigna's reference generator splitmix64.c (the SplitMix scheme of
+    Steele, Lea and Flood, OOPSLA 2014, with D. Stafford's Mix13 finaliser) from state 0 gives
+    the published outputs 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f, 0xf88bb8a8724c81ec; the
+    state advances by the golden-ratio increment between outputs.  The vectorised start vector
+    draws the same numbers (entry k of seed s is the output for state s * 2^32 + k)."""
+    golden, m64 = 0x9E3779B97F4A7C15, (1 << 64) - 1
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    x = 0
+    for w in want:
+        assert spectral.splitmix64(x) == w
+        x = (x + golden) & m64
+    seed, n = 7, 64
+    v = spectral.start_vector(n, seed)
+    ref = np.array([(spectral.splitmix64((seed << 32) + k) >> 11) * 2.0 ** -53 * 2.0 - 1.0 for k in range(n)])
+    assert np.array_equal(v, ref)
