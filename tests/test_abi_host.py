@@ -529,3 +529,24 @@ def test_power_iteration_static_checks_its_tensors_before_the_library(ue, bad):
         msg = "must be a CUDA tensor"
     with pytest.raises(ValueError, match=msg):
         ue.power_iteration_static(**a)
+
+
+def test_stepping_calls_refuse_a_mesh_without_geometry(ue):
+    """Before ue_geometry_build the stepping calls and the step counter return UE_ERR_ARG with a
+    text, touching no device state (runs without a GPU): ue_step_n, ue_step_prepare,
+    ue_set_step, ue_get_step."""
+    import ctypes as C
+    import meshgen
+    from paper_1812_01448_gb300 import _native as N
+    ms = meshgen.cavity_te11_mesh()
+    m = ue.Mesh(ms.xy, ms.tris)
+    L = N.lib()
+    step = C.c_int64(-1)
+    try:
+        for rc in (L.ue_step_n(m._h, 5, None), L.ue_step_prepare(m._h, None), L.ue_set_step(m._h, 3),
+                   L.ue_get_step(m._h, C.byref(step))):
+            assert rc == N.UE_ERR_ARG
+            assert b"geometry not built" in L.ue_last_error()
+        assert step.value == -1
+    finally:
+        m.close()
